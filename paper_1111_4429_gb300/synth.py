@@ -1,0 +1,188 @@
+"""Seeded synthetic inputs for the RPA epsilon path.
+
+This module only *generates inputs*: integer G-vector lists on cutoff spheres,
+orthonormal random plane-wave coefficients, sorted band energies, frequency
+grids and request streams.  It holds none of the method's arithmetic (no
+matrix elements, no polarizability, no Coulomb factor, no inversion), so both
+the CPU oracle (through the tests) and the CUDA path can consume the same
+arrays.
+
+Conventions (BerkeleyGW paper, Appendix "Specification of file formats"):
+G vectors are integer triples in reciprocal-lattice units, listed as a full
+sphere; coefficients of each band are normalized so that the sum of their
+squared magnitudes is one.  Cutoffs are in Rydberg, i.e. |k|^2 in bohr^-2.
+Energies are in Hartree.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+# Sub-seed order for one system (one base seed per configuration):
+# valence coefficients, conduction coefficients, E_v, E_c, subblock, arrivals.
+_STREAMS = ("cv", "cc", "ev", "ec", "subblock", "arrivals")
+
+
+def cubic_cell(a: float):
+    """Simple cubic cell of side a (bohr): reciprocal vectors (rows, bohr^-1) and volume."""
+    b = 2.0 * math.pi / a
+    bvec = np.eye(3) * b
+    return bvec, a ** 3
+
+
+def gsphere(bvec: np.ndarray, kfrac: Sequence[float], ecut: float) -> np.ndarray:
+    """All integer G with |(G + k) . B|^2 < ecut (strict, FP64).
+
+    Ordered by |(G+k)B|^2 ascending, ties broken lexicographically on
+    (Gx, Gy, Gz).  Returns int32 [n][3].
+    """
+    bvec = np.asarray(bvec, dtype=np.float64)
+    kf = np.asarray(kfrac, dtype=np.float64)
+    radius = math.sqrt(ecut)
+    # Bound each integer component: |G_i + k_i| <= radius * |a_i| / 2pi where
+    # a_i is the real-space vector dual to b_i.  Use the inverse of B.
+    binv = np.linalg.inv(bvec)  # columns: a_i / (2 pi) ... rows of B^-1
+    lim = [int(math.ceil(radius * np.linalg.norm(binv[:, i]) + abs(kf[i]))) + 1 for i in range(3)]
+    rng = [np.arange(-l, l + 1) for l in lim]
+    gx, gy, gz = np.meshgrid(*rng, indexing="ij")
+    g = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1)
+    kc = (g + kf) @ bvec
+    e = np.einsum("ij,ij->i", kc, kc)
+    keep = e < ecut
+    g, e = g[keep], e[keep]
+    order = np.lexsort((g[:, 2], g[:, 1], g[:, 0], e))
+    return np.ascontiguousarray(g[order].astype(np.int32))
+
+
+def orthonormal_bands(gen: np.random.Generator, npw: int, nb: int) -> np.ndarray:
+    """nb orthonormal coefficient vectors of length npw, band-major [nb][npw].
+
+    Real and imaginary parts are i.i.d. N(0,1); the reduced QR of the
+    [npw x nb] matrix gives the bands as Q's columns.
+    """
+    if nb > npw:
+        raise ValueError(f"cannot orthonormalize {nb} bands on {npw} plane waves")
+    a = gen.standard_normal((npw, nb)) + 1j * gen.standard_normal((npw, nb))
+    q, _ = np.linalg.qr(a)
+    return np.ascontiguousarray(q.T.astype(np.complex128))
+
+
+def gauss_legendre_frequencies(nfreq: int, lo: float = 0.0, hi: float = 2.0) -> np.ndarray:
+    """nfreq Gauss-Legendre nodes mapped linearly from [-1, 1] to [lo, hi] (Ha)."""
+    x, _ = np.polynomial.legendre.leggauss(nfreq)
+    return (lo + (x + 1.0) * 0.5 * (hi - lo)).astype(np.float64)
+
+
+@dataclasses.dataclass
+class System:
+    """One q-point problem: everything bgw_mtxel/bgw_chi_sum/bgw_epsinv consume."""
+    name: str
+    a: float
+    bvec: np.ndarray      # [3][3] rows b1,b2,b3 (bohr^-1)
+    omega: float          # cell volume (bohr^3)
+    q_frac: np.ndarray    # [3] crystal coordinates
+    fft: int              # cubic FFT grid n
+    gv: np.ndarray        # int32 [npw_v][3] valence sphere (|q+G|^2 < ecut_wfn)
+    gc: np.ndarray        # int32 [npw_c][3] conduction sphere (|G|^2 < ecut_wfn)
+    geps: np.ndarray      # int32 [ng][3] epsilon sphere (|q+G|^2 < ecut_eps)
+    cv: np.ndarray        # complex128 [nv][npw_v]
+    cc: np.ndarray        # complex128 [nc][npw_c]
+    ev: np.ndarray        # float64 [nv] Ha, ascending
+    ec: np.ndarray        # float64 [nc] Ha, ascending
+    seed: int = 0
+
+    @property
+    def nv(self):
+        return self.cv.shape[0]
+
+    @property
+    def nc(self):
+        return self.cc.shape[0]
+
+    @property
+    def ng(self):
+        return self.geps.shape[0]
+
+    @property
+    def npairs(self):
+        return self.nv * self.nc
+
+
+def make_system(name: str, a: float, fft: int, ecut_wfn: float, ecut_eps: float,
+                nv: int, nc: int, seed: int, q_frac=(0.1, 0.0, 0.0),
+                ev_range=(-0.5, 0.0), ec_range=(0.04, 1.5)) -> System:
+    """Build one seeded system with the recipe of the benchmark configurations."""
+    bvec, omega = cubic_cell(a)
+    q = np.asarray(q_frac, dtype=np.float64)
+    gv = gsphere(bvec, q, ecut_wfn)
+    gc = gsphere(bvec, (0.0, 0.0, 0.0), ecut_wfn)
+    geps = gsphere(bvec, q, ecut_eps)
+    ss = np.random.SeedSequence(seed).spawn(len(_STREAMS))
+    gens = {k: np.random.Generator(np.random.PCG64(s)) for k, s in zip(_STREAMS, ss)}
+    cv = orthonormal_bands(gens["cv"], gv.shape[0], nv)
+    cc = orthonormal_bands(gens["cc"], gc.shape[0], nc)
+    ev = np.sort(gens["ev"].uniform(ev_range[0], ev_range[1], nv))
+    ec = np.sort(gens["ec"].uniform(ec_range[0], ec_range[1], nc))
+    return System(name=name, a=a, bvec=bvec, omega=omega, q_frac=q, fft=fft, gv=gv, gc=gc,
+                  geps=geps, cv=cv, cc=cc, ev=ev, ec=ec, seed=seed)
+
+
+# Benchmark configurations: plain FP64 oracle-sized (c0), plain FP64 larger cell
+# (c1), mixed-precision large cell (c2).  Base seeds are fixed per configuration.
+CONFIGS: Dict[str, dict] = {
+    "c0": dict(a=10.26, fft=20, ecut_wfn=10.0, ecut_eps=3.0, nv=4, nc=60, seed=1000),
+    "c1": dict(a=20.52, fft=40, ecut_wfn=12.0, ecut_eps=6.0, nv=32, nc=800, seed=1001),
+    "c2": dict(a=30.78, fft=60, ecut_wfn=12.0, ecut_eps=6.0, nv=108, nc=3000, seed=1002),
+}
+
+
+def config_system(name: str, **overrides) -> System:
+    p = dict(CONFIGS[name])
+    p.update(overrides)
+    return make_system(name, **p)
+
+
+def batched_q_systems(nq: int = 8, seed: int = 1003) -> List[System]:
+    """The c1 cell at q = (0.05 j, 0, 0), j = 1..nq: uneven epsilon spheres."""
+    out = []
+    for j in range(1, nq + 1):
+        out.append(make_system(f"c3_q{j}", a=20.52, fft=40, ecut_wfn=12.0, ecut_eps=6.0,
+                               nv=32, nc=800, seed=seed + j, q_frac=(0.05 * j, 0.0, 0.0)))
+    return out
+
+
+def subblock_indices(ng: int, size: int, seed: int) -> np.ndarray:
+    """Seeded principal-subblock indices (distinct, sorted)."""
+    ss = np.random.SeedSequence(seed).spawn(len(_STREAMS))
+    gen = np.random.Generator(np.random.PCG64(ss[_STREAMS.index("subblock")]))
+    return np.sort(gen.permutation(ng)[:size])
+
+
+def serve_requests(n: int = 200, seed: int = 1004):
+    """Request mix of the served stream: scale s, eps cutoff, band counts.
+
+    N_c is drawn uniform in [50, 1500] and clamped to the number of conduction
+    plane waves available at the 10 Ry wavefunction cutoff.
+    """
+    gen = np.random.Generator(np.random.PCG64(seed))
+    reqs = []
+    for i in range(n):
+        s = int(gen.integers(1, 4))
+        e = float(gen.choice([3.0, 4.0, 6.0]))
+        nc_draw = int(gen.integers(50, 1501))
+        reqs.append(dict(index=i, s=s, ecut_eps=e, nv=4 * s ** 3, nc_draw=nc_draw,
+                         seed=seed * 1000 + i))
+    return reqs
+
+
+def request_system(req: dict) -> System:
+    s = req["s"]
+    a = 10.26 * s
+    bvec, _ = cubic_cell(a)
+    npw_c = gsphere(bvec, (0, 0, 0), 10.0).shape[0]
+    nc = min(req["nc_draw"], npw_c)
+    return make_system(f"req{req['index']}", a=a, fft=20 * s, ecut_wfn=10.0,
+                       ecut_eps=req["ecut_eps"], nv=req["nv"], nc=nc, seed=req["seed"])

@@ -1,0 +1,310 @@
+"""Pins for the CPU oracle: closed forms, invariants and brute force.
+
+The paper prints no numeric chi or eps^-1 values (its figures are
+placeholders), so the oracle is pinned by mathematics: each test below fails
+for a plausible mistake (a dropped conjugate, a wrong FFT sign or scale, a
+missing 4/Omega, a transposed operand, v in place of v^{1/2}, a wrong pair
+order or a wrong frequency weight).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1111_4429_gb300 import synth
+
+
+def _tiny(seed=7, a=8.0, n=12, ew=4.0, ee=1.5, nv=3, nc=5, q=(0.1, 0.0, 0.0)):
+    return synth.make_system("tiny", a=a, fft=n, ecut_wfn=ew, ecut_eps=ee, nv=nv, nc=nc,
+                             seed=seed, q_frac=q)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+# --------------------------------------------------------------------- spheres
+
+def test_gsphere_strict_cutoff_and_order():
+    bvec, _ = synth.cubic_cell(10.26)
+    g = synth.gsphere(bvec, (0.1, 0, 0), 3.0)
+    k = (g + np.array([0.1, 0, 0])) @ bvec
+    e = np.einsum("ij,ij->i", k, k)
+    assert np.all(e < 3.0)
+    assert np.all(np.diff(e) >= -1e-15)
+    # brute-force count over a generous box
+    r = np.arange(-8, 9)
+    gx, gy, gz = np.meshgrid(r, r, r, indexing="ij")
+    allg = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], 1)
+    ka = (allg + np.array([0.1, 0, 0])) @ bvec
+    assert g.shape[0] == int(np.sum(np.einsum("ij,ij->i", ka, ka) < 3.0)) == 85
+    assert len({tuple(x) for x in g.tolist()}) == g.shape[0]
+
+
+def test_config_sphere_sizes():
+    for name, ng, npw_c, npw_v in [("c0", 85, 587, 583), ("c1", 2120, 6031, 6059)]:
+        p = synth.CONFIGS[name]
+        bvec, _ = synth.cubic_cell(p["a"])
+        assert synth.gsphere(bvec, (0.1, 0, 0), p["ecut_eps"]).shape[0] == ng
+        assert synth.gsphere(bvec, (0, 0, 0), p["ecut_wfn"]).shape[0] == npw_c
+        assert synth.gsphere(bvec, (0.1, 0, 0), p["ecut_wfn"]).shape[0] == npw_v
+
+
+def test_bands_orthonormal():
+    s = _tiny()
+    for c in (s.cv, s.cc):
+        assert np.allclose(c @ np.conj(c).T, np.eye(c.shape[0]), atol=1e-13)
+
+
+def test_gauss_legendre_nodes_closed_form():
+    # 2-point nodes +-1/sqrt(3), 3-point 0, +-sqrt(3/5), mapped from [-1,1] to [0,2]
+    assert np.allclose(synth.gauss_legendre_frequencies(2), 1.0 + np.array([-1, 1]) / math.sqrt(3))
+    assert np.allclose(synth.gauss_legendre_frequencies(3), 1.0 + np.array([-1, 0, 1]) * math.sqrt(0.6))
+    w12 = synth.gauss_legendre_frequencies(12)
+    assert abs(w12[0] - 0.018439365753281) < 1e-12 and abs(w12[-1] - 1.981560634246719) < 1e-12
+
+
+# ---------------------------------------------------------------- matrix elements
+
+def test_mtxel_direct_vs_fft_bruteforce():
+    for seed, n in [(1, 12), (2, 16)]:
+        s = _tiny(seed=seed, n=n)
+        m1 = oracle.mtxel_direct(s.gv, s.cv, s.gc, s.cc, s.geps)
+        m2 = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+        assert _rel(m2, m1) < 1e-13
+
+
+def test_mtxel_c0_direct_vs_fft():
+    s = synth.config_system("c0")
+    m1 = oracle.mtxel_direct(s.gv, s.cv, s.gc, s.cc, s.geps)
+    m2 = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    assert _rel(m2, m1) < 1e-13
+    assert np.abs(m1).max() <= 1.0 + 1e-12          # Cauchy-Schwarz, sum |c|^2 = 1
+
+
+def test_mtxel_fft_pairs_matches_full():
+    s = _tiny(seed=3)
+    full = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    pairs = [0, 4, 7, 14]
+    sub = oracle.mtxel_fft_pairs(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft, pairs)
+    assert np.allclose(sub, full[pairs], atol=1e-15)
+
+
+def _plane_wave_system(seed=5):
+    s = _tiny(seed=seed, nv=4, nc=6)
+    gen = np.random.default_rng(seed)
+    iv = gen.choice(s.gv.shape[0], s.nv, replace=False)
+    ic = gen.choice(s.gc.shape[0], s.nc, replace=False)
+    cv = np.zeros_like(s.cv)
+    cc = np.zeros_like(s.cc)
+    cv[np.arange(s.nv), iv] = 1.0
+    cc[np.arange(s.nc), ic] = 1.0
+    s.cv, s.cc = cv, cc
+    return s, iv, ic
+
+
+def test_mtxel_plane_wave_closed_form():
+    # c_v = e_{G_v}, c_c = e_{G_c}  =>  M_vc(G) = 1 iff G = G_v - G_c, else 0.
+    s, iv, ic = _plane_wave_system()
+    expect = np.zeros((s.nv * s.nc, s.ng))
+    gidx = {tuple(g): i for i, g in enumerate(s.geps.tolist())}
+    for v in range(s.nv):
+        for c in range(s.nc):
+            d = tuple((s.gv[iv[v]] - s.gc[ic[c]]).tolist())
+            if d in gidx:
+                expect[v * s.nc + c, gidx[d]] = 1.0
+    assert expect.sum() > 0
+    for m in (oracle.mtxel_direct(s.gv, s.cv, s.gc, s.cc, s.geps),
+              oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)):
+        assert np.allclose(m, expect, atol=1e-14)
+
+
+def test_mtxel_q0_joint_orthonormal_head_is_delta():
+    # q = 0, one sphere, jointly orthonormal bands: M_nn'(G=0) = <n|n'> = delta.
+    bvec, _ = synth.cubic_cell(8.0)
+    g = synth.gsphere(bvec, (0, 0, 0), 4.0)
+    c = synth.orthonormal_bands(np.random.default_rng(11), g.shape[0], 7)
+    geps = synth.gsphere(bvec, (0, 0, 0), 1.5)
+    assert tuple(geps[0]) == (0, 0, 0)
+    m = oracle.mtxel_fft(g, c, g, c, geps, 12).reshape(7, 7, -1)
+    assert np.allclose(m[:, :, 0], np.eye(7), atol=1e-13)
+    md = oracle.mtxel_direct(g, c, g, c, geps).reshape(7, 7, -1)
+    assert np.allclose(md[:, :, 0], np.eye(7), atol=1e-13)
+
+
+def test_mtxel_parseval_full_grid():
+    # Over every G of the grid: sum_G |F(G)|^2 = (1/N_r) sum_j |u_v u_c|^2.
+    s = _tiny(seed=9, n=10, ew=2.5)
+    n = s.fft
+    r = np.arange(-n // 2, n // 2)
+    gx, gy, gz = np.meshgrid(r, r, r, indexing="ij")
+    gall = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], 1).astype(np.int32)
+    m = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, gall, n)
+    uv = oracle.band_grids(s.gv, s.cv, n)
+    uc = oracle.band_grids(s.gc, s.cc, n)
+    for v in range(s.nv):
+        for c in range(s.nc):
+            lhs = np.sum(np.abs(m[v * s.nc + c]) ** 2)
+            rhs = np.sum(np.abs(np.conj(uv[v]) * uc[c]) ** 2) / n ** 3
+            assert abs(lhs - rhs) < 1e-12 * rhs
+
+
+def test_band_grid_normalization():
+    # sum_j |u_b(r_j)|^2 = N_r sum_G |c_b(G)|^2 = N_r (unnormalized inverse transform)
+    s = _tiny(seed=4)
+    u = oracle.band_grids(s.gc, s.cc, s.fft)
+    assert np.allclose(np.sum(np.abs(u) ** 2, axis=(1, 2, 3)), s.fft ** 3, rtol=1e-13)
+
+
+# -------------------------------------------------------------- polarizability
+
+def test_chi_weights_pair_order_and_values():
+    ev = np.array([-0.3, -0.1])
+    ec = np.array([0.2, 0.5, 0.9])
+    w = oracle.chi_weights(ev, ec)
+    assert np.allclose(w, [1 / (-0.5), 1 / (-0.8), 1 / (-1.2), 1 / (-0.3), 1 / (-0.6), 1 / (-1.0)])
+    wi = oracle.chi_weights(ev, ec, 0.7)
+    d = -0.5
+    assert abs(wi[0] - d / (d * d + 0.49)) < 1e-15
+    # the imaginary-axis weight is the average of the two time orderings
+    assert abs(wi[0] - 0.5 * (1 / (d - 0.7j) + 1 / (d + 0.7j)).real) < 1e-15
+
+
+def test_chi_hand_example_conjugation_side():
+    # One empty band c = e_0 and one occupied band v = (e_G1 + i e_G2)/sqrt(2):
+    # M(G) = conj(c_v(G)), so M(G1) = 1/sqrt2, M(G2) = -i/sqrt2 and
+    # chi_{G1 G2} = (4/Omega) w conj(M(G1)) M(G2) = -i (2/Omega) w.
+    g = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=np.int32)
+    gc = g[:1]
+    cc = np.array([[1.0 + 0j]])
+    cv = np.array([[0.0, 1.0, 1.0j]]) / math.sqrt(2.0)
+    geps = g[1:]
+    m = oracle.mtxel_direct(g, cv, gc, cc, geps)
+    assert np.allclose(m, [[1 / math.sqrt(2), -1j / math.sqrt(2)]])
+    mf = oracle.mtxel_fft(g, cv, gc, cc, geps, 6)
+    assert np.allclose(mf, m, atol=1e-15)
+    omega_cell, w = 100.0, np.array([-2.0])
+    x = oracle.chi(m, w, omega_cell)
+    assert np.allclose(x[0, 1], -1j * (2 / omega_cell) * w[0])
+    assert np.allclose(x[0, 0], (4 / omega_cell) * w[0] * 0.5)
+    assert np.allclose(oracle.chi_direct(m, w, omega_cell), x, atol=1e-15)
+
+
+def test_chi_tier1_vs_tier2_and_hermitian_nsd():
+    s = synth.config_system("c0")
+    m = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    w = oracle.chi_weights(s.ev, s.ec)
+    x1 = oracle.chi_direct(m, w, s.omega)
+    x2 = oracle.chi(m, w, s.omega)
+    assert _rel(x2, x1) < 1e-14
+    assert np.linalg.norm(x2 - np.conj(x2).T) < 1e-14 * np.linalg.norm(x2)
+    assert np.linalg.eigvalsh(x2).max() <= 1e-14 * np.abs(x2).max()
+    # trace identity: tr chi = (4/Omega) sum_p w_p ||M_p||^2
+    assert abs(np.trace(x2) - (4 / s.omega) * np.sum(w * np.sum(np.abs(m) ** 2, 1))) < 1e-13 * abs(np.trace(x2))
+
+
+def test_chi_plane_wave_closed_form_diagonal():
+    s, iv, ic = _plane_wave_system(seed=8)
+    m = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    w = oracle.chi_weights(s.ev, s.ec)
+    x = oracle.chi(m, w, s.omega)
+    expect = np.zeros((s.ng, s.ng), dtype=np.complex128)
+    gidx = {tuple(g): i for i, g in enumerate(s.geps.tolist())}
+    for v in range(s.nv):
+        for c in range(s.nc):
+            d = tuple((s.gv[iv[v]] - s.gc[ic[c]]).tolist())
+            if d in gidx:
+                expect[gidx[d], gidx[d]] += (4 / s.omega) / (s.ev[v] - s.ec[c])
+    assert np.allclose(x, expect, atol=1e-14)
+
+
+# --------------------------------------------------------- dielectric matrix
+
+def test_coulomb_closed_form():
+    bvec, _ = synth.cubic_cell(10.26)
+    b = 2 * math.pi / 10.26
+    geps = np.array([[0, 0, 0], [1, 0, 0], [0, -1, 2]], dtype=np.int32)
+    v = oracle.coulomb(bvec, (0.1, 0, 0), geps)
+    expect = [4 * math.pi / (0.1 * b) ** 2, 4 * math.pi / (1.1 * b) ** 2,
+              4 * math.pi / ((0.01 + 1 + 4) * b * b)]
+    assert np.allclose(v, expect, rtol=1e-15)
+    with pytest.raises(ValueError):
+        oracle.coulomb(bvec, (0, 0, 0), geps)
+
+
+def test_gauss_jordan_closed_forms_and_pivoting():
+    a = np.array([[2.0 + 1j, 1.0], [3.0, 4.0 - 2j]])
+    det = a[0, 0] * a[1, 1] - a[0, 1] * a[1, 0]
+    expect = np.array([[a[1, 1], -a[0, 1]], [-a[1, 0], a[0, 0]]]) / det
+    assert np.allclose(oracle.inv_gauss_jordan(a), expect, atol=1e-15)
+    perm = np.array([[0.0, 1.0, 0.0], [0.0, 0.0, 2.0], [4.0, 0.0, 0.0]])  # zero leading pivot
+    assert np.allclose(oracle.inv_gauss_jordan(perm) @ perm, np.eye(3), atol=1e-15)
+    r = np.random.default_rng(0)
+    b = r.standard_normal((40, 40)) + 1j * r.standard_normal((40, 40))
+    assert _rel(oracle.inv_gauss_jordan(b), np.linalg.inv(b)) < 1e-12
+
+
+def test_eps_spectrum_and_inverse_c0():
+    s = synth.config_system("c0")
+    r = oracle.solve(s, tier=2)
+    e, ei = r["eps"], r["epsinv"]
+    assert np.linalg.norm(e - np.conj(e).T) < 1e-14 * np.linalg.norm(e)
+    assert np.linalg.eigvalsh(e).min() >= 1.0 - 1e-12
+    lam = np.linalg.eigvalsh(0.5 * (ei + np.conj(ei).T))
+    assert lam.min() > 0 and lam.max() <= 1.0 + 1e-12
+    assert np.linalg.norm(e @ ei - np.eye(s.ng)) / math.sqrt(s.ng) < 1e-13
+    assert _rel(oracle.inv_gauss_jordan(e), ei) < 1e-13
+
+
+def test_eps_symmetric_vs_asymmetric_route_and_w_hermitian():
+    s = synth.config_system("c0")
+    r = oracle.solve(s)
+    v = r["v"]
+    ea = oracle.eps_asym(r["chi"], v)
+    eia = oracle.inv(ea)
+    sv = np.sqrt(v)
+    # eps^-1 (paper's asymmetric) = V^{1/2} eps~^-1 V^{-1/2}
+    assert _rel(sv[:, None] * r["epsinv"] / sv[None, :], eia) < 1e-13
+    w = oracle.screened_w(eia, v)
+    assert np.linalg.norm(w - np.conj(w).T) < 1e-12 * np.linalg.norm(w)
+
+
+def test_eps_plane_wave_closed_form_diagonal():
+    s, _, _ = _plane_wave_system(seed=12)
+    r = oracle.solve(s)
+    x = np.diag(r["chi"]).real
+    expect = 1.0 / (1.0 - r["v"] * x)
+    assert np.allclose(r["epsinv"], np.diag(expect), atol=1e-14)
+
+
+def test_tier1_whole_chain_matches_tier2():
+    s = _tiny(seed=21, nv=3, nc=7)
+    r1 = oracle.solve(s, tier=1)
+    r2 = oracle.solve(s, tier=2)
+    for k in ("M", "chi", "eps", "epsinv"):
+        assert _rel(r2[k], r1[k]) < 1e-13, k
+
+
+# ------------------------------------------------------------ imaginary axis
+
+def test_imaginary_frequency_limits_and_monotonicity():
+    s = synth.config_system("c0")
+    m = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    v = oracle.coulomb(s.bvec, s.q_frac, s.geps)
+    x0 = oracle.chi(m, oracle.chi_weights(s.ev, s.ec), s.omega)
+    xw0 = oracle.chi(m, oracle.chi_weights(s.ev, s.ec, 0.0), s.omega)
+    assert _rel(xw0, x0) < 1e-15
+    prev_x, prev_ei = None, None
+    for om in synth.gauss_legendre_frequencies(4):
+        x = oracle.chi(m, oracle.chi_weights(s.ev, s.ec, om), s.omega)
+        _, ei = oracle.epsinv_sym(x, v)
+        if prev_x is not None:
+            # chi(i w1) <= chi(i w2) <= 0 and eps~^-1(i w1) <= eps~^-1(i w2) <= I (Loewner)
+            assert np.linalg.eigvalsh(prev_x - x).max() <= 1e-14
+            assert np.linalg.eigvalsh(prev_ei - ei).max() <= 1e-12
+        assert np.linalg.eigvalsh(x).max() <= 1e-14
+        prev_x, prev_ei = x, 0.5 * (ei + np.conj(ei).T)
+    xinf = oracle.chi(m, oracle.chi_weights(s.ev, s.ec, 1e6), s.omega)
+    _, eiinf = oracle.epsinv_sym(xinf, v)
+    assert np.abs(eiinf - np.eye(s.ng)).max() < 1e-8
