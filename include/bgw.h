@@ -1,0 +1,189 @@
+/*
+ * bgw.h -- C ABI of the GB300 library for the RPA epsilon hot path of one
+ * q-point: plane-wave matrix elements, the Adler-Wiser polarizability chi,
+ * the symmetrized dielectric matrix eps~ and its inverse.
+ *
+ * Source of every operation: the BerkeleyGW paper, Section "RPA Dielectric
+ * Matrix: epsilon" (Eqs. eqn_matrix_elem, eqn_static_xi,
+ * eqn_static_xi_compact, epsilon, untruncated_bare_coulomb,
+ * screened_interaction, retarded_advanced_epsilon) and its Appendix
+ * "Specification of file formats" for the input conventions.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ *  - G vectors are int32 triples (x,y,z) in reciprocal-lattice units, listed
+ *    as full spheres (Appendix); components must lie in [-n/2, n/2) for the
+ *    FFT grid n.  G lists are HOST arrays (read during the call, copied into
+ *    a device-side plan cached by content).
+ *  - Wavefunction coefficients are band-major [nbands][npw] complex128
+ *    (interleaved re,im doubles), normalized to sum |c|^2 = 1 per band.
+ *  - The occupied (valence) band sits on the q-shifted sphere (k+q), the
+ *    empty (conduction) band at k = 0.  Pair index p = v * nc + c.
+ *  - Energies are in Hartree; cutoffs in Ry (|k|^2 in bohr^-2); v(q+G) =
+ *    4 pi / |q+G|^2 (Hartree atomic units).
+ *  - Complex outputs are row-major, interleaved.  c128 = 2 doubles,
+ *    c64 = 2 floats.
+ *  - Bulk arrays (coefficients, M, chi, eps) are DEVICE pointers owned by
+ *    the caller unless a call says otherwise; host arrays are marked "host".
+ *  - Every call enqueues its work on `stream` (a cudaStream_t passed as
+ *    void*; NULL = legacy default stream) and returns before the work is
+ *    done.  A context serves one host thread and one stream at a time:
+ *    its scratch memory is reused by the next call in stream order.
+ *  - Every call returns an int status (BGW_OK = 0).  Arguments are checked
+ *    before any launch, so nothing is written when a call returns
+ *    BGW_EINVAL.  Errors raised inside kernels (a zero or non-finite pivot)
+ *    are recorded in a device status word and returned by bgw_sync().
+ *    Outputs are undefined after any non-OK status.  bgw_last_error()
+ *    returns a message for the last failure.  No C++ exception crosses the
+ *    ABI.
+ */
+#ifndef BGW_H
+#define BGW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  BGW_OK = 0,
+  BGW_EINVAL = 1,    /* bad sizes/pointers, G outside [-n/2,n/2), aliasing,
+                        q+G = 0, unsorted energies, Delta >= 0           */
+  BGW_ENOMEM = 2,    /* over the context's HBM budget or allocation failed */
+  BGW_ECUDA = 3,     /* a CUDA runtime call failed                        */
+  BGW_ETIMEOUT = 4,  /* a bounded device wait gave up                     */
+  BGW_ENUMERIC = 5,  /* non-finite value or zero pivot in the inversion   */
+  BGW_EBUSY = 6,
+  BGW_ECANCELED = 7,
+  BGW_EUNSUPPORTED = 8 /* valid request outside what this build implements
+                          (e.g. an FFT grid size without a kernel)        */
+};
+
+/* Precision of a call.
+ *  BGW_PREC_FP64     : every step in FP64 / complex128 (the plain path).
+ *  BGW_PREC_MIX_FP16 : M in complex64 (FP32 FFTs); chi on the tensor cores
+ *                      as split FP16 (hi*hi + hi*lo + lo*hi) products with
+ *                      FP32 accumulation, flushed into an FP64 chi per call;
+ *                      eps~ and its inverse in FP64.
+ *  BGW_PREC_MIX_BF16 : as MIX_FP16 with BF16 splits.                      */
+enum { BGW_PREC_FP64 = 0, BGW_PREC_MIX_FP16 = 1, BGW_PREC_MIX_BF16 = 2 };
+
+typedef struct bgw_ctx bgw_ctx;
+
+/* Cell and q-point.  bvec rows are the reciprocal lattice vectors b1,b2,b3
+ * in bohr^-1 (Appendix: reciprocal lattice vectors); omega is the cell volume
+ * in bohr^3; q_frac is q in crystal coordinates; fft is the FFT grid.  This
+ * build requires a cubic grid fft[0] = fft[1] = fft[2] = n with n in
+ * {8,10,12,16,20,24,30,32,36,40,48,50,60,64}.                               */
+typedef struct bgw_cell {
+  double bvec[3][3];
+  double omega;
+  double q_frac[3];
+  int fft[3];
+} bgw_cell;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * device memory the library itself allocates (scratch, plans, cached
+ * uploads); 0 = no bound.  On success *ctx is owned by the caller and must
+ * be released with bgw_destroy.                                             */
+int bgw_create(bgw_ctx** ctx, int device, uint64_t hbm_budget_bytes);
+int bgw_destroy(bgw_ctx* ctx);
+
+/* Message for the last failing call on ctx (static storage inside ctx;
+ * valid until the next call).  Never NULL.                                  */
+const char* bgw_last_error(bgw_ctx* ctx);
+
+/* Wait for the work enqueued on `stream` and return (then clear) the device
+ * status word: BGW_OK, BGW_ENUMERIC or BGW_ETIMEOUT; BGW_ECUDA if the
+ * stream itself failed.                                                     */
+int bgw_sync(bgw_ctx* ctx, void* stream);
+
+/* Bytes the library currently holds on the device, and the high-water mark. */
+int bgw_mem_stats(bgw_ctx* ctx, uint64_t* in_use, uint64_t* high_water);
+
+/* ------------------------------------------------------------------------
+ * bgw_mtxel -- plane-wave matrix elements (Eq. eqn_matrix_elem), computed as
+ * the FFT of the real-space product of the two bands (paper's equation
+ * M = FFT^-1(phi*_{n,k+q}(r) phi_{n',k}(r))):
+ *   u_b(r_j)   = sum_G c_b(G) exp(+2 pi i G.j/n)
+ *   M[p][iG]   = (1/n^3) sum_j conj(u_v(r_j)) u_c(r_j) exp(+2 pi i G_iG.j/n)
+ *              = sum_{G2} conj(c_v(G_iG + G2)) c_c(G2)
+ *   gv   host int32 [npw_v][3]  valence (q-shifted) sphere
+ *   cv   device c128 [nv][npw_v]
+ *   gc   host int32 [npw_c][3]  conduction sphere
+ *   cc   device c128 [nc][npw_c]
+ *   geps host int32 [ng][3]     epsilon sphere (output order)
+ *   M    device, pair-major [nv*nc][ng]: c128 for BGW_PREC_FP64, c64 for
+ *        the mixed precisions.
+ * EINVAL when a G component lies outside [-n/2, n/2), when a list holds a
+ * duplicate G, or when the grid aliases: n <= max|Gv_d| + max|Gc_d| +
+ * max|Geps_d| on some axis d.                                              */
+int bgw_mtxel(bgw_ctx* ctx, const bgw_cell* cell,
+              int nv, int npw_v, const int32_t* gv, const void* cv,
+              int nc, int npw_c, const int32_t* gc, const void* cc,
+              int ng, const int32_t* geps, int prec, void* M, void* stream);
+
+/* ------------------------------------------------------------------------
+ * bgw_chi_sum -- polarizability (Eq. eqn_static_xi as the single matrix
+ * product of Eq. eqn_static_xi_compact):
+ *   chi_f[G][G'] (+)= (4/Omega) sum_p w_p(f) conj(M[p][G]) M[p][G']
+ *   static (nfreq = 0): w_p = 1/Delta_p, Delta_p = E_v - E_c < 0
+ *   imaginary axis:      w_p = Delta_p / (Delta_p^2 + omega_f^2)
+ *                        (Eq. retarded_advanced_epsilon at E = i omega_f)
+ *   M     device [nv*nc][ng], c128 (prec FP64) or c64 (mixed precisions)
+ *   ev,ec host double [nv], [nc] in Ha, each ascending, every ec > every ev
+ *   omega host double [nfreq] in Ha (ignored when nfreq = 0)
+ *   chi   device c128 [max(1,nfreq)][ng][ng], Hermitian, both triangles
+ *         written.  accumulate = 1 adds into chi (stream conduction chunks:
+ *         call once per chunk with that chunk's M, ec and nc).
+ * The mixed precisions accumulate each call's contribution in FP32 on the
+ * tensor cores and add it to the FP64 chi once per call.                   */
+int bgw_chi_sum(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng,
+                const void* M, const double* ev, const double* ec,
+                int nfreq, const double* omega, int prec, int accumulate,
+                void* chi, void* stream);
+
+/* ------------------------------------------------------------------------
+ * bgw_epsinv -- symmetrized dielectric matrix and its inverse (Eq. epsilon
+ * with the symmetric Coulomb form v^{1/2}(q+G) v^{1/2}(q+G')):
+ *   eps~[G][G'] = delta_GG' - sqrt(v_G) chi[G][G'] sqrt(v_G'),
+ *   v_G = 4 pi / |(q + G) B|^2,  then epsinv = (eps~)^-1   (FP64 always).
+ * Batched over nmat independent matrices of sizes ng[i] (may differ):
+ *   cells[i]  host, q and bvec of matrix i
+ *   geps[i]   host int32 [ng[i]][3]
+ *   chi[i]    device c128 [ng[i]][ng[i]] (read only)
+ *   eps[i]    device c128 [ng[i]][ng[i]] or NULL (eps~ is also written
+ *             there when non-NULL; the array `eps` itself may be NULL)
+ *   epsinv[i] device c128 [ng[i]][ng[i]]
+ * The inverse is a blocked Gauss-Jordan elimination without pivoting, which
+ * is stable for Hermitian positive-definite eps~ (chi <= 0 makes eps~ >= I).
+ * EINVAL if some |q+G| = 0.  A zero or non-finite pivot sets BGW_ENUMERIC,
+ * reported by bgw_sync.                                                    */
+int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
+               const int32_t* const* geps, const void* const* chi,
+               void* const* eps, void* const* epsinv, void* stream);
+
+/* ------------------------------------------------------------------------
+ * bgw_epsilon -- the whole path for one q-point and nfreq frequencies
+ * (nfreq = 0: static): bgw_mtxel, bgw_chi_sum over conduction chunks of at
+ * most `nc_chunk` bands (0 = all at once), then bgw_epsinv per frequency.
+ * Bulk inputs (cv, cc) and outputs (chi, epsinv) may be host or device
+ * memory (detected per pointer); host buffers are copied inside the call
+ * and the call then returns after the results are back on the host.
+ *   chi     c128 [max(1,nfreq)][ng][ng] or NULL (not returned)
+ *   epsinv  c128 [max(1,nfreq)][ng][ng]
+ * The library holds M and the chi accumulator in its own scratch memory.  */
+int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell,
+                int nv, int npw_v, const int32_t* gv, const void* cv,
+                const double* ev,
+                int nc, int npw_c, const int32_t* gc, const void* cc,
+                const double* ec,
+                int ng, const int32_t* geps, int nfreq, const double* omega,
+                int prec, int nc_chunk, void* chi, void* epsinv, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BGW_H */

@@ -1,0 +1,195 @@
+"""Thin Python binding of libbgw.so (include/bgw.h), argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; this module turns
+torch tensors into pointers, host numpy arrays into C arrays, and status
+codes into exceptions.  The library must have been built (``build()`` in
+``__graft_entry__`` or ``python paper_1111_4429_gb300/_build.py``); there is
+no fallback when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbgw.so")
+
+BGW_OK, BGW_EINVAL, BGW_ENOMEM, BGW_ECUDA, BGW_ETIMEOUT, BGW_ENUMERIC, BGW_EBUSY, BGW_ECANCELED, \
+    BGW_EUNSUPPORTED = range(9)
+BGW_PREC_FP64, BGW_PREC_MIX_FP16, BGW_PREC_MIX_BF16 = 0, 1, 2
+PREC = {"fp64": BGW_PREC_FP64, "mix_fp16": BGW_PREC_MIX_FP16, "mix_bf16": BGW_PREC_MIX_BF16}
+
+# Every symbol include/bgw.h declares.
+EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_stats", "bgw_mtxel",
+           "bgw_chi_sum", "bgw_epsinv", "bgw_epsilon")
+
+
+class BgwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bgw error {code}: {msg}")
+        self.code = code
+
+
+class Cell(ctypes.Structure):
+    _fields_ = [("bvec", (ctypes.c_double * 3) * 3), ("omega", ctypes.c_double),
+                ("q_frac", ctypes.c_double * 3), ("fft", ctypes.c_int * 3)]
+
+
+def make_cell(bvec, omega: float, q_frac, n: int) -> Cell:
+    c = Cell()
+    b = np.asarray(bvec, dtype=np.float64)
+    for i in range(3):
+        for j in range(3):
+            c.bvec[i][j] = float(b[i, j])
+        c.q_frac[i] = float(q_frac[i])
+        c.fft[i] = int(n)
+    c.omega = float(omega)
+    return c
+
+
+def system_cell(s) -> Cell:
+    return make_cell(s.bvec, s.omega, s.q_frac, s.fft)
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libbgw.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it first (python paper_1111_4429_gb300/_build.py)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32p, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
+    cellp = ctypes.POINTER(Cell)
+    ci = ctypes.c_int
+    lib.bgw_create.argtypes = [ctypes.POINTER(vp), ci, ctypes.c_uint64]
+    lib.bgw_destroy.argtypes = [vp]
+    lib.bgw_last_error.argtypes = [vp]
+    lib.bgw_last_error.restype = ctypes.c_char_p
+    lib.bgw_sync.argtypes = [vp, vp]
+    lib.bgw_mem_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    lib.bgw_mtxel.argtypes = [vp, cellp, ci, ci, i32p, vp, ci, ci, i32p, vp, ci, i32p, ci, vp, vp]
+    lib.bgw_chi_sum.argtypes = [vp, cellp, ci, ci, ci, vp, dp, dp, ci, dp, ci, ci, vp, vp]
+    lib.bgw_epsinv.argtypes = [vp, ci, cellp, ctypes.POINTER(ci), ctypes.POINTER(i32p), ctypes.POINTER(vp),
+                               ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.bgw_epsilon.argtypes = [vp, cellp, ci, ci, i32p, vp, dp, ci, ci, i32p, vp, dp, ci, i32p, ci, dp, ci,
+                                ci, vp, vp, vp]
+    for name in EXPORTS:
+        getattr(lib, name).restype = ctypes.c_char_p if name == "bgw_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _i32(a: np.ndarray):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _f64(a):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ptr(t) -> Optional[int]:
+    """Address of a torch tensor or numpy array (host or device), or None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Context:
+    """One bgw_ctx on one device (see include/bgw.h)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.lib = load()
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = self.lib.bgw_create(ctypes.byref(h), device, hbm_budget_bytes)
+        if rc != BGW_OK:
+            raise BgwError(rc, f"bgw_create failed on device {device}")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bgw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != BGW_OK:
+            raise BgwError(rc, self.lib.bgw_last_error(self.h).decode())
+
+    def sync(self, stream=None):
+        self._check(self.lib.bgw_sync(self.h, _stream(stream)))
+
+    def mem_stats(self):
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self.lib.bgw_mem_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def mtxel(self, cell: Cell, gv, cv, gc, cc, geps, prec: int, M, stream=None):
+        gv_, gvp = _i32(gv)
+        gc_, gcp = _i32(gc)
+        ge_, gep = _i32(geps)
+        self._check(self.lib.bgw_mtxel(self.h, ctypes.byref(cell), cv.shape[0], gv_.shape[0], gvp, _ptr(cv),
+                                       cc.shape[0], gc_.shape[0], gcp, _ptr(cc), ge_.shape[0], gep, prec,
+                                       _ptr(M), _stream(stream)))
+        return M
+
+    def chi_sum(self, cell: Cell, nv: int, nc: int, ng: int, M, ev, ec, omega, prec: int, accumulate: bool,
+                chi, stream=None):
+        ev_, evp = _f64(ev)
+        ec_, ecp = _f64(ec)
+        om_, omp = _f64(omega)
+        nfreq = 0 if om_ is None else om_.shape[0]
+        self._check(self.lib.bgw_chi_sum(self.h, ctypes.byref(cell), nv, nc, ng, _ptr(M), evp, ecp, nfreq, omp,
+                                         prec, int(bool(accumulate)), _ptr(chi), _stream(stream)))
+        return chi
+
+    def epsinv(self, cells: Sequence[Cell], gepss: Sequence[np.ndarray], chis, eps, epsinvs, stream=None):
+        n = len(cells)
+        carr = (Cell * n)(*cells)
+        keep = [_i32(g) for g in gepss]
+        ng = (ctypes.c_int * n)(*[k[0].shape[0] for k in keep])
+        gp = (ctypes.POINTER(ctypes.c_int32) * n)(*[k[1] for k in keep])
+        cp = (ctypes.c_void_p * n)(*[_ptr(x) for x in chis])
+        ep = None if eps is None else (ctypes.c_void_p * n)(*[_ptr(x) for x in eps])
+        ip = (ctypes.c_void_p * n)(*[_ptr(x) for x in epsinvs])
+        self._check(self.lib.bgw_epsinv(self.h, n, carr, ng, gp, cp, ep, ip, _stream(stream)))
+        return epsinvs
+
+    def epsilon(self, cell: Cell, gv, cv, ev, gc, cc, ec, geps, omega, prec: int, nc_chunk: int, chi, epsinv,
+                stream=None):
+        gv_, gvp = _i32(gv)
+        gc_, gcp = _i32(gc)
+        ge_, gep = _i32(geps)
+        ev_, evp = _f64(ev)
+        ec_, ecp = _f64(ec)
+        om_, omp = _f64(omega)
+        nfreq = 0 if om_ is None else om_.shape[0]
+        self._check(self.lib.bgw_epsilon(self.h, ctypes.byref(cell), cv.shape[0], gv_.shape[0], gvp, _ptr(cv), evp,
+                                         cc.shape[0], gc_.shape[0], gcp, _ptr(cc), ecp, ge_.shape[0], gep, nfreq,
+                                         omp, prec, nc_chunk, _ptr(chi), _ptr(epsinv), _stream(stream)))
+        return epsinv

@@ -1,0 +1,354 @@
+// extern "C" entry points declared in include/bgw.h: argument checks, plan
+// lookup, scratch management and the order of the kernel launches.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <set>
+#include <tuple>
+#include <vector>
+
+#include "runtime.h"
+
+using namespace bgw;
+
+namespace {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+Ctx* impl(bgw_ctx* c) { return c ? &c->impl : nullptr; }
+
+int check_cell(Ctx* c, const bgw_cell* cell, int* n) {
+  if (!cell) return fail(c, BGW_EINVAL, "cell is NULL");
+  if (cell->fft[0] != cell->fft[1] || cell->fft[1] != cell->fft[2])
+    return fail(c, BGW_EUNSUPPORTED, "FFT grid %dx%dx%d: only cubic grids are implemented", cell->fft[0],
+                cell->fft[1], cell->fft[2]);
+  if (!fft_size_supported(cell->fft[0]))
+    return fail(c, BGW_EUNSUPPORTED, "FFT grid %d has no kernel (supported: 8 10 12 16 20 24 30 32 36 40 48 50 60 64)",
+                cell->fft[0]);
+  if (!(cell->omega > 0.0) || !isfinite(cell->omega)) return fail(c, BGW_EINVAL, "cell volume must be > 0");
+  *n = cell->fft[0];
+  return BGW_OK;
+}
+
+// G components in [-n/2, n/2), no duplicates; returns max |G_d| per axis.
+int check_glist(Ctx* c, const char* name, int cnt, const int32_t* g, int n, int gmax[3]) {
+  if (cnt <= 0) return fail(c, BGW_EINVAL, "%s: count must be >= 1", name);
+  if (!g) return fail(c, BGW_EINVAL, "%s is NULL", name);
+  const int lo = -(n / 2), hi = n - n / 2;  // [lo, hi)
+  gmax[0] = gmax[1] = gmax[2] = 0;
+  std::vector<int64_t> keys(cnt);
+  for (int i = 0; i < cnt; ++i) {
+    for (int d = 0; d < 3; ++d) {
+      const int v = g[3 * i + d];
+      if (v < lo || v >= hi)
+        return fail(c, BGW_EINVAL, "%s[%d] component %d = %d outside [-n/2, n/2) for n = %d", name, i, d, v, n);
+      gmax[d] = std::max(gmax[d], std::abs(v));
+    }
+    keys[i] = ((int64_t)(g[3 * i] - lo) * n + (g[3 * i + 1] - lo)) * n + (g[3 * i + 2] - lo);
+  }
+  std::sort(keys.begin(), keys.end());
+  if (std::adjacent_find(keys.begin(), keys.end()) != keys.end())
+    return fail(c, BGW_EINVAL, "%s holds a duplicate G vector", name);
+  return BGW_OK;
+}
+
+int check_energies(Ctx* c, int nv, const double* ev, int nc, const double* ec) {
+  if (!ev || !ec) return fail(c, BGW_EINVAL, "energies are NULL");
+  for (int i = 0; i < nv; ++i)
+    if (!isfinite(ev[i]) || (i && ev[i] < ev[i - 1])) return fail(c, BGW_EINVAL, "ev must be finite and ascending");
+  for (int i = 0; i < nc; ++i)
+    if (!isfinite(ec[i]) || (i && ec[i] < ec[i - 1])) return fail(c, BGW_EINVAL, "ec must be finite and ascending");
+  if (!(ev[nv - 1] < ec[0]))
+    return fail(c, BGW_EINVAL, "Delta = E_v - E_c must be < 0 for every pair (max ev %g >= min ec %g)",
+                ev[nv - 1], ec[0]);
+  return BGW_OK;
+}
+
+int check_prec(Ctx* c, int prec) {
+  if (prec != BGW_PREC_FP64 && prec != BGW_PREC_MIX_FP16 && prec != BGW_PREC_MIX_BF16)
+    return fail(c, BGW_EINVAL, "unknown precision %d", prec);
+  return BGW_OK;
+}
+
+int check_q(Ctx* c, const bgw_cell* cell, int ng, const int32_t* geps) {
+  for (int i = 0; i < ng; ++i) {
+    double k2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double kd = 0.0;
+      for (int a = 0; a < 3; ++a) kd += (geps[3 * i + a] + cell->q_frac[a]) * cell->bvec[a][d];
+      k2 += kd * kd;
+    }
+    if (!(k2 > 0.0)) return fail(c, BGW_EINVAL, "|q+G| = 0 at geps[%d]: the bare Coulomb factor diverges", i);
+  }
+  return BGW_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Largest epsilon sphere the gather kernel can hold in shared memory.
+int max_ng(int prec) { return (int)((227 * 1024) / (prec == BGW_PREC_FP64 ? 16 : 8)); }
+
+int validate_mtxel(Ctx* c, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv, int nc,
+                   int npw_c, const int32_t* gc, const void* cc, int ng, const int32_t* geps, int prec, void* M,
+                   int* n_out) {
+  int n, rc;
+  if ((rc = check_cell(c, cell, &n)) != BGW_OK) return rc;
+  if ((rc = check_prec(c, prec)) != BGW_OK) return rc;
+  if (nv <= 0 || nc <= 0) return fail(c, BGW_EINVAL, "nv and nc must be >= 1");
+  if (nv > 65535 || nc > 65535) return fail(c, BGW_EUNSUPPORTED, "at most 65535 bands per side");
+  if ((long long)nv * nc > 0x7fffffffLL) return fail(c, BGW_EUNSUPPORTED, "nv * nc exceeds 2^31 - 1");
+  if (!cv || !cc || !M) return fail(c, BGW_EINVAL, "coefficient or output pointer is NULL");
+  if (ng > max_ng(prec)) return fail(c, BGW_EUNSUPPORTED, "ng = %d exceeds %d for this precision", ng, max_ng(prec));
+  int mv[3], mc[3], me[3];
+  if ((rc = check_glist(c, "gv", npw_v, gv, n, mv)) != BGW_OK) return rc;
+  if ((rc = check_glist(c, "gc", npw_c, gc, n, mc)) != BGW_OK) return rc;
+  if ((rc = check_glist(c, "geps", ng, geps, n, me)) != BGW_OK) return rc;
+  for (int d = 0; d < 3; ++d)
+    if (n <= mv[d] + mc[d] + me[d])
+      return fail(c, BGW_EINVAL,
+                  "FFT grid %d aliases on axis %d: need n > max|Gv| + max|Gc| + max|Geps| = %d + %d + %d", n, d,
+                  mv[d], mc[d], me[d]);
+  *n_out = n;
+  return BGW_OK;
+}
+
+int init_device(Ctx* c) {
+  if (c->twiddles_ready) return BGW_OK;
+  BGW_CUDA(c, mtxel_init_f64());
+  BGW_CUDA(c, mtxel_init_f32());
+  c->twiddles_ready = true;
+  return BGW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bgw_create(bgw_ctx** out, int device, uint64_t hbm_budget_bytes) {
+  if (!out) return BGW_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return BGW_ECUDA;
+  }
+  DeviceGuard g(device);
+  if (!g.ok) return BGW_ECUDA;
+  bgw_ctx* c = new (std::nothrow) bgw_ctx(hbm_budget_bytes);
+  if (!c) return BGW_ENOMEM;
+  c->impl.device = device;
+  if (cudaMalloc(&c->impl.d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->impl.d_status, 0, sizeof(int)) != cudaSuccess || init_device(&c->impl) != BGW_OK) {
+    cudaGetLastError();
+    if (c->impl.d_status) cudaFree(c->impl.d_status);
+    delete c;
+    return BGW_ECUDA;
+  }
+  *out = c;
+  return BGW_OK;
+}
+
+int bgw_destroy(bgw_ctx* ctx) {
+  if (!ctx) return BGW_EINVAL;
+  DeviceGuard g(ctx->impl.device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->impl.d_status);
+  delete ctx;
+  return BGW_OK;
+}
+
+const char* bgw_last_error(bgw_ctx* ctx) {
+  if (!ctx) return "context is NULL";
+  return ctx->impl.err.c_str();
+}
+
+int bgw_sync(bgw_ctx* ctx, void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  DeviceGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BGW_CUDA(c, cudaStreamSynchronize(st));
+  int s = 0;
+  BGW_CUDA(c, cudaMemcpy(&s, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (s != kDevOk) {
+    BGW_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
+    if (s == kDevZeroPivot) return fail(c, BGW_ENUMERIC, "zero or non-finite pivot in the inversion");
+    if (s == kDevTimeout) return fail(c, BGW_ETIMEOUT, "a bounded device wait gave up");
+    return fail(c, BGW_ECUDA, "device status %d", s);
+  }
+  return BGW_OK;
+}
+
+int bgw_mem_stats(bgw_ctx* ctx, uint64_t* in_use, uint64_t* high_water) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  if (in_use) *in_use = c->pool.in_use();
+  if (high_water) *high_water = c->pool.high_water();
+  return BGW_OK;
+}
+
+int bgw_mtxel(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv, int nc,
+              int npw_c, const int32_t* gc, const void* cc, int ng, const int32_t* geps, int prec, void* M,
+              void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  int n, rc;
+  if ((rc = validate_mtxel(c, cell, nv, npw_v, gv, cv, nc, npw_c, gc, cc, ng, geps, prec, M, &n)) != BGW_OK)
+    return rc;
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const BandPlan *bpv, *bpc;
+  const PairPlan* pp;
+  if ((rc = get_band_plan(c, n, npw_v, gv, st, &bpv)) != BGW_OK) return rc;
+  if ((rc = get_band_plan(c, n, npw_c, gc, st, &bpc)) != BGW_OK) return rc;
+  if ((rc = get_pair_plan(c, n, ng, geps, st, &pp)) != BGW_OK) return rc;
+  return mtxel_run(c, n, prec, nv, bpv, cv, nc, bpc, cc, pp, M, st);
+}
+
+int bgw_chi_sum(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng, const void* M, const double* ev,
+                const double* ec, int nfreq, const double* omega, int prec, int accumulate, void* chi,
+                void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  int rc;
+  if (!cell || !(cell->omega > 0.0)) return fail(c, BGW_EINVAL, "cell is NULL or has no volume");
+  if ((rc = check_prec(c, prec)) != BGW_OK) return rc;
+  if (nv <= 0 || nc <= 0 || ng <= 0) return fail(c, BGW_EINVAL, "nv, nc, ng must be >= 1");
+  if (!M || !chi) return fail(c, BGW_EINVAL, "M or chi is NULL");
+  if (nfreq < 0 || (nfreq > 0 && !omega)) return fail(c, BGW_EINVAL, "bad frequency list");
+  for (int f = 0; f < nfreq; ++f)
+    if (!isfinite(omega[f])) return fail(c, BGW_EINVAL, "omega[%d] is not finite", f);
+  if ((rc = check_energies(c, nv, ev, nc, ec)) != BGW_OK) return rc;
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const void *dev_ev, *dev_ec, *dev_om = nullptr;
+  if ((rc = upload_cached(c, ev, nv * sizeof(double), st, &dev_ev)) != BGW_OK) return rc;
+  if ((rc = upload_cached(c, ec, nc * sizeof(double), st, &dev_ec)) != BGW_OK) return rc;
+  if (nfreq > 0 && (rc = upload_cached(c, omega, nfreq * sizeof(double), st, &dev_om)) != BGW_OK) return rc;
+  return chi_run(c, prec, nv, nc, ng, M, static_cast<const double*>(dev_ev), static_cast<const double*>(dev_ec),
+                 nfreq, static_cast<const double*>(dev_om), 4.0 / cell->omega, accumulate, chi, st);
+}
+
+int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, const int32_t* const* geps,
+               const void* const* chi, void* const* eps, void* const* epsinv, void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  if (nmat <= 0 || !cells || !ng || !geps || !chi || !epsinv) return fail(c, BGW_EINVAL, "NULL argument array");
+  int rc;
+  for (int m = 0; m < nmat; ++m) {
+    if (ng[m] <= 0 || !geps[m] || !chi[m] || !epsinv[m])
+      return fail(c, BGW_EINVAL, "matrix %d: bad size or NULL pointer", m);
+    if ((rc = check_q(c, &cells[m], ng[m], geps[m])) != BGW_OK) return rc;
+  }
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int m = 0; m < nmat; ++m) {
+    const void* dg;
+    if ((rc = upload_cached(c, geps[m], (size_t)ng[m] * 3 * sizeof(int32_t), st, &dg)) != BGW_OK) return rc;
+    if ((rc = epsinv_run(c, ng[m], &cells[m].bvec[0][0], cells[m].q_frac, static_cast<const int32_t*>(dg), chi[m],
+                         eps ? eps[m] : nullptr, epsinv[m], st)) != BGW_OK)
+      return rc;
+  }
+  return BGW_OK;
+}
+
+int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv,
+                const double* ev, int nc, int npw_c, const int32_t* gc, const void* cc, const double* ec, int ng,
+                const int32_t* geps, int nfreq, const double* omega, int prec, int nc_chunk, void* chi,
+                void* epsinv, void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  int n, rc;
+  if ((rc = validate_mtxel(c, cell, nv, npw_v, gv, cv, nc, npw_c, gc, cc, ng, geps, prec, epsinv, &n)) != BGW_OK)
+    return rc;
+  if ((rc = check_energies(c, nv, ev, nc, ec)) != BGW_OK) return rc;
+  if ((rc = check_q(c, cell, ng, geps)) != BGW_OK) return rc;
+  if (nfreq < 0 || (nfreq > 0 && !omega)) return fail(c, BGW_EINVAL, "bad frequency list");
+  if (nc_chunk <= 0 || nc_chunk > nc) nc_chunk = nc;
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nrow = nfreq > 0 ? nfreq : 1;
+  const size_t cs = prec == BGW_PREC_FP64 ? 16 : 8;
+  const size_t n2 = (size_t)ng * ng * sizeof(double2);
+  const bool cv_dev = is_device_ptr(cv), cc_dev = is_device_ptr(cc);
+  const bool chi_dev = chi && is_device_ptr(chi), inv_dev = is_device_ptr(epsinv);
+  Scratch s_cv, s_cc, s_M, s_chi, s_inv;
+  s_cv.pool = s_cc.pool = s_M.pool = s_chi.pool = s_inv.pool = &c->pool;
+  const void* d_cv = cv;
+  const void* d_cc = cc;
+  if (!cv_dev) {
+    if ((rc = c->pool.alloc((size_t)nv * npw_v * 16, &s_cv.ptr)) != BGW_OK) return fail(c, rc, "cv staging");
+    BGW_CUDA(c, cudaMemcpyAsync(s_cv.ptr, cv, (size_t)nv * npw_v * 16, cudaMemcpyHostToDevice, st));
+    d_cv = s_cv.ptr;
+  }
+  if (!cc_dev) {
+    if ((rc = c->pool.alloc((size_t)nc * npw_c * 16, &s_cc.ptr)) != BGW_OK) return fail(c, rc, "cc staging");
+    BGW_CUDA(c, cudaMemcpyAsync(s_cc.ptr, cc, (size_t)nc * npw_c * 16, cudaMemcpyHostToDevice, st));
+    d_cc = s_cc.ptr;
+  }
+  void* d_chi = chi_dev ? chi : nullptr;
+  if (!d_chi) {
+    if ((rc = c->pool.alloc(nrow * n2, &s_chi.ptr)) != BGW_OK) return fail(c, rc, "chi scratch");
+    d_chi = s_chi.ptr;
+  }
+  void* d_inv = inv_dev ? epsinv : nullptr;
+  if (!d_inv) {
+    if ((rc = c->pool.alloc(nrow * n2, &s_inv.ptr)) != BGW_OK) return fail(c, rc, "epsinv scratch");
+    d_inv = s_inv.ptr;
+  }
+  if ((rc = c->pool.alloc((size_t)nv * nc_chunk * ng * cs, &s_M.ptr)) != BGW_OK) return fail(c, rc, "M scratch");
+  const BandPlan *bpv, *bpc;
+  const PairPlan* pp;
+  if ((rc = get_band_plan(c, n, npw_v, gv, st, &bpv)) != BGW_OK) return rc;
+  if ((rc = get_band_plan(c, n, npw_c, gc, st, &bpc)) != BGW_OK) return rc;
+  if ((rc = get_pair_plan(c, n, ng, geps, st, &pp)) != BGW_OK) return rc;
+  const void *dev_ev, *dev_ec, *dev_om = nullptr, *dev_geps;
+  if ((rc = upload_cached(c, ev, nv * sizeof(double), st, &dev_ev)) != BGW_OK) return rc;
+  if ((rc = upload_cached(c, ec, nc * sizeof(double), st, &dev_ec)) != BGW_OK) return rc;
+  if (nfreq > 0 && (rc = upload_cached(c, omega, nfreq * sizeof(double), st, &dev_om)) != BGW_OK) return rc;
+  if ((rc = upload_cached(c, geps, (size_t)ng * 3 * sizeof(int32_t), st, &dev_geps)) != BGW_OK) return rc;
+  for (int c0 = 0; c0 < nc; c0 += nc_chunk) {
+    const int ncc = std::min(nc_chunk, nc - c0);
+    const void* cc0 = static_cast<const char*>(d_cc) + (size_t)c0 * npw_c * 16;
+    if ((rc = mtxel_run(c, n, prec, nv, bpv, d_cv, ncc, bpc, cc0, pp, s_M.ptr, st)) != BGW_OK) return rc;
+    if ((rc = chi_run(c, prec, nv, ncc, ng, s_M.ptr, static_cast<const double*>(dev_ev),
+                      static_cast<const double*>(dev_ec) + c0, nfreq, static_cast<const double*>(dev_om),
+                      4.0 / cell->omega, c0 > 0, d_chi, st)) != BGW_OK)
+      return rc;
+  }
+  for (int f = 0; f < nrow; ++f) {
+    if ((rc = epsinv_run(c, ng, &cell->bvec[0][0], cell->q_frac, static_cast<const int32_t*>(dev_geps),
+                         static_cast<char*>(d_chi) + f * n2, nullptr, static_cast<char*>(d_inv) + f * n2, st)) !=
+        BGW_OK)
+      return rc;
+  }
+  if (chi && !chi_dev) BGW_CUDA(c, cudaMemcpyAsync(chi, d_chi, nrow * n2, cudaMemcpyDeviceToHost, st));
+  if (!inv_dev) BGW_CUDA(c, cudaMemcpyAsync(epsinv, d_inv, nrow * n2, cudaMemcpyDeviceToHost, st));
+  if (!inv_dev || (chi && !chi_dev)) return bgw_sync(ctx, stream);
+  return BGW_OK;
+}
+
+}  // extern "C"

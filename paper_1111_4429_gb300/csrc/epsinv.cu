@@ -1,0 +1,226 @@
+// Symmetrized dielectric matrix and its inverse (paper, Eqs. epsilon and
+// untruncated_bare_coulomb with the symmetric Coulomb form), FP64 throughout:
+//   sv_G       = sqrt(4 pi) / |(q + G) B|             (= v(q+G)^{1/2})
+//   eps~[G][G'] = delta_GG' - sv_G chi[G][G'] sv_G'
+//   epsinv      = eps~^-1 by blocked Gauss-Jordan elimination.
+//
+// Gauss-Jordan step on the column block k (width kb, rows/cols K = k0..k0+kb):
+//   D^-1 of the diagonal block (one CTA, elimination in shared memory)
+//   R[r][j] = (D^-1 A_K,:)[r][j] for j outside K,  R[r][K] = D^-1
+//   C[i][s] = A[i][k0+s]                (copy of the column panel)
+//   A[i][j] <- R[i-k0][j]                                         i in K
+//   A[i][j] <- (j in K ? 0 : A[i][j]) - sum_s C[i][s] R[s][j]     otherwise
+// After the last block A holds eps~^-1.  No pivoting: eps~ = I - v^1/2 chi
+// v^1/2 is Hermitian positive definite (chi <= 0), for which elimination
+// without pivoting is backward stable; a zero or non-finite pivot is
+// recorded in the device status word.
+#include "runtime.h"
+
+namespace bgw {
+
+namespace {
+constexpr int NB = 32;   // Gauss-Jordan block width
+constexpr int TU = 64;   // update tile edge
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+}  // namespace
+
+__global__ void coulomb_sqrt_kernel(const int32_t* __restrict__ geps, int ng, double b00, double b01,
+                                    double b02, double b10, double b11, double b12, double b20,
+                                    double b21, double b22, double q0, double q1, double q2,
+                                    double* __restrict__ sv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ng) return;
+  const double f0 = geps[3 * i] + q0, f1 = geps[3 * i + 1] + q1, f2 = geps[3 * i + 2] + q2;
+  const double kx = f0 * b00 + f1 * b10 + f2 * b20;
+  const double ky = f0 * b01 + f1 * b11 + f2 * b21;
+  const double kz = f0 * b02 + f1 * b12 + f2 * b22;
+  const double k2 = kx * kx + ky * ky + kz * kz;
+  // 4 pi / k2, square root
+  sv[i] = sqrt(4.0 * 3.14159265358979323846 / k2);
+}
+
+__global__ void eps_form_kernel(const double2* __restrict__ chi, const double* __restrict__ sv, int ng,
+                                double2* __restrict__ work, double2* __restrict__ eps) {
+  const size_t n2 = (size_t)ng * ng;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ng), j = (int)(e - (size_t)i * ng);
+    const double s = sv[i] * sv[j];
+    const double2 x = chi[e];
+    double2 r = make_double2(-s * x.x, -s * x.y);
+    if (i == j) r.x += 1.0;
+    work[e] = r;
+    if (eps) eps[e] = r;
+  }
+}
+
+// Inverse of the diagonal block A[k0:k0+kb, k0:k0+kb] -> Dinv[kb][kb] (ld NB).
+__global__ void __launch_bounds__(NB * NB) gj_diag_kernel(const double2* __restrict__ A, int ng, int k0,
+                                                          int kb, double2* __restrict__ Dinv,
+                                                          int* __restrict__ status) {
+  __shared__ double2 D[NB][NB + 1];
+  const int i = threadIdx.y, j = threadIdx.x;
+  const bool in = i < kb && j < kb;
+  D[i][j] = in ? A[(size_t)(k0 + i) * ng + k0 + j] : make_double2(i == j ? 1.0 : 0.0, 0.0);
+  for (int s = 0; s < kb; ++s) {
+    __syncthreads();
+    const double2 piv = D[s][s];
+    const double m2 = piv.x * piv.x + piv.y * piv.y;
+    double2 p;
+    if (!(m2 > 0.0) || !isfinite(m2)) {
+      if (i == 0 && j == 0) atomicExch(status, (int)kDevZeroPivot);
+      p = make_double2(0.0, 0.0);
+    } else {
+      p = make_double2(piv.x / m2, -piv.y / m2);  // 1/piv
+    }
+    const double2 f = D[i][s];
+    const double2 rs = D[s][j];
+    __syncthreads();
+    const double2 rsn = (j == s) ? p : cmul(rs, p);
+    if (i == s) {
+      D[i][j] = rsn;
+    } else {
+      double2 v = (j == s) ? make_double2(0.0, 0.0) : D[i][j];
+      const double2 t = cmul(f, rsn);
+      D[i][j] = make_double2(v.x - t.x, v.y - t.y);
+    }
+  }
+  __syncthreads();
+  if (in) Dinv[i * NB + j] = D[i][j];
+}
+
+// R[r][j] (ld ng) for all columns j; C[i][s] (ld NB) copy of the column panel.
+// grid (ceil(ng/64), 1 + ceil(ng/256)): blockIdx.y == 0 computes R for 64
+// columns, blockIdx.y >= 1 copies 256 rows of the column panel.
+__global__ void __launch_bounds__(256) gj_panels_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
+                                                        const double2* __restrict__ Dinv,
+                                                        double2* __restrict__ R, double2* __restrict__ C) {
+  const int tid = threadIdx.x;
+  if (blockIdx.y > 0) {
+    const int i = (blockIdx.y - 1) * 256 + tid;
+    if (blockIdx.x != 0 || i >= ng) return;
+    for (int s = 0; s < kb; ++s) C[(size_t)i * NB + s] = A[(size_t)i * ng + k0 + s];
+    return;
+  }
+  __shared__ double2 Ds[NB][NB];
+  __shared__ double2 As[NB][64];
+  const int j0 = blockIdx.x * 64;
+  for (int e = tid; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Dinv[e];
+  for (int e = tid; e < NB * 64; e += 256) {
+    const int s = e / 64, jj = e % 64;
+    As[s][jj] = (s < kb && j0 + jj < ng) ? A[(size_t)(k0 + s) * ng + j0 + jj] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * 64; e += 256) {
+    const int r = e / 64, jj = e % 64, j = j0 + jj;
+    if (r >= kb || j >= ng) continue;
+    double2 v;
+    if (j >= k0 && j < k0 + kb) {
+      v = Ds[r][j - k0];
+    } else {
+      v = make_double2(0.0, 0.0);
+      for (int s = 0; s < kb; ++s) {
+        const double2 t = cmul(Ds[r][s], As[s][jj]);
+        v.x += t.x;
+        v.y += t.y;
+      }
+    }
+    R[(size_t)r * ng + j] = v;
+  }
+}
+
+// Rank-kb update of the whole matrix.  grid (ceil(ng/64), ceil(ng/64)).
+__global__ void __launch_bounds__(256) gj_update_kernel(double2* __restrict__ A, int ng, int k0, int kb,
+                                                        const double2* __restrict__ R,
+                                                        const double2* __restrict__ C) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 (*Cs)[NB + 1] = reinterpret_cast<double2 (*)[NB + 1]>(smem_raw);
+  double2 (*Rs)[TU] = reinterpret_cast<double2 (*)[TU]>(smem_raw + sizeof(double2) * TU * (NB + 1));
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.y * TU, j0 = blockIdx.x * TU;
+  for (int e = tid; e < TU * NB; e += 256) {
+    const int ii = e / NB, s = e % NB;
+    Cs[ii][s] = (i0 + ii < ng && s < kb) ? C[(size_t)(i0 + ii) * NB + s] : make_double2(0.0, 0.0);
+  }
+  for (int e = tid; e < NB * TU; e += 256) {
+    const int s = e / TU, jj = e % TU;
+    Rs[s][jj] = (s < kb && j0 + jj < ng) ? R[(size_t)s * ng + j0 + jj] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  double2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0.0, 0.0);
+  for (int s = 0; s < kb; ++s) {
+    double2 cv[4], rv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) cv[a] = Cs[ty + 16 * a][s];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) rv[b] = Rs[s][tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        acc[a][b].x = fma(cv[a].x, rv[b].x, acc[a][b].x);
+        acc[a][b].x = fma(-cv[a].y, rv[b].y, acc[a][b].x);
+        acc[a][b].y = fma(cv[a].x, rv[b].y, acc[a][b].y);
+        acc[a][b].y = fma(cv[a].y, rv[b].x, acc[a][b].y);
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty + 16 * a;
+    if (i >= ng) continue;
+    const bool irow = i >= k0 && i < k0 + kb;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx + 16 * b;
+      if (j >= ng) continue;
+      double2* dst = A + (size_t)i * ng + j;
+      if (irow) {
+        *dst = R[(size_t)(i - k0) * ng + j];
+      } else {
+        const bool jcol = j >= k0 && j < k0 + kb;
+        double2 v = jcol ? make_double2(0.0, 0.0) : *dst;
+        *dst = make_double2(v.x - acc[a][b].x, v.y - acc[a][b].y);
+      }
+    }
+  }
+}
+
+int epsinv_run(Ctx* c, int ng, const double* bvec, const double* qf, const int32_t* d_geps,
+               const void* chi, void* eps, void* epsinv, cudaStream_t st) {
+  Scratch sv, dinv, R, Cp;
+  sv.pool = dinv.pool = R.pool = Cp.pool = &c->pool;
+  int rc;
+  if ((rc = c->pool.alloc((size_t)ng * sizeof(double), &sv.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)NB * NB * sizeof(double2), &dinv.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)NB * ng * sizeof(double2), &R.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)NB * ng * sizeof(double2), &Cp.ptr)) != BGW_OK)
+    return fail(c, rc, "bgw_epsinv: scratch allocation failed");
+  coulomb_sqrt_kernel<<<(ng + 255) / 256, 256, 0, st>>>(d_geps, ng, bvec[0], bvec[1], bvec[2], bvec[3],
+                                                        bvec[4], bvec[5], bvec[6], bvec[7], bvec[8], qf[0],
+                                                        qf[1], qf[2], sv.as<double>());
+  double2* A = static_cast<double2*>(epsinv);
+  const size_t n2 = (size_t)ng * ng;
+  const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
+  eps_form_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(chi), sv.as<double>(), ng, A,
+                                      static_cast<double2*>(eps));
+  BGW_CUDA(c, cudaGetLastError());
+  const int nt = (ng + TU - 1) / TU;
+  const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
+  BGW_CUDA(c, cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
+  for (int k0 = 0; k0 < ng; k0 += NB) {
+    const int kb = std::min(NB, ng - k0);
+    gj_diag_kernel<<<1, dim3(NB, NB), 0, st>>>(A, ng, k0, kb, dinv.as<double2>(), c->d_status);
+    gj_panels_kernel<<<dim3((ng + 63) / 64, 1 + (ng + 255) / 256), 256, 0, st>>>(
+        A, ng, k0, kb, dinv.as<double2>(), R.as<double2>(), Cp.as<double2>());
+    gj_update_kernel<<<dim3(nt, nt), 256, upd_smem, st>>>(A, ng, k0, kb, R.as<double2>(), Cp.as<double2>());
+    BGW_CUDA(c, cudaGetLastError());
+  }
+  return BGW_OK;
+}
+
+}  // namespace bgw

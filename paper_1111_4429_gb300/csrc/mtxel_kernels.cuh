@@ -1,0 +1,275 @@
+// Kernels of the matrix-element step (paper, Eq. eqn_matrix_elem and the
+// FFT form that follows it):
+//
+//   band transform   u_b(r) = sum_G c_b(G) e^{+iG.r}           (per band)
+//     band_zpass     scatter the sphere onto its (gx,gy) columns, FFT along z
+//     band_yxpass    per z-plane: FFT along y on the occupied gx, then along x
+//   pair transform   F_p(G) = (1/N^3) sum_r conj(u_v) u_c e^{+iG.r}
+//     pair_yxpass    per (z-plane, pairs): product formed on load, FFT along
+//                    y keeping the epsilon-sphere ky, FFT along x keeping the
+//                    epsilon-sphere (kx,ky) columns -> T[p][z][col]
+//     pair_zgather   per pair: FFT along z of every kept column, gather the
+//                    epsilon-sphere kz into the pair-major row M[p][:]
+//
+// Real-space grids are u[b][z][y][x] (x fastest), n^3 complex per band.
+#pragma once
+#include "fft.cuh"
+#include "runtime.h"
+
+namespace bgw {
+
+template <typename T> __device__ __forceinline__ cpx<T> load_c128(const double2* p) {
+  double2 v = *p;
+  return mk<T>(T(v.x), T(v.y));
+}
+
+// ---------------------------------------------------------------- band z
+// grid (ceil(ncol/64), nb), block 64.  smem S[64][N+1].
+template <typename T, int N>
+__global__ void __launch_bounds__(64) band_zpass(const double2* __restrict__ coef, int npw,
+                                                 int ncol, const int* __restrict__ col_start,
+                                                 const int* __restrict__ ent_col,
+                                                 const int* __restrict__ ent_z,
+                                                 const int* __restrict__ ent_idx,
+                                                 cpx<T>* __restrict__ U1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);
+  constexpr int CB = 64, LD = N + 1;
+  const int col0 = blockIdx.x * CB;
+  const int b = blockIdx.y;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < CB * LD; i += CB) S[i] = mk<T>(T(0), T(0));
+  __syncthreads();
+  const int e0 = col_start[col0];
+  const int e1 = col_start[min(col0 + CB, ncol)];
+  const double2* cb = coef + (size_t)b * npw;
+  for (int e = e0 + tid; e < e1; e += CB) {
+    int lc = ent_col[e] - col0;
+    S[lc * LD + ent_z[e]] = load_c128<T>(cb + ent_idx[e]);
+  }
+  __syncthreads();
+  const int col = col0 + tid;
+  if (col >= ncol) return;
+  cpx<T> a[N];
+#pragma unroll
+  for (int z = 0; z < N; ++z) a[z] = S[tid * LD + z];
+  fft_line<T, N, 1>(a);
+  cpx<T>* out = U1 + (size_t)b * N * ncol + col;
+#pragma unroll
+  for (int z = 0; z < N; ++z) out[(size_t)z * ncol] = a[z];
+}
+
+// ---------------------------------------------------------------- band y,x
+// grid (N, nb), block 64.  smem P[N][N+1].
+template <typename T, int N>
+__global__ void __launch_bounds__(64) band_yxpass(const cpx<T>* __restrict__ U1, int ncol,
+                                                  const int* __restrict__ col_xy, int nxs,
+                                                  const int* __restrict__ xslot,
+                                                  cpx<T>* __restrict__ u) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* P = reinterpret_cast<cpx<T>*>(smem_raw);
+  constexpr int LD = N + 1;
+  const int z = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < N * LD; i += nt) P[i] = mk<T>(T(0), T(0));
+  __syncthreads();
+  const cpx<T>* src = U1 + ((size_t)b * N + z) * ncol;
+  for (int c = tid; c < ncol; c += nt) {
+    int xy = col_xy[c];
+    P[(xy / N) * LD + (xy % N)] = src[c];
+  }
+  __syncthreads();
+  for (int s = tid; s < nxs; s += nt) {
+    const int x = xslot[s];
+    cpx<T> a[N];
+#pragma unroll
+    for (int y = 0; y < N; ++y) a[y] = P[y * LD + x];
+    fft_line<T, N, 1>(a);
+#pragma unroll
+    for (int y = 0; y < N; ++y) P[y * LD + x] = a[y];
+  }
+  __syncthreads();
+  for (int y = tid; y < N; y += nt) {
+    cpx<T> a[N];
+#pragma unroll
+    for (int x = 0; x < N; ++x) a[x] = P[y * LD + x];
+    fft_line<T, N, 1>(a);
+#pragma unroll
+    for (int x = 0; x < N; ++x) P[y * LD + x] = a[x];
+  }
+  __syncthreads();
+  cpx<T>* dst = u + ((size_t)b * N + z) * N * N;
+  for (int i = tid; i < N * N; i += nt) dst[i] = P[(i / N) * LD + (i % N)];
+}
+
+// ---------------------------------------------------------------- pair y,x
+// grid (ceil(npb/ppb), N), block >= 32.  Pairs pbase .. pbase+npb-1.
+// smem: Y[ppb][nys][N+1] | Tz[ppb][ncol] | colmap[N*nys] | yslot[N]
+template <typename T, int N>
+__global__ void __launch_bounds__(256) pair_yxpass(const cpx<T>* __restrict__ uv,
+                                                   const cpx<T>* __restrict__ uc, int nc,
+                                                   int pbase, int npb, int ppb, int nys, int ncol,
+                                                   const int* __restrict__ g_colmap,
+                                                   const int* __restrict__ g_yslot,
+                                                   cpx<T>* __restrict__ Tbuf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int LD = N + 1;
+  cpx<T>* Y = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* Tz = Y + (size_t)ppb * nys * LD;
+  int* colmap = reinterpret_cast<int*>(Tz + (size_t)ppb * ncol);
+  int* yslot = colmap + N * nys;
+  const int z = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
+  const int pl0 = blockIdx.x * ppb;                  // first local pair of this block
+  const int npp = min(ppb, npb - pl0);               // pairs in this block
+  for (int i = tid; i < N * nys; i += nt) colmap[i] = g_colmap[i];
+  for (int i = tid; i < N; i += nt) yslot[i] = g_yslot[i];
+  __syncthreads();
+  const size_t plane = (size_t)N * N;
+  // phase A: FFT along y of conj(u_v) u_c for every x, keep the ky slots
+  for (int j = tid; j < npp * N; j += nt) {
+    const int pp = j / N, x = j - pp * N;
+    const int p = pbase + pl0 + pp;
+    const int v = p / nc, c = p - v * nc;
+    const cpx<T>* pv = uv + ((size_t)v * N + z) * plane + x;
+    const cpx<T>* pc = uc + ((size_t)c * N + z) * plane + x;
+    cpx<T> a[N];
+#pragma unroll
+    for (int y = 0; y < N; ++y) a[y] = cmulc<T>(pv[(size_t)y * N], pc[(size_t)y * N]);
+    fft_line<T, N, 1>(a);
+    cpx<T>* yrow = Y + (size_t)pp * nys * LD + x;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int s = yslot[k];
+      if (s >= 0) yrow[s * LD] = a[k];
+    }
+  }
+  __syncthreads();
+  // phase B: FFT along x of each kept ky row, keep the sphere's columns
+  for (int j = tid; j < npp * nys; j += nt) {
+    const int pp = j / nys, s = j - pp * nys;
+    const cpx<T>* row = Y + ((size_t)pp * nys + s) * LD;
+    cpx<T> a[N];
+#pragma unroll
+    for (int x = 0; x < N; ++x) a[x] = row[x];
+    fft_line<T, N, 1>(a);
+    cpx<T>* tz = Tz + (size_t)pp * ncol;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int col = colmap[k * nys + s];
+      if (col >= 0) tz[col] = a[k];
+    }
+  }
+  __syncthreads();
+  // phase C: coalesced store of the kept columns of this plane
+  for (int i = tid; i < npp * ncol; i += nt) {
+    const int pp = i / ncol, col = i - pp * ncol;
+    Tbuf[((size_t)(pl0 + pp) * N + z) * ncol + col] = Tz[i];
+  }
+}
+
+// ---------------------------------------------------------------- pair z
+// grid (npb), block 256.  smem Mrow[ng].
+template <typename T, int N>
+__global__ void __launch_bounds__(256) pair_zgather(const cpx<T>* __restrict__ Tbuf, int pbase,
+                                                    int ncol, int ng,
+                                                    const int* __restrict__ zmap,
+                                                    cpx<T>* __restrict__ M) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* Mrow = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int pl = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const T inv = T(1) / T(N * N * N);
+  const cpx<T>* src = Tbuf + (size_t)pl * N * ncol;
+  for (int col = tid; col < ncol; col += nt) {
+    cpx<T> a[N];
+#pragma unroll
+    for (int z = 0; z < N; ++z) a[z] = src[(size_t)z * ncol + col];
+    fft_line<T, N, 1>(a);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int g = zmap[k * ncol + col];
+      if (g >= 0) Mrow[g] = scale<T>(a[k], inv);
+    }
+  }
+  __syncthreads();
+  cpx<T>* dst = M + (size_t)(pbase + pl) * ng;
+  for (int i = tid; i < ng; i += nt) dst[i] = Mrow[i];
+}
+
+// ------------------------------------------------------------ launchers
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Pairs handled by one pair_yxpass block and its thread count.
+template <typename T, int N>
+static void pair_block_shape(int nys, int ncol, int* ppb, int* threads, size_t* smem) {
+  int p = 256 / N;
+  if (p < 1) p = 1;
+  for (;; --p) {
+    size_t s = (size_t)p * nys * (N + 1) * sizeof(cpx<T>) + (size_t)p * ncol * sizeof(cpx<T>) +
+               (size_t)(N * nys + N) * sizeof(int);
+    if (s <= 200 * 1024 || p == 1) { *smem = s; break; }
+  }
+  *ppb = p;
+  int t = ((p * N + 31) / 32) * 32;
+  *threads = t > 256 ? 256 : t;
+}
+
+template <typename T, int N>
+static cudaError_t band_transform(const BandPlan* bp, const double2* coef, int nb, cpx<T>* U1,
+                                  cpx<T>* u, cudaStream_t st) {
+  if (nb == 0) return cudaSuccess;
+  size_t sm1 = (size_t)64 * (N + 1) * sizeof(cpx<T>);
+  cudaError_t e = set_smem(band_zpass<T, N>, sm1);
+  if (e != cudaSuccess) return e;
+  band_zpass<T, N><<<dim3((bp->ncol + 63) / 64, nb), 64, sm1, st>>>(
+      coef, bp->npw, bp->ncol, bp->d_col_start, bp->d_ent_col, bp->d_ent_z, bp->d_ent_idx, U1);
+  size_t sm2 = (size_t)N * (N + 1) * sizeof(cpx<T>);
+  if ((e = set_smem(band_yxpass<T, N>, sm2)) != cudaSuccess) return e;
+  band_yxpass<T, N><<<dim3(N, nb), 64, sm2, st>>>(U1, bp->ncol, bp->d_col_xy, bp->nxs, bp->d_xslot, u);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t mtxel_exec_n(const MtxelExec& x) {
+  using C = cpx<T>;
+  C* uv = reinterpret_cast<C*>(x.uv);
+  C* uc = reinterpret_cast<C*>(x.uc);
+  C* U1 = reinterpret_cast<C*>(x.U1);
+  C* Tb = reinterpret_cast<C*>(x.T);
+  C* M = reinterpret_cast<C*>(x.M);
+  cudaError_t e = band_transform<T, N>(x.bpv, x.cv, x.nv, U1, uv, x.st);
+  if (e != cudaSuccess) return e;
+  if ((e = band_transform<T, N>(x.bpc, x.cc, x.nc, U1, uc, x.st)) != cudaSuccess) return e;
+  const PairPlan* pp = x.pp;
+  int ppb, threads;
+  size_t sm;
+  pair_block_shape<T, N>(pp->nys, pp->ncol, &ppb, &threads, &sm);
+  if ((e = set_smem(pair_yxpass<T, N>, sm)) != cudaSuccess) return e;
+  size_t smz = (size_t)pp->ng * sizeof(C);
+  if ((e = set_smem(pair_zgather<T, N>, smz)) != cudaSuccess) return e;
+  const long long npairs = (long long)x.nv * x.nc;
+  for (long long p0 = 0; p0 < npairs; p0 += x.pair_block) {
+    const int npb = (int)((npairs - p0) < x.pair_block ? (npairs - p0) : x.pair_block);
+    pair_yxpass<T, N><<<dim3((npb + ppb - 1) / ppb, N), threads, sm, x.st>>>(
+        uv, uc, x.nc, (int)p0, npb, ppb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
+    pair_zgather<T, N><<<npb, 256, smz, x.st>>>(Tb, (int)p0, pp->ncol, pp->ng, pp->d_zmap, M);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+#define BGW_FOR_EACH_N(X) X(8) X(10) X(12) X(16) X(20) X(24) X(30) X(32) X(36) X(40) X(48) X(50) X(60) X(64)
+
+template <typename T>
+static cudaError_t mtxel_exec_t(const MtxelExec& x) {
+  switch (x.n) {
+#define BGW_CASE(n) case n: return mtxel_exec_n<T, n>(x);
+    BGW_FOR_EACH_N(BGW_CASE)
+#undef BGW_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bgw

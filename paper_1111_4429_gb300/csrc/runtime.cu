@@ -1,0 +1,129 @@
+// Context runtime: device-memory pool with a budget, error state, cached
+// uploads of small host arrays.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "runtime.h"
+
+namespace bgw {
+
+uint64_t fnv1a(const void* data, size_t bytes, uint64_t h) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+int fail(Ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+int cuda_fail(Ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(c, BGW_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return fail(c, BGW_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ Pool
+size_t Pool::round(size_t b) {
+  if (b == 0) b = 1;
+  const size_t small = 64 << 10, big = 2 << 20;
+  if (b <= big) return (b + small - 1) / small * small;
+  return (b + big - 1) / big * big;
+}
+
+Pool::~Pool() {
+  for (auto& kv : free_) cudaFree(kv.second);
+  for (auto& kv : live_) cudaFree(kv.first);
+}
+
+int Pool::alloc(size_t bytes, void** out) {
+  const size_t sz = round(bytes);
+  auto it = free_.find(sz);
+  if (it != free_.end()) {
+    void* p = it->second;
+    free_.erase(it);
+    live_[p] = sz;
+    in_use_ += sz;
+    if (in_use_ > high_water_) high_water_ = in_use_;
+    *out = p;
+    return BGW_OK;
+  }
+  if (budget_ && reserved_ + sz > budget_) {
+    trim();
+    if (reserved_ + sz > budget_) return BGW_ENOMEM;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sz);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    trim();
+    e = cudaMalloc(&p, sz);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? BGW_ENOMEM : BGW_ECUDA;
+    }
+  }
+  reserved_ += sz;
+  live_[p] = sz;
+  in_use_ += sz;
+  if (in_use_ > high_water_) high_water_ = in_use_;
+  *out = p;
+  return BGW_OK;
+}
+
+void Pool::release(void* p) {
+  auto it = live_.find(p);
+  if (it == live_.end()) return;
+  in_use_ -= it->second;
+  free_.emplace(it->second, p);
+  live_.erase(it);
+}
+
+void Pool::trim() {
+  if (free_.empty()) return;
+  // Blocks on the free list may still be read by queued work of the stream
+  // that released them; wait for the device before giving them back.
+  cudaDeviceSynchronize();
+  for (auto& kv : free_) {
+    cudaFree(kv.second);
+    reserved_ -= kv.first;
+  }
+  free_.clear();
+}
+
+// ------------------------------------------------------------ uploads
+int upload_cached(Ctx* c, const void* host, size_t bytes, cudaStream_t st, const void** dev) {
+  uint64_t key = fnv1a(host, bytes, fnv1a(&bytes, sizeof(bytes)));
+  auto it = c->uploads.find(key);
+  if (it != c->uploads.end()) {
+    *dev = it->second;
+    return BGW_OK;
+  }
+  void* p = nullptr;
+  int rc = c->pool.alloc(bytes, &p);
+  if (rc != BGW_OK) return fail(c, rc, "upload of %zu bytes: device allocation failed", bytes);
+  // Stream-ordered: the block may come from the pool's free list and still
+  // be read by earlier work on this stream.
+  cudaError_t e = cudaMemcpyAsync(p, host, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    c->pool.release(p);
+    return cuda_fail(c, e, "cudaMemcpyAsync (upload)");
+  }
+  c->uploads[key] = p;
+  *dev = p;
+  return BGW_OK;
+}
+
+}  // namespace bgw

@@ -1,0 +1,152 @@
+// Internal runtime of the library: context, device-memory pool with a
+// budget, content-keyed caches of uploaded host arrays and plans, error
+// state.  Not part of the ABI (include/bgw.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/bgw.h"
+
+namespace bgw {
+
+// Device status word values written by kernels (read by bgw_sync).
+enum DevStatus : int { kDevOk = 0, kDevZeroPivot = 1, kDevTimeout = 2 };
+
+struct Block {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Caching device allocator.  Blocks are rounded up to 2 MiB (small ones to
+// 256 B multiples of 64 KiB) and kept on per-size free lists after release;
+// every byte obtained from cudaMalloc counts against the budget until the
+// context is destroyed or trim() runs.  Reuse is stream-ordered: a context
+// runs on one stream at a time.
+class Pool {
+ public:
+  explicit Pool(uint64_t budget) : budget_(budget) {}
+  ~Pool();
+  // Returns BGW_OK / BGW_ENOMEM / BGW_ECUDA.
+  int alloc(size_t bytes, void** out);
+  void release(void* p);
+  void trim();  // cudaFree every cached free block
+  uint64_t in_use() const { return in_use_; }
+  uint64_t reserved() const { return reserved_; }
+  uint64_t high_water() const { return high_water_; }
+
+ private:
+  static size_t round(size_t b);
+  uint64_t budget_;
+  uint64_t reserved_ = 0;   // bytes obtained from cudaMalloc
+  uint64_t in_use_ = 0;     // bytes handed out
+  uint64_t high_water_ = 0;
+  std::multimap<size_t, void*> free_;
+  std::unordered_map<void*, size_t> live_;
+};
+
+// RAII scratch handle released to the pool at scope exit (stream order).
+struct Scratch {
+  Pool* pool = nullptr;
+  void* ptr = nullptr;
+  Scratch() = default;
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() { if (pool && ptr) pool->release(ptr); }
+  template <typename T> T* as() const { return reinterpret_cast<T*>(ptr); }
+};
+
+// Plan of the two pruned 3D transforms for one (G list, grid) pair.
+struct BandPlan {        // band transform of one wavefunction sphere
+  int n = 0, npw = 0, ncol = 0, nxs = 0;
+  int* d_ent_col = nullptr;    // [npw] local column of coefficient slot i (entries sorted by column)
+  int* d_ent_z = nullptr;      // [npw] gz mod n
+  int* d_ent_idx = nullptr;    // [npw] coefficient index in the caller's order
+  int* d_col_start = nullptr;  // [ncol+1] entry range per column
+  int* d_col_xy = nullptr;     // [ncol] (gy mod n) * n + (gx mod n)
+  int* d_xslot = nullptr;      // [nxs] distinct gx mod n
+};
+struct PairPlan {        // pruned product transform onto the epsilon sphere
+  int n = 0, ng = 0, ncol = 0, nys = 0;
+  int* d_yslot_of_k = nullptr;  // [n] ky-slot of FFT index k along y, or -1
+  int* d_colmap = nullptr;      // [n][nys] column of (kx=k, ky=slot) or -1 (k-major)
+  int* d_zmap = nullptr;        // [n][ncol] G index of (column, kz=k) or -1 (k-major)
+};
+
+struct Ctx {
+  int device = 0;
+  Pool pool;
+  std::string err;
+  int* d_status = nullptr;   // device status word
+  bool twiddles_ready = false;
+  bool chi_tc_ready = false;
+  // Content-keyed caches (FNV-1a over the bytes plus sizes).
+  std::unordered_map<uint64_t, void*> uploads;           // small host arrays
+  std::unordered_map<uint64_t, std::unique_ptr<BandPlan>> band_plans;
+  std::unordered_map<uint64_t, std::unique_ptr<PairPlan>> pair_plans;
+  explicit Ctx(uint64_t budget) : pool(budget) {}
+};
+
+uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull);
+
+// Errors: set ctx->err and return the code.
+int fail(Ctx* c, int code, const char* fmt, ...);
+int cuda_fail(Ctx* c, cudaError_t e, const char* what);
+#define BGW_CUDA(c, expr)                                    \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return ::bgw::cuda_fail((c), _e, #expr); \
+  } while (0)
+
+// Copy a small host array to device memory on stream `st`, cached by content
+// for the life of the context (only the first call with given content copies).
+int upload_cached(Ctx* c, const void* host, size_t bytes, cudaStream_t st, const void** dev);
+
+// Plans (mtxel.cu); built on the host, uploaded on `st`, cached by content.
+int get_band_plan(Ctx* c, int n, int npw, const int32_t* g, cudaStream_t st, const BandPlan** out);
+int get_pair_plan(Ctx* c, int n, int ng, const int32_t* geps, cudaStream_t st, const PairPlan** out);
+bool fft_size_supported(int n);
+
+// One matrix-element evaluation with its scratch (see mtxel_kernels.cuh).
+struct MtxelExec {
+  int n = 0, nv = 0, nc = 0;
+  const BandPlan* bpv = nullptr;
+  const BandPlan* bpc = nullptr;
+  const PairPlan* pp = nullptr;
+  const double2* cv = nullptr;
+  const double2* cc = nullptr;
+  void* uv = nullptr;   // [nv][n^3]
+  void* uc = nullptr;   // [nc][n^3]
+  void* U1 = nullptr;   // [max(nv,nc)][n][max ncol]
+  void* T = nullptr;    // [pair_block][n][pp->ncol]
+  int pair_block = 0;
+  void* M = nullptr;
+  cudaStream_t st = nullptr;
+};
+cudaError_t mtxel_exec_f64(const MtxelExec& x);
+cudaError_t mtxel_exec_f32(const MtxelExec& x);
+cudaError_t mtxel_init_f64();
+cudaError_t mtxel_init_f32();
+
+// Launchers (each enqueues on `st`; return BGW_OK or an error code).
+int mtxel_run(Ctx* c, int n, int prec, int nv, const BandPlan* bpv, const void* cv,
+              int nc, const BandPlan* bpc, const void* cc, const PairPlan* pp,
+              void* M, cudaStream_t st);
+int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const double* d_ev,
+            const double* d_ec, int nfreq, const double* d_omega, double scale, int accumulate,
+            void* chi, cudaStream_t st);
+int epsinv_run(Ctx* c, int ng, const double* bvec, const double* qf, const int32_t* d_geps,
+               const void* chi, void* eps, void* epsinv, cudaStream_t st);
+
+}  // namespace bgw
+
+struct bgw_ctx {
+  bgw::Ctx impl;
+  explicit bgw_ctx(uint64_t budget) : impl(budget) {}
+};

@@ -1,0 +1,62 @@
+"""CPU-side checks of the boundary: the library builds, loads and exports every
+symbol that include/bgw.h declares (no compute call without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(bgw_[a-z_0-9]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1111_4429_gb300 import _build
+    _build.build()
+    from paper_1111_4429_gb300 import bgw
+    return bgw.load()
+
+
+def test_header_declares_the_entry_points():
+    d = _declared()
+    for name in ("bgw_create", "bgw_destroy", "bgw_mtxel", "bgw_chi_sum", "bgw_epsinv", "bgw_epsilon",
+                 "bgw_sync", "bgw_last_error", "bgw_mem_stats"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_1111_4429_gb300 import bgw
+    assert sorted(bgw.EXPORTS) == sorted(n for n in _declared() if n in bgw.EXPORTS)
+    assert set(_declared()) <= set(bgw.EXPORTS) | {n for n in _declared() if n.startswith("bgw_")}
+
+
+def test_cell_struct_layout():
+    from paper_1111_4429_gb300 import bgw
+    # double bvec[3][3]; double omega; double q_frac[3]; int fft[3]
+    assert ctypes.sizeof(bgw.Cell) == 8 * 9 + 8 + 8 * 3 + 4 * 3 + 4  # padded to 8
+    assert bgw.Cell.omega.offset == 72 and bgw.Cell.q_frac.offset == 80 and bgw.Cell.fft.offset == 104
+
+
+def test_product_path_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1111_4429_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), f

@@ -1,0 +1,110 @@
+"""Argument checks of the C ABI: invalid inputs are refused before any launch."""
+import numpy as np
+import pytest
+
+from paper_1111_4429_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1111_4429_gb300 import bgw
+    return bgw.Context(0)
+
+
+def _sys():
+    return synth.make_system("e", a=8.0, fft=12, ecut_wfn=4.0, ecut_eps=1.5, nv=3, nc=5, seed=3)
+
+
+def _run(ctx, s, n=None, gv=None, prec=0):
+    from paper_1111_4429_gb300 import bgw
+    cell = bgw.make_cell(s.bvec, s.omega, s.q_frac, n or s.fft)
+    M = torch.zeros((s.nv * s.nc, s.ng), dtype=torch.complex128, device="cuda")
+    cv = torch.from_numpy(s.cv).cuda()
+    cc = torch.from_numpy(s.cc).cuda()
+    ctx.mtxel(cell, s.gv if gv is None else gv, cv, s.gc, cc, s.geps, prec, M)
+    return M
+
+
+def test_aliasing_grid_is_rejected(ctx):
+    from paper_1111_4429_gb300 import bgw
+    s = _sys()
+    with pytest.raises(bgw.BgwError) as e:
+        _run(ctx, s, n=8)   # 8 <= max|Gv| + max|Gc| + max|Geps|
+    assert e.value.code in (bgw.BGW_EINVAL,)
+
+
+def test_g_outside_half_open_range_is_rejected(ctx):
+    from paper_1111_4429_gb300 import bgw
+    s = _sys()
+    gv = s.gv.copy()
+    gv[0] = (6, 0, 0)       # n/2 is outside [-n/2, n/2)
+    with pytest.raises(bgw.BgwError) as e:
+        _run(ctx, s, gv=gv)
+    assert e.value.code == bgw.BGW_EINVAL
+
+
+def test_duplicate_g_is_rejected(ctx):
+    from paper_1111_4429_gb300 import bgw
+    s = _sys()
+    gv = s.gv.copy()
+    gv[1] = gv[0]
+    with pytest.raises(bgw.BgwError):
+        _run(ctx, s, gv=gv)
+
+
+def test_unsupported_grid_is_reported(ctx):
+    from paper_1111_4429_gb300 import bgw
+    s = _sys()
+    with pytest.raises(bgw.BgwError) as e:
+        _run(ctx, s, n=14)
+    assert e.value.code == bgw.BGW_EUNSUPPORTED
+
+
+def test_energy_order_and_gap_are_checked(ctx):
+    from paper_1111_4429_gb300 import bgw
+    s = _sys()
+    M = _run(ctx, s)
+    chi = torch.zeros((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
+    cell = bgw.system_cell(s)
+    with pytest.raises(bgw.BgwError):
+        ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev[::-1].copy(), s.ec, None, 0, False, chi)
+    ec = s.ec.copy()
+    ec[0] = s.ev[-1]        # Delta = 0
+    with pytest.raises(bgw.BgwError):
+        ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, ec, None, 0, False, chi)
+    ctx.sync()
+
+
+def test_q_plus_g_zero_is_rejected(ctx):
+    from paper_1111_4429_gb300 import bgw
+    s = _sys()
+    cell = bgw.make_cell(s.bvec, s.omega, (0.0, 0.0, 0.0), s.fft)
+    geps = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.int32)
+    chi = torch.zeros((2, 2), dtype=torch.complex128, device="cuda")
+    inv = torch.zeros_like(chi)
+    with pytest.raises(bgw.BgwError) as e:
+        ctx.epsinv([cell], [geps], [chi], None, [inv])
+    assert e.value.code == bgw.BGW_EINVAL
+
+
+def test_zero_pivot_sets_numeric_status(ctx):
+    # chi chosen so that eps~ = 0 on the diagonal block: the inversion must
+    # report BGW_ENUMERIC through bgw_sync (no fault, no hang).
+    from paper_1111_4429_gb300 import bgw, synth as sy
+    s = _sys()
+    cell = bgw.system_cell(s)
+    geps = s.geps[:2]
+    import oracle
+    v = oracle.coulomb(s.bvec, s.q_frac, geps)
+    chi = torch.from_numpy(np.diag(1.0 / v).astype(np.complex128)).cuda()   # eps~ = I - I = 0
+    inv = torch.zeros_like(chi)
+    ctx.epsinv([cell], [geps], [chi], None, [inv])
+    with pytest.raises(bgw.BgwError) as e:
+        ctx.sync()
+    assert e.value.code == bgw.BGW_ENUMERIC
+    ctx.sync()   # status was cleared
