@@ -103,6 +103,9 @@ int bgw_sync(bgw_ctx* ctx, void* stream);
 /* Bytes the library currently holds on the device, and the high-water mark. */
 int bgw_mem_stats(bgw_ctx* ctx, uint64_t* in_use, uint64_t* high_water);
 
+/* Number of kernels this context has launched since it was created.        */
+int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
+
 /* ------------------------------------------------------------------------
  * bgw_mtxel -- plane-wave matrix elements (Eq. eqn_matrix_elem), computed as
  * the FFT of the real-space product of the two bands (paper's equation

@@ -23,7 +23,8 @@ BGW_PREC_FP64, BGW_PREC_MIX_FP16, BGW_PREC_MIX_BF16 = 0, 1, 2
 PREC = {"fp64": BGW_PREC_FP64, "mix_fp16": BGW_PREC_MIX_FP16, "mix_bf16": BGW_PREC_MIX_BF16}
 
 # Every symbol include/bgw.h declares.
-EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_stats", "bgw_mtxel",
+EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_stats", "bgw_launch_count",
+           "bgw_mtxel",
            "bgw_chi_sum", "bgw_epsinv", "bgw_epsilon")
 
 
@@ -74,6 +75,7 @@ def load() -> ctypes.CDLL:
     lib.bgw_last_error.restype = ctypes.c_char_p
     lib.bgw_sync.argtypes = [vp, vp]
     lib.bgw_mem_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    lib.bgw_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.bgw_mtxel.argtypes = [vp, cellp, ci, ci, i32p, vp, ci, ci, i32p, vp, ci, i32p, ci, vp, vp]
     lib.bgw_chi_sum.argtypes = [vp, cellp, ci, ci, ci, vp, dp, dp, ci, dp, ci, ci, vp, vp]
     lib.bgw_epsinv.argtypes = [vp, ci, cellp, ctypes.POINTER(ci), ctypes.POINTER(i32p), ctypes.POINTER(vp),
@@ -148,6 +150,11 @@ class Context:
         a, b = ctypes.c_uint64(), ctypes.c_uint64()
         self._check(self.lib.bgw_mem_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def launch_count(self) -> int:
+        a = ctypes.c_uint64()
+        self._check(self.lib.bgw_launch_count(self.h, ctypes.byref(a)))
+        return a.value
 
     def mtxel(self, cell: Cell, gv, cv, gc, cc, geps, prec: int, M, stream=None):
         gv_, gvp = _i32(gv)

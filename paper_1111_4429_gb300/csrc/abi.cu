@@ -206,6 +206,13 @@ int bgw_mem_stats(bgw_ctx* ctx, uint64_t* in_use, uint64_t* high_water) {
   return BGW_OK;
 }
 
+int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches) {
+  Ctx* c = impl(ctx);
+  if (!c || !launches) return BGW_EINVAL;
+  *launches = c->launches;
+  return BGW_OK;
+}
+
 int bgw_mtxel(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv, int nc,
               int npw_c, const int32_t* gc, const void* cc, int ng, const int32_t* geps, int prec, void* M,
               void* stream) {

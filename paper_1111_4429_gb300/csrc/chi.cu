@@ -134,6 +134,7 @@ int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const doubl
   chi_weights_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(d_ev, d_ec, nv, nc, nrow, d_omega,
                                                                    nfreq == 0, w.as<double>());
   BGW_CUDA(c, cudaGetLastError());
+  c->launches += 1;
   if (prec != BGW_PREC_FP64)
     return chi_mixed_run(c, prec, K, ng, M, w.as<double>(), nrow, scale, accumulate, chi, st);
   const int nt = (ng + TB - 1) / TB;
@@ -143,6 +144,7 @@ int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const doubl
                                                       w.as<double>() + (size_t)f * K, scale, accumulate,
                                                       static_cast<double2*>(chi) + (size_t)f * ng * ng);
     BGW_CUDA(c, cudaGetLastError());
+    c->launches += 1;
   }
   return BGW_OK;
 }

@@ -209,6 +209,7 @@ int epsinv_run(Ctx* c, int ng, const double* bvec, const double* qf, const int32
   eps_form_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(chi), sv.as<double>(), ng, A,
                                       static_cast<double2*>(eps));
   BGW_CUDA(c, cudaGetLastError());
+  c->launches += 2;
   const int nt = (ng + TU - 1) / TU;
   const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
   BGW_CUDA(c, cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
@@ -219,6 +220,7 @@ int epsinv_run(Ctx* c, int ng, const double* bvec, const double* qf, const int32
         A, ng, k0, kb, dinv.as<double2>(), R.as<double2>(), Cp.as<double2>());
     gj_update_kernel<<<dim3(nt, nt), 256, upd_smem, st>>>(A, ng, k0, kb, R.as<double2>(), Cp.as<double2>());
     BGW_CUDA(c, cudaGetLastError());
+    c->launches += 3;
   }
   return BGW_OK;
 }

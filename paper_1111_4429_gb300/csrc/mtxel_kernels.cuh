@@ -242,6 +242,7 @@ static cudaError_t mtxel_exec_n(const MtxelExec& x) {
   cudaError_t e = band_transform<T, N>(x.bpv, x.cv, x.nv, U1, uv, x.st);
   if (e != cudaSuccess) return e;
   if ((e = band_transform<T, N>(x.bpc, x.cc, x.nc, U1, uc, x.st)) != cudaSuccess) return e;
+  *x.launches += 4;
   const PairPlan* pp = x.pp;
   int ppb, threads;
   size_t sm;
@@ -256,6 +257,7 @@ static cudaError_t mtxel_exec_n(const MtxelExec& x) {
         uv, uc, x.nc, (int)p0, npb, ppb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
     pair_zgather<T, N><<<npb, 256, smz, x.st>>>(Tb, (int)p0, pp->ncol, pp->ng, pp->d_zmap, M);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *x.launches += 2;
   }
   return cudaSuccess;
 }

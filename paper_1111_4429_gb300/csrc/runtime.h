@@ -86,6 +86,7 @@ struct Ctx {
   int* d_status = nullptr;   // device status word
   bool twiddles_ready = false;
   bool chi_tc_ready = false;
+  uint64_t launches = 0;     // kernels launched by this context
   // Content-keyed caches (FNV-1a over the bytes plus sizes).
   std::unordered_map<uint64_t, void*> uploads;           // small host arrays
   std::unordered_map<uint64_t, std::unique_ptr<BandPlan>> band_plans;
@@ -128,6 +129,7 @@ struct MtxelExec {
   int pair_block = 0;
   void* M = nullptr;
   cudaStream_t st = nullptr;
+  uint64_t* launches = nullptr;  // incremented per kernel launch
 };
 cudaError_t mtxel_exec_f64(const MtxelExec& x);
 cudaError_t mtxel_exec_f32(const MtxelExec& x);
