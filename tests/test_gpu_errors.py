@@ -32,10 +32,13 @@ def _run(ctx, s, n=None, gv=None, prec=0):
 
 def test_aliasing_grid_is_rejected(ctx):
     from paper_1111_4429_gb300 import bgw
-    s = _sys()
+    s = synth.config_system("c0")        # max|Gv| + max|Gc| + max|Geps| = 5 + 5 + 2
     with pytest.raises(bgw.BgwError) as e:
-        _run(ctx, s, n=8)   # 8 <= max|Gv| + max|Gc| + max|Geps|
-    assert e.value.code in (bgw.BGW_EINVAL,)
+        _run(ctx, s, n=12)               # components fit [-6, 6) but 12 <= 12 aliases
+    assert e.value.code == bgw.BGW_EINVAL
+    assert "aliases" in str(e.value)
+    _run(ctx, s, n=20)                   # the configured grid is accepted
+    ctx.sync()
 
 
 def test_g_outside_half_open_range_is_rejected(ctx):
