@@ -298,6 +298,28 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_profile_case(args):
+    """One solve of a reduced c1 case for ncu captures: c1 cell and spheres
+    with N_c = 200 (K = 6400 pairs, M = 217 MB > L2, about 1.5 GB on the
+    device), after one warm-up solve."""
+    import torch
+    from paper_1111_4429_gb300 import bgw, synth
+    s = synth.config_system("c1", nc=200)
+    ctx = bgw.Context(0)
+    cell = bgw.system_cell(s)
+    cv = torch.from_numpy(s.cv).cuda()
+    cc = torch.from_numpy(s.cc).cuda()
+    M = torch.empty((s.npairs, s.ng), dtype=torch.complex128, device="cuda")
+    chi = torch.empty((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
+    inv = torch.empty_like(chi)
+    for _ in range(2):
+        ctx.mtxel(cell, s.gv, cv, s.gc, cc, s.geps, 0, M)
+        ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, s.ec, None, 0, False, chi)
+        ctx.epsinv([cell], [s.geps], [chi], None, [inv])
+    ctx.sync()
+    print(json.dumps({"profile_case": "c1 cell, N_c=200", "launches": ctx.launch_count()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,8 +327,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true", help="reduced c1 solve for ncu captures")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
