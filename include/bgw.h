@@ -169,6 +169,32 @@ int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
                void* const* eps, void* const* epsinv, void* stream);
 
 /* ------------------------------------------------------------------------
+ * bgw_epsinv_noalloc -- bgw_epsinv for one matrix without any device
+ * allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc, such as an application whose own
+ * allocator has already reserved the device memory it may use (a serving
+ * engine or framework holding the GPU's memory in its caching pool), or a
+ * loop that cannot accept the device-wide synchronization an allocation may
+ * cause.  It needs no bgw_ctx and runs on the caller's current device.
+ *   cell, ng, geps  as bgw_epsinv (geps host int32 [ng][3])
+ *   chi     device c128 [ng][ng] (read only)
+ *   eps     device c128 [ng][ng] or NULL (eps~ is also written there)
+ *   epsinv  device c128 [ng][ng]
+ * Scratch: one fixed file-scope device array of about 4.1 MiB inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits; it bounds ng <= 4096 (larger ng returns BGW_EINVAL).  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress,
+ * with the device current) and caches it; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents, so calls whose work overlaps on the GPU (other streams, other
+ * host threads) race: serialize them.  Returns BGW_EINVAL for bad
+ * arguments or |q+G| = 0, BGW_ECUDA when a CUDA call fails.  A zero or
+ * non-finite pivot is not reported (there is no context to carry the status
+ * word); the result is then meaningless.                                   */
+int bgw_epsinv_noalloc(const bgw_cell* cell, int ng, const int32_t* geps,
+                       const void* chi, void* eps, void* epsinv, void* stream);
+
+/* ------------------------------------------------------------------------
  * bgw_epsilon -- the whole path for one q-point and nfreq frequencies
  * (nfreq = 0: static): bgw_mtxel, bgw_chi_sum over conduction chunks of at
  * most `nc_chunk` bands (0 = all at once), then bgw_epsinv per frequency.

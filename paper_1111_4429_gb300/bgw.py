@@ -25,7 +25,7 @@ PREC = {"fp64": BGW_PREC_FP64, "mix_fp16": BGW_PREC_MIX_FP16, "mix_bf16": BGW_PR
 # Every symbol include/bgw.h declares.
 EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_stats", "bgw_launch_count",
            "bgw_mtxel",
-           "bgw_chi_sum", "bgw_epsinv", "bgw_epsilon")
+           "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_epsilon")
 
 
 class BgwError(RuntimeError):
@@ -80,6 +80,7 @@ def load() -> ctypes.CDLL:
     lib.bgw_chi_sum.argtypes = [vp, cellp, ci, ci, ci, vp, dp, dp, ci, dp, ci, ci, vp, vp]
     lib.bgw_epsinv.argtypes = [vp, ci, cellp, ctypes.POINTER(ci), ctypes.POINTER(i32p), ctypes.POINTER(vp),
                                ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.bgw_epsinv_noalloc.argtypes = [cellp, ci, i32p, vp, vp, vp, vp]
     lib.bgw_epsilon.argtypes = [vp, cellp, ci, ci, i32p, vp, dp, ci, ci, i32p, vp, dp, ci, i32p, ci, dp, ci,
                                 ci, vp, vp, vp]
     for name in EXPORTS:
@@ -114,6 +115,17 @@ def _stream(stream) -> Optional[int]:
         return stream if isinstance(stream, int) else stream.cuda_stream
     import torch
     return torch.cuda.current_stream().cuda_stream
+
+
+def epsinv_noalloc(cell: Cell, geps, chi, eps, epsinv, stream=None) -> None:
+    """bgw_epsinv_noalloc: the inverse of one matrix with no device allocation
+    (scratch in a fixed array inside the library; ng <= 4096; current device)."""
+    lib = load()
+    ge_, gep = _i32(geps)
+    rc = lib.bgw_epsinv_noalloc(ctypes.byref(cell), ge_.shape[0], gep, _ptr(chi), _ptr(eps), _ptr(epsinv),
+                                _stream(stream))
+    if rc != BGW_OK:
+        raise BgwError(rc, "bgw_epsinv_noalloc failed")
 
 
 class Context:

@@ -225,4 +225,112 @@ int epsinv_run(Ctx* c, int ng, const double* bvec, const double* qf, const int32
   return BGW_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free inverse: bgw_epsinv_noalloc (include/bgw.h).
+//
+// Same kernels and launch sequence as epsinv_run, but every scratch buffer
+// (Coulomb factors, the G list, the diagonal-block inverse, the two panels and
+// the status word) lives in one file-scope device array of fixed size, so the
+// call makes no device allocation.  The array is part of the library's device
+// image: every GPU that loads the library holds it until the process exits.
+namespace {
+constexpr int kNoAllocMaxNg = 4096;
+// Byte offsets inside the array; each region starts on a 256-byte boundary.
+constexpr size_t kNaSv = 0;                                                // double[kNoAllocMaxNg]
+constexpr size_t kNaDinv = kNaSv + sizeof(double) * kNoAllocMaxNg;          // double2[NB*NB]
+constexpr size_t kNaR = kNaDinv + sizeof(double2) * NB * NB;                // double2[NB*kNoAllocMaxNg]
+constexpr size_t kNaC = kNaR + sizeof(double2) * NB * kNoAllocMaxNg;        // double2[kNoAllocMaxNg*NB]
+constexpr size_t kNaGeps = kNaC + sizeof(double2) * NB * kNoAllocMaxNg;     // int32[3*kNoAllocMaxNg]
+constexpr size_t kNaStatus = kNaGeps + sizeof(int32_t) * 3 * kNoAllocMaxNg; // int
+constexpr size_t kNaBytes = kNaStatus + 256;
+static_assert(kNaDinv % 256 == 0 && kNaR % 256 == 0 && kNaC % 256 == 0 && kNaGeps % 256 == 0 &&
+                  kNaStatus % 256 == 0,
+              "scratch regions must stay 256-byte aligned");
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+// The scratch itself (about 4.1 MiB).  Host code must not use this name as an
+// address: it is a host-side stand-in; the device address comes from
+// cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the lookup needs that device current).
+static cudaError_t noalloc_scratch_address(unsigned char** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (!p) return cudaErrorInvalidSymbol;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return cudaSuccess;
+}
+
 }  // namespace bgw
+
+extern "C" int bgw_epsinv_noalloc(const bgw_cell* cell, int ng, const int32_t* geps, const void* chi, void* eps,
+                                  void* epsinv, void* stream) {
+  using namespace bgw;
+  if (!cell || !geps || !chi || !epsinv || ng <= 0) return BGW_EINVAL;
+  if (ng > kNoAllocMaxNg) return BGW_EINVAL;
+  for (int i = 0; i < ng; ++i) {
+    double k2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double kd = 0.0;
+      for (int a = 0; a < 3; ++a) kd += (geps[3 * i + a] + cell->q_frac[a]) * cell->bvec[a][d];
+      k2 += kd * kd;
+    }
+    if (!(k2 > 0.0)) return BGW_EINVAL;
+  }
+  unsigned char* base = nullptr;
+  if (noalloc_scratch_address(&base) != cudaSuccess) {
+    cudaGetLastError();
+    return BGW_ECUDA;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* sv = reinterpret_cast<double*>(base + kNaSv);
+  double2* dinv = reinterpret_cast<double2*>(base + kNaDinv);
+  double2* R = reinterpret_cast<double2*>(base + kNaR);
+  double2* Cp = reinterpret_cast<double2*>(base + kNaC);
+  int32_t* dgeps = reinterpret_cast<int32_t*>(base + kNaGeps);
+  int* status = reinterpret_cast<int*>(base + kNaStatus);
+  const double* bvec = &cell->bvec[0][0];
+  const double* qf = cell->q_frac;
+  // The array keeps the previous call's contents: the status word must start at 0.
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess ||
+      cudaMemcpyAsync(dgeps, geps, sizeof(int32_t) * 3 * (size_t)ng, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaGetLastError();
+    return BGW_ECUDA;
+  }
+  coulomb_sqrt_kernel<<<(ng + 255) / 256, 256, 0, st>>>(dgeps, ng, bvec[0], bvec[1], bvec[2], bvec[3], bvec[4],
+                                                        bvec[5], bvec[6], bvec[7], bvec[8], qf[0], qf[1], qf[2], sv);
+  double2* A = static_cast<double2*>(epsinv);
+  const size_t n2 = (size_t)ng * ng;
+  const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
+  eps_form_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(chi), sv, ng, A, static_cast<double2*>(eps));
+  const int nt = (ng + TU - 1) / TU;
+  const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
+  if (cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return BGW_ECUDA;
+  }
+  for (int k0 = 0; k0 < ng; k0 += NB) {
+    const int kb = std::min(NB, ng - k0);
+    gj_diag_kernel<<<1, dim3(NB, NB), 0, st>>>(A, ng, k0, kb, dinv, status);
+    gj_panels_kernel<<<dim3((ng + 63) / 64, 1 + (ng + 255) / 256), 256, 0, st>>>(A, ng, k0, kb, dinv, R, Cp);
+    gj_update_kernel<<<dim3(nt, nt), 256, upd_smem, st>>>(A, ng, k0, kb, R, Cp);
+  }
+  if (cudaGetLastError() != cudaSuccess) return BGW_ECUDA;
+  return BGW_OK;
+}
+
