@@ -106,6 +106,15 @@ int bgw_mem_stats(bgw_ctx* ctx, uint64_t* in_use, uint64_t* high_water);
 /* Number of kernels this context has launched since it was created.        */
 int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
 
+/* Tuning options of a context (EINVAL for an unknown option or value).
+ *  BGW_OPT_CHI_SEGMENT_PAIRS: mixed-precision chi accumulates the products
+ *    of this many pairs in FP32 on the tensor cores before adding them in
+ *    FP64 (rounded down to a multiple of 32; 0 restores the default, 512).
+ *    Shorter segments lower the FP32 accumulation error and cost more
+ *    workspace traffic.                                                     */
+enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1 };
+int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
+
 /* ------------------------------------------------------------------------
  * bgw_mtxel -- plane-wave matrix elements (Eq. eqn_matrix_elem), computed as
  * the FFT of the real-space product of the two bands (paper's equation

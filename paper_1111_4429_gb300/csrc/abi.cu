@@ -213,6 +213,18 @@ int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches) {
   return BGW_OK;
 }
 
+int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  if (option == BGW_OPT_CHI_SEGMENT_PAIRS) {
+    if (value < 0 || value > (1 << 24)) return fail(c, BGW_EINVAL, "segment pairs must be in [0, 2^24]");
+    if (value > 0 && value < 32) return fail(c, BGW_EINVAL, "segment pairs must be >= 32");
+    c->chi_segment_pairs = (int)value;
+    return BGW_OK;
+  }
+  return fail(c, BGW_EINVAL, "unknown option %d", option);
+}
+
 int bgw_mtxel(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv, int nc,
               int npw_c, const int32_t* gc, const void* cc, int ng, const int32_t* geps, int prec, void* M,
               void* stream) {

@@ -1,11 +1,509 @@
-// Mixed-precision polarizability on the tensor cores (placeholder until the
-// tcgen05 kernel lands).
+// Mixed-precision polarizability on the 5th-generation tensor cores (paper,
+// Eq. eqn_static_xi as the matrix product of Eq. eqn_static_xi_compact):
+//
+//   X[p][G] = M[p][G] sqrt|w_p| 2^e        (w_p < 0 always: the sign is pulled out)
+//   chi[G][G'] (+)= -(4/Omega) 2^{-2e} sum_p conj(X[p][G]) X[p][G']
+//   Re = sum_p xr(G) xr(G') + xi(G) xi(G')          Im = sum_p xr(G) xi(G') - xi(G) xr(G')
+//
+// Each real part x is split into two 16-bit numbers x = hi + lo (FP16 with a
+// power-of-two scale 2^e chosen from max|X|, or BF16 without scale) and every
+// real product is taken as hi*hi + hi*lo + lo*hi, so one complex lower-
+// triangle tile needs 12 MMAs per K step (6 into Re, 6 into Im, three of them
+// with the A operand negated).
+//
+// GEMM kernel (one CTA = one 128 x BN tile of the lower triangle and one
+// segment of KS pairs):
+//   * operands: planes P[4][NGpad][Kpad] (xr_hi, xi_hi, xr_lo, xi_lo), K-major,
+//     streamed by TMA (SWIZZLE_64B boxes of 32 pairs) through a STAGES-deep
+//     shared-memory ring guarded by mbarriers;
+//   * one thread issues tcgen05.mma (M = 128, N = BN, K = 16) into four FP32
+//     accumulators in tensor memory (Re and Im of the hi*hi products and of
+//     the corrections) and tcgen05.commit frees a stage;
+//   * four warps drain tensor memory (tcgen05.ld 32x32b) into an FP32
+//     workspace W[seg][tile][re|im][128][BN];
+//   * every wait on an mbarrier gives up after kWaitNs, records
+//     BGW_ETIMEOUT in the status word and lets the CTA release its tensor
+//     memory and return.
+// A reduce kernel adds the segments in FP64 (fixed order: deterministic) and
+// writes both triangles of the FP64 chi.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
 #include "runtime.h"
 
 namespace bgw {
-int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double* w, int nrow,
-                  double scale, int accumulate, void* chi, cudaStream_t st) {
-  (void)prec; (void)K; (void)ng; (void)M; (void)w; (void)nrow; (void)scale; (void)accumulate; (void)chi; (void)st;
-  return fail(c, BGW_EUNSUPPORTED, "mixed-precision chi is not built yet");
+
+namespace tc {
+
+constexpr int BM = 128;          // tile rows (G)
+constexpr int BK = 32;           // pairs per TMA box / stage (64 B of 16-bit values)
+constexpr int kThreads = 128;    // 4 warps
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the barrier did not complete within kWaitNs or the
+// CTA is aborting.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of
+// 64 bytes, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address
+  d |= (uint64_t)1u << 16;                            // leading byte offset (unused here)
+  d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;       // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1u << 46;                            // descriptor version
+  d |= (uint64_t)4u << 61;                            // SWIZZLE_64B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, A/B FP16 or BF16,
+// K-major A and B, optional negation of A.
+__host__ __device__ constexpr uint32_t idesc(int n, bool bf16, bool neg_a) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((neg_a ? 1u : 0u) << 13) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+template <int BN>
+struct Layout {
+  static constexpr int kATile = BM * BK * 2;    // bytes of one A-side plane tile
+  static constexpr int kBTile = BN * BK * 2;    // bytes of one B-side plane tile
+  static constexpr int kStage = 4 * kATile + 4 * kBTile;
+  // Four FP32 accumulators of BN columns: Re and Im of the hi*hi products
+  // (the large values) and of the hi*lo + lo*hi corrections.  Keeping the
+  // corrections apart cuts the adds into the large accumulators threefold;
+  // the accumulator's rounding error grows with the number of adds.
+  static constexpr int kTmemCols = 4 * BN;
+};
+
+// grid: nseg * ntiles CTAs (segment-major), block 128, dynamic smem
+// STAGES * stage + 1 KiB (alignment) + barriers.
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    chi_tc_kernel(const __grid_constant__ CUtensorMap tmap, int ngpad, int nkb, int kb_per_seg, int ntiles,
+                  const int2* __restrict__ tiles, int bf16, float* __restrict__ work, int* __restrict__ status) {
+  using L = Layout<BN>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = blockIdx.x / ntiles, tix = blockIdx.x - seg * ntiles;
+  const int2 tile = tiles[tix];
+  const int row0 = tile.x * BM, col0 = tile.y * BN;
+  const int kb0 = seg * kb_per_seg;
+  const int kb1 = min(nkb, kb0 + kb_per_seg);
+  const int nk = kb1 - kb0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)L::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t t_re = tmem, t_im = tmem + BN, t_rec = tmem + 2 * BN, t_imc = tmem + 3 * BN;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % STAGES;
+      if (i >= STAGES && !mbar_wait(&empty[s], ((i / STAGES) - 1) & 1, abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      unsigned char* st = smem + s * L::kStage;
+      mbar_expect_tx(&full[s], L::kStage);
+      const int kx = (kb0 + i) * BK;
+#pragma unroll
+      for (int pl = 0; pl < 4; ++pl) {
+        tma_load_2d(st + pl * L::kATile, &tmap, &full[s], kx, pl * ngpad + row0);
+        tma_load_2d(st + 4 * L::kATile + pl * L::kBTile, &tmap, &full[s], kx, pl * ngpad + col0);
+      }
+      issued = i + 1;
+    }
+    // Never leave copies in flight: wait (bounded) until every issued stage
+    // has landed before this CTA may exit.
+    for (int i = max(0, issued - STAGES); i < issued; ++i) {
+      uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&full[i % STAGES], (i / STAGES) & 1) && globaltimer() - t0 < kWaitNs) {
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t id = idesc(BN, bf16 != 0, false);
+    const uint32_t idn = idesc(BN, bf16 != 0, true);
+    bool ok = true;
+    for (int i = 0; i < nk && ok; ++i) {
+      const int s = i % STAGES;
+      if (!mbar_wait(&full[s], (i / STAGES) & 1, abort_flag)) {
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      fence_after();
+      const uint32_t base = smem_u32(smem + s * L::kStage);
+#pragma unroll
+      for (int ks = 0; ks < BK / 16; ++ks) {
+        const uint32_t off = ks * 32;  // 16 values x 2 B along K
+        const uint64_t arh = sdesc(base + 0 * L::kATile + off), aih = sdesc(base + 1 * L::kATile + off);
+        const uint64_t arl = sdesc(base + 2 * L::kATile + off), ail = sdesc(base + 3 * L::kATile + off);
+        const uint32_t bb = base + 4 * L::kATile;
+        const uint64_t brh = sdesc(bb + 0 * L::kBTile + off), bih = sdesc(bb + 1 * L::kBTile + off);
+        const uint64_t brl = sdesc(bb + 2 * L::kBTile + off), bil = sdesc(bb + 3 * L::kBTile + off);
+        const uint32_t first = (i > 0 || ks > 0) ? 1u : 0u;
+        // Re += xr xr' + xi xi': hi*hi into t_re, hi*lo + lo*hi into t_rec
+        mma(t_re, arh, brh, id, first);
+        mma(t_re, aih, bih, id, 1);
+        mma(t_rec, arh, brl, id, first);
+        mma(t_rec, arl, brh, id, 1);
+        mma(t_rec, aih, bil, id, 1);
+        mma(t_rec, ail, bih, id, 1);
+        // Im += xr xi' - xi xr': hi*hi into t_im, corrections into t_imc
+        mma(t_im, arh, bih, id, first);
+        mma(t_im, aih, brh, idn, 1);
+        mma(t_imc, arh, bil, id, first);
+        mma(t_imc, arl, bih, id, 1);
+        mma(t_imc, aih, brl, idn, 1);
+        mma(t_imc, ail, brh, idn, 1);
+      }
+      mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+    }
+    if (ok) mma_commit(done);
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: tensor memory -> FP32 workspace
+  bool have = mbar_wait(done, 0, abort_flag);
+  have = __all_sync(0xffffffffu, have) != 0;   // tcgen05.ld needs the whole warp
+  if (!have) {
+    if (threadIdx.x == 0) atomicExch(status, (int)kDevTimeout);
+    *abort_flag = 1;
+  }
+  fence_after();
+  __syncwarp();
+  if (have && nk > 0) {
+    const int row = warp * 32 + lane;
+    float* wre = work + ((size_t)seg * ntiles + tix) * 2 * BM * BN;
+    float* wim = wre + BM * BN;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t a[16], b[16], ac[16], bc[16];
+      tmem_ld16(t_re + lane_off + c0, a);
+      tmem_ld16(t_im + lane_off + c0, b);
+      tmem_ld16(t_rec + lane_off + c0, ac);
+      tmem_ld16(t_imc + lane_off + c0, bc);
+      tmem_ld_wait();
+      float4* pr = reinterpret_cast<float4*>(wre + (size_t)row * BN + c0);
+      float4* pi = reinterpret_cast<float4*>(wim + (size_t)row * BN + c0);
+#define BGW_SUM(x, y, k) (__uint_as_float(x[k]) + __uint_as_float(y[k]))
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        pr[q] = make_float4(BGW_SUM(a, ac, 4 * q), BGW_SUM(a, ac, 4 * q + 1), BGW_SUM(a, ac, 4 * q + 2),
+                            BGW_SUM(a, ac, 4 * q + 3));
+        pi[q] = make_float4(BGW_SUM(b, bc, 4 * q), BGW_SUM(b, bc, 4 * q + 1), BGW_SUM(b, bc, 4 * q + 2),
+                            BGW_SUM(b, bc, 4 * q + 3));
+      }
+#undef BGW_SUM
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)L::kTmemCols)
+                 : "memory");
+  }
+}
+
+// max |Re|, |Im| of M[p][g] sqrt|w_p| over all p, g (as float bits: the
+// values are >= 0 so integer order is float order).
+__global__ void maxabs_kernel(const float2* __restrict__ M, const double* __restrict__ w, long long K, int ng,
+                              unsigned int* __restrict__ out) {
+  float m = 0.f;
+  const long long n = K * ng;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / ng;
+    const float s = (float)sqrt(fabs(w[p]));
+    const float2 v = M[e];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)) * s);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// Power-of-two scale exponent e with max|X| 2^e in [2^13, 2^14) for FP16
+// (largest |hi * hi| products stay far below the FP16 and FP32 limits); 0 for BF16.
+__device__ __forceinline__ int scale_exp(const unsigned int* maxbits, int bf16) {
+  if (bf16) return 0;
+  const float m = __uint_as_float(*maxbits);
+  if (!(m > 0.f) || !isfinite(m)) return 0;
+  int ex;
+  frexpf(m, &ex);  // m = f 2^ex, f in [0.5, 1)
+  return 14 - ex;
+}
+
+// planes[pl][g][p] for g < ngpad, p < kpad (zero padded), from M[p][g]:
+// x = M sqrt|w_p| 2^e split into hi + lo.  32 x 32 transposing tiles.
+template <typename H>
+__global__ void split_kernel(const float2* __restrict__ M, const double* __restrict__ w, long long K, int ng,
+                             int ngpad, int kpad, const unsigned int* __restrict__ maxbits, int bf16,
+                             H* __restrict__ planes) {
+  __shared__ float2 t[32][33];
+  const int p0 = blockIdx.x * 32, g0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const float sc = ldexpf(1.f, scale_exp(maxbits, bf16));
+  for (int r = ty; r < 32; r += 8) {
+    const long long p = p0 + r;
+    const int g = g0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (p < K && g < ng) {
+      v = M[p * ng + g];
+      const float s = (float)sqrt(fabs(w[p])) * sc;
+      v.x *= s;
+      v.y *= s;
+    }
+    t[r][tx] = v;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)ngpad * kpad;
+  for (int r = ty; r < 32; r += 8) {
+    const int g = g0 + r;
+    const int p = p0 + tx;
+    const float2 v = t[tx][r];
+    H rh, ih, rl, il;
+    if constexpr (sizeof(H) == 2 && std::is_same<H, __half>::value) {
+      rh = __float2half_rn(v.x);
+      ih = __float2half_rn(v.y);
+      rl = __float2half_rn(v.x - __half2float(rh));
+      il = __float2half_rn(v.y - __half2float(ih));
+    } else {
+      rh = __float2bfloat16_rn(v.x);
+      ih = __float2bfloat16_rn(v.y);
+      rl = __float2bfloat16_rn(v.x - __bfloat162float(rh));
+      il = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+    }
+    const size_t o = (size_t)g * kpad + p;
+    planes[o] = rh;
+    planes[plane + o] = ih;
+    planes[2 * plane + o] = rl;
+    planes[3 * plane + o] = il;
+  }
+}
+
+// chi[g][g'] (+)= factor 2^{-2e} sum_seg W, lower triangle of every tile,
+// mirrored (conjugated) into the upper triangle.  One thread per tile element.
+template <int BN>
+__global__ void reduce_kernel(const float* __restrict__ work, int nseg, int ntiles, const int2* __restrict__ tiles,
+                              int ng, double factor, const unsigned int* __restrict__ maxbits, int bf16,
+                              int accumulate, double2* __restrict__ chi) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)BM * BN;
+  if (e >= per * ntiles) return;
+  const int tix = (int)(e / per);
+  const int r = (int)((e - (long long)tix * per) / BN), c = (int)(e % BN);
+  const int2 tl = tiles[tix];
+  const int g = tl.x * BM + r, gp = tl.y * BN + c;
+  if (g >= ng || gp >= ng || gp > g) return;
+  double re = 0.0, im = 0.0;
+  for (int s = 0; s < nseg; ++s) {
+    const float* w = work + ((size_t)s * ntiles + tix) * 2 * per;
+    re += (double)w[r * BN + c];
+    im += (double)w[per + r * BN + c];
+  }
+  const double f = factor * ldexp(1.0, -2 * scale_exp(maxbits, bf16));
+  double2 v = make_double2(re * f, im * f);
+  double2* lo = chi + (size_t)g * ng + gp;
+  if (accumulate) {
+    const double2 o = *lo;
+    v.x += o.x;
+    v.y += o.y;
+  }
+  if (g == gp) v.y = 0.0;
+  *lo = v;
+  if (g != gp) chi[(size_t)gp * ng + g] = make_double2(v.x, -v.y);
+}
+
+}  // namespace tc
+
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+
+int get_encode(Ctx* c) {
+  if (g_encode) return BGW_OK;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+    return fail(c, BGW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  return BGW_OK;
+}
+
+constexpr int kBN = 128;
+constexpr int kStages = 3;
+// Default pairs per K segment (FP32 accumulation span before the FP64 sum).
+constexpr int kSegPairsDefault = 512;
+}  // namespace
+
+int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double* w, int nrow, double scale,
+                  int accumulate, void* chi, cudaStream_t st) {
+  using namespace tc;
+  int rc;
+  if ((rc = get_encode(c)) != BGW_OK) return rc;
+  const int bf16 = prec == BGW_PREC_MIX_BF16;
+  const int ntr = (ng + BM - 1) / BM, ntc = (ng + kBN - 1) / kBN;
+  const int ngpad = std::max(ntr * BM, ntc * kBN);
+  const long long kpad = (K + BK - 1) / BK * BK;
+  if (kpad > 0x7fffffffLL / 1) return fail(c, BGW_EUNSUPPORTED, "too many pairs for one call");
+  const int nkb = (int)(kpad / BK);
+  const int seg_pairs = c->chi_segment_pairs > 0 ? c->chi_segment_pairs : kSegPairsDefault;
+  const int kb_per_seg = std::max(1, seg_pairs / BK);
+  const int nseg = (nkb + kb_per_seg - 1) / kb_per_seg;
+  std::vector<int2> tl;
+  for (int I = 0; I < ntr; ++I)
+    for (int J = 0; J < ntc; ++J)
+      if (J * kBN <= I * BM + BM - 1) tl.push_back(make_int2(I, J));
+  const int ntiles = (int)tl.size();
+  const void* d_tiles;
+  if ((rc = upload_cached(c, tl.data(), tl.size() * sizeof(int2), st, &d_tiles)) != BGW_OK) return rc;
+  Scratch planes, work, mx;
+  planes.pool = work.pool = mx.pool = &c->pool;
+  const size_t plane_bytes = (size_t)4 * ngpad * kpad * 2;
+  const size_t work_bytes = (size_t)nseg * ntiles * 2 * BM * kBN * sizeof(float);
+  if ((rc = c->pool.alloc(plane_bytes, &planes.ptr)) != BGW_OK || (rc = c->pool.alloc(work_bytes, &work.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc(sizeof(unsigned int), &mx.ptr)) != BGW_OK)
+    return fail(c, rc, "bgw_chi_sum (mixed): scratch allocation failed (planes %zu B, workspace %zu B)", plane_bytes,
+                work_bytes);
+  CUtensorMap tmap;
+  cuuint64_t gdim[2] = {(cuuint64_t)kpad, (cuuint64_t)4 * ngpad};
+  cuuint64_t gstride[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  // One map serves both operands: the B box has kBN rows; with kBN == BM the
+  // same box height applies.
+  static_assert(kBN == BM, "one tensor map per operand height");
+  CUresult cr = g_encode(&tmap, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                         planes.ptr, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return fail(c, BGW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  const size_t smem = (size_t)kStages * Layout<kBN>::kStage + 1024 + 256;
+  BGW_CUDA(c, cudaFuncSetAttribute(chi_tc_kernel<kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  for (int f = 0; f < nrow; ++f) {
+    const double* wf = w + (size_t)f * K;
+    BGW_CUDA(c, cudaMemsetAsync(mx.ptr, 0, sizeof(unsigned int), st));
+    const long long n = K * ng;
+    const unsigned mb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8);
+    maxabs_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wf, K, ng, mx.as<unsigned int>());
+    dim3 sg((unsigned)(kpad / 32), (unsigned)(ngpad / 32));
+    if (bf16)
+      split_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, K, ng, ngpad,
+                                                              (int)kpad, mx.as<unsigned int>(), 1,
+                                                              planes.as<__nv_bfloat16>());
+    else
+      split_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, K, ng, ngpad, (int)kpad,
+                                                       mx.as<unsigned int>(), 0, planes.as<__half>());
+    chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
+        tmap, ngpad, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(), c->d_status);
+    const long long ne = (long long)ntiles * BM * kBN;
+    reduce_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+        work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(), bf16,
+        accumulate, static_cast<double2*>(chi) + (size_t)f * ng * ng);
+    BGW_CUDA(c, cudaGetLastError());
+    c->launches += 4;
+  }
+  return BGW_OK;
+}
+
 }  // namespace bgw

@@ -87,6 +87,7 @@ struct Ctx {
   bool twiddles_ready = false;
   bool chi_tc_ready = false;
   uint64_t launches = 0;     // kernels launched by this context
+  int chi_segment_pairs = 0; // mixed chi: pairs per FP32 accumulation segment (0 = default)
   // Content-keyed caches (FNV-1a over the bytes plus sizes).
   std::unordered_map<uint64_t, void*> uploads;           // small host arrays
   std::unordered_map<uint64_t, std::unique_ptr<BandPlan>> band_plans;
