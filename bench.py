@@ -1,10 +1,14 @@
 """Benchmark of the RPA epsilon hot path for one q-point on GB300.
 
-One step = one eps~^-1 solve of the plain-FP64 larger-cell workload
+One step = one eps~^-1 solve of the larger-cell workload
 (a = 20.52 bohr, 40^3 FFT grid, 12 Ry wavefunction sphere, 6 Ry epsilon sphere
 with N_G = 2120, N_v = 32, N_c = 800): matrix elements (band and pair
 transforms), chi, eps~ formation and the inverse, all through the C ABI
-(bgw_mtxel, bgw_chi_sum, bgw_epsinv) on device-resident inputs.  The e2e
+(bgw_mtxel, bgw_chi_sum, bgw_epsinv) on device-resident inputs, in the
+mixed precision by default (complex64 M, split-FP16 chi on the tensor cores,
+FP64 eps~ and inverse); the plain FP64 solve of the same inputs runs after it
+as the comparison, and the eps~^-1 difference between the two is reported.
+The e2e
 figure is the same solve through bgw_epsilon with host buffers: the
 coefficient upload and the eps~^-1 download are inside its timed region.
 
@@ -32,7 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "χ TFLOP/s & ε̃⁻¹ solves/s at ≤1e-6 rel err vs plain FP64 GPU; p50/p99 latency"
-WORKLOAD = "c1 plain FP64: a=20.52 bohr, fft 40^3, wfn 12 Ry, eps 6 Ry (N_G=2120), N_v=32, N_c=800, q=(0.1,0,0)"
+WORKLOAD = "c1: a=20.52 bohr, fft 40^3, wfn 12 Ry, eps 6 Ry (N_G=2120), N_v=32, N_c=800, q=(0.1,0,0)"
 
 
 def _peaks():
@@ -117,6 +121,53 @@ def flops_of(s):
     return {"chi_zgemm": chi_zgemm, "chi_herm": chi_herm, "inv": inv}
 
 
+def _solve_steps(ctx, s, prec, steps, warmup, flush, timing):
+    """Timed one-q solves through bgw_mtxel / bgw_chi_sum / bgw_epsinv.
+    Returns per-step stage times [steps][3] (ms), the library's kernel-group
+    totals (when timing) and the last eps~^-1."""
+    import torch
+    from paper_1111_4429_gb300 import bgw
+    cell = bgw.system_cell(s)
+    st = torch.cuda.current_stream()
+    cv = torch.from_numpy(s.cv).cuda()
+    cc = torch.from_numpy(s.cc).cuda()
+    cdt = torch.complex128 if prec == bgw.BGW_PREC_FP64 else torch.complex64
+    M = torch.empty((s.npairs, s.ng), dtype=cdt, device="cuda")
+    chi = torch.empty((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
+    inv = torch.empty_like(chi)
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(st)
+        ctx.mtxel(cell, s.gv, cv, s.gc, cc, s.geps, prec, M)
+        if evs:
+            evs[1].record(st)
+        ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, s.ec, None, prec, False, chi)
+        if evs:
+            evs[2].record(st)
+        ctx.epsinv([cell], [s.geps], [chi], None, [inv])
+        if evs:
+            evs[3].record(st)
+
+    for _ in range(warmup):
+        step()
+    ctx.sync()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    ctx.set_option(bgw.BGW_OPT_TIMING, 1 if timing else 0)
+    ctx.timing_report(reset=True)
+    l0 = ctx.launch_count()
+    for k in range(steps):
+        flush.fill_(k & 0xff)       # evict L2 between steps (outside the events)
+        step(ev[k])
+    torch.cuda.synchronize()
+    ctx.sync()
+    launches = ctx.launch_count() - l0
+    kt = ctx.timing_report(reset=True) if timing else {}
+    ctx.set_option(bgw.BGW_OPT_TIMING, 0)
+    stage = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in ev])
+    return stage, kt, inv, launches
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -129,76 +180,90 @@ def run_ours(args):
     s = synth.config_system("c1")
     ctx = bgw.Context(local)
     cell = bgw.system_cell(s)
-    st = torch.cuda.current_stream()
-    cv = torch.from_numpy(s.cv).cuda()
-    cc = torch.from_numpy(s.cc).cuda()
-    M = torch.empty((s.npairs, s.ng), dtype=torch.complex128, device="cuda")
-    chi = torch.empty((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
-    inv = torch.empty_like(chi)
+    prec = bgw.PREC[args.prec]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    fl = flops_of(s)
 
-    def step(evs=None):
-        if evs:
-            evs[0].record(st)
-        ctx.mtxel(cell, s.gv, cv, s.gc, cc, s.geps, 0, M)
-        if evs:
-            evs[1].record(st)
-        ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, s.ec, None, 0, False, chi)
-        if evs:
-            evs[2].record(st)
-        ctx.epsinv([cell], [s.geps], [chi], None, [inv])
-        if evs:
-            evs[3].record(st)
-
-    for _ in range(args.warmup):
-        step()
-    ctx.sync()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    l0 = ctx.launch_count()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.fill_(k & 0xff)       # evict L2 between steps (untimed by the events)
-            step(ev[k])
-        torch.cuda.synchronize()
+        stage, kt, inv, launches = _solve_steps(ctx, s, prec, args.steps, args.warmup, flush, timing=True)
         wall = time.perf_counter() - t0
-    ctx.sync()
-    launches = ctx.launch_count() - l0
     if ws > 1:
         dist.barrier()
-    stage = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in ev])
-    step_ms = stage.sum(1)
-    t_total = float(step_ms.sum()) / 1e3
+    t_total = float(stage.sum()) / 1e3
     if ws > 1:
         tt = torch.tensor([t_total], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt.item())
-    fl = flops_of(s)
     mean = stage.mean(0)
-    chi_s = mean[1] / 1e3
-    chi_tflops = fl["chi_zgemm"] / chi_s / 1e12
-    chi_herm_tflops = fl["chi_herm"] / chi_s / 1e12
+    chi_ms = mean[1]
+
+    # the plain FP64 solve on the same inputs: the comparison point, and the
+    # reference of the eps~^-1 error the metric is quoted at
+    comp = {}
+    if prec != bgw.BGW_PREC_FP64:
+        st64, kt64, inv64, _ = _solve_steps(ctx, s, bgw.BGW_PREC_FP64, 2, 1, flush, timing=True)
+        m64 = st64.mean(0)
+        err = float(torch.linalg.matrix_norm(inv - inv64) / torch.linalg.matrix_norm(inv64))
+        comp = {"plain_fp64": {"solves_per_s": 1e3 / float(st64.sum(1).mean()),
+                               "stage_ms": {"mtxel": m64[0], "chi_sum": m64[1], "epsinv": m64[2]},
+                               "chi_tflops_zgemm_eq": fl["chi_zgemm"] / (m64[1] / 1e3) / 1e12,
+                               "kernel_ms": {k: v[1] / v[0] for k, v in kt64.items()}},
+                "epsinv_rel_err_vs_plain_fp64_gpu": err}
+
+    # kernel-group durations during the timed steps (CUDA events in the library)
+    kms = {k: v[1] / v[0] for k, v in kt.items()}
+    per_step_ms = {k: v[1] / args.steps for k, v in kt.items()}
+    dom = max(per_step_ms, key=per_step_ms.get)
+    peaks, peak_src = _peaks()
+    if dom == "inverse":
+        roof = {"bound": "alu", "kernel": "Gauss-Jordan inverse (gj_diag/gj_panels/gj_update, FP64 FMA)",
+                "achieved": fl["inv"] / (kms[dom] / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "algorithmic": "8 N_G^3 flop per inverse", "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz"}
+    elif dom == "chi_f64":
+        roof = {"bound": "alu", "kernel": "chi_f64_kernel (FP64 FMA)",
+                "achieved": fl["chi_herm"] / (kms[dom] / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "algorithmic": "4 N_G^2 K flop (Hermitian lower triangle)",
+                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz"}
+    elif dom == "chi_tc":
+        roof = {"bound": "tensor", "kernel": "chi_tc_kernel (tcgen05 kind::f16)",
+                "achieved": fl["chi_herm"] / (kms[dom] / 1e3) / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "algorithmic": "4 N_G^2 K flop (Hermitian lower triangle)",
+                "peak_source": "measured bf16 burst (fp16 has the same nominal rate)"}
+    else:
+        roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": "TFLOP/s"}
+    if roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["share_of_step"] = per_step_ms[dom] / float(stage.sum(1).mean())
+    chi_tc = None
+    if "chi_tc" in kms:
+        ntr = (s.ng + 127) // 128
+        tiles = ntr * (ntr + 1) // 2
+        kpad = (s.npairs + 31) // 32 * 32
+        issued = tiles * 12 * 2.0 * 128 * 128 * kpad   # 12 real MMAs of 128x128 per K step
+        chi_tc = {"ms": kms["chi_tc"], "algorithmic_tflops": fl["chi_herm"] / (kms["chi_tc"] / 1e3) / 1e12,
+                  "zgemm_eq_tflops": fl["chi_zgemm"] / (kms["chi_tc"] / 1e3) / 1e12,
+                  "issued_tensor_tflops": issued / (kms["chi_tc"] / 1e3) / 1e12,
+                  "issued_frac_of_measured_peak": issued / (kms["chi_tc"] / 1e3) / 1e12 / peaks["bf16_tflops"]}
 
     # end to end through bgw_epsilon with pinned host buffers
     cvh = torch.from_numpy(s.cv).pin_memory()
     cch = torch.from_numpy(s.cc).pin_memory()
     invh = torch.empty((1, s.ng, s.ng), dtype=torch.complex128).pin_memory()
     for _ in range(2):
-        ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, 0, 0, None, invh)
+        ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, prec, 0, None, invh)
     e2e_steps = max(2, min(args.steps, 5))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, 0, 0, None, invh)
+        ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, prec, 0, None, invh)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    h2d = s.cv.nbytes + s.cc.nbytes
-    d2h = invh.numel() * 16
 
-    peaks, peak_src = _peaks()
     out = {
         "metric": METRIC,
         "value": ws * args.steps / t_total,
@@ -210,20 +275,19 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64" if prec == bgw.BGW_PREC_FP64 else "c64 M + fp16x3 chi (fp32 acc, fp64 sum) + f64 inverse",
         "data": "synthetic (seeded QR-orthonormal complex Gaussian coefficients, uniform sorted energies)",
-        "config": {"workload": WORKLOAD, "precision": "fp64", "replicas": ws,
+        "config": {"workload": WORKLOAD, "precision": args.prec, "replicas": ws,
                    "l2": "flushed between steps (256 MiB write); working set > L2"},
-        "chi_tflops_zgemm_eq": chi_tflops,
-        "chi_tflops_hermitian": chi_herm_tflops,
+        "chi_tflops_zgemm_eq": fl["chi_zgemm"] / (chi_ms / 1e3) / 1e12,
+        "chi_tflops_hermitian": fl["chi_herm"] / (chi_ms / 1e3) / 1e12,
         "stage_ms": {"mtxel": mean[0], "chi_sum": mean[1], "epsinv": mean[2]},
-        "roofline": {"bound": "alu", "kernel": "chi_f64_kernel (bgw_chi_sum stage, FP64 FMA)",
-                     "achieved": chi_herm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": chi_herm_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                     "algorithmic": "4 N_G^2 K flop (Hermitian lower triangle) per launch"},
-        "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "kernel_ms": kms,
+        "roofline": roof,
+        "chi_tc": chi_tc,
+        **comp,
+        "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(s.cv.nbytes + s.cc.nbytes),
+                "d2h_bytes_per_step": int(invh.numel() * 16)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "wall_s_timed": wall,
@@ -307,17 +371,18 @@ def run_profile_case(args):
     s = synth.config_system("c1", nc=200)
     ctx = bgw.Context(0)
     cell = bgw.system_cell(s)
+    prec = bgw.PREC[args.prec]
     cv = torch.from_numpy(s.cv).cuda()
     cc = torch.from_numpy(s.cc).cuda()
-    M = torch.empty((s.npairs, s.ng), dtype=torch.complex128, device="cuda")
+    M = torch.empty((s.npairs, s.ng), dtype=torch.complex128 if prec == 0 else torch.complex64, device="cuda")
     chi = torch.empty((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
     inv = torch.empty_like(chi)
     for _ in range(2):
-        ctx.mtxel(cell, s.gv, cv, s.gc, cc, s.geps, 0, M)
-        ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, s.ec, None, 0, False, chi)
+        ctx.mtxel(cell, s.gv, cv, s.gc, cc, s.geps, prec, M)
+        ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, s.ec, None, prec, False, chi)
         ctx.epsinv([cell], [s.geps], [chi], None, [inv])
     ctx.sync()
-    print(json.dumps({"profile_case": "c1 cell, N_c=200", "launches": ctx.launch_count()}))
+    print(json.dumps({"profile_case": "c1 cell, N_c=200", "precision": args.prec, "launches": ctx.launch_count()}))
 
 
 def main():
@@ -327,6 +392,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="mix_fp16", choices=["fp64", "mix_fp16", "mix_bf16"])
     ap.add_argument("--profile-case", action="store_true", help="reduced c1 solve for ncu captures")
     args = ap.parse_args()
     if args.profile_case:

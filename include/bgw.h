@@ -112,8 +112,16 @@ int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
  *    FP64 (rounded down to a multiple of 32; 0 restores the default, 512).
  *    Shorter segments lower the FP32 accumulation error and cost more
  *    workspace traffic.                                                     */
-enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1 };
+enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
+
+/* With BGW_OPT_TIMING = 1 the context records CUDA events around its main
+ * kernel groups (band transform, pair passes, chi kernels, eps~ formation,
+ * the inverse).  bgw_timing_report waits for the recorded events, adds them
+ * to running totals and writes the totals as a JSON object
+ * {"name": [launches, milliseconds], ...} into buf (NUL-terminated,
+ * truncated to len).  reset = 1 clears the totals afterwards.             */
+int bgw_timing_report(bgw_ctx* ctx, char* buf, size_t len, int reset);
 
 /* ------------------------------------------------------------------------
  * bgw_mtxel -- plane-wave matrix elements (Eq. eqn_matrix_elem), computed as

@@ -25,8 +25,8 @@ PREC = {"fp64": BGW_PREC_FP64, "mix_fp16": BGW_PREC_MIX_FP16, "mix_bf16": BGW_PR
 # Every symbol include/bgw.h declares.
 EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_stats", "bgw_launch_count",
            "bgw_mtxel",
-           "bgw_set_option", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_epsilon")
-BGW_OPT_CHI_SEGMENT_PAIRS = 1
+           "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_epsilon")
+BGW_OPT_CHI_SEGMENT_PAIRS, BGW_OPT_TIMING = 1, 2
 
 
 class BgwError(RuntimeError):
@@ -78,6 +78,7 @@ def load() -> ctypes.CDLL:
     lib.bgw_mem_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     lib.bgw_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.bgw_set_option.argtypes = [vp, ci, ctypes.c_int64]
+    lib.bgw_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ci]
     lib.bgw_mtxel.argtypes = [vp, cellp, ci, ci, i32p, vp, ci, ci, i32p, vp, ci, i32p, ci, vp, vp]
     lib.bgw_chi_sum.argtypes = [vp, cellp, ci, ci, ci, vp, dp, dp, ci, dp, ci, ci, vp, vp]
     lib.bgw_epsinv.argtypes = [vp, ci, cellp, ctypes.POINTER(ci), ctypes.POINTER(i32p), ctypes.POINTER(vp),
@@ -172,6 +173,12 @@ class Context:
 
     def set_option(self, option: int, value: int):
         self._check(self.lib.bgw_set_option(self.h, option, value))
+
+    def timing_report(self, reset: bool = True) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(4096)
+        self._check(self.lib.bgw_timing_report(self.h, buf, len(buf), int(bool(reset))))
+        return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
 
     def mtxel(self, cell: Cell, gv, cv, gc, cc, geps, prec: int, M, stream=None):
         gv_, gvp = _i32(gv)

@@ -1,7 +1,10 @@
 // extern "C" entry points declared in include/bgw.h: argument checks, plan
 // lookup, scratch management and the order of the kernel launches.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
+
+#include <string>
 
 #include <algorithm>
 #include <new>
@@ -171,6 +174,8 @@ int bgw_destroy(bgw_ctx* ctx) {
   if (!ctx) return BGW_EINVAL;
   DeviceGuard g(ctx->impl.device);
   cudaDeviceSynchronize();
+  timing_collect(&ctx->impl);
+  for (cudaEvent_t e : ctx->impl.timing.free_events) cudaEventDestroy(e);
   cudaFree(ctx->impl.d_status);
   delete ctx;
   return BGW_OK;
@@ -222,7 +227,32 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
     c->chi_segment_pairs = (int)value;
     return BGW_OK;
   }
+  if (option == BGW_OPT_TIMING) {
+    if (value != 0 && value != 1) return fail(c, BGW_EINVAL, "timing is 0 or 1");
+    c->timing.on = value == 1;
+    return BGW_OK;
+  }
   return fail(c, BGW_EINVAL, "unknown option %d", option);
+}
+
+int bgw_timing_report(bgw_ctx* ctx, char* buf, size_t len, int reset) {
+  Ctx* c = impl(ctx);
+  if (!c || !buf || len == 0) return BGW_EINVAL;
+  DeviceGuard g(c->device);
+  timing_collect(c);
+  std::string out = "{";
+  bool first = true;
+  for (auto& kv : c->timing.acc) {
+    char item[160];
+    snprintf(item, sizeof(item), "%s\"%s\": [%lld, %.6f]", first ? "" : ", ", timed_name(kv.first),
+             kv.second.first, kv.second.second);
+    out += item;
+    first = false;
+  }
+  out += "}";
+  snprintf(buf, len, "%s", out.c_str());
+  if (reset) c->timing.acc.clear();
+  return BGW_OK;
 }
 
 int bgw_mtxel(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv, int nc,

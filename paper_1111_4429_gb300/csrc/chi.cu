@@ -140,6 +140,7 @@ int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const doubl
   const int nt = (ng + TB - 1) / TB;
   const long long ntiles = (long long)nt * (nt + 1) / 2;
   for (int f = 0; f < nrow; ++f) {
+    TimedScope ts(c, kTChiF64, st);
     chi_f64_kernel<<<(unsigned)ntiles, 256, 0, st>>>(static_cast<const double2*>(M), K, ng,
                                                       w.as<double>() + (size_t)f * K, scale, accumulate,
                                                       static_cast<double2*>(chi) + (size_t)f * ng * ng);

@@ -482,24 +482,34 @@ int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const do
                                    (int)smem));
   for (int f = 0; f < nrow; ++f) {
     const double* wf = w + (size_t)f * K;
-    BGW_CUDA(c, cudaMemsetAsync(mx.ptr, 0, sizeof(unsigned int), st));
-    const long long n = K * ng;
-    const unsigned mb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8);
-    maxabs_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wf, K, ng, mx.as<unsigned int>());
-    dim3 sg((unsigned)(kpad / 32), (unsigned)(ngpad / 32));
-    if (bf16)
-      split_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, K, ng, ngpad,
-                                                              (int)kpad, mx.as<unsigned int>(), 1,
-                                                              planes.as<__nv_bfloat16>());
-    else
-      split_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, K, ng, ngpad, (int)kpad,
-                                                       mx.as<unsigned int>(), 0, planes.as<__half>());
-    chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
-        tmap, ngpad, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(), c->d_status);
-    const long long ne = (long long)ntiles * BM * kBN;
-    reduce_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-        work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(), bf16,
-        accumulate, static_cast<double2*>(chi) + (size_t)f * ng * ng);
+    {
+      TimedScope ts(c, kTChiSplit, st);
+      BGW_CUDA(c, cudaMemsetAsync(mx.ptr, 0, sizeof(unsigned int), st));
+      const long long n = K * ng;
+      const unsigned mb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8);
+      maxabs_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wf, K, ng, mx.as<unsigned int>());
+      dim3 sg((unsigned)(kpad / 32), (unsigned)(ngpad / 32));
+      if (bf16)
+        split_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, K, ng, ngpad,
+                                                                (int)kpad, mx.as<unsigned int>(), 1,
+                                                                planes.as<__nv_bfloat16>());
+      else
+        split_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, K, ng, ngpad, (int)kpad,
+                                                         mx.as<unsigned int>(), 0, planes.as<__half>());
+    }
+    {
+      TimedScope ts(c, kTChiTc, st);
+      chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
+          tmap, ngpad, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
+          c->d_status);
+    }
+    {
+      TimedScope ts(c, kTChiReduce, st);
+      const long long ne = (long long)ntiles * BM * kBN;
+      reduce_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+          work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(), bf16,
+          accumulate, static_cast<double2*>(chi) + (size_t)f * ng * ng);
+    }
     BGW_CUDA(c, cudaGetLastError());
     c->launches += 4;
   }

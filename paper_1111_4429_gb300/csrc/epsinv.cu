@@ -200,16 +200,20 @@ int epsinv_run(Ctx* c, int ng, const double* bvec, const double* qf, const int32
       (rc = c->pool.alloc((size_t)NB * ng * sizeof(double2), &R.ptr)) != BGW_OK ||
       (rc = c->pool.alloc((size_t)NB * ng * sizeof(double2), &Cp.ptr)) != BGW_OK)
     return fail(c, rc, "bgw_epsinv: scratch allocation failed");
-  coulomb_sqrt_kernel<<<(ng + 255) / 256, 256, 0, st>>>(d_geps, ng, bvec[0], bvec[1], bvec[2], bvec[3],
-                                                        bvec[4], bvec[5], bvec[6], bvec[7], bvec[8], qf[0],
-                                                        qf[1], qf[2], sv.as<double>());
   double2* A = static_cast<double2*>(epsinv);
-  const size_t n2 = (size_t)ng * ng;
-  const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
-  eps_form_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(chi), sv.as<double>(), ng, A,
-                                      static_cast<double2*>(eps));
-  BGW_CUDA(c, cudaGetLastError());
-  c->launches += 2;
+  {
+    TimedScope ts(c, kTEpsForm, st);
+    coulomb_sqrt_kernel<<<(ng + 255) / 256, 256, 0, st>>>(d_geps, ng, bvec[0], bvec[1], bvec[2], bvec[3],
+                                                          bvec[4], bvec[5], bvec[6], bvec[7], bvec[8], qf[0],
+                                                          qf[1], qf[2], sv.as<double>());
+    const size_t n2 = (size_t)ng * ng;
+    const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
+    eps_form_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(chi), sv.as<double>(), ng, A,
+                                        static_cast<double2*>(eps));
+    BGW_CUDA(c, cudaGetLastError());
+    c->launches += 2;
+  }
+  TimedScope ts_inv(c, kTInverse, st);
   const int nt = (ng + TU - 1) / TU;
   const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
   BGW_CUDA(c, cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));

@@ -161,6 +161,7 @@ int mtxel_run(Ctx* c, int n, int prec, int nv, const BandPlan* bpv, const void* 
   x.M = M;
   x.st = st;
   x.launches = &c->launches;
+  x.ctx = c;
   cudaError_t e = prec == BGW_PREC_FP64 ? mtxel_exec_f64(x) : mtxel_exec_f32(x);
   if (e != cudaSuccess) return cuda_fail(c, e, "bgw_mtxel kernels");
   return BGW_OK;

@@ -239,9 +239,12 @@ static cudaError_t mtxel_exec_n(const MtxelExec& x) {
   C* U1 = reinterpret_cast<C*>(x.U1);
   C* Tb = reinterpret_cast<C*>(x.T);
   C* M = reinterpret_cast<C*>(x.M);
-  cudaError_t e = band_transform<T, N>(x.bpv, x.cv, x.nv, U1, uv, x.st);
-  if (e != cudaSuccess) return e;
-  if ((e = band_transform<T, N>(x.bpc, x.cc, x.nc, U1, uc, x.st)) != cudaSuccess) return e;
+  cudaError_t e;
+  {
+    TimedScope ts(x.ctx, kTBand, x.st);
+    if ((e = band_transform<T, N>(x.bpv, x.cv, x.nv, U1, uv, x.st)) != cudaSuccess) return e;
+    if ((e = band_transform<T, N>(x.bpc, x.cc, x.nc, U1, uc, x.st)) != cudaSuccess) return e;
+  }
   *x.launches += 4;
   const PairPlan* pp = x.pp;
   int ppb, threads;
@@ -253,9 +256,15 @@ static cudaError_t mtxel_exec_n(const MtxelExec& x) {
   const long long npairs = (long long)x.nv * x.nc;
   for (long long p0 = 0; p0 < npairs; p0 += x.pair_block) {
     const int npb = (int)((npairs - p0) < x.pair_block ? (npairs - p0) : x.pair_block);
-    pair_yxpass<T, N><<<dim3((npb + ppb - 1) / ppb, N), threads, sm, x.st>>>(
-        uv, uc, x.nc, (int)p0, npb, ppb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
-    pair_zgather<T, N><<<npb, 256, smz, x.st>>>(Tb, (int)p0, pp->ncol, pp->ng, pp->d_zmap, M);
+    {
+      TimedScope ts(x.ctx, kTPairYX, x.st);
+      pair_yxpass<T, N><<<dim3((npb + ppb - 1) / ppb, N), threads, sm, x.st>>>(
+          uv, uc, x.nc, (int)p0, npb, ppb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
+    }
+    {
+      TimedScope ts(x.ctx, kTPairZ, x.st);
+      pair_zgather<T, N><<<npb, 256, smz, x.st>>>(Tb, (int)p0, pp->ncol, pp->ng, pp->d_zmap, M);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *x.launches += 2;
   }

@@ -103,6 +103,62 @@ void Pool::trim() {
   free_.clear();
 }
 
+// ------------------------------------------------------------ timing
+const char* timed_name(int n) {
+  static const char* names[kTNumNames] = {"band_transform", "pair_yxpass", "pair_zgather", "chi_f64",
+                                          "chi_split", "chi_tc", "chi_reduce", "eps_form", "inverse"};
+  return (n >= 0 && n < kTNumNames) ? names[n] : "?";
+}
+
+static cudaEvent_t take_event(Ctx* c) {
+  if (!c->timing.free_events.empty()) {
+    cudaEvent_t e = c->timing.free_events.back();
+    c->timing.free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+TimedScope::TimedScope(Ctx* c, int name, cudaStream_t st) : c_(c), name_(name), st_(st) {
+  if (!c_->timing.on) return;
+  a_ = take_event(c_);
+  if (a_ && cudaEventRecord(a_, st_) != cudaSuccess) {
+    cudaGetLastError();
+    a_ = nullptr;
+  }
+}
+
+TimedScope::~TimedScope() {
+  if (!a_) return;
+  cudaEvent_t b = take_event(c_);
+  if (!b || cudaEventRecord(b, st_) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  c_->timing.pending.push_back({name_, a_, b});
+}
+
+void timing_collect(Ctx* c) {
+  for (auto& r : c->timing.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      auto& a = c->timing.acc[r.name];
+      a.first += 1;
+      a.second += ms;
+    } else {
+      cudaGetLastError();
+    }
+    c->timing.free_events.push_back(r.a);
+    c->timing.free_events.push_back(r.b);
+  }
+  c->timing.pending.clear();
+}
+
 // ------------------------------------------------------------ uploads
 int upload_cached(Ctx* c, const void* host, size_t bytes, cudaStream_t st, const void** dev) {
   uint64_t key = fnv1a(host, bytes, fnv1a(&bytes, sizeof(bytes)));

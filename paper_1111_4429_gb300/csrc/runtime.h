@@ -79,8 +79,21 @@ struct PairPlan {        // pruned product transform onto the epsilon sphere
   int* d_zmap = nullptr;        // [n][ncol] G index of (column, kz=k) or -1 (k-major)
 };
 
+// Optional CUDA-event timing of named kernel groups (BGW_OPT_TIMING).
+struct Timing {
+  bool on = false;
+  struct Rec { int name; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> free_events;
+  std::map<int, std::pair<long long, double>> acc;  // name -> (launches, ms)
+};
+enum TimedName { kTBand = 0, kTPairYX, kTPairZ, kTChiF64, kTChiSplit, kTChiTc, kTChiReduce, kTEpsForm, kTInverse,
+                 kTNumNames };
+const char* timed_name(int n);
+
 struct Ctx {
   int device = 0;
+  Timing timing;
   Pool pool;
   std::string err;
   int* d_status = nullptr;   // device status word
@@ -96,6 +109,21 @@ struct Ctx {
 };
 
 uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull);
+
+// Records CUDA events around its scope on `st` when timing is enabled.
+class TimedScope {
+ public:
+  TimedScope(Ctx* c, int name, cudaStream_t st);
+  ~TimedScope();
+
+ private:
+  Ctx* c_;
+  int name_;
+  cudaStream_t st_;
+  cudaEvent_t a_ = nullptr;
+};
+// Collects the finished records (synchronizing on their events).
+void timing_collect(Ctx* c);
 
 // Errors: set ctx->err and return the code.
 int fail(Ctx* c, int code, const char* fmt, ...);
@@ -131,6 +159,7 @@ struct MtxelExec {
   void* M = nullptr;
   cudaStream_t st = nullptr;
   uint64_t* launches = nullptr;  // incremented per kernel launch
+  Ctx* ctx = nullptr;            // for optional event timing
 };
 cudaError_t mtxel_exec_f64(const MtxelExec& x);
 cudaError_t mtxel_exec_f32(const MtxelExec& x);
