@@ -177,8 +177,11 @@ int bgw_chi_sum(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng,
  *   eps[i]    device c128 [ng[i]][ng[i]] or NULL (eps~ is also written
  *             there when non-NULL; the array `eps` itself may be NULL)
  *   epsinv[i] device c128 [ng[i]][ng[i]]
- * The inverse is a blocked Gauss-Jordan elimination without pivoting, which
- * is stable for Hermitian positive-definite eps~ (chi <= 0 makes eps~ >= I).
+ * eps~ is Hermitian positive definite (chi <= 0 makes eps~ >= I); the
+ * inverse is a blocked sweep (Gauss-Jordan without pivoting in its
+ * Hermitian form) that reads and updates only the lower triangle of chi's
+ * Hermitian eps~, then writes both triangles of epsinv.  Elimination without
+ * pivoting is backward stable for such matrices.
  * EINVAL if some |q+G| = 0.  A zero or non-finite pivot sets BGW_ENUMERIC,
  * reported by bgw_sync.                                                    */
 int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,

@@ -2,7 +2,9 @@
 // untruncated_bare_coulomb with the symmetric Coulomb form), FP64 throughout:
 //   sv_G       = sqrt(4 pi) / |(q + G) B|             (= v(q+G)^{1/2})
 //   eps~[G][G'] = delta_GG' - sv_G chi[G][G'] sv_G'
-//   epsinv      = eps~^-1 by blocked Gauss-Jordan elimination.
+//   epsinv      = eps~^-1 by a Hermitian blocked sweep (bgw_epsinv) or by
+//                 blocked Gauss-Jordan elimination (the allocation-free
+//                 entry point).
 //
 // Gauss-Jordan step on the column block k (width kb, rows/cols K = k0..k0+kb):
 //   D^-1 of the diagonal block (one CTA, elimination in shared memory)
@@ -190,6 +192,193 @@ __global__ void __launch_bounds__(256) gj_update_kernel(double2* __restrict__ A,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Hermitian blocked sweep (the inverse used by bgw_epsinv).
+//
+// eps~ is Hermitian positive definite, so only its lower triangle is kept
+// and updated.  Sweeping the block K (rows/cols k0..k0+kb) with D = A_KK and
+// R the other indices maps
+//   A_KK -> -D^-1,  A_RK -> A_RK D^-1,  A_KR -> D^-1 A_KR,
+//   A_RR -> A_RR - A_RK D^-1 A_KR,
+// which keeps the matrix Hermitian; after every block has been swept the
+// matrix holds -eps~^-1.  With C = A_RK (read from the stored lower triangle:
+// the column panel below K, the conjugated row panel left of K) and
+// P = C D^-1 the trailing update of a lower element is
+//   A_ij -= sum_s P_is conj(C_js),
+// half the work of a full Gauss-Jordan step.
+__global__ void __launch_bounds__(NB * NB) sw_diag_kernel(double2* __restrict__ A, int ng, int k0, int kb,
+                                                          double2* __restrict__ Dinv, int* __restrict__ status) {
+  __shared__ double2 D[NB][NB + 1];
+  __shared__ double2 recip;  // 1/pivot, computed once per step (FP64 division is costly on one SM)
+  const int i = threadIdx.y, j = threadIdx.x;
+  const bool in = i < kb && j < kb;
+  double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  if (in) {
+    if (i >= j) {
+      v = A[(size_t)(k0 + i) * ng + k0 + j];
+    } else {
+      const double2 t = A[(size_t)(k0 + j) * ng + k0 + i];
+      v = make_double2(t.x, -t.y);
+    }
+  }
+  D[i][j] = v;
+  for (int s = 0; s < kb; ++s) {
+    __syncthreads();
+    if (i == 0 && j == 0) {
+      const double2 piv = D[s][s];
+      const double m2 = piv.x * piv.x + piv.y * piv.y;
+      if (!(m2 > 0.0) || !isfinite(m2)) {
+        atomicExch(status, (int)kDevZeroPivot);
+        recip = make_double2(0.0, 0.0);
+      } else {
+        const double r = 1.0 / m2;
+        recip = make_double2(piv.x * r, -piv.y * r);
+      }
+    }
+    __syncthreads();
+    const double2 p = recip;
+    const double2 f = D[i][s];
+    const double2 rs = D[s][j];
+    __syncthreads();
+    const double2 rsn = (j == s) ? p : cmul(rs, p);
+    if (i == s) {
+      D[i][j] = rsn;
+    } else {
+      double2 w = (j == s) ? make_double2(0.0, 0.0) : D[i][j];
+      const double2 t = cmul(f, rsn);
+      D[i][j] = make_double2(w.x - t.x, w.y - t.y);
+    }
+  }
+  __syncthreads();
+  if (in) {
+    const double2 d = D[i][j];
+    Dinv[i * NB + j] = d;
+    if (i >= j) A[(size_t)(k0 + i) * ng + k0 + j] = make_double2(-d.x, -d.y);
+  }
+}
+
+// One warp per row i outside K (lane = column s of the panel):
+//   C_i = A_iK (stored lower part), P_i = C_i D^-1, then A_iK <- P_i.
+// C and P go to scratch (ld NB) for the update.  grid ceil(ng/8), block 256.
+__global__ void __launch_bounds__(256) sw_panel_kernel(double2* __restrict__ A, int ng, int k0, int kb,
+                                                       const double2* __restrict__ Dinv, double2* __restrict__ C,
+                                                       double2* __restrict__ P) {
+  __shared__ double2 Ds[NB][NB];
+  __shared__ double2 Cs[8][NB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Dinv[e];
+  const int i = blockIdx.x * 8 + warp;
+  const bool row_ok = i < ng && (i < k0 || i >= k0 + kb);
+  double2 cv = make_double2(0.0, 0.0);
+  if (row_ok && lane < kb) {
+    if (i >= k0 + kb) {
+      cv = A[(size_t)i * ng + k0 + lane];
+    } else {
+      const double2 t = A[(size_t)(k0 + lane) * ng + i];
+      cv = make_double2(t.x, -t.y);
+    }
+  }
+  Cs[warp][lane] = cv;
+  __syncthreads();
+  if (!row_ok) return;
+  double2 pv = make_double2(0.0, 0.0);
+  for (int t = 0; t < kb; ++t) {
+    const double2 a = Cs[warp][t], d = Ds[t][lane];
+    pv.x = fma(a.x, d.x, fma(-a.y, d.y, pv.x));
+    pv.y = fma(a.x, d.y, fma(a.y, d.x, pv.y));
+  }
+  if (lane < kb) {
+    C[(size_t)i * NB + lane] = cv;
+    P[(size_t)i * NB + lane] = pv;
+    if (i >= k0 + kb)
+      A[(size_t)i * ng + k0 + lane] = pv;
+    else
+      A[(size_t)(k0 + lane) * ng + i] = make_double2(pv.x, -pv.y);
+  }
+}
+
+// Lower 64x64 tiles: A_ij -= sum_s P_is conj(C_js) for i >= j outside K.
+// grid: nt (nt+1) / 2 tiles, block 256, dynamic smem.
+__global__ void __launch_bounds__(256) sw_update_kernel(double2* __restrict__ A, int ng, int k0, int kb,
+                                                        const double2* __restrict__ P,
+                                                        const double2* __restrict__ C) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 (*Ps)[NB + 1] = reinterpret_cast<double2 (*)[NB + 1]>(smem_raw);
+  double2 (*Cs)[NB + 1] = reinterpret_cast<double2 (*)[NB + 1]>(smem_raw + sizeof(double2) * TU * (NB + 1));
+  const long long t = blockIdx.x;
+  int I = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((long long)(I + 1) * (I + 2) / 2 <= t) ++I;
+  while ((long long)I * (I + 1) / 2 > t) --I;
+  const int J = (int)(t - (long long)I * (I + 1) / 2);
+  const int i0 = I * TU, j0 = J * TU;
+  // tiles whose rows or columns all lie inside K have nothing to update
+  if (i0 >= k0 && min(i0 + TU, ng) <= k0 + kb) return;
+  if (j0 >= k0 && min(j0 + TU, ng) <= k0 + kb) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int e = tid; e < TU * NB; e += 256) {
+    const int r = e / NB, s = e % NB;
+    const bool sk = s < kb;
+    Ps[r][s] = (sk && i0 + r < ng) ? P[(size_t)(i0 + r) * NB + s] : make_double2(0.0, 0.0);
+    const double2 cc = (sk && j0 + r < ng) ? C[(size_t)(j0 + r) * NB + s] : make_double2(0.0, 0.0);
+    Cs[r][s] = make_double2(cc.x, -cc.y);  // conj(C_js)
+  }
+  __syncthreads();
+  double2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0.0, 0.0);
+  for (int s = 0; s < kb; ++s) {
+    double2 pv[4], cv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) pv[a] = Ps[ty + 16 * a][s];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) cv[b] = Cs[tx + 16 * b][s];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        acc[a][b].x = fma(pv[a].x, cv[b].x, acc[a][b].x);
+        acc[a][b].x = fma(-pv[a].y, cv[b].y, acc[a][b].x);
+        acc[a][b].y = fma(pv[a].x, cv[b].y, acc[a][b].y);
+        acc[a][b].y = fma(pv[a].y, cv[b].x, acc[a][b].y);
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty + 16 * a;
+    if (i >= ng || (i >= k0 && i < k0 + kb)) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx + 16 * b;
+      if (j > i || (j >= k0 && j < k0 + kb)) continue;
+      double2* dst = A + (size_t)i * ng + j;
+      const double2 v = *dst;
+      *dst = make_double2(v.x - acc[a][b].x, v.y - acc[a][b].y);
+    }
+  }
+}
+
+// The swept lower triangle holds -eps~^-1: negate and mirror into both
+// triangles.  One thread per lower element.
+__global__ void sw_finish_kernel(double2* __restrict__ A, int ng) {
+  const long long nlow = (long long)ng * (ng + 1) / 2;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nlow;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
+    while ((long long)i * (i + 1) / 2 > e) --i;
+    const int j = (int)(e - (long long)i * (i + 1) / 2);
+    const double2 v = A[(size_t)i * ng + j];
+    if (i == j) {
+      A[(size_t)i * ng + j] = make_double2(-v.x, 0.0);
+    } else {
+      A[(size_t)i * ng + j] = make_double2(-v.x, -v.y);
+      A[(size_t)j * ng + i] = make_double2(-v.x, v.y);
+    }
+  }
+}
+
 int epsinv_run(Ctx* c, int ng, const double* bvec, const double* qf, const int32_t* d_geps,
                const void* chi, void* eps, void* epsinv, cudaStream_t st) {
   Scratch sv, dinv, R, Cp;
@@ -215,17 +404,22 @@ int epsinv_run(Ctx* c, int ng, const double* bvec, const double* qf, const int32
   }
   TimedScope ts_inv(c, kTInverse, st);
   const int nt = (ng + TU - 1) / TU;
-  const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
-  BGW_CUDA(c, cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
+  const long long ntl = (long long)nt * (nt + 1) / 2;
+  const size_t upd_smem = sizeof(double2) * 2 * TU * (NB + 1);
+  BGW_CUDA(c, cudaFuncSetAttribute(sw_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
   for (int k0 = 0; k0 < ng; k0 += NB) {
     const int kb = std::min(NB, ng - k0);
-    gj_diag_kernel<<<1, dim3(NB, NB), 0, st>>>(A, ng, k0, kb, dinv.as<double2>(), c->d_status);
-    gj_panels_kernel<<<dim3((ng + 63) / 64, 1 + (ng + 255) / 256), 256, 0, st>>>(
-        A, ng, k0, kb, dinv.as<double2>(), R.as<double2>(), Cp.as<double2>());
-    gj_update_kernel<<<dim3(nt, nt), 256, upd_smem, st>>>(A, ng, k0, kb, R.as<double2>(), Cp.as<double2>());
+    sw_diag_kernel<<<1, dim3(NB, NB), 0, st>>>(A, ng, k0, kb, dinv.as<double2>(), c->d_status);
+    sw_panel_kernel<<<(ng + 7) / 8, 256, 0, st>>>(A, ng, k0, kb, dinv.as<double2>(), Cp.as<double2>(),
+                                                  R.as<double2>());
+    sw_update_kernel<<<(unsigned)ntl, 256, upd_smem, st>>>(A, ng, k0, kb, R.as<double2>(), Cp.as<double2>());
     BGW_CUDA(c, cudaGetLastError());
     c->launches += 3;
   }
+  const long long nlow = (long long)ng * (ng + 1) / 2;
+  sw_finish_kernel<<<(unsigned)std::min<long long>((nlow + 255) / 256, 152LL * 16), 256, 0, st>>>(A, ng);
+  BGW_CUDA(c, cudaGetLastError());
+  c->launches += 1;
   return BGW_OK;
 }
 
