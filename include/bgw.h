@@ -112,7 +112,11 @@ int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
  *    FP64 (rounded down to a multiple of 32; 0 restores the default, 512).
  *    Shorter segments lower the FP32 accumulation error and cost more
  *    workspace traffic.                                                     */
-enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2 };
+/*  BGW_OPT_AUTOTUNE: 1 (default) lets the context time the candidate tile
+ *    shapes of the pair transform (pairs per block) the first time it meets
+ *    a (grid, precision, epsilon-sphere shape) and keep the fastest; 0 uses
+ *    the fixed default for shapes not yet tuned.                           */
+enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
 
 /* With BGW_OPT_TIMING = 1 the context records CUDA events around its main
@@ -213,6 +217,42 @@ int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
  * word); the result is then meaningless.                                   */
 int bgw_epsinv_noalloc(const bgw_cell* cell, int ng, const int32_t* geps,
                        const void* chi, void* eps, void* epsinv, void* stream);
+
+/* ------------------------------------------------------------------------
+ * bgw_epsilon_batch -- independent q-points, each at the same nfreq
+ * imaginary frequencies (nfreq = 0: static), as one stream of work: per
+ * q-point the matrix elements are computed once and serve every frequency
+ * (the paper's observation that the summation, not the matrix elements,
+ * repeats per frequency), then chi for each frequency and the batched
+ * inverses of all frequencies.  The q-points' epsilon spheres may differ in
+ * size (uneven N_G).
+ *   problems[q]  one q-point; all bulk arrays (cv, cc) are DEVICE arrays,
+ *                G lists and energies host arrays (as in the single calls)
+ *   omega        host double [nfreq] (Ha)
+ *   epsinv[q]    device c128 [max(1,nfreq)][ng_q][ng_q]
+ * On a stream other than the legacy default stream the first call with a
+ * given argument set runs the work directly and also captures it into a
+ * CUDA graph; later calls with the same arguments (same pointers, sizes and
+ * host-array contents) replay that graph with one launch.  Device array
+ * contents may change between calls.  The library's scratch memory used by
+ * a captured graph stays reserved until the context is destroyed.          */
+typedef struct bgw_problem {
+  bgw_cell cell;
+  int nv, npw_v;
+  const int32_t* gv;
+  const void* cv;
+  const double* ev;
+  int nc, npw_c;
+  const int32_t* gc;
+  const void* cc;
+  const double* ec;
+  int ng;
+  const int32_t* geps;
+} bgw_problem;
+
+int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* problems,
+                      int nfreq, const double* omega, int prec,
+                      void* const* epsinv, void* stream);
 
 /* ------------------------------------------------------------------------
  * bgw_epsilon -- the whole path for one q-point and nfreq frequencies

@@ -25,8 +25,9 @@ PREC = {"fp64": BGW_PREC_FP64, "mix_fp16": BGW_PREC_MIX_FP16, "mix_bf16": BGW_PR
 # Every symbol include/bgw.h declares.
 EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_stats", "bgw_launch_count",
            "bgw_mtxel",
-           "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_epsilon")
-BGW_OPT_CHI_SEGMENT_PAIRS, BGW_OPT_TIMING = 1, 2
+           "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_epsilon",
+           "bgw_epsilon_batch")
+BGW_OPT_CHI_SEGMENT_PAIRS, BGW_OPT_TIMING, BGW_OPT_AUTOTUNE = 1, 2, 3
 
 
 class BgwError(RuntimeError):
@@ -38,6 +39,15 @@ class BgwError(RuntimeError):
 class Cell(ctypes.Structure):
     _fields_ = [("bvec", (ctypes.c_double * 3) * 3), ("omega", ctypes.c_double),
                 ("q_frac", ctypes.c_double * 3), ("fft", ctypes.c_int * 3)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("cell", Cell),
+                ("nv", ctypes.c_int), ("npw_v", ctypes.c_int), ("gv", ctypes.POINTER(ctypes.c_int32)),
+                ("cv", ctypes.c_void_p), ("ev", ctypes.POINTER(ctypes.c_double)),
+                ("nc", ctypes.c_int), ("npw_c", ctypes.c_int), ("gc", ctypes.POINTER(ctypes.c_int32)),
+                ("cc", ctypes.c_void_p), ("ec", ctypes.POINTER(ctypes.c_double)),
+                ("ng", ctypes.c_int), ("geps", ctypes.POINTER(ctypes.c_int32))]
 
 
 def make_cell(bvec, omega: float, q_frac, n: int) -> Cell:
@@ -84,6 +94,7 @@ def load() -> ctypes.CDLL:
     lib.bgw_epsinv.argtypes = [vp, ci, cellp, ctypes.POINTER(ci), ctypes.POINTER(i32p), ctypes.POINTER(vp),
                                ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.bgw_epsinv_noalloc.argtypes = [cellp, ci, i32p, vp, vp, vp, vp]
+    lib.bgw_epsilon_batch.argtypes = [vp, ci, ctypes.POINTER(Problem), ci, dp, ci, ctypes.POINTER(vp), vp]
     lib.bgw_epsilon.argtypes = [vp, cellp, ci, ci, i32p, vp, dp, ci, ci, i32p, vp, dp, ci, i32p, ci, dp, ci,
                                 ci, vp, vp, vp]
     for name in EXPORTS:
@@ -224,3 +235,28 @@ class Context:
                                          cc.shape[0], gc_.shape[0], gcp, _ptr(cc), ecp, ge_.shape[0], gep, nfreq,
                                          omp, prec, nc_chunk, _ptr(chi), _ptr(epsinv), _stream(stream)))
         return epsinv
+
+    def epsilon_batch(self, systems, cvs, ccs, omega, prec: int, epsinvs, stream=None):
+        """bgw_epsilon_batch over q-points: `systems` give the host arrays (G
+        lists, energies, cell), `cvs`/`ccs` the device coefficient tensors,
+        `epsinvs` the device outputs [max(1,nfreq)][ng][ng] per q-point."""
+        n = len(systems)
+        keep = []
+        probs = (Problem * n)()
+        for k, s in enumerate(systems):
+            gv_, gvp = _i32(s.gv)
+            gc_, gcp = _i32(s.gc)
+            ge_, gep = _i32(s.geps)
+            ev_, evp = _f64(s.ev)
+            ec_, ecp = _f64(s.ec)
+            keep += [gv_, gc_, ge_, ev_, ec_]
+            p = probs[k]
+            p.cell = make_cell(s.bvec, s.omega, s.q_frac, s.fft)
+            p.nv, p.npw_v, p.gv, p.cv, p.ev = cvs[k].shape[0], gv_.shape[0], gvp, _ptr(cvs[k]), evp
+            p.nc, p.npw_c, p.gc, p.cc, p.ec = ccs[k].shape[0], gc_.shape[0], gcp, _ptr(ccs[k]), ecp
+            p.ng, p.geps = ge_.shape[0], gep
+        om_, omp = _f64(omega)
+        nfreq = 0 if om_ is None else om_.shape[0]
+        outs = (ctypes.c_void_p * n)(*[_ptr(x) for x in epsinvs])
+        self._check(self.lib.bgw_epsilon_batch(self.h, n, probs, nfreq, omp, prec, outs, _stream(stream)))
+        return epsinvs

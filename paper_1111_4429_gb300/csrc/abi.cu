@@ -176,6 +176,10 @@ int bgw_destroy(bgw_ctx* ctx) {
   cudaDeviceSynchronize();
   timing_collect(&ctx->impl);
   for (cudaEvent_t e : ctx->impl.timing.free_events) cudaEventDestroy(e);
+  for (auto& kv : ctx->impl.graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  ctx->impl.graphs.clear();
+  ctx->impl.pool.unpin_all();
   cudaFree(ctx->impl.d_status);
   delete ctx;
   return BGW_OK;
@@ -225,6 +229,11 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
     if (value < 0 || value > (1 << 24)) return fail(c, BGW_EINVAL, "segment pairs must be in [0, 2^24]");
     if (value > 0 && value < 32) return fail(c, BGW_EINVAL, "segment pairs must be >= 32");
     c->chi_segment_pairs = (int)value;
+    return BGW_OK;
+  }
+  if (option == BGW_OPT_AUTOTUNE) {
+    if (value != 0 && value != 1) return fail(c, BGW_EINVAL, "autotune is 0 or 1");
+    c->autotune = value == 1;
     return BGW_OK;
   }
   if (option == BGW_OPT_TIMING) {
@@ -313,15 +322,166 @@ int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, con
   DeviceGuard g(c->device);
   if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<const int32_t*> dgeps(nmat);
+  std::vector<const double*> bv(nmat), qv(nmat);
   for (int m = 0; m < nmat; ++m) {
     const void* dg;
     if ((rc = upload_cached(c, geps[m], (size_t)ng[m] * 3 * sizeof(int32_t), st, &dg)) != BGW_OK) return rc;
-    if ((rc = epsinv_run(c, ng[m], &cells[m].bvec[0][0], cells[m].q_frac, static_cast<const int32_t*>(dg), chi[m],
-                         eps ? eps[m] : nullptr, epsinv[m], st)) != BGW_OK)
+    dgeps[m] = static_cast<const int32_t*>(dg);
+    bv[m] = &cells[m].bvec[0][0];
+    qv[m] = cells[m].q_frac;
+  }
+  if ((rc = epsinv_batch_run(c, nmat, ng, bv.data(), qv.data(), dgeps.data(), chi, eps, epsinv, st)) != BGW_OK)
+    return rc;
+  return BGW_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The whole batch, in stream order on st (no host synchronization once the
+// plans and uploads of its arguments are cached).
+int run_batch(Ctx* c, int nq, const bgw_problem* pr, int nfreq, const double* dev_om, int prec,
+              void* const* epsinv, const std::vector<const void*>& dev_ev, const std::vector<const void*>& dev_ec,
+              const std::vector<const void*>& dev_geps, cudaStream_t st) {
+  const int nrow = nfreq > 0 ? nfreq : 1;
+  const size_t cs = prec == BGW_PREC_FP64 ? 16 : 8;
+  size_t mbytes = 0, cbytes = 0;
+  for (int q = 0; q < nq; ++q) {
+    mbytes = std::max(mbytes, (size_t)pr[q].nv * pr[q].nc * pr[q].ng * cs);
+    cbytes = std::max(cbytes, (size_t)nrow * pr[q].ng * pr[q].ng * sizeof(double2));
+  }
+  Scratch sM, sChi;
+  sM.pool = sChi.pool = &c->pool;
+  int rc;
+  if ((rc = c->pool.alloc(mbytes, &sM.ptr)) != BGW_OK || (rc = c->pool.alloc(cbytes, &sChi.ptr)) != BGW_OK)
+    return fail(c, rc, "bgw_epsilon_batch: scratch allocation failed (M %zu B, chi %zu B)", mbytes, cbytes);
+  for (int q = 0; q < nq; ++q) {
+    const bgw_problem& p = pr[q];
+    const int n = p.cell.fft[0];
+    const BandPlan *bpv, *bpc;
+    const PairPlan* pp;
+    if ((rc = get_band_plan(c, n, p.npw_v, p.gv, st, &bpv)) != BGW_OK) return rc;
+    if ((rc = get_band_plan(c, n, p.npw_c, p.gc, st, &bpc)) != BGW_OK) return rc;
+    if ((rc = get_pair_plan(c, n, p.ng, p.geps, st, &pp)) != BGW_OK) return rc;
+    if ((rc = mtxel_run(c, n, prec, p.nv, bpv, p.cv, p.nc, bpc, p.cc, pp, sM.ptr, st)) != BGW_OK) return rc;
+    if ((rc = chi_run(c, prec, p.nv, p.nc, p.ng, sM.ptr, static_cast<const double*>(dev_ev[q]),
+                      static_cast<const double*>(dev_ec[q]), nfreq, dev_om, 4.0 / p.cell.omega, 0, sChi.ptr, st)) !=
+        BGW_OK)
+      return rc;
+    const size_t n2 = (size_t)p.ng * p.ng * sizeof(double2);
+    std::vector<int> ngv(nrow, p.ng);
+    std::vector<const double*> bv(nrow, &p.cell.bvec[0][0]), qv(nrow, p.cell.q_frac);
+    std::vector<const int32_t*> gv(nrow, static_cast<const int32_t*>(dev_geps[q]));
+    std::vector<const void*> chis(nrow);
+    std::vector<void*> invs(nrow);
+    for (int f = 0; f < nrow; ++f) {
+      chis[f] = static_cast<char*>(sChi.ptr) + f * n2;
+      invs[f] = static_cast<char*>(epsinv[q]) + f * n2;
+    }
+    if ((rc = epsinv_batch_run(c, nrow, ngv.data(), bv.data(), qv.data(), gv.data(), chis.data(), nullptr,
+                               invs.data(), st)) != BGW_OK)
       return rc;
   }
   return BGW_OK;
 }
+
+}  // namespace
+
+extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* problems, int nfreq, const double* omega,
+                                 int prec, void* const* epsinv, void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  if (nq <= 0 || !problems || !epsinv) return fail(c, BGW_EINVAL, "bad batch arguments");
+  if (nfreq < 0 || (nfreq > 0 && !omega)) return fail(c, BGW_EINVAL, "bad frequency list");
+  for (int f = 0; f < nfreq; ++f)
+    if (!isfinite(omega[f])) return fail(c, BGW_EINVAL, "omega[%d] is not finite", f);
+  int rc, n;
+  for (int q = 0; q < nq; ++q) {
+    const bgw_problem& p = problems[q];
+    if ((rc = validate_mtxel(c, &p.cell, p.nv, p.npw_v, p.gv, p.cv, p.nc, p.npw_c, p.gc, p.cc, p.ng, p.geps, prec,
+                             epsinv[q], &n)) != BGW_OK)
+      return fail(c, rc, "problem %d: %s", q, c->err.c_str());
+    if ((rc = check_energies(c, p.nv, p.ev, p.nc, p.ec)) != BGW_OK) return fail(c, rc, "problem %d: %s", q, c->err.c_str());
+    if ((rc = check_q(c, &p.cell, p.ng, p.geps)) != BGW_OK) return fail(c, rc, "problem %d: %s", q, c->err.c_str());
+    if (!is_device_ptr(p.cv) || !is_device_ptr(p.cc) || !is_device_ptr(epsinv[q]))
+      return fail(c, BGW_EINVAL, "problem %d: cv, cc and epsinv must be device arrays", q);
+  }
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Key of the argument set: sizes, pointers and host-array contents.
+  uint64_t key = fnv1a(&nq, sizeof(nq), fnv1a(&prec, sizeof(prec), fnv1a(&nfreq, sizeof(nfreq))));
+  if (nfreq > 0) key = fnv1a(omega, nfreq * sizeof(double), key);
+  key = fnv1a(&st, sizeof(st), key);
+  for (int q = 0; q < nq; ++q) {
+    const bgw_problem& p = problems[q];
+    key = fnv1a(&p.cell, sizeof(p.cell), key);
+    const void* ptrs[3] = {p.cv, p.cc, epsinv[q]};
+    key = fnv1a(ptrs, sizeof(ptrs), key);
+    const int dims[4] = {p.nv, p.npw_v, p.nc, p.npw_c};
+    key = fnv1a(dims, sizeof(dims), key);
+    key = fnv1a(p.gv, (size_t)p.npw_v * 12, key);
+    key = fnv1a(p.gc, (size_t)p.npw_c * 12, key);
+    key = fnv1a(p.geps, (size_t)p.ng * 12, key);
+    key = fnv1a(p.ev, (size_t)p.nv * 8, key);
+    key = fnv1a(p.ec, (size_t)p.nc * 8, key);
+  }
+  auto it = c->graphs.find(key);
+  if (it != c->graphs.end()) {
+    BGW_CUDA(c, cudaGraphLaunch(it->second.exec, st));
+    c->launches += 1;
+    return BGW_OK;
+  }
+  // Uploads of the small host arrays (cached by content).
+  const void* dev_om = nullptr;
+  if (nfreq > 0 && (rc = upload_cached(c, omega, nfreq * sizeof(double), st, &dev_om)) != BGW_OK) return rc;
+  std::vector<const void*> dev_ev(nq), dev_ec(nq), dev_geps(nq);
+  for (int q = 0; q < nq; ++q) {
+    const bgw_problem& p = problems[q];
+    if ((rc = upload_cached(c, p.ev, p.nv * sizeof(double), st, &dev_ev[q])) != BGW_OK) return rc;
+    if ((rc = upload_cached(c, p.ec, p.nc * sizeof(double), st, &dev_ec[q])) != BGW_OK) return rc;
+    if ((rc = upload_cached(c, p.geps, (size_t)p.ng * 12, st, &dev_geps[q])) != BGW_OK) return rc;
+  }
+  // Direct run: produces this call's results, creates the plans, tunes and
+  // fills the pool with the blocks the capture below will reuse.
+  if ((rc = run_batch(c, nq, problems, nfreq, static_cast<const double*>(dev_om), prec, epsinv, dev_ev, dev_ec,
+                      dev_geps, st)) != BGW_OK)
+    return rc;
+  if (st == nullptr || st == cudaStreamLegacy) return BGW_OK;  // the legacy stream cannot be captured
+  const bool timing = c->timing.on;
+  c->timing.on = false;
+  c->pool.set_pinning(true);
+  const uint64_t l0 = c->launches;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = run_batch(c, nq, problems, nfreq, static_cast<const double*>(dev_om), prec, epsinv, dev_ev, dev_ec,
+                   dev_geps, st);
+    e = cudaStreamEndCapture(st, &graph);
+  }
+  c->pool.set_pinning(false);
+  c->timing.on = timing;
+  c->launches = l0;  // captured launches did not run
+  if (e != cudaSuccess || rc != BGW_OK || !graph) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    c->err.clear();
+    return BGW_OK;  // results of the direct run stand; the next call runs directly again
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return BGW_OK;
+  }
+  c->graphs[key].exec = exec;
+  return BGW_OK;
+}
+
+extern "C" {
 
 int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv,
                 const double* ev, int nc, int npw_c, const int32_t* gc, const void* cc, const double* ec, int ng,
@@ -388,10 +548,18 @@ int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
                       4.0 / cell->omega, c0 > 0, d_chi, st)) != BGW_OK)
       return rc;
   }
-  for (int f = 0; f < nrow; ++f) {
-    if ((rc = epsinv_run(c, ng, &cell->bvec[0][0], cell->q_frac, static_cast<const int32_t*>(dev_geps),
-                         static_cast<char*>(d_chi) + f * n2, nullptr, static_cast<char*>(d_inv) + f * n2, st)) !=
-        BGW_OK)
+  {
+    std::vector<int> ngv(nrow, ng);
+    std::vector<const double*> bv(nrow, &cell->bvec[0][0]), qv(nrow, cell->q_frac);
+    std::vector<const int32_t*> gv2(nrow, static_cast<const int32_t*>(dev_geps));
+    std::vector<const void*> chis(nrow);
+    std::vector<void*> invs(nrow);
+    for (int f = 0; f < nrow; ++f) {
+      chis[f] = static_cast<char*>(d_chi) + f * n2;
+      invs[f] = static_cast<char*>(d_inv) + f * n2;
+    }
+    if ((rc = epsinv_batch_run(c, nrow, ngv.data(), bv.data(), qv.data(), gv2.data(), chis.data(), nullptr,
+                               invs.data(), st)) != BGW_OK)
       return rc;
   }
   if (chi && !chi_dev) BGW_CUDA(c, cudaMemcpyAsync(chi, d_chi, nrow * n2, cudaMemcpyDeviceToHost, st));

@@ -206,10 +206,31 @@ __global__ void __launch_bounds__(256) gj_update_kernel(double2* __restrict__ A,
 // P = C D^-1 the trailing update of a lower element is
 //   A_ij -= sum_s P_is conj(C_js),
 // half the work of a full Gauss-Jordan step.
-__global__ void __launch_bounds__(NB * NB) sw_diag_kernel(double2* __restrict__ A, int ng, int k0, int kb,
-                                                          double2* __restrict__ Dinv, int* __restrict__ status) {
+// Matrices swept together: one launch per step serves every matrix
+// (blockIdx.y / blockIdx.x selects the matrix), so the single-CTA diagonal
+// step of one matrix runs beside those of the others.
+constexpr int kSweepBatch = 128;
+struct SweepMat {
+  double2* A;     // the matrix (lower triangle swept in place)
+  double2* C;     // [ng][NB] column panel of the current block
+  double2* P;     // [ng][NB] C D^-1
+  double2* Dinv;  // [NB][NB]
+  int ng;
+};
+struct SweepBatch {
+  int n;
+  SweepMat m[kSweepBatch];
+};
+
+__global__ void __launch_bounds__(NB * NB) sw_diag_kernel(const __grid_constant__ SweepBatch b, int k0,
+                                                          int* __restrict__ status) {
   __shared__ double2 D[NB][NB + 1];
   __shared__ double2 recip;  // 1/pivot, computed once per step (FP64 division is costly on one SM)
+  const SweepMat& M = b.m[blockIdx.x];
+  const int ng = M.ng;
+  if (k0 >= ng) return;
+  const int kb = min(NB, ng - k0);
+  double2* A = M.A;
   const int i = threadIdx.y, j = threadIdx.x;
   const bool in = i < kb && j < kb;
   double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
@@ -252,21 +273,24 @@ __global__ void __launch_bounds__(NB * NB) sw_diag_kernel(double2* __restrict__ 
   __syncthreads();
   if (in) {
     const double2 d = D[i][j];
-    Dinv[i * NB + j] = d;
+    M.Dinv[i * NB + j] = d;
     if (i >= j) A[(size_t)(k0 + i) * ng + k0 + j] = make_double2(-d.x, -d.y);
   }
 }
 
 // One warp per row i outside K (lane = column s of the panel):
 //   C_i = A_iK (stored lower part), P_i = C_i D^-1, then A_iK <- P_i.
-// C and P go to scratch (ld NB) for the update.  grid ceil(ng/8), block 256.
-__global__ void __launch_bounds__(256) sw_panel_kernel(double2* __restrict__ A, int ng, int k0, int kb,
-                                                       const double2* __restrict__ Dinv, double2* __restrict__ C,
-                                                       double2* __restrict__ P) {
+// grid (ceil(max ng / 8), nmat), block 256.
+__global__ void __launch_bounds__(256) sw_panel_kernel(const __grid_constant__ SweepBatch b, int k0) {
   __shared__ double2 Ds[NB][NB];
   __shared__ double2 Cs[8][NB];
+  const SweepMat& M = b.m[blockIdx.y];
+  const int ng = M.ng;
+  if (k0 >= ng || blockIdx.x * 8 >= ng) return;
+  const int kb = min(NB, ng - k0);
+  double2* A = M.A;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Dinv[e];
+  for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = M.Dinv[e];
   const int i = blockIdx.x * 8 + warp;
   const bool row_ok = i < ng && (i < k0 || i >= k0 + kb);
   double2 cv = make_double2(0.0, 0.0);
@@ -288,8 +312,8 @@ __global__ void __launch_bounds__(256) sw_panel_kernel(double2* __restrict__ A, 
     pv.y = fma(a.x, d.y, fma(a.y, d.x, pv.y));
   }
   if (lane < kb) {
-    C[(size_t)i * NB + lane] = cv;
-    P[(size_t)i * NB + lane] = pv;
+    M.C[(size_t)i * NB + lane] = cv;
+    M.P[(size_t)i * NB + lane] = pv;
     if (i >= k0 + kb)
       A[(size_t)i * ng + k0 + lane] = pv;
     else
@@ -298,14 +322,18 @@ __global__ void __launch_bounds__(256) sw_panel_kernel(double2* __restrict__ A, 
 }
 
 // Lower 64x64 tiles: A_ij -= sum_s P_is conj(C_js) for i >= j outside K.
-// grid: nt (nt+1) / 2 tiles, block 256, dynamic smem.
-__global__ void __launch_bounds__(256) sw_update_kernel(double2* __restrict__ A, int ng, int k0, int kb,
-                                                        const double2* __restrict__ P,
-                                                        const double2* __restrict__ C) {
+// grid (tiles of the largest matrix, nmat), block 256, dynamic smem.
+__global__ void __launch_bounds__(256) sw_update_kernel(const __grid_constant__ SweepBatch b, int k0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2 (*Ps)[NB + 1] = reinterpret_cast<double2 (*)[NB + 1]>(smem_raw);
   double2 (*Cs)[NB + 1] = reinterpret_cast<double2 (*)[NB + 1]>(smem_raw + sizeof(double2) * TU * (NB + 1));
+  const SweepMat& M = b.m[blockIdx.y];
+  const int ng = M.ng;
+  if (k0 >= ng) return;
+  const int kb = min(NB, ng - k0);
+  const int nt = (ng + TU - 1) / TU;
   const long long t = blockIdx.x;
+  if (t >= (long long)nt * (nt + 1) / 2) return;
   int I = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
   while ((long long)(I + 1) * (I + 2) / 2 <= t) ++I;
   while ((long long)I * (I + 1) / 2 > t) --I;
@@ -314,6 +342,9 @@ __global__ void __launch_bounds__(256) sw_update_kernel(double2* __restrict__ A,
   // tiles whose rows or columns all lie inside K have nothing to update
   if (i0 >= k0 && min(i0 + TU, ng) <= k0 + kb) return;
   if (j0 >= k0 && min(j0 + TU, ng) <= k0 + kb) return;
+  double2* A = M.A;
+  const double2* P = M.P;
+  const double2* C = M.C;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int e = tid; e < TU * NB; e += 256) {
     const int r = e / NB, s = e % NB;
@@ -327,21 +358,21 @@ __global__ void __launch_bounds__(256) sw_update_kernel(double2* __restrict__ A,
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0.0, 0.0);
+    for (int c = 0; c < 4; ++c) acc[a][c] = make_double2(0.0, 0.0);
   for (int s = 0; s < kb; ++s) {
     double2 pv[4], cv[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) pv[a] = Ps[ty + 16 * a][s];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) cv[b] = Cs[tx + 16 * b][s];
+    for (int c = 0; c < 4; ++c) cv[c] = Cs[tx + 16 * c][s];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        acc[a][b].x = fma(pv[a].x, cv[b].x, acc[a][b].x);
-        acc[a][b].x = fma(-pv[a].y, cv[b].y, acc[a][b].x);
-        acc[a][b].y = fma(pv[a].x, cv[b].y, acc[a][b].y);
-        acc[a][b].y = fma(pv[a].y, cv[b].x, acc[a][b].y);
+      for (int c = 0; c < 4; ++c) {
+        acc[a][c].x = fma(pv[a].x, cv[c].x, acc[a][c].x);
+        acc[a][c].x = fma(-pv[a].y, cv[c].y, acc[a][c].x);
+        acc[a][c].y = fma(pv[a].x, cv[c].y, acc[a][c].y);
+        acc[a][c].y = fma(pv[a].y, cv[c].x, acc[a][c].y);
       }
   }
 #pragma unroll
@@ -349,19 +380,22 @@ __global__ void __launch_bounds__(256) sw_update_kernel(double2* __restrict__ A,
     const int i = i0 + ty + 16 * a;
     if (i >= ng || (i >= k0 && i < k0 + kb)) continue;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = j0 + tx + 16 * b;
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx + 16 * c;
       if (j > i || (j >= k0 && j < k0 + kb)) continue;
       double2* dst = A + (size_t)i * ng + j;
       const double2 v = *dst;
-      *dst = make_double2(v.x - acc[a][b].x, v.y - acc[a][b].y);
+      *dst = make_double2(v.x - acc[a][c].x, v.y - acc[a][c].y);
     }
   }
 }
 
 // The swept lower triangle holds -eps~^-1: negate and mirror into both
-// triangles.  One thread per lower element.
-__global__ void sw_finish_kernel(double2* __restrict__ A, int ng) {
+// triangles.  One thread per lower element; grid (blocks, nmat).
+__global__ void sw_finish_kernel(const __grid_constant__ SweepBatch b) {
+  const SweepMat& M = b.m[blockIdx.y];
+  const int ng = M.ng;
+  double2* A = M.A;
   const long long nlow = (long long)ng * (ng + 1) / 2;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nlow;
        e += (long long)gridDim.x * blockDim.x) {
@@ -379,54 +413,77 @@ __global__ void sw_finish_kernel(double2* __restrict__ A, int ng) {
   }
 }
 
-int epsinv_run(Ctx* c, int ng, const double* bvec, const double* qf, const int32_t* d_geps,
-               const void* chi, void* eps, void* epsinv, cudaStream_t st) {
-  Scratch sv, dinv, R, Cp;
-  sv.pool = dinv.pool = R.pool = Cp.pool = &c->pool;
-  int rc;
-  if ((rc = c->pool.alloc((size_t)ng * sizeof(double), &sv.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)NB * NB * sizeof(double2), &dinv.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)NB * ng * sizeof(double2), &R.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)NB * ng * sizeof(double2), &Cp.ptr)) != BGW_OK)
-    return fail(c, rc, "bgw_epsinv: scratch allocation failed");
-  double2* A = static_cast<double2*>(epsinv);
-  {
-    TimedScope ts(c, kTEpsForm, st);
-    coulomb_sqrt_kernel<<<(ng + 255) / 256, 256, 0, st>>>(d_geps, ng, bvec[0], bvec[1], bvec[2], bvec[3],
-                                                          bvec[4], bvec[5], bvec[6], bvec[7], bvec[8], qf[0],
-                                                          qf[1], qf[2], sv.as<double>());
-    const size_t n2 = (size_t)ng * ng;
-    const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
-    eps_form_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(chi), sv.as<double>(), ng, A,
-                                        static_cast<double2*>(eps));
+// eps~ formation for every matrix of the batch, then the batched sweep.
+int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec, const double* const* qf,
+                     const int32_t* const* d_geps, const void* const* chi, void* const* eps, void* const* epsinv,
+                     cudaStream_t st) {
+  for (int m0 = 0; m0 < nmat; m0 += kSweepBatch) {
+    const int nb = std::min(kSweepBatch, nmat - m0);
+    size_t pan = 0;
+    int ngmax = 0;
+    for (int m = m0; m < m0 + nb; ++m) {
+      pan += (size_t)ng[m] * NB;
+      ngmax = std::max(ngmax, ng[m]);
+    }
+    Scratch sv, dinv, R, Cp;
+    sv.pool = dinv.pool = R.pool = Cp.pool = &c->pool;
+    int rc;
+    if ((rc = c->pool.alloc((size_t)ngmax * sizeof(double), &sv.ptr)) != BGW_OK ||
+        (rc = c->pool.alloc((size_t)nb * NB * NB * sizeof(double2), &dinv.ptr)) != BGW_OK ||
+        (rc = c->pool.alloc(pan * sizeof(double2), &R.ptr)) != BGW_OK ||
+        (rc = c->pool.alloc(pan * sizeof(double2), &Cp.ptr)) != BGW_OK)
+      return fail(c, rc, "bgw_epsinv: scratch allocation failed");
+    SweepBatch sb;
+    sb.n = nb;
+    size_t off = 0;
+    for (int k = 0; k < nb; ++k) {
+      const int m = m0 + k;
+      double2* A = static_cast<double2*>(epsinv[m]);
+      {
+        TimedScope ts(c, kTEpsForm, st);
+        const double* bv = bvec[m];
+        const double* q = qf[m];
+        coulomb_sqrt_kernel<<<(ng[m] + 255) / 256, 256, 0, st>>>(d_geps[m], ng[m], bv[0], bv[1], bv[2], bv[3],
+                                                                 bv[4], bv[5], bv[6], bv[7], bv[8], q[0], q[1], q[2],
+                                                                 sv.as<double>());
+        const size_t n2 = (size_t)ng[m] * ng[m];
+        const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
+        eps_form_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(chi[m]), sv.as<double>(), ng[m], A,
+                                            static_cast<double2*>(eps ? eps[m] : nullptr));
+        BGW_CUDA(c, cudaGetLastError());
+        c->launches += 2;
+      }
+      sb.m[k].A = A;
+      sb.m[k].C = Cp.as<double2>() + off;
+      sb.m[k].P = R.as<double2>() + off;
+      sb.m[k].Dinv = dinv.as<double2>() + (size_t)k * NB * NB;
+      sb.m[k].ng = ng[m];
+      off += (size_t)ng[m] * NB;
+    }
+    TimedScope ts_inv(c, kTInverse, st);
+    const int nt = (ngmax + TU - 1) / TU;
+    const long long ntl = (long long)nt * (nt + 1) / 2;
+    const size_t upd_smem = sizeof(double2) * 2 * TU * (NB + 1);
+    BGW_CUDA(c, cudaFuncSetAttribute(sw_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
+    for (int k0 = 0; k0 < ngmax; k0 += NB) {
+      sw_diag_kernel<<<nb, dim3(NB, NB), 0, st>>>(sb, k0, c->d_status);
+      sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, st>>>(sb, k0);
+      sw_update_kernel<<<dim3((unsigned)ntl, nb), 256, upd_smem, st>>>(sb, k0);
+      BGW_CUDA(c, cudaGetLastError());
+      c->launches += 3;
+    }
+    const long long nlow = (long long)ngmax * (ngmax + 1) / 2;
+    sw_finish_kernel<<<dim3((unsigned)std::min<long long>((nlow + 255) / 256, 152LL * 16), nb), 256, 0, st>>>(sb);
     BGW_CUDA(c, cudaGetLastError());
-    c->launches += 2;
+    c->launches += 1;
   }
-  TimedScope ts_inv(c, kTInverse, st);
-  const int nt = (ng + TU - 1) / TU;
-  const long long ntl = (long long)nt * (nt + 1) / 2;
-  const size_t upd_smem = sizeof(double2) * 2 * TU * (NB + 1);
-  BGW_CUDA(c, cudaFuncSetAttribute(sw_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
-  for (int k0 = 0; k0 < ng; k0 += NB) {
-    const int kb = std::min(NB, ng - k0);
-    sw_diag_kernel<<<1, dim3(NB, NB), 0, st>>>(A, ng, k0, kb, dinv.as<double2>(), c->d_status);
-    sw_panel_kernel<<<(ng + 7) / 8, 256, 0, st>>>(A, ng, k0, kb, dinv.as<double2>(), Cp.as<double2>(),
-                                                  R.as<double2>());
-    sw_update_kernel<<<(unsigned)ntl, 256, upd_smem, st>>>(A, ng, k0, kb, R.as<double2>(), Cp.as<double2>());
-    BGW_CUDA(c, cudaGetLastError());
-    c->launches += 3;
-  }
-  const long long nlow = (long long)ng * (ng + 1) / 2;
-  sw_finish_kernel<<<(unsigned)std::min<long long>((nlow + 255) / 256, 152LL * 16), 256, 0, st>>>(A, ng);
-  BGW_CUDA(c, cudaGetLastError());
-  c->launches += 1;
   return BGW_OK;
 }
 
 // ---------------------------------------------------------------------------
 // Allocation-free inverse: bgw_epsinv_noalloc (include/bgw.h).
 //
-// Same kernels and launch sequence as epsinv_run, but every scratch buffer
+// The Gauss-Jordan kernels above, with every scratch buffer
 // (Coulomb factors, the G list, the diagonal-block inverse, the two panels and
 // the status word) lives in one file-scope device array of fixed size, so the
 // call makes no device allocation.  The array is part of the library's device

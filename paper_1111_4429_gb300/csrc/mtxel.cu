@@ -162,6 +162,12 @@ int mtxel_run(Ctx* c, int n, int prec, int nv, const BandPlan* bpv, const void* 
   x.st = st;
   x.launches = &c->launches;
   x.ctx = c;
+  // Pairs per pair_yxpass block: autotuned once per shape, or the default
+  // (as many pairs as 256 threads hold) when tuning is off.
+  const int ppb_default = std::max(1, 256 / n);
+  int* slot = &c->tuned_ppb[std::make_tuple(n, prec == BGW_PREC_FP64 ? 0 : 1, pp->nys, pp->ncol)];
+  if (!c->autotune && *slot <= 0) *slot = ppb_default;
+  x.tuned_ppb = slot;
   cudaError_t e = prec == BGW_PREC_FP64 ? mtxel_exec_f64(x) : mtxel_exec_f32(x);
   if (e != cudaSuccess) return cuda_fail(c, e, "bgw_mtxel kernels");
   return BGW_OK;

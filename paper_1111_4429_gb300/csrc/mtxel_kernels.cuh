@@ -13,6 +13,8 @@
 //
 // Real-space grids are u[b][z][y][x] (x fastest), n^3 complex per band.
 #pragma once
+#include <algorithm>
+
 #include "fft.cuh"
 #include "runtime.h"
 
@@ -201,19 +203,61 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Pairs handled by one pair_yxpass block and its thread count.
+// Shared memory and threads of a pair_yxpass block holding ppb pairs.
 template <typename T, int N>
-static void pair_block_shape(int nys, int ncol, int* ppb, int* threads, size_t* smem) {
-  int p = 256 / N;
-  if (p < 1) p = 1;
-  for (;; --p) {
-    size_t s = (size_t)p * nys * (N + 1) * sizeof(cpx<T>) + (size_t)p * ncol * sizeof(cpx<T>) +
-               (size_t)(N * nys + N) * sizeof(int);
-    if (s <= 200 * 1024 || p == 1) { *smem = s; break; }
-  }
-  *ppb = p;
-  int t = ((p * N + 31) / 32) * 32;
+static void pair_block_shape(int ppb, int nys, int ncol, int* threads, size_t* smem) {
+  *smem = (size_t)ppb * nys * (N + 1) * sizeof(cpx<T>) + (size_t)ppb * ncol * sizeof(cpx<T>) +
+          (size_t)(N * nys + N) * sizeof(int);
+  const int t = ((ppb * N + 31) / 32) * 32;
   *threads = t > 256 ? 256 : t;
+}
+
+// Autotuner of the pairs per pair_yxpass block: each candidate runs twice on
+// the first pairs of the call (the second run is timed with CUDA events on
+// the call's stream) and the fastest is kept for this (grid, precision,
+// epsilon-sphere shape).  Runs once per shape, outside graph capture.
+template <typename T, int N>
+static int tune_pairs_per_block(const MtxelExec& x, const cpx<T>* uv, const cpx<T>* uc, cpx<T>* Tb) {
+  const PairPlan* pp = x.pp;
+  const int npb = (int)std::min<long long>((long long)x.nv * x.nc, std::min<long long>(x.pair_block, 4096));
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return 256 / N > 0 ? 256 / N : 1;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return 256 / N > 0 ? 256 / N : 1;
+  }
+  int best = 0;
+  float best_ms = 1e30f;
+  const int cands[] = {1, 2, 3, 4, 6, 8, 12};
+  for (int p : cands) {
+    int threads;
+    size_t sm;
+    pair_block_shape<T, N>(p, pp->nys, pp->ncol, &threads, &sm);
+    if (sm > 200 * 1024 || p * N > 1024) continue;
+    if (set_smem(pair_yxpass<T, N>, sm) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, x.st);
+      pair_yxpass<T, N><<<dim3((npb + p - 1) / p, N), threads, sm, x.st>>>(
+          uv, uc, x.nc, 0, npb, p, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
+      cudaEventRecord(e1, x.st);
+    }
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    *x.launches += 2;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = p;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best > 0 ? best : (256 / N > 0 ? 256 / N : 1);
 }
 
 template <typename T, int N>
@@ -247,9 +291,14 @@ static cudaError_t mtxel_exec_n(const MtxelExec& x) {
   }
   *x.launches += 4;
   const PairPlan* pp = x.pp;
-  int ppb, threads;
+  int ppb = x.tuned_ppb ? *x.tuned_ppb : 0;
+  if (ppb <= 0) {
+    ppb = tune_pairs_per_block<T, N>(x, uv, uc, Tb);
+    if (x.tuned_ppb) *x.tuned_ppb = ppb;
+  }
+  int threads;
   size_t sm;
-  pair_block_shape<T, N>(pp->nys, pp->ncol, &ppb, &threads, &sm);
+  pair_block_shape<T, N>(ppb, pp->nys, pp->ncol, &threads, &sm);
   if ((e = set_smem(pair_yxpass<T, N>, sm)) != cudaSuccess) return e;
   size_t smz = (size_t)pp->ng * sizeof(C);
   if ((e = set_smem(pair_zgather<T, N>, smz)) != cudaSuccess) return e;

@@ -57,9 +57,11 @@ int Pool::alloc(size_t bytes, void** out) {
     live_[p] = sz;
     in_use_ += sz;
     if (in_use_ > high_water_) high_water_ = in_use_;
+    if (pinning_) pinned_[p] = sz;
     *out = p;
     return BGW_OK;
   }
+  if (pinning_) return BGW_EBUSY;  // no new device memory while a graph is being captured
   if (budget_ && reserved_ + sz > budget_) {
     trim();
     if (reserved_ + sz > budget_) return BGW_ENOMEM;
@@ -96,11 +98,16 @@ void Pool::trim() {
   // Blocks on the free list may still be read by queued work of the stream
   // that released them; wait for the device before giving them back.
   cudaDeviceSynchronize();
+  std::multimap<size_t, void*> keep;
   for (auto& kv : free_) {
+    if (pinned_.count(kv.second)) {
+      keep.emplace(kv.first, kv.second);
+      continue;
+    }
     cudaFree(kv.second);
     reserved_ -= kv.first;
   }
-  free_.clear();
+  free_.swap(keep);
 }
 
 // ------------------------------------------------------------ timing

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -36,7 +37,11 @@ class Pool {
   // Returns BGW_OK / BGW_ENOMEM / BGW_ECUDA.
   int alloc(size_t bytes, void** out);
   void release(void* p);
-  void trim();  // cudaFree every cached free block
+  void trim();  // cudaFree every cached free block not pinned by a graph
+  // While pinning is on, every block handed out is marked pinned: a CUDA
+  // graph captured meanwhile refers to it, so trim() must never free it.
+  void set_pinning(bool on) { pinning_ = on; }
+  void unpin_all() { pinned_.clear(); }
   uint64_t in_use() const { return in_use_; }
   uint64_t reserved() const { return reserved_; }
   uint64_t high_water() const { return high_water_; }
@@ -49,6 +54,8 @@ class Pool {
   uint64_t high_water_ = 0;
   std::multimap<size_t, void*> free_;
   std::unordered_map<void*, size_t> live_;
+  std::unordered_map<void*, size_t> pinned_;
+  bool pinning_ = false;
 };
 
 // RAII scratch handle released to the pool at scope exit (stream order).
@@ -91,9 +98,17 @@ enum TimedName { kTBand = 0, kTPairYX, kTPairZ, kTChiF64, kTChiSplit, kTChiTc, k
                  kTNumNames };
 const char* timed_name(int n);
 
+// A captured batch (bgw_epsilon_batch) replayed while its key is unchanged.
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+};
+
 struct Ctx {
   int device = 0;
   Timing timing;
+  std::unordered_map<uint64_t, BatchGraph> graphs;
+  std::map<std::tuple<int, int, int, int>, int> tuned_ppb;  // (n, prec, nys, ncol) -> pairs per CTA
+  bool autotune = true;
   Pool pool;
   std::string err;
   int* d_status = nullptr;   // device status word
@@ -160,6 +175,7 @@ struct MtxelExec {
   cudaStream_t st = nullptr;
   uint64_t* launches = nullptr;  // incremented per kernel launch
   Ctx* ctx = nullptr;            // for optional event timing
+  int* tuned_ppb = nullptr;      // in/out: pairs per pair_yxpass CTA (0 = tune now)
 };
 cudaError_t mtxel_exec_f64(const MtxelExec& x);
 cudaError_t mtxel_exec_f32(const MtxelExec& x);
@@ -173,8 +189,10 @@ int mtxel_run(Ctx* c, int n, int prec, int nv, const BandPlan* bpv, const void* 
 int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const double* d_ev,
             const double* d_ec, int nfreq, const double* d_omega, double scale, int accumulate,
             void* chi, cudaStream_t st);
-int epsinv_run(Ctx* c, int ng, const double* bvec, const double* qf, const int32_t* d_geps,
-               const void* chi, void* eps, void* epsinv, cudaStream_t st);
+// eps~ and its inverse for nmat matrices (per-matrix size, cell and q).
+int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec, const double* const* qf,
+                     const int32_t* const* d_geps, const void* const* chi, void* const* eps, void* const* epsinv,
+                     cudaStream_t st);
 
 }  // namespace bgw
 
