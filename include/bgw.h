@@ -116,7 +116,11 @@ int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
  *    shapes of the pair transform (pairs per block) the first time it meets
  *    a (grid, precision, epsilon-sphere shape) and keep the fastest; 0 uses
  *    the fixed default for shapes not yet tuned.                           */
-enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3 };
+/*  BGW_OPT_CHI_CHUNK_PAIRS: mixed-precision chi converts and sums the pairs
+ *    in chunks of this many pairs (rounded down to a multiple of 32), each
+ *    chunk's FP64 sum added into chi; 0 (default) sizes chunks so that their
+ *    operand planes and FP32 workspace stay near 1 GiB each.               */
+enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3, BGW_OPT_CHI_CHUNK_PAIRS = 4 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
 
 /* With BGW_OPT_TIMING = 1 the context records CUDA events around its main
@@ -253,6 +257,59 @@ typedef struct bgw_problem {
 int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* problems,
                       int nfreq, const double* omega, int prec,
                       void* const* epsinv, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a stream of independent eps~^-1 requests of different sizes.
+ * The server keeps max_slots requests in flight, each on its own CUDA
+ * stream and context; a request waiting in the FIFO is admitted as soon as
+ * a slot is free and its device-memory estimate fits in what the HBM budget
+ * has left, so its work overlaps with the requests already running
+ * (continuous batching across streams).  Inputs are copied into pinned host
+ * memory at submit time, so the caller's arrays may be reused immediately.
+ * Every request runs the whole path (bgw_epsilon) in opts->prec.
+ * Thread safety: submit, poll and cancel may be called from any thread.
+ *
+ *   opts.hbm_budget_bytes  bound on the sum of the estimates of admitted
+ *                          requests (0 = 90 % of the free device memory at
+ *                          open); a request whose estimate exceeds it alone
+ *                          completes with BGW_ENOMEM
+ *   opts.max_slots         1..64 requests in flight
+ *   request.problem        one q-point; cv, cc are HOST arrays here
+ *   request.epsinv_out     host c128 [ng][ng]; written before the request
+ *                          completes; must stay valid until then
+ *   bgw_serve_poll         waits up to timeout_ms; BGW_EBUSY if the request
+ *                          is still pending, else fills *out and forgets the
+ *                          ticket (out->status is the request's own status)
+ *   bgw_serve_cancel       removes a request that has not been admitted
+ *                          (BGW_EBUSY once it runs); its status becomes
+ *                          BGW_ECANCELED
+ *   bgw_serve_close        cancels waiting requests, lets running ones
+ *                          finish, and frees the server                    */
+typedef struct bgw_serve_opts {
+  uint64_t hbm_budget_bytes;
+  int max_slots;
+  int prec;
+} bgw_serve_opts;
+
+typedef struct bgw_request {
+  bgw_problem problem;
+  void* epsinv_out;
+} bgw_request;
+
+typedef struct bgw_result {
+  int status;
+  double latency_ms;   /* submit -> eps~^-1 on the host */
+  double queue_ms;     /* submit -> admission */
+  uint64_t hbm_bytes;  /* admission estimate */
+} bgw_result;
+
+typedef struct bgw_server bgw_server;
+
+int bgw_serve_open(int device, const bgw_serve_opts* opts, bgw_server** out);
+int bgw_serve_submit(bgw_server* srv, const bgw_request* req, uint64_t* ticket);
+int bgw_serve_poll(bgw_server* srv, uint64_t ticket, int timeout_ms, bgw_result* out);
+int bgw_serve_cancel(bgw_server* srv, uint64_t ticket);
+int bgw_serve_close(bgw_server* srv);
 
 /* ------------------------------------------------------------------------
  * bgw_epsilon -- the whole path for one q-point and nfreq frequencies

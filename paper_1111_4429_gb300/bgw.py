@@ -26,8 +26,9 @@ PREC = {"fp64": BGW_PREC_FP64, "mix_fp16": BGW_PREC_MIX_FP16, "mix_bf16": BGW_PR
 EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_stats", "bgw_launch_count",
            "bgw_mtxel",
            "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_epsilon",
-           "bgw_epsilon_batch")
-BGW_OPT_CHI_SEGMENT_PAIRS, BGW_OPT_TIMING, BGW_OPT_AUTOTUNE = 1, 2, 3
+           "bgw_epsilon_batch", "bgw_serve_open", "bgw_serve_submit", "bgw_serve_poll", "bgw_serve_cancel",
+           "bgw_serve_close")
+BGW_OPT_CHI_SEGMENT_PAIRS, BGW_OPT_TIMING, BGW_OPT_AUTOTUNE, BGW_OPT_CHI_CHUNK_PAIRS = 1, 2, 3, 4
 
 
 class BgwError(RuntimeError):
@@ -48,6 +49,19 @@ class Problem(ctypes.Structure):
                 ("nc", ctypes.c_int), ("npw_c", ctypes.c_int), ("gc", ctypes.POINTER(ctypes.c_int32)),
                 ("cc", ctypes.c_void_p), ("ec", ctypes.POINTER(ctypes.c_double)),
                 ("ng", ctypes.c_int), ("geps", ctypes.POINTER(ctypes.c_int32))]
+
+
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("problem", Problem), ("epsinv_out", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("hbm_bytes", ctypes.c_uint64)]
 
 
 def make_cell(bvec, omega: float, q_frac, n: int) -> Cell:
@@ -95,6 +109,11 @@ def load() -> ctypes.CDLL:
                                ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.bgw_epsinv_noalloc.argtypes = [cellp, ci, i32p, vp, vp, vp, vp]
     lib.bgw_epsilon_batch.argtypes = [vp, ci, ctypes.POINTER(Problem), ci, dp, ci, ctypes.POINTER(vp), vp]
+    lib.bgw_serve_open.argtypes = [ci, ctypes.POINTER(ServeOpts), ctypes.POINTER(vp)]
+    lib.bgw_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.bgw_serve_poll.argtypes = [vp, ctypes.c_uint64, ci, ctypes.POINTER(Result)]
+    lib.bgw_serve_cancel.argtypes = [vp, ctypes.c_uint64]
+    lib.bgw_serve_close.argtypes = [vp]
     lib.bgw_epsilon.argtypes = [vp, cellp, ci, ci, i32p, vp, dp, ci, ci, i32p, vp, dp, ci, i32p, ci, dp, ci,
                                 ci, vp, vp, vp]
     for name in EXPORTS:
@@ -260,3 +279,74 @@ class Context:
         outs = (ctypes.c_void_p * n)(*[_ptr(x) for x in epsinvs])
         self._check(self.lib.bgw_epsilon_batch(self.h, n, probs, nfreq, omp, prec, outs, _stream(stream)))
         return epsinvs
+
+
+def _problem(s, cv, cc, keep):
+    """Fill a Problem from a synthetic system; cv/cc are arrays or tensors."""
+    gv_, gvp = _i32(s.gv)
+    gc_, gcp = _i32(s.gc)
+    ge_, gep = _i32(s.geps)
+    ev_, evp = _f64(s.ev)
+    ec_, ecp = _f64(s.ec)
+    keep += [gv_, gc_, ge_, ev_, ec_, cv, cc]
+    p = Problem()
+    p.cell = make_cell(s.bvec, s.omega, s.q_frac, s.fft)
+    p.nv, p.npw_v, p.gv, p.cv, p.ev = cv.shape[0], gv_.shape[0], gvp, _ptr(cv), evp
+    p.nc, p.npw_c, p.gc, p.cc, p.ec = cc.shape[0], gc_.shape[0], gcp, _ptr(cc), ecp
+    p.ng, p.geps = ge_.shape[0], gep
+    return p
+
+
+class Server:
+    """bgw_serve_*: requests of different sizes, admitted by an HBM budget
+    and run concurrently on per-slot streams."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_slots: int = 4, prec: int = BGW_PREC_MIX_FP16):
+        self.lib = load()
+        o = ServeOpts(hbm_budget_bytes, max_slots, prec)
+        h = ctypes.c_void_p()
+        rc = self.lib.bgw_serve_open(device, ctypes.byref(o), ctypes.byref(h))
+        if rc != BGW_OK:
+            raise BgwError(rc, "bgw_serve_open failed")
+        self.h = h
+        self._outs = {}
+
+    def submit(self, system, out) -> int:
+        """Queue one request (host cv/cc taken from `system`); `out` is a host
+        array [ng][ng] complex128 that receives eps~^-1."""
+        keep = []
+        r = Request()
+        r.problem = _problem(system, np.ascontiguousarray(system.cv), np.ascontiguousarray(system.cc), keep)
+        r.epsinv_out = _ptr(out)
+        t = ctypes.c_uint64()
+        rc = self.lib.bgw_serve_submit(self.h, ctypes.byref(r), ctypes.byref(t))
+        if rc != BGW_OK:
+            raise BgwError(rc, "bgw_serve_submit failed")
+        self._outs[t.value] = out
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 0):
+        """Result of a request, or None while it is still pending."""
+        res = Result()
+        rc = self.lib.bgw_serve_poll(self.h, ticket, timeout_ms, ctypes.byref(res))
+        if rc == BGW_EBUSY:
+            return None
+        if rc != BGW_OK:
+            raise BgwError(rc, "bgw_serve_poll failed")
+        self._outs.pop(ticket, None)
+        return {"status": res.status, "latency_ms": res.latency_ms, "queue_ms": res.queue_ms,
+                "hbm_bytes": res.hbm_bytes}
+
+    def cancel(self, ticket: int) -> int:
+        return self.lib.bgw_serve_cancel(self.h, ticket)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bgw_serve_close(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

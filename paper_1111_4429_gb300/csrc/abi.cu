@@ -231,6 +231,11 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
     c->chi_segment_pairs = (int)value;
     return BGW_OK;
   }
+  if (option == BGW_OPT_CHI_CHUNK_PAIRS) {
+    if (value < 0 || value > (1 << 30)) return fail(c, BGW_EINVAL, "chunk pairs must be in [0, 2^30]");
+    c->chi_chunk_pairs = (int)value;
+    return BGW_OK;
+  }
   if (option == BGW_OPT_AUTOTUNE) {
     if (value != 0 && value != 1) return fail(c, BGW_EINVAL, "autotune is 0 or 1");
     c->autotune = value == 1;

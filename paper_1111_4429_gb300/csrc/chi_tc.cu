@@ -329,23 +329,25 @@ __device__ __forceinline__ int scale_exp(const unsigned int* maxbits, int bf16) 
   return 14 - ex;
 }
 
-// planes[pl][g][p] for g < ngpad, p < kpad (zero padded), from M[p][g]:
+// planes[pl][g][p] for g < ngpad, p < kpad (zero padded), from M[p0 + p][g]
+// for the K pairs of one chunk:
 // x = M sqrt|w_p| 2^e split into hi + lo.  32 x 32 transposing tiles.
 template <typename H>
-__global__ void split_kernel(const float2* __restrict__ M, const double* __restrict__ w, long long K, int ng,
-                             int ngpad, int kpad, const unsigned int* __restrict__ maxbits, int bf16,
+__global__ void split_kernel(const float2* __restrict__ M, const double* __restrict__ w, long long p0, long long K,
+                             int ng, int ngpad, int kpad, const unsigned int* __restrict__ maxbits, int bf16,
                              H* __restrict__ planes) {
   __shared__ float2 t[32][33];
-  const int p0 = blockIdx.x * 32, g0 = blockIdx.y * 32;
+  const long long pc0 = (long long)blockIdx.x * 32;
+  const int g0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   const float sc = ldexpf(1.f, scale_exp(maxbits, bf16));
   for (int r = ty; r < 32; r += 8) {
-    const long long p = p0 + r;
+    const long long p = pc0 + r;   // pair inside the chunk
     const int g = g0 + tx;
     float2 v = make_float2(0.f, 0.f);
     if (p < K && g < ng) {
-      v = M[p * ng + g];
-      const float s = (float)sqrt(fabs(w[p])) * sc;
+      v = M[(p0 + p) * ng + g];
+      const float s = (float)sqrt(fabs(w[p0 + p])) * sc;
       v.x *= s;
       v.y *= s;
     }
@@ -355,7 +357,7 @@ __global__ void split_kernel(const float2* __restrict__ M, const double* __restr
   const size_t plane = (size_t)ngpad * kpad;
   for (int r = ty; r < 32; r += 8) {
     const int g = g0 + r;
-    const int p = p0 + tx;
+    const long long p = pc0 + tx;
     const float2 v = t[tx][r];
     H rh, ih, rl, il;
     if constexpr (sizeof(H) == 2 && std::is_same<H, __half>::value) {
@@ -435,6 +437,11 @@ constexpr int kStages = 3;
 constexpr int kSegPairsDefault = 512;
 }  // namespace
 
+// Bound of the FP32 segment workspace and of the operand planes of one chunk
+// of pairs; larger calls are processed chunk by chunk, each chunk's FP64 sum
+// added into chi.
+constexpr size_t kChunkBytes = size_t(1) << 30;
+
 int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double* w, int nrow, double scale,
                   int accumulate, void* chi, cudaStream_t st) {
   using namespace tc;
@@ -443,30 +450,35 @@ int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const do
   const int bf16 = prec == BGW_PREC_MIX_BF16;
   const int ntr = (ng + BM - 1) / BM, ntc = (ng + kBN - 1) / kBN;
   const int ngpad = std::max(ntr * BM, ntc * kBN);
-  const long long kpad = (K + BK - 1) / BK * BK;
-  if (kpad > 0x7fffffffLL / 1) return fail(c, BGW_EUNSUPPORTED, "too many pairs for one call");
-  const int nkb = (int)(kpad / BK);
-  const int seg_pairs = c->chi_segment_pairs > 0 ? c->chi_segment_pairs : kSegPairsDefault;
-  const int kb_per_seg = std::max(1, seg_pairs / BK);
-  const int nseg = (nkb + kb_per_seg - 1) / kb_per_seg;
+  const int seg_pairs_opt = c->chi_segment_pairs > 0 ? c->chi_segment_pairs : kSegPairsDefault;
+  const int kb_per_seg = std::max(1, seg_pairs_opt / BK);
+  const long long seg_pairs = (long long)kb_per_seg * BK;
   std::vector<int2> tl;
   for (int I = 0; I < ntr; ++I)
     for (int J = 0; J < ntc; ++J)
       if (J * kBN <= I * BM + BM - 1) tl.push_back(make_int2(I, J));
   const int ntiles = (int)tl.size();
+  const size_t seg_bytes = (size_t)ntiles * 2 * BM * kBN * sizeof(float);
+  long long segs_per_chunk = std::max<long long>(1, (long long)(kChunkBytes / seg_bytes));
+  segs_per_chunk = std::min<long long>(segs_per_chunk,
+                                       std::max<long long>(1, (long long)(kChunkBytes / (8ull * ngpad * seg_pairs))));
+  long long kchunk = std::min<long long>(segs_per_chunk * seg_pairs, (K + BK - 1) / BK * BK);
+  if (c->chi_chunk_pairs > 0) kchunk = std::max<long long>(BK, (long long)c->chi_chunk_pairs / BK * BK);
+  const long long kcpad = (kchunk + BK - 1) / BK * BK;
   const void* d_tiles;
   if ((rc = upload_cached(c, tl.data(), tl.size() * sizeof(int2), st, &d_tiles)) != BGW_OK) return rc;
   Scratch planes, work, mx;
   planes.pool = work.pool = mx.pool = &c->pool;
-  const size_t plane_bytes = (size_t)4 * ngpad * kpad * 2;
-  const size_t work_bytes = (size_t)nseg * ntiles * 2 * BM * kBN * sizeof(float);
+  const long long nseg_max = (kcpad / BK + kb_per_seg - 1) / kb_per_seg;
+  const size_t plane_bytes = (size_t)4 * ngpad * kcpad * 2;
+  const size_t work_bytes = (size_t)nseg_max * seg_bytes;
   if ((rc = c->pool.alloc(plane_bytes, &planes.ptr)) != BGW_OK || (rc = c->pool.alloc(work_bytes, &work.ptr)) != BGW_OK ||
       (rc = c->pool.alloc(sizeof(unsigned int), &mx.ptr)) != BGW_OK)
     return fail(c, rc, "bgw_chi_sum (mixed): scratch allocation failed (planes %zu B, workspace %zu B)", plane_bytes,
                 work_bytes);
   CUtensorMap tmap;
-  cuuint64_t gdim[2] = {(cuuint64_t)kpad, (cuuint64_t)4 * ngpad};
-  cuuint64_t gstride[1] = {(cuuint64_t)kpad * 2};
+  cuuint64_t gdim[2] = {(cuuint64_t)kcpad, (cuuint64_t)4 * ngpad};
+  cuuint64_t gstride[1] = {(cuuint64_t)kcpad * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
   cuuint32_t estr[2] = {1, 1};
   // One map serves both operands: the B box has kBN rows; with kBN == BM the
@@ -488,30 +500,43 @@ int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const do
       const long long n = K * ng;
       const unsigned mb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8);
       maxabs_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wf, K, ng, mx.as<unsigned int>());
-      dim3 sg((unsigned)(kpad / 32), (unsigned)(ngpad / 32));
-      if (bf16)
-        split_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, K, ng, ngpad,
-                                                                (int)kpad, mx.as<unsigned int>(), 1,
-                                                                planes.as<__nv_bfloat16>());
-      else
-        split_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, K, ng, ngpad, (int)kpad,
-                                                         mx.as<unsigned int>(), 0, planes.as<__half>());
+      c->launches += 1;
     }
-    {
-      TimedScope ts(c, kTChiTc, st);
-      chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
-          tmap, ngpad, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
-          c->d_status);
+    for (long long p0 = 0; p0 < K; p0 += kchunk) {
+      const long long kc = std::min(kchunk, K - p0);
+      const long long kpad = (kc + BK - 1) / BK * BK;
+      const int nkb = (int)(kpad / BK);
+      const int nseg = (nkb + kb_per_seg - 1) / kb_per_seg;
+      {
+        TimedScope ts(c, kTChiSplit, st);
+        dim3 sg((unsigned)(kpad / 32), (unsigned)(ngpad / 32));
+        // rows of the planes are kcpad long (the tensor map's stride); a
+        // shorter last chunk fills the first kpad of each row, and the GEMM
+        // reads no further than nkb = kpad / BK k-blocks
+        if (bf16)
+          split_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, p0, kc, ng,
+                                                                  ngpad, (int)kcpad, mx.as<unsigned int>(), 1,
+                                                                  planes.as<__nv_bfloat16>());
+        else
+          split_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, p0, kc, ng, ngpad,
+                                                           (int)kcpad, mx.as<unsigned int>(), 0, planes.as<__half>());
+      }
+      {
+        TimedScope ts(c, kTChiTc, st);
+        chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
+            tmap, ngpad, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
+            c->d_status);
+      }
+      {
+        TimedScope ts(c, kTChiReduce, st);
+        const long long ne = (long long)ntiles * BM * kBN;
+        reduce_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+            work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(),
+            bf16, (accumulate || p0 > 0) ? 1 : 0, static_cast<double2*>(chi) + (size_t)f * ng * ng);
+      }
+      BGW_CUDA(c, cudaGetLastError());
+      c->launches += 3;
     }
-    {
-      TimedScope ts(c, kTChiReduce, st);
-      const long long ne = (long long)ntiles * BM * kBN;
-      reduce_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-          work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(), bf16,
-          accumulate, static_cast<double2*>(chi) + (size_t)f * ng * ng);
-    }
-    BGW_CUDA(c, cudaGetLastError());
-    c->launches += 4;
   }
   return BGW_OK;
 }

@@ -105,6 +105,25 @@ def test_mixed_segment_option(ctx, seg):
     assert e_chi <= 1e-4 and e_inv <= 1e-5
 
 
+@pytest.mark.parametrize("chunk", [1000, 3000])
+def test_mixed_pair_chunks(ctx, chunk):
+    # K = 5400 pairs summed in chunks of 992 / 2976 pairs (ragged last chunk)
+    from paper_1111_4429_gb300 import bgw
+    s = synth.make_system("k", a=14.0, fft=24, ecut_wfn=8.0, ecut_eps=2.0, nv=6, nc=900, seed=57)
+    r = oracle.solve(s)
+    ctx.set_option(bgw.BGW_OPT_CHI_CHUNK_PAIRS, chunk)
+    try:
+        chi, inv = _run(ctx, s, 1, omega=np.array([0.0, 0.5]))
+    finally:
+        ctx.set_option(bgw.BGW_OPT_CHI_CHUNK_PAIRS, 0)
+    m = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    v = oracle.coulomb(s.bvec, s.q_frac, s.geps)
+    for f, w in enumerate([0.0, 0.5]):
+        x = oracle.chi(m, oracle.chi_weights(s.ev, s.ec, w), s.omega)
+        assert _rel(chi[f], x) <= 1e-5
+        assert _rel(inv[f], oracle.epsinv_sym(x, v)[1]) <= 1e-6
+
+
 def test_mixed_c1_full_size_vs_oracle(ctx):
     """c1 at full size (N_G = 2120, K = 25,600) in mixed precision against the
     full FP64 oracle solve."""
