@@ -266,6 +266,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
+    batch = run_batch_c3(ctx, prec) if (ws == 1 and not args.skip_extra) else None
+    serve = run_serve_c4(prec) if (ws == 1 and not args.skip_extra) else None
+
     out = {
         "metric": METRIC,
         "value": ws * args.steps / t_total,
@@ -288,6 +291,8 @@ def run_ours(args):
         "roofline": roof,
         "chi_tc": chi_tc,
         **comp,
+        "batch_c3": batch,
+        "serve_c4": serve,
         "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(s.cv.nbytes + s.cc.nbytes),
                 "d2h_bytes_per_step": int(invh.numel() * 16)},
         "gpu_launches": int(launches),
@@ -301,6 +306,98 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def run_batch_c3(ctx, prec, steps=2):
+    """8 q-points of the c1 cell (q = 0.05 j, j = 1..8: uneven epsilon spheres)
+    x 12 imaginary frequencies on a Gauss-Legendre grid over [0, 2] Ha, through
+    bgw_epsilon_batch on a side stream: the first call runs directly and
+    captures a CUDA graph, the timed calls replay it (96 solves per step)."""
+    import torch
+    from paper_1111_4429_gb300 import bgw, synth
+    systems = synth.batched_q_systems(8)
+    om = synth.gauss_legendre_frequencies(12)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        cvs = [torch.from_numpy(s.cv).cuda() for s in systems]
+        ccs = [torch.from_numpy(s.cc).cuda() for s in systems]
+        outs = [torch.empty((12, s.ng, s.ng), dtype=torch.complex128, device="cuda") for s in systems]
+        ctx.epsilon_batch(systems, cvs, ccs, om, prec, outs, stream=st)     # direct run + capture
+        st.synchronize()
+        l0 = ctx.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            ctx.epsilon_batch(systems, cvs, ccs, om, prec, outs, stream=st)
+        e1.record(st)
+        st.synchronize()
+        graph_launches = ctx.launch_count() - l0
+    ms = e0.elapsed_time(e1) / steps
+    # error of two (q, omega) results against the plain FP64 path
+    s0 = systems[0]
+    ref = torch.empty((2, s0.ng, s0.ng), dtype=torch.complex128, device="cuda")
+    ctx.epsilon(bgw.system_cell(s0), s0.gv, cvs[0], s0.ev, s0.gc, ccs[0], s0.ec, s0.geps, om[[0, 11]],
+                bgw.BGW_PREC_FP64, 0, None, ref)
+    ctx.sync()
+    err = max(float(torch.linalg.matrix_norm(outs[0][f] - ref[i]) / torch.linalg.matrix_norm(ref[i]))
+              for i, f in enumerate((0, 11)))
+    chi_flops = sum(12 * 8.0 * s.ng * s.ng * s.npairs for s in systems)
+    return {"workload": "c1 cell, q = (0.05 j, 0, 0) for j = 1..8, 12 Gauss-Legendre iw in [0, 2] Ha, "
+                        "N_G " + "/".join(str(s.ng) for s in systems),
+            "solves_per_s": 96.0 / (ms / 1e3), "ms_per_batch": ms,
+            "chi_zgemm_eq_tflops_over_batch": chi_flops / (ms / 1e3) / 1e12,
+            "graph_launches_per_batch": graph_launches / steps,
+            "epsinv_rel_err_vs_plain_fp64_gpu": err}
+
+
+def run_serve_c4(prec, nreq=24, seed=1004):
+    """A seeded sample of the served stream (cell scale s in {1,2,3}, eps
+    cutoff in {3,4,6} Ry, N_v = 4 s^3, N_c ~ U[50,1500] clamped to the
+    conduction plane waves at 10 Ry): a calibration pass submits all requests
+    at once (capacity), then the same requests arrive as a Poisson stream at
+    0.7 x capacity; p50/p99 latency (submit -> eps~^-1 on the host)."""
+    import torch
+    from paper_1111_4429_gb300 import bgw, synth
+    reqs = synth.serve_requests(200, seed)[:nreq]
+    systems = [synth.request_system(r) for r in reqs]
+    outs = [torch.empty((s.ng, s.ng), dtype=torch.complex128).pin_memory() for s in systems]
+    srv = bgw.Server(0, hbm_budget_bytes=120 << 30, max_slots=4, prec=prec)
+    # warm the slots' plans and tuning with one pass, then calibrate
+    t = [srv.submit(s, o) for s, o in zip(systems, outs)]
+    for x in t:
+        srv.poll(x, timeout_ms=600000)
+    t0 = time.perf_counter()
+    t = [srv.submit(s, o) for s, o in zip(systems, outs)]
+    res = [srv.poll(x, timeout_ms=600000) for x in t]
+    cap = len(systems) / (time.perf_counter() - t0)
+    lam = 0.7 * cap
+    gen = np.random.Generator(np.random.PCG64(seed + 1))
+    gaps = gen.exponential(1.0 / lam, len(systems))
+    t0 = time.perf_counter()
+    tickets = []
+    for s, o, g in zip(systems, outs, gaps):
+        time.sleep(g)
+        tickets.append(srv.submit(s, o))
+    res = [srv.poll(x, timeout_ms=600000) for x in tickets]
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([r["latency_ms"] for r in res])
+    ok = all(r["status"] == 0 for r in res)
+    # the smallest request served in the mix against the plain FP64 path alone
+    k = int(np.argmin([s.ng * s.npairs for s in systems]))
+    ctx = bgw.Context(0)
+    ref = np.zeros((1, systems[k].ng, systems[k].ng), dtype=np.complex128)
+    sk = systems[k]
+    ctx.epsilon(bgw.system_cell(sk), sk.gv, sk.cv, sk.ev, sk.gc, sk.cc, sk.ec, sk.geps, None, bgw.BGW_PREC_FP64, 0,
+                None, ref)
+    err = float(np.linalg.norm(outs[k].numpy() - ref[0]) / np.linalg.norm(ref[0]))
+    ctx.close()
+    return {"workload": f"{len(systems)} requests of the served stream (seed {seed}), Poisson arrivals at 0.7 x "
+                        f"measured capacity, 4 slots, 120 GB budget",
+            "solves_per_s": len(systems) / wall, "capacity_solves_per_s": cap, "arrival_rate_per_s": lam,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "all_ok": ok, "smallest_request_epsinv_rel_err_vs_plain_fp64_gpu": err,
+            "sizes_ng": sorted({s.ng for s in systems})}
 
 
 def _oracle_sample(s, frac_c):
@@ -395,6 +492,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="mix_fp16", choices=["fp64", "mix_fp16", "mix_bf16"])
+    ap.add_argument("--skip-extra", action="store_true", help="skip the batched q x iw and served-stream parts")
     ap.add_argument("--profile-case", action="store_true", help="reduced c1 solve for ncu captures")
     args = ap.parse_args()
     if args.profile_case:
