@@ -120,7 +120,16 @@ int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
  *    in chunks of this many pairs (rounded down to a multiple of 32), each
  *    chunk's FP64 sum added into chi; 0 (default) sizes chunks so that their
  *    operand planes and FP32 workspace stay near 1 GiB each.               */
-enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3, BGW_OPT_CHI_CHUNK_PAIRS = 4 };
+/*  BGW_OPT_INVERSE: how the sweep's trailing updates run.  -1 (default):
+ *    bgw_epsilon, bgw_epsilon_batch and the server use the tensor cores for
+ *    the mixed precisions and FP64 FMA for BGW_PREC_FP64, bgw_epsinv uses
+ *    FP64 FMA; 0: FP64 FMA everywhere; 1: the tensor cores everywhere.  The
+ *    tensor-core update splits P and C into seven 8-bit slices held exactly
+ *    in FP16, accumulates every slice product exactly in FP32 and combines
+ *    them in double-FP32 before the FP64 subtraction: its error is near
+ *    2^-48 of the update's scale (FP64 FMA: 2^-53).                        */
+enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3, BGW_OPT_CHI_CHUNK_PAIRS = 4,
+       BGW_OPT_INVERSE = 5 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
 
 /* With BGW_OPT_TIMING = 1 the context records CUDA events around its main

@@ -28,7 +28,7 @@ EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_s
            "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_epsilon",
            "bgw_epsilon_batch", "bgw_serve_open", "bgw_serve_submit", "bgw_serve_poll", "bgw_serve_cancel",
            "bgw_serve_close")
-BGW_OPT_CHI_SEGMENT_PAIRS, BGW_OPT_TIMING, BGW_OPT_AUTOTUNE, BGW_OPT_CHI_CHUNK_PAIRS = 1, 2, 3, 4
+BGW_OPT_CHI_SEGMENT_PAIRS, BGW_OPT_TIMING, BGW_OPT_AUTOTUNE, BGW_OPT_CHI_CHUNK_PAIRS, BGW_OPT_INVERSE = 1, 2, 3, 4, 5
 
 
 class BgwError(RuntimeError):

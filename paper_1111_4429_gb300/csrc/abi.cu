@@ -134,6 +134,14 @@ int validate_mtxel(Ctx* c, const bgw_cell* cell, int nv, int npw_v, const int32_
   return BGW_OK;
 }
 
+// The mixed precisions invert with the tensor-core trailing update unless
+// BGW_OPT_INVERSE selects otherwise; the plain FP64 path uses FP64 FMA.
+bool use_tc_inverse(Ctx* c, int prec) {
+  if (c->inverse_mode == 0) return false;
+  if (c->inverse_mode == 1) return true;
+  return prec != BGW_PREC_FP64;
+}
+
 int init_device(Ctx* c) {
   if (c->twiddles_ready) return BGW_OK;
   BGW_CUDA(c, mtxel_init_f64());
@@ -236,6 +244,11 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
     c->chi_chunk_pairs = (int)value;
     return BGW_OK;
   }
+  if (option == BGW_OPT_INVERSE) {
+    if (value < -1 || value > 1) return fail(c, BGW_EINVAL, "inverse mode is -1, 0 or 1");
+    c->inverse_mode = (int)value;
+    return BGW_OK;
+  }
   if (option == BGW_OPT_AUTOTUNE) {
     if (value != 0 && value != 1) return fail(c, BGW_EINVAL, "autotune is 0 or 1");
     c->autotune = value == 1;
@@ -336,7 +349,8 @@ int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, con
     bv[m] = &cells[m].bvec[0][0];
     qv[m] = cells[m].q_frac;
   }
-  if ((rc = epsinv_batch_run(c, nmat, ng, bv.data(), qv.data(), dgeps.data(), chi, eps, epsinv, st)) != BGW_OK)
+  if ((rc = epsinv_batch_run(c, nmat, ng, bv.data(), qv.data(), dgeps.data(), chi, eps, epsinv, st,
+                             c->inverse_mode == 1)) != BGW_OK)
     return rc;
   return BGW_OK;
 }
@@ -386,7 +400,7 @@ int run_batch(Ctx* c, int nq, const bgw_problem* pr, int nfreq, const double* de
       invs[f] = static_cast<char*>(epsinv[q]) + f * n2;
     }
     if ((rc = epsinv_batch_run(c, nrow, ngv.data(), bv.data(), qv.data(), gv.data(), chis.data(), nullptr,
-                               invs.data(), st)) != BGW_OK)
+                               invs.data(), st, use_tc_inverse(c, prec))) != BGW_OK)
       return rc;
   }
   return BGW_OK;
@@ -564,7 +578,7 @@ int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
       invs[f] = static_cast<char*>(d_inv) + f * n2;
     }
     if ((rc = epsinv_batch_run(c, nrow, ngv.data(), bv.data(), qv.data(), gv2.data(), chis.data(), nullptr,
-                               invs.data(), st)) != BGW_OK)
+                               invs.data(), st, use_tc_inverse(c, prec))) != BGW_OK)
       return rc;
   }
   if (chi && !chi_dev) BGW_CUDA(c, cudaMemcpyAsync(chi, d_chi, nrow * n2, cudaMemcpyDeviceToHost, st));

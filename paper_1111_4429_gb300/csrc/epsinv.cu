@@ -16,6 +16,9 @@
 // v^1/2 is Hermitian positive definite (chi <= 0), for which elimination
 // without pivoting is backward stable; a zero or non-finite pivot is
 // recorded in the device status word.
+#include <memory>
+#include <vector>
+
 #include "runtime.h"
 
 namespace bgw {
@@ -416,9 +419,10 @@ __global__ void sw_finish_kernel(const __grid_constant__ SweepBatch b) {
 // eps~ formation for every matrix of the batch, then the batched sweep.
 int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec, const double* const* qf,
                      const int32_t* const* d_geps, const void* const* chi, void* const* eps, void* const* epsinv,
-                     cudaStream_t st) {
-  for (int m0 = 0; m0 < nmat; m0 += kSweepBatch) {
-    const int nb = std::min(kSweepBatch, nmat - m0);
+                     cudaStream_t st, bool tc_update) {
+  const int group = tc_update ? 96 : kSweepBatch;
+  for (int m0 = 0; m0 < nmat; m0 += group) {
+    const int nb = std::min(group, nmat - m0);
     size_t pan = 0;
     int ngmax = 0;
     for (int m = m0; m < m0 + nb; ++m) {
@@ -465,12 +469,31 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
     const long long ntl = (long long)nt * (nt + 1) / 2;
     const size_t upd_smem = sizeof(double2) * 2 * TU * (NB + 1);
     BGW_CUDA(c, cudaFuncSetAttribute(sw_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
+    std::unique_ptr<OzPlan, void (*)(OzPlan*)> oz(nullptr, oz_plan_delete);
+    if (tc_update) {
+      oz.reset(oz_plan_new());
+      std::vector<int> ngs(nb);
+      std::vector<double2*> As(nb);
+      std::vector<const double2*> Cs(nb), Ps(nb);
+      for (int k = 0; k < nb; ++k) {
+        ngs[k] = sb.m[k].ng;
+        As[k] = sb.m[k].A;
+        Cs[k] = sb.m[k].C;
+        Ps[k] = sb.m[k].P;
+      }
+      if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), oz.get())) != BGW_OK) return rc;
+    }
     for (int k0 = 0; k0 < ngmax; k0 += NB) {
       sw_diag_kernel<<<nb, dim3(NB, NB), 0, st>>>(sb, k0, c->d_status);
       sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, st>>>(sb, k0);
-      sw_update_kernel<<<dim3((unsigned)ntl, nb), 256, upd_smem, st>>>(sb, k0);
+      if (tc_update) {
+        if ((rc = oz_update(c, oz.get(), k0, ngmax, st)) != BGW_OK) return rc;
+        c->launches += 2;
+      } else {
+        sw_update_kernel<<<dim3((unsigned)ntl, nb), 256, upd_smem, st>>>(sb, k0);
+        c->launches += 3;
+      }
       BGW_CUDA(c, cudaGetLastError());
-      c->launches += 3;
     }
     const long long nlow = (long long)ngmax * (ngmax + 1) / 2;
     sw_finish_kernel<<<dim3((unsigned)std::min<long long>((nlow + 255) / 256, 152LL * 16), nb), 256, 0, st>>>(sb);

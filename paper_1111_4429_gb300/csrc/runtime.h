@@ -109,6 +109,7 @@ struct Ctx {
   std::unordered_map<uint64_t, BatchGraph> graphs;
   std::map<std::tuple<int, int, int, int>, int> tuned_ppb;  // (n, prec, nys, ncol) -> pairs per CTA
   bool autotune = true;
+  int inverse_mode = -1;     // -1: tensor-core update for the mixed precisions; 0: FP64 FMA; 1: tensor cores
   Pool pool;
   std::string err;
   int* d_status = nullptr;   // device status word
@@ -191,9 +192,19 @@ int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const doubl
             const double* d_ec, int nfreq, const double* d_omega, double scale, int accumulate,
             void* chi, cudaStream_t st);
 // eps~ and its inverse for nmat matrices (per-matrix size, cell and q).
+// tc_update: the sweep's trailing updates run on the tensor cores with
+// FP64-level accuracy (sweep_tc.cu) instead of FP64 FMA.
 int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec, const double* const* qf,
                      const int32_t* const* d_geps, const void* const* chi, void* const* eps, void* const* epsinv,
-                     cudaStream_t st);
+                     cudaStream_t st, bool tc_update);
+
+// Tensor-core trailing update of the sweep (sweep_tc.cu).
+struct OzPlan;
+OzPlan* oz_plan_new();
+void oz_plan_delete(OzPlan* p);
+int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
+               OzPlan* plan);
+int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, cudaStream_t st);
 
 }  // namespace bgw
 

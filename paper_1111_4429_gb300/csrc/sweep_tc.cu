@@ -1,0 +1,408 @@
+// Trailing update of the Hermitian sweep on the tensor cores with FP64-level
+// accuracy (error-free splitting of the operands, the Ozaki scheme).
+//
+// Each sweep step subtracts the rank-kb product P C^H from the lower triangle
+// (kb <= 32).  With u_i = [Re P_i, Im P_i] and v_j = [Re C_j, Im C_j] (64 real
+// values each), Re(P_i C_j^H) = u_i . v_j and
+// Im(P_i C_j^H) = u_i[32:64] . v_j[0:32] - u_i[0:32] . v_j[32:64].
+// Every row is scaled by a power of two sigma_i (>= its largest entry) and cut
+// into S slices of 8 bits: u_i = sigma_i sum_a 2^{-8(a+1)} h_a, with integer
+// h_a (|h_0| <= 256, |h_a| <= 128 for a >= 1) held exactly in FP16.  The
+// slice products h_a . g_b are integers whose sums over 64 terms and over
+// the pairs of one level L = a + b stay below 2^24, so the tensor cores'
+// FP32 accumulation is exact: one FP32 accumulator per level (Re and Im) in
+// tensor memory.  The levels a + b < S are kept; they are combined in
+// double-FP32 (two-sum) and the result, scaled by sigma_i tau_j 2^-16, is
+// subtracted from A in FP64.  The dropped levels and the double-FP32 sum
+// bound the error near 2^-48 of |u_i| |v_j| 64.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "runtime.h"
+
+namespace bgw {
+
+namespace oz {
+
+constexpr int S = 7;             // slices per value
+constexpr int BETA = 8;          // bits per slice
+constexpr int KR = 64;           // real inner length (32 complex)
+constexpr int BM = 128;          // tile rows (i)
+constexpr int BN = 32;           // tile cols (j)
+constexpr int NB = 32;           // sweep block width
+constexpr int kThreads = 128;
+constexpr int kUTile = BM * KR * 2;    // 16 KiB
+constexpr int kVTile = BN * KR * 2;    // 4 KiB
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer() - t0 > kWaitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+// K-major operand, 128-byte swizzle: rows of 128 bytes, 8-row groups 1024
+// bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;  // SWIZZLE_128B
+  return d;
+}
+__host__ __device__ constexpr uint32_t idesc(bool neg_a) {
+  return (1u << 4) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+// Per-matrix description of one batched sweep (device pointers).
+struct OzMat {
+  double2* A;
+  const double2* C;   // [ng][NB]
+  const double2* P;   // [ng][NB]
+  int ng;
+  int row_off;        // first slice row of this matrix (multiple of BM)
+};
+constexpr int kBatch = 96;
+struct OzBatch {
+  int n;
+  OzMat m[kBatch];
+};
+
+// Slices of P (z = 0) and C (z = 1): one warp per row, lane k holds the real
+// parts of column k and the imaginary parts (k + 32).  Rows inside the swept
+// block and padding rows get zero slices.
+__global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBatch b, int k0, int rows_total,
+                                                    __half* __restrict__ U, __half* __restrict__ V,
+                                                    double* __restrict__ sig, double* __restrict__ tau) {
+  const OzMat& M = b.m[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  const int ngpad = (M.ng + BM - 1) / BM * BM;
+  if (i >= ngpad) return;
+  const int kb = min(NB, M.ng - k0);
+  const bool live = k0 < M.ng && i < M.ng && (i < k0 || i >= k0 + kb);
+  const double2* src = blockIdx.z == 0 ? M.P : M.C;
+  double re = 0.0, im = 0.0;
+  if (live && lane < kb) {
+    const double2 v = src[(size_t)i * NB + lane];
+    re = v.x;
+    im = v.y;
+  }
+  double m = fmax(fabs(re), fabs(im));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |x| < 1 after scaling by 2^-e
+  const double inv = ldexp(1.0, -e);
+  double xr = re * inv, xi = im * inv;
+  const size_t row = (size_t)M.row_off + i;
+  __half* out = blockIdx.z == 0 ? U : V;
+  for (int a = 0; a < S; ++a) {
+    const double sc = ldexp(1.0, BETA * (a + 1));
+    const double hr = rint(xr * sc), hi = rint(xi * sc);
+    xr -= hr / sc;
+    xi -= hi / sc;
+    __half* o = out + ((size_t)a * rows_total + row) * KR;
+    o[lane] = __double2half((double)hr);
+    o[lane + 32] = __double2half((double)hi);
+  }
+  if (lane == 0) (blockIdx.z == 0 ? sig : tau)[row] = ldexp(1.0, e);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// One CTA: the 128 x 32 tile (I, J) of the lower triangle of one matrix.
+__global__ void __launch_bounds__(kThreads, 1)
+    update_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
+                  const __grid_constant__ OzBatch b, int k0, int rows_total, const double* __restrict__ sig,
+                  const double* __restrict__ tau, int* __restrict__ status) {
+  const OzMat& M = b.m[blockIdx.y];
+  const int ng = M.ng;
+  if (k0 >= ng) return;
+  const int kb = min(NB, ng - k0);
+  // tile decode: row tile I holds column tiles J = 0 .. min(4I+3, nJ-1)
+  const int nI = (ng + BM - 1) / BM, nJ = (ng + BN - 1) / BN;
+  int t = blockIdx.x, I = 0;
+  for (; I < nI; ++I) {
+    const int cI = min(4 * I + 4, nJ);
+    if (t < cI) break;
+    t -= cI;
+  }
+  if (I >= nI) return;
+  const int J = t;
+  const int i0 = I * BM, j0 = J * BN;
+  if (i0 >= k0 && min(i0 + BM, ng) <= k0 + kb) return;
+  if (j0 >= k0 && min(j0 + BN, ng) <= k0 + kb) return;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* us = smem;                  // S x 16 KiB
+  unsigned char* vs = smem + S * kUTile;     // S x 4 KiB
+  uint64_t* full = reinterpret_cast<uint64_t*>(vs + S * kVTile);
+  uint64_t* done = full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(full)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(full)),
+                 "r"((uint32_t)(S * (kUTile + kVTile)))
+                 : "memory");
+    for (int a = 0; a < S; ++a) {
+      tma_load_2d(us + a * kUTile, &umap, full, 0, a * rows_total + M.row_off + i0);
+      tma_load_2d(vs + a * kVTile, &vmap, full, 0, a * rows_total + M.row_off + j0);
+    }
+    // the copies must land before this CTA may exit, whatever happens next
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(full, 0) && globaltimer() - t0 < kWaitNs) {
+    }
+  } else if (warp == 1 && lane == 0) {
+    if (!mbar_wait(full, 0)) {
+      ok = false;
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ub = smem_u32(us), vb = smem_u32(vs);
+      const uint32_t id = idesc(false), idn = idesc(true);
+      bool first[S];
+#pragma unroll
+      for (int L = 0; L < S; ++L) first[L] = true;
+#pragma unroll 1
+      for (int a = 0; a < S; ++a) {
+#pragma unroll 1
+        for (int bb = 0; bb + a < S; ++bb) {
+          const int L = a + bb;
+          const uint32_t dre = tmem + L * 2 * BN, dim = dre + BN;
+          const uint32_t ua = ub + a * kUTile, vb2 = vb + bb * kVTile;
+          // Re: u . v over the 64 real components (4 steps of 16)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) mma(dre, sdesc(ua + 32 * k), sdesc(vb2 + 32 * k), id, (first[L] && k == 0) ? 0u : 1u);
+          // Im: u[32:64] . v[0:32] - u[0:32] . v[32:64]
+          mma(dim, sdesc(ua + 64), sdesc(vb2 + 0), id, first[L] ? 0u : 1u);
+          mma(dim, sdesc(ua + 96), sdesc(vb2 + 32), id, 1u);
+          mma(dim, sdesc(ua + 0), sdesc(vb2 + 64), idn, 1u);
+          mma(dim, sdesc(ua + 32), sdesc(vb2 + 96), idn, 1u);
+          first[L] = false;
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(done))
+                   : "memory");
+    }
+  }
+  __syncwarp();
+  bool have = mbar_wait(done, 0);
+  have = __all_sync(0xffffffffu, have) != 0;
+  if (!have && threadIdx.x == 0) atomicExch(status, (int)kDevTimeout);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncwarp();
+  if (have && ok) {
+    const int r = warp * 32 + lane;
+    const int i = i0 + r;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const bool row_ok = i < ng && !(i >= k0 && i < k0 + kb);
+    const double si = row_ok ? sig[M.row_off + i] : 0.0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float hr[16], lr[16], hm[16], lm[16];
+#pragma unroll 1
+      for (int L = 0; L < S; ++L) {
+        uint32_t x[16], y[16];
+        tmem_ld16(tmem + lane_off + L * 2 * BN + c0, x);
+        tmem_ld16(tmem + lane_off + L * 2 * BN + BN + c0, y);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const float w = ldexpf(1.f, -BETA * L);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float vr = __fmul_rn(__uint_as_float(x[q]), w), vi = __fmul_rn(__uint_as_float(y[q]), w);
+          if (L == 0) {
+            hr[q] = vr;
+            lr[q] = 0.f;
+            hm[q] = vi;
+            lm[q] = 0.f;
+          } else {
+            float s, e;
+            two_sum(hr[q], vr, s, e);
+            hr[q] = s;
+            lr[q] = __fadd_rn(lr[q], e);
+            two_sum(hm[q], vi, s, e);
+            hm[q] = s;
+            lm[q] = __fadd_rn(lm[q], e);
+          }
+        }
+      }
+      if (row_ok) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int j = j0 + c0 + q;
+          if (j > i || j >= ng || (j >= k0 && j < k0 + kb)) continue;
+          const double f = si * tau[M.row_off + j] * (1.0 / 65536.0);
+          double2* dst = M.A + (size_t)i * ng + j;
+          const double2 v = *dst;
+          *dst = make_double2(v.x - f * ((double)hr[q] + (double)lr[q]), v.y - f * ((double)hm[q] + (double)lm[q]));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+}  // namespace oz
+
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode_oz = nullptr;
+}  // namespace
+
+// State of one batched sweep that uses the tensor-core update.
+struct OzPlan {
+  int nmat = 0;
+  int rows_total = 0;
+  int max_tiles = 0;
+  oz::OzBatch batch;
+  CUtensorMap umap, vmap;
+  Scratch U, V, sig, tau;
+};
+
+int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
+               OzPlan* plan) {
+  using namespace oz;
+  if (nmat > kBatch) return fail(c, BGW_EUNSUPPORTED, "tensor-core inverse: at most %d matrices per batch", kBatch);
+  if (!g_encode_oz) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return fail(c, BGW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    g_encode_oz = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  plan->nmat = nmat;
+  plan->batch.n = nmat;
+  int rows = 0, tiles = 0;
+  for (int m = 0; m < nmat; ++m) {
+    plan->batch.m[m].A = A[m];
+    plan->batch.m[m].C = C[m];
+    plan->batch.m[m].P = P[m];
+    plan->batch.m[m].ng = ng[m];
+    plan->batch.m[m].row_off = rows;
+    rows += (ng[m] + BM - 1) / BM * BM;
+    const int nI = (ng[m] + BM - 1) / BM, nJ = (ng[m] + BN - 1) / BN;
+    int t = 0;
+    for (int I = 0; I < nI; ++I) t += std::min(4 * I + 4, nJ);
+    tiles = std::max(tiles, t);
+  }
+  plan->rows_total = rows;
+  plan->max_tiles = tiles;
+  plan->U.pool = plan->V.pool = plan->sig.pool = plan->tau.pool = &c->pool;
+  int rc;
+  const size_t sb = (size_t)S * rows * KR * sizeof(__half);
+  if ((rc = c->pool.alloc(sb, &plan->U.ptr)) != BGW_OK || (rc = c->pool.alloc(sb, &plan->V.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)rows * sizeof(double), &plan->sig.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)rows * sizeof(double), &plan->tau.ptr)) != BGW_OK)
+    return fail(c, rc, "tensor-core inverse: slice buffers (%zu B each) could not be allocated", sb);
+  cuuint64_t gdim[2] = {(cuuint64_t)KR, (cuuint64_t)S * rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)KR * sizeof(__half)};
+  cuuint32_t estr[2] = {1, 1};
+  cuuint32_t ubox[2] = {(cuuint32_t)KR, (cuuint32_t)BM};
+  cuuint32_t vbox[2] = {(cuuint32_t)KR, (cuuint32_t)BN};
+  if (g_encode_oz(&plan->umap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, plan->U.ptr, gdim, gstride, ubox, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      g_encode_oz(&plan->vmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, plan->V.ptr, gdim, gstride, vbox, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return fail(c, BGW_ECUDA, "tensor-core inverse: tensor map encoding failed");
+  const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
+  BGW_CUDA(c, cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return BGW_OK;
+}
+
+// One sweep step's trailing update for every matrix of the plan.
+int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, cudaStream_t st) {
+  using namespace oz;
+  const int rpad = (ngmax + BM - 1) / BM * BM;
+  slice_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total,
+                                                              plan->U.as<__half>(), plan->V.as<__half>(),
+                                                              plan->sig.as<double>(), plan->tau.as<double>());
+  const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
+  update_kernel<<<dim3(plan->max_tiles, plan->nmat), kThreads, smem, st>>>(
+      plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, plan->sig.as<double>(), plan->tau.as<double>(),
+      c->d_status);
+  BGW_CUDA(c, cudaGetLastError());
+  return BGW_OK;
+}
+
+OzPlan* oz_plan_new() { return new OzPlan(); }
+void oz_plan_delete(OzPlan* p) { delete p; }
+
+}  // namespace bgw

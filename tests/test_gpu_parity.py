@@ -261,3 +261,32 @@ def test_c1_full_size_sampled_parity(ctx):
     e = torch.eye(s.ng, dtype=torch.complex128, device="cuda") - v[:, None] * chi[0] * v[None, :]
     res = torch.linalg.matrix_norm(e @ inv[0] - torch.eye(s.ng, dtype=torch.complex128, device="cuda"))
     assert float(res) / math.sqrt(s.ng) <= 1e-13
+
+
+# ------------------------------------------------------------------ tensor-core inverse
+
+@pytest.mark.parametrize("which", ["c0", "ragged", "two"])
+def test_epsinv_tensor_core_update_vs_oracle(ctx, which):
+    """The sweep with its trailing updates on the tensor cores (FP16 slices,
+    exact FP32 level sums, double-FP32 combination) keeps FP64-level accuracy:
+    same 1e-12 bar as the FP64 FMA sweep, on the oracle's chi."""
+    from paper_1111_4429_gb300 import bgw
+    if which == "c0":
+        systems = [synth.config_system("c0")]
+    elif which == "ragged":
+        systems = [synth.make_system("r", a=14.0, fft=24, ecut_wfn=6.0, ecut_eps=2.5, nv=5, nc=37, seed=78)]
+    else:  # two matrices of different size in one batch, several 128-row tiles
+        systems = [synth.make_system("r", a=20.52, fft=40, ecut_wfn=8.0, ecut_eps=3.0, nv=4, nc=90, seed=88),
+                   synth.make_system("s", a=17.0, fft=40, ecut_wfn=8.0, ecut_eps=3.5, nv=4, nc=90, seed=89)]
+    refs, chis = [], []
+    for s in systems:
+        r = oracle.solve(s)
+        refs.append(r)
+        chis.append(_dev(r["chi"]))
+    ctx.set_option(bgw.BGW_OPT_INVERSE, 1)
+    try:
+        eps, inv = _epsinv(ctx, systems, chis)
+    finally:
+        ctx.set_option(bgw.BGW_OPT_INVERSE, -1)
+    for r, i in zip(refs, inv):
+        assert _rel(i, r["epsinv"]) <= TOL64
