@@ -225,59 +225,74 @@ struct SweepBatch {
   SweepMat m[kSweepBatch];
 };
 
+// Sweep of the diagonal block D (Hermitian positive definite) on its lower
+// triangle, the same map as the big sweep: after pivot s every lower element
+// outside row/column s loses col_i conj(col_j) / d, the pivot column is
+// divided by d and the pivot becomes -1/d.  The result is -D^-1; Dinv gets
+// D^-1 (both triangles) and A_KK gets -D^-1 (lower).  The pivot column
+// scaled by 1/d is formed once per pivot by 32 threads, so each lower
+// element costs one complex multiply-subtract in FP64.
 __global__ void __launch_bounds__(NB * NB) sw_diag_kernel(const __grid_constant__ SweepBatch b, int k0,
                                                           int* __restrict__ status) {
-  __shared__ double2 D[NB][NB + 1];
-  __shared__ double2 recip;  // 1/pivot, computed once per step (FP64 division is costly on one SM)
+  __shared__ double2 L[NB][NB + 1];
+  __shared__ double2 col[NB];   // column s of the current matrix
+  __shared__ double2 colr[NB];  // conj(col) / d
+  __shared__ double rpiv;
   const SweepMat& M = b.m[blockIdx.x];
   const int ng = M.ng;
   if (k0 >= ng) return;
   const int kb = min(NB, ng - k0);
   double2* A = M.A;
   const int i = threadIdx.y, j = threadIdx.x;
-  const bool in = i < kb && j < kb;
-  double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
-  if (in) {
-    if (i >= j) {
-      v = A[(size_t)(k0 + i) * ng + k0 + j];
-    } else {
-      const double2 t = A[(size_t)(k0 + j) * ng + k0 + i];
-      v = make_double2(t.x, -t.y);
-    }
-  }
-  D[i][j] = v;
+  const bool low = i < kb && j < kb && i >= j;
+  if (low) L[i][j] = A[(size_t)(k0 + i) * ng + k0 + j];
   for (int s = 0; s < kb; ++s) {
     __syncthreads();
-    if (i == 0 && j == 0) {
-      const double2 piv = D[s][s];
-      const double m2 = piv.x * piv.x + piv.y * piv.y;
-      if (!(m2 > 0.0) || !isfinite(m2)) {
-        atomicExch(status, (int)kDevZeroPivot);
-        recip = make_double2(0.0, 0.0);
+    if (i == 0 && j < kb) {
+      double2 cv;
+      if (j > s) {
+        cv = L[j][s];
+      } else if (j < s) {
+        const double2 t = L[s][j];
+        cv = make_double2(t.x, -t.y);
       } else {
-        const double r = 1.0 / m2;
-        recip = make_double2(piv.x * r, -piv.y * r);
+        cv = L[s][s];
       }
+      col[j] = cv;
+      const double d = L[s][s].x;
+      double r;
+      if (!(d > 0.0) || !isfinite(d)) {
+        if (j == 0) atomicExch(status, (int)kDevZeroPivot);
+        r = 0.0;
+      } else {
+        r = 1.0 / d;
+      }
+      colr[j] = make_double2(cv.x * r, -cv.y * r);
+      if (j == s) rpiv = r;
     }
     __syncthreads();
-    const double2 p = recip;
-    const double2 f = D[i][s];
-    const double2 rs = D[s][j];
-    __syncthreads();
-    const double2 rsn = (j == s) ? p : cmul(rs, p);
-    if (i == s) {
-      D[i][j] = rsn;
-    } else {
-      double2 w = (j == s) ? make_double2(0.0, 0.0) : D[i][j];
-      const double2 t = cmul(f, rsn);
-      D[i][j] = make_double2(w.x - t.x, w.y - t.y);
+    if (low) {
+      if (i != s && j != s) {
+        const double2 a = col[i], c = colr[j];
+        double2 v = L[i][j];
+        v.x -= a.x * c.x - a.y * c.y;
+        v.y -= a.x * c.y + a.y * c.x;
+        L[i][j] = v;
+      } else if (i == s && j == s) {
+        L[s][s] = make_double2(-rpiv, 0.0);
+      } else if (j == s) {  // i > s: A_is / d
+        const double2 a = col[i];
+        L[i][s] = make_double2(a.x * rpiv, a.y * rpiv);
+      } else {              // i == s, j < s: A_sj / d = conj(col_j) / d
+        L[s][j] = colr[j];
+      }
     }
   }
   __syncthreads();
-  if (in) {
-    const double2 d = D[i][j];
-    M.Dinv[i * NB + j] = d;
-    if (i >= j) A[(size_t)(k0 + i) * ng + k0 + j] = make_double2(-d.x, -d.y);
+  if (i < kb && j < kb) {
+    const double2 v = (i >= j) ? L[i][j] : make_double2(L[j][i].x, -L[j][i].y);
+    M.Dinv[i * NB + j] = make_double2(-v.x, -v.y);
+    if (i >= j) A[(size_t)(k0 + i) * ng + k0 + j] = v;
   }
 }
 

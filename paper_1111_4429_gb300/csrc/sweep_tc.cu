@@ -12,8 +12,8 @@
 // the pairs of one level L = a + b stay below 2^24, so the tensor cores'
 // FP32 accumulation is exact: one FP32 accumulator per level (Re and Im) in
 // tensor memory.  The levels a + b < S are kept; they are combined in
-// double-FP32 (two-sum) and the result, scaled by sigma_i tau_j 2^-16, is
-// subtracted from A in FP64.  The dropped levels and the double-FP32 sum
+// double-FP32 (two-sum); the pair, scaled by the power of two
+// sigma_i tau_j 2^-16, is subtracted from A in FP64.  The dropped levels and the double-FP32 sum
 // bound the error near 2^-48 of |u_i| |v_j| 64.
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -120,7 +120,7 @@ struct OzBatch {
 // block and padding rows get zero slices.
 __global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBatch b, int k0, int rows_total,
                                                     __half* __restrict__ U, __half* __restrict__ V,
-                                                    double* __restrict__ sig, double* __restrict__ tau) {
+                                                    int* __restrict__ sig, int* __restrict__ tau) {
   const OzMat& M = b.m[blockIdx.y];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 8 + warp;
@@ -139,20 +139,22 @@ __global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBa
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   int e = 0;
   if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |x| < 1 after scaling by 2^-e
-  const double inv = ldexp(1.0, -e);
-  double xr = re * inv, xi = im * inv;
+  // y_a = x 2^{8(a+1)} relative to the row scale: h_a = rint(y_a) and
+  // y_{a+1} = (y_a - h_a) 2^8, both steps exact in FP64 (no division)
+  const double up = 256.0;
+  double xr = ldexp(re, BETA - e), xi = ldexp(im, BETA - e);  // x 2^8
   const size_t row = (size_t)M.row_off + i;
   __half* out = blockIdx.z == 0 ? U : V;
+#pragma unroll
   for (int a = 0; a < S; ++a) {
-    const double sc = ldexp(1.0, BETA * (a + 1));
-    const double hr = rint(xr * sc), hi = rint(xi * sc);
-    xr -= hr / sc;
-    xi -= hi / sc;
+    const double hr = rint(xr), hi = rint(xi);
+    xr = (xr - hr) * up;  // exact: the remainder has fewer than 45 significant bits
+    xi = (xi - hi) * up;
     __half* o = out + ((size_t)a * rows_total + row) * KR;
-    o[lane] = __double2half((double)hr);
-    o[lane + 32] = __double2half((double)hi);
+    o[lane] = __double2half(hr);
+    o[lane + 32] = __double2half(hi);
   }
-  if (lane == 0) (blockIdx.z == 0 ? sig : tau)[row] = ldexp(1.0, e);
+  if (lane == 0) (blockIdx.z == 0 ? sig : tau)[row] = e;
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -164,8 +166,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // One CTA: the 128 x 32 tile (I, J) of the lower triangle of one matrix.
 __global__ void __launch_bounds__(kThreads, 1)
     update_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
-                  const __grid_constant__ OzBatch b, int k0, int rows_total, const double* __restrict__ sig,
-                  const double* __restrict__ tau, int* __restrict__ status) {
+                  const __grid_constant__ OzBatch b, int k0, int rows_total, const int* __restrict__ sig,
+                  const int* __restrict__ tau, int* __restrict__ status) {
   const OzMat& M = b.m[blockIdx.y];
   const int ng = M.ng;
   if (k0 >= ng) return;
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int i = i0 + r;
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
     const bool row_ok = i < ng && !(i >= k0 && i < k0 + kb);
-    const double si = row_ok ? sig[M.row_off + i] : 0.0;
+    const int ei = row_ok ? sig[M.row_off + i] : 0;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float hr[16], lr[16], hm[16], lm[16];
@@ -299,10 +301,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int q = 0; q < 16; ++q) {
           const int j = j0 + c0 + q;
           if (j > i || j >= ng || (j >= k0 && j < k0 + kb)) continue;
-          const double f = si * tau[M.row_off + j] * (1.0 / 65536.0);
+          // scale by sigma_i tau_j 2^-16 = 2^(ei + ej - 16): exact power of two,
+          // applied to the FP32 pair when it stays a normal number, else in FP64
+          const int ex = ei + tau[M.row_off + j] - 2 * BETA;
+          double dr, di;
+          if (ex > -100 && ex < 100) {
+            dr = (double)ldexpf(hr[q], ex) + (double)ldexpf(lr[q], ex);
+            di = (double)ldexpf(hm[q], ex) + (double)ldexpf(lm[q], ex);
+          } else {
+            dr = ldexp((double)hr[q] + (double)lr[q], ex);
+            di = ldexp((double)hm[q] + (double)lm[q], ex);
+          }
           double2* dst = M.A + (size_t)i * ng + j;
           const double2 v = *dst;
-          *dst = make_double2(v.x - f * ((double)hr[q] + (double)lr[q]), v.y - f * ((double)hm[q] + (double)lm[q]));
+          *dst = make_double2(v.x - dr, v.y - di);
         }
       }
     }
@@ -367,8 +379,8 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
   int rc;
   const size_t sb = (size_t)S * rows * KR * sizeof(__half);
   if ((rc = c->pool.alloc(sb, &plan->U.ptr)) != BGW_OK || (rc = c->pool.alloc(sb, &plan->V.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)rows * sizeof(double), &plan->sig.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)rows * sizeof(double), &plan->tau.ptr)) != BGW_OK)
+      (rc = c->pool.alloc((size_t)rows * sizeof(int), &plan->sig.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)rows * sizeof(int), &plan->tau.ptr)) != BGW_OK)
     return fail(c, rc, "tensor-core inverse: slice buffers (%zu B each) could not be allocated", sb);
   cuuint64_t gdim[2] = {(cuuint64_t)KR, (cuuint64_t)S * rows};
   cuuint64_t gstride[1] = {(cuuint64_t)KR * sizeof(__half)};
@@ -393,10 +405,10 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, cudaStream_t st) {
   const int rpad = (ngmax + BM - 1) / BM * BM;
   slice_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total,
                                                               plan->U.as<__half>(), plan->V.as<__half>(),
-                                                              plan->sig.as<double>(), plan->tau.as<double>());
+                                                              plan->sig.as<int>(), plan->tau.as<int>());
   const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
   update_kernel<<<dim3(plan->max_tiles, plan->nmat), kThreads, smem, st>>>(
-      plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, plan->sig.as<double>(), plan->tau.as<double>(),
+      plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, plan->sig.as<int>(), plan->tau.as<int>(),
       c->d_status);
   BGW_CUDA(c, cudaGetLastError());
   return BGW_OK;
