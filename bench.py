@@ -484,6 +484,7 @@ def run_profile_case(args):
     ctx = bgw.Context(0)
     cell = bgw.system_cell(s)
     prec = bgw.PREC[args.prec]
+    ctx.set_option(bgw.BGW_OPT_INVERSE, 0 if prec == bgw.BGW_PREC_FP64 else 1)
     cv = torch.from_numpy(s.cv).cuda()
     cc = torch.from_numpy(s.cc).cuda()
     M = torch.empty((s.npairs, s.ng), dtype=torch.complex128 if prec == 0 else torch.complex64, device="cuda")
