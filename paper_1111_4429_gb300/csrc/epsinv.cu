@@ -229,54 +229,63 @@ struct SweepBatch {
 // triangle, the same map as the big sweep: after pivot s every lower element
 // outside row/column s loses col_i conj(col_j) / d, the pivot column is
 // divided by d and the pivot becomes -1/d.  The result is -D^-1; Dinv gets
-// D^-1 (both triangles) and A_KK gets -D^-1 (lower).  The pivot column
-// scaled by 1/d is formed once per pivot by 32 threads, so each lower
-// element costs one complex multiply-subtract in FP64.
-__global__ void __launch_bounds__(NB * NB) sw_diag_kernel(const __grid_constant__ SweepBatch b, int k0,
-                                                          int* __restrict__ status) {
+// D^-1 (both triangles) and A_KK gets -D^-1 (lower).  The 528 lower elements
+// are packed into 17 full warps (the FP64 pipe of the one SM this runs on is
+// the limit, and idle lanes of a warp still occupy it); the pivot column
+// scaled by -1/d is formed once per pivot, so each element costs four FMAs.
+constexpr int kDiagThreads = (NB * (NB + 1) / 2 + 31) / 32 * 32;  // 544
+
+__global__ void __launch_bounds__(kDiagThreads) sw_diag_kernel(const __grid_constant__ SweepBatch b, int k0,
+                                                               int* __restrict__ status) {
   __shared__ double2 L[NB][NB + 1];
-  __shared__ double2 col[NB];   // column s of the current matrix
-  __shared__ double2 colr[NB];  // conj(col) / d
+  __shared__ double2 col[NB];    // column s of the current matrix
+  __shared__ double2 ncolr[NB];  // -conj(col) / d
   __shared__ double rpiv;
   const SweepMat& M = b.m[blockIdx.x];
   const int ng = M.ng;
   if (k0 >= ng) return;
   const int kb = min(NB, ng - k0);
   double2* A = M.A;
-  const int i = threadIdx.y, j = threadIdx.x;
-  const bool low = i < kb && j < kb && i >= j;
+  // thread -> lower element (i, j), i >= j, in triangular order
+  const int t = threadIdx.x;
+  int i = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  const int j = t - i * (i + 1) / 2;
+  const bool low = t < NB * (NB + 1) / 2 && i < kb;  // j <= i < kb
   if (low) L[i][j] = A[(size_t)(k0 + i) * ng + k0 + j];
   for (int s = 0; s < kb; ++s) {
     __syncthreads();
-    if (i == 0 && j < kb) {
+    if (t < kb) {
+      const int r = t;
       double2 cv;
-      if (j > s) {
-        cv = L[j][s];
-      } else if (j < s) {
-        const double2 t = L[s][j];
-        cv = make_double2(t.x, -t.y);
+      if (r > s) {
+        cv = L[r][s];
+      } else if (r < s) {
+        const double2 x = L[s][r];
+        cv = make_double2(x.x, -x.y);
       } else {
         cv = L[s][s];
       }
-      col[j] = cv;
+      col[r] = cv;
       const double d = L[s][s].x;
-      double r;
+      double rr;
       if (!(d > 0.0) || !isfinite(d)) {
-        if (j == 0) atomicExch(status, (int)kDevZeroPivot);
-        r = 0.0;
+        if (r == 0) atomicExch(status, (int)kDevZeroPivot);
+        rr = 0.0;
       } else {
-        r = 1.0 / d;
+        rr = 1.0 / d;
       }
-      colr[j] = make_double2(cv.x * r, -cv.y * r);
-      if (j == s) rpiv = r;
+      ncolr[r] = make_double2(-cv.x * rr, cv.y * rr);
+      if (r == s) rpiv = rr;
     }
     __syncthreads();
     if (low) {
       if (i != s && j != s) {
-        const double2 a = col[i], c = colr[j];
+        const double2 a = col[i], c = ncolr[j];
         double2 v = L[i][j];
-        v.x -= a.x * c.x - a.y * c.y;
-        v.y -= a.x * c.y + a.y * c.x;
+        v.x = fma(a.x, c.x, fma(-a.y, c.y, v.x));
+        v.y = fma(a.x, c.y, fma(a.y, c.x, v.y));
         L[i][j] = v;
       } else if (i == s && j == s) {
         L[s][s] = make_double2(-rpiv, 0.0);
@@ -284,15 +293,18 @@ __global__ void __launch_bounds__(NB * NB) sw_diag_kernel(const __grid_constant_
         const double2 a = col[i];
         L[i][s] = make_double2(a.x * rpiv, a.y * rpiv);
       } else {              // i == s, j < s: A_sj / d = conj(col_j) / d
-        L[s][j] = colr[j];
+        const double2 c = ncolr[j];
+        L[s][j] = make_double2(-c.x, -c.y);
       }
     }
   }
   __syncthreads();
-  if (i < kb && j < kb) {
-    const double2 v = (i >= j) ? L[i][j] : make_double2(L[j][i].x, -L[j][i].y);
-    M.Dinv[i * NB + j] = make_double2(-v.x, -v.y);
-    if (i >= j) A[(size_t)(k0 + i) * ng + k0 + j] = v;
+  for (int e2 = threadIdx.x; e2 < NB * NB; e2 += blockDim.x) {
+    const int r = e2 / NB, c = e2 % NB;
+    if (r >= kb || c >= kb) continue;
+    const double2 v = (r >= c) ? L[r][c] : make_double2(L[c][r].x, -L[c][r].y);
+    M.Dinv[r * NB + c] = make_double2(-v.x, -v.y);
+    if (r >= c) A[(size_t)(k0 + r) * ng + k0 + c] = v;
   }
 }
 
@@ -499,7 +511,7 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
       if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), oz.get())) != BGW_OK) return rc;
     }
     for (int k0 = 0; k0 < ngmax; k0 += NB) {
-      sw_diag_kernel<<<nb, dim3(NB, NB), 0, st>>>(sb, k0, c->d_status);
+      sw_diag_kernel<<<nb, kDiagThreads, 0, st>>>(sb, k0, c->d_status);
       sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, st>>>(sb, k0);
       if (tc_update) {
         if ((rc = oz_update(c, oz.get(), k0, ngmax, st)) != BGW_OK) return rc;

@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* us = smem;                  // S x 16 KiB
   unsigned char* vs = smem + S * kUTile;     // S x 4 KiB
-  uint64_t* full = reinterpret_cast<uint64_t*>(vs + S * kVTile);
+  double2* as = reinterpret_cast<double2*>(vs + S * kVTile);  // A tile [BM][BN + 1]
+  uint64_t* full = reinterpret_cast<uint64_t*>(as + BM * (BN + 1));
   uint64_t* done = full + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -209,6 +210,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
+  // Prefetch this thread's row of the A tile into shared memory while the
+  // slices load and the MMAs run (the epilogue then reads A from smem).
+  {
+    const int r = threadIdx.x, i = i0 + r;
+    if (i < ng) {
+      const double2* src = M.A + (size_t)i * ng + j0;
+      const uint32_t dst = smem_u32(as + r * (BN + 1));
+      const int jn = min(BN, ng - j0);
+      for (int q = 0; q < jn; ++q)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * q), "l"(src + q) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
 
   if (warp == 0 && lane == 0) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(full)),
@@ -261,6 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (!have && threadIdx.x == 0) atomicExch(status, (int)kDevTimeout);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncwarp();
+  asm volatile("cp.async.wait_all;" ::: "memory");
   if (have && ok) {
     const int r = warp * 32 + lane;
     const int i = i0 + r;
@@ -312,9 +327,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             dr = ldexp((double)hr[q] + (double)lr[q], ex);
             di = ldexp((double)hm[q] + (double)lm[q], ex);
           }
-          double2* dst = M.A + (size_t)i * ng + j;
-          const double2 v = *dst;
-          *dst = make_double2(v.x - dr, v.y - di);
+          const double2 v = as[r * (BN + 1) + c0 + q];
+          M.A[(size_t)i * ng + j] = make_double2(v.x - dr, v.y - di);
         }
       }
     }
@@ -394,7 +408,7 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return fail(c, BGW_ECUDA, "tensor-core inverse: tensor map encoding failed");
-  const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
+  const size_t smem = (size_t)S * (kUTile + kVTile) + sizeof(double2) * BM * (BN + 1) + 1024 + 64;
   BGW_CUDA(c, cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   return BGW_OK;
 }
@@ -406,7 +420,7 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, cudaStream_t st) {
   slice_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total,
                                                               plan->U.as<__half>(), plan->V.as<__half>(),
                                                               plan->sig.as<int>(), plan->tau.as<int>());
-  const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
+  const size_t smem = (size_t)S * (kUTile + kVTile) + sizeof(double2) * BM * (BN + 1) + 1024 + 64;
   update_kernel<<<dim3(plan->max_tiles, plan->nmat), kThreads, smem, st>>>(
       plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, plan->sig.as<int>(), plan->tau.as<int>(),
       c->d_status);
