@@ -186,6 +186,9 @@ int bgw_destroy(bgw_ctx* ctx) {
   for (cudaEvent_t e : ctx->impl.timing.free_events) cudaEventDestroy(e);
   for (auto& kv : ctx->impl.graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (ctx->impl.side) cudaStreamDestroy(ctx->impl.side);
+  for (cudaEvent_t e : ctx->impl.la_ev)
+    if (e) cudaEventDestroy(e);
   ctx->impl.graphs.clear();
   ctx->impl.pool.unpin_all();
   cudaFree(ctx->impl.d_status);

@@ -510,17 +510,53 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
       }
       if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), oz.get())) != BGW_OK) return rc;
     }
-    for (int k0 = 0; k0 < ngmax; k0 += NB) {
-      sw_diag_kernel<<<nb, kDiagThreads, 0, st>>>(sb, k0, c->d_status);
-      sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, st>>>(sb, k0);
-      if (tc_update) {
-        if ((rc = oz_update(c, oz.get(), k0, ngmax, st)) != BGW_OK) return rc;
-        c->launches += 2;
-      } else {
+    if (!tc_update) {
+      for (int k0 = 0; k0 < ngmax; k0 += NB) {
+        sw_diag_kernel<<<nb, kDiagThreads, 0, st>>>(sb, k0, c->d_status);
+        sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, st>>>(sb, k0);
         sw_update_kernel<<<dim3((unsigned)ntl, nb), 256, upd_smem, st>>>(sb, k0);
+        BGW_CUDA(c, cudaGetLastError());
         c->launches += 3;
       }
-      BGW_CUDA(c, cudaGetLastError());
+    } else {
+      // Look-ahead: the chain that the next step waits for (diagonal block,
+      // panel, slices, then the update of the tiles touching the next block)
+      // runs on a high-priority side stream, while the main stream updates the
+      // other tiles of the current step.  Dependencies:
+      //   step k's chain waits for the main-stream update of step k-2 (same
+      //     slice buffer; tiles of block k may still be pending there);
+      //   step k's next-block update waits for the main-stream update of k-1;
+      //   step k's main-stream update waits for step k's slices.
+      if (!c->side) {
+        int lo = 0, hi = 0;
+        BGW_CUDA(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        BGW_CUDA(c, cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi));
+        for (auto& e : c->la_ev) BGW_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      }
+      cudaStream_t s2 = c->side;
+      cudaEvent_t ev_fork = c->la_ev[0], ev_slice = c->la_ev[1];
+      cudaEvent_t ev_rest[2] = {c->la_ev[2], c->la_ev[3]};
+      BGW_CUDA(c, cudaEventRecord(ev_fork, st));
+      BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_fork, 0));
+      int k = 0;
+      for (int k0 = 0; k0 < ngmax; k0 += NB, ++k) {
+        const int buf = k & 1;
+        if (k >= 2) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf], 0));
+        sw_diag_kernel<<<nb, kDiagThreads, 0, s2>>>(sb, k0, c->d_status);
+        sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, s2>>>(sb, k0);
+        if ((rc = oz_slice(c, oz.get(), k0, ngmax, buf, s2)) != BGW_OK) return rc;
+        BGW_CUDA(c, cudaEventRecord(ev_slice, s2));
+        if (k >= 1) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf ^ 1], 0));
+        if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 1, s2)) != BGW_OK) return rc;
+        BGW_CUDA(c, cudaStreamWaitEvent(st, ev_slice, 0));
+        if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 2, st)) != BGW_OK) return rc;
+        BGW_CUDA(c, cudaEventRecord(ev_rest[buf], st));
+        BGW_CUDA(c, cudaGetLastError());
+        c->launches += 5;
+      }
+      // join: the main stream waits for the side stream's last work
+      BGW_CUDA(c, cudaEventRecord(ev_fork, s2));
+      BGW_CUDA(c, cudaStreamWaitEvent(st, ev_fork, 0));
     }
     const long long nlow = (long long)ngmax * (ngmax + 1) / 2;
     sw_finish_kernel<<<dim3((unsigned)std::min<long long>((nlow + 255) / 256, 152LL * 16), nb), 256, 0, st>>>(sb);

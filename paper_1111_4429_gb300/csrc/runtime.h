@@ -109,6 +109,8 @@ struct Ctx {
   std::unordered_map<uint64_t, BatchGraph> graphs;
   std::map<std::tuple<int, int, int, int>, int> tuned_ppb;  // (n, prec, nys, ncol) -> pairs per CTA
   bool autotune = true;
+  cudaStream_t side = nullptr;     // high-priority stream of the sweep's look-ahead chain
+  cudaEvent_t la_ev[4] = {};       // look-ahead dependencies (fork, slice, rest x2)
   int inverse_mode = -1;     // -1: tensor-core update for the mixed precisions; 0: FP64 FMA; 1: tensor cores
   Pool pool;
   std::string err;
@@ -204,7 +206,8 @@ OzPlan* oz_plan_new();
 void oz_plan_delete(OzPlan* p);
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
                OzPlan* plan);
-int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, cudaStream_t st);
+int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);
+int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaStream_t st);
 
 }  // namespace bgw
 

@@ -119,7 +119,7 @@ struct OzBatch {
 // parts of column k and the imaginary parts (k + 32).  Rows inside the swept
 // block and padding rows get zero slices.
 __global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBatch b, int k0, int rows_total,
-                                                    __half* __restrict__ U, __half* __restrict__ V,
+                                                    int buf, __half* __restrict__ U, __half* __restrict__ V,
                                                     int* __restrict__ sig, int* __restrict__ tau) {
   const OzMat& M = b.m[blockIdx.y];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBa
   const double up = 256.0;
   double xr = ldexp(re, BETA - e), xi = ldexp(im, BETA - e);  // x 2^8
   const size_t row = (size_t)M.row_off + i;
-  __half* out = blockIdx.z == 0 ? U : V;
+  __half* out = (blockIdx.z == 0 ? U : V) + (size_t)buf * S * rows_total * KR;
 #pragma unroll
   for (int a = 0; a < S; ++a) {
     const double hr = rint(xr), hi = rint(xi);
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBa
     o[lane] = __double2half(hr);
     o[lane + 32] = __double2half(hi);
   }
-  if (lane == 0) (blockIdx.z == 0 ? sig : tau)[row] = e;
+  if (lane == 0) (blockIdx.z == 0 ? sig : tau)[(size_t)buf * rows_total + row] = e;
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -164,25 +164,49 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // One CTA: the 128 x 32 tile (I, J) of the lower triangle of one matrix.
+// mode 0: every lower tile; 1: only the tiles touching the next block
+// (rows or columns k0 + NB .. k0 + 2 NB), which the next sweep step reads
+// first; 2: every other tile.  Modes 1 and 2 split one step's update so the
+// next step's diagonal block, panel and slices can proceed after mode 1.
 __global__ void __launch_bounds__(kThreads, 1)
     update_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
-                  const __grid_constant__ OzBatch b, int k0, int rows_total, const int* __restrict__ sig,
-                  const int* __restrict__ tau, int* __restrict__ status) {
+                  const __grid_constant__ OzBatch b, int k0, int rows_total, int buf, int mode,
+                  const int* __restrict__ sig, const int* __restrict__ tau, int* __restrict__ status) {
   const OzMat& M = b.m[blockIdx.y];
   const int ng = M.ng;
   if (k0 >= ng) return;
   const int kb = min(NB, ng - k0);
-  // tile decode: row tile I holds column tiles J = 0 .. min(4I+3, nJ-1)
   const int nI = (ng + BM - 1) / BM, nJ = (ng + BN - 1) / BN;
-  int t = blockIdx.x, I = 0;
-  for (; I < nI; ++I) {
-    const int cI = min(4 * I + 4, nJ);
-    if (t < cI) break;
-    t -= cI;
+  const int k1 = k0 + NB;                      // next block
+  const bool has_next = k1 < ng;
+  const int In = k1 / BM, Jn = k1 / BN;
+  int I = 0, J = 0;
+  if (mode == 1) {
+    if (!has_next) return;
+    const int crow = min(4 * In + 4, nJ);
+    const int t = blockIdx.x;
+    if (t < crow) {
+      I = In;
+      J = t;
+    } else {
+      I = In + 1 + (t - crow);
+      J = Jn;
+      if (I >= nI) return;
+    }
+  } else {
+    // tile decode: row tile I holds column tiles J = 0 .. min(4I+3, nJ-1)
+    int t = blockIdx.x;
+    for (; I < nI; ++I) {
+      const int cI = min(4 * I + 4, nJ);
+      if (t < cI) break;
+      t -= cI;
+    }
+    if (I >= nI) return;
+    J = t;
+    if (mode == 2 && has_next && (I == In || J == Jn)) return;
   }
-  if (I >= nI) return;
-  const int J = t;
   const int i0 = I * BM, j0 = J * BN;
+  const int slice_base = buf * S * rows_total;  // first slice row of this step's buffer
   if (i0 >= k0 && min(i0 + BM, ng) <= k0 + kb) return;
   if (j0 >= k0 && min(j0 + BN, ng) <= k0 + kb) return;
 
@@ -229,8 +253,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                  "r"((uint32_t)(S * (kUTile + kVTile)))
                  : "memory");
     for (int a = 0; a < S; ++a) {
-      tma_load_2d(us + a * kUTile, &umap, full, 0, a * rows_total + M.row_off + i0);
-      tma_load_2d(vs + a * kVTile, &vmap, full, 0, a * rows_total + M.row_off + j0);
+      tma_load_2d(us + a * kUTile, &umap, full, 0, slice_base + a * rows_total + M.row_off + i0);
+      tma_load_2d(vs + a * kVTile, &vmap, full, 0, slice_base + a * rows_total + M.row_off + j0);
     }
     // the copies must land before this CTA may exit, whatever happens next
     const uint64_t t0 = globaltimer();
@@ -281,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int i = i0 + r;
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
     const bool row_ok = i < ng && !(i >= k0 && i < k0 + kb);
-    const int ei = row_ok ? sig[M.row_off + i] : 0;
+    const int ei = row_ok ? sig[buf * rows_total + M.row_off + i] : 0;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float hr[16], lr[16], hm[16], lm[16];
@@ -318,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (j > i || j >= ng || (j >= k0 && j < k0 + kb)) continue;
           // scale by sigma_i tau_j 2^-16 = 2^(ei + ej - 16): exact power of two,
           // applied to the FP32 pair when it stays a normal number, else in FP64
-          const int ex = ei + tau[M.row_off + j] - 2 * BETA;
+          const int ex = ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA;
           double dr, di;
           if (ex > -100 && ex < 100) {
             dr = (double)ldexpf(hr[q], ex) + (double)ldexpf(lr[q], ex);
@@ -391,12 +415,14 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
   plan->max_tiles = tiles;
   plan->U.pool = plan->V.pool = plan->sig.pool = plan->tau.pool = &c->pool;
   int rc;
-  const size_t sb = (size_t)S * rows * KR * sizeof(__half);
+  // two slice buffers: a step may slice while the previous step's update
+  // still reads its own
+  const size_t sb = (size_t)2 * S * rows * KR * sizeof(__half);
   if ((rc = c->pool.alloc(sb, &plan->U.ptr)) != BGW_OK || (rc = c->pool.alloc(sb, &plan->V.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)rows * sizeof(int), &plan->sig.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)rows * sizeof(int), &plan->tau.ptr)) != BGW_OK)
+      (rc = c->pool.alloc((size_t)2 * rows * sizeof(int), &plan->sig.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)2 * rows * sizeof(int), &plan->tau.ptr)) != BGW_OK)
     return fail(c, rc, "tensor-core inverse: slice buffers (%zu B each) could not be allocated", sb);
-  cuuint64_t gdim[2] = {(cuuint64_t)KR, (cuuint64_t)S * rows};
+  cuuint64_t gdim[2] = {(cuuint64_t)KR, (cuuint64_t)2 * S * rows};
   cuuint64_t gstride[1] = {(cuuint64_t)KR * sizeof(__half)};
   cuuint32_t estr[2] = {1, 1};
   cuuint32_t ubox[2] = {(cuuint32_t)KR, (cuuint32_t)BM};
@@ -413,17 +439,32 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
   return BGW_OK;
 }
 
-// One sweep step's trailing update for every matrix of the plan.
-int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, cudaStream_t st) {
+// Slices of one sweep step (P and C of every matrix) into buffer buf.
+int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) {
   using namespace oz;
   const int rpad = (ngmax + BM - 1) / BM * BM;
-  slice_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total,
+  slice_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
                                                               plan->U.as<__half>(), plan->V.as<__half>(),
                                                               plan->sig.as<int>(), plan->tau.as<int>());
+  BGW_CUDA(c, cudaGetLastError());
+  return BGW_OK;
+}
+
+// The trailing update of one sweep step from slice buffer buf: mode 0 all
+// tiles, 1 the tiles touching the next block, 2 the others.
+int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaStream_t st) {
+  using namespace oz;
+  int grid = plan->max_tiles;
+  if (mode == 1) {
+    const int k1 = k0 + NB;
+    if (k1 >= ngmax) return BGW_OK;
+    const int nI = (ngmax + BM - 1) / BM, nJ = (ngmax + BN - 1) / BN, In = k1 / BM;
+    grid = std::min(4 * In + 4, nJ) + std::max(0, nI - In - 1);
+  }
   const size_t smem = (size_t)S * (kUTile + kVTile) + sizeof(double2) * BM * (BN + 1) + 1024 + 64;
-  update_kernel<<<dim3(plan->max_tiles, plan->nmat), kThreads, smem, st>>>(
-      plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, plan->sig.as<int>(), plan->tau.as<int>(),
-      c->d_status);
+  update_kernel<<<dim3(grid, plan->nmat), kThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,
+                                                                plan->rows_total, buf, mode, plan->sig.as<int>(),
+                                                                plan->tau.as<int>(), c->d_status);
   BGW_CUDA(c, cudaGetLastError());
   return BGW_OK;
 }
