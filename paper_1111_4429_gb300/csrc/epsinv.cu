@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "runtime.h"
+#include "sweep_common.cuh"
 
 namespace bgw {
 
@@ -225,84 +226,26 @@ struct SweepBatch {
   SweepMat m[kSweepBatch];
 };
 
-// Sweep of the diagonal block D (Hermitian positive definite) on its lower
-// triangle, the same map as the big sweep: after pivot s every lower element
-// outside row/column s loses col_i conj(col_j) / d, the pivot column is
-// divided by d and the pivot becomes -1/d.  The result is -D^-1; Dinv gets
-// D^-1 (both triangles) and A_KK gets -D^-1 (lower).  The 528 lower elements
-// are packed into 17 full warps (the FP64 pipe of the one SM this runs on is
-// the limit, and idle lanes of a warp still occupy it); the pivot column
-// scaled by -1/d is formed once per pivot, so each element costs four FMAs.
-constexpr int kDiagThreads = (NB * (NB + 1) / 2 + 31) / 32 * 32;  // 544
-
+// Diagonal block of one sweep step (sweep_common.cuh): Dinv gets D^-1 (both
+// triangles) and A_KK gets -D^-1 (lower).
 __global__ void __launch_bounds__(kDiagThreads) sw_diag_kernel(const __grid_constant__ SweepBatch b, int k0,
                                                                int* __restrict__ status) {
-  __shared__ double2 L[NB][NB + 1];
-  __shared__ double2 col[NB];    // column s of the current matrix
-  __shared__ double2 ncolr[NB];  // -conj(col) / d
-  __shared__ double rpiv;
+  __shared__ DiagSmem sm;
   const SweepMat& M = b.m[blockIdx.x];
   const int ng = M.ng;
   if (k0 >= ng) return;
   const int kb = min(NB, ng - k0);
   double2* A = M.A;
-  // thread -> lower element (i, j), i >= j, in triangular order
   const int t = threadIdx.x;
-  int i = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
-  while ((i + 1) * (i + 2) / 2 <= t) ++i;
-  while (i * (i + 1) / 2 > t) --i;
-  const int j = t - i * (i + 1) / 2;
-  const bool low = t < NB * (NB + 1) / 2 && i < kb;  // j <= i < kb
-  if (low) L[i][j] = A[(size_t)(k0 + i) * ng + k0 + j];
-  for (int s = 0; s < kb; ++s) {
-    __syncthreads();
-    if (t < kb) {
-      const int r = t;
-      double2 cv;
-      if (r > s) {
-        cv = L[r][s];
-      } else if (r < s) {
-        const double2 x = L[s][r];
-        cv = make_double2(x.x, -x.y);
-      } else {
-        cv = L[s][s];
-      }
-      col[r] = cv;
-      const double d = L[s][s].x;
-      double rr;
-      if (!(d > 0.0) || !isfinite(d)) {
-        if (r == 0) atomicExch(status, (int)kDevZeroPivot);
-        rr = 0.0;
-      } else {
-        rr = 1.0 / d;
-      }
-      ncolr[r] = make_double2(-cv.x * rr, cv.y * rr);
-      if (r == s) rpiv = rr;
-    }
-    __syncthreads();
-    if (low) {
-      if (i != s && j != s) {
-        const double2 a = col[i], c = ncolr[j];
-        double2 v = L[i][j];
-        v.x = fma(a.x, c.x, fma(-a.y, c.y, v.x));
-        v.y = fma(a.x, c.y, fma(a.y, c.x, v.y));
-        L[i][j] = v;
-      } else if (i == s && j == s) {
-        L[s][s] = make_double2(-rpiv, 0.0);
-      } else if (j == s) {  // i > s: A_is / d
-        const double2 a = col[i];
-        L[i][s] = make_double2(a.x * rpiv, a.y * rpiv);
-      } else {              // i == s, j < s: A_sj / d = conj(col_j) / d
-        const double2 c = ncolr[j];
-        L[s][j] = make_double2(-c.x, -c.y);
-      }
-    }
-  }
-  __syncthreads();
+  int i, j;
+  bool low;
+  diag_thread_element(t, kb, i, j, low);
+  if (low) sm.L[i][j] = A[(size_t)(k0 + i) * ng + k0 + j];
+  diag_sweep_smem(sm, kb, t, i, j, low, status);
   for (int e2 = threadIdx.x; e2 < NB * NB; e2 += blockDim.x) {
     const int r = e2 / NB, c = e2 % NB;
     if (r >= kb || c >= kb) continue;
-    const double2 v = (r >= c) ? L[r][c] : make_double2(L[c][r].x, -L[c][r].y);
+    const double2 v = (r >= c) ? sm.L[r][c] : make_double2(sm.L[c][r].x, -sm.L[c][r].y);
     M.Dinv[r * NB + c] = make_double2(-v.x, -v.y);
     if (r >= c) A[(size_t)(k0 + r) * ng + k0 + c] = v;
   }
@@ -502,13 +445,16 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
       std::vector<int> ngs(nb);
       std::vector<double2*> As(nb);
       std::vector<const double2*> Cs(nb), Ps(nb);
+      std::vector<double2*> Ds(nb);
       for (int k = 0; k < nb; ++k) {
         ngs[k] = sb.m[k].ng;
         As[k] = sb.m[k].A;
         Cs[k] = sb.m[k].C;
         Ps[k] = sb.m[k].P;
+        Ds[k] = sb.m[k].Dinv;
       }
-      if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), oz.get())) != BGW_OK) return rc;
+      if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), Ds.data(), oz.get())) != BGW_OK)
+        return rc;
     }
     if (!tc_update) {
       for (int k0 = 0; k0 < ngmax; k0 += NB) {
@@ -542,9 +488,8 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
       for (int k0 = 0; k0 < ngmax; k0 += NB, ++k) {
         const int buf = k & 1;
         if (k >= 2) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf], 0));
-        sw_diag_kernel<<<nb, kDiagThreads, 0, s2>>>(sb, k0, c->d_status);
-        sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, s2>>>(sb, k0);
-        if ((rc = oz_slice(c, oz.get(), k0, ngmax, buf, s2)) != BGW_OK) return rc;
+        // diagonal block, panel and slices of step k in one launch
+        if ((rc = oz_chain(c, oz.get(), k0, ngmax, buf, s2)) != BGW_OK) return rc;
         BGW_CUDA(c, cudaEventRecord(ev_slice, s2));
         if (k >= 1) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf ^ 1], 0));
         if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 1, s2)) != BGW_OK) return rc;
@@ -552,7 +497,7 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
         if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 2, st)) != BGW_OK) return rc;
         BGW_CUDA(c, cudaEventRecord(ev_rest[buf], st));
         BGW_CUDA(c, cudaGetLastError());
-        c->launches += 5;
+        c->launches += 4;
       }
       // join: the main stream waits for the side stream's last work
       BGW_CUDA(c, cudaEventRecord(ev_fork, s2));
