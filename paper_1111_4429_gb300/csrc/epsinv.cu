@@ -445,16 +445,13 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
       std::vector<int> ngs(nb);
       std::vector<double2*> As(nb);
       std::vector<const double2*> Cs(nb), Ps(nb);
-      std::vector<double2*> Ds(nb);
       for (int k = 0; k < nb; ++k) {
         ngs[k] = sb.m[k].ng;
         As[k] = sb.m[k].A;
         Cs[k] = sb.m[k].C;
         Ps[k] = sb.m[k].P;
-        Ds[k] = sb.m[k].Dinv;
       }
-      if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), Ds.data(), oz.get())) != BGW_OK)
-        return rc;
+      if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), oz.get())) != BGW_OK) return rc;
     }
     if (!tc_update) {
       for (int k0 = 0; k0 < ngmax; k0 += NB) {
@@ -488,8 +485,9 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
       for (int k0 = 0; k0 < ngmax; k0 += NB, ++k) {
         const int buf = k & 1;
         if (k >= 2) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf], 0));
-        // diagonal block, panel and slices of step k in one launch
-        if ((rc = oz_chain(c, oz.get(), k0, ngmax, buf, s2)) != BGW_OK) return rc;
+        sw_diag_kernel<<<nb, kDiagThreads, 0, s2>>>(sb, k0, c->d_status);
+        sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, s2>>>(sb, k0);
+        if ((rc = oz_slice(c, oz.get(), k0, ngmax, buf, s2)) != BGW_OK) return rc;
         BGW_CUDA(c, cudaEventRecord(ev_slice, s2));
         if (k >= 1) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf ^ 1], 0));
         if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 1, s2)) != BGW_OK) return rc;
@@ -497,7 +495,7 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
         if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 2, st)) != BGW_OK) return rc;
         BGW_CUDA(c, cudaEventRecord(ev_rest[buf], st));
         BGW_CUDA(c, cudaGetLastError());
-        c->launches += 4;
+        c->launches += 5;
       }
       // join: the main stream waits for the side stream's last work
       BGW_CUDA(c, cudaEventRecord(ev_fork, s2));

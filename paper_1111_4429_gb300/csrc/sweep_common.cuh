@@ -1,6 +1,5 @@
-// Sweep of one diagonal block in shared memory, shared by the FP64 sweep
-// (epsinv.cu) and the fused look-ahead chain of the tensor-core sweep
-// (sweep_tc.cu).
+// Sweep of one diagonal block in shared memory (the diagonal step of both
+// sweeps in epsinv.cu).
 //
 // D (Hermitian positive definite, kb <= 32) is held as its lower triangle
 // L[i][j], i >= j.  Pivot s: every lower element outside row/column s loses

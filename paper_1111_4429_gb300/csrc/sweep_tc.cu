@@ -22,7 +22,6 @@
 #include <vector>
 
 #include "runtime.h"
-#include "sweep_common.cuh"
 
 namespace bgw {
 
@@ -107,7 +106,6 @@ struct OzMat {
   double2* A;
   const double2* C;   // [ng][NB]
   const double2* P;   // [ng][NB]
-  double2* D;         // [NB][NB] -D^-1 of the current diagonal block (lower)
   int ng;
   int row_off;        // first slice row of this matrix (multiple of BM)
 };
@@ -116,48 +114,6 @@ struct OzBatch {
   int n;
   OzMat m[kBatch];
 };
-
-// Slices of P (z = 0) and C (z = 1): one warp per row, lane k holds the real
-// parts of column k and the imaginary parts (k + 32).  Rows inside the swept
-// block and padding rows get zero slices.
-__global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBatch b, int k0, int rows_total,
-                                                    int buf, __half* __restrict__ U, __half* __restrict__ V,
-                                                    int* __restrict__ sig, int* __restrict__ tau) {
-  const OzMat& M = b.m[blockIdx.y];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * 8 + warp;
-  const int ngpad = (M.ng + BM - 1) / BM * BM;
-  if (i >= ngpad) return;
-  const int kb = min(NB, M.ng - k0);
-  const bool live = k0 < M.ng && i < M.ng && (i < k0 || i >= k0 + kb);
-  const double2* src = blockIdx.z == 0 ? M.P : M.C;
-  double re = 0.0, im = 0.0;
-  if (live && lane < kb) {
-    const double2 v = src[(size_t)i * NB + lane];
-    re = v.x;
-    im = v.y;
-  }
-  double m = fmax(fabs(re), fabs(im));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |x| < 1 after scaling by 2^-e
-  // y_a = x 2^{8(a+1)} relative to the row scale: h_a = rint(y_a) and
-  // y_{a+1} = (y_a - h_a) 2^8, both steps exact in FP64 (no division)
-  const double up = 256.0;
-  double xr = ldexp(re, BETA - e), xi = ldexp(im, BETA - e);  // x 2^8
-  const size_t row = (size_t)M.row_off + i;
-  __half* out = (blockIdx.z == 0 ? U : V) + (size_t)buf * S * rows_total * KR;
-#pragma unroll
-  for (int a = 0; a < S; ++a) {
-    const double hr = rint(xr), hi = rint(xi);
-    xr = (xr - hr) * up;  // exact: the remainder has fewer than 45 significant bits
-    xi = (xi - hi) * up;
-    __half* o = out + ((size_t)a * rows_total + row) * KR;
-    o[lane] = __double2half(hr);
-    o[lane + 32] = __double2half(hi);
-  }
-  if (lane == 0) (blockIdx.z == 0 ? sig : tau)[(size_t)buf * rows_total + row] = e;
-}
 
 // Balanced base-256 digits of a 56-bit fixed-point value: x = sum_a h_a
 // 2^{-8(a+1)} for |x| < 1, |h_0| <= 256 and |h_a| <= 128 (a >= 1).  X is
@@ -188,88 +144,30 @@ __device__ __forceinline__ void slice_row(double re, double im, int lane, __half
   if (lane == 0) *exp_out = e;
 }
 
-// The look-ahead chain of one sweep step, fused: every CTA sweeps the
-// diagonal block itself (its own SM's FP64 pipe; no single-CTA launch on the
-// critical path), then each warp takes rows i outside the block:
-// C_i = A_iK, P_i = C_i D^-1, A_iK <- P_i, and writes the slices of P_i (U)
-// and C_i (V) with their exponents into buffer buf.  Rows inside the block
-// and padding rows get zero slices.  CTA 0 saves -D^-1 to M.D; A_KK is
-// written by diag_store_kernel afterwards (other CTAs of this launch may
-// still be reading D from A_KK).
-constexpr int kChainWarps = kDiagThreads / 32;  // 17
-
-__global__ void __launch_bounds__(kDiagThreads) chain_kernel(const __grid_constant__ OzBatch b, int k0,
-                                                             int rows_total, int buf, __half* __restrict__ U,
-                                                             __half* __restrict__ V, int* __restrict__ sig,
-                                                             int* __restrict__ tau, int* __restrict__ status) {
-  __shared__ DiagSmem sm;
-  __shared__ double2 Dinv[NB][NB + 1];
-  __shared__ double2 Cw[kChainWarps][NB];
+// Slices of P (z = 0) and C (z = 1): one warp per row, lane k holds the real
+// parts of column k and the imaginary parts (k + 32).  Rows inside the swept
+// block and padding rows get zero slices.
+__global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBatch b, int k0, int rows_total,
+                                                    int buf, __half* __restrict__ U, __half* __restrict__ V,
+                                                    int* __restrict__ sig, int* __restrict__ tau) {
   const OzMat& M = b.m[blockIdx.y];
-  const int ng = M.ng;
-  if (k0 >= ng) return;
-  const int kb = min(NB, ng - k0);
-  double2* A = M.A;
-  const int t = threadIdx.x;
-  int di, dj;
-  bool low;
-  diag_thread_element(t, kb, di, dj, low);
-  if (low) sm.L[di][dj] = A[(size_t)(k0 + di) * ng + k0 + dj];
-  diag_sweep_smem(sm, kb, t, di, dj, low, status);
-  for (int e2 = t; e2 < NB * NB; e2 += blockDim.x) {
-    const int r = e2 / NB, c = e2 % NB;
-    double2 v = make_double2(0.0, 0.0);
-    if (r < kb && c < kb) v = (r >= c) ? sm.L[r][c] : make_double2(sm.L[c][r].x, -sm.L[c][r].y);
-    Dinv[r][c] = make_double2(-v.x, -v.y);
-    if (blockIdx.x == 0) M.D[r * NB + c] = v;
-  }
-  __syncthreads();
-  const int warp = t >> 5, lane = t & 31;
-  const int ngpad = (ng + BM - 1) / BM * BM;
-  const size_t stride = (size_t)rows_total * KR;  // between slices
-  __half* ub = U + (size_t)buf * S * rows_total * KR;
-  __half* vb = V + (size_t)buf * S * rows_total * KR;
-  for (int i = blockIdx.x * kChainWarps + warp; i < ngpad; i += gridDim.x * kChainWarps) {
-    const bool live = i < ng && (i < k0 || i >= k0 + kb);
-    double2 cv = make_double2(0.0, 0.0);
-    if (live && lane < kb) {
-      if (i >= k0 + kb) {
-        cv = A[(size_t)i * ng + k0 + lane];
-      } else {
-        const double2 x = A[(size_t)(k0 + lane) * ng + i];
-        cv = make_double2(x.x, -x.y);
-      }
-    }
-    Cw[warp][lane] = cv;
-    __syncwarp();
-    double2 pv = make_double2(0.0, 0.0);
-    for (int s2 = 0; s2 < kb; ++s2) {
-      const double2 a = Cw[warp][s2], d = Dinv[s2][lane];
-      pv.x = fma(a.x, d.x, fma(-a.y, d.y, pv.x));
-      pv.y = fma(a.x, d.y, fma(a.y, d.x, pv.y));
-    }
-    __syncwarp();
-    if (live && lane < kb) {
-      if (i >= k0 + kb)
-        A[(size_t)i * ng + k0 + lane] = pv;
-      else
-        A[(size_t)(k0 + lane) * ng + i] = make_double2(pv.x, -pv.y);
-    }
-    const size_t row = (size_t)M.row_off + i;
-    slice_row(pv.x, pv.y, lane, ub + row * KR, stride, sig + (size_t)buf * rows_total + row);
-    slice_row(cv.x, cv.y, lane, vb + row * KR, stride, tau + (size_t)buf * rows_total + row);
-  }
-}
-
-// A_KK <- -D^-1 (lower) from the chain's saved copy.  grid nmat, block 256.
-__global__ void diag_store_kernel(const __grid_constant__ OzBatch b, int k0) {
-  const OzMat& M = b.m[blockIdx.x];
-  if (k0 >= M.ng) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  const int ngpad = (M.ng + BM - 1) / BM * BM;
+  if (i >= ngpad) return;
   const int kb = min(NB, M.ng - k0);
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    if (r < kb && c <= r) M.A[(size_t)(k0 + r) * M.ng + k0 + c] = M.D[r * NB + c];
+  const bool live = k0 < M.ng && i < M.ng && (i < k0 || i >= k0 + kb);
+  const double2* src = blockIdx.z == 0 ? M.P : M.C;
+  double re = 0.0, im = 0.0;
+  if (live && lane < kb) {
+    const double2 v = src[(size_t)i * NB + lane];
+    re = v.x;
+    im = v.y;
   }
+  const size_t row = (size_t)M.row_off + i;
+  __half* out = (blockIdx.z == 0 ? U : V) + (size_t)buf * S * rows_total * KR + row * KR;
+  slice_row(re, im, lane, out, (size_t)rows_total * KR,
+            (blockIdx.z == 0 ? sig : tau) + (size_t)buf * rows_total + row);
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -500,7 +398,7 @@ struct OzPlan {
 };
 
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               double2* const* D, OzPlan* plan) {
+               OzPlan* plan) {
   using namespace oz;
   if (nmat > kBatch) return fail(c, BGW_EUNSUPPORTED, "tensor-core inverse: at most %d matrices per batch", kBatch);
   if (!g_encode_oz) {
@@ -518,7 +416,6 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
     plan->batch.m[m].A = A[m];
     plan->batch.m[m].C = C[m];
     plan->batch.m[m].P = P[m];
-    plan->batch.m[m].D = D[m];
     plan->batch.m[m].ng = ng[m];
     plan->batch.m[m].row_off = rows;
     rows += (ng[m] + BM - 1) / BM * BM;
@@ -562,20 +459,6 @@ int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) 
   slice_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
                                                               plan->U.as<__half>(), plan->V.as<__half>(),
                                                               plan->sig.as<int>(), plan->tau.as<int>());
-  BGW_CUDA(c, cudaGetLastError());
-  return BGW_OK;
-}
-
-// The fused look-ahead chain of one sweep step (chain_kernel).
-int oz_chain(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) {
-  using namespace oz;
-  const int rpad = (ngmax + BM - 1) / BM * BM;
-  const int grid = std::min((rpad + kChainWarps - 1) / kChainWarps, 2 * 152);
-  chain_kernel<<<dim3(grid, plan->nmat), kDiagThreads, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
-                                                                plan->U.as<__half>(), plan->V.as<__half>(),
-                                                                plan->sig.as<int>(), plan->tau.as<int>(),
-                                                                c->d_status);
-  diag_store_kernel<<<plan->nmat, 256, 0, st>>>(plan->batch, k0);
   BGW_CUDA(c, cudaGetLastError());
   return BGW_OK;
 }
