@@ -24,8 +24,8 @@
 //   * every wait on an mbarrier gives up after kWaitNs, records
 //     BGW_ETIMEOUT in the status word and lets the CTA release its tensor
 //     memory and return.
-// A reduce kernel adds the segments in FP64 (fixed order: deterministic) and
-// writes both triangles of the FP64 chi.
+// A reduce kernel adds the segments (compensated FP32 sums in a fixed order:
+// deterministic) and writes both triangles of the FP64 chi.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -310,7 +310,7 @@ __global__ void maxabs_kernel(const float2* __restrict__ M, const double* __rest
   const long long n = K * ng;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const long long p = e / ng;
-    const float s = (float)sqrt(fabs(w[p]));
+    const float s = sqrtf(fabsf((float)w[p]));  // FP32: the split itself is FP32-based
     const float2 v = M[e];
     m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)) * s);
   }
@@ -347,7 +347,7 @@ __global__ void split_kernel(const float2* __restrict__ M, const double* __restr
     float2 v = make_float2(0.f, 0.f);
     if (p < K && g < ng) {
       v = M[(p0 + p) * ng + g];
-      const float s = (float)sqrt(fabs(w[p0 + p])) * sc;
+      const float s = sqrtf(fabsf((float)w[p0 + p])) * sc;
       v.x *= s;
       v.y *= s;
     }
@@ -393,14 +393,23 @@ __global__ void reduce_kernel(const float* __restrict__ work, int nseg, int ntil
   const int2 tl = tiles[tix];
   const int g = tl.x * BM + r, gp = tl.y * BN + c;
   if (g >= ng || gp >= ng || gp > g) return;
-  double re = 0.0, im = 0.0;
+  // compensated FP32 sum of the segments (two-sum; the FP64 pipe is far
+  // slower on this part), converted to FP64 once
+  float re = 0.f, rel = 0.f, im = 0.f, iml = 0.f;
   for (int s = 0; s < nseg; ++s) {
     const float* w = work + ((size_t)s * ntiles + tix) * 2 * per;
-    re += (double)w[r * BN + c];
-    im += (double)w[per + r * BN + c];
+    const float a = w[r * BN + c], b = w[per + r * BN + c];
+    float t = __fadd_rn(re, a);
+    float z = __fsub_rn(t, re);
+    rel = __fadd_rn(rel, __fadd_rn(__fsub_rn(re, __fsub_rn(t, z)), __fsub_rn(a, z)));
+    re = t;
+    t = __fadd_rn(im, b);
+    z = __fsub_rn(t, im);
+    iml = __fadd_rn(iml, __fadd_rn(__fsub_rn(im, __fsub_rn(t, z)), __fsub_rn(b, z)));
+    im = t;
   }
   const double f = factor * ldexp(1.0, -2 * scale_exp(maxbits, bf16));
-  double2 v = make_double2(re * f, im * f);
+  double2 v = make_double2(((double)re + (double)rel) * f, ((double)im + (double)iml) * f);
   double2* lo = chi + (size_t)g * ng + gp;
   if (accumulate) {
     const double2 o = *lo;
