@@ -485,14 +485,23 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
       for (int k0 = 0; k0 < ngmax; k0 += NB, ++k) {
         const int buf = k & 1;
         if (k >= 2) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf], 0));
-        sw_diag_kernel<<<nb, kDiagThreads, 0, s2>>>(sb, k0, c->d_status);
-        sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, s2>>>(sb, k0);
-        if ((rc = oz_slice(c, oz.get(), k0, ngmax, buf, s2)) != BGW_OK) return rc;
+        {
+          TimedScope ts(c, kTSweepChain, s2);
+          sw_diag_kernel<<<nb, kDiagThreads, 0, s2>>>(sb, k0, c->d_status);
+          sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, s2>>>(sb, k0);
+          if ((rc = oz_slice(c, oz.get(), k0, ngmax, buf, s2)) != BGW_OK) return rc;
+        }
         BGW_CUDA(c, cudaEventRecord(ev_slice, s2));
         if (k >= 1) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf ^ 1], 0));
-        if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 1, s2)) != BGW_OK) return rc;
+        {
+          TimedScope ts(c, kTOzUpdate, s2);
+          if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 1, s2)) != BGW_OK) return rc;
+        }
         BGW_CUDA(c, cudaStreamWaitEvent(st, ev_slice, 0));
-        if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 2, st)) != BGW_OK) return rc;
+        {
+          TimedScope ts(c, kTOzUpdate, st);
+          if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 2, st)) != BGW_OK) return rc;
+        }
         BGW_CUDA(c, cudaEventRecord(ev_rest[buf], st));
         BGW_CUDA(c, cudaGetLastError());
         c->launches += 5;

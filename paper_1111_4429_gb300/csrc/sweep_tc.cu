@@ -170,6 +170,18 @@ __global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBa
             (blockIdx.z == 0 ? sig : tau) + (size_t)buf * rows_total + row);
 }
 
+// (double)f for a finite float, built from its bits with integer operations
+// (the FP64 pipe, which a conversion would occupy, is the scarce one here).
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0u && m == 0u) return __longlong_as_double((long long)sign);  // +-0
+  if (e == 0u || e == 0xFFu) return (double)f;                          // denormal, inf, nan
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+                                          ((unsigned long long)m << 29)));
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
@@ -356,16 +368,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           // scale by sigma_i tau_j 2^-16 = 2^(ei + ej - 16): exact power of two,
           // applied to the FP32 pair when it stays a normal number, else in FP64
           const int ex = ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA;
-          double dr, di;
-          if (ex > -100 && ex < 100) {
-            dr = (double)ldexpf(hr[q], ex) + (double)ldexpf(lr[q], ex);
-            di = (double)ldexpf(hm[q], ex) + (double)ldexpf(lm[q], ex);
-          } else {
-            dr = ldexp((double)hr[q] + (double)lr[q], ex);
-            di = ldexp((double)hm[q] + (double)lm[q], ex);
-          }
           const double2 v = as[r * (BN + 1) + c0 + q];
-          M.A[(size_t)i * ng + j] = make_double2(v.x - dr, v.y - di);
+          double2 o;
+          if (ex > -100 && ex < 100) {
+            // four FP64 adds per element; scaling and conversion off the FP64 pipe
+            o.x = (v.x - f2d(ldexpf(hr[q], ex))) - f2d(ldexpf(lr[q], ex));
+            o.y = (v.y - f2d(ldexpf(hm[q], ex))) - f2d(ldexpf(lm[q], ex));
+          } else {
+            o.x = v.x - ldexp((double)hr[q] + (double)lr[q], ex);
+            o.y = v.y - ldexp((double)hm[q] + (double)lm[q], ex);
+          }
+          M.A[(size_t)i * ng + j] = o;
         }
       }
     }
