@@ -445,13 +445,16 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
       std::vector<int> ngs(nb);
       std::vector<double2*> As(nb);
       std::vector<const double2*> Cs(nb), Ps(nb);
+      std::vector<double2*> Ds(nb);
       for (int k = 0; k < nb; ++k) {
         ngs[k] = sb.m[k].ng;
         As[k] = sb.m[k].A;
         Cs[k] = sb.m[k].C;
         Ps[k] = sb.m[k].P;
+        Ds[k] = sb.m[k].Dinv;
       }
-      if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), oz.get())) != BGW_OK) return rc;
+      if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), Ds.data(), oz.get())) != BGW_OK)
+        return rc;
     }
     if (!tc_update) {
       for (int k0 = 0; k0 < ngmax; k0 += NB) {
@@ -462,8 +465,9 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
         c->launches += 3;
       }
     } else {
-      // Look-ahead: the chain that the next step waits for (diagonal block,
-      // panel, slices, then the update of the tiles touching the next block)
+      // Look-ahead: the chain that the next step waits for (panel, slices, then
+      // the update of the tiles touching the next block, whose CTA holding the
+      // next diagonal block also sweeps it)
       // runs on a high-priority side stream, while the main stream updates the
       // other tiles of the current step.  Dependencies:
       //   step k's chain waits for the main-stream update of step k-2 (same
@@ -487,7 +491,9 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
         if (k >= 2) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf], 0));
         {
           TimedScope ts(c, kTSweepChain, s2);
-          sw_diag_kernel<<<nb, kDiagThreads, 0, s2>>>(sb, k0, c->d_status);
+          // the diagonal block of step k >= 1 was swept by step k-1's
+          // next-block update (the CTA of the tile holding it)
+          if (k == 0) sw_diag_kernel<<<nb, kDiagThreads, 0, s2>>>(sb, k0, c->d_status);
           sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, s2>>>(sb, k0);
           if ((rc = oz_slice(c, oz.get(), k0, ngmax, buf, s2)) != BGW_OK) return rc;
         }

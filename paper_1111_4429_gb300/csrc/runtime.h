@@ -205,7 +205,7 @@ struct OzPlan;
 OzPlan* oz_plan_new();
 void oz_plan_delete(OzPlan* p);
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               OzPlan* plan);
+               double2* const* D, OzPlan* plan);
 int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);
 int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaStream_t st);
 

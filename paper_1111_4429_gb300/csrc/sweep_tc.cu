@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "runtime.h"
+#include "sweep_common.cuh"
 
 namespace bgw {
 
@@ -106,6 +107,7 @@ struct OzMat {
   double2* A;
   const double2* C;   // [ng][NB]
   const double2* P;   // [ng][NB]
+  double2* Dinv;      // [NB][NB] D^-1 of the next diagonal block (written by mode 1)
   int ng;
   int row_off;        // first slice row of this matrix (multiple of BM)
 };
@@ -239,8 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* us = smem;                  // S x 16 KiB
   unsigned char* vs = smem + S * kUTile;     // S x 4 KiB
-  double2* as = reinterpret_cast<double2*>(vs + S * kVTile);  // A tile [BM][BN + 1]
-  uint64_t* full = reinterpret_cast<uint64_t*>(as + BM * (BN + 1));
+  uint64_t* full = reinterpret_cast<uint64_t*>(vs + S * kVTile);
   uint64_t* done = full + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -259,20 +260,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
-  // Prefetch this thread's row of the A tile into shared memory while the
-  // slices load and the MMAs run (the epilogue then reads A from smem).
-  {
-    const int r = threadIdx.x, i = i0 + r;
-    if (i < ng) {
-      const double2* src = M.A + (size_t)i * ng + j0;
-      const uint32_t dst = smem_u32(as + r * (BN + 1));
-      const int jn = min(BN, ng - j0);
-      for (int q = 0; q < jn; ++q)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * q), "l"(src + q) : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-
   if (warp == 0 && lane == 0) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(full)),
                  "r"((uint32_t)(S * (kUTile + kVTile)))
@@ -324,7 +311,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (!have && threadIdx.x == 0) atomicExch(status, (int)kDevTimeout);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncwarp();
-  asm volatile("cp.async.wait_all;" ::: "memory");
   if (have && ok) {
     const int r = warp * 32 + lane;
     const int i = i0 + r;
@@ -368,7 +354,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           // scale by sigma_i tau_j 2^-16 = 2^(ei + ej - 16): exact power of two,
           // applied to the FP32 pair when it stays a normal number, else in FP64
           const int ex = ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA;
-          const double2 v = as[r * (BN + 1) + c0 + q];
+          double2* dst = M.A + (size_t)i * ng + j;
+          const double2 v = *dst;
           double2 o;
           if (ex > -100 && ex < 100) {
             // four FP64 adds per element; scaling and conversion off the FP64 pipe
@@ -378,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             o.x = v.x - ldexp((double)hr[q] + (double)lr[q], ex);
             o.y = v.y - ldexp((double)hm[q] + (double)lm[q], ex);
           }
-          M.A[(size_t)i * ng + j] = o;
+          *dst = o;
         }
       }
     }
@@ -388,6 +375,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+  // The tile holding the next diagonal block (rows and columns k1 .. k1+31)
+  // now has that block's final values: sweep it here, which leaves the next
+  // step's D^-1 in Dinv and -D^-1 in A_K1K1 without a separate launch.
+  // (I, J, mode) are the same for every thread of the CTA; the success
+  // flags are combined by the barrier so that all threads agree.
+  if (mode == 1 && I == In && J == Jn && __syncthreads_and(have && ok)) {
+    __shared__ DiagSmem dsm;
+    const int kb1 = min(NB, ng - k1);
+    for (int e = threadIdx.x; e < NB * NB; e += kThreads) {
+      const int r = e / NB, c2 = e % NB;
+      if (r < kb1 && c2 <= r) dsm.L[r][c2] = M.A[(size_t)(k1 + r) * ng + k1 + c2];
+    }
+    diag_sweep_smem_n<kThreads>(dsm, kb1, threadIdx.x, status);
+    for (int e = threadIdx.x; e < NB * NB; e += kThreads) {
+      const int r = e / NB, c2 = e % NB;
+      if (r >= kb1 || c2 >= kb1) continue;
+      const double2 v = (r >= c2) ? dsm.L[r][c2] : make_double2(dsm.L[c2][r].x, -dsm.L[c2][r].y);
+      M.Dinv[r * NB + c2] = make_double2(-v.x, -v.y);
+      if (r >= c2) M.A[(size_t)(k1 + r) * ng + k1 + c2] = v;
+    }
   }
 }
 
@@ -411,7 +419,7 @@ struct OzPlan {
 };
 
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               OzPlan* plan) {
+               double2* const* D, OzPlan* plan) {
   using namespace oz;
   if (nmat > kBatch) return fail(c, BGW_EUNSUPPORTED, "tensor-core inverse: at most %d matrices per batch", kBatch);
   if (!g_encode_oz) {
@@ -429,6 +437,7 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
     plan->batch.m[m].A = A[m];
     plan->batch.m[m].C = C[m];
     plan->batch.m[m].P = P[m];
+    plan->batch.m[m].Dinv = D[m];
     plan->batch.m[m].ng = ng[m];
     plan->batch.m[m].row_off = rows;
     rows += (ng[m] + BM - 1) / BM * BM;
@@ -460,7 +469,8 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return fail(c, BGW_ECUDA, "tensor-core inverse: tensor map encoding failed");
-  const size_t smem = (size_t)S * (kUTile + kVTile) + sizeof(double2) * BM * (BN + 1) + 1024 + 64;
+  // about 142 KiB: leaves room on each SM for the look-ahead chain's kernels
+  const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
   BGW_CUDA(c, cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   return BGW_OK;
 }
@@ -487,7 +497,7 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
     const int nI = (ngmax + BM - 1) / BM, nJ = (ngmax + BN - 1) / BN, In = k1 / BM;
     grid = std::min(4 * In + 4, nJ) + std::max(0, nI - In - 1);
   }
-  const size_t smem = (size_t)S * (kUTile + kVTile) + sizeof(double2) * BM * (BN + 1) + 1024 + 64;
+  const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
   update_kernel<<<dim3(grid, plan->nmat), kThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,
                                                                 plan->rows_total, buf, mode, plan->sig.as<int>(),
                                                                 plan->tau.as<int>(), c->d_status);
