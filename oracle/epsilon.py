@@ -181,13 +181,38 @@ def chi_entries(M_rows_g: np.ndarray, M_rows_gp: np.ndarray, w: np.ndarray,
 # Dielectric matrix and its inverse, Eqs. (epsilon), (untruncated_bare_coulomb)
 # ---------------------------------------------------------------------------
 
-def coulomb(bvec: np.ndarray, q_frac: Sequence[float], geps: np.ndarray) -> np.ndarray:
-    """v(q+G) = 4 pi / |q+G|^2 with q+G in Cartesian bohr^-1 (rows of bvec are b_i)."""
+def coulomb(bvec: np.ndarray, q_frac: Sequence[float], geps: np.ndarray, model: str = "bulk",
+            rc: float = 0.0) -> np.ndarray:
+    """v(q+G) with q+G in Cartesian bohr^-1 (rows of bvec are b_i).
+
+    bulk (Eq. untruncated_bare_coulomb): 4 pi / k^2.
+    sphere (Section "Coulomb Interaction", spherical truncation at r_c):
+        4 pi / k^2 (1 - cos(r_c k)), finite at k = 0 (limit 2 pi r_c^2).
+    slab (same Section, truncation at z_c along the slab normal z):
+        4 pi / k^2 (1 - exp(-k_xy z_c) cos(k_z z_c)), divergent at k = 0.
+
+    The brackets are evaluated through the identities 1 - cos x = 2 sin^2(x/2)
+    and 1 - e^-a cos b = -expm1(-a) + e^-a 2 sin^2(b/2), whose terms are all
+    non-negative, so small r_c k loses no digits to cancellation.
+    """
     k = (np.asarray(geps, dtype=np.float64) + np.asarray(q_frac, dtype=np.float64)) @ np.asarray(bvec, dtype=np.float64)
     k2 = np.einsum("ij,ij->i", k, k)
+    if model == "sphere":
+        v = np.empty_like(k2)
+        nz = k2 > 0.0
+        kk = np.sqrt(k2[nz])
+        v[nz] = 4.0 * math.pi / k2[nz] * (2.0 * np.sin(0.5 * rc * kk) ** 2)
+        v[~nz] = 2.0 * math.pi * rc * rc
+        return v
     if np.any(k2 == 0.0):
-        raise ValueError("q+G = 0: the bare Coulomb factor diverges")
-    return 4.0 * math.pi / k2
+        raise ValueError("q+G = 0: the Coulomb factor diverges for this model")
+    if model == "bulk":
+        return 4.0 * math.pi / k2
+    if model == "slab":
+        kxy = np.sqrt(k[:, 0] ** 2 + k[:, 1] ** 2)
+        bracket = -np.expm1(-kxy * rc) + np.exp(-kxy * rc) * 2.0 * np.sin(0.5 * k[:, 2] * rc) ** 2
+        return 4.0 * math.pi / k2 * bracket
+    raise ValueError(f"unknown Coulomb model {model}")
 
 
 def eps_sym(chi_m: np.ndarray, v: np.ndarray) -> np.ndarray:
@@ -204,6 +229,12 @@ def eps_asym(chi_m: np.ndarray, v: np.ndarray) -> np.ndarray:
 def screened_w(epsinv_asym: np.ndarray, v: np.ndarray) -> np.ndarray:
     """W_GG' = eps^-1_GG' v(q+G') (Eq. screened_interaction)."""
     return epsinv_asym * v[None, :]
+
+
+def screened_w_sym(epsinv_sym: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """The same W from the symmetrized inverse: W = V^{1/2} eps~^-1 V^{1/2}."""
+    s = np.sqrt(v)
+    return s[:, None] * epsinv_sym * s[None, :]
 
 
 def inv_gauss_jordan(a: np.ndarray) -> np.ndarray:
@@ -239,7 +270,7 @@ def epsinv_sym(chi_m: np.ndarray, v: np.ndarray, tier: int = 2):
     return e, (inv_gauss_jordan(e) if tier == 1 else inv(e))
 
 
-def solve(system, omega: Optional[float] = None, tier: int = 2):
+def solve(system, omega: Optional[float] = None, tier: int = 2, model: str = "bulk", rc: float = 0.0):
     """Whole chain for one q-point: returns dict(M, chi, eps, epsinv, v)."""
     if tier == 1:
         M = mtxel_direct(system.gv, system.cv, system.gc, system.cc, system.geps)
@@ -247,6 +278,6 @@ def solve(system, omega: Optional[float] = None, tier: int = 2):
         M = mtxel_fft(system.gv, system.cv, system.gc, system.cc, system.geps, system.fft)
     w = chi_weights(system.ev, system.ec, omega)
     x = chi_direct(M, w, system.omega) if tier == 1 else chi(M, w, system.omega)
-    v = coulomb(system.bvec, system.q_frac, system.geps)
+    v = coulomb(system.bvec, system.q_frac, system.geps, model, rc)
     e, ei = epsinv_sym(x, v, tier=tier)
     return dict(M=M, chi=x, eps=e, epsinv=ei, v=v)

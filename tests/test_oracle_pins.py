@@ -308,3 +308,52 @@ def test_imaginary_frequency_limits_and_monotonicity():
     xinf = oracle.chi(m, oracle.chi_weights(s.ev, s.ec, 1e6), s.omega)
     _, eiinf = oracle.epsinv_sym(xinf, v)
     assert np.abs(eiinf - np.eye(s.ng)).max() < 1e-8
+
+
+# ------------------------------------------------------------ Coulomb truncations and W
+
+def test_truncated_coulomb_closed_forms():
+    bvec, _ = synth.cubic_cell(10.0)
+    b = 2 * math.pi / 10.0
+    geps = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 1], [1, 1, 2]], dtype=np.int32)
+    rc = 5.0
+    vs = oracle.coulomb(bvec, (0, 0, 0), geps, "sphere", rc)
+    assert abs(vs[0] - 2 * math.pi * rc * rc) < 1e-12             # k -> 0 limit
+    assert abs(vs[1] - 4 * math.pi / b ** 2 * (1 - math.cos(rc * b))) < 1e-12
+    # k r_c = 2 pi: the truncated interaction vanishes
+    v0 = oracle.coulomb(bvec, (0, 0, 0), np.array([[1, 0, 0]], dtype=np.int32), "sphere", 10.0)
+    assert abs(v0[0]) < 1e-12
+    # small k: 4 pi/k^2 (1 - cos(r_c k)) -> 2 pi r_c^2 (1 - (r_c k)^2 / 12)
+    tiny = oracle.coulomb(bvec, (1e-4, 0, 0), np.array([[0, 0, 0]], dtype=np.int32), "sphere", rc)
+    kk = 1e-4 * b
+    assert abs(tiny[0] - 2 * math.pi * rc * rc * (1 - (rc * kk) ** 2 / 12)) < 1e-9
+    zc = 5.0
+    vl = oracle.coulomb(bvec, (0.1, 0, 0), geps, "slab", zc)
+    k0 = 0.1 * b
+    assert abs(vl[0] - 4 * math.pi / k0 ** 2 * (1 - math.exp(-k0 * zc))) < 1e-9  # in-plane: cos(0) = 1
+    kz = b                                                                          # [0,0,1] + q: k_xy = 0.1 b
+    kxy = 0.1 * b
+    expect = 4 * math.pi / (kxy ** 2 + kz ** 2) * (1 - math.exp(-kxy * zc) * math.cos(kz * zc))
+    assert abs(vl[2] - expect) < 1e-12
+    # both truncations are bounded by twice the bulk interaction and are >= 0
+    vb = oracle.coulomb(bvec, (0.1, 0.2, 0.3), geps)
+    for model in ("sphere", "slab"):
+        vt = oracle.coulomb(bvec, (0.1, 0.2, 0.3), geps, model, 3.0)
+        assert np.all(vt >= 0) and np.all(vt <= 2 * vb + 1e-12)
+    with pytest.raises(ValueError):
+        oracle.coulomb(bvec, (0, 0, 0), geps, "slab", zc)
+
+
+def test_screened_w_routes_agree_and_hermitian_truncated():
+    s = synth.config_system("c0")
+    for model, rc in (("bulk", 0.0), ("sphere", 4.0), ("slab", 5.13)):
+        r = oracle.solve(s, model=model, rc=rc)
+        v = r["v"]
+        w_sym = oracle.screened_w_sym(r["epsinv"], v)
+        # the paper's route: asymmetric eps = I - v chi, W = eps^-1 v
+        w_asym = oracle.screened_w(oracle.inv(oracle.eps_asym(r["chi"], v)), v)
+        assert np.linalg.norm(w_sym - w_asym) <= 1e-12 * np.linalg.norm(w_asym)
+        assert np.linalg.norm(w_sym - np.conj(w_sym).T) <= 1e-14 * np.linalg.norm(w_sym)
+        # W = v^1/2 eps~^-1 v^1/2 with 0 < eps~^-1 <= I: 0 <= W <= V
+        lam = np.linalg.eigvalsh(np.diag(v) - w_sym)
+        assert lam.min() >= -1e-12 * v.max()
