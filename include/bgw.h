@@ -72,16 +72,37 @@ enum { BGW_PREC_FP64 = 0, BGW_PREC_MIX_FP16 = 1, BGW_PREC_MIX_BF16 = 2 };
 
 typedef struct bgw_ctx bgw_ctx;
 
+/* Coulomb interaction v(k), k = (q + G) B in bohr^-1, Hartree units
+ * (Section "Coulomb Interaction"):
+ *  BGW_COULOMB_BULK   v = 4 pi / k^2 (Eq. untruncated_bare_coulomb);
+ *                     k = 0 is rejected (EINVAL).
+ *  BGW_COULOMB_SPHERE v = 4 pi / k^2 (1 - cos(k r_c)), the interaction cut
+ *                     off beyond a sphere of radius r_c = coulomb_cut; finite
+ *                     at k = 0, where it takes its limit 2 pi r_c^2.
+ *  BGW_COULOMB_SLAB   v = 4 pi / k^2 (1 - exp(-k_xy z_c) cos(k_z z_c)), cut off
+ *                     beyond |z| = z_c = coulomb_cut along Cartesian z (the
+ *                     slab normal), k_xy = (k_x^2 + k_y^2)^{1/2}; k = 0 is
+ *                     rejected (the slab form diverges there as 1/k).
+ * Both truncated forms are evaluated as 2 sin^2(k r_c / 2) and
+ * -expm1(-k_xy z_c) + exp(-k_xy z_c) 2 sin^2(k_z z_c / 2), which equal the
+ * brackets above and lose no digits at small k.                            */
+enum { BGW_COULOMB_BULK = 0, BGW_COULOMB_SPHERE = 1, BGW_COULOMB_SLAB = 2 };
+
 /* Cell and q-point.  bvec rows are the reciprocal lattice vectors b1,b2,b3
  * in bohr^-1 (Appendix: reciprocal lattice vectors); omega is the cell volume
  * in bohr^3; q_frac is q in crystal coordinates; fft is the FFT grid.  This
  * build requires a cubic grid fft[0] = fft[1] = fft[2] = n with n in
- * {8,10,12,16,20,24,30,32,36,40,48,50,60,64}.                               */
+ * {8,10,12,16,20,24,30,32,36,40,48,50,60,64}.  coulomb selects v (a
+ * zero-filled cell is the bulk interaction); coulomb_cut is r_c or z_c in
+ * bohr, finite and > 0 for the truncated forms, ignored for bulk.  EINVAL
+ * for another model or a bad cut length.                                   */
 typedef struct bgw_cell {
   double bvec[3][3];
   double omega;
   double q_frac[3];
   int fft[3];
+  int coulomb;
+  double coulomb_cut;
 } bgw_cell;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
@@ -128,8 +149,18 @@ int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
  *    in FP16, accumulates every slice product exactly in FP32 and combines
  *    them in double-FP32 before the FP64 subtraction: its error is near
  *    2^-48 of the update's scale (FP64 FMA: 2^-53).                        */
+/*  BGW_OPT_HEAD: the q0 head of the mixed precisions.  At a small q0 the
+ *    head column M_vc(G = 0) is O(|q0|) while v(q0) = 4 pi / |q0|^2, so the
+ *    FP32 FFTs' absolute error on it (near 2^-24 |M|) becomes a relative
+ *    error near 2^-24 / |q0| in v chi_00, the macroscopic response.  With
+ *    the head on, bgw_epsilon, bgw_epsilon_batch and the server compute
+ *    M_vc(0) = sum_G conj(c_v(G)) c_c(G) as an FP64 dot product, leave it out
+ *    of the tensor-core sum and add row and column G = 0 of chi in FP64.
+ *    -1 (default): on when the epsilon list holds G = 0, the interaction is
+ *    bulk or slab and |q| < 0.02 min_i |b_i|; 0: off; 1: on whenever G = 0
+ *    is in the list.  No effect on BGW_PREC_FP64 or on bgw_chi_sum.         */
 enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3, BGW_OPT_CHI_CHUNK_PAIRS = 4,
-       BGW_OPT_INVERSE = 5 };
+       BGW_OPT_INVERSE = 5, BGW_OPT_HEAD = 6 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
 
 /* With BGW_OPT_TIMING = 1 the context records CUDA events around its main
@@ -186,7 +217,8 @@ int bgw_chi_sum(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng,
  * bgw_epsinv -- symmetrized dielectric matrix and its inverse (Eq. epsilon
  * with the symmetric Coulomb form v^{1/2}(q+G) v^{1/2}(q+G')):
  *   eps~[G][G'] = delta_GG' - sqrt(v_G) chi[G][G'] sqrt(v_G'),
- *   v_G = 4 pi / |(q + G) B|^2,  then epsinv = (eps~)^-1   (FP64 always).
+ *   v_G = v((q + G) B) of the cell's Coulomb model (4 pi / |(q + G) B|^2
+ *   for bulk),  then epsinv = (eps~)^-1   (FP64 always).
  * Batched over nmat independent matrices of sizes ng[i] (may differ):
  *   cells[i]  host, q and bvec of matrix i
  *   geps[i]   host int32 [ng[i]][3]
@@ -199,11 +231,29 @@ int bgw_chi_sum(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng,
  * Hermitian form) that reads and updates only the lower triangle of chi's
  * Hermitian eps~, then writes both triangles of epsinv.  Elimination without
  * pivoting is backward stable for such matrices.
- * EINVAL if some |q+G| = 0.  A zero or non-finite pivot sets BGW_ENUMERIC,
- * reported by bgw_sync.                                                    */
+ * EINVAL if some |q+G| = 0 under the bulk or slab interaction.  A zero or
+ * non-finite pivot sets BGW_ENUMERIC, reported by bgw_sync.                */
 int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
                const int32_t* const* geps, const void* const* chi,
                void* const* eps, void* const* epsinv, void* stream);
+
+/* ------------------------------------------------------------------------
+ * bgw_screened_w -- the screened Coulomb interaction (Eq.
+ * screened_interaction), W_GG' = eps^-1_GG' v(q+G'), from the symmetrized
+ * inverse bgw_epsinv returns: since eps~ = v^{-1/2} eps v^{1/2},
+ *   W[G][G'] = sqrt(v_G) epsinv[G][G'] sqrt(v_G'),
+ * with v of the cell's Coulomb model (see bgw_cell).  W is Hermitian.
+ * Batched over nmat matrices like bgw_epsinv:
+ *   cells[i]  host, q, bvec and Coulomb model of matrix i
+ *   geps[i]   host int32 [ng[i]][3]
+ *   epsinv[i] device c128 [ng[i]][ng[i]] (read)
+ *   W[i]      device c128 [ng[i]][ng[i]] (written; may equal epsinv[i]
+ *             for an in-place update, must not overlap it otherwise)
+ * One pass over HBM: 16 B read and 16 B written per element.
+ * EINVAL on NULL pointers, bad sizes or |q+G| = 0 where v diverges.       */
+int bgw_screened_w(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
+                   const int32_t* const* geps, const void* const* epsinv,
+                   void* const* W, void* stream);
 
 /* ------------------------------------------------------------------------
  * bgw_epsinv_noalloc -- bgw_epsinv for one matrix without any device

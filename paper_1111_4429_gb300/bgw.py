@@ -25,10 +25,14 @@ PREC = {"fp64": BGW_PREC_FP64, "mix_fp16": BGW_PREC_MIX_FP16, "mix_bf16": BGW_PR
 # Every symbol include/bgw.h declares.
 EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_stats", "bgw_launch_count",
            "bgw_mtxel",
-           "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_epsilon",
+           "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_screened_w",
+           "bgw_epsilon",
            "bgw_epsilon_batch", "bgw_serve_open", "bgw_serve_submit", "bgw_serve_poll", "bgw_serve_cancel",
            "bgw_serve_close")
 BGW_OPT_CHI_SEGMENT_PAIRS, BGW_OPT_TIMING, BGW_OPT_AUTOTUNE, BGW_OPT_CHI_CHUNK_PAIRS, BGW_OPT_INVERSE = 1, 2, 3, 4, 5
+BGW_OPT_HEAD = 6
+BGW_COULOMB_BULK, BGW_COULOMB_SPHERE, BGW_COULOMB_SLAB = 0, 1, 2
+COULOMB_MODELS = {"bulk": BGW_COULOMB_BULK, "sphere": BGW_COULOMB_SPHERE, "slab": BGW_COULOMB_SLAB}
 
 
 class BgwError(RuntimeError):
@@ -39,7 +43,8 @@ class BgwError(RuntimeError):
 
 class Cell(ctypes.Structure):
     _fields_ = [("bvec", (ctypes.c_double * 3) * 3), ("omega", ctypes.c_double),
-                ("q_frac", ctypes.c_double * 3), ("fft", ctypes.c_int * 3)]
+                ("q_frac", ctypes.c_double * 3), ("fft", ctypes.c_int * 3),
+                ("coulomb", ctypes.c_int), ("coulomb_cut", ctypes.c_double)]
 
 
 class Problem(ctypes.Structure):
@@ -64,8 +69,10 @@ class Result(ctypes.Structure):
                 ("hbm_bytes", ctypes.c_uint64)]
 
 
-def make_cell(bvec, omega: float, q_frac, n: int) -> Cell:
+def make_cell(bvec, omega: float, q_frac, n: int, coulomb: str = "bulk", cut: float = 0.0) -> Cell:
     c = Cell()
+    c.coulomb = COULOMB_MODELS[coulomb]
+    c.coulomb_cut = float(cut)
     b = np.asarray(bvec, dtype=np.float64)
     for i in range(3):
         for j in range(3):
@@ -76,8 +83,8 @@ def make_cell(bvec, omega: float, q_frac, n: int) -> Cell:
     return c
 
 
-def system_cell(s) -> Cell:
-    return make_cell(s.bvec, s.omega, s.q_frac, s.fft)
+def system_cell(s, coulomb: str = "bulk", cut: float = 0.0) -> Cell:
+    return make_cell(s.bvec, s.omega, s.q_frac, s.fft, coulomb, cut)
 
 
 _lib = None
@@ -241,6 +248,17 @@ class Context:
         self._check(self.lib.bgw_epsinv(self.h, n, carr, ng, gp, cp, ep, ip, _stream(stream)))
         return epsinvs
 
+    def screened_w(self, cells: Sequence[Cell], gepss: Sequence[np.ndarray], epsinvs, ws, stream=None):
+        n = len(cells)
+        carr = (Cell * n)(*cells)
+        keep = [_i32(g) for g in gepss]
+        ng = (ctypes.c_int * n)(*[k[0].shape[0] for k in keep])
+        gp = (ctypes.POINTER(ctypes.c_int32) * n)(*[k[1] for k in keep])
+        ip = (ctypes.c_void_p * n)(*[_ptr(x) for x in epsinvs])
+        wp = (ctypes.c_void_p * n)(*[_ptr(x) for x in ws])
+        self._check(self.lib.bgw_screened_w(self.h, n, carr, ng, gp, ip, wp, _stream(stream)))
+        return ws
+
     def epsilon(self, cell: Cell, gv, cv, ev, gc, cc, ec, geps, omega, prec: int, nc_chunk: int, chi, epsinv,
                 stream=None):
         gv_, gvp = _i32(gv)
@@ -255,10 +273,12 @@ class Context:
                                          omp, prec, nc_chunk, _ptr(chi), _ptr(epsinv), _stream(stream)))
         return epsinv
 
-    def epsilon_batch(self, systems, cvs, ccs, omega, prec: int, epsinvs, stream=None):
+    def epsilon_batch(self, systems, cvs, ccs, omega, prec: int, epsinvs, stream=None, cells=None):
         """bgw_epsilon_batch over q-points: `systems` give the host arrays (G
         lists, energies, cell), `cvs`/`ccs` the device coefficient tensors,
-        `epsinvs` the device outputs [max(1,nfreq)][ng][ng] per q-point."""
+        `epsinvs` the device outputs [max(1,nfreq)][ng][ng] per q-point;
+        `cells` (optional) replaces the systems' cells, e.g. to select a
+        truncated Coulomb interaction."""
         n = len(systems)
         keep = []
         probs = (Problem * n)()
@@ -270,7 +290,7 @@ class Context:
             ec_, ecp = _f64(s.ec)
             keep += [gv_, gc_, ge_, ev_, ec_]
             p = probs[k]
-            p.cell = make_cell(s.bvec, s.omega, s.q_frac, s.fft)
+            p.cell = cells[k] if cells is not None else make_cell(s.bvec, s.omega, s.q_frac, s.fft)
             p.nv, p.npw_v, p.gv, p.cv, p.ev = cvs[k].shape[0], gv_.shape[0], gvp, _ptr(cvs[k]), evp
             p.nc, p.npw_c, p.gc, p.cc, p.ec = ccs[k].shape[0], gc_.shape[0], gcp, _ptr(ccs[k]), ecp
             p.ng, p.geps = ge_.shape[0], gep

@@ -1,5 +1,6 @@
 // extern "C" entry points declared in include/bgw.h: argument checks, plan
 // lookup, scratch management and the order of the kernel launches.
+#include <cstddef>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -31,6 +32,11 @@ struct DeviceGuard {
 };
 
 Ctx* impl(bgw_ctx* c) { return c ? &c->impl : nullptr; }
+
+// The Python binding mirrors this layout field by field.
+static_assert(offsetof(bgw_cell, fft) == 104 && offsetof(bgw_cell, coulomb) == 116 &&
+                  offsetof(bgw_cell, coulomb_cut) == 120 && sizeof(bgw_cell) == 128,
+              "bgw_cell layout");
 
 int check_cell(Ctx* c, const bgw_cell* cell, int* n) {
   if (!cell) return fail(c, BGW_EINVAL, "cell is NULL");
@@ -86,16 +92,12 @@ int check_prec(Ctx* c, int prec) {
 }
 
 int check_q(Ctx* c, const bgw_cell* cell, int ng, const int32_t* geps) {
-  for (int i = 0; i < ng; ++i) {
-    double k2 = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      double kd = 0.0;
-      for (int a = 0; a < 3; ++a) kd += (geps[3 * i + a] + cell->q_frac[a]) * cell->bvec[a][d];
-      k2 += kd * kd;
-    }
-    if (!(k2 > 0.0)) return fail(c, BGW_EINVAL, "|q+G| = 0 at geps[%d]: the bare Coulomb factor diverges", i);
-  }
-  return BGW_OK;
+  int what, bad;
+  if (coulomb_check(cell, ng, geps, &what, &bad) == BGW_OK) return BGW_OK;
+  if (what == 1) return fail(c, BGW_EINVAL, "unknown Coulomb model %d", cell->coulomb);
+  if (what == 2) return fail(c, BGW_EINVAL, "Coulomb cut length %g must be finite and > 0", cell->coulomb_cut);
+  return fail(c, BGW_EINVAL, "|q+G| = 0 at geps[%d]: the %s Coulomb factor diverges", bad,
+              cell->coulomb == BGW_COULOMB_SLAB ? "slab-truncated" : "bare");
 }
 
 bool is_device_ptr(const void* p) {
@@ -252,6 +254,11 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
     c->inverse_mode = (int)value;
     return BGW_OK;
   }
+  if (option == BGW_OPT_HEAD) {
+    if (value < -1 || value > 1) return fail(c, BGW_EINVAL, "head mode is -1, 0 or 1");
+    c->head_mode = (int)value;
+    return BGW_OK;
+  }
   if (option == BGW_OPT_AUTOTUNE) {
     if (value != 0 && value != 1) return fail(c, BGW_EINVAL, "autotune is 0 or 1");
     c->autotune = value == 1;
@@ -344,18 +351,47 @@ int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, con
   if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::vector<const int32_t*> dgeps(nmat);
-  std::vector<const double*> bv(nmat), qv(nmat);
+  std::vector<const bgw_cell*> cp(nmat);
   for (int m = 0; m < nmat; ++m) {
     const void* dg;
     if ((rc = upload_cached(c, geps[m], (size_t)ng[m] * 3 * sizeof(int32_t), st, &dg)) != BGW_OK) return rc;
     dgeps[m] = static_cast<const int32_t*>(dg);
-    bv[m] = &cells[m].bvec[0][0];
-    qv[m] = cells[m].q_frac;
+    cp[m] = &cells[m];
   }
-  if ((rc = epsinv_batch_run(c, nmat, ng, bv.data(), qv.data(), dgeps.data(), chi, eps, epsinv, st,
-                             c->inverse_mode == 1)) != BGW_OK)
+  if ((rc = epsinv_batch_run(c, nmat, ng, cp.data(), dgeps.data(), chi, eps, epsinv, st, c->inverse_mode == 1)) !=
+      BGW_OK)
     return rc;
   return BGW_OK;
+}
+
+int bgw_screened_w(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, const int32_t* const* geps,
+                   const void* const* epsinv, void* const* W, void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  if (nmat <= 0 || !cells || !ng || !geps || !epsinv || !W) return fail(c, BGW_EINVAL, "NULL argument array");
+  int rc;
+  for (int m = 0; m < nmat; ++m) {
+    if (ng[m] <= 0 || !geps[m] || !epsinv[m] || !W[m])
+      return fail(c, BGW_EINVAL, "matrix %d: bad size or NULL pointer", m);
+    if ((rc = check_q(c, &cells[m], ng[m], geps[m])) != BGW_OK) return rc;
+    if (W[m] != epsinv[m]) {
+      const size_t bytes = (size_t)ng[m] * ng[m] * sizeof(double2);
+      const char *a = static_cast<const char*>(epsinv[m]), *b = static_cast<const char*>(W[m]);
+      if (a < b + bytes && b < a + bytes) return fail(c, BGW_EINVAL, "matrix %d: W overlaps epsinv", m);
+    }
+  }
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<const int32_t*> dgeps(nmat);
+  std::vector<const bgw_cell*> cp(nmat);
+  for (int m = 0; m < nmat; ++m) {
+    const void* dg;
+    if ((rc = upload_cached(c, geps[m], (size_t)ng[m] * 3 * sizeof(int32_t), st, &dg)) != BGW_OK) return rc;
+    dgeps[m] = static_cast<const int32_t*>(dg);
+    cp[m] = &cells[m];
+  }
+  return screened_w_run(c, nmat, ng, cp.data(), dgeps.data(), epsinv, W, st);
 }
 
 }  // extern "C"
@@ -388,13 +424,24 @@ int run_batch(Ctx* c, int nq, const bgw_problem* pr, int nfreq, const double* de
     if ((rc = get_band_plan(c, n, p.npw_c, p.gc, st, &bpc)) != BGW_OK) return rc;
     if ((rc = get_pair_plan(c, n, p.ng, p.geps, st, &pp)) != BGW_OK) return rc;
     if ((rc = mtxel_run(c, n, prec, p.nv, bpv, p.cv, p.nc, bpc, p.cc, pp, sM.ptr, st)) != BGW_OK) return rc;
+    HeadPlan hp;
+    Scratch sH;
+    sH.pool = &c->pool;
+    if ((rc = head_prepare(c, &p.cell, p.npw_v, p.gv, p.npw_c, p.gc, p.ng, p.geps, prec, st, &hp)) != BGW_OK)
+      return rc;
+    if (hp.g0 >= 0) {
+      if ((rc = c->pool.alloc((size_t)p.nv * p.nc * sizeof(double2), &sH.ptr)) != BGW_OK)
+        return fail(c, rc, "head scratch");
+      if ((rc = head_dot(c, &hp, p.nv, p.cv, p.npw_v, p.nc, p.cc, p.ng, sM.ptr, sH.as<double2>(), st)) != BGW_OK)
+        return rc;
+    }
     if ((rc = chi_run(c, prec, p.nv, p.nc, p.ng, sM.ptr, static_cast<const double*>(dev_ev[q]),
-                      static_cast<const double*>(dev_ec[q]), nfreq, dev_om, 4.0 / p.cell.omega, 0, sChi.ptr, st)) !=
-        BGW_OK)
+                      static_cast<const double*>(dev_ec[q]), nfreq, dev_om, 4.0 / p.cell.omega, 0, sChi.ptr, st,
+                      &hp, sH.as<double2>())) != BGW_OK)
       return rc;
     const size_t n2 = (size_t)p.ng * p.ng * sizeof(double2);
     std::vector<int> ngv(nrow, p.ng);
-    std::vector<const double*> bv(nrow, &p.cell.bvec[0][0]), qv(nrow, p.cell.q_frac);
+    std::vector<const bgw_cell*> cp(nrow, &p.cell);
     std::vector<const int32_t*> gv(nrow, static_cast<const int32_t*>(dev_geps[q]));
     std::vector<const void*> chis(nrow);
     std::vector<void*> invs(nrow);
@@ -402,7 +449,7 @@ int run_batch(Ctx* c, int nq, const bgw_problem* pr, int nfreq, const double* de
       chis[f] = static_cast<char*>(sChi.ptr) + f * n2;
       invs[f] = static_cast<char*>(epsinv[q]) + f * n2;
     }
-    if ((rc = epsinv_batch_run(c, nrow, ngv.data(), bv.data(), qv.data(), gv.data(), chis.data(), nullptr,
+    if ((rc = epsinv_batch_run(c, nrow, ngv.data(), cp.data(), gv.data(), chis.data(), nullptr,
                                invs.data(), st, use_tc_inverse(c, prec))) != BGW_OK)
       return rc;
   }
@@ -437,6 +484,8 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   uint64_t key = fnv1a(&nq, sizeof(nq), fnv1a(&prec, sizeof(prec), fnv1a(&nfreq, sizeof(nfreq))));
   if (nfreq > 0) key = fnv1a(omega, nfreq * sizeof(double), key);
   key = fnv1a(&st, sizeof(st), key);
+  const int modes[2] = {c->inverse_mode, c->head_mode};
+  key = fnv1a(modes, sizeof(modes), key);
   for (int q = 0; q < nq; ++q) {
     const bgw_problem& p = problems[q];
     key = fnv1a(&p.cell, sizeof(p.cell), key);
@@ -561,18 +610,27 @@ int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
   if ((rc = upload_cached(c, ec, nc * sizeof(double), st, &dev_ec)) != BGW_OK) return rc;
   if (nfreq > 0 && (rc = upload_cached(c, omega, nfreq * sizeof(double), st, &dev_om)) != BGW_OK) return rc;
   if ((rc = upload_cached(c, geps, (size_t)ng * 3 * sizeof(int32_t), st, &dev_geps)) != BGW_OK) return rc;
+  HeadPlan hp;
+  Scratch s_h;
+  s_h.pool = &c->pool;
+  if ((rc = head_prepare(c, cell, npw_v, gv, npw_c, gc, ng, geps, prec, st, &hp)) != BGW_OK) return rc;
+  if (hp.g0 >= 0 && (rc = c->pool.alloc((size_t)nv * nc_chunk * sizeof(double2), &s_h.ptr)) != BGW_OK)
+    return fail(c, rc, "head scratch");
   for (int c0 = 0; c0 < nc; c0 += nc_chunk) {
     const int ncc = std::min(nc_chunk, nc - c0);
     const void* cc0 = static_cast<const char*>(d_cc) + (size_t)c0 * npw_c * 16;
     if ((rc = mtxel_run(c, n, prec, nv, bpv, d_cv, ncc, bpc, cc0, pp, s_M.ptr, st)) != BGW_OK) return rc;
+    if (hp.g0 >= 0 &&
+        (rc = head_dot(c, &hp, nv, d_cv, npw_v, ncc, cc0, ng, s_M.ptr, s_h.as<double2>(), st)) != BGW_OK)
+      return rc;
     if ((rc = chi_run(c, prec, nv, ncc, ng, s_M.ptr, static_cast<const double*>(dev_ev),
                       static_cast<const double*>(dev_ec) + c0, nfreq, static_cast<const double*>(dev_om),
-                      4.0 / cell->omega, c0 > 0, d_chi, st)) != BGW_OK)
+                      4.0 / cell->omega, c0 > 0, d_chi, st, &hp, s_h.as<double2>())) != BGW_OK)
       return rc;
   }
   {
     std::vector<int> ngv(nrow, ng);
-    std::vector<const double*> bv(nrow, &cell->bvec[0][0]), qv(nrow, cell->q_frac);
+    std::vector<const bgw_cell*> cp(nrow, cell);
     std::vector<const int32_t*> gv2(nrow, static_cast<const int32_t*>(dev_geps));
     std::vector<const void*> chis(nrow);
     std::vector<void*> invs(nrow);
@@ -580,7 +638,7 @@ int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
       chis[f] = static_cast<char*>(d_chi) + f * n2;
       invs[f] = static_cast<char*>(d_inv) + f * n2;
     }
-    if ((rc = epsinv_batch_run(c, nrow, ngv.data(), bv.data(), qv.data(), gv2.data(), chis.data(), nullptr,
+    if ((rc = epsinv_batch_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr,
                                invs.data(), st, use_tc_inverse(c, prec))) != BGW_OK)
       return rc;
   }

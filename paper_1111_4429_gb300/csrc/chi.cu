@@ -123,7 +123,7 @@ int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const do
 
 int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const double* d_ev,
             const double* d_ec, int nfreq, const double* d_omega, double scale, int accumulate,
-            void* chi, cudaStream_t st) {
+            void* chi, cudaStream_t st, const HeadPlan* hp, const double2* h) {
   const long long K = (long long)nv * nc;
   const int nrow = nfreq > 0 ? nfreq : 1;
   Scratch w;
@@ -135,8 +135,12 @@ int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const doubl
                                                                    nfreq == 0, w.as<double>());
   BGW_CUDA(c, cudaGetLastError());
   c->launches += 1;
-  if (prec != BGW_PREC_FP64)
-    return chi_mixed_run(c, prec, K, ng, M, w.as<double>(), nrow, scale, accumulate, chi, st);
+  if (prec != BGW_PREC_FP64) {
+    if ((rc = chi_mixed_run(c, prec, K, ng, M, w.as<double>(), nrow, scale, accumulate, chi, st)) != BGW_OK)
+      return rc;
+    if (hp && hp->g0 >= 0) return head_wings(c, hp, K, ng, M, h, w.as<double>(), nrow, scale, chi, st);
+    return BGW_OK;
+  }
   const int nt = (ng + TB - 1) / TB;
   const long long ntiles = (long long)nt * (nt + 1) / 2;
   for (int f = 0; f < nrow; ++f) {

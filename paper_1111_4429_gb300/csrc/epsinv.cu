@@ -16,6 +16,7 @@
 // v^1/2 is Hermitian positive definite (chi <= 0), for which elimination
 // without pivoting is backward stable; a zero or non-finite pivot is
 // recorded in the device status word.
+#include <cmath>
 #include <memory>
 #include <vector>
 
@@ -32,19 +33,67 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 }  // namespace
 
-__global__ void coulomb_sqrt_kernel(const int32_t* __restrict__ geps, int ng, double b00, double b01,
-                                    double b02, double b10, double b11, double b12, double b20,
-                                    double b21, double b22, double q0, double q1, double q2,
+// Cell, q and Coulomb model as one by-value kernel argument.
+struct CoulombArgs {
+  double b[9];  // bvec rows
+  double q[3];
+  double cut;   // r_c or z_c
+  int model;    // BGW_COULOMB_*
+};
+
+CoulombArgs coulomb_args(const bgw_cell* cell) {
+  CoulombArgs a;
+  for (int i = 0; i < 9; ++i) a.b[i] = (&cell->bvec[0][0])[i];
+  for (int i = 0; i < 3; ++i) a.q[i] = cell->q_frac[i];
+  a.cut = cell->coulomb_cut;
+  a.model = cell->coulomb;
+  return a;
+}
+
+// sqrt(v(k)), k = (q + G) B (Section "Coulomb Interaction"; bulk form Eq.
+// untruncated_bare_coulomb).  The truncated brackets 1 - cos(k r_c) and
+// 1 - exp(-k_xy z_c) cos(k_z z_c) are taken as 2 sin^2(k r_c / 2) and
+// -expm1(-k_xy z_c) + exp(-k_xy z_c) 2 sin^2(k_z z_c / 2): sums of
+// non-negative terms, exact rewrites that keep full relative precision at
+// small k.  The host has rejected k = 0 except for the sphere.
+__device__ __forceinline__ double coulomb_sqrt_at(const CoulombArgs& a, const int32_t* g) {
+  const double f0 = g[0] + a.q[0], f1 = g[1] + a.q[1], f2 = g[2] + a.q[2];
+  const double kx = f0 * a.b[0] + f1 * a.b[3] + f2 * a.b[6];
+  const double ky = f0 * a.b[1] + f1 * a.b[4] + f2 * a.b[7];
+  const double kz = f0 * a.b[2] + f1 * a.b[5] + f2 * a.b[8];
+  const double k2 = kx * kx + ky * ky + kz * kz;
+  constexpr double kFourPi = 4.0 * 3.14159265358979323846;
+  if (a.model == BGW_COULOMB_SPHERE) {
+    if (k2 == 0.0) return sqrt(2.0 * 3.14159265358979323846) * a.cut;  // (2 pi r_c^2)^{1/2}
+    const double s = sin(0.5 * a.cut * sqrt(k2));
+    return sqrt(kFourPi * 2.0 / k2) * fabs(s);
+  }
+  if (a.model == BGW_COULOMB_SLAB) {
+    const double x = sqrt(kx * kx + ky * ky) * a.cut;
+    const double s = sin(0.5 * kz * a.cut);
+    return sqrt(kFourPi / k2 * (-expm1(-x) + exp(-x) * 2.0 * s * s));
+  }
+  return sqrt(kFourPi / k2);
+}
+
+__global__ void coulomb_sqrt_kernel(const int32_t* __restrict__ geps, int ng, CoulombArgs a,
                                     double* __restrict__ sv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ng) return;
-  const double f0 = geps[3 * i] + q0, f1 = geps[3 * i + 1] + q1, f2 = geps[3 * i + 2] + q2;
-  const double kx = f0 * b00 + f1 * b10 + f2 * b20;
-  const double ky = f0 * b01 + f1 * b11 + f2 * b21;
-  const double kz = f0 * b02 + f1 * b12 + f2 * b22;
-  const double k2 = kx * kx + ky * ky + kz * kz;
-  // 4 pi / k2, square root
-  sv[i] = sqrt(4.0 * 3.14159265358979323846 / k2);
+  sv[i] = coulomb_sqrt_at(a, geps + 3 * i);
+}
+
+// W[i][j] = sv_i epsinv[i][j] sv_j over one matrix (row-major), one
+// element per thread-iteration; sv stays in L1/L2, the matrix streams once.
+__global__ void screened_w_kernel(const double2* __restrict__ epsinv, const double* __restrict__ sv, int ng,
+                                  double2* W) {
+  const size_t n2 = (size_t)ng * ng;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ng), j = (int)(e - (size_t)i * ng);
+    const double s = sv[i] * sv[j];
+    const double2 x = epsinv[e];
+    W[e] = make_double2(s * x.x, s * x.y);
+  }
 }
 
 __global__ void eps_form_kernel(const double2* __restrict__ chi, const double* __restrict__ sv, int ng,
@@ -387,7 +436,7 @@ __global__ void sw_finish_kernel(const __grid_constant__ SweepBatch b) {
 }
 
 // eps~ formation for every matrix of the batch, then the batched sweep.
-int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec, const double* const* qf,
+int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells,
                      const int32_t* const* d_geps, const void* const* chi, void* const* eps, void* const* epsinv,
                      cudaStream_t st, bool tc_update) {
   const int group = tc_update ? 96 : kSweepBatch;
@@ -415,10 +464,7 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
       double2* A = static_cast<double2*>(epsinv[m]);
       {
         TimedScope ts(c, kTEpsForm, st);
-        const double* bv = bvec[m];
-        const double* q = qf[m];
-        coulomb_sqrt_kernel<<<(ng[m] + 255) / 256, 256, 0, st>>>(d_geps[m], ng[m], bv[0], bv[1], bv[2], bv[3],
-                                                                 bv[4], bv[5], bv[6], bv[7], bv[8], q[0], q[1], q[2],
+        coulomb_sqrt_kernel<<<(ng[m] + 255) / 256, 256, 0, st>>>(d_geps[m], ng[m], coulomb_args(cells[m]),
                                                                  sv.as<double>());
         const size_t n2 = (size_t)ng[m] * ng[m];
         const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
@@ -525,6 +571,58 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec,
 }
 
 // ---------------------------------------------------------------------------
+int screened_w_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
+                   const void* const* epsinv, void* const* W, cudaStream_t st) {
+  int ngmax = 0;
+  for (int m = 0; m < nmat; ++m) ngmax = std::max(ngmax, ng[m]);
+  Scratch sv;
+  sv.pool = &c->pool;
+  int rc;
+  if ((rc = c->pool.alloc((size_t)ngmax * sizeof(double), &sv.ptr)) != BGW_OK)
+    return fail(c, rc, "bgw_screened_w: scratch allocation failed");
+  TimedScope ts(c, kTEpsForm, st);
+  for (int m = 0; m < nmat; ++m) {
+    coulomb_sqrt_kernel<<<(ng[m] + 255) / 256, 256, 0, st>>>(d_geps[m], ng[m], coulomb_args(cells[m]),
+                                                             sv.as<double>());
+    const size_t n2 = (size_t)ng[m] * ng[m];
+    const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
+    screened_w_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(epsinv[m]), sv.as<double>(), ng[m],
+                                          static_cast<double2*>(W[m]));
+    BGW_CUDA(c, cudaGetLastError());
+    c->launches += 2;
+  }
+  return BGW_OK;
+}
+
+int coulomb_check(const bgw_cell* cell, int ng, const int32_t* geps, int* what, int* bad) {
+  *what = 0;
+  *bad = -1;
+  const int model = cell->coulomb;
+  if (model != BGW_COULOMB_BULK && model != BGW_COULOMB_SPHERE && model != BGW_COULOMB_SLAB) {
+    *what = 1;
+    return BGW_EINVAL;
+  }
+  if (model != BGW_COULOMB_BULK && !(cell->coulomb_cut > 0.0 && std::isfinite(cell->coulomb_cut))) {
+    *what = 2;
+    return BGW_EINVAL;
+  }
+  if (model == BGW_COULOMB_SPHERE) return BGW_OK;  // finite everywhere
+  for (int i = 0; i < ng; ++i) {
+    double k2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double kd = 0.0;
+      for (int a = 0; a < 3; ++a) kd += (geps[3 * i + a] + cell->q_frac[a]) * cell->bvec[a][d];
+      k2 += kd * kd;
+    }
+    if (!(k2 > 0.0)) {
+      *what = 3;
+      *bad = i;
+      return BGW_EINVAL;
+    }
+  }
+  return BGW_OK;
+}
+
 // Allocation-free inverse: bgw_epsinv_noalloc (include/bgw.h).
 //
 // The Gauss-Jordan kernels above, with every scratch buffer
@@ -581,15 +679,8 @@ extern "C" int bgw_epsinv_noalloc(const bgw_cell* cell, int ng, const int32_t* g
   using namespace bgw;
   if (!cell || !geps || !chi || !epsinv || ng <= 0) return BGW_EINVAL;
   if (ng > kNoAllocMaxNg) return BGW_EINVAL;
-  for (int i = 0; i < ng; ++i) {
-    double k2 = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      double kd = 0.0;
-      for (int a = 0; a < 3; ++a) kd += (geps[3 * i + a] + cell->q_frac[a]) * cell->bvec[a][d];
-      k2 += kd * kd;
-    }
-    if (!(k2 > 0.0)) return BGW_EINVAL;
-  }
+  int what, bad;
+  if (coulomb_check(cell, ng, geps, &what, &bad) != BGW_OK) return BGW_EINVAL;
   unsigned char* base = nullptr;
   if (noalloc_scratch_address(&base) != cudaSuccess) {
     cudaGetLastError();
@@ -602,16 +693,13 @@ extern "C" int bgw_epsinv_noalloc(const bgw_cell* cell, int ng, const int32_t* g
   double2* Cp = reinterpret_cast<double2*>(base + kNaC);
   int32_t* dgeps = reinterpret_cast<int32_t*>(base + kNaGeps);
   int* status = reinterpret_cast<int*>(base + kNaStatus);
-  const double* bvec = &cell->bvec[0][0];
-  const double* qf = cell->q_frac;
   // The array keeps the previous call's contents: the status word must start at 0.
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess ||
       cudaMemcpyAsync(dgeps, geps, sizeof(int32_t) * 3 * (size_t)ng, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     cudaGetLastError();
     return BGW_ECUDA;
   }
-  coulomb_sqrt_kernel<<<(ng + 255) / 256, 256, 0, st>>>(dgeps, ng, bvec[0], bvec[1], bvec[2], bvec[3], bvec[4],
-                                                        bvec[5], bvec[6], bvec[7], bvec[8], qf[0], qf[1], qf[2], sv);
+  coulomb_sqrt_kernel<<<(ng + 255) / 256, 256, 0, st>>>(dgeps, ng, coulomb_args(cell), sv);
   double2* A = static_cast<double2*>(epsinv);
   const size_t n2 = (size_t)ng * ng;
   const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);

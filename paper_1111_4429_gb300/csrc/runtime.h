@@ -112,6 +112,8 @@ struct Ctx {
   cudaStream_t side = nullptr;     // high-priority stream of the sweep's look-ahead chain
   cudaEvent_t la_ev[4] = {};       // look-ahead dependencies (fork, slice, rest x2)
   int inverse_mode = -1;     // -1: tensor-core update for the mixed precisions; 0: FP64 FMA; 1: tensor cores
+  int head_mode = -1;        // mixed chi head/wings in FP64: -1 automatic at small q, 0 off, 1 on
+  std::unordered_map<uint64_t, const int32_t*> head_maps;  // conduction G -> valence index (head dot products)
   Pool pool;
   std::string err;
   int* d_status = nullptr;   // device status word
@@ -190,15 +192,38 @@ cudaError_t mtxel_init_f32();
 int mtxel_run(Ctx* c, int n, int prec, int nv, const BandPlan* bpv, const void* cv,
               int nc, const BandPlan* bpc, const void* cc, const PairPlan* pp,
               void* M, cudaStream_t st);
+// FP64 head of the mixed precisions at a small q (head.cu).  g0 < 0: not used.
+struct HeadPlan {
+  int g0 = -1;                   // index of G = 0 in the epsilon list
+  int npw_c = 0;
+  const int32_t* d_map = nullptr;  // [npw_c] valence index of each conduction G, or -1
+};
+int head_prepare(Ctx* c, const bgw_cell* cell, int npw_v, const int32_t* gv, int npw_c, const int32_t* gc, int ng,
+                 const int32_t* geps, int prec, cudaStream_t st, HeadPlan* out);
+// h[p] = M_p(G = 0) in FP64 for the nv x nc pairs; zeroes column g0 of the FP32 M.
+int head_dot(Ctx* c, const HeadPlan* hp, int nv, const void* cv, int npw_v, int nc, const void* cc, int ng,
+             void* M, double2* h, cudaStream_t st);
+// Adds row and column g0 of chi from h and M (weights w[nrow][K]).
+int head_wings(Ctx* c, const HeadPlan* hp, long long K, int ng, const void* M, const double2* h, const double* w,
+               int nrow, double scale, void* chi, cudaStream_t st);
+// hp/h: when hp->g0 >= 0 the mixed precisions add the FP64 head and wings
+// (column g0 of M must have been zeroed by head_dot).
 int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const double* d_ev,
             const double* d_ec, int nfreq, const double* d_omega, double scale, int accumulate,
-            void* chi, cudaStream_t st);
+            void* chi, cudaStream_t st, const HeadPlan* hp = nullptr, const double2* h = nullptr);
 // eps~ and its inverse for nmat matrices (per-matrix size, cell and q).
 // tc_update: the sweep's trailing updates run on the tensor cores with
 // FP64-level accuracy (sweep_tc.cu) instead of FP64 FMA.
-int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const double* const* bvec, const double* const* qf,
+int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells,
                      const int32_t* const* d_geps, const void* const* chi, void* const* eps, void* const* epsinv,
                      cudaStream_t st, bool tc_update);
+// W = v^1/2 epsinv v^1/2 for nmat matrices (bgw_screened_w).
+int screened_w_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
+                   const void* const* epsinv, void* const* W, cudaStream_t st);
+// Host check of a cell's Coulomb model against its G list: BGW_OK, or
+// BGW_EINVAL with *what = 1 (unknown model), 2 (bad cut length) or
+// 3 (v diverges at geps[*bad]).
+int coulomb_check(const bgw_cell* cell, int ng, const int32_t* geps, int* what, int* bad);
 
 // Tensor-core trailing update of the sweep (sweep_tc.cu).
 struct OzPlan;

@@ -22,8 +22,9 @@ from typing import Dict, List, Optional, Sequence
 import numpy as np
 
 # Sub-seed order for one system (one base seed per configuration):
-# valence coefficients, conduction coefficients, E_v, E_c, subblock, arrivals.
-_STREAMS = ("cv", "cc", "ev", "ec", "subblock", "arrivals")
+# valence coefficients, conduction coefficients, E_v, E_c, subblock, arrivals,
+# the band set and the momentum matrix of a small-q system.
+_STREAMS = ("cv", "cc", "ev", "ec", "subblock", "arrivals", "bands", "kp")
 
 
 def cubic_cell(a: float):
@@ -128,6 +129,49 @@ def make_system(name: str, a: float, fft: int, ecut_wfn: float, ecut_eps: float,
     ec = np.sort(gens["ec"].uniform(ec_range[0], ec_range[1], nc))
     return System(name=name, a=a, bvec=bvec, omega=omega, q_frac=q, fft=fft, gv=gv, gc=gc,
                   geps=geps, cv=cv, cc=cc, ev=ev, ec=ec, seed=seed)
+
+
+def q0_system(name: str, a: float, fft: int, ecut_wfn: float, ecut_eps: float, nv: int, nc: int,
+              seed: int, q_frac=(0.001, 0.0, 0.0), p_scale: float = 0.5,
+              ev_range=(-0.5, 0.0), ec_range=(0.04, 1.5)) -> System:
+    """A system at a small q0 (the q -> 0 limit of Section "RPA Dielectric
+    Matrix: epsilon" is taken at q0 about 1/1000 of the zone on a shifted grid).
+
+    The occupied bands at k + q0 are not independent of the empty bands at k
+    as in make_system: one orthonormal set on the k sphere gives the empty
+    bands u_c and the unshifted occupied bands u_v, and the shifted occupied
+    bands follow first-order k.p perturbation theory,
+        u_v(k + q0) = u_v + |q0| sum_c P_vc / (E_v - E_c) u_c,
+    re-orthonormalized, with a seeded complex momentum matrix P (entries of
+    scale p_scale).  The head M_vc(G = 0) = <u_v(k + q0)|u_c> is then O(|q0|)
+    and v(q0) chi_00 stays finite as q0 -> 0, as it does for an insulator.
+    The coefficients are moved onto the k + q0 sphere by G vector (zero for a
+    G the shifted sphere gains).
+    """
+    bvec, omega = cubic_cell(a)
+    q = np.asarray(q_frac, dtype=np.float64)
+    qlen = float(np.linalg.norm(q @ bvec))
+    gv = gsphere(bvec, q, ecut_wfn)
+    gc = gsphere(bvec, (0.0, 0.0, 0.0), ecut_wfn)
+    geps = gsphere(bvec, q, ecut_eps)
+    ss = np.random.SeedSequence(seed).spawn(len(_STREAMS))
+    gens = {k: np.random.Generator(np.random.PCG64(s)) for k, s in zip(_STREAMS, ss)}
+    u = orthonormal_bands(gens["bands"], gc.shape[0], nv + nc)
+    uv, cc = u[:nv], np.ascontiguousarray(u[nv:])
+    ev = np.sort(gens["ev"].uniform(ev_range[0], ev_range[1], nv))
+    ec = np.sort(gens["ec"].uniform(ec_range[0], ec_range[1], nc))
+    pm = p_scale * (gens["kp"].standard_normal((nv, nc)) + 1j * gens["kp"].standard_normal((nv, nc))) / math.sqrt(2)
+    shifted = uv + qlen * ((pm / (ev[:, None] - ec[None, :])) @ cc)
+    qq, _ = np.linalg.qr(shifted.T)
+    on_k = qq.T
+    index = {tuple(g): i for i, g in enumerate(gc.tolist())}
+    cv = np.zeros((nv, gv.shape[0]), dtype=np.complex128)
+    for j, g in enumerate(gv.tolist()):
+        i = index.get(tuple(g))
+        if i is not None:
+            cv[:, j] = on_k[:, i]
+    return System(name=name, a=a, bvec=bvec, omega=omega, q_frac=q, fft=fft, gv=gv, gc=gc,
+                  geps=geps, cv=np.ascontiguousarray(cv), cc=cc, ev=ev, ec=ec, seed=seed)
 
 
 # Benchmark configurations: plain FP64 oracle-sized (c0), plain FP64 larger cell

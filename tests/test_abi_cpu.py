@@ -48,9 +48,10 @@ def test_binding_lists_every_declared_symbol():
 
 def test_cell_struct_layout():
     from paper_1111_4429_gb300 import bgw
-    # double bvec[3][3]; double omega; double q_frac[3]; int fft[3]
-    assert ctypes.sizeof(bgw.Cell) == 8 * 9 + 8 + 8 * 3 + 4 * 3 + 4  # padded to 8
+    # double bvec[3][3]; double omega; double q_frac[3]; int fft[3]; int coulomb; double coulomb_cut
+    assert ctypes.sizeof(bgw.Cell) == 8 * 9 + 8 + 8 * 3 + 4 * 3 + 4 + 8
     assert bgw.Cell.omega.offset == 72 and bgw.Cell.q_frac.offset == 80 and bgw.Cell.fft.offset == 104
+    assert bgw.Cell.coulomb.offset == 116 and bgw.Cell.coulomb_cut.offset == 120
 
 
 def test_product_path_does_not_import_oracle():

@@ -357,3 +357,38 @@ def test_screened_w_routes_agree_and_hermitian_truncated():
         # W = v^1/2 eps~^-1 v^1/2 with 0 < eps~^-1 <= I: 0 <= W <= V
         lam = np.linalg.eigvalsh(np.diag(v) - w_sym)
         assert lam.min() >= -1e-12 * v.max()
+
+
+def _q0(qf, **kw):
+    p = dict(synth.CONFIGS["c0"])
+    p.update(kw)
+    return synth.q0_system("q0", **p, q_frac=(qf, 0.0, 0.0))
+
+
+def test_q0_head_direct_dot_and_limit():
+    # At q0 the head M_vc(G=0) = <u_v(k+q0)|u_c> is a plain dot product of the
+    # coefficient vectors over the common G (Eq. eqn_matrix_elem at G = 0); the
+    # oracle's FFT route must agree, and the head v(q0) chi_00 -- the
+    # macroscopic response -- must tend to a finite limit as q0 -> 0.
+    heads = []
+    for qf in (1e-3, 5e-4):
+        s = _q0(qf)
+        r = oracle.solve(s)
+        assert tuple(s.geps[0]) == (0, 0, 0)
+        idx = {tuple(g): i for i, g in enumerate(s.gc.tolist())}
+        cvk = np.zeros((s.nv, s.gc.shape[0]), dtype=np.complex128)
+        for j, g in enumerate(s.gv.tolist()):
+            cvk[:, idx[tuple(g)]] = s.cv[:, j]
+        m0 = (np.conj(cvk) @ s.cc.T).ravel()                       # [p], p = v*nc + c
+        assert np.abs(m0).max() < 50 * np.linalg.norm(s.q_frac @ s.bvec)  # O(|q0|)
+        mf = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps[:1], s.fft)[:, 0]
+        assert np.abs(mf - m0).max() <= 1e-15
+        w = oracle.chi_weights(s.ev, s.ec)
+        head = r["v"][0] * (4.0 / s.omega) * np.sum(w * np.abs(m0) ** 2)
+        assert abs(head - r["v"][0] * r["chi"][0, 0].real) <= 1e-12 * abs(head)
+        heads.append(head)
+        # the symmetrized wings sqrt(v0 vG) chi_0G stay O(1) although v0 ~ 1/q0^2
+        wing = np.sqrt(r["v"][0] * r["v"][1:]) * r["chi"][0, 1:]
+        assert np.abs(wing).max() < 1.0
+    assert -20 < heads[0] < -1
+    assert abs(heads[0] - heads[1]) <= 1e-3 * abs(heads[1])        # O(q0) approach to the limit
