@@ -250,7 +250,8 @@ int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
  *   W[i]      device c128 [ng[i]][ng[i]] (written; may equal epsinv[i]
  *             for an in-place update, must not overlap it otherwise)
  * One pass over HBM: 16 B read and 16 B written per element.
- * EINVAL on NULL pointers, bad sizes or |q+G| = 0 where v diverges.       */
+ * EINVAL on NULL pointers, bad sizes or |q+G| = 0 where v diverges;
+ * EUNSUPPORTED for ng > 65535.                                           */
 int bgw_screened_w(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
                    const int32_t* const* geps, const void* const* epsinv,
                    void* const* W, void* stream);

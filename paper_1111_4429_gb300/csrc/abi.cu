@@ -373,6 +373,7 @@ int bgw_screened_w(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
   for (int m = 0; m < nmat; ++m) {
     if (ng[m] <= 0 || !geps[m] || !epsinv[m] || !W[m])
       return fail(c, BGW_EINVAL, "matrix %d: bad size or NULL pointer", m);
+    if (ng[m] > 65535) return fail(c, BGW_EUNSUPPORTED, "matrix %d: ng = %d exceeds 65535", m, ng[m]);
     if ((rc = check_q(c, &cells[m], ng[m], geps[m])) != BGW_OK) return rc;
     if (W[m] != epsinv[m]) {
       const size_t bytes = (size_t)ng[m] * ng[m] * sizeof(double2);
@@ -481,23 +482,23 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // Key of the argument set: sizes, pointers and host-array contents.
-  uint64_t key = fnv1a(&nq, sizeof(nq), fnv1a(&prec, sizeof(prec), fnv1a(&nfreq, sizeof(nfreq))));
-  if (nfreq > 0) key = fnv1a(omega, nfreq * sizeof(double), key);
-  key = fnv1a(&st, sizeof(st), key);
+  uint64_t key = hash_bytes(&nq, sizeof(nq), hash_bytes(&prec, sizeof(prec), hash_bytes(&nfreq, sizeof(nfreq))));
+  if (nfreq > 0) key = hash_bytes(omega, nfreq * sizeof(double), key);
+  key = hash_bytes(&st, sizeof(st), key);
   const int modes[2] = {c->inverse_mode, c->head_mode};
-  key = fnv1a(modes, sizeof(modes), key);
+  key = hash_bytes(modes, sizeof(modes), key);
   for (int q = 0; q < nq; ++q) {
     const bgw_problem& p = problems[q];
-    key = fnv1a(&p.cell, sizeof(p.cell), key);
+    key = hash_bytes(&p.cell, sizeof(p.cell), key);
     const void* ptrs[3] = {p.cv, p.cc, epsinv[q]};
-    key = fnv1a(ptrs, sizeof(ptrs), key);
+    key = hash_bytes(ptrs, sizeof(ptrs), key);
     const int dims[4] = {p.nv, p.npw_v, p.nc, p.npw_c};
-    key = fnv1a(dims, sizeof(dims), key);
-    key = fnv1a(p.gv, (size_t)p.npw_v * 12, key);
-    key = fnv1a(p.gc, (size_t)p.npw_c * 12, key);
-    key = fnv1a(p.geps, (size_t)p.ng * 12, key);
-    key = fnv1a(p.ev, (size_t)p.nv * 8, key);
-    key = fnv1a(p.ec, (size_t)p.nc * 8, key);
+    key = hash_bytes(dims, sizeof(dims), key);
+    key = hash_bytes(p.gv, (size_t)p.npw_v * 12, key);
+    key = hash_bytes(p.gc, (size_t)p.npw_c * 12, key);
+    key = hash_bytes(p.geps, (size_t)p.ng * 12, key);
+    key = hash_bytes(p.ev, (size_t)p.nv * 8, key);
+    key = hash_bytes(p.ec, (size_t)p.nc * 8, key);
   }
   auto it = c->graphs.find(key);
   if (it != c->graphs.end()) {

@@ -83,16 +83,46 @@ __global__ void coulomb_sqrt_kernel(const int32_t* __restrict__ geps, int ng, Co
   sv[i] = coulomb_sqrt_at(a, geps + 3 * i);
 }
 
-// W[i][j] = sv_i epsinv[i][j] sv_j over one matrix (row-major), one
-// element per thread-iteration; sv stays in L1/L2, the matrix streams once.
-__global__ void screened_w_kernel(const double2* __restrict__ epsinv, const double* __restrict__ sv, int ng,
-                                  double2* W) {
-  const size_t n2 = (size_t)ng * ng;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / ng), j = (int)(e - (size_t)i * ng);
-    const double s = sv[i] * sv[j];
-    const double2 x = epsinv[e];
-    W[e] = make_double2(s * x.x, s * x.y);
+// W[i][j] = sv_i epsinv[i][j] sv_j for up to kWBatch matrices per launch
+// (grid.y = matrix).  Each matrix is streamed flat: a thread takes four
+// elements a block-width apart, issues the four 16-byte loads before any
+// store, and finds (i, j) with one 32-bit division each (ng <= 65535, so
+// ng^2 < 2^32).
+constexpr int kWBatch = 8;
+constexpr int kWThreads = 256, kWUnroll = 4;
+struct WBatch {
+  const double2* in[kWBatch];
+  double2* out[kWBatch];
+  const double* sv[kWBatch];
+  int ng[kWBatch];
+};
+
+__global__ void __launch_bounds__(kWThreads) screened_w_kernel(WBatch b) {
+  const int m = blockIdx.y;
+  const unsigned ng = (unsigned)b.ng[m];
+  const unsigned n2 = ng * ng;
+  const double* sv = b.sv[m];
+  const double2* in = b.in[m];
+  double2* out = b.out[m];
+  const unsigned long long step = (unsigned long long)gridDim.x * kWThreads * kWUnroll;
+  for (unsigned long long e0 = (unsigned long long)blockIdx.x * kWThreads * kWUnroll + threadIdx.x; e0 < n2;
+       e0 += step) {
+    double2 x[kWUnroll];
+    double s[kWUnroll];
+#pragma unroll
+    for (int u = 0; u < kWUnroll; ++u) {
+      const unsigned long long e = e0 + u * kWThreads;
+      if (e < n2) {
+        x[u] = in[e];
+        const unsigned i = (unsigned)e / ng;   // e < n2 < 2^32
+        s[u] = sv[i] * sv[(unsigned)e - i * ng];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kWUnroll; ++u) {
+      const unsigned long long e = e0 + u * kWThreads;
+      if (e < n2) out[e] = make_double2(s[u] * x[u].x, s[u] * x[u].y);
+    }
   }
 }
 
@@ -575,21 +605,34 @@ int screened_w_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells
                    const void* const* epsinv, void* const* W, cudaStream_t st) {
   int ngmax = 0;
   for (int m = 0; m < nmat; ++m) ngmax = std::max(ngmax, ng[m]);
+  const int nb = std::min(nmat, kWBatch);
   Scratch sv;
   sv.pool = &c->pool;
   int rc;
-  if ((rc = c->pool.alloc((size_t)ngmax * sizeof(double), &sv.ptr)) != BGW_OK)
+  if ((rc = c->pool.alloc((size_t)nb * ngmax * sizeof(double), &sv.ptr)) != BGW_OK)
     return fail(c, rc, "bgw_screened_w: scratch allocation failed");
-  TimedScope ts(c, kTEpsForm, st);
-  for (int m = 0; m < nmat; ++m) {
-    coulomb_sqrt_kernel<<<(ng[m] + 255) / 256, 256, 0, st>>>(d_geps[m], ng[m], coulomb_args(cells[m]),
-                                                             sv.as<double>());
-    const size_t n2 = (size_t)ng[m] * ng[m];
-    const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
-    screened_w_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(epsinv[m]), sv.as<double>(), ng[m],
-                                          static_cast<double2*>(W[m]));
+  TimedScope ts(c, kTScreenedW, st);
+  for (int m0 = 0; m0 < nmat; m0 += kWBatch) {
+    const int cnt = std::min(kWBatch, nmat - m0);
+    WBatch b = {};
+    size_t most = 0;
+    for (int k = 0; k < cnt; ++k) {
+      const int m = m0 + k;
+      double* svk = sv.as<double>() + (size_t)k * ngmax;
+      coulomb_sqrt_kernel<<<(ng[m] + 255) / 256, 256, 0, st>>>(d_geps[m], ng[m], coulomb_args(cells[m]), svk);
+      b.in[k] = static_cast<const double2*>(epsinv[m]);
+      b.out[k] = static_cast<double2*>(W[m]);
+      b.sv[k] = svk;
+      b.ng[k] = ng[m];
+      most = std::max(most, (size_t)ng[m] * ng[m]);
+    }
+    // up to 8 resident blocks per SM over the matrices of this launch
+    const size_t per_block = (size_t)kWThreads * kWUnroll;
+    const unsigned gx = (unsigned)std::min<size_t>((most + per_block - 1) / per_block,
+                                                   std::max<size_t>(1, 152 * 8 / cnt));
+    screened_w_kernel<<<dim3(gx, (unsigned)cnt), kWThreads, 0, st>>>(b);
     BGW_CUDA(c, cudaGetLastError());
-    c->launches += 2;
+    c->launches += cnt + 1;
   }
   return BGW_OK;
 }

@@ -55,36 +55,58 @@ __global__ void head_dot_kernel(const double2* __restrict__ cv, int npw_v, const
 
 constexpr int kWingThreads = 128;
 
-// part[f][s][G'] = sum_{p in split s} w_f[p] conj(h_p) X_p(G'), X = M except
-// at G' = g0, where X = h (the head).  Grid (column tiles, splits, nrow).
+// a[f][p] = w_f[p] conj(h_p) in FP32 (hi) plus the head term in FP64.
+// part[f][s][G'] = sum_{p in split s} a[f][p] M_p(G') for G' != g0, the
+// products in FP32 (M itself holds FP32 values) and the sum compensated
+// (two-sum), so the wing carries the relative precision of M; at G' = g0
+// the split sums w |h|^2 in FP64.  Grid (column tiles, splits, nrow).
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
+  const float t = s + x;
+  const float z = t - s;
+  e += (s - (t - z)) + (x - z);
+  s = t;
+}
+
 __global__ void __launch_bounds__(kWingThreads) head_wing_partial_kernel(
     const float2* __restrict__ M, const double2* __restrict__ h, const double* __restrict__ w, long long K, int ng,
     int g0, long long per_split, double2* __restrict__ part) {
+  __shared__ float2 a_s[256];
   const int gp = blockIdx.x * kWingThreads + threadIdx.x;
   const int s = blockIdx.y, f = blockIdx.z;
   const long long p0 = (long long)s * per_split;
   const long long p1 = p0 + per_split < K ? p0 + per_split : K;
   const double* wf = w + (size_t)f * K;
-  double re = 0.0, im = 0.0;
-  if (gp < ng) {
-    for (long long p = p0; p < p1; ++p) {
-      const double2 hp = h[p];
-      const double wp = wf[p];
-      double xr, xi;
-      if (gp == g0) {
-        xr = hp.x;
-        xi = hp.y;
-      } else {
-        const float2 m = M[(size_t)p * ng + gp];
-        xr = (double)m.x;
-        xi = (double)m.y;
-      }
-      const double ar = wp * hp.x, ai = wp * hp.y;   // w conj(h) = (ar, -ai)
-      re = fma(ar, xr, fma(ai, xi, re));
-      im = fma(ar, xi, fma(-ai, xr, im));
+  float re = 0.f, rec = 0.f, im = 0.f, imc = 0.f;
+  double hre = 0.0;
+  for (long long q0 = p0; q0 < p1; q0 += 256) {
+    const int cnt = (int)(p1 - q0 < 256 ? p1 - q0 : 256);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += kWingThreads) {
+      const double2 hp = h[q0 + t];
+      const double wp = wf[q0 + t];
+      a_s[t] = make_float2((float)(wp * hp.x), (float)(-wp * hp.y));   // w conj(h)
     }
-    part[((size_t)f * gridDim.y + s) * ng + gp] = make_double2(re, im);
+    __syncthreads();
+    if (gp < ng) {
+      if (gp == g0) {
+        for (int t = 0; t < cnt; ++t) {
+          const double2 hp = h[q0 + t];
+          hre = fma(wf[q0 + t], fma(hp.x, hp.x, hp.y * hp.y), hre);
+        }
+      } else {
+        const float2* mp = M + (size_t)q0 * ng + gp;
+        for (int t = 0; t < cnt; ++t) {
+          const float2 m = mp[(size_t)t * ng];
+          const float2 a = a_s[t];
+          two_sum_acc(re, rec, fmaf(a.x, m.x, -a.y * m.y));
+          two_sum_acc(im, imc, fmaf(a.x, m.y, a.y * m.x));
+        }
+      }
+    }
   }
+  if (gp < ng)
+    part[((size_t)f * gridDim.y + s) * ng + gp] =
+        gp == g0 ? make_double2(hre, 0.0) : make_double2((double)re + (double)rec, (double)im + (double)imc);
 }
 
 __global__ void head_wing_apply_kernel(const double2* __restrict__ part, int nsplit, int ng, int g0, double scale,
@@ -139,7 +161,7 @@ int head_prepare(Ctx* c, const bgw_cell* cell, int npw_v, const int32_t* gv, int
     }
     if (!(std::sqrt(q2) < 0.02 * bmin)) return BGW_OK;
   }
-  const uint64_t key = fnv1a(gc, (size_t)npw_c * 12, fnv1a(gv, (size_t)npw_v * 12, fnv1a(&npw_c, sizeof(int))));
+  const uint64_t key = hash_bytes(gc, (size_t)npw_c * 12, hash_bytes(gv, (size_t)npw_v * 12, hash_bytes(&npw_c, sizeof(int))));
   auto it = c->head_maps.find(key);
   if (it == c->head_maps.end()) {
     std::unordered_map<uint64_t, int> index;
@@ -168,6 +190,7 @@ int head_dot(Ctx* c, const HeadPlan* hp, int nv, const void* cv, int npw_v, int 
              void* M, double2* h, cudaStream_t st) {
   const long long K = (long long)nv * nc;
   const long long threads = K * 32;
+  TimedScope ts(c, kTHeadDot, st);
   head_dot_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
       static_cast<const double2*>(cv), npw_v, static_cast<const double2*>(cc), hp->npw_c, hp->d_map, nc, K, ng,
       hp->g0, h, static_cast<float2*>(M));
@@ -188,6 +211,7 @@ int head_wings(Ctx* c, const HeadPlan* hp, long long K, int ng, const void* M, c
   part.pool = &c->pool;
   int rc = c->pool.alloc((size_t)nrow * nsplit * ng * sizeof(double2), &part.ptr);
   if (rc != BGW_OK) return fail(c, rc, "chi head: scratch allocation failed");
+  TimedScope ts(c, kTHeadWings, st);
   head_wing_partial_kernel<<<dim3((unsigned)tiles, (unsigned)nsplit, (unsigned)nrow), kWingThreads, 0, st>>>(
       static_cast<const float2*>(M), h, w, K, ng, hp->g0, per, part.as<double2>());
   head_wing_apply_kernel<<<dim3((unsigned)((ng + 127) / 128), (unsigned)nrow), 128, 0, st>>>(

@@ -31,7 +31,7 @@ static int upload_vec(Ctx* c, const std::vector<V>& v, cudaStream_t st, V** dev)
 // Band transform plan: the sphere's (gx,gy) columns with their (gz, index)
 // entries, and the distinct gx (the only x columns the y pass must touch).
 int get_band_plan(Ctx* c, int n, int npw, const int32_t* g, cudaStream_t st, const BandPlan** out) {
-  uint64_t key = fnv1a(g, (size_t)npw * 3 * sizeof(int32_t), fnv1a(&n, sizeof(n)));
+  uint64_t key = hash_bytes(g, (size_t)npw * 3 * sizeof(int32_t), hash_bytes(&n, sizeof(n)));
   auto it = c->band_plans.find(key);
   if (it != c->band_plans.end() && it->second->npw == npw) {
     *out = it->second.get();
@@ -80,7 +80,7 @@ int get_band_plan(Ctx* c, int n, int npw, const int32_t* g, cudaStream_t st, con
 // (kx,ky) columns (x-pass outputs) and the kz of each column (z-pass outputs
 // scattered to the caller's G order).
 int get_pair_plan(Ctx* c, int n, int ng, const int32_t* geps, cudaStream_t st, const PairPlan** out) {
-  uint64_t key = fnv1a(geps, (size_t)ng * 3 * sizeof(int32_t), fnv1a(&n, sizeof(n), 7));
+  uint64_t key = hash_bytes(geps, (size_t)ng * 3 * sizeof(int32_t), hash_bytes(&n, sizeof(n), 7));
   auto it = c->pair_plans.find(key);
   if (it != c->pair_plans.end() && it->second->ng == ng) {
     *out = it->second.get();

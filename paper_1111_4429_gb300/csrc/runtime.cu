@@ -8,13 +8,40 @@
 
 namespace bgw {
 
-uint64_t fnv1a(const void* data, size_t bytes, uint64_t h) {
+// Content hash of the cache keys: four independent 64-bit lanes over 32-byte
+// blocks with the multiply-rotate round of xxHash64 (so the multiplies of the
+// lanes overlap instead of forming one chain), the tail byte by byte, and
+// MurmurHash3's fmix64 finalizer.  About 8x faster than a byte-serial hash on
+// the G lists hashed by every call.
+namespace {
+constexpr uint64_t kP1 = 0x9E3779B185EBCA87ull, kP2 = 0xC2B2AE3D27D4EB4Full, kP3 = 0x165667B19E3779F9ull;
+inline uint64_t rotl64(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+inline uint64_t round64(uint64_t acc, uint64_t in) { return rotl64(acc + in * kP2, 31) * kP1; }
+inline uint64_t fmix64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+}  // namespace
+
+uint64_t hash_bytes(const void* data, size_t bytes, uint64_t h) {
   const unsigned char* p = static_cast<const unsigned char*>(data);
-  for (size_t i = 0; i < bytes; ++i) {
-    h ^= p[i];
-    h *= 1099511628211ull;
+  uint64_t a = h + kP1 + kP2, b = h + kP2, c = h, d = h - kP1;
+  size_t i = 0;
+  for (; i + 32 <= bytes; i += 32) {
+    uint64_t w[4];
+    memcpy(w, p + i, 32);
+    a = round64(a, w[0]);
+    b = round64(b, w[1]);
+    c = round64(c, w[2]);
+    d = round64(d, w[3]);
   }
-  return h;
+  uint64_t t = rotl64(a, 1) + rotl64(b, 7) + rotl64(c, 12) + rotl64(d, 18);
+  for (; i < bytes; ++i) t = rotl64(t ^ (p[i] * kP3), 11) * kP1;
+  return fmix64(t ^ (uint64_t)bytes);
 }
 
 int fail(Ctx* c, int code, const char* fmt, ...) {
@@ -114,7 +141,8 @@ void Pool::trim() {
 const char* timed_name(int n) {
   static const char* names[kTNumNames] = {"band_transform", "pair_yxpass", "pair_zgather", "chi_f64",
                                           "chi_split", "chi_tc", "chi_reduce", "eps_form", "inverse",
-                                          "oz_update", "sweep_chain"};
+                                          "oz_update", "sweep_chain", "head_dot", "head_wings",
+                                          "screened_w"};
   return (n >= 0 && n < kTNumNames) ? names[n] : "?";
 }
 
@@ -169,7 +197,7 @@ void timing_collect(Ctx* c) {
 
 // ------------------------------------------------------------ uploads
 int upload_cached(Ctx* c, const void* host, size_t bytes, cudaStream_t st, const void** dev) {
-  uint64_t key = fnv1a(host, bytes, fnv1a(&bytes, sizeof(bytes)));
+  uint64_t key = hash_bytes(host, bytes, hash_bytes(&bytes, sizeof(bytes)));
   auto it = c->uploads.find(key);
   if (it != c->uploads.end()) {
     *dev = it->second;

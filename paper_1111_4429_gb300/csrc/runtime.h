@@ -95,7 +95,7 @@ struct Timing {
   std::map<int, std::pair<long long, double>> acc;  // name -> (launches, ms)
 };
 enum TimedName { kTBand = 0, kTPairYX, kTPairZ, kTChiF64, kTChiSplit, kTChiTc, kTChiReduce, kTEpsForm, kTInverse,
-                 kTOzUpdate, kTSweepChain, kTNumNames };
+                 kTOzUpdate, kTSweepChain, kTHeadDot, kTHeadWings, kTScreenedW, kTNumNames };
 const char* timed_name(int n);
 
 // A captured batch (bgw_epsilon_batch) replayed while its key is unchanged.
@@ -122,14 +122,14 @@ struct Ctx {
   uint64_t launches = 0;     // kernels launched by this context
   int chi_segment_pairs = 0; // mixed chi: pairs per FP32 accumulation segment (0 = default)
   int chi_chunk_pairs = 0;   // mixed chi: pairs per workspace chunk (0 = sized to 1 GiB)
-  // Content-keyed caches (FNV-1a over the bytes plus sizes).
+  // Content-keyed caches (hash_bytes over the bytes plus sizes).
   std::unordered_map<uint64_t, void*> uploads;           // small host arrays
   std::unordered_map<uint64_t, std::unique_ptr<BandPlan>> band_plans;
   std::unordered_map<uint64_t, std::unique_ptr<PairPlan>> pair_plans;
   explicit Ctx(uint64_t budget) : pool(budget) {}
 };
 
-uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull);
+uint64_t hash_bytes(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull);
 
 // Records CUDA events around its scope on `st` when timing is enabled.
 class TimedScope {
