@@ -18,6 +18,9 @@ epsilon":
 * Eq. (screened_interaction): W_GG' = eps^-1_GG' v(q+G').
 * Eq. (retarded_advanced_epsilon) at E = i omega, delta -> 0: the pair weight
   becomes Delta / (Delta^2 + omega^2), Delta = E_v - E_c.
+* Eq. (retarded_advanced_epsilon) on the real axis with broadening delta: complex
+  weights, a non-Hermitian chi and eps~ (inverted with pivoting); the
+  frequency grid of Fig. (frequency_grid).
 
 Pair index p = v * nc + c (valence-major).  All floating point is float64 /
 complex128.  G lists are integer triples in reciprocal-lattice units; FFT
@@ -178,6 +181,51 @@ def chi_entries(M_rows_g: np.ndarray, M_rows_gp: np.ndarray, w: np.ndarray,
 
 
 # ---------------------------------------------------------------------------
+# Real-axis ("full-frequency") response, Eq. (retarded_advanced_epsilon)
+# ---------------------------------------------------------------------------
+
+def chi_weights_real(ev: np.ndarray, ec: np.ndarray, energy, delta: float,
+                     advanced: bool = False) -> np.ndarray:
+    """Complex pair weights of Eq. retarded_advanced_epsilon at frequency E.
+
+    w_p = (1/2) [1/(D - E - s i delta) + 1/(D + E + s i delta)], D = E_v - E_c,
+    s = +1 for the retarded function (upper signs), -1 for the advanced one.
+    `energy` may be complex: E = i omega with delta = 0 gives the imaginary-axis
+    weight D / (D^2 + omega^2) of chi_weights.
+    """
+    d = (np.asarray(ev, dtype=np.float64)[:, None] - np.asarray(ec, dtype=np.float64)[None, :]).ravel()
+    s = -1.0 if advanced else 1.0
+    e = complex(energy)
+    return 0.5 * (1.0 / (d - e - s * 1j * delta) + 1.0 / (d + e + s * 1j * delta))
+
+
+def frequency_grid(spacing: float, low_cutoff: float, high_cutoff: float, increment: float) -> np.ndarray:
+    """Real-frequency grid of Section "RPA Dielectric Matrix: epsilon" (Fig.
+    frequency_grid): 0, spacing, 2 spacing, ... while <= low_cutoff; after the
+    last uniform point every step is `increment` longer than the one before,
+    while the frequency stays <= high_cutoff.  Points k*spacing are formed by
+    multiplication; a relative slack of 1e-12 absorbs rounding at the cutoffs.
+    """
+    if not (spacing > 0 and increment >= 0 and 0 <= low_cutoff <= high_cutoff):
+        raise ValueError("need spacing > 0, increment >= 0, 0 <= low <= high")
+    tol = 1e-12
+    pts = []
+    k = 0
+    while k * spacing <= low_cutoff * (1 + tol) + tol:
+        pts.append(k * spacing)
+        k += 1
+    e = pts[-1]
+    step = spacing
+    while True:
+        step += increment
+        e = e + step
+        if e > high_cutoff * (1 + tol) + tol:
+            break
+        pts.append(e)
+    return np.array(pts, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
 # Dielectric matrix and its inverse, Eqs. (epsilon), (untruncated_bare_coulomb)
 # ---------------------------------------------------------------------------
 
@@ -268,6 +316,24 @@ def epsinv_sym(chi_m: np.ndarray, v: np.ndarray, tier: int = 2):
     """eps~ and eps~^-1 from chi and v."""
     e = eps_sym(chi_m, v)
     return e, (inv_gauss_jordan(e) if tier == 1 else inv(e))
+
+
+def solve_real(system, energies: Sequence[float], delta: float, advanced: bool = False,
+               model: str = "bulk", rc: float = 0.0):
+    """Real-axis chain for one q-point (Eq. retarded_advanced_epsilon in the
+    symmetric Coulomb form): per frequency E, chi^{r/a}(E), eps~ = I - V^1/2
+    chi V^1/2 (no longer Hermitian) and its inverse by an LU with partial
+    pivoting.  Returns dict(M, chi[f], eps[f], epsinv[f], v)."""
+    M = mtxel_fft(system.gv, system.cv, system.gc, system.cc, system.geps, system.fft)
+    v = coulomb(system.bvec, system.q_frac, system.geps, model, rc)
+    xs, es, eis = [], [], []
+    for e in energies:
+        x = chi(M, chi_weights_real(system.ev, system.ec, e, delta, advanced), system.omega)
+        ee, ei = epsinv_sym(x, v)
+        xs.append(x)
+        es.append(ee)
+        eis.append(ei)
+    return dict(M=M, chi=np.array(xs), eps=np.array(es), epsinv=np.array(eis), v=v)
 
 
 def solve(system, omega: Optional[float] = None, tier: int = 2, model: str = "bulk", rc: float = 0.0):

@@ -392,3 +392,78 @@ def test_q0_head_direct_dot_and_limit():
         assert np.abs(wing).max() < 1.0
     assert -20 < heads[0] < -1
     assert abs(heads[0] - heads[1]) <= 1e-3 * abs(heads[1])        # O(q0) approach to the limit
+
+
+# ------------------------------------------------- real-axis (full-frequency) response
+
+def test_real_axis_weights_limits_signs_and_conjugation():
+    ev = np.array([-0.4, -0.05])
+    ec = np.array([0.1, 0.35, 1.2])
+    d = (ev[:, None] - ec[None, :]).ravel()
+    e, dl = 0.3, 0.07
+    wr = oracle.chi_weights_real(ev, ec, e, dl)
+    wa = oracle.chi_weights_real(ev, ec, e, dl, advanced=True)
+    # real and imaginary parts written out separately (upper signs: retarded)
+    re = 0.5 * ((d - e) / ((d - e) ** 2 + dl ** 2) + (d + e) / ((d + e) ** 2 + dl ** 2))
+    im = 0.5 * dl * (1 / ((d - e) ** 2 + dl ** 2) - 1 / ((d + e) ** 2 + dl ** 2))
+    assert np.allclose(wr.real, re, rtol=1e-14, atol=0) and np.allclose(wr.imag, im, rtol=1e-13, atol=0)
+    assert np.all(wr.imag < 0)                          # absorption: Im chi^r <= 0 for E > 0
+    assert np.array_equal(wa, np.conj(wr))
+    # E = i omega, delta = 0: the imaginary-axis weight; E = 0: Delta / (Delta^2 + delta^2)
+    assert np.allclose(oracle.chi_weights_real(ev, ec, 0.8j, 0.0), oracle.chi_weights(ev, ec, 0.8), rtol=1e-15)
+    assert np.allclose(oracle.chi_weights_real(ev, ec, 0.0, dl), oracle.chi_weights(ev, ec, dl), rtol=1e-15)
+    assert np.allclose(oracle.chi_weights_real(ev, ec, 0.0, 0.0), oracle.chi_weights(ev, ec), rtol=1e-15)
+
+
+def test_frequency_grid_closed_form():
+    g = oracle.frequency_grid(0.1, 0.5, 2.0, 0.1)
+    assert np.allclose(g, [0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.7, 1.0, 1.4, 1.9], atol=1e-15)
+    assert np.allclose(oracle.frequency_grid(0.25, 1.0, 2.0, 0.0), np.arange(9) * 0.25, atol=1e-15)
+    g = oracle.frequency_grid(0.2, 1.0, 10.0, 0.05)
+    steps = np.diff(g)
+    assert np.allclose(steps[:5], 0.2) and np.allclose(np.diff(steps[5:]), 0.05) and g[-1] <= 10.0 + 1e-11
+    assert g[-1] + steps[-1] + 0.05 > 10.0
+    with pytest.raises(ValueError):
+        oracle.frequency_grid(0.0, 1.0, 2.0, 0.1)
+
+
+def test_real_axis_chi_structure():
+    s = _tiny(seed=12, nv=3, nc=9)
+    m = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    for e in (0.2, 0.9):
+        wr = oracle.chi_weights_real(s.ev, s.ec, e, 0.05)
+        xr = oracle.chi(m, wr, s.omega)
+        xa = oracle.chi(m, oracle.chi_weights_real(s.ev, s.ec, e, 0.05, advanced=True), s.omega)
+        assert np.allclose(xa, np.conj(xr).T, atol=1e-15)
+        assert np.linalg.norm(xr - np.conj(xr).T) > 1e-3 * np.linalg.norm(xr)   # not Hermitian
+        # the anti-Hermitian part (chi - chi^H) / 2i is negative semidefinite
+        lam = np.linalg.eigvalsh((xr - np.conj(xr).T) / 2j)
+        assert lam.max() <= 1e-14 * np.abs(lam).max()
+        assert np.allclose(oracle.chi_direct(m, wr, s.omega), xr, atol=1e-14)
+    # E = 0: chi^r(0; delta) = chi(i omega = delta), real weights, Hermitian
+    x0 = oracle.chi(m, oracle.chi_weights_real(s.ev, s.ec, 0.0, 0.3), s.omega)
+    assert np.allclose(x0, oracle.chi(m, oracle.chi_weights(s.ev, s.ec, 0.3), s.omega), atol=1e-15)
+
+
+def test_real_axis_plane_wave_closed_form_and_adjoint_inverse():
+    s, iv, ic = _plane_wave_system(seed=8)
+    e, dl = 0.6, 0.05
+    r = oracle.solve_real(s, [e], dl)
+    gidx = {tuple(g): i for i, g in enumerate(s.geps.tolist())}
+    diag = np.zeros(s.ng, dtype=np.complex128)
+    for v in range(s.nv):
+        for c in range(s.nc):
+            d = tuple((s.gv[iv[v]] - s.gc[ic[c]]).tolist())
+            if d in gidx:
+                dd = s.ev[v] - s.ec[c]
+                diag[gidx[d]] += (4 / s.omega) * 0.5 * (1 / (dd - e - 1j * dl) + 1 / (dd + e + 1j * dl))
+    assert np.allclose(r["chi"][0], np.diag(diag), atol=1e-14)
+    assert np.allclose(r["epsinv"][0], np.diag(1.0 / (1.0 - r["v"] * diag)), atol=1e-13)
+    # advanced = adjoint of retarded, through the whole chain
+    s2 = _tiny(seed=13, nv=3, nc=9)
+    rr = oracle.solve_real(s2, [0.4, 1.1], 0.04)
+    ra = oracle.solve_real(s2, [0.4, 1.1], 0.04, advanced=True)
+    for f in range(2):
+        assert np.allclose(ra["epsinv"][f], np.conj(rr["epsinv"][f]).T, atol=1e-12)
+        # tier 1 (Gauss-Jordan with partial pivoting) = tier 2 (library LU)
+        assert _rel(oracle.inv_gauss_jordan(rr["eps"][f]), rr["epsinv"][f]) < 1e-13
