@@ -389,6 +389,59 @@ int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell,
                 int ng, const int32_t* geps, int nfreq, const double* omega,
                 int prec, int nc_chunk, void* chi, void* epsinv, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Real axis ("full frequency"): the retarded or advanced response of Eq.
+ * retarded_advanced_epsilon at real frequencies E_f with broadening delta,
+ *   chi_f[G][G'] (+)= (4/Omega) sum_p w_p(E_f) conj(M[p][G]) M[p][G'],
+ *   w_p(E) = (1/2) [1/(D_p - E - s i delta) + 1/(D_p + E + s i delta)],
+ * D_p = E_v - E_c, s = +1 retarded (advanced = 0), -1 advanced (advanced =
+ * 1).  The weights are complex, so chi is not Hermitian (chi^a = (chi^r)^H);
+ * every element is computed.  At E = 0 the weight is D/(D^2 + delta^2), the
+ * imaginary-axis weight at omega = delta.
+ *   energy host double [nfreq] (Ha, finite), delta > 0 (Ha)
+ *   M, prec, accumulate, chi as bgw_chi_sum (chi [nfreq][ng][ng], both
+ *   triangles).  The mixed precisions split X = M and Y = w M (two operand
+ *   sets) and run every 128 x 128 tile on the tensor cores.
+ * EINVAL for nfreq < 1, a non-finite energy, delta <= 0 or advanced not 0/1. */
+int bgw_chi_sum_real(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng,
+                     const void* M, const double* ev, const double* ec,
+                     int nfreq, const double* energy, double delta, int advanced,
+                     int prec, int accumulate, void* chi, void* stream);
+
+/* bgw_epsinv_general -- eps~ = I - sqrt(v_G) chi sqrt(v_G') for a general
+ * (non-Hermitian) chi, and its inverse by blocked Gauss-Jordan elimination
+ * with partial pivoting (pivot rows of each 32-column block chosen by a
+ * tournament of partial-pivoting LUs over 256-row slices; the paper inverts
+ * with ZGESV).  Arguments as bgw_epsinv; every element of chi is read.
+ * EUNSUPPORTED for ng > 14336; a zero pivot (singular eps~) sets
+ * BGW_ENUMERIC, reported by bgw_sync.                                      */
+int bgw_epsinv_general(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
+                       const int32_t* const* geps, const void* const* chi,
+                       void* const* eps, void* const* epsinv, void* stream);
+
+/* bgw_epsilon_real -- bgw_epsilon on the real axis: bgw_mtxel,
+ * bgw_chi_sum_real over conduction chunks, bgw_epsinv_general per frequency.
+ * chi and epsinv are c128 [nfreq][ng][ng]; other arguments as bgw_epsilon
+ * and bgw_chi_sum_real.                                                    */
+int bgw_epsilon_real(bgw_ctx* ctx, const bgw_cell* cell,
+                     int nv, int npw_v, const int32_t* gv, const void* cv, const double* ev,
+                     int nc, int npw_c, const int32_t* gc, const void* cc, const double* ec,
+                     int ng, const int32_t* geps, int nfreq, const double* energy,
+                     double delta, int advanced, int prec, int nc_chunk,
+                     void* chi, void* epsinv, void* stream);
+
+/* bgw_frequency_grid -- the real-frequency grid of the paper's full-frequency
+ * calculation (Fig. frequency_grid): 0, spacing, 2 spacing, ... while
+ * <= low_cutoff; after the last uniform point each step is `increment`
+ * longer than the one before, while the frequency stays <= high_cutoff (a
+ * relative slack of 1e-12 absorbs rounding at both cutoffs).  Writes up to
+ * max_points values to out (host, may be NULL to count) and the number of
+ * points to *npoints.  EINVAL for spacing <= 0, increment < 0, low < 0,
+ * high < low or more than 2^24 points; ENOMEM when out is too short (the
+ * count is still written).  Host only, no context.                        */
+int bgw_frequency_grid(double spacing, double low_cutoff, double high_cutoff, double increment,
+                       int max_points, double* out, int* npoints);
+
 #ifdef __cplusplus
 }
 #endif

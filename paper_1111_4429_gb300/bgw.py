@@ -26,6 +26,7 @@ PREC = {"fp64": BGW_PREC_FP64, "mix_fp16": BGW_PREC_MIX_FP16, "mix_bf16": BGW_PR
 EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_stats", "bgw_launch_count",
            "bgw_mtxel",
            "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_screened_w",
+           "bgw_chi_sum_real", "bgw_epsinv_general", "bgw_epsilon_real", "bgw_frequency_grid",
            "bgw_epsilon",
            "bgw_epsilon_batch", "bgw_serve_open", "bgw_serve_submit", "bgw_serve_poll", "bgw_serve_cancel",
            "bgw_serve_close")
@@ -123,6 +124,15 @@ def load() -> ctypes.CDLL:
     lib.bgw_serve_close.argtypes = [vp]
     lib.bgw_epsilon.argtypes = [vp, cellp, ci, ci, i32p, vp, dp, ci, ci, i32p, vp, dp, ci, i32p, ci, dp, ci,
                                 ci, vp, vp, vp]
+    cd = ctypes.c_double
+    lib.bgw_screened_w.argtypes = [vp, ci, cellp, ctypes.POINTER(ci), ctypes.POINTER(i32p), ctypes.POINTER(vp),
+                                   ctypes.POINTER(vp), vp]
+    lib.bgw_chi_sum_real.argtypes = [vp, cellp, ci, ci, ci, vp, dp, dp, ci, dp, cd, ci, ci, ci, vp, vp]
+    lib.bgw_epsinv_general.argtypes = [vp, ci, cellp, ctypes.POINTER(ci), ctypes.POINTER(i32p), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.bgw_epsilon_real.argtypes = [vp, cellp, ci, ci, i32p, vp, dp, ci, ci, i32p, vp, dp, ci, i32p, ci, dp, cd,
+                                     ci, ci, ci, vp, vp, vp]
+    lib.bgw_frequency_grid.argtypes = [cd, cd, cd, cd, ci, dp, ctypes.POINTER(ci)]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_char_p if name == "bgw_last_error" else ctypes.c_int
     _lib = lib
@@ -166,6 +176,23 @@ def epsinv_noalloc(cell: Cell, geps, chi, eps, epsinv, stream=None) -> None:
                                 _stream(stream))
     if rc != BGW_OK:
         raise BgwError(rc, "bgw_epsinv_noalloc failed")
+
+
+def frequency_grid(spacing: float, low_cutoff: float, high_cutoff: float, increment: float) -> np.ndarray:
+    """bgw_frequency_grid: the paper's real-frequency grid (host only)."""
+    lib = load()
+    n = ctypes.c_int(0)
+    args = [ctypes.c_double(spacing), ctypes.c_double(low_cutoff), ctypes.c_double(high_cutoff),
+            ctypes.c_double(increment)]
+    rc = lib.bgw_frequency_grid(*args, 0, None, ctypes.byref(n))
+    if rc != BGW_OK:
+        raise BgwError(rc, "bgw_frequency_grid: bad parameters")
+    out = np.zeros(n.value, dtype=np.float64)
+    rc = lib.bgw_frequency_grid(*args, n.value, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                ctypes.byref(n))
+    if rc != BGW_OK:
+        raise BgwError(rc, "bgw_frequency_grid failed")
+    return out
 
 
 class Context:
@@ -247,6 +274,42 @@ class Context:
         ip = (ctypes.c_void_p * n)(*[_ptr(x) for x in epsinvs])
         self._check(self.lib.bgw_epsinv(self.h, n, carr, ng, gp, cp, ep, ip, _stream(stream)))
         return epsinvs
+
+    def chi_sum_real(self, cell: Cell, nv: int, nc: int, ng: int, M, ev, ec, energy, delta: float,
+                     advanced: bool, prec: int, accumulate: bool, chi, stream=None):
+        ev_, evp = _f64(ev)
+        ec_, ecp = _f64(ec)
+        e_, ep = _f64(energy)
+        self._check(self.lib.bgw_chi_sum_real(self.h, ctypes.byref(cell), nv, nc, ng, _ptr(M), evp, ecp,
+                                              e_.shape[0], ep, ctypes.c_double(delta), int(advanced), prec,
+                                              int(accumulate), _ptr(chi), _stream(stream)))
+        return chi
+
+    def epsinv_general(self, cells: Sequence[Cell], gepss: Sequence[np.ndarray], chis, eps, epsinvs, stream=None):
+        n = len(cells)
+        carr = (Cell * n)(*cells)
+        keep = [_i32(g) for g in gepss]
+        ng = (ctypes.c_int * n)(*[k[0].shape[0] for k in keep])
+        gp = (ctypes.POINTER(ctypes.c_int32) * n)(*[k[1] for k in keep])
+        cp = (ctypes.c_void_p * n)(*[_ptr(x) for x in chis])
+        ep = None if eps is None else (ctypes.c_void_p * n)(*[_ptr(x) for x in eps])
+        ip = (ctypes.c_void_p * n)(*[_ptr(x) for x in epsinvs])
+        self._check(self.lib.bgw_epsinv_general(self.h, n, carr, ng, gp, cp, ep, ip, _stream(stream)))
+        return epsinvs
+
+    def epsilon_real(self, cell: Cell, gv, cv, ev, gc, cc, ec, geps, energy, delta: float, advanced: bool,
+                     prec: int, nc_chunk: int, chi, epsinv, stream=None):
+        gv_, gvp = _i32(gv)
+        gc_, gcp = _i32(gc)
+        ge_, gep = _i32(geps)
+        ev_, evp = _f64(ev)
+        ec_, ecp = _f64(ec)
+        e_, ep = _f64(energy)
+        self._check(self.lib.bgw_epsilon_real(self.h, ctypes.byref(cell), cv.shape[0], gv_.shape[0], gvp, _ptr(cv),
+                                              evp, cc.shape[0], gc_.shape[0], gcp, _ptr(cc), ecp, ge_.shape[0], gep,
+                                              e_.shape[0], ep, ctypes.c_double(delta), int(advanced), prec, nc_chunk,
+                                              _ptr(chi), _ptr(epsinv), _stream(stream)))
+        return epsinv
 
     def screened_w(self, cells: Sequence[Cell], gepss: Sequence[np.ndarray], epsinvs, ws, stream=None):
         n = len(cells)

@@ -85,6 +85,15 @@ int check_energies(Ctx* c, int nv, const double* ev, int nc, const double* ec) {
   return BGW_OK;
 }
 
+int check_real_axis(Ctx* c, int nfreq, const double* energy, double delta, int advanced) {
+  if (nfreq <= 0 || !energy) return fail(c, BGW_EINVAL, "real axis: need nfreq >= 1 frequencies");
+  for (int f = 0; f < nfreq; ++f)
+    if (!isfinite(energy[f])) return fail(c, BGW_EINVAL, "energy[%d] is not finite", f);
+  if (!(delta > 0.0) || !isfinite(delta)) return fail(c, BGW_EINVAL, "broadening delta must be finite and > 0");
+  if (advanced != 0 && advanced != 1) return fail(c, BGW_EINVAL, "advanced must be 0 (retarded) or 1");
+  return BGW_OK;
+}
+
 int check_prec(Ctx* c, int prec) {
   if (prec != BGW_PREC_FP64 && prec != BGW_PREC_MIX_FP16 && prec != BGW_PREC_MIX_BF16)
     return fail(c, BGW_EINVAL, "unknown precision %d", prec);
@@ -336,6 +345,58 @@ int bgw_chi_sum(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng, cons
                  nfreq, static_cast<const double*>(dev_om), 4.0 / cell->omega, accumulate, chi, st);
 }
 
+int bgw_chi_sum_real(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng, const void* M, const double* ev,
+                     const double* ec, int nfreq, const double* energy, double delta, int advanced, int prec,
+                     int accumulate, void* chi, void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  int rc;
+  if (!cell || !(cell->omega > 0.0)) return fail(c, BGW_EINVAL, "cell is NULL or has no volume");
+  if ((rc = check_prec(c, prec)) != BGW_OK) return rc;
+  if (nv <= 0 || nc <= 0 || ng <= 0) return fail(c, BGW_EINVAL, "nv, nc, ng must be >= 1");
+  if (!M || !chi) return fail(c, BGW_EINVAL, "M or chi is NULL");
+  if ((rc = check_real_axis(c, nfreq, energy, delta, advanced)) != BGW_OK) return rc;
+  if ((rc = check_energies(c, nv, ev, nc, ec)) != BGW_OK) return rc;
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const void *dev_ev, *dev_ec, *dev_e;
+  if ((rc = upload_cached(c, ev, nv * sizeof(double), st, &dev_ev)) != BGW_OK) return rc;
+  if ((rc = upload_cached(c, ec, nc * sizeof(double), st, &dev_ec)) != BGW_OK) return rc;
+  if ((rc = upload_cached(c, energy, nfreq * sizeof(double), st, &dev_e)) != BGW_OK) return rc;
+  return chi_real_run(c, prec, nv, nc, ng, M, static_cast<const double*>(dev_ev), static_cast<const double*>(dev_ec),
+                      nfreq, static_cast<const double*>(dev_e), delta, advanced, 4.0 / cell->omega, accumulate, chi,
+                      st);
+}
+
+int bgw_epsinv_general(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, const int32_t* const* geps,
+                       const void* const* chi, void* const* eps, void* const* epsinv, void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  if (nmat <= 0 || !cells || !ng || !geps || !chi || !epsinv) return fail(c, BGW_EINVAL, "NULL argument array");
+  int rc;
+  for (int m = 0; m < nmat; ++m) {
+    if (ng[m] <= 0 || !geps[m] || !chi[m] || !epsinv[m])
+      return fail(c, BGW_EINVAL, "matrix %d: bad size or NULL pointer", m);
+    if (ng[m] > kGeneralMaxNg)
+      return fail(c, BGW_EUNSUPPORTED, "matrix %d: ng = %d exceeds %d for the general inverse", m, ng[m],
+                  kGeneralMaxNg);
+    if ((rc = check_q(c, &cells[m], ng[m], geps[m])) != BGW_OK) return rc;
+  }
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<const int32_t*> dgeps(nmat);
+  std::vector<const bgw_cell*> cp(nmat);
+  for (int m = 0; m < nmat; ++m) {
+    const void* dg;
+    if ((rc = upload_cached(c, geps[m], (size_t)ng[m] * 3 * sizeof(int32_t), st, &dg)) != BGW_OK) return rc;
+    dgeps[m] = static_cast<const int32_t*>(dg);
+    cp[m] = &cells[m];
+  }
+  return epsinv_general_run(c, nmat, ng, cp.data(), dgeps.data(), chi, eps, epsinv, st);
+}
+
 int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, const int32_t* const* geps,
                const void* const* chi, void* const* eps, void* const* epsinv, void* stream) {
   Ctx* c = impl(ctx);
@@ -553,12 +614,22 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   return BGW_OK;
 }
 
-extern "C" {
+namespace {
 
-int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv,
+// Frequencies of one whole-path call: the imaginary axis (nfreq = 0: static)
+// or the real axis with broadening (bgw_epsilon_real).
+struct FreqArgs {
+  bool real = false;
+  int nfreq = 0;
+  const double* w = nullptr;   // omega (imaginary axis) or E (real axis), host
+  double delta = 0.0;
+  int advanced = 0;
+};
+
+int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv,
                 const double* ev, int nc, int npw_c, const int32_t* gc, const void* cc, const double* ec, int ng,
-                const int32_t* geps, int nfreq, const double* omega, int prec, int nc_chunk, void* chi,
-                void* epsinv, void* stream) {
+                const int32_t* geps, const FreqArgs& fa, int prec, int nc_chunk, void* chi, void* epsinv,
+                void* stream) {
   Ctx* c = impl(ctx);
   if (!c) return BGW_EINVAL;
   int n, rc;
@@ -566,7 +637,15 @@ int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
     return rc;
   if ((rc = check_energies(c, nv, ev, nc, ec)) != BGW_OK) return rc;
   if ((rc = check_q(c, cell, ng, geps)) != BGW_OK) return rc;
-  if (nfreq < 0 || (nfreq > 0 && !omega)) return fail(c, BGW_EINVAL, "bad frequency list");
+  const int nfreq = fa.nfreq;
+  const double* omega = fa.w;
+  if (fa.real) {
+    if ((rc = check_real_axis(c, nfreq, omega, fa.delta, fa.advanced)) != BGW_OK) return rc;
+    if (ng > kGeneralMaxNg)
+      return fail(c, BGW_EUNSUPPORTED, "ng = %d exceeds %d for the general inverse", ng, kGeneralMaxNg);
+  } else if (nfreq < 0 || (nfreq > 0 && !omega)) {
+    return fail(c, BGW_EINVAL, "bad frequency list");
+  }
   if (nc_chunk <= 0 || nc_chunk > nc) nc_chunk = nc;
   DeviceGuard g(c->device);
   if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
@@ -614,7 +693,7 @@ int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
   HeadPlan hp;
   Scratch s_h;
   s_h.pool = &c->pool;
-  if ((rc = head_prepare(c, cell, npw_v, gv, npw_c, gc, ng, geps, prec, st, &hp)) != BGW_OK) return rc;
+  if (!fa.real && (rc = head_prepare(c, cell, npw_v, gv, npw_c, gc, ng, geps, prec, st, &hp)) != BGW_OK) return rc;
   if (hp.g0 >= 0 && (rc = c->pool.alloc((size_t)nv * nc_chunk * sizeof(double2), &s_h.ptr)) != BGW_OK)
     return fail(c, rc, "head scratch");
   for (int c0 = 0; c0 < nc; c0 += nc_chunk) {
@@ -624,10 +703,15 @@ int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
     if (hp.g0 >= 0 &&
         (rc = head_dot(c, &hp, nv, d_cv, npw_v, ncc, cc0, ng, s_M.ptr, s_h.as<double2>(), st)) != BGW_OK)
       return rc;
-    if ((rc = chi_run(c, prec, nv, ncc, ng, s_M.ptr, static_cast<const double*>(dev_ev),
-                      static_cast<const double*>(dev_ec) + c0, nfreq, static_cast<const double*>(dev_om),
-                      4.0 / cell->omega, c0 > 0, d_chi, st, &hp, s_h.as<double2>())) != BGW_OK)
-      return rc;
+    if (fa.real)
+      rc = chi_real_run(c, prec, nv, ncc, ng, s_M.ptr, static_cast<const double*>(dev_ev),
+                        static_cast<const double*>(dev_ec) + c0, nfreq, static_cast<const double*>(dev_om), fa.delta,
+                        fa.advanced, 4.0 / cell->omega, c0 > 0, d_chi, st);
+    else
+      rc = chi_run(c, prec, nv, ncc, ng, s_M.ptr, static_cast<const double*>(dev_ev),
+                   static_cast<const double*>(dev_ec) + c0, nfreq, static_cast<const double*>(dev_om),
+                   4.0 / cell->omega, c0 > 0, d_chi, st, &hp, s_h.as<double2>());
+    if (rc != BGW_OK) return rc;
   }
   {
     std::vector<int> ngv(nrow, ng);
@@ -639,14 +723,75 @@ int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
       chis[f] = static_cast<char*>(d_chi) + f * n2;
       invs[f] = static_cast<char*>(d_inv) + f * n2;
     }
-    if ((rc = epsinv_batch_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr,
-                               invs.data(), st, use_tc_inverse(c, prec))) != BGW_OK)
-      return rc;
+    if (fa.real)
+      rc = epsinv_general_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st);
+    else
+      rc = epsinv_batch_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
+                            use_tc_inverse(c, prec));
+    if (rc != BGW_OK) return rc;
   }
   if (chi && !chi_dev) BGW_CUDA(c, cudaMemcpyAsync(chi, d_chi, nrow * n2, cudaMemcpyDeviceToHost, st));
   if (!inv_dev) BGW_CUDA(c, cudaMemcpyAsync(epsinv, d_inv, nrow * n2, cudaMemcpyDeviceToHost, st));
   if (!inv_dev || (chi && !chi_dev)) return bgw_sync(ctx, stream);
   return BGW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv,
+                const double* ev, int nc, int npw_c, const int32_t* gc, const void* cc, const double* ec, int ng,
+                const int32_t* geps, int nfreq, const double* omega, int prec, int nc_chunk, void* chi,
+                void* epsinv, void* stream) {
+  FreqArgs fa;
+  fa.nfreq = nfreq;
+  fa.w = omega;
+  return epsilon_run(ctx, cell, nv, npw_v, gv, cv, ev, nc, npw_c, gc, cc, ec, ng, geps, fa, prec, nc_chunk, chi,
+                     epsinv, stream);
+}
+
+int bgw_epsilon_real(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32_t* gv, const void* cv,
+                     const double* ev, int nc, int npw_c, const int32_t* gc, const void* cc, const double* ec,
+                     int ng, const int32_t* geps, int nfreq, const double* energy, double delta, int advanced,
+                     int prec, int nc_chunk, void* chi, void* epsinv, void* stream) {
+  FreqArgs fa;
+  fa.real = true;
+  fa.nfreq = nfreq;
+  fa.w = energy;
+  fa.delta = delta;
+  fa.advanced = advanced;
+  return epsilon_run(ctx, cell, nv, npw_v, gv, cv, ev, nc, npw_c, gc, cc, ec, ng, geps, fa, prec, nc_chunk, chi,
+                     epsinv, stream);
+}
+
+int bgw_frequency_grid(double spacing, double low_cutoff, double high_cutoff, double increment, int max_points,
+                       double* out, int* npoints) {
+  if (!npoints || !(spacing > 0.0) || !(increment >= 0.0) || !(low_cutoff >= 0.0) || !(high_cutoff >= low_cutoff) ||
+      !isfinite(spacing) || !isfinite(increment) || !isfinite(high_cutoff))
+    return BGW_EINVAL;
+  const double tol = 1e-12;
+  int n = 0;
+  auto put = [&](double e) {
+    if (out && n < max_points) out[n] = e;
+    ++n;
+  };
+  double e = 0.0;
+  for (long long k = 0; (double)k * spacing <= low_cutoff * (1 + tol) + tol; ++k) {
+    e = (double)k * spacing;
+    put(e);
+    if (n > (1 << 24)) return BGW_EINVAL;
+  }
+  double step = spacing;
+  for (;;) {
+    step += increment;
+    e += step;
+    if (e > high_cutoff * (1 + tol) + tol) break;
+    put(e);
+    if (n > (1 << 24)) return BGW_EINVAL;
+  }
+  *npoints = n;
+  return (out && n > max_points) ? BGW_ENOMEM : BGW_OK;
 }
 
 }  // extern "C"

@@ -145,10 +145,13 @@ struct Layout {
 };
 
 // grid: nseg * ntiles CTAs (segment-major), block 128, dynamic smem
-// STAGES * stage + 1 KiB (alignment) + barriers.
+// STAGES * stage + 1 KiB (alignment) + barriers.  The A operand (rows G)
+// reads planes 0..3; the B operand (columns G') reads the planes starting at
+// row brow of the tensor map: 0 for the Hermitian product (X = Y), 4 ngpad
+// when a second operand Y follows X (real-axis chi).
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
-    chi_tc_kernel(const __grid_constant__ CUtensorMap tmap, int ngpad, int nkb, int kb_per_seg, int ntiles,
+    chi_tc_kernel(const __grid_constant__ CUtensorMap tmap, int ngpad, int brow, int nkb, int kb_per_seg, int ntiles,
                   const int2* __restrict__ tiles, int bf16, float* __restrict__ work, int* __restrict__ status) {
   using L = Layout<BN>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int pl = 0; pl < 4; ++pl) {
         tma_load_2d(st + pl * L::kATile, &tmap, &full[s], kx, pl * ngpad + row0);
-        tma_load_2d(st + 4 * L::kATile + pl * L::kBTile, &tmap, &full[s], kx, pl * ngpad + col0);
+        tma_load_2d(st + 4 * L::kATile + pl * L::kBTile, &tmap, &full[s], kx, brow + pl * ngpad + col0);
       }
       issued = i + 1;
     }
@@ -379,6 +382,124 @@ __global__ void split_kernel(const float2* __restrict__ M, const double* __restr
   }
 }
 
+// Real-axis operands: X = M 2^eX and Y = (w_p M) 2^eY with complex w_p.
+// out[0] = max|Re,Im| of M, out[1] = that of w M (float bits, values >= 0).
+__global__ void maxabs_general_kernel(const float2* __restrict__ M, const double2* __restrict__ w, long long K,
+                                      int ng, unsigned int* __restrict__ out) {
+  float mx = 0.f, my = 0.f;
+  const long long n = K * ng;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / ng;
+    const float2 v = M[e];
+    const float wr = (float)w[p].x, wi = (float)w[p].y;
+    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    my = fmaxf(my, fmaxf(fabsf(fmaf(wr, v.x, -wi * v.y)), fabsf(fmaf(wr, v.y, wi * v.x))));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, __float_as_uint(mx));
+    atomicMax(out + 1, __float_as_uint(my));
+  }
+}
+
+template <typename H>
+__device__ __forceinline__ void split4(float2 v, H* planes, size_t plane, size_t o) {
+  H rh, ih, rl, il;
+  if constexpr (std::is_same<H, __half>::value) {
+    rh = __float2half_rn(v.x);
+    ih = __float2half_rn(v.y);
+    rl = __float2half_rn(v.x - __half2float(rh));
+    il = __float2half_rn(v.y - __half2float(ih));
+  } else {
+    rh = __float2bfloat16_rn(v.x);
+    ih = __float2bfloat16_rn(v.y);
+    rl = __float2bfloat16_rn(v.x - __bfloat162float(rh));
+    il = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+  }
+  planes[o] = rh;
+  planes[plane + o] = ih;
+  planes[2 * plane + o] = rl;
+  planes[3 * plane + o] = il;
+}
+
+// planes[0..3] <- X = M 2^eX, planes[4..7] <- Y = w M 2^eY, transposed to
+// [plane][g][p] like split_kernel.
+template <typename H>
+__global__ void split_general_kernel(const float2* __restrict__ M, const double2* __restrict__ w, long long p0,
+                                     long long K, int ng, int ngpad, int kpad,
+                                     const unsigned int* __restrict__ maxbits, int bf16, H* __restrict__ planes) {
+  __shared__ float2 tx_[32][33];
+  __shared__ float2 ty_[32][33];
+  const long long pc0 = (long long)blockIdx.x * 32;
+  const int g0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const float sx = ldexpf(1.f, scale_exp(maxbits, bf16)), sy = ldexpf(1.f, scale_exp(maxbits + 1, bf16));
+  for (int r = ty; r < 32; r += 8) {
+    const long long p = pc0 + r;
+    const int g = g0 + tx;
+    float2 x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+    if (p < K && g < ng) {
+      const float2 v = M[(p0 + p) * ng + g];
+      const float wr = (float)w[p0 + p].x, wi = (float)w[p0 + p].y;
+      x = make_float2(v.x * sx, v.y * sx);
+      y = make_float2(fmaf(wr, v.x, -wi * v.y) * sy, fmaf(wr, v.y, wi * v.x) * sy);
+    }
+    tx_[r][tx] = x;
+    ty_[r][tx] = y;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)ngpad * kpad;
+  for (int r = ty; r < 32; r += 8) {
+    const int g = g0 + r;
+    const long long p = pc0 + tx;
+    const size_t o = (size_t)g * kpad + p;
+    split4<H>(tx_[tx][r], planes, plane, o);
+    split4<H>(ty_[tx][r], planes + 4 * plane, plane, o);
+  }
+}
+
+// General (non-Hermitian) reduce: every element of every tile, factor
+// 2^{-(eX + eY)}, no mirroring.
+template <int BN>
+__global__ void reduce_general_kernel(const float* __restrict__ work, int nseg, int ntiles,
+                                      const int2* __restrict__ tiles, int ng, double factor,
+                                      const unsigned int* __restrict__ maxbits, int bf16, int accumulate,
+                                      double2* __restrict__ chi) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)BM * BN;
+  if (e >= per * ntiles) return;
+  const int tix = (int)(e / per);
+  const int r = (int)((e - (long long)tix * per) / BN), c = (int)(e % BN);
+  const int2 tl = tiles[tix];
+  const int g = tl.x * BM + r, gp = tl.y * BN + c;
+  if (g >= ng || gp >= ng) return;
+  float re = 0.f, rel = 0.f, im = 0.f, iml = 0.f;
+  for (int s = 0; s < nseg; ++s) {
+    const float* w = work + ((size_t)s * ntiles + tix) * 2 * per;
+    const float a = w[r * BN + c], b = w[per + r * BN + c];
+    float t = __fadd_rn(re, a);
+    float z = __fsub_rn(t, re);
+    rel = __fadd_rn(rel, __fadd_rn(__fsub_rn(re, __fsub_rn(t, z)), __fsub_rn(a, z)));
+    re = t;
+    t = __fadd_rn(im, b);
+    z = __fsub_rn(t, im);
+    iml = __fadd_rn(iml, __fadd_rn(__fsub_rn(im, __fsub_rn(t, z)), __fsub_rn(b, z)));
+    im = t;
+  }
+  const double f = factor * ldexp(1.0, -(scale_exp(maxbits, bf16) + scale_exp(maxbits + 1, bf16)));
+  double2 v = make_double2(((double)re + (double)rel) * f, ((double)im + (double)iml) * f);
+  double2* dst = chi + (size_t)g * ng + gp;
+  if (accumulate) {
+    const double2 o = *dst;
+    v.x += o.x;
+    v.y += o.y;
+  }
+  *dst = v;
+}
+
 // chi[g][g'] (+)= factor 2^{-2e} sum_seg W, lower triangle of every tile,
 // mirrored (conjugated) into the upper triangle.  One thread per tile element.
 template <int BN>
@@ -451,26 +572,33 @@ constexpr int kSegPairsDefault = 512;
 // added into chi.
 constexpr size_t kChunkBytes = size_t(1) << 30;
 
-int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double* w, int nrow, double scale,
-                  int accumulate, void* chi, cudaStream_t st) {
+namespace {
+
+// Both products: the Hermitian one (wr: real weights, X = Y = M sqrt|w|,
+// lower tiles, mirrored) and the general one (wc: complex weights, X = M,
+// Y = w M, all tiles).
+int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const double* wr, const double2* wc, int nrow,
+               double scale, int accumulate, void* chi, cudaStream_t st) {
   using namespace tc;
+  const bool general = wc != nullptr;
   int rc;
   if ((rc = get_encode(c)) != BGW_OK) return rc;
   const int bf16 = prec == BGW_PREC_MIX_BF16;
   const int ntr = (ng + BM - 1) / BM, ntc = (ng + kBN - 1) / kBN;
   const int ngpad = std::max(ntr * BM, ntc * kBN);
+  const int nplanes = general ? 8 : 4;
   const int seg_pairs_opt = c->chi_segment_pairs > 0 ? c->chi_segment_pairs : kSegPairsDefault;
   const int kb_per_seg = std::max(1, seg_pairs_opt / BK);
   const long long seg_pairs = (long long)kb_per_seg * BK;
   std::vector<int2> tl;
   for (int I = 0; I < ntr; ++I)
     for (int J = 0; J < ntc; ++J)
-      if (J * kBN <= I * BM + BM - 1) tl.push_back(make_int2(I, J));
+      if (general || J * kBN <= I * BM + BM - 1) tl.push_back(make_int2(I, J));
   const int ntiles = (int)tl.size();
   const size_t seg_bytes = (size_t)ntiles * 2 * BM * kBN * sizeof(float);
   long long segs_per_chunk = std::max<long long>(1, (long long)(kChunkBytes / seg_bytes));
-  segs_per_chunk = std::min<long long>(segs_per_chunk,
-                                       std::max<long long>(1, (long long)(kChunkBytes / (8ull * ngpad * seg_pairs))));
+  segs_per_chunk = std::min<long long>(
+      segs_per_chunk, std::max<long long>(1, (long long)(kChunkBytes / (2ull * nplanes * ngpad * seg_pairs))));
   long long kchunk = std::min<long long>(segs_per_chunk * seg_pairs, (K + BK - 1) / BK * BK);
   if (c->chi_chunk_pairs > 0) kchunk = std::max<long long>(BK, (long long)c->chi_chunk_pairs / BK * BK);
   const long long kcpad = (kchunk + BK - 1) / BK * BK;
@@ -479,14 +607,14 @@ int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const do
   Scratch planes, work, mx;
   planes.pool = work.pool = mx.pool = &c->pool;
   const long long nseg_max = (kcpad / BK + kb_per_seg - 1) / kb_per_seg;
-  const size_t plane_bytes = (size_t)4 * ngpad * kcpad * 2;
+  const size_t plane_bytes = (size_t)nplanes * ngpad * kcpad * 2;
   const size_t work_bytes = (size_t)nseg_max * seg_bytes;
   if ((rc = c->pool.alloc(plane_bytes, &planes.ptr)) != BGW_OK || (rc = c->pool.alloc(work_bytes, &work.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc(sizeof(unsigned int), &mx.ptr)) != BGW_OK)
+      (rc = c->pool.alloc(2 * sizeof(unsigned int), &mx.ptr)) != BGW_OK)
     return fail(c, rc, "bgw_chi_sum (mixed): scratch allocation failed (planes %zu B, workspace %zu B)", plane_bytes,
                 work_bytes);
   CUtensorMap tmap;
-  cuuint64_t gdim[2] = {(cuuint64_t)kcpad, (cuuint64_t)4 * ngpad};
+  cuuint64_t gdim[2] = {(cuuint64_t)kcpad, (cuuint64_t)nplanes * ngpad};
   cuuint64_t gstride[1] = {(cuuint64_t)kcpad * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
   cuuint32_t estr[2] = {1, 1};
@@ -501,14 +629,19 @@ int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const do
   const size_t smem = (size_t)kStages * Layout<kBN>::kStage + 1024 + 256;
   BGW_CUDA(c, cudaFuncSetAttribute(chi_tc_kernel<kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
+  const int brow = general ? 4 * ngpad : 0;
   for (int f = 0; f < nrow; ++f) {
-    const double* wf = w + (size_t)f * K;
+    const double* wf = general ? nullptr : wr + (size_t)f * K;
+    const double2* wcf = general ? wc + (size_t)f * K : nullptr;
     {
       TimedScope ts(c, kTChiSplit, st);
-      BGW_CUDA(c, cudaMemsetAsync(mx.ptr, 0, sizeof(unsigned int), st));
+      BGW_CUDA(c, cudaMemsetAsync(mx.ptr, 0, 2 * sizeof(unsigned int), st));
       const long long n = K * ng;
       const unsigned mb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8);
-      maxabs_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wf, K, ng, mx.as<unsigned int>());
+      if (general)
+        maxabs_general_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wcf, K, ng, mx.as<unsigned int>());
+      else
+        maxabs_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wf, K, ng, mx.as<unsigned int>());
       c->launches += 1;
     }
     for (long long p0 = 0; p0 < K; p0 += kchunk) {
@@ -522,32 +655,58 @@ int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const do
         // rows of the planes are kcpad long (the tensor map's stride); a
         // shorter last chunk fills the first kpad of each row, and the GEMM
         // reads no further than nkb = kpad / BK k-blocks
-        if (bf16)
+        const unsigned int* mb = mx.as<unsigned int>();
+        if (general && bf16)
+          split_general_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(
+              static_cast<const float2*>(M), wcf, p0, kc, ng, ngpad, (int)kcpad, mb, 1, planes.as<__nv_bfloat16>());
+        else if (general)
+          split_general_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wcf, p0, kc, ng,
+                                                                   ngpad, (int)kcpad, mb, 0, planes.as<__half>());
+        else if (bf16)
           split_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, p0, kc, ng,
-                                                                  ngpad, (int)kcpad, mx.as<unsigned int>(), 1,
+                                                                  ngpad, (int)kcpad, mb, 1,
                                                                   planes.as<__nv_bfloat16>());
         else
           split_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, p0, kc, ng, ngpad,
-                                                           (int)kcpad, mx.as<unsigned int>(), 0, planes.as<__half>());
+                                                           (int)kcpad, mb, 0, planes.as<__half>());
       }
       {
         TimedScope ts(c, kTChiTc, st);
         chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
-            tmap, ngpad, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
+            tmap, ngpad, brow, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
             c->d_status);
       }
       {
         TimedScope ts(c, kTChiReduce, st);
         const long long ne = (long long)ntiles * BM * kBN;
-        reduce_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-            work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(),
-            bf16, (accumulate || p0 > 0) ? 1 : 0, static_cast<double2*>(chi) + (size_t)f * ng * ng);
+        double2* cf = static_cast<double2*>(chi) + (size_t)f * ng * ng;
+        const int acc = (accumulate || p0 > 0) ? 1 : 0;
+        if (general)
+          reduce_general_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+              work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, scale, mx.as<unsigned int>(),
+              bf16, acc, cf);
+        else
+          reduce_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+              work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(),
+              bf16, acc, cf);
       }
       BGW_CUDA(c, cudaGetLastError());
       c->launches += 3;
     }
   }
   return BGW_OK;
+}
+
+}  // namespace
+
+int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double* w, int nrow, double scale,
+                  int accumulate, void* chi, cudaStream_t st) {
+  return chi_tc_run(c, prec, K, ng, M, w, nullptr, nrow, scale, accumulate, chi, st);
+}
+
+int chi_real_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double2* w, int nrow,
+                       double scale, int accumulate, void* chi, cudaStream_t st) {
+  return chi_tc_run(c, prec, K, ng, M, nullptr, w, nrow, scale, accumulate, chi, st);
 }
 
 }  // namespace bgw

@@ -601,6 +601,31 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cel
 }
 
 // ---------------------------------------------------------------------------
+int eps_form_run(Ctx* c, const bgw_cell* cell, const int32_t* d_geps, int ng, const void* chi, double* sv,
+                 double2* A, void* eps, cudaStream_t st) {
+  TimedScope ts(c, kTEpsForm, st);
+  coulomb_sqrt_kernel<<<(ng + 255) / 256, 256, 0, st>>>(d_geps, ng, coulomb_args(cell), sv);
+  const size_t n2 = (size_t)ng * ng;
+  const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
+  eps_form_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(chi), sv, ng, A, static_cast<double2*>(eps));
+  BGW_CUDA(c, cudaGetLastError());
+  c->launches += 2;
+  return BGW_OK;
+}
+
+int gj_step_run(Ctx* c, double2* A, int ng, int k0, int kb, double2* dinv, double2* R, double2* Cp,
+                cudaStream_t st) {
+  const int nt = (ng + TU - 1) / TU;
+  const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
+  BGW_CUDA(c, cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
+  gj_diag_kernel<<<1, dim3(NB, NB), 0, st>>>(A, ng, k0, kb, dinv, c->d_status);
+  gj_panels_kernel<<<dim3((ng + 63) / 64, 1 + (ng + 255) / 256), 256, 0, st>>>(A, ng, k0, kb, dinv, R, Cp);
+  gj_update_kernel<<<dim3(nt, nt), 256, upd_smem, st>>>(A, ng, k0, kb, R, Cp);
+  BGW_CUDA(c, cudaGetLastError());
+  c->launches += 3;
+  return BGW_OK;
+}
+
 int screened_w_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
                    const void* const* epsinv, void* const* W, cudaStream_t st) {
   int ngmax = 0;

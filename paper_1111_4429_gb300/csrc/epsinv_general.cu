@@ -1,0 +1,279 @@
+// General (non-Hermitian) dielectric matrix and its inverse, for the real-axis
+// response of Eq. retarded_advanced_epsilon: with complex pair weights chi is
+// no longer Hermitian, eps~ = I - V^1/2 chi V^1/2 is a general complex matrix,
+// and its inverse needs pivoting (the paper inverts with ZGESV, an LU with
+// partial pivoting).
+//
+// Blocked Gauss-Jordan elimination with row interchanges, 32 columns a step:
+//   1. pivot rows for the block's columns among the rows not yet used, chosen
+//      by tournament pivoting: CTAs run a partial-pivoting LU on 256-row
+//      slices of the column panel and keep 32 candidates each; merge rounds
+//      run the same LU on up to 8 candidate sets at a time until 32 rows
+//      remain (the selection of a partial-pivoting LU of the panel when one
+//      slice holds every row, a tournament among slices otherwise);
+//   2. the chosen rows are swapped into the block's rows (whole rows of the
+//      working matrix: row operations on the augmented system), the
+//      interchanges recorded LAPACK-style (ipiv[j] >= j);
+//   3. one Gauss-Jordan block step without further pivoting (the block's
+//      diagonal block is the chosen rows, eliminated in their selection order).
+// After the last step the working matrix holds the inverse with permuted
+// columns; undoing the interchanges on the columns in reverse order gives
+// eps~^-1.
+#include <algorithm>
+#include <vector>
+
+#include "runtime.h"
+
+namespace bgw {
+
+namespace {
+
+constexpr int kPB = 32;      // block width of the Gauss-Jordan step
+constexpr int kTRows = 256;  // rows per selection CTA (one per thread)
+constexpr int kSwapCols = 64;
+
+__device__ __forceinline__ double cabs1(double2 z) { return fabs(z.x) + fabs(z.y); }
+
+// Partial-pivoting LU of nr (<= 256) rows x kb columns held in P; thread t
+// owns row t.  Picks, column by column, the active row of largest |Re|+|Im|
+// (ties: smallest global row), eliminates that column from the other active
+// rows.  Writes the global rows in selection order to sel and returns their
+// number (min(nr, kb)).
+__device__ int select_rows(double2 (*P)[kPB + 1], const int* gid, int nr, int kb, int* sel) {
+  __shared__ double wv[kTRows / 32];
+  __shared__ int wg[kTRows / 32], wl[kTRows / 32];
+  __shared__ int win;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  bool active = t < nr;
+  const int cnt = min(nr, kb);
+  for (int j = 0; j < cnt; ++j) {
+    double v = active ? cabs1(P[t][j]) : -1.0;
+    int g = active ? gid[t] : 0x7fffffff, l = t;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+      const int g2 = __shfl_xor_sync(0xffffffffu, g, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+      if (v2 > v || (v2 == v && g2 < g)) {
+        v = v2;
+        g = g2;
+        l = l2;
+      }
+    }
+    if (lane == 0) {
+      wv[warp] = v;
+      wg[warp] = g;
+      wl[warp] = l;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double bv = wv[0];
+      int bg = wg[0], bl = wl[0];
+      for (int w = 1; w < kTRows / 32; ++w)
+        if (wv[w] > bv || (wv[w] == bv && wg[w] < bg)) {
+          bv = wv[w];
+          bg = wg[w];
+          bl = wl[w];
+        }
+      win = bl;
+      sel[j] = bg;
+    }
+    __syncthreads();
+    const int w = win;
+    if (t == w) active = false;
+    const double2 pv = P[w][j];
+    const double m2 = pv.x * pv.x + pv.y * pv.y;
+    if (active && m2 > 0.0) {
+      const double2 a = P[t][j];
+      // l = a / pv
+      const double2 l = make_double2((a.x * pv.x + a.y * pv.y) / m2, (a.y * pv.x - a.x * pv.y) / m2);
+      for (int c = j + 1; c < kb; ++c) {
+        const double2 u = P[w][c];
+        P[t][c] = make_double2(P[t][c].x - (l.x * u.x - l.y * u.y), P[t][c].y - (l.x * u.y + l.y * u.x));
+      }
+    }
+    __syncthreads();
+  }
+  return cnt;
+}
+
+// Leaf round: CTA b takes rows k0 + 256 b ... of the panel.
+__global__ void __launch_bounds__(kTRows) pivot_leaf_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
+                                                            int* __restrict__ out, int* __restrict__ cnt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 (*P)[kPB + 1] = reinterpret_cast<double2 (*)[kPB + 1]>(smem_raw);
+  __shared__ int gid[kTRows];
+  __shared__ int sel[kPB];
+  const int r0 = k0 + blockIdx.x * kTRows;
+  const int nr = min(kTRows, ng - r0);
+  const int t = threadIdx.x;
+  gid[t] = r0 + t;
+  if (t < nr)
+    for (int c = 0; c < kb; ++c) P[t][c] = A[(size_t)(r0 + t) * ng + k0 + c];
+  __syncthreads();
+  const int n = select_rows(P, gid, nr, kb, sel);
+  __syncthreads();
+  if (t < n) out[blockIdx.x * kPB + t] = sel[t];
+  if (t == 0) cnt[blockIdx.x] = n;
+}
+
+// Merge round: CTA m takes candidate sets 8m .. 8m+7 (of ngroups).
+__global__ void __launch_bounds__(kTRows) pivot_merge_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
+                                                             const int* __restrict__ in, const int* __restrict__ cin,
+                                                             int ngroups, int* __restrict__ out,
+                                                             int* __restrict__ cout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 (*P)[kPB + 1] = reinterpret_cast<double2 (*)[kPB + 1]>(smem_raw);
+  __shared__ int gid[kTRows];
+  __shared__ int sel[kPB];
+  __shared__ int nr_s;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    int n = 0;
+    for (int g = blockIdx.x * 8; g < min(ngroups, blockIdx.x * 8 + 8); ++g)
+      for (int i = 0; i < cin[g]; ++i) gid[n++] = in[g * kPB + i];
+    nr_s = n;
+  }
+  __syncthreads();
+  const int nr = nr_s;
+  if (t < nr)
+    for (int c = 0; c < kb; ++c) P[t][c] = A[(size_t)gid[t] * ng + k0 + c];
+  __syncthreads();
+  const int n = select_rows(P, gid, nr, kb, sel);
+  __syncthreads();
+  if (t < n) out[blockIdx.x * kPB + t] = sel[t];
+  if (t == 0) cout[blockIdx.x] = n;
+}
+
+// Brings row sel[j] to row k0 + j for j < kb by successive interchanges
+// (recorded in ipiv[k0 + j]).  Every CTA replays the interchanges on the set
+// of affected rows (at most 64) and moves its 64 columns of them.
+__global__ void __launch_bounds__(256) pivot_swap_kernel(double2* __restrict__ A, int ng, int k0, int kb,
+                                                         const int* __restrict__ sel, int* __restrict__ ipiv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 (*buf)[kSwapCols] = reinterpret_cast<double2 (*)[kSwapCols]>(smem_raw);
+  __shared__ int pos[2 * kPB];   // positions of the affected rows
+  __shared__ int from[2 * kPB];  // original row that ends at pos[i]
+  __shared__ int ns;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    int n = 0;
+    for (int j = 0; j < kb; ++j) pos[n++] = k0 + j;
+    for (int j = 0; j < kb; ++j)
+      if (sel[j] >= k0 + kb) pos[n++] = sel[j];
+    for (int i = 0; i < n; ++i) from[i] = pos[i];
+    for (int j = 0; j < kb; ++j) {
+      int cur = -1;   // slot currently holding original row sel[j]
+      for (int i = 0; i < n; ++i)
+        if (from[i] == sel[j]) cur = i;
+      const int tmp = from[j];
+      from[j] = from[cur];
+      from[cur] = tmp;
+      if (blockIdx.x == 0) ipiv[k0 + j] = pos[cur];
+    }
+    ns = n;
+  }
+  __syncthreads();
+  const int n = ns;
+  const int c0 = blockIdx.x * kSwapCols;
+  for (int e = t; e < n * kSwapCols; e += 256) {
+    const int i = e / kSwapCols, cc = e % kSwapCols;
+    if (c0 + cc < ng && from[i] != pos[i]) buf[i][cc] = A[(size_t)from[i] * ng + c0 + cc];
+  }
+  __syncthreads();
+  for (int e = t; e < n * kSwapCols; e += 256) {
+    const int i = e / kSwapCols, cc = e % kSwapCols;
+    if (c0 + cc < ng && from[i] != pos[i]) A[(size_t)pos[i] * ng + c0 + cc] = buf[i][cc];
+  }
+}
+
+// Column j of the inverse is column src[j] of the working matrix: the
+// interchanges undone on the columns, last first.
+__global__ void colperm_build_kernel(const int* __restrict__ ipiv, int ng, int* __restrict__ src) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int j = 0; j < ng; ++j) src[j] = j;
+  for (int j = ng - 1; j >= 0; --j) {
+    const int p = ipiv[j];
+    const int tmp = src[j];
+    src[j] = src[p];
+    src[p] = tmp;
+  }
+}
+
+__global__ void __launch_bounds__(256) colperm_apply_kernel(double2* __restrict__ A, int ng,
+                                                            const int* __restrict__ src) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* row = reinterpret_cast<double2*>(smem_raw);
+  double2* a = A + (size_t)blockIdx.x * ng;
+  for (int j = threadIdx.x; j < ng; j += 256) row[j] = a[j];
+  __syncthreads();
+  for (int j = threadIdx.x; j < ng; j += 256) a[j] = row[src[j]];
+}
+
+}  // namespace
+
+int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
+                       const void* const* chi, void* const* eps, void* const* epsinv, cudaStream_t st) {
+  int ngmax = 0;
+  for (int m = 0; m < nmat; ++m) ngmax = std::max(ngmax, ng[m]);
+  const int nleaf_max = (ngmax + kTRows - 1) / kTRows;
+  Scratch sv, dinv, R, Cp, cand, ipiv;
+  sv.pool = dinv.pool = R.pool = Cp.pool = cand.pool = ipiv.pool = &c->pool;
+  int rc;
+  if ((rc = c->pool.alloc((size_t)ngmax * sizeof(double), &sv.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)kPB * kPB * sizeof(double2), &dinv.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)kPB * ngmax * sizeof(double2), &R.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)kPB * ngmax * sizeof(double2), &Cp.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)2 * nleaf_max * (kPB + 1) * sizeof(int), &cand.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)2 * ngmax * sizeof(int), &ipiv.ptr)) != BGW_OK)
+    return fail(c, rc, "general inverse: scratch allocation failed");
+  const size_t psmem = sizeof(double2) * kTRows * (kPB + 1);
+  const size_t ssmem = sizeof(double2) * 2 * kPB * kSwapCols;
+  BGW_CUDA(c, cudaFuncSetAttribute(pivot_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+  BGW_CUDA(c, cudaFuncSetAttribute(pivot_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+  BGW_CUDA(c, cudaFuncSetAttribute(pivot_swap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
+  BGW_CUDA(c, cudaFuncSetAttribute(colperm_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(double2) * ngmax)));
+  int* cbuf[2] = {cand.as<int>(), cand.as<int>() + (size_t)nleaf_max * (kPB + 1)};
+  int* piv = ipiv.as<int>();
+  int* src = piv + ngmax;
+  for (int m = 0; m < nmat; ++m) {
+    const int n = ng[m];
+    double2* A = static_cast<double2*>(epsinv[m]);
+    if ((rc = eps_form_run(c, cells[m], d_geps[m], n, chi[m], sv.as<double>(), A, eps ? eps[m] : nullptr, st)) !=
+        BGW_OK)
+      return rc;
+    TimedScope ts(c, kTInverse, st);
+    for (int k0 = 0; k0 < n; k0 += kPB) {
+      const int kb = std::min(kPB, n - k0);
+      int groups = (n - k0 + kTRows - 1) / kTRows;
+      int cur = 0;
+      {
+        TimedScope tp(c, kTPivot, st);
+        // candidates of set g at buf[g * 32], counts after the candidates
+        int* cnt0 = cbuf[0] + (size_t)nleaf_max * kPB;
+        pivot_leaf_kernel<<<groups, kTRows, psmem, st>>>(A, n, k0, kb, cbuf[0], cnt0);
+        c->launches += 1;
+        while (groups > 1) {
+          const int next = (groups + 7) / 8;
+          int* cin = cbuf[cur] + (size_t)nleaf_max * kPB;
+          int* cout = cbuf[1 - cur] + (size_t)nleaf_max * kPB;
+          pivot_merge_kernel<<<next, kTRows, psmem, st>>>(A, n, k0, kb, cbuf[cur], cin, groups, cbuf[1 - cur], cout);
+          c->launches += 1;
+          cur = 1 - cur;
+          groups = next;
+        }
+        pivot_swap_kernel<<<(n + kSwapCols - 1) / kSwapCols, 256, ssmem, st>>>(A, n, k0, kb, cbuf[cur], piv);
+        c->launches += 1;
+        BGW_CUDA(c, cudaGetLastError());
+      }
+      if ((rc = gj_step_run(c, A, n, k0, kb, dinv.as<double2>(), R.as<double2>(), Cp.as<double2>(), st)) != BGW_OK)
+        return rc;
+    }
+    colperm_build_kernel<<<1, 1, 0, st>>>(piv, n, src);
+    colperm_apply_kernel<<<n, 256, sizeof(double2) * n, st>>>(A, n, src);
+    BGW_CUDA(c, cudaGetLastError());
+    c->launches += 2;
+  }
+  return BGW_OK;
+}
+
+}  // namespace bgw

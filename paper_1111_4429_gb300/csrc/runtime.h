@@ -95,7 +95,7 @@ struct Timing {
   std::map<int, std::pair<long long, double>> acc;  // name -> (launches, ms)
 };
 enum TimedName { kTBand = 0, kTPairYX, kTPairZ, kTChiF64, kTChiSplit, kTChiTc, kTChiReduce, kTEpsForm, kTInverse,
-                 kTOzUpdate, kTSweepChain, kTHeadDot, kTHeadWings, kTScreenedW, kTNumNames };
+                 kTOzUpdate, kTSweepChain, kTHeadDot, kTHeadWings, kTScreenedW, kTPivot, kTNumNames };
 const char* timed_name(int n);
 
 // A captured batch (bgw_epsilon_batch) replayed while its key is unchanged.
@@ -217,6 +217,23 @@ int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const doubl
 int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells,
                      const int32_t* const* d_geps, const void* const* chi, void* const* eps, void* const* epsinv,
                      cudaStream_t st, bool tc_update);
+// eps~ = I - sv chi sv of one matrix into A (and eps when non-NULL), sv from
+// the cell's Coulomb model (epsinv.cu).
+int eps_form_run(Ctx* c, const bgw_cell* cell, const int32_t* d_geps, int ng, const void* chi, double* sv,
+                 double2* A, void* eps, cudaStream_t st);
+// One blocked Gauss-Jordan step without pivoting on columns k0..k0+kb
+// (kb <= 32) of the general matrix A; dinv [32][32], R [32][ng], Cp [ng][32].
+int gj_step_run(Ctx* c, double2* A, int ng, int k0, int kb, double2* dinv, double2* R, double2* Cp,
+                cudaStream_t st);
+// General (non-Hermitian) eps~ and its inverse with partial pivoting
+// (epsinv_general.cu), one matrix after the other.
+int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
+                       const void* const* chi, void* const* eps, void* const* epsinv, cudaStream_t st);
+constexpr int kGeneralMaxNg = 14336;   // row of the column unscramble in shared memory
+// Real-axis chi (chi.cu): complex weights of Eq. retarded_advanced_epsilon.
+int chi_real_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const double* d_ev, const double* d_ec,
+                 int nfreq, const double* d_energy, double delta, int advanced, double scale, int accumulate,
+                 void* chi, cudaStream_t st);
 // W = v^1/2 epsinv v^1/2 for nmat matrices (bgw_screened_w).
 int screened_w_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
                    const void* const* epsinv, void* const* W, cudaStream_t st);

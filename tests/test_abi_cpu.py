@@ -61,3 +61,16 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), f
+
+
+def test_frequency_grid_host_matches_oracle():
+    from paper_1111_4429_gb300 import bgw
+    import numpy as np
+    import oracle
+    for args in [(0.1, 0.5, 2.0, 0.1), (0.25, 1.0, 2.0, 0.0), (0.2, 1.0, 10.0, 0.05), (0.01, 3.0, 60.0, 0.01),
+                 (0.5, 0.0, 0.0, 0.0)]:
+        assert np.array_equal(bgw.frequency_grid(*args), oracle.frequency_grid(*args))
+    import pytest
+    for bad in [(0.0, 1.0, 2.0, 0.1), (0.1, 1.0, 0.5, 0.1), (0.1, 1.0, 2.0, -0.1)]:
+        with pytest.raises(bgw.BgwError):
+            bgw.frequency_grid(*bad)
