@@ -394,7 +394,7 @@ int bgw_epsinv_general(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int*
     dgeps[m] = static_cast<const int32_t*>(dg);
     cp[m] = &cells[m];
   }
-  return epsinv_general_run(c, nmat, ng, cp.data(), dgeps.data(), chi, eps, epsinv, st);
+  return epsinv_general_run(c, nmat, ng, cp.data(), dgeps.data(), chi, eps, epsinv, st, c->inverse_mode == 1);
 }
 
 int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, const int32_t* const* geps,
@@ -724,7 +724,8 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
       invs[f] = static_cast<char*>(d_inv) + f * n2;
     }
     if (fa.real)
-      rc = epsinv_general_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st);
+      rc = epsinv_general_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
+                              use_tc_inverse(c, prec));
     else
       rc = epsinv_batch_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
                             use_tc_inverse(c, prec));

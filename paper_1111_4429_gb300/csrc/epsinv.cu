@@ -141,24 +141,31 @@ __global__ void eps_form_kernel(const double2* __restrict__ chi, const double* _
 }
 
 // Inverse of the diagonal block A[k0:k0+kb, k0:k0+kb] -> Dinv[kb][kb] (ld NB).
+// The reciprocal of each pivot is formed once (thread 0) and shared: on this
+// part every FP64 operation of one SM counts.
 __global__ void __launch_bounds__(NB * NB) gj_diag_kernel(const double2* __restrict__ A, int ng, int k0,
                                                           int kb, double2* __restrict__ Dinv,
                                                           int* __restrict__ status) {
   __shared__ double2 D[NB][NB + 1];
+  __shared__ double2 pinv;
   const int i = threadIdx.y, j = threadIdx.x;
   const bool in = i < kb && j < kb;
   D[i][j] = in ? A[(size_t)(k0 + i) * ng + k0 + j] : make_double2(i == j ? 1.0 : 0.0, 0.0);
   for (int s = 0; s < kb; ++s) {
     __syncthreads();
-    const double2 piv = D[s][s];
-    const double m2 = piv.x * piv.x + piv.y * piv.y;
-    double2 p;
-    if (!(m2 > 0.0) || !isfinite(m2)) {
-      if (i == 0 && j == 0) atomicExch(status, (int)kDevZeroPivot);
-      p = make_double2(0.0, 0.0);
-    } else {
-      p = make_double2(piv.x / m2, -piv.y / m2);  // 1/piv
+    if (i == 0 && j == 0) {
+      const double2 piv = D[s][s];
+      const double m2 = piv.x * piv.x + piv.y * piv.y;
+      if (!(m2 > 0.0) || !isfinite(m2)) {
+        atomicExch(status, (int)kDevZeroPivot);
+        pinv = make_double2(0.0, 0.0);
+      } else {
+        const double r = 1.0 / m2;
+        pinv = make_double2(piv.x * r, -piv.y * r);  // 1/piv
+      }
     }
+    __syncthreads();
+    const double2 p = pinv;
     const double2 f = D[i][s];
     const double2 rs = D[s][j];
     __syncthreads();
@@ -199,6 +206,46 @@ __global__ void __launch_bounds__(256) gj_panels_kernel(const double2* __restric
   __syncthreads();
   for (int e = tid; e < NB * 64; e += 256) {
     const int r = e / 64, jj = e % 64, j = j0 + jj;
+    if (r >= kb || j >= ng) continue;
+    double2 v;
+    if (j >= k0 && j < k0 + kb) {
+      v = Ds[r][j - k0];
+    } else {
+      v = make_double2(0.0, 0.0);
+      for (int s = 0; s < kb; ++s) {
+        const double2 t = cmul(Ds[r][s], As[s][jj]);
+        v.x += t.x;
+        v.y += t.y;
+      }
+    }
+    R[(size_t)r * ng + j] = v;
+  }
+}
+
+// R = D^-1 A_K,: (ld ng) over 16 columns per CTA and C = A_:,K (ld NB):
+// grid (ceil(ng/16), 1 + ceil(ng/256)); many more CTAs than gj_panels_kernel,
+// whose 64-column CTAs leave most SMs idle at this size of work.
+__global__ void __launch_bounds__(256) gj_panels16_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
+                                                          const double2* __restrict__ Dinv,
+                                                          double2* __restrict__ R, double2* __restrict__ C) {
+  const int tid = threadIdx.x;
+  if (blockIdx.y > 0) {
+    const int i = (blockIdx.y - 1) * 256 + tid;
+    if (blockIdx.x != 0 || i >= ng) return;
+    for (int s = 0; s < kb; ++s) C[(size_t)i * NB + s] = A[(size_t)i * ng + k0 + s];
+    return;
+  }
+  __shared__ double2 Ds[NB][NB + 1];
+  __shared__ double2 As[NB][16];
+  const int j0 = blockIdx.x * 16;
+  for (int e = tid; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Dinv[e];
+  for (int e = tid; e < NB * 16; e += 256) {
+    const int s = e / 16, jj = e % 16;
+    As[s][jj] = (s < kb && j0 + jj < ng) ? A[(size_t)(k0 + s) * ng + j0 + jj] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * 16; e += 256) {
+    const int r = e / 16, jj = e % 16, j = j0 + jj;
     if (r >= kb || j >= ng) continue;
     double2 v;
     if (j >= k0 && j < k0 + kb) {
@@ -614,15 +661,18 @@ int eps_form_run(Ctx* c, const bgw_cell* cell, const int32_t* d_geps, int ng, co
 }
 
 int gj_step_run(Ctx* c, double2* A, int ng, int k0, int kb, double2* dinv, double2* R, double2* Cp,
-                cudaStream_t st) {
-  const int nt = (ng + TU - 1) / TU;
-  const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
-  BGW_CUDA(c, cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
+                cudaStream_t st, bool update) {
   gj_diag_kernel<<<1, dim3(NB, NB), 0, st>>>(A, ng, k0, kb, dinv, c->d_status);
-  gj_panels_kernel<<<dim3((ng + 63) / 64, 1 + (ng + 255) / 256), 256, 0, st>>>(A, ng, k0, kb, dinv, R, Cp);
-  gj_update_kernel<<<dim3(nt, nt), 256, upd_smem, st>>>(A, ng, k0, kb, R, Cp);
+  gj_panels16_kernel<<<dim3((ng + 15) / 16, 1 + (ng + 255) / 256), 256, 0, st>>>(A, ng, k0, kb, dinv, R, Cp);
+  c->launches += 2;
+  if (update) {
+    const int nt = (ng + TU - 1) / TU;
+    const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
+    BGW_CUDA(c, cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
+    gj_update_kernel<<<dim3(nt, nt), 256, upd_smem, st>>>(A, ng, k0, kb, R, Cp);
+    c->launches += 1;
+  }
   BGW_CUDA(c, cudaGetLastError());
-  c->launches += 3;
   return BGW_OK;
 }
 

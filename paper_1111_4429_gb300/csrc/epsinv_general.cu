@@ -10,7 +10,8 @@
 //      slices of the column panel and keep 32 candidates each; merge rounds
 //      run the same LU on up to 8 candidate sets at a time until 32 rows
 //      remain (the selection of a partial-pivoting LU of the panel when one
-//      slice holds every row, a tournament among slices otherwise);
+//      slice holds every row, a tournament among slices otherwise).  The
+//      selection LUs run in FP32: they only choose rows;
 //   2. the chosen rows are swapped into the block's rows (whole rows of the
 //      working matrix: row operations on the augmented system), the
 //      interchanges recorded LAPACK-style (ipiv[j] >= j);
@@ -20,6 +21,7 @@
 // columns; undoing the interchanges on the columns in reverse order gives
 // eps~^-1.
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "runtime.h"
@@ -38,19 +40,23 @@ __device__ __forceinline__ double cabs1(double2 z) { return fabs(z.x) + fabs(z.y
 // owns row t.  Picks, column by column, the active row of largest |Re|+|Im|
 // (ties: smallest global row), eliminates that column from the other active
 // rows.  Writes the global rows in selection order to sel and returns their
-// number (min(nr, kb)).
-__device__ int select_rows(double2 (*P)[kPB + 1], const int* gid, int nr, int kb, int* sel) {
-  __shared__ double wv[kTRows / 32];
+// number (min(nr, kb)).  The selection runs in FP32: it only orders the rows
+// (the elimination itself is the FP64 Gauss-Jordan step that follows), and
+// FP32 runs at 64 times the FP64 rate of one SM.
+__device__ __forceinline__ float cabs1f(float2 z) { return fabsf(z.x) + fabsf(z.y); }
+
+__device__ int select_rows(float2 (*P)[kPB + 1], const int* gid, int nr, int kb, int* sel) {
+  __shared__ float wv[kTRows / 32];
   __shared__ int wg[kTRows / 32], wl[kTRows / 32];
   __shared__ int win;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   bool active = t < nr;
   const int cnt = min(nr, kb);
   for (int j = 0; j < cnt; ++j) {
-    double v = active ? cabs1(P[t][j]) : -1.0;
+    float v = active ? cabs1f(P[t][j]) : -1.f;
     int g = active ? gid[t] : 0x7fffffff, l = t;
     for (int o = 16; o > 0; o >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+      const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
       const int g2 = __shfl_xor_sync(0xffffffffu, g, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
       if (v2 > v || (v2 == v && g2 < g)) {
         v = v2;
@@ -65,7 +71,7 @@ __device__ int select_rows(double2 (*P)[kPB + 1], const int* gid, int nr, int kb
     }
     __syncthreads();
     if (t == 0) {
-      double bv = wv[0];
+      float bv = wv[0];
       int bg = wg[0], bl = wl[0];
       for (int w = 1; w < kTRows / 32; ++w)
         if (wv[w] > bv || (wv[w] == bv && wg[w] < bg)) {
@@ -79,15 +85,14 @@ __device__ int select_rows(double2 (*P)[kPB + 1], const int* gid, int nr, int kb
     __syncthreads();
     const int w = win;
     if (t == w) active = false;
-    const double2 pv = P[w][j];
-    const double m2 = pv.x * pv.x + pv.y * pv.y;
-    if (active && m2 > 0.0) {
-      const double2 a = P[t][j];
-      // l = a / pv
-      const double2 l = make_double2((a.x * pv.x + a.y * pv.y) / m2, (a.y * pv.x - a.x * pv.y) / m2);
+    const float2 pv = P[w][j];
+    const float m2 = pv.x * pv.x + pv.y * pv.y;
+    if (active && m2 > 0.f) {
+      const float2 a = P[t][j];
+      const float2 l = make_float2((a.x * pv.x + a.y * pv.y) / m2, (a.y * pv.x - a.x * pv.y) / m2);
       for (int c = j + 1; c < kb; ++c) {
-        const double2 u = P[w][c];
-        P[t][c] = make_double2(P[t][c].x - (l.x * u.x - l.y * u.y), P[t][c].y - (l.x * u.y + l.y * u.x));
+        const float2 u = P[w][c];
+        P[t][c] = make_float2(P[t][c].x - (l.x * u.x - l.y * u.y), P[t][c].y - (l.x * u.y + l.y * u.x));
       }
     }
     __syncthreads();
@@ -95,11 +100,15 @@ __device__ int select_rows(double2 (*P)[kPB + 1], const int* gid, int nr, int kb
   return cnt;
 }
 
+// FP32 copy of a panel entry.  The values are eps~ entries (finite, far
+// inside the FP32 range); a zero pivot column stays zero.
+__device__ __forceinline__ float2 to_f2(double2 z) { return make_float2((float)z.x, (float)z.y); }
+
 // Leaf round: CTA b takes rows k0 + 256 b ... of the panel.
 __global__ void __launch_bounds__(kTRows) pivot_leaf_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
                                                             int* __restrict__ out, int* __restrict__ cnt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2 (*P)[kPB + 1] = reinterpret_cast<double2 (*)[kPB + 1]>(smem_raw);
+  float2 (*P)[kPB + 1] = reinterpret_cast<float2 (*)[kPB + 1]>(smem_raw);
   __shared__ int gid[kTRows];
   __shared__ int sel[kPB];
   const int r0 = k0 + blockIdx.x * kTRows;
@@ -107,7 +116,7 @@ __global__ void __launch_bounds__(kTRows) pivot_leaf_kernel(const double2* __res
   const int t = threadIdx.x;
   gid[t] = r0 + t;
   if (t < nr)
-    for (int c = 0; c < kb; ++c) P[t][c] = A[(size_t)(r0 + t) * ng + k0 + c];
+    for (int c = 0; c < kb; ++c) P[t][c] = to_f2(A[(size_t)(r0 + t) * ng + k0 + c]);
   __syncthreads();
   const int n = select_rows(P, gid, nr, kb, sel);
   __syncthreads();
@@ -121,7 +130,7 @@ __global__ void __launch_bounds__(kTRows) pivot_merge_kernel(const double2* __re
                                                              int ngroups, int* __restrict__ out,
                                                              int* __restrict__ cout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2 (*P)[kPB + 1] = reinterpret_cast<double2 (*)[kPB + 1]>(smem_raw);
+  float2 (*P)[kPB + 1] = reinterpret_cast<float2 (*)[kPB + 1]>(smem_raw);
   __shared__ int gid[kTRows];
   __shared__ int sel[kPB];
   __shared__ int nr_s;
@@ -135,7 +144,7 @@ __global__ void __launch_bounds__(kTRows) pivot_merge_kernel(const double2* __re
   __syncthreads();
   const int nr = nr_s;
   if (t < nr)
-    for (int c = 0; c < kb; ++c) P[t][c] = A[(size_t)gid[t] * ng + k0 + c];
+    for (int c = 0; c < kb; ++c) P[t][c] = to_f2(A[(size_t)gid[t] * ng + k0 + c]);
   __syncthreads();
   const int n = select_rows(P, gid, nr, kb, sel);
   __syncthreads();
@@ -211,7 +220,8 @@ __global__ void __launch_bounds__(256) colperm_apply_kernel(double2* __restrict_
 }  // namespace
 
 int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
-                       const void* const* chi, void* const* eps, void* const* epsinv, cudaStream_t st) {
+                       const void* const* chi, void* const* eps, void* const* epsinv, cudaStream_t st,
+                       bool tc_update) {
   int ngmax = 0;
   for (int m = 0; m < nmat; ++m) ngmax = std::max(ngmax, ng[m]);
   const int nleaf_max = (ngmax + kTRows - 1) / kTRows;
@@ -225,7 +235,7 @@ int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
       (rc = c->pool.alloc((size_t)2 * nleaf_max * (kPB + 1) * sizeof(int), &cand.ptr)) != BGW_OK ||
       (rc = c->pool.alloc((size_t)2 * ngmax * sizeof(int), &ipiv.ptr)) != BGW_OK)
     return fail(c, rc, "general inverse: scratch allocation failed");
-  const size_t psmem = sizeof(double2) * kTRows * (kPB + 1);
+  const size_t psmem = sizeof(float2) * kTRows * (kPB + 1);
   const size_t ssmem = sizeof(double2) * 2 * kPB * kSwapCols;
   BGW_CUDA(c, cudaFuncSetAttribute(pivot_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
   BGW_CUDA(c, cudaFuncSetAttribute(pivot_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
@@ -242,6 +252,14 @@ int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
         BGW_OK)
       return rc;
     TimedScope ts(c, kTInverse, st);
+    std::unique_ptr<OzPlan, void (*)(OzPlan*)> oz(nullptr, oz_plan_delete);
+    if (tc_update) {
+      oz.reset(oz_plan_new());
+      double2* Am = A;
+      const double2* Rm = R.as<double2>();
+      const double2* Cm = Cp.as<double2>();
+      if ((rc = oz_prepare(c, 1, &n, &Am, &Rm, &Cm, nullptr, oz.get(), true)) != BGW_OK) return rc;
+    }
     for (int k0 = 0; k0 < n; k0 += kPB) {
       const int kb = std::min(kPB, n - k0);
       int groups = (n - k0 + kTRows - 1) / kTRows;
@@ -265,8 +283,18 @@ int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
         c->launches += 1;
         BGW_CUDA(c, cudaGetLastError());
       }
-      if ((rc = gj_step_run(c, A, n, k0, kb, dinv.as<double2>(), R.as<double2>(), Cp.as<double2>(), st)) != BGW_OK)
-        return rc;
+      {
+        TimedScope tg(c, kTSweepChain, st);
+        if ((rc = gj_step_run(c, A, n, k0, kb, dinv.as<double2>(), R.as<double2>(), Cp.as<double2>(), st,
+                              !tc_update)) != BGW_OK)
+          return rc;
+      }
+      if (tc_update) {
+        TimedScope tu(c, kTOzUpdate, st);
+        if ((rc = oz_slice(c, oz.get(), k0, n, 0, st)) != BGW_OK || (rc = oz_update(c, oz.get(), k0, n, 0, 0, st)) != BGW_OK)
+          return rc;
+        c->launches += 3;
+      }
     }
     colperm_build_kernel<<<1, 1, 0, st>>>(piv, n, src);
     colperm_apply_kernel<<<n, 256, sizeof(double2) * n, st>>>(A, n, src);

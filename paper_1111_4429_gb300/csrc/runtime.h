@@ -223,12 +223,16 @@ int eps_form_run(Ctx* c, const bgw_cell* cell, const int32_t* d_geps, int ng, co
                  double2* A, void* eps, cudaStream_t st);
 // One blocked Gauss-Jordan step without pivoting on columns k0..k0+kb
 // (kb <= 32) of the general matrix A; dinv [32][32], R [32][ng], Cp [ng][32].
+// update = false stops after the panels (the caller updates A itself).
 int gj_step_run(Ctx* c, double2* A, int ng, int k0, int kb, double2* dinv, double2* R, double2* Cp,
-                cudaStream_t st);
+                cudaStream_t st, bool update = true);
 // General (non-Hermitian) eps~ and its inverse with partial pivoting
 // (epsinv_general.cu), one matrix after the other.
+// tc_update: the trailing updates on the tensor cores (Ozaki split, FP64-level
+// accuracy) instead of FP64 FMA.
 int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
-                       const void* const* chi, void* const* eps, void* const* epsinv, cudaStream_t st);
+                       const void* const* chi, void* const* eps, void* const* epsinv, cudaStream_t st,
+                       bool tc_update = false);
 constexpr int kGeneralMaxNg = 14336;   // row of the column unscramble in shared memory
 // Real-axis chi (chi.cu): complex weights of Eq. retarded_advanced_epsilon.
 int chi_real_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const double* d_ev, const double* d_ec,
@@ -246,8 +250,11 @@ int coulomb_check(const bgw_cell* cell, int ng, const int32_t* geps, int* what, 
 struct OzPlan;
 OzPlan* oz_plan_new();
 void oz_plan_delete(OzPlan* p);
+// general = false: the Hermitian sweep's update (C, P: [ng][32] panels, D
+// the next diagonal inverse).  general = true: the pivoted Gauss-Jordan
+// update A -= P R with P the column panel [ng][32] and C = R [32][ng].
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               double2* const* D, OzPlan* plan);
+               double2* const* D, OzPlan* plan, bool general = false);
 int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);
 int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaStream_t st);
 

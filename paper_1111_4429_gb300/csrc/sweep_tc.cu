@@ -172,6 +172,49 @@ __global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBa
             (blockIdx.z == 0 ? sig : tau) + (size_t)buf * rows_total + row);
 }
 
+// Slices for the general (Gauss-Jordan) update A -= Cp R of the pivoted
+// inverse: z = 0 slices the column panel Cp [ng][NB] (rows of the block K
+// zero: they are overwritten with R afterwards), z = 1 slices R^H, read
+// transposed from R [NB][ng] (every row live: the block's columns receive
+// -Cp D^-1).  M.P holds Cp, M.C holds R.
+__global__ void __launch_bounds__(256) slice_general_kernel(const __grid_constant__ OzBatch b, int k0,
+                                                            int rows_total, int buf, __half* __restrict__ U,
+                                                            __half* __restrict__ V, int* __restrict__ sig,
+                                                            int* __restrict__ tau) {
+  const OzMat& M = b.m[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  const int ngpad = (M.ng + BM - 1) / BM * BM;
+  if (i >= ngpad) return;
+  const int kb = min(NB, M.ng - k0);
+  double re = 0.0, im = 0.0;
+  if (blockIdx.z == 0) {
+    if (i < M.ng && (i < k0 || i >= k0 + kb) && lane < kb) {
+      const double2 v = M.P[(size_t)i * NB + lane];
+      re = v.x;
+      im = v.y;
+    }
+  } else if (i < M.ng && lane < kb) {
+    const double2 v = M.C[(size_t)lane * M.ng + i];
+    re = v.x;
+    im = -v.y;
+  }
+  const size_t row = (size_t)M.row_off + i;
+  __half* out = (blockIdx.z == 0 ? U : V) + (size_t)buf * S * rows_total * KR + row * KR;
+  slice_row(re, im, lane, out, (size_t)rows_total * KR,
+            (blockIdx.z == 0 ? sig : tau) + (size_t)buf * rows_total + row);
+}
+
+// Rows of the block K after the general update: A[k0 + r][j] = R[r][j].
+__global__ void rows_from_r_kernel(const __grid_constant__ OzBatch b, int k0) {
+  const OzMat& M = b.m[blockIdx.y];
+  const int kb = min(NB, M.ng - k0);
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= M.ng || e >= (long long)kb * M.ng) return;
+  const int r = (int)(e / M.ng), j = (int)(e - (long long)r * M.ng);
+  M.A[(size_t)(k0 + r) * M.ng + j] = M.C[(size_t)r * M.ng + j];
+}
+
 // (double)f for a finite float, built from its bits with integer operations
 // (the FP64 pipe, which a conversion would occupy, is the scarce one here).
 __device__ __forceinline__ double f2d(float f) {
@@ -195,6 +238,9 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // (rows or columns k0 + NB .. k0 + 2 NB), which the next sweep step reads
 // first; 2: every other tile.  Modes 1 and 2 split one step's update so the
 // next step's diagonal block, panel and slices can proceed after mode 1.
+// mode 3: the general Gauss-Jordan update of the pivoted inverse, every
+// tile of the matrix: A_ij = (j in K ? 0 : A_ij) - (Cp R)_ij for rows
+// outside K (slices from slice_general_kernel).
 __global__ void __launch_bounds__(kThreads, 1)
     update_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
                   const __grid_constant__ OzBatch b, int k0, int rows_total, int buf, int mode,
@@ -220,6 +266,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       J = Jn;
       if (I >= nI) return;
     }
+  } else if (mode == 3) {
+    I = blockIdx.x / nJ;
+    J = blockIdx.x - I * nJ;
+    if (I >= nI) return;
   } else {
     // tile decode: row tile I holds column tiles J = 0 .. min(4I+3, nJ-1)
     int t = blockIdx.x;
@@ -235,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int i0 = I * BM, j0 = J * BN;
   const int slice_base = buf * S * rows_total;  // first slice row of this step's buffer
   if (i0 >= k0 && min(i0 + BM, ng) <= k0 + kb) return;
-  if (j0 >= k0 && min(j0 + BN, ng) <= k0 + kb) return;
+  if (mode != 3 && j0 >= k0 && min(j0 + BN, ng) <= k0 + kb) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -350,12 +400,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int j = j0 + c0 + q;
-          if (j > i || j >= ng || (j >= k0 && j < k0 + kb)) continue;
+          const bool jblock = j >= k0 && j < k0 + kb;
+          if (j >= ng || (mode != 3 && (j > i || jblock))) continue;
           // scale by sigma_i tau_j 2^-16 = 2^(ei + ej - 16): exact power of two,
           // applied to the FP32 pair when it stays a normal number, else in FP64
           const int ex = ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA;
           double2* dst = M.A + (size_t)i * ng + j;
-          const double2 v = *dst;
+          const double2 v = jblock ? make_double2(0.0, 0.0) : *dst;   // mode 3 only
           double2 o;
           if (ex > -100 && ex < 100) {
             // four FP64 adds per element; scaling and conversion off the FP64 pipe
@@ -410,6 +461,7 @@ EncodeTiledFn g_encode_oz = nullptr;
 
 // State of one batched sweep that uses the tensor-core update.
 struct OzPlan {
+  bool general = false;   // Gauss-Jordan update (mode 3) of the pivoted inverse
   int nmat = 0;
   int rows_total = 0;
   int max_tiles = 0;
@@ -419,7 +471,7 @@ struct OzPlan {
 };
 
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               double2* const* D, OzPlan* plan) {
+               double2* const* D, OzPlan* plan, bool general) {
   using namespace oz;
   if (nmat > kBatch) return fail(c, BGW_EUNSUPPORTED, "tensor-core inverse: at most %d matrices per batch", kBatch);
   if (!g_encode_oz) {
@@ -431,19 +483,23 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
     g_encode_oz = reinterpret_cast<EncodeTiledFn>(fn);
   }
   plan->nmat = nmat;
+  plan->general = general;
   plan->batch.n = nmat;
   int rows = 0, tiles = 0;
   for (int m = 0; m < nmat; ++m) {
     plan->batch.m[m].A = A[m];
     plan->batch.m[m].C = C[m];
     plan->batch.m[m].P = P[m];
-    plan->batch.m[m].Dinv = D[m];
+    plan->batch.m[m].Dinv = D ? D[m] : nullptr;
     plan->batch.m[m].ng = ng[m];
     plan->batch.m[m].row_off = rows;
     rows += (ng[m] + BM - 1) / BM * BM;
     const int nI = (ng[m] + BM - 1) / BM, nJ = (ng[m] + BN - 1) / BN;
     int t = 0;
-    for (int I = 0; I < nI; ++I) t += std::min(4 * I + 4, nJ);
+    if (general)
+      t = nI * nJ;
+    else
+      for (int I = 0; I < nI; ++I) t += std::min(4 * I + 4, nJ);
     tiles = std::max(tiles, t);
   }
   plan->rows_total = rows;
@@ -479,15 +535,21 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
 int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) {
   using namespace oz;
   const int rpad = (ngmax + BM - 1) / BM * BM;
-  slice_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
-                                                              plan->U.as<__half>(), plan->V.as<__half>(),
-                                                              plan->sig.as<int>(), plan->tau.as<int>());
+  if (plan->general)
+    slice_general_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
+                                                                        plan->U.as<__half>(), plan->V.as<__half>(),
+                                                                        plan->sig.as<int>(), plan->tau.as<int>());
+  else
+    slice_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
+                                                                plan->U.as<__half>(), plan->V.as<__half>(),
+                                                                plan->sig.as<int>(), plan->tau.as<int>());
   BGW_CUDA(c, cudaGetLastError());
   return BGW_OK;
 }
 
 // The trailing update of one sweep step from slice buffer buf: mode 0 all
-// tiles, 1 the tiles touching the next block, 2 the others.
+// tiles, 1 the tiles touching the next block, 2 the others; a general plan
+// runs mode 3 (every tile) and then writes R into the block's rows.
 int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaStream_t st) {
   using namespace oz;
   int grid = plan->max_tiles;
@@ -497,10 +559,15 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
     const int nI = (ngmax + BM - 1) / BM, nJ = (ngmax + BN - 1) / BN, In = k1 / BM;
     grid = std::min(4 * In + 4, nJ) + std::max(0, nI - In - 1);
   }
+  if (plan->general) mode = 3;
   const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
   update_kernel<<<dim3(grid, plan->nmat), kThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,
                                                                 plan->rows_total, buf, mode, plan->sig.as<int>(),
                                                                 plan->tau.as<int>(), c->d_status);
+  if (plan->general) {
+    const long long ne = (long long)NB * ngmax;
+    rows_from_r_kernel<<<dim3((unsigned)((ne + 255) / 256), plan->nmat), 256, 0, st>>>(plan->batch, k0);
+  }
   BGW_CUDA(c, cudaGetLastError());
   return BGW_OK;
 }
