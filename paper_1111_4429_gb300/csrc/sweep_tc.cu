@@ -34,7 +34,7 @@ constexpr int KR = 64;           // real inner length (32 complex)
 constexpr int BM = 128;          // tile rows (i)
 constexpr int BN = 32;           // tile cols (j)
 constexpr int NB = 32;           // sweep block width
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;          // 8 warps: two per tensor-memory lane quadrant in the epilogue
 constexpr int kUTile = BM * KR * 2;    // 16 KiB
 constexpr int kVTile = BN * KR * 2;    // 4 KiB
 constexpr unsigned long long kWaitNs = 1000000000ull;
@@ -93,6 +93,11 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(id), "r"(acc)
       : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
@@ -362,62 +367,66 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncwarp();
   if (have && ok) {
-    const int r = warp * 32 + lane;
+    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows of the tile)
+    // and columns 16 (w / 4) .. + 15, in chunks of 8: the A values of the
+    // chunk are loaded first, then all 14 level loads (7 levels, Re and Im)
+    // are issued before a single wait.
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = quad * 32 + lane;
     const int i = i0 + r;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     const bool row_ok = i < ng && !(i >= k0 && i < k0 + kb);
     const int ei = row_ok ? sig[buf * rows_total + M.row_off + i] : 0;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float hr[16], lr[16], hm[16], lm[16];
-#pragma unroll 1
-      for (int L = 0; L < S; ++L) {
-        uint32_t x[16], y[16];
-        tmem_ld16(tmem + lane_off + L * 2 * BN + c0, x);
-        tmem_ld16(tmem + lane_off + L * 2 * BN + BN + c0, y);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const float w = ldexpf(1.f, -BETA * L);
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 8) {
+      double2 av[8];
+      int ex[8];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float vr = __fmul_rn(__uint_as_float(x[q]), w), vi = __fmul_rn(__uint_as_float(y[q]), w);
-          if (L == 0) {
-            hr[q] = vr;
-            lr[q] = 0.f;
-            hm[q] = vi;
-            lm[q] = 0.f;
-          } else {
-            float s, e;
-            two_sum(hr[q], vr, s, e);
-            hr[q] = s;
-            lr[q] = __fadd_rn(lr[q], e);
-            two_sum(hm[q], vi, s, e);
-            hm[q] = s;
-            lm[q] = __fadd_rn(lm[q], e);
-          }
-        }
+      for (int q = 0; q < 8; ++q) {
+        const int j = j0 + c0 + q;
+        const bool jblock = j >= k0 && j < k0 + kb;
+        const bool live = row_ok && j < ng && (mode == 3 ? true : (j <= i && !jblock));
+        av[q] = (live && !jblock) ? M.A[(size_t)i * ng + j] : make_double2(0.0, 0.0);
+        ex[q] = live ? ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA : 1 << 20;
       }
-      if (row_ok) {
+      uint32_t x[S][8], y[S][8];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int j = j0 + c0 + q;
-          const bool jblock = j >= k0 && j < k0 + kb;
-          if (j >= ng || (mode != 3 && (j > i || jblock))) continue;
-          // scale by sigma_i tau_j 2^-16 = 2^(ei + ej - 16): exact power of two,
-          // applied to the FP32 pair when it stays a normal number, else in FP64
-          const int ex = ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA;
-          double2* dst = M.A + (size_t)i * ng + j;
-          const double2 v = jblock ? make_double2(0.0, 0.0) : *dst;   // mode 3 only
-          double2 o;
-          if (ex > -100 && ex < 100) {
-            // four FP64 adds per element; scaling and conversion off the FP64 pipe
-            o.x = (v.x - f2d(ldexpf(hr[q], ex))) - f2d(ldexpf(lr[q], ex));
-            o.y = (v.y - f2d(ldexpf(hm[q], ex))) - f2d(ldexpf(lm[q], ex));
-          } else {
-            o.x = v.x - ldexp((double)hr[q] + (double)lr[q], ex);
-            o.y = v.y - ldexp((double)hm[q] + (double)lm[q], ex);
-          }
-          *dst = o;
+      for (int L = 0; L < S; ++L) {
+        tmem_ld8(tmem + lane_off + L * 2 * BN + c0, x[L]);
+        tmem_ld8(tmem + lane_off + L * 2 * BN + BN + c0, y[L]);
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float hr = __uint_as_float(x[0][q]), lr = 0.f, hm = __uint_as_float(y[0][q]), lm = 0.f;
+#pragma unroll
+        for (int L = 1; L < S; ++L) {
+          const float w = ldexpf(1.f, -BETA * L);
+          const float vr = __fmul_rn(__uint_as_float(x[L][q]), w), vi = __fmul_rn(__uint_as_float(y[L][q]), w);
+          float sm, e;
+          two_sum(hr, vr, sm, e);
+          hr = sm;
+          lr = __fadd_rn(lr, e);
+          two_sum(hm, vi, sm, e);
+          hm = sm;
+          lm = __fadd_rn(lm, e);
         }
+        if (ex[q] == (1 << 20)) continue;
+        const int j = j0 + c0 + q;
+        // scale by sigma_i tau_j 2^-16 = 2^ex: exact power of two, applied to
+        // the FP32 pair when it stays a normal number, else in FP64; four
+        // FP64 adds per element, scaling and conversion off the FP64 pipe
+        const double2 v = av[q];
+        double2 o;
+        const int e2 = ex[q];
+        if (e2 > -100 && e2 < 100) {
+          o.x = (v.x - f2d(ldexpf(hr, e2))) - f2d(ldexpf(lr, e2));
+          o.y = (v.y - f2d(ldexpf(hm, e2))) - f2d(ldexpf(lm, e2));
+        } else {
+          o.x = v.x - ldexp((double)hr + (double)lr, e2);
+          o.y = v.y - ldexp((double)hm + (double)lm, e2);
+        }
+        M.A[(size_t)i * ng + j] = o;
       }
     }
   }
