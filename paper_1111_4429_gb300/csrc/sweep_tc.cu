@@ -34,7 +34,8 @@ constexpr int KR = 64;           // real inner length (32 complex)
 constexpr int BM = 128;          // tile rows (i)
 constexpr int BN = 32;           // tile cols (j)
 constexpr int NB = 32;           // sweep block width
-constexpr int kThreads = 256;          // 8 warps: two per tensor-memory lane quadrant in the epilogue
+constexpr int kThreads = 512;          // 16 warps: four per tensor-memory lane quadrant in the epilogue
+constexpr int kChunk = 4;              // epilogue columns per tensor-memory load round
 constexpr int kUTile = BM * KR * 2;    // 16 KiB
 constexpr int kVTile = BN * KR * 2;    // 4 KiB
 constexpr unsigned long long kWaitNs = 1000000000ull;
@@ -93,6 +94,11 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(id), "r"(acc)
       : "memory");
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -368,36 +374,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncwarp();
   if (have && ok) {
     // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows of the tile)
-    // and columns 16 (w / 4) .. + 15, in chunks of 8: the A values of the
-    // chunk are loaded first, then all 14 level loads (7 levels, Re and Im)
-    // are issued before a single wait.
-    const int quad = warp & 3, half = warp >> 2;
+    // and the columns BN/4 (w / 4) .. + BN/4 - 1, in chunks of kChunk: the
+    // A values of a chunk are loaded first, then all 14 level loads (7
+    // levels, Re and Im) are issued before a single wait.
+    const int quad = warp & 3, part = warp >> 2;
+    constexpr int kCols = BN / (kThreads / 128);
     const int r = quad * 32 + lane;
     const int i = i0 + r;
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     const bool row_ok = i < ng && !(i >= k0 && i < k0 + kb);
     const int ei = row_ok ? sig[buf * rows_total + M.row_off + i] : 0;
 #pragma unroll 1
-    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 8) {
-      double2 av[8];
-      int ex[8];
+    for (int c0 = part * kCols; c0 < (part + 1) * kCols; c0 += kChunk) {
+      double2 av[kChunk];
+      int ex[kChunk];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < kChunk; ++q) {
         const int j = j0 + c0 + q;
         const bool jblock = j >= k0 && j < k0 + kb;
         const bool live = row_ok && j < ng && (mode == 3 ? true : (j <= i && !jblock));
         av[q] = (live && !jblock) ? M.A[(size_t)i * ng + j] : make_double2(0.0, 0.0);
         ex[q] = live ? ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA : 1 << 20;
       }
-      uint32_t x[S][8], y[S][8];
+      uint32_t x[S][kChunk], y[S][kChunk];
 #pragma unroll
       for (int L = 0; L < S; ++L) {
-        tmem_ld8(tmem + lane_off + L * 2 * BN + c0, x[L]);
-        tmem_ld8(tmem + lane_off + L * 2 * BN + BN + c0, y[L]);
+        tmem_ld4(tmem + lane_off + L * 2 * BN + c0, x[L]);
+        tmem_ld4(tmem + lane_off + L * 2 * BN + BN + c0, y[L]);
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < kChunk; ++q) {
         float hr = __uint_as_float(x[0][q]), lr = 0.f, hm = __uint_as_float(y[0][q]), lm = 0.f;
 #pragma unroll
         for (int L = 1; L < S; ++L) {
