@@ -222,46 +222,6 @@ __global__ void __launch_bounds__(256) gj_panels_kernel(const double2* __restric
   }
 }
 
-// R = D^-1 A_K,: (ld ng) over 16 columns per CTA and C = A_:,K (ld NB):
-// grid (ceil(ng/16), 1 + ceil(ng/256)); many more CTAs than gj_panels_kernel,
-// whose 64-column CTAs leave most SMs idle at this size of work.
-__global__ void __launch_bounds__(256) gj_panels16_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
-                                                          const double2* __restrict__ Dinv,
-                                                          double2* __restrict__ R, double2* __restrict__ C) {
-  const int tid = threadIdx.x;
-  if (blockIdx.y > 0) {
-    const int i = (blockIdx.y - 1) * 256 + tid;
-    if (blockIdx.x != 0 || i >= ng) return;
-    for (int s = 0; s < kb; ++s) C[(size_t)i * NB + s] = A[(size_t)i * ng + k0 + s];
-    return;
-  }
-  __shared__ double2 Ds[NB][NB + 1];
-  __shared__ double2 As[NB][16];
-  const int j0 = blockIdx.x * 16;
-  for (int e = tid; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Dinv[e];
-  for (int e = tid; e < NB * 16; e += 256) {
-    const int s = e / 16, jj = e % 16;
-    As[s][jj] = (s < kb && j0 + jj < ng) ? A[(size_t)(k0 + s) * ng + j0 + jj] : make_double2(0.0, 0.0);
-  }
-  __syncthreads();
-  for (int e = tid; e < NB * 16; e += 256) {
-    const int r = e / 16, jj = e % 16, j = j0 + jj;
-    if (r >= kb || j >= ng) continue;
-    double2 v;
-    if (j >= k0 && j < k0 + kb) {
-      v = Ds[r][j - k0];
-    } else {
-      v = make_double2(0.0, 0.0);
-      for (int s = 0; s < kb; ++s) {
-        const double2 t = cmul(Ds[r][s], As[s][jj]);
-        v.x += t.x;
-        v.y += t.y;
-      }
-    }
-    R[(size_t)r * ng + j] = v;
-  }
-}
-
 // Rank-kb update of the whole matrix.  grid (ceil(ng/64), ceil(ng/64)).
 __global__ void __launch_bounds__(256) gj_update_kernel(double2* __restrict__ A, int ng, int k0, int kb,
                                                         const double2* __restrict__ R,
@@ -660,19 +620,14 @@ int eps_form_run(Ctx* c, const bgw_cell* cell, const int32_t* d_geps, int ng, co
   return BGW_OK;
 }
 
-int gj_step_run(Ctx* c, double2* A, int ng, int k0, int kb, double2* dinv, double2* R, double2* Cp,
-                cudaStream_t st, bool update) {
-  gj_diag_kernel<<<1, dim3(NB, NB), 0, st>>>(A, ng, k0, kb, dinv, c->d_status);
-  gj_panels16_kernel<<<dim3((ng + 15) / 16, 1 + (ng + 255) / 256), 256, 0, st>>>(A, ng, k0, kb, dinv, R, Cp);
-  c->launches += 2;
-  if (update) {
-    const int nt = (ng + TU - 1) / TU;
-    const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
-    BGW_CUDA(c, cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
-    gj_update_kernel<<<dim3(nt, nt), 256, upd_smem, st>>>(A, ng, k0, kb, R, Cp);
-    c->launches += 1;
-  }
+int gj_update_run(Ctx* c, double2* A, int ng, int k0, int kb, const double2* R, const double2* Cp,
+                  cudaStream_t st) {
+  const int nt = (ng + TU - 1) / TU;
+  const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
+  BGW_CUDA(c, cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
+  gj_update_kernel<<<dim3(nt, nt), 256, upd_smem, st>>>(A, ng, k0, kb, R, Cp);
   BGW_CUDA(c, cudaGetLastError());
+  c->launches += 1;
   return BGW_OK;
 }
 

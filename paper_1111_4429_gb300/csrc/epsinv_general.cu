@@ -104,9 +104,118 @@ __device__ int select_rows(float2 (*P)[kPB + 1], const int* gid, int nr, int kb,
 // inside the FP32 range); a zero pivot column stays zero.
 __device__ __forceinline__ float2 to_f2(double2 z) { return make_float2((float)z.x, (float)z.y); }
 
+__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// FP64 LU (without further pivoting) of the block D = A[sel][K], the chosen
+// rows in selection order: lu[r][c] holds L below the diagonal (unit
+// diagonal implied) and U on and above it, lu[NB*NB + s] = 1/U_ss.  Run by
+// the CTA that makes the final choice, before the rows are swapped; the
+// buffer P (no longer needed) holds D.
+__device__ void factor_block(const double2* __restrict__ A, int ng, int k0, int kb, const int* sel, void* scratch,
+                             double2* __restrict__ lu, int* __restrict__ status) {
+  double2 (*D)[kPB + 1] = reinterpret_cast<double2 (*)[kPB + 1]>(scratch);
+  __shared__ double2 rinv[kPB];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kPB * kPB; e += blockDim.x) {
+    const int r = e / kPB, c = e % kPB;
+    D[r][c] = (r < kb && c < kb) ? A[(size_t)sel[r] * ng + k0 + c] : make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
+  for (int s = 0; s < kb; ++s) {
+    __syncthreads();
+    if (tid == 0) {
+      const double2 p = D[s][s];
+      const double m2 = p.x * p.x + p.y * p.y;
+      if (!(m2 > 0.0) || !isfinite(m2)) {
+        atomicExch(status, (int)kDevZeroPivot);
+        rinv[s] = make_double2(0.0, 0.0);
+      } else {
+        const double q = 1.0 / m2;
+        rinv[s] = make_double2(p.x * q, -p.y * q);
+      }
+    }
+    __syncthreads();
+    for (int r = s + 1 + tid; r < kb; r += blockDim.x) D[r][s] = cmul2(D[r][s], rinv[s]);
+    __syncthreads();
+    const int w = kb - 1 - s;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int r = s + 1 + e / w, c = s + 1 + e % w;
+      const double2 t = cmul2(D[r][s], D[s][c]);
+      D[r][c] = make_double2(D[r][c].x - t.x, D[r][c].y - t.y);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < kPB * kPB; e += blockDim.x) lu[e] = D[e / kPB][e % kPB];
+  for (int e = tid; e < kPB; e += blockDim.x) lu[kPB * kPB + e] = e < kb ? rinv[e] : make_double2(1.0, 0.0);
+}
+
+// Row panel R = D^-1 A_K,: from the factors (after the swap, row k0 + r is
+// the r-th chosen row): each CTA solves L U x = b for 16 columns of A_K,:,
+// the block's own columns replaced by identity columns (R = D^-1 there).
+// blockIdx.y >= 1 copies the column panel Cp = A_:,K (ld NB).  256 threads:
+// 16 columns x 16 row groups (rows g, g + 16).
+__global__ void __launch_bounds__(256) solve_panels_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
+                                                           const double2* __restrict__ lu, double2* __restrict__ R,
+                                                           double2* __restrict__ C) {
+  const int tid = threadIdx.x;
+  if (blockIdx.y > 0) {
+    const int i = (blockIdx.y - 1) * 256 + tid;
+    if (blockIdx.x != 0 || i >= ng) return;
+    for (int s = 0; s < kb; ++s) C[(size_t)i * kPB + s] = A[(size_t)i * ng + k0 + s];
+    return;
+  }
+  __shared__ double2 D[kPB][kPB + 1];
+  __shared__ double2 B[kPB][17];
+  __shared__ double2 rinv[kPB];
+  const int j0 = blockIdx.x * 16;
+  for (int e = tid; e < kPB * kPB; e += 256) D[e / kPB][e % kPB] = lu[e];
+  if (tid < kPB) rinv[tid] = lu[kPB * kPB + tid];
+  for (int e = tid; e < kPB * 16; e += 256) {
+    const int r = e / 16, jj = e % 16, j = j0 + jj;
+    double2 v = make_double2(0.0, 0.0);
+    if (r < kb && j < ng)
+      v = (j >= k0 && j < k0 + kb) ? make_double2(j - k0 == r ? 1.0 : 0.0, 0.0) : A[(size_t)(k0 + r) * ng + j];
+    B[r][jj] = v;
+  }
+  const int col = tid & 15, g = tid >> 4;
+  for (int s = 0; s < kb; ++s) {   // unit lower factor
+    __syncthreads();
+    const double2 y = B[s][col];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = g + 16 * h;
+      if (r > s && r < kb) {
+        const double2 t = cmul2(D[r][s], y);
+        B[r][col] = make_double2(B[r][col].x - t.x, B[r][col].y - t.y);
+      }
+    }
+  }
+  for (int s = kb - 1; s >= 0; --s) {   // upper factor
+    __syncthreads();
+    if (g == (s & 15)) B[s][col] = cmul2(B[s][col], rinv[s]);
+    __syncthreads();
+    const double2 x = B[s][col];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = g + 16 * h;
+      if (r < s) {
+        const double2 t = cmul2(D[r][s], x);
+        B[r][col] = make_double2(B[r][col].x - t.x, B[r][col].y - t.y);
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < kPB * 16; e += 256) {
+    const int r = e / 16, jj = e % 16, j = j0 + jj;
+    if (r < kb && j < ng) R[(size_t)r * ng + j] = B[r][jj];
+  }
+}
+
 // Leaf round: CTA b takes rows k0 + 256 b ... of the panel.
 __global__ void __launch_bounds__(kTRows) pivot_leaf_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
-                                                            int* __restrict__ out, int* __restrict__ cnt) {
+                                                            int* __restrict__ out, int* __restrict__ cnt,
+                                                            double2* __restrict__ lu, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 (*P)[kPB + 1] = reinterpret_cast<float2 (*)[kPB + 1]>(smem_raw);
   __shared__ int gid[kTRows];
@@ -122,13 +231,15 @@ __global__ void __launch_bounds__(kTRows) pivot_leaf_kernel(const double2* __res
   __syncthreads();
   if (t < n) out[blockIdx.x * kPB + t] = sel[t];
   if (t == 0) cnt[blockIdx.x] = n;
+  if (gridDim.x == 1) factor_block(A, ng, k0, kb, sel, smem_raw, lu, status);   // the final choice
 }
 
 // Merge round: CTA m takes candidate sets 8m .. 8m+7 (of ngroups).
 __global__ void __launch_bounds__(kTRows) pivot_merge_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
                                                              const int* __restrict__ in, const int* __restrict__ cin,
                                                              int ngroups, int* __restrict__ out,
-                                                             int* __restrict__ cout) {
+                                                             int* __restrict__ cout, double2* __restrict__ lu,
+                                                             int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 (*P)[kPB + 1] = reinterpret_cast<float2 (*)[kPB + 1]>(smem_raw);
   __shared__ int gid[kTRows];
@@ -150,6 +261,7 @@ __global__ void __launch_bounds__(kTRows) pivot_merge_kernel(const double2* __re
   __syncthreads();
   if (t < n) out[blockIdx.x * kPB + t] = sel[t];
   if (t == 0) cout[blockIdx.x] = n;
+  if (gridDim.x == 1) factor_block(A, ng, k0, kb, sel, smem_raw, lu, status);   // the final choice
 }
 
 // Brings row sel[j] to row k0 + j for j < kb by successive interchanges
@@ -229,7 +341,7 @@ int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
   sv.pool = dinv.pool = R.pool = Cp.pool = cand.pool = ipiv.pool = &c->pool;
   int rc;
   if ((rc = c->pool.alloc((size_t)ngmax * sizeof(double), &sv.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)kPB * kPB * sizeof(double2), &dinv.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)kPB * (kPB + 1) * sizeof(double2), &dinv.ptr)) != BGW_OK ||
       (rc = c->pool.alloc((size_t)kPB * ngmax * sizeof(double2), &R.ptr)) != BGW_OK ||
       (rc = c->pool.alloc((size_t)kPB * ngmax * sizeof(double2), &Cp.ptr)) != BGW_OK ||
       (rc = c->pool.alloc((size_t)2 * nleaf_max * (kPB + 1) * sizeof(int), &cand.ptr)) != BGW_OK ||
@@ -268,13 +380,15 @@ int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
         TimedScope tp(c, kTPivot, st);
         // candidates of set g at buf[g * 32], counts after the candidates
         int* cnt0 = cbuf[0] + (size_t)nleaf_max * kPB;
-        pivot_leaf_kernel<<<groups, kTRows, psmem, st>>>(A, n, k0, kb, cbuf[0], cnt0);
+        pivot_leaf_kernel<<<groups, kTRows, psmem, st>>>(A, n, k0, kb, cbuf[0], cnt0, dinv.as<double2>(),
+                                                         c->d_status);
         c->launches += 1;
         while (groups > 1) {
           const int next = (groups + 7) / 8;
           int* cin = cbuf[cur] + (size_t)nleaf_max * kPB;
           int* cout = cbuf[1 - cur] + (size_t)nleaf_max * kPB;
-          pivot_merge_kernel<<<next, kTRows, psmem, st>>>(A, n, k0, kb, cbuf[cur], cin, groups, cbuf[1 - cur], cout);
+          pivot_merge_kernel<<<next, kTRows, psmem, st>>>(A, n, k0, kb, cbuf[cur], cin, groups, cbuf[1 - cur], cout,
+                                                          dinv.as<double2>(), c->d_status);
           c->launches += 1;
           cur = 1 - cur;
           groups = next;
@@ -285,10 +399,13 @@ int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
       }
       {
         TimedScope tg(c, kTSweepChain, st);
-        if ((rc = gj_step_run(c, A, n, k0, kb, dinv.as<double2>(), R.as<double2>(), Cp.as<double2>(), st,
-                              !tc_update)) != BGW_OK)
-          return rc;
+        solve_panels_kernel<<<dim3((n + 15) / 16, 1 + (n + 255) / 256), 256, 0, st>>>(
+            A, n, k0, kb, dinv.as<double2>(), R.as<double2>(), Cp.as<double2>());
+        c->launches += 1;
+        BGW_CUDA(c, cudaGetLastError());
       }
+      if (!tc_update && (rc = gj_update_run(c, A, n, k0, kb, R.as<double2>(), Cp.as<double2>(), st)) != BGW_OK)
+        return rc;
       if (tc_update) {
         TimedScope tu(c, kTOzUpdate, st);
         if ((rc = oz_slice(c, oz.get(), k0, n, 0, st)) != BGW_OK || (rc = oz_update(c, oz.get(), k0, n, 0, 0, st)) != BGW_OK)

@@ -221,11 +221,11 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cel
 // the cell's Coulomb model (epsinv.cu).
 int eps_form_run(Ctx* c, const bgw_cell* cell, const int32_t* d_geps, int ng, const void* chi, double* sv,
                  double2* A, void* eps, cudaStream_t st);
-// One blocked Gauss-Jordan step without pivoting on columns k0..k0+kb
-// (kb <= 32) of the general matrix A; dinv [32][32], R [32][ng], Cp [ng][32].
-// update = false stops after the panels (the caller updates A itself).
-int gj_step_run(Ctx* c, double2* A, int ng, int k0, int kb, double2* dinv, double2* R, double2* Cp,
-                cudaStream_t st, bool update = true);
+// FP64 FMA trailing update of one general Gauss-Jordan step on columns
+// k0..k0+kb (kb <= 32): rows of K become R [32][ng], the others
+// A_ij = (j in K ? 0 : A_ij) - (Cp R)_ij with Cp [ng][32].
+int gj_update_run(Ctx* c, double2* A, int ng, int k0, int kb, const double2* R, const double2* Cp,
+                  cudaStream_t st);
 // General (non-Hermitian) eps~ and its inverse with partial pivoting
 // (epsinv_general.cu), one matrix after the other.
 // tc_update: the trailing updates on the tensor cores (Ozaki split, FP64-level
