@@ -235,6 +235,10 @@ def run_ours(args):
         issued_step = tiles * 224 * 2.0 * 128 * 32 * 16
         n_inv = kt["oz_update"][0] / (2 * nsteps)
         t_step = kt["oz_update"][1] / 1e3 / (n_inv * nsteps)      # s of update per sweep step
+        # DRAM bytes of one sweep step's two update launches at N_G = 2120 (dram__bytes_read.sum +
+        # dram__bytes_write.sum of one ncu capture of this kernel): 3.85 MB + 37.4 MB.  The matrix
+        # stays in L2, so this is below the tiles' algorithmic traffic.
+        oz_traffic_step = 41.2e6 if s.ng == 2120 else None
         roof = {"bound": "tensor", "kernel": "oz::update_kernel (tcgen05 kind::f16 M128 N32: the sweep's trailing "
                                              "update from exact FP16 slices, FP64-level result)",
                 "achieved": issued_step / t_step / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
@@ -242,7 +246,8 @@ def run_ours(args):
                                "(28 slice pairs per FP64 product)",
                 "peak_source": "measured bf16 burst (fp16 has the same nominal rate)",
                 "fp64_equivalent_tflops": 4.0 * 32 * s.ng * s.ng / t_step / 1e12,
-                "fp64_pipe_peak_tflops": FP64_PEAK_TFLOPS}
+                "fp64_pipe_peak_tflops": FP64_PEAK_TFLOPS,
+                "traffic_bytes_per_sweep_step": oz_traffic_step}
     elif dom == "inverse":
         roof = {"bound": "alu", "kernel": "Hermitian blocked sweep inverse (sw_diag/sw_panel/sw_update/sw_finish, FP64 FMA)",
                 "achieved": fl["inv_herm"] / (kms[dom] / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -262,7 +267,7 @@ def run_ours(args):
         roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": "TFLOP/s"}
     if roof.get("achieved") is not None:
         roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = roof.pop("traffic_bytes_per_sweep_step", None)
     roof["share_of_step"] = per_step_ms[dom] / float(stage.sum(1).mean())
     chi_tc = None
     if "chi_tc" in kms:
@@ -291,6 +296,7 @@ def run_ours(args):
 
     batch = run_batch_c3(ctx, prec) if (ws == 1 and not args.skip_extra) else None
     f2 = run_f2(ctx, prec, flush) if (ws == 1 and not args.skip_extra) else None
+    ra = run_real_axis(ctx, prec, flush) if (ws == 1 and not args.skip_extra) else None
     serve = run_serve_c4(prec) if (ws == 1 and not args.skip_extra) else None
 
     out = {
@@ -318,6 +324,7 @@ def run_ours(args):
         "batch_c3": batch,
         "serve_c4": serve,
         "w_and_q0": f2,
+        "real_axis_c1": ra,
         "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(s.cv.nbytes + s.cc.nbytes),
                 "d2h_bytes_per_step": int(invh.numel() * 16)},
         "gpu_launches": int(launches),
@@ -424,6 +431,53 @@ def run_f2(ctx, prec, flush, steps=3, warmup=2):
           "head_fp32": {"solves_per_s": 1e3 / ms_off, "ms": ms_off, **errs(inv_off)},
           "eps_head_00": float(1.0 / ref[0, 0].real)}
     return {"screened_w": wout, "q0_c1": q0}
+
+
+def run_real_axis(ctx, prec, flush, steps=2, warmup=1):
+    """Real-axis (full-frequency) solve of the c1 sizes: bgw_epsilon_real with
+    device buffers, retarded, delta = 0.05 Ha, on the paper's grid with
+    spacing 0.1 Ha up to 0.5 Ha, then steps growing by 0.1 Ha up to 1.5 Ha
+    (9 frequencies).  One frequency of the same input through the plain FP64
+    path gives the error figure."""
+    import torch
+    from paper_1111_4429_gb300 import bgw, synth
+    st = torch.cuda.current_stream()
+    s = synth.config_system("c1")
+    grid = bgw.frequency_grid(0.1, 0.5, 1.5, 0.1)
+    cell = bgw.system_cell(s)
+    cv = torch.from_numpy(s.cv).cuda()
+    cc = torch.from_numpy(s.cc).cuda()
+    nf = len(grid)
+    out = torch.empty((nf, s.ng, s.ng), dtype=torch.complex128, device="cuda")
+    for _ in range(warmup):
+        ctx.epsilon_real(cell, s.gv, cv, s.ev, s.gc, cc, s.ec, s.geps, grid, 0.05, False, prec, 0, None, out)
+    ctx.sync()
+    ctx.set_option(bgw.BGW_OPT_TIMING, 1)
+    ctx.timing_report(reset=True)
+    tt = []
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        ctx.epsilon_real(cell, s.gv, cv, s.ev, s.gc, cc, s.ec, s.geps, grid, 0.05, False, prec, 0, None, out)
+        b.record(st)
+        b.synchronize()
+        tt.append(a.elapsed_time(b))
+    kt = ctx.timing_report(reset=True)
+    ctx.set_option(bgw.BGW_OPT_TIMING, 0)
+    ctx.sync()
+    ms = float(np.mean(tt))
+    one = torch.empty((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
+    ctx.epsilon_real(cell, s.gv, cv, s.ev, s.gc, cc, s.ec, s.geps, grid[-1:], 0.05, False, bgw.BGW_PREC_FP64, 0,
+                     None, one)
+    ctx.sync()
+    err = float(torch.linalg.matrix_norm(out[-1] - one[0]) / torch.linalg.matrix_norm(one[0]))
+    return {"workload": "c1 sizes (N_v 32, N_c 800, N_G 2120), retarded, delta 0.05 Ha, %d real frequencies "
+                        "(grid: spacing 0.1, low cutoff 0.5, high cutoff 1.5, increment 0.1 Ha)" % nf,
+            "frequencies": [float(x) for x in grid],
+            "ms_per_call": ms, "frequency_solves_per_s": nf * 1e3 / ms,
+            "kernel_ms_per_call": {k: v[1] / steps for k, v in kt.items()},
+            "epsinv_rel_err_vs_plain_fp64_gpu_at_1.4Ha": err}
 
 
 def run_batch_c3(ctx, prec, steps=2):
@@ -580,27 +634,52 @@ def run_reference(args):
 
 
 def run_profile_case(args):
-    """One solve of a reduced c1 case for ncu captures: c1 cell and spheres
-    with N_c = 200 (K = 6400 pairs, M = 217 MB > L2, about 1.5 GB on the
-    device), after one warm-up solve."""
+    """Small cases for ncu captures (each after one warm-up call):
+    solve   -- one solve of the c1 cell and spheres with N_c = 200 (K = 6400
+               pairs, M = 217 MB > L2, about 1.5 GB on the device);
+    general -- one pivoted general inverse (bgw_epsinv_general, tensor-core
+               update) of a seeded random complex N_G = 2120 chi;
+    w       -- bgw_screened_w on 8 seeded random N_G = 2120 matrices."""
     import torch
     from paper_1111_4429_gb300 import bgw, synth
-    s = synth.config_system("c1", nc=200)
     ctx = bgw.Context(0)
-    cell = bgw.system_cell(s)
-    prec = bgw.PREC[args.prec]
-    ctx.set_option(bgw.BGW_OPT_INVERSE, 0 if prec == bgw.BGW_PREC_FP64 else 1)
-    cv = torch.from_numpy(s.cv).cuda()
-    cc = torch.from_numpy(s.cc).cuda()
-    M = torch.empty((s.npairs, s.ng), dtype=torch.complex128 if prec == 0 else torch.complex64, device="cuda")
-    chi = torch.empty((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
-    inv = torch.empty_like(chi)
-    for _ in range(2):
-        ctx.mtxel(cell, s.gv, cv, s.gc, cc, s.geps, prec, M)
-        ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, s.ec, None, prec, False, chi)
-        ctx.epsinv([cell], [s.geps], [chi], None, [inv])
-    ctx.sync()
-    print(json.dumps({"profile_case": "c1 cell, N_c=200", "precision": args.prec, "launches": ctx.launch_count()}))
+    case = args.profile_case
+    if case == "solve":
+        s = synth.config_system("c1", nc=200)
+        cell = bgw.system_cell(s)
+        prec = bgw.PREC[args.prec]
+        ctx.set_option(bgw.BGW_OPT_INVERSE, 0 if prec == bgw.BGW_PREC_FP64 else 1)
+        cv = torch.from_numpy(s.cv).cuda()
+        cc = torch.from_numpy(s.cc).cuda()
+        M = torch.empty((s.npairs, s.ng), dtype=torch.complex128 if prec == 0 else torch.complex64, device="cuda")
+        chi = torch.empty((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
+        inv = torch.empty_like(chi)
+        for _ in range(2):
+            ctx.mtxel(cell, s.gv, cv, s.gc, cc, s.geps, prec, M)
+            ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, s.ec, None, prec, False, chi)
+            ctx.epsinv([cell], [s.geps], [chi], None, [inv])
+        ctx.sync()
+        desc = "c1 cell, N_c=200"
+    else:
+        s = synth.config_system("c1")
+        ng = s.ng
+        gen = torch.Generator(device="cuda").manual_seed(1)
+        cell = bgw.system_cell(s)
+        if case == "general":
+            x = torch.randn((ng, ng), dtype=torch.complex128, device="cuda", generator=gen) * 1e-3
+            inv = torch.empty_like(x)
+            ctx.set_option(bgw.BGW_OPT_INVERSE, 1)
+            for _ in range(2):
+                ctx.epsinv_general([cell], [s.geps], [x], None, [inv])
+            desc = "general inverse N_G=2120, tensor-core update"
+        else:
+            x = torch.randn((8, ng, ng), dtype=torch.complex128, device="cuda", generator=gen)
+            w = torch.empty_like(x)
+            for _ in range(2):
+                ctx.screened_w([cell] * 8, [s.geps] * 8, list(x), list(w))
+            desc = "screened W, 8 x N_G=2120"
+        ctx.sync()
+    print(json.dumps({"profile_case": desc, "precision": args.prec, "launches": ctx.launch_count()}))
 
 
 def main():
@@ -612,7 +691,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="mix_fp16", choices=["fp64", "mix_fp16", "mix_bf16"])
     ap.add_argument("--skip-extra", action="store_true", help="skip the batched q x iw and served-stream parts")
-    ap.add_argument("--profile-case", action="store_true", help="reduced c1 solve for ncu captures")
+    ap.add_argument("--profile-case", nargs="?", const="solve", default=None, choices=["solve", "general", "w"],
+                    help="small case for ncu captures (solve: reduced c1 solve; general: one pivoted general "
+                         "inverse; w: screened W on 8 matrices)")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)

@@ -33,6 +33,11 @@ namespace {
 constexpr int kPB = 32;      // block width of the Gauss-Jordan step
 constexpr int kTRows = 256;  // rows per selection CTA (one per thread)
 constexpr int kSwapCols = 64;
+constexpr int kGB = 16;      // matrices of one size stepped together (grid.y / grid.z = matrix)
+
+struct GenPtrs {
+  double2* A[kGB];
+};
 
 __device__ __forceinline__ double cabs1(double2 z) { return fabs(z.x) + fabs(z.y); }
 
@@ -155,10 +160,15 @@ __device__ void factor_block(const double2* __restrict__ A, int ng, int k0, int 
 // the block's own columns replaced by identity columns (R = D^-1 there).
 // blockIdx.y >= 1 copies the column panel Cp = A_:,K (ld NB).  256 threads:
 // 16 columns x 16 row groups (rows g, g + 16).
-__global__ void __launch_bounds__(256) solve_panels_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
-                                                           const double2* __restrict__ lu, double2* __restrict__ R,
-                                                           double2* __restrict__ C) {
+__global__ void __launch_bounds__(256) solve_panels_kernel(const __grid_constant__ GenPtrs P, int ng, int k0,
+                                                           int kb, const double2* __restrict__ lu_all,
+                                                           double2* __restrict__ R_all, double2* __restrict__ C_all) {
   const int tid = threadIdx.x;
+  const int m = blockIdx.z;
+  const double2* __restrict__ A = P.A[m];
+  const double2* __restrict__ lu = lu_all + (size_t)m * kPB * (kPB + 1);
+  double2* __restrict__ R = R_all + (size_t)m * kPB * ng;
+  double2* __restrict__ C = C_all + (size_t)m * kPB * ng;
   if (blockIdx.y > 0) {
     const int i = (blockIdx.y - 1) * 256 + tid;
     if (blockIdx.x != 0 || i >= ng) return;
@@ -213,10 +223,15 @@ __global__ void __launch_bounds__(256) solve_panels_kernel(const double2* __rest
 }
 
 // Leaf round: CTA b takes rows k0 + 256 b ... of the panel.
-__global__ void __launch_bounds__(kTRows) pivot_leaf_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
-                                                            int* __restrict__ out, int* __restrict__ cnt,
-                                                            double2* __restrict__ lu, int* __restrict__ status) {
+__global__ void __launch_bounds__(kTRows) pivot_leaf_kernel(const __grid_constant__ GenPtrs Pm, int ng, int k0,
+                                                            int kb, int* __restrict__ out_all, int cstride,
+                                                            double2* __restrict__ lu_all, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = blockIdx.y;
+  const double2* __restrict__ A = Pm.A[m];
+  int* __restrict__ out = out_all + (size_t)m * cstride;
+  int* __restrict__ cnt = out + (cstride / (kPB + 1)) * kPB;
+  double2* __restrict__ lu = lu_all + (size_t)m * kPB * (kPB + 1);
   float2 (*P)[kPB + 1] = reinterpret_cast<float2 (*)[kPB + 1]>(smem_raw);
   __shared__ int gid[kTRows];
   __shared__ int sel[kPB];
@@ -235,12 +250,18 @@ __global__ void __launch_bounds__(kTRows) pivot_leaf_kernel(const double2* __res
 }
 
 // Merge round: CTA m takes candidate sets 8m .. 8m+7 (of ngroups).
-__global__ void __launch_bounds__(kTRows) pivot_merge_kernel(const double2* __restrict__ A, int ng, int k0, int kb,
-                                                             const int* __restrict__ in, const int* __restrict__ cin,
-                                                             int ngroups, int* __restrict__ out,
-                                                             int* __restrict__ cout, double2* __restrict__ lu,
-                                                             int* __restrict__ status) {
+__global__ void __launch_bounds__(kTRows) pivot_merge_kernel(const __grid_constant__ GenPtrs Pm, int ng, int k0,
+                                                             int kb, const int* __restrict__ in_all,
+                                                             int ngroups, int* __restrict__ out_all, int cstride,
+                                                             double2* __restrict__ lu_all, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = blockIdx.y;
+  const double2* __restrict__ A = Pm.A[m];
+  const int* __restrict__ in = in_all + (size_t)m * cstride;
+  const int* __restrict__ cin = in + (cstride / (kPB + 1)) * kPB;
+  int* __restrict__ out = out_all + (size_t)m * cstride;
+  int* __restrict__ cout = out + (cstride / (kPB + 1)) * kPB;
+  double2* __restrict__ lu = lu_all + (size_t)m * kPB * (kPB + 1);
   float2 (*P)[kPB + 1] = reinterpret_cast<float2 (*)[kPB + 1]>(smem_raw);
   __shared__ int gid[kTRows];
   __shared__ int sel[kPB];
@@ -267,9 +288,14 @@ __global__ void __launch_bounds__(kTRows) pivot_merge_kernel(const double2* __re
 // Brings row sel[j] to row k0 + j for j < kb by successive interchanges
 // (recorded in ipiv[k0 + j]).  Every CTA replays the interchanges on the set
 // of affected rows (at most 64) and moves its 64 columns of them.
-__global__ void __launch_bounds__(256) pivot_swap_kernel(double2* __restrict__ A, int ng, int k0, int kb,
-                                                         const int* __restrict__ sel, int* __restrict__ ipiv) {
+__global__ void __launch_bounds__(256) pivot_swap_kernel(const __grid_constant__ GenPtrs Pm, int ng, int k0, int kb,
+                                                         const int* __restrict__ sel_all, int cstride,
+                                                         int* __restrict__ ipiv_all) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = blockIdx.y;
+  double2* __restrict__ A = Pm.A[m];
+  const int* __restrict__ sel = sel_all + (size_t)m * cstride;
+  int* __restrict__ ipiv = ipiv_all + (size_t)m * ng;
   double2 (*buf)[kSwapCols] = reinterpret_cast<double2 (*)[kSwapCols]>(smem_raw);
   __shared__ int pos[2 * kPB];   // positions of the affected rows
   __shared__ int from[2 * kPB];  // original row that ends at pos[i]
@@ -308,8 +334,10 @@ __global__ void __launch_bounds__(256) pivot_swap_kernel(double2* __restrict__ A
 
 // Column j of the inverse is column src[j] of the working matrix: the
 // interchanges undone on the columns, last first.
-__global__ void colperm_build_kernel(const int* __restrict__ ipiv, int ng, int* __restrict__ src) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void colperm_build_kernel(const int* __restrict__ ipiv_all, int ng, int* __restrict__ src_all) {
+  if (threadIdx.x != 0) return;
+  const int* __restrict__ ipiv = ipiv_all + (size_t)blockIdx.x * ng;
+  int* __restrict__ src = src_all + (size_t)blockIdx.x * ng;
   for (int j = 0; j < ng; ++j) src[j] = j;
   for (int j = ng - 1; j >= 0; --j) {
     const int p = ipiv[j];
@@ -319,11 +347,12 @@ __global__ void colperm_build_kernel(const int* __restrict__ ipiv, int ng, int* 
   }
 }
 
-__global__ void __launch_bounds__(256) colperm_apply_kernel(double2* __restrict__ A, int ng,
-                                                            const int* __restrict__ src) {
+__global__ void __launch_bounds__(256) colperm_apply_kernel(const __grid_constant__ GenPtrs Pm, int ng,
+                                                            const int* __restrict__ src_all) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* row = reinterpret_cast<double2*>(smem_raw);
-  double2* a = A + (size_t)blockIdx.x * ng;
+  double2* a = Pm.A[blockIdx.y] + (size_t)blockIdx.x * ng;
+  const int* __restrict__ src = src_all + (size_t)blockIdx.y * ng;
   for (int j = threadIdx.x; j < ng; j += 256) row[j] = a[j];
   __syncthreads();
   for (int j = threadIdx.x; j < ng; j += 256) a[j] = row[src[j]];
@@ -337,15 +366,16 @@ int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
   int ngmax = 0;
   for (int m = 0; m < nmat; ++m) ngmax = std::max(ngmax, ng[m]);
   const int nleaf_max = (ngmax + kTRows - 1) / kTRows;
-  Scratch sv, dinv, R, Cp, cand, ipiv;
-  sv.pool = dinv.pool = R.pool = Cp.pool = cand.pool = ipiv.pool = &c->pool;
+  const int cstride = nleaf_max * (kPB + 1);   // candidates then counts, per matrix
+  Scratch sv, lu, R, Cp, cand, ipiv;
+  sv.pool = lu.pool = R.pool = Cp.pool = cand.pool = ipiv.pool = &c->pool;
   int rc;
   if ((rc = c->pool.alloc((size_t)ngmax * sizeof(double), &sv.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)kPB * (kPB + 1) * sizeof(double2), &dinv.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)kPB * ngmax * sizeof(double2), &R.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)kPB * ngmax * sizeof(double2), &Cp.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)2 * nleaf_max * (kPB + 1) * sizeof(int), &cand.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)2 * ngmax * sizeof(int), &ipiv.ptr)) != BGW_OK)
+      (rc = c->pool.alloc((size_t)kGB * kPB * (kPB + 1) * sizeof(double2), &lu.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)kGB * kPB * ngmax * sizeof(double2), &R.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)kGB * kPB * ngmax * sizeof(double2), &Cp.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)2 * kGB * cstride * sizeof(int), &cand.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)2 * kGB * ngmax * sizeof(int), &ipiv.ptr)) != BGW_OK)
     return fail(c, rc, "general inverse: scratch allocation failed");
   const size_t psmem = sizeof(float2) * kTRows * (kPB + 1);
   const size_t ssmem = sizeof(double2) * 2 * kPB * kSwapCols;
@@ -354,69 +384,84 @@ int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
   BGW_CUDA(c, cudaFuncSetAttribute(pivot_swap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
   BGW_CUDA(c, cudaFuncSetAttribute(colperm_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(sizeof(double2) * ngmax)));
-  int* cbuf[2] = {cand.as<int>(), cand.as<int>() + (size_t)nleaf_max * (kPB + 1)};
-  int* piv = ipiv.as<int>();
-  int* src = piv + ngmax;
-  for (int m = 0; m < nmat; ++m) {
-    const int n = ng[m];
-    double2* A = static_cast<double2*>(epsinv[m]);
-    if ((rc = eps_form_run(c, cells[m], d_geps[m], n, chi[m], sv.as<double>(), A, eps ? eps[m] : nullptr, st)) !=
-        BGW_OK)
-      return rc;
+  int* cbuf[2] = {cand.as<int>(), cand.as<int>() + (size_t)kGB * cstride};
+  // Matrices of equal size are stepped together, up to kGB at a time: every
+  // launch below serves the whole group.
+  for (int m0 = 0; m0 < nmat;) {
+    const int n = ng[m0];
+    int nb = 1;
+    while (m0 + nb < nmat && nb < kGB && ng[m0 + nb] == n) ++nb;
+    GenPtrs P = {};
+    for (int k = 0; k < nb; ++k) {
+      const int m = m0 + k;
+      P.A[k] = static_cast<double2*>(epsinv[m]);
+      if ((rc = eps_form_run(c, cells[m], d_geps[m], n, chi[m], sv.as<double>(), P.A[k], eps ? eps[m] : nullptr,
+                             st)) != BGW_OK)
+        return rc;
+    }
     TimedScope ts(c, kTInverse, st);
     std::unique_ptr<OzPlan, void (*)(OzPlan*)> oz(nullptr, oz_plan_delete);
     if (tc_update) {
       oz.reset(oz_plan_new());
-      double2* Am = A;
-      const double2* Rm = R.as<double2>();
-      const double2* Cm = Cp.as<double2>();
-      if ((rc = oz_prepare(c, 1, &n, &Am, &Rm, &Cm, nullptr, oz.get(), true)) != BGW_OK) return rc;
+      std::vector<int> ngs(nb, n);
+      std::vector<double2*> As(nb);
+      std::vector<const double2*> Rs(nb), Cs(nb);
+      for (int k = 0; k < nb; ++k) {
+        As[k] = P.A[k];
+        Rs[k] = R.as<double2>() + (size_t)k * kPB * n;
+        Cs[k] = Cp.as<double2>() + (size_t)k * kPB * n;
+      }
+      if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Rs.data(), Cs.data(), nullptr, oz.get(), true)) != BGW_OK)
+        return rc;
     }
+    int* piv = ipiv.as<int>();
+    int* src = piv + (size_t)kGB * ngmax;
     for (int k0 = 0; k0 < n; k0 += kPB) {
       const int kb = std::min(kPB, n - k0);
       int groups = (n - k0 + kTRows - 1) / kTRows;
       int cur = 0;
       {
         TimedScope tp(c, kTPivot, st);
-        // candidates of set g at buf[g * 32], counts after the candidates
-        int* cnt0 = cbuf[0] + (size_t)nleaf_max * kPB;
-        pivot_leaf_kernel<<<groups, kTRows, psmem, st>>>(A, n, k0, kb, cbuf[0], cnt0, dinv.as<double2>(),
-                                                         c->d_status);
+        pivot_leaf_kernel<<<dim3(groups, nb), kTRows, psmem, st>>>(P, n, k0, kb, cbuf[0], cstride, lu.as<double2>(),
+                                                                   c->d_status);
         c->launches += 1;
         while (groups > 1) {
           const int next = (groups + 7) / 8;
-          int* cin = cbuf[cur] + (size_t)nleaf_max * kPB;
-          int* cout = cbuf[1 - cur] + (size_t)nleaf_max * kPB;
-          pivot_merge_kernel<<<next, kTRows, psmem, st>>>(A, n, k0, kb, cbuf[cur], cin, groups, cbuf[1 - cur], cout,
-                                                          dinv.as<double2>(), c->d_status);
+          pivot_merge_kernel<<<dim3(next, nb), kTRows, psmem, st>>>(P, n, k0, kb, cbuf[cur], groups, cbuf[1 - cur],
+                                                                    cstride, lu.as<double2>(), c->d_status);
           c->launches += 1;
           cur = 1 - cur;
           groups = next;
         }
-        pivot_swap_kernel<<<(n + kSwapCols - 1) / kSwapCols, 256, ssmem, st>>>(A, n, k0, kb, cbuf[cur], piv);
+        pivot_swap_kernel<<<dim3((n + kSwapCols - 1) / kSwapCols, nb), 256, ssmem, st>>>(P, n, k0, kb, cbuf[cur],
+                                                                                         cstride, piv);
         c->launches += 1;
         BGW_CUDA(c, cudaGetLastError());
       }
       {
         TimedScope tg(c, kTSweepChain, st);
-        solve_panels_kernel<<<dim3((n + 15) / 16, 1 + (n + 255) / 256), 256, 0, st>>>(
-            A, n, k0, kb, dinv.as<double2>(), R.as<double2>(), Cp.as<double2>());
+        solve_panels_kernel<<<dim3((n + 15) / 16, 1 + (n + 255) / 256, nb), 256, 0, st>>>(
+            P, n, k0, kb, lu.as<double2>(), R.as<double2>(), Cp.as<double2>());
         c->launches += 1;
         BGW_CUDA(c, cudaGetLastError());
       }
-      if (!tc_update && (rc = gj_update_run(c, A, n, k0, kb, R.as<double2>(), Cp.as<double2>(), st)) != BGW_OK)
-        return rc;
-      if (tc_update) {
+      if (!tc_update) {
+        for (int k = 0; k < nb; ++k)
+          if ((rc = gj_update_run(c, P.A[k], n, k0, kb, R.as<double2>() + (size_t)k * kPB * n,
+                                  Cp.as<double2>() + (size_t)k * kPB * n, st)) != BGW_OK)
+            return rc;
+      } else {
         TimedScope tu(c, kTOzUpdate, st);
         if ((rc = oz_slice(c, oz.get(), k0, n, 0, st)) != BGW_OK || (rc = oz_update(c, oz.get(), k0, n, 0, 0, st)) != BGW_OK)
           return rc;
         c->launches += 3;
       }
     }
-    colperm_build_kernel<<<1, 1, 0, st>>>(piv, n, src);
-    colperm_apply_kernel<<<n, 256, sizeof(double2) * n, st>>>(A, n, src);
+    colperm_build_kernel<<<nb, 1, 0, st>>>(piv, n, src);
+    colperm_apply_kernel<<<dim3(n, nb), 256, sizeof(double2) * n, st>>>(P, n, src);
     BGW_CUDA(c, cudaGetLastError());
     c->launches += 2;
+    m0 += nb;
   }
   return BGW_OK;
 }
