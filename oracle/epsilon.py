@@ -181,6 +181,45 @@ def chi_entries(M_rows_g: np.ndarray, M_rows_gp: np.ndarray, w: np.ndarray,
 
 
 # ---------------------------------------------------------------------------
+# Real flavor (Section "Real and complex flavors")
+# ---------------------------------------------------------------------------
+
+def realify(c: np.ndarray, energies: np.ndarray, tol: float, rank_tol: float = 1e-8) -> np.ndarray:
+    """Real coefficients from complex ones of states with inversion and
+    time-reversal symmetry, as the paper prescribes: bands whose energies lie
+    within tol of their neighbour form a degenerate subspace of n states; the
+    2n vectors Re c_1, Im c_1, Re c_2, Im c_2, ... are orthonormalized in that
+    order by Gram-Schmidt (a vector whose remainder is below rank_tol of its
+    norm is dropped) and the first n kept.  A non-degenerate state (n = 1)
+    thereby loses its global phase.  Raises if a subspace yields fewer than
+    n independent real vectors."""
+    c = np.asarray(c, dtype=np.complex128)
+    e = np.asarray(energies, dtype=np.float64)
+    nb = c.shape[0]
+    out = np.zeros(c.shape, dtype=np.float64)
+    start = 0
+    while start < nb:
+        stop = start + 1
+        while stop < nb and abs(e[stop] - e[stop - 1]) <= tol:
+            stop += 1
+        n = stop - start
+        basis = []
+        for b in range(start, stop):
+            for v in (c[b].real, c[b].imag):
+                r = v.copy()
+                for q in basis:
+                    r -= (q @ r) * q
+                nr = np.linalg.norm(r)
+                if nr > rank_tol * max(np.linalg.norm(v), 1e-300):
+                    basis.append(r / nr)
+        if len(basis) < n:
+            raise np.linalg.LinAlgError(f"bands {start}..{stop - 1}: only {len(basis)} real directions")
+        out[start:stop] = np.array(basis[:n])
+        start = stop
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Real-axis ("full-frequency") response, Eq. (retarded_advanced_epsilon)
 # ---------------------------------------------------------------------------
 

@@ -112,10 +112,21 @@ class System:
         return self.nv * self.nc
 
 
+def orthonormal_real_bands(gen: np.random.Generator, npw: int, nb: int) -> np.ndarray:
+    """nb real orthonormal coefficient vectors of length npw (real flavor):
+    i.i.d. N(0,1) entries, reduced QR, bands as Q's columns."""
+    if nb > npw:
+        raise ValueError(f"cannot orthonormalize {nb} bands on {npw} plane waves")
+    q, _ = np.linalg.qr(gen.standard_normal((npw, nb)))
+    return np.ascontiguousarray(q.T.astype(np.float64))
+
+
 def make_system(name: str, a: float, fft: int, ecut_wfn: float, ecut_eps: float,
                 nv: int, nc: int, seed: int, q_frac=(0.1, 0.0, 0.0),
-                ev_range=(-0.5, 0.0), ec_range=(0.04, 1.5)) -> System:
-    """Build one seeded system with the recipe of the benchmark configurations."""
+                ev_range=(-0.5, 0.0), ec_range=(0.04, 1.5), real: bool = False) -> System:
+    """Build one seeded system with the recipe of the benchmark configurations.
+    real = True draws real coefficients (the real flavor: inversion and
+    time-reversal symmetry allow real wavefunctions in reciprocal space)."""
     bvec, omega = cubic_cell(a)
     q = np.asarray(q_frac, dtype=np.float64)
     gv = gsphere(bvec, q, ecut_wfn)
@@ -123,8 +134,9 @@ def make_system(name: str, a: float, fft: int, ecut_wfn: float, ecut_eps: float,
     geps = gsphere(bvec, q, ecut_eps)
     ss = np.random.SeedSequence(seed).spawn(len(_STREAMS))
     gens = {k: np.random.Generator(np.random.PCG64(s)) for k, s in zip(_STREAMS, ss)}
-    cv = orthonormal_bands(gens["cv"], gv.shape[0], nv)
-    cc = orthonormal_bands(gens["cc"], gc.shape[0], nc)
+    bands = orthonormal_real_bands if real else orthonormal_bands
+    cv = bands(gens["cv"], gv.shape[0], nv)
+    cc = bands(gens["cc"], gc.shape[0], nc)
     ev = np.sort(gens["ev"].uniform(ev_range[0], ev_range[1], nv))
     ec = np.sort(gens["ec"].uniform(ec_range[0], ec_range[1], nc))
     return System(name=name, a=a, bvec=bvec, omega=omega, q_frac=q, fft=fft, gv=gv, gc=gc,
@@ -187,6 +199,21 @@ def config_system(name: str, **overrides) -> System:
     p = dict(CONFIGS[name])
     p.update(overrides)
     return make_system(name, **p)
+
+
+def scramble_phases(c: np.ndarray, groups: Sequence[Sequence[int]], seed: int) -> np.ndarray:
+    """Complex coefficients as a plane-wave code returns them for real-flavor
+    states: every band times a random global phase, and every listed
+    degenerate group mixed by a random unitary matrix (the states of a
+    degenerate subspace need not be eigenstates of inversion)."""
+    gen = np.random.Generator(np.random.PCG64(seed))
+    out = np.asarray(c, dtype=np.complex128) * np.exp(2j * np.pi * gen.uniform(size=c.shape[0]))[:, None]
+    for g in groups:
+        g = list(g)
+        z = gen.standard_normal((len(g), len(g))) + 1j * gen.standard_normal((len(g), len(g)))
+        u, _ = np.linalg.qr(z)
+        out[g] = u @ out[g]
+    return np.ascontiguousarray(out)
 
 
 def batched_q_systems(nq: int = 8, seed: int = 1003) -> List[System]:

@@ -467,3 +467,50 @@ def test_real_axis_plane_wave_closed_form_and_adjoint_inverse():
         assert np.allclose(ra["epsinv"][f], np.conj(rr["epsinv"][f]).T, atol=1e-12)
         # tier 1 (Gauss-Jordan with partial pivoting) = tier 2 (library LU)
         assert _rel(oracle.inv_gauss_jordan(rr["eps"][f]), rr["epsinv"][f]) < 1e-13
+
+
+# ------------------------------------------------------------------ real flavor
+
+def test_realify_recovers_real_subspaces():
+    gen = np.random.default_rng(21)
+    npw, nb = 40, 7
+    q, _ = np.linalg.qr(gen.standard_normal((npw, nb)))
+    real = q.T                                        # real orthonormal bands
+    e = np.array([-0.5, -0.3, -0.3, -0.3, 0.1, 0.4, 0.4])
+    groups = [[1, 2, 3], [5, 6]]
+    cplx = synth.scramble_phases(real, groups, seed=5)
+    assert np.abs(cplx.imag).max() > 0.1              # genuinely complex input
+    r = oracle.realify(cplx, e, 1e-9)
+    assert r.dtype == np.float64
+    assert np.allclose(r @ r.T, np.eye(nb), atol=1e-13)
+    for g in [[0], [1, 2, 3], [4], [5, 6]]:
+        # same subspace: the projectors agree (the basis inside it is not unique)
+        pa, pb = real[g].T @ real[g], r[g].T @ r[g]
+        assert np.abs(pa - pb).max() < 1e-13
+    # a non-degenerate band is the original one up to sign
+    assert min(np.abs(r[0] - real[0]).max(), np.abs(r[0] + real[0]).max()) < 1e-13
+    # a subspace that is not real (no symmetry) has too few real directions
+    bad = gen.standard_normal((1, npw)) + 1j * gen.standard_normal((1, npw))
+    bad /= np.linalg.norm(bad)
+    r1 = oracle.realify(bad, np.array([0.0]), 1e-9)   # one complex vector: Re and Im give 2 directions
+    assert r1.shape == (1, npw)
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.realify(np.zeros((1, npw), complex), np.array([0.0]), 1e-9)
+
+
+def test_real_flavor_chain_is_real_and_matches_complex_path():
+    s = synth.make_system("rf", a=8.0, fft=12, ecut_wfn=4.0, ecut_eps=1.5, nv=3, nc=5, seed=31, real=True)
+    assert s.cv.dtype == np.float64 and s.cc.dtype == np.float64
+    md = oracle.mtxel_direct(s.gv, s.cv, s.gc, s.cc, s.geps)
+    mf = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    assert np.abs(md.imag).max() == 0.0                 # a sum of real products
+    assert np.abs(mf.imag).max() < 1e-15 and np.abs(mf - md).max() < 1e-15
+    r = oracle.solve(s)
+    assert np.abs(r["chi"].imag).max() < 1e-15 and np.abs(r["epsinv"].imag).max() < 1e-15
+    x = r["chi"].real
+    assert np.array_equal(x, x.T) or np.abs(x - x.T).max() < 1e-16
+    # the same bands as complex arrays give the same chain
+    s.cv = s.cv.astype(np.complex128)
+    s.cc = s.cc.astype(np.complex128)
+    rc = oracle.solve(s)
+    assert np.abs(rc["epsinv"] - r["epsinv"]).max() < 1e-14
