@@ -70,6 +70,19 @@ enum {
  *  BGW_PREC_MIX_BF16 : as MIX_FP16 with BF16 splits.                      */
 enum { BGW_PREC_FP64 = 0, BGW_PREC_MIX_FP16 = 1, BGW_PREC_MIX_BF16 = 2 };
 
+/* Real flavor (Section "Real and complex flavors"): with inversion and
+ * time-reversal symmetry the coefficients can be chosen real, and then M,
+ * chi, eps~ and eps~^-1 are real (M_vc(G) = sum c_v(G+G') c_c(G')).  OR this
+ * flag into the precision of bgw_mtxel, bgw_chi_sum and bgw_epsilon: the
+ * coefficients are double [nb][npw], M is double (FP64) or float (mixed)
+ * [nv*nc][ng], chi, eps~ and eps~^-1 are double [..][ng][ng] (symmetric,
+ * both triangles).  chi is a real SYRK (a quarter of the complex flops; the
+ * mixed precisions split hi/lo into two planes and take 3 MMAs per K step
+ * instead of 12); the inverse runs on the complex embedding of the real
+ * matrix (its imaginary parts stay exactly zero).  EUNSUPPORTED with the
+ * real-axis entry points (complex chi) and bgw_epsilon_batch.             */
+enum { BGW_FLAVOR_REAL = 0x100 };
+
 typedef struct bgw_ctx bgw_ctx;
 
 /* Coulomb interaction v(k), k = (q + G) B in bohr^-1, Hartree units
@@ -255,6 +268,25 @@ int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
 int bgw_screened_w(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
                    const int32_t* const* geps, const void* const* epsinv,
                    void* const* W, void* stream);
+
+/* bgw_epsinv_rflavor -- bgw_epsinv for the real flavor: chi[i], eps[i] (or
+ * NULL) and epsinv[i] are real double [ng[i]][ng[i]], symmetric.            */
+int bgw_epsinv_rflavor(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
+                       const int32_t* const* geps, const void* const* chi,
+                       void* const* eps, void* const* epsinv, void* stream);
+
+/* bgw_real_coefficients -- real-flavor coefficients from complex ones (host
+ * arrays), as the paper prescribes: bands whose energies (ascending) differ
+ * by at most tol from their neighbour form a degenerate subspace of n
+ * states; the 2n vectors Re c_1, Im c_1, Re c_2, ... are orthonormalized in
+ * that order by modified Gram-Schmidt (a remainder below 1e-8 of the
+ * vector's norm is dropped) and the first n kept, so a non-degenerate
+ * state loses its global phase.
+ *   c   host c128 [nb][npw];  energies host double [nb];  out host double
+ *       [nb][npw].
+ * ENUMERIC if a subspace gives fewer than n real directions (no inversion
+ * and time-reversal symmetry).  Host only, no context.                    */
+int bgw_real_coefficients(int nb, int npw, const void* c, const double* energies, double tol, double* out);
 
 /* ------------------------------------------------------------------------
  * bgw_epsinv_noalloc -- bgw_epsinv for one matrix without any device

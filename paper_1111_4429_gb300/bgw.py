@@ -27,11 +27,13 @@ EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_s
            "bgw_mtxel",
            "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_screened_w",
            "bgw_chi_sum_real", "bgw_epsinv_general", "bgw_epsilon_real", "bgw_frequency_grid",
+           "bgw_epsinv_rflavor", "bgw_real_coefficients",
            "bgw_epsilon",
            "bgw_epsilon_batch", "bgw_serve_open", "bgw_serve_submit", "bgw_serve_poll", "bgw_serve_cancel",
            "bgw_serve_close")
 BGW_OPT_CHI_SEGMENT_PAIRS, BGW_OPT_TIMING, BGW_OPT_AUTOTUNE, BGW_OPT_CHI_CHUNK_PAIRS, BGW_OPT_INVERSE = 1, 2, 3, 4, 5
 BGW_OPT_HEAD = 6
+BGW_FLAVOR_REAL = 0x100
 BGW_COULOMB_BULK, BGW_COULOMB_SPHERE, BGW_COULOMB_SLAB = 0, 1, 2
 COULOMB_MODELS = {"bulk": BGW_COULOMB_BULK, "sphere": BGW_COULOMB_SPHERE, "slab": BGW_COULOMB_SLAB}
 
@@ -133,6 +135,8 @@ def load() -> ctypes.CDLL:
     lib.bgw_epsilon_real.argtypes = [vp, cellp, ci, ci, i32p, vp, dp, ci, ci, i32p, vp, dp, ci, i32p, ci, dp, cd,
                                      ci, ci, ci, vp, vp, vp]
     lib.bgw_frequency_grid.argtypes = [cd, cd, cd, cd, ci, dp, ctypes.POINTER(ci)]
+    lib.bgw_epsinv_rflavor.argtypes = lib.bgw_epsinv.argtypes
+    lib.bgw_real_coefficients.argtypes = [ci, ci, vp, dp, cd, dp]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_char_p if name == "bgw_last_error" else ctypes.c_int
     _lib = lib
@@ -176,6 +180,19 @@ def epsinv_noalloc(cell: Cell, geps, chi, eps, epsinv, stream=None) -> None:
                                 _stream(stream))
     if rc != BGW_OK:
         raise BgwError(rc, "bgw_epsinv_noalloc failed")
+
+
+def real_coefficients(c: np.ndarray, energies, tol: float) -> np.ndarray:
+    """bgw_real_coefficients: real-flavor coefficients (host only)."""
+    lib = load()
+    cz = np.ascontiguousarray(c, dtype=np.complex128)
+    e = np.ascontiguousarray(energies, dtype=np.float64)
+    out = np.zeros(cz.shape, dtype=np.float64)
+    rc = lib.bgw_real_coefficients(cz.shape[0], cz.shape[1], cz.ctypes.data, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   ctypes.c_double(tol), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != BGW_OK:
+        raise BgwError(rc, "bgw_real_coefficients failed")
+    return out
 
 
 def frequency_grid(spacing: float, low_cutoff: float, high_cutoff: float, increment: float) -> np.ndarray:
@@ -310,6 +327,18 @@ class Context:
                                               e_.shape[0], ep, ctypes.c_double(delta), int(advanced), prec, nc_chunk,
                                               _ptr(chi), _ptr(epsinv), _stream(stream)))
         return epsinv
+
+    def epsinv_rflavor(self, cells: Sequence[Cell], gepss: Sequence[np.ndarray], chis, eps, epsinvs, stream=None):
+        n = len(cells)
+        carr = (Cell * n)(*cells)
+        keep = [_i32(g) for g in gepss]
+        ng = (ctypes.c_int * n)(*[k[0].shape[0] for k in keep])
+        gp = (ctypes.POINTER(ctypes.c_int32) * n)(*[k[1] for k in keep])
+        cp = (ctypes.c_void_p * n)(*[_ptr(x) for x in chis])
+        ep = None if eps is None else (ctypes.c_void_p * n)(*[_ptr(x) for x in eps])
+        ip = (ctypes.c_void_p * n)(*[_ptr(x) for x in epsinvs])
+        self._check(self.lib.bgw_epsinv_rflavor(self.h, n, carr, ng, gp, cp, ep, ip, _stream(stream)))
+        return epsinvs
 
     def screened_w(self, cells: Sequence[Cell], gepss: Sequence[np.ndarray], epsinvs, ws, stream=None):
         n = len(cells)

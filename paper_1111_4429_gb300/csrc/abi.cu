@@ -2,6 +2,8 @@
 // lookup, scratch management and the order of the kernel launches.
 #include <cstddef>
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -98,6 +100,13 @@ int check_prec(Ctx* c, int prec) {
   if (prec != BGW_PREC_FP64 && prec != BGW_PREC_MIX_FP16 && prec != BGW_PREC_MIX_BF16)
     return fail(c, BGW_EINVAL, "unknown precision %d", prec);
   return BGW_OK;
+}
+
+// Splits a precision argument into the precision and the real-flavor flag.
+int split_flavor(Ctx* c, int* prec, bool* real) {
+  *real = (*prec & BGW_FLAVOR_REAL) != 0;
+  *prec &= ~BGW_FLAVOR_REAL;
+  return check_prec(c, *prec);
 }
 
 int check_q(Ctx* c, const bgw_cell* cell, int ng, const int32_t* geps) {
@@ -307,6 +316,8 @@ int bgw_mtxel(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32
   Ctx* c = impl(ctx);
   if (!c) return BGW_EINVAL;
   int n, rc;
+  bool real;
+  if ((rc = split_flavor(c, &prec, &real)) != BGW_OK) return rc;
   if ((rc = validate_mtxel(c, cell, nv, npw_v, gv, cv, nc, npw_c, gc, cc, ng, geps, prec, M, &n)) != BGW_OK)
     return rc;
   DeviceGuard g(c->device);
@@ -317,7 +328,7 @@ int bgw_mtxel(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int32
   if ((rc = get_band_plan(c, n, npw_v, gv, st, &bpv)) != BGW_OK) return rc;
   if ((rc = get_band_plan(c, n, npw_c, gc, st, &bpc)) != BGW_OK) return rc;
   if ((rc = get_pair_plan(c, n, ng, geps, st, &pp)) != BGW_OK) return rc;
-  return mtxel_run(c, n, prec, nv, bpv, cv, nc, bpc, cc, pp, M, st);
+  return mtxel_run(c, n, prec, nv, bpv, cv, nc, bpc, cc, pp, M, st, real);
 }
 
 int bgw_chi_sum(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng, const void* M, const double* ev,
@@ -326,8 +337,9 @@ int bgw_chi_sum(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng, cons
   Ctx* c = impl(ctx);
   if (!c) return BGW_EINVAL;
   int rc;
+  bool real;
   if (!cell || !(cell->omega > 0.0)) return fail(c, BGW_EINVAL, "cell is NULL or has no volume");
-  if ((rc = check_prec(c, prec)) != BGW_OK) return rc;
+  if ((rc = split_flavor(c, &prec, &real)) != BGW_OK) return rc;
   if (nv <= 0 || nc <= 0 || ng <= 0) return fail(c, BGW_EINVAL, "nv, nc, ng must be >= 1");
   if (!M || !chi) return fail(c, BGW_EINVAL, "M or chi is NULL");
   if (nfreq < 0 || (nfreq > 0 && !omega)) return fail(c, BGW_EINVAL, "bad frequency list");
@@ -342,7 +354,8 @@ int bgw_chi_sum(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng, cons
   if ((rc = upload_cached(c, ec, nc * sizeof(double), st, &dev_ec)) != BGW_OK) return rc;
   if (nfreq > 0 && (rc = upload_cached(c, omega, nfreq * sizeof(double), st, &dev_om)) != BGW_OK) return rc;
   return chi_run(c, prec, nv, nc, ng, M, static_cast<const double*>(dev_ev), static_cast<const double*>(dev_ec),
-                 nfreq, static_cast<const double*>(dev_om), 4.0 / cell->omega, accumulate, chi, st);
+                 nfreq, static_cast<const double*>(dev_om), 4.0 / cell->omega, accumulate, chi, st, nullptr, nullptr,
+                 real);
 }
 
 int bgw_chi_sum_real(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng, const void* M, const double* ev,
@@ -352,6 +365,8 @@ int bgw_chi_sum_real(bgw_ctx* ctx, const bgw_cell* cell, int nv, int nc, int ng,
   if (!c) return BGW_EINVAL;
   int rc;
   if (!cell || !(cell->omega > 0.0)) return fail(c, BGW_EINVAL, "cell is NULL or has no volume");
+  if (prec & BGW_FLAVOR_REAL)
+    return fail(c, BGW_EUNSUPPORTED, "the real-axis response has complex chi: no real flavor");
   if ((rc = check_prec(c, prec)) != BGW_OK) return rc;
   if (nv <= 0 || nc <= 0 || ng <= 0) return fail(c, BGW_EINVAL, "nv, nc, ng must be >= 1");
   if (!M || !chi) return fail(c, BGW_EINVAL, "M or chi is NULL");
@@ -395,6 +410,31 @@ int bgw_epsinv_general(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int*
     cp[m] = &cells[m];
   }
   return epsinv_general_run(c, nmat, ng, cp.data(), dgeps.data(), chi, eps, epsinv, st, c->inverse_mode == 1);
+}
+
+int bgw_epsinv_rflavor(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, const int32_t* const* geps,
+                       const void* const* chi, void* const* eps, void* const* epsinv, void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  if (nmat <= 0 || !cells || !ng || !geps || !chi || !epsinv) return fail(c, BGW_EINVAL, "NULL argument array");
+  int rc;
+  for (int m = 0; m < nmat; ++m) {
+    if (ng[m] <= 0 || !geps[m] || !chi[m] || !epsinv[m])
+      return fail(c, BGW_EINVAL, "matrix %d: bad size or NULL pointer", m);
+    if ((rc = check_q(c, &cells[m], ng[m], geps[m])) != BGW_OK) return rc;
+  }
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<const int32_t*> dgeps(nmat);
+  std::vector<const bgw_cell*> cp(nmat);
+  for (int m = 0; m < nmat; ++m) {
+    const void* dg;
+    if ((rc = upload_cached(c, geps[m], (size_t)ng[m] * 3 * sizeof(int32_t), st, &dg)) != BGW_OK) return rc;
+    dgeps[m] = static_cast<const int32_t*>(dg);
+    cp[m] = &cells[m];
+  }
+  return epsinv_rflavor_run(c, nmat, ng, cp.data(), dgeps.data(), chi, eps, epsinv, st, c->inverse_mode == 1);
 }
 
 int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, const int32_t* const* geps,
@@ -525,6 +565,7 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   Ctx* c = impl(ctx);
   if (!c) return BGW_EINVAL;
   if (nq <= 0 || !problems || !epsinv) return fail(c, BGW_EINVAL, "bad batch arguments");
+  if (prec & BGW_FLAVOR_REAL) return fail(c, BGW_EUNSUPPORTED, "bgw_epsilon_batch: complex flavor only");
   if (nfreq < 0 || (nfreq > 0 && !omega)) return fail(c, BGW_EINVAL, "bad frequency list");
   for (int f = 0; f < nfreq; ++f)
     if (!isfinite(omega[f])) return fail(c, BGW_EINVAL, "omega[%d] is not finite", f);
@@ -633,6 +674,9 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
   Ctx* c = impl(ctx);
   if (!c) return BGW_EINVAL;
   int n, rc;
+  bool rf;   // real flavor
+  if ((rc = split_flavor(c, &prec, &rf)) != BGW_OK) return rc;
+  if (rf && fa.real) return fail(c, BGW_EUNSUPPORTED, "the real-axis response has complex chi: no real flavor");
   if ((rc = validate_mtxel(c, cell, nv, npw_v, gv, cv, nc, npw_c, gc, cc, ng, geps, prec, epsinv, &n)) != BGW_OK)
     return rc;
   if ((rc = check_energies(c, nv, ev, nc, ec)) != BGW_OK) return rc;
@@ -651,8 +695,10 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
   if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int nrow = nfreq > 0 ? nfreq : 1;
-  const size_t cs = prec == BGW_PREC_FP64 ? 16 : 8;
-  const size_t n2 = (size_t)ng * ng * sizeof(double2);
+  // element sizes: coefficients, M, chi and eps~^-1 are real in the real flavor
+  const size_t coef = rf ? 8 : 16;
+  const size_t cs = (prec == BGW_PREC_FP64 ? 16 : 8) / (rf ? 2 : 1);
+  const size_t n2 = (size_t)ng * ng * (rf ? sizeof(double) : sizeof(double2));
   const bool cv_dev = is_device_ptr(cv), cc_dev = is_device_ptr(cc);
   const bool chi_dev = chi && is_device_ptr(chi), inv_dev = is_device_ptr(epsinv);
   Scratch s_cv, s_cc, s_M, s_chi, s_inv;
@@ -660,13 +706,13 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
   const void* d_cv = cv;
   const void* d_cc = cc;
   if (!cv_dev) {
-    if ((rc = c->pool.alloc((size_t)nv * npw_v * 16, &s_cv.ptr)) != BGW_OK) return fail(c, rc, "cv staging");
-    BGW_CUDA(c, cudaMemcpyAsync(s_cv.ptr, cv, (size_t)nv * npw_v * 16, cudaMemcpyHostToDevice, st));
+    if ((rc = c->pool.alloc((size_t)nv * npw_v * coef, &s_cv.ptr)) != BGW_OK) return fail(c, rc, "cv staging");
+    BGW_CUDA(c, cudaMemcpyAsync(s_cv.ptr, cv, (size_t)nv * npw_v * coef, cudaMemcpyHostToDevice, st));
     d_cv = s_cv.ptr;
   }
   if (!cc_dev) {
-    if ((rc = c->pool.alloc((size_t)nc * npw_c * 16, &s_cc.ptr)) != BGW_OK) return fail(c, rc, "cc staging");
-    BGW_CUDA(c, cudaMemcpyAsync(s_cc.ptr, cc, (size_t)nc * npw_c * 16, cudaMemcpyHostToDevice, st));
+    if ((rc = c->pool.alloc((size_t)nc * npw_c * coef, &s_cc.ptr)) != BGW_OK) return fail(c, rc, "cc staging");
+    BGW_CUDA(c, cudaMemcpyAsync(s_cc.ptr, cc, (size_t)nc * npw_c * coef, cudaMemcpyHostToDevice, st));
     d_cc = s_cc.ptr;
   }
   void* d_chi = chi_dev ? chi : nullptr;
@@ -693,13 +739,13 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
   HeadPlan hp;
   Scratch s_h;
   s_h.pool = &c->pool;
-  if (!fa.real && (rc = head_prepare(c, cell, npw_v, gv, npw_c, gc, ng, geps, prec, st, &hp)) != BGW_OK) return rc;
+  if (!fa.real && !rf && (rc = head_prepare(c, cell, npw_v, gv, npw_c, gc, ng, geps, prec, st, &hp)) != BGW_OK) return rc;
   if (hp.g0 >= 0 && (rc = c->pool.alloc((size_t)nv * nc_chunk * sizeof(double2), &s_h.ptr)) != BGW_OK)
     return fail(c, rc, "head scratch");
   for (int c0 = 0; c0 < nc; c0 += nc_chunk) {
     const int ncc = std::min(nc_chunk, nc - c0);
-    const void* cc0 = static_cast<const char*>(d_cc) + (size_t)c0 * npw_c * 16;
-    if ((rc = mtxel_run(c, n, prec, nv, bpv, d_cv, ncc, bpc, cc0, pp, s_M.ptr, st)) != BGW_OK) return rc;
+    const void* cc0 = static_cast<const char*>(d_cc) + (size_t)c0 * npw_c * coef;
+    if ((rc = mtxel_run(c, n, prec, nv, bpv, d_cv, ncc, bpc, cc0, pp, s_M.ptr, st, rf)) != BGW_OK) return rc;
     if (hp.g0 >= 0 &&
         (rc = head_dot(c, &hp, nv, d_cv, npw_v, ncc, cc0, ng, s_M.ptr, s_h.as<double2>(), st)) != BGW_OK)
       return rc;
@@ -710,7 +756,7 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
     else
       rc = chi_run(c, prec, nv, ncc, ng, s_M.ptr, static_cast<const double*>(dev_ev),
                    static_cast<const double*>(dev_ec) + c0, nfreq, static_cast<const double*>(dev_om),
-                   4.0 / cell->omega, c0 > 0, d_chi, st, &hp, s_h.as<double2>());
+                   4.0 / cell->omega, c0 > 0, d_chi, st, &hp, s_h.as<double2>(), rf);
     if (rc != BGW_OK) return rc;
   }
   {
@@ -725,6 +771,9 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
     }
     if (fa.real)
       rc = epsinv_general_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
+                              use_tc_inverse(c, prec));
+    else if (rf)
+      rc = epsinv_rflavor_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
                               use_tc_inverse(c, prec));
     else
       rc = epsinv_batch_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
@@ -764,6 +813,45 @@ int bgw_epsilon_real(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, cons
   fa.advanced = advanced;
   return epsilon_run(ctx, cell, nv, npw_v, gv, cv, ev, nc, npw_c, gc, cc, ec, ng, geps, fa, prec, nc_chunk, chi,
                      epsinv, stream);
+}
+
+int bgw_real_coefficients(int nb, int npw, const void* c, const double* energies, double tol, double* out) {
+  if (nb <= 0 || npw <= 0 || !c || !energies || !out || !(tol >= 0.0)) return BGW_EINVAL;
+  const double* z = static_cast<const double*>(c);   // interleaved (re, im)
+  std::vector<double> v(npw);
+  std::vector<std::vector<double>> basis;
+  for (int start = 0; start < nb;) {
+    int stop = start + 1;
+    while (stop < nb && std::fabs(energies[stop] - energies[stop - 1]) <= tol) ++stop;
+    const int n = stop - start;
+    basis.clear();
+    for (int b = start; b < stop && (int)basis.size() < n; ++b) {
+      for (int part = 0; part < 2 && (int)basis.size() < n; ++part) {
+        double norm0 = 0.0;
+        for (int k = 0; k < npw; ++k) {
+          v[k] = z[2 * ((size_t)b * npw + k) + part];
+          norm0 += v[k] * v[k];
+        }
+        for (const auto& q : basis) {   // modified Gram-Schmidt
+          double d = 0.0;
+          for (int k = 0; k < npw; ++k) d += q[k] * v[k];
+          for (int k = 0; k < npw; ++k) v[k] -= d * q[k];
+        }
+        double nr = 0.0;
+        for (int k = 0; k < npw; ++k) nr += v[k] * v[k];
+        nr = std::sqrt(nr);
+        if (nr > 1e-8 * std::max(std::sqrt(norm0), 1e-300)) {
+          for (int k = 0; k < npw; ++k) v[k] /= nr;
+          basis.push_back(v);
+        }
+      }
+    }
+    if ((int)basis.size() < n) return BGW_ENUMERIC;
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < npw; ++k) out[(size_t)(start + i) * npw + k] = basis[i][k];
+    start = stop;
+  }
+  return BGW_OK;
 }
 
 int bgw_frequency_grid(double spacing, double low_cutoff, double high_cutoff, double increment, int max_points,

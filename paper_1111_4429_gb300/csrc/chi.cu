@@ -118,12 +118,78 @@ __global__ void __launch_bounds__(256) chi_f64_kernel(const double2* __restrict_
   }
 }
 
+// Real flavor, FP64: chi[G][G'] (+)= scale sum_p w_p M[p][G] M[p][G'] with real
+// M (a real SYRK: a quarter of the complex flops), lower 64x64 tiles,
+// mirrored; 4x4 register blocking as the complex kernel.
+__global__ void __launch_bounds__(256) chi_f64_real_kernel(const double* __restrict__ M, long long K, int ng,
+                                                           const double* __restrict__ w, double scale,
+                                                           int accumulate, double* __restrict__ chi) {
+  __shared__ double As[KB][TB];
+  __shared__ double Bs[KB][TB];
+  const long long t = blockIdx.x;
+  int I = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((long long)(I + 1) * (I + 2) / 2 <= t) ++I;
+  while ((long long)I * (I + 1) / 2 > t) --I;
+  const int J = (int)(t - (long long)I * (I + 1) / 2);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int row0 = I * TB, col0 = J * TB;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (long long k0 = 0; k0 < K; k0 += KB) {
+#pragma unroll
+    for (int q = 0; q < (KB * TB) / 256; ++q) {
+      const int e = tid + 256 * q;
+      const int kk = e / TB, r = e % TB;
+      const long long k = k0 + kk;
+      double a = 0.0, b = 0.0;
+      if (k < K) {
+        if (row0 + r < ng) a = M[k * ng + row0 + r];
+        if (col0 + r < ng) b = M[k * ng + col0 + r] * w[k];
+      }
+      As[kk][r] = a;
+      Bs[kk][r] = b;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KB; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int g = row0 + ty + 16 * i;
+    if (g >= ng) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gp = col0 + tx + 16 * j;
+      if (gp >= ng || gp > g) continue;
+      double v = acc[i][j] * scale;
+      double* lo = chi + (size_t)g * ng + gp;
+      if (accumulate) v += *lo;
+      *lo = v;
+      if (g != gp) chi[(size_t)gp * ng + g] = v;
+    }
+  }
+}
+
 int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double* w, int nrow,
-                  double scale, int accumulate, void* chi, cudaStream_t st);
+                  double scale, int accumulate, void* chi, cudaStream_t st, bool real);
 
 int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const double* d_ev,
             const double* d_ec, int nfreq, const double* d_omega, double scale, int accumulate,
-            void* chi, cudaStream_t st, const HeadPlan* hp, const double2* h) {
+            void* chi, cudaStream_t st, const HeadPlan* hp, const double2* h, bool real) {
   const long long K = (long long)nv * nc;
   const int nrow = nfreq > 0 ? nfreq : 1;
   Scratch w;
@@ -136,13 +202,24 @@ int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const doubl
   BGW_CUDA(c, cudaGetLastError());
   c->launches += 1;
   if (prec != BGW_PREC_FP64) {
-    if ((rc = chi_mixed_run(c, prec, K, ng, M, w.as<double>(), nrow, scale, accumulate, chi, st)) != BGW_OK)
+    if ((rc = chi_mixed_run(c, prec, K, ng, M, w.as<double>(), nrow, scale, accumulate, chi, st, real)) != BGW_OK)
       return rc;
     if (hp && hp->g0 >= 0) return head_wings(c, hp, K, ng, M, h, w.as<double>(), nrow, scale, chi, st);
     return BGW_OK;
   }
   const int nt = (ng + TB - 1) / TB;
   const long long ntiles = (long long)nt * (nt + 1) / 2;
+  if (real) {
+    for (int f = 0; f < nrow; ++f) {
+      TimedScope ts(c, kTChiF64, st);
+      chi_f64_real_kernel<<<(unsigned)ntiles, 256, 0, st>>>(static_cast<const double*>(M), K, ng,
+                                                             w.as<double>() + (size_t)f * K, scale, accumulate,
+                                                             static_cast<double*>(chi) + (size_t)f * ng * ng);
+      BGW_CUDA(c, cudaGetLastError());
+      c->launches += 1;
+    }
+    return BGW_OK;
+  }
   for (int f = 0; f < nrow; ++f) {
     TimedScope ts(c, kTChiF64, st);
     chi_f64_kernel<<<(unsigned)ntiles, 256, 0, st>>>(static_cast<const double2*>(M), K, ng,

@@ -132,11 +132,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-template <int BN>
+template <int BN, int NP = 4>
 struct Layout {
   static constexpr int kATile = BM * BK * 2;    // bytes of one A-side plane tile
   static constexpr int kBTile = BN * BK * 2;    // bytes of one B-side plane tile
-  static constexpr int kStage = 4 * kATile + 4 * kBTile;
+  static constexpr int kStage = NP * kATile + NP * kBTile;   // NP planes per operand (4 complex, 2 real)
   // Four FP32 accumulators of BN columns: Re and Im of the hi*hi products
   // (the large values) and of the hi*lo + lo*hi corrections.  Keeping the
   // corrections apart cuts the adds into the large accumulators threefold;
@@ -149,11 +149,11 @@ struct Layout {
 // reads planes 0..3; the B operand (columns G') reads the planes starting at
 // row brow of the tensor map: 0 for the Hermitian product (X = Y), 4 ngpad
 // when a second operand Y follows X (real-axis chi).
-template <int BN, int STAGES>
+template <int BN, int STAGES, int NP = 4>
 __global__ void __launch_bounds__(kThreads, 1)
     chi_tc_kernel(const __grid_constant__ CUtensorMap tmap, int ngpad, int brow, int nkb, int kb_per_seg, int ntiles,
                   const int2* __restrict__ tiles, int bf16, float* __restrict__ work, int* __restrict__ status) {
-  using L = Layout<BN>;
+  using L = Layout<BN, NP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage);
@@ -204,9 +204,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_expect_tx(&full[s], L::kStage);
       const int kx = (kb0 + i) * BK;
 #pragma unroll
-      for (int pl = 0; pl < 4; ++pl) {
+      for (int pl = 0; pl < NP; ++pl) {
         tma_load_2d(st + pl * L::kATile, &tmap, &full[s], kx, pl * ngpad + row0);
-        tma_load_2d(st + 4 * L::kATile + pl * L::kBTile, &tmap, &full[s], kx, brow + pl * ngpad + col0);
+        tma_load_2d(st + NP * L::kATile + pl * L::kBTile, &tmap, &full[s], kx, brow + pl * ngpad + col0);
       }
       issued = i + 1;
     }
@@ -234,12 +234,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int ks = 0; ks < BK / 16; ++ks) {
         const uint32_t off = ks * 32;  // 16 values x 2 B along K
+        const uint32_t first = (i > 0 || ks > 0) ? 1u : 0u;
+        if constexpr (NP == 2) {
+          // real flavor: planes (x_hi, x_lo); x x' = hi hi' + (hi lo' + lo hi')
+          const uint64_t ah = sdesc(base + off), al = sdesc(base + L::kATile + off);
+          const uint64_t bh = sdesc(base + 2 * L::kATile + off), bl = sdesc(base + 2 * L::kATile + L::kBTile + off);
+          mma(t_re, ah, bh, id, first);
+          mma(t_rec, ah, bl, id, first);
+          mma(t_rec, al, bh, id, 1);
+          continue;
+        }
         const uint64_t arh = sdesc(base + 0 * L::kATile + off), aih = sdesc(base + 1 * L::kATile + off);
         const uint64_t arl = sdesc(base + 2 * L::kATile + off), ail = sdesc(base + 3 * L::kATile + off);
         const uint32_t bb = base + 4 * L::kATile;
         const uint64_t brh = sdesc(bb + 0 * L::kBTile + off), bih = sdesc(bb + 1 * L::kBTile + off);
         const uint64_t brl = sdesc(bb + 2 * L::kBTile + off), bil = sdesc(bb + 3 * L::kBTile + off);
-        const uint32_t first = (i > 0 || ks > 0) ? 1u : 0u;
         // Re += xr xr' + xi xi': hi*hi into t_re, hi*lo + lo*hi into t_rec
         mma(t_re, arh, brh, id, first);
         mma(t_re, aih, bih, id, 1);
@@ -279,9 +288,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t a[16], b[16], ac[16], bc[16];
       tmem_ld16(t_re + lane_off + c0, a);
-      tmem_ld16(t_im + lane_off + c0, b);
       tmem_ld16(t_rec + lane_off + c0, ac);
-      tmem_ld16(t_imc + lane_off + c0, bc);
+      if constexpr (NP == 2) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) b[q] = bc[q] = 0u;   // real flavor: no imaginary part
+      } else {
+        tmem_ld16(t_im + lane_off + c0, b);
+        tmem_ld16(t_imc + lane_off + c0, bc);
+      }
       tmem_ld_wait();
       float4* pr = reinterpret_cast<float4*>(wre + (size_t)row * BN + c0);
       float4* pi = reinterpret_cast<float4*>(wim + (size_t)row * BN + c0);
@@ -380,6 +394,81 @@ __global__ void split_kernel(const float2* __restrict__ M, const double* __restr
     planes[2 * plane + o] = rl;
     planes[3 * plane + o] = il;
   }
+}
+
+// Real flavor: X[p][G] = M[p][G] sqrt|w_p| 2^e with real M, two planes
+// (hi, lo) per operand, chi real symmetric.
+__global__ void maxabs_real_kernel(const float* __restrict__ M, const double* __restrict__ w, long long K, int ng,
+                                   unsigned int* __restrict__ out) {
+  float m = 0.f;
+  const long long n = K * ng;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(M[e]) * sqrtf(fabsf((float)w[e / ng])));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+template <typename H>
+__global__ void split_real_kernel(const float* __restrict__ M, const double* __restrict__ w, long long p0,
+                                  long long K, int ng, int ngpad, int kpad, const unsigned int* __restrict__ maxbits,
+                                  int bf16, H* __restrict__ planes) {
+  __shared__ float t[32][33];
+  const long long pc0 = (long long)blockIdx.x * 32;
+  const int g0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const float sc = ldexpf(1.f, scale_exp(maxbits, bf16));
+  for (int r = ty; r < 32; r += 8) {
+    const long long p = pc0 + r;
+    const int g = g0 + tx;
+    float v = 0.f;
+    if (p < K && g < ng) v = M[(p0 + p) * ng + g] * (sqrtf(fabsf((float)w[p0 + p])) * sc);
+    t[r][tx] = v;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)ngpad * kpad;
+  for (int r = ty; r < 32; r += 8) {
+    const size_t o = (size_t)(g0 + r) * kpad + pc0 + tx;
+    const float v = t[tx][r];
+    H h, l;
+    if constexpr (std::is_same<H, __half>::value) {
+      h = __float2half_rn(v);
+      l = __float2half_rn(v - __half2float(h));
+    } else {
+      h = __float2bfloat16_rn(v);
+      l = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+    planes[o] = h;
+    planes[plane + o] = l;
+  }
+}
+
+// chi[g][g'] (+)= factor 2^{-2e} sum_seg W_re, lower triangle, mirrored (real symmetric).
+template <int BN>
+__global__ void reduce_real_kernel(const float* __restrict__ work, int nseg, int ntiles,
+                                   const int2* __restrict__ tiles, int ng, double factor,
+                                   const unsigned int* __restrict__ maxbits, int bf16, int accumulate,
+                                   double* __restrict__ chi) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)BM * BN;
+  if (e >= per * ntiles) return;
+  const int tix = (int)(e / per);
+  const int r = (int)((e - (long long)tix * per) / BN), c = (int)(e % BN);
+  const int2 tl = tiles[tix];
+  const int g = tl.x * BM + r, gp = tl.y * BN + c;
+  if (g >= ng || gp >= ng || gp > g) return;
+  float re = 0.f, rel = 0.f;
+  for (int s = 0; s < nseg; ++s) {
+    const float a = work[((size_t)s * ntiles + tix) * 2 * per + r * BN + c];
+    const float t = __fadd_rn(re, a);
+    const float z = __fsub_rn(t, re);
+    rel = __fadd_rn(rel, __fadd_rn(__fsub_rn(re, __fsub_rn(t, z)), __fsub_rn(a, z)));
+    re = t;
+  }
+  double v = ((double)re + (double)rel) * (factor * ldexp(1.0, -2 * scale_exp(maxbits, bf16)));
+  double* lo = chi + (size_t)g * ng + gp;
+  if (accumulate) v += *lo;
+  *lo = v;
+  if (g != gp) chi[(size_t)gp * ng + g] = v;
 }
 
 // Real-axis operands: X = M 2^eX and Y = (w_p M) 2^eY with complex w_p.
@@ -578,7 +667,7 @@ namespace {
 // lower tiles, mirrored) and the general one (wc: complex weights, X = M,
 // Y = w M, all tiles).
 int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const double* wr, const double2* wc, int nrow,
-               double scale, int accumulate, void* chi, cudaStream_t st) {
+               double scale, int accumulate, void* chi, cudaStream_t st, bool real = false) {
   using namespace tc;
   const bool general = wc != nullptr;
   int rc;
@@ -586,7 +675,7 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
   const int bf16 = prec == BGW_PREC_MIX_BF16;
   const int ntr = (ng + BM - 1) / BM, ntc = (ng + kBN - 1) / kBN;
   const int ngpad = std::max(ntr * BM, ntc * kBN);
-  const int nplanes = general ? 8 : 4;
+  const int nplanes = general ? 8 : (real ? 2 : 4);
   const int seg_pairs_opt = c->chi_segment_pairs > 0 ? c->chi_segment_pairs : kSegPairsDefault;
   const int kb_per_seg = std::max(1, seg_pairs_opt / BK);
   const long long seg_pairs = (long long)kb_per_seg * BK;
@@ -626,9 +715,13 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return fail(c, BGW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
-  const size_t smem = (size_t)kStages * Layout<kBN>::kStage + 1024 + 256;
-  BGW_CUDA(c, cudaFuncSetAttribute(chi_tc_kernel<kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+  const size_t smem = (size_t)kStages * (real ? Layout<kBN, 2>::kStage : Layout<kBN>::kStage) + 1024 + 256;
+  if (real)
+    BGW_CUDA(c, cudaFuncSetAttribute(chi_tc_kernel<kBN, kStages, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  else
+    BGW_CUDA(c, cudaFuncSetAttribute(chi_tc_kernel<kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
   const int brow = general ? 4 * ngpad : 0;
   for (int f = 0; f < nrow; ++f) {
     const double* wf = general ? nullptr : wr + (size_t)f * K;
@@ -640,6 +733,8 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
       const unsigned mb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8);
       if (general)
         maxabs_general_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wcf, K, ng, mx.as<unsigned int>());
+      else if (real)
+        maxabs_real_kernel<<<mb, 256, 0, st>>>(static_cast<const float*>(M), wf, K, ng, mx.as<unsigned int>());
       else
         maxabs_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wf, K, ng, mx.as<unsigned int>());
       c->launches += 1;
@@ -656,7 +751,14 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
         // shorter last chunk fills the first kpad of each row, and the GEMM
         // reads no further than nkb = kpad / BK k-blocks
         const unsigned int* mb = mx.as<unsigned int>();
-        if (general && bf16)
+        if (real && bf16)
+          split_real_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float*>(M), wf, p0, kc, ng,
+                                                                       ngpad, (int)kcpad, mb, 1,
+                                                                       planes.as<__nv_bfloat16>());
+        else if (real)
+          split_real_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float*>(M), wf, p0, kc, ng, ngpad,
+                                                                (int)kcpad, mb, 0, planes.as<__half>());
+        else if (general && bf16)
           split_general_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(
               static_cast<const float2*>(M), wcf, p0, kc, ng, ngpad, (int)kcpad, mb, 1, planes.as<__nv_bfloat16>());
         else if (general)
@@ -672,16 +774,25 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
       }
       {
         TimedScope ts(c, kTChiTc, st);
-        chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
-            tmap, ngpad, brow, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
-            c->d_status);
+        if (real)
+          chi_tc_kernel<kBN, kStages, 2><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
+              tmap, ngpad, brow, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
+              c->d_status);
+        else
+          chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
+              tmap, ngpad, brow, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
+              c->d_status);
       }
       {
         TimedScope ts(c, kTChiReduce, st);
         const long long ne = (long long)ntiles * BM * kBN;
         double2* cf = static_cast<double2*>(chi) + (size_t)f * ng * ng;
         const int acc = (accumulate || p0 > 0) ? 1 : 0;
-        if (general)
+        if (real)
+          reduce_real_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+              work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(),
+              bf16, acc, static_cast<double*>(chi) + (size_t)f * ng * ng);
+        else if (general)
           reduce_general_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
               work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, scale, mx.as<unsigned int>(),
               bf16, acc, cf);
@@ -700,8 +811,8 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
 }  // namespace
 
 int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double* w, int nrow, double scale,
-                  int accumulate, void* chi, cudaStream_t st) {
-  return chi_tc_run(c, prec, K, ng, M, w, nullptr, nrow, scale, accumulate, chi, st);
+                  int accumulate, void* chi, cudaStream_t st, bool real) {
+  return chi_tc_run(c, prec, K, ng, M, w, nullptr, nrow, scale, accumulate, chi, st, real);
 }
 
 int chi_real_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double2* w, int nrow,

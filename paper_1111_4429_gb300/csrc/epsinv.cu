@@ -631,6 +631,55 @@ int gj_update_run(Ctx* c, double2* A, int ng, int k0, int kb, const double2* R, 
   return BGW_OK;
 }
 
+__global__ void real_to_complex_kernel(const double* __restrict__ x, size_t n, double2* __restrict__ out) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = make_double2(x[e], 0.0);
+}
+__global__ void real_part_kernel(const double2* __restrict__ x, size_t n, double* __restrict__ out) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = x[e].x;
+}
+
+int epsinv_rflavor_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
+                       const void* const* chi, void* const* eps, void* const* epsinv, cudaStream_t st,
+                       bool tc_update) {
+  size_t total = 0;
+  for (int m = 0; m < nmat; ++m) total += (size_t)ng[m] * ng[m];
+  Scratch A, E;
+  A.pool = E.pool = &c->pool;
+  int rc;
+  if ((rc = c->pool.alloc(total * sizeof(double2), &A.ptr)) != BGW_OK ||
+      (eps && (rc = c->pool.alloc(total * sizeof(double2), &E.ptr)) != BGW_OK))
+    return fail(c, rc, "real-flavor inverse: scratch allocation failed");
+  std::vector<const void*> xin(nmat);
+  std::vector<void*> ain(nmat), ein(nmat);
+  size_t off = 0;
+  for (int m = 0; m < nmat; ++m) {
+    const size_t n2 = (size_t)ng[m] * ng[m];
+    double2* a = A.as<double2>() + off;
+    const unsigned gb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
+    real_to_complex_kernel<<<gb, 256, 0, st>>>(static_cast<const double*>(chi[m]), n2, a);
+    xin[m] = a;
+    ain[m] = a;   // eps~ is formed in place: every element is read before it is written
+    ein[m] = eps ? static_cast<void*>(E.as<double2>() + off) : nullptr;
+    off += n2;
+  }
+  BGW_CUDA(c, cudaGetLastError());
+  c->launches += nmat;
+  if ((rc = epsinv_batch_run(c, nmat, ng, cells, d_geps, xin.data(), eps ? ein.data() : nullptr, ain.data(), st,
+                             tc_update)) != BGW_OK)
+    return rc;
+  for (int m = 0; m < nmat; ++m) {
+    const size_t n2 = (size_t)ng[m] * ng[m];
+    const unsigned gb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
+    real_part_kernel<<<gb, 256, 0, st>>>(static_cast<const double2*>(ain[m]), n2, static_cast<double*>(epsinv[m]));
+    if (eps) real_part_kernel<<<gb, 256, 0, st>>>(static_cast<const double2*>(ein[m]), n2, static_cast<double*>(eps[m]));
+  }
+  BGW_CUDA(c, cudaGetLastError());
+  c->launches += nmat * (eps ? 2 : 1);
+  return BGW_OK;
+}
+
 int screened_w_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
                    const void* const* epsinv, void* const* W, cudaStream_t st) {
   int ngmax = 0;

@@ -125,7 +125,7 @@ int get_pair_plan(Ctx* c, int n, int ng, const int32_t* geps, cudaStream_t st, c
 static const size_t kPairScratchBytes = size_t(4) << 30;
 
 int mtxel_run(Ctx* c, int n, int prec, int nv, const BandPlan* bpv, const void* cv, int nc,
-              const BandPlan* bpc, const void* cc, const PairPlan* pp, void* M, cudaStream_t st) {
+              const BandPlan* bpc, const void* cc, const PairPlan* pp, void* M, cudaStream_t st, bool real) {
   const size_t cs = prec == BGW_PREC_FP64 ? 16 : 8;
   const size_t n3 = (size_t)n * n * n;
   const long long npairs = (long long)nv * nc;
@@ -151,8 +151,9 @@ int mtxel_run(Ctx* c, int n, int prec, int nv, const BandPlan* bpv, const void* 
   x.bpv = bpv;
   x.bpc = bpc;
   x.pp = pp;
-  x.cv = static_cast<const double2*>(cv);
-  x.cc = static_cast<const double2*>(cc);
+  x.cv = cv;
+  x.cc = cc;
+  x.real = real ? 1 : 0;
   x.uv = uv.ptr;
   x.uc = uc.ptr;
   x.U1 = U1.ptr;

@@ -28,7 +28,7 @@ template <typename T> __device__ __forceinline__ cpx<T> load_c128(const double2*
 // ---------------------------------------------------------------- band z
 // grid (ceil(ncol/64), nb), block 64.  smem S[64][N+1].
 template <typename T, int N>
-__global__ void __launch_bounds__(64) band_zpass(const double2* __restrict__ coef, int npw,
+__global__ void __launch_bounds__(64) band_zpass(const void* __restrict__ coef, int real_coef, int npw,
                                                  int ncol, const int* __restrict__ col_start,
                                                  const int* __restrict__ ent_col,
                                                  const int* __restrict__ ent_z,
@@ -44,10 +44,12 @@ __global__ void __launch_bounds__(64) band_zpass(const double2* __restrict__ coe
   __syncthreads();
   const int e0 = col_start[col0];
   const int e1 = col_start[min(col0 + CB, ncol)];
-  const double2* cb = coef + (size_t)b * npw;
-  for (int e = e0 + tid; e < e1; e += CB) {
-    int lc = ent_col[e] - col0;
-    S[lc * LD + ent_z[e]] = load_c128<T>(cb + ent_idx[e]);
+  if (real_coef) {   // real flavor: real coefficients, imaginary part zero
+    const double* cb = static_cast<const double*>(coef) + (size_t)b * npw;
+    for (int e = e0 + tid; e < e1; e += CB) S[(ent_col[e] - col0) * LD + ent_z[e]] = mk<T>(T(cb[ent_idx[e]]), T(0));
+  } else {
+    const double2* cb = static_cast<const double2*>(coef) + (size_t)b * npw;
+    for (int e = e0 + tid; e < e1; e += CB) S[(ent_col[e] - col0) * LD + ent_z[e]] = load_c128<T>(cb + ent_idx[e]);
   }
   __syncthreads();
   const int col = col0 + tid;
@@ -174,7 +176,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(256) pair_zgather(const cpx<T>* __restrict__ Tbuf, int pbase,
                                                     int ncol, int ng,
                                                     const int* __restrict__ zmap,
-                                                    cpx<T>* __restrict__ M) {
+                                                    void* __restrict__ M, int real_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* Mrow = reinterpret_cast<cpx<T>*>(smem_raw);
   const int pl = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -192,8 +194,13 @@ __global__ void __launch_bounds__(256) pair_zgather(const cpx<T>* __restrict__ T
     }
   }
   __syncthreads();
-  cpx<T>* dst = M + (size_t)(pbase + pl) * ng;
-  for (int i = tid; i < ng; i += nt) dst[i] = Mrow[i];
+  if (real_out) {   // real flavor: M is real (its imaginary part vanishes up to rounding)
+    T* dst = static_cast<T*>(M) + (size_t)(pbase + pl) * ng;
+    for (int i = tid; i < ng; i += nt) dst[i] = Mrow[i].x;
+  } else {
+    cpx<T>* dst = static_cast<cpx<T>*>(M) + (size_t)(pbase + pl) * ng;
+    for (int i = tid; i < ng; i += nt) dst[i] = Mrow[i];
+  }
 }
 
 // ------------------------------------------------------------ launchers
@@ -261,14 +268,14 @@ static int tune_pairs_per_block(const MtxelExec& x, const cpx<T>* uv, const cpx<
 }
 
 template <typename T, int N>
-static cudaError_t band_transform(const BandPlan* bp, const double2* coef, int nb, cpx<T>* U1,
+static cudaError_t band_transform(const BandPlan* bp, const void* coef, int real_coef, int nb, cpx<T>* U1,
                                   cpx<T>* u, cudaStream_t st) {
   if (nb == 0) return cudaSuccess;
   size_t sm1 = (size_t)64 * (N + 1) * sizeof(cpx<T>);
   cudaError_t e = set_smem(band_zpass<T, N>, sm1);
   if (e != cudaSuccess) return e;
   band_zpass<T, N><<<dim3((bp->ncol + 63) / 64, nb), 64, sm1, st>>>(
-      coef, bp->npw, bp->ncol, bp->d_col_start, bp->d_ent_col, bp->d_ent_z, bp->d_ent_idx, U1);
+      coef, real_coef, bp->npw, bp->ncol, bp->d_col_start, bp->d_ent_col, bp->d_ent_z, bp->d_ent_idx, U1);
   size_t sm2 = (size_t)N * (N + 1) * sizeof(cpx<T>);
   if ((e = set_smem(band_yxpass<T, N>, sm2)) != cudaSuccess) return e;
   band_yxpass<T, N><<<dim3(N, nb), 64, sm2, st>>>(U1, bp->ncol, bp->d_col_xy, bp->nxs, bp->d_xslot, u);
@@ -282,12 +289,12 @@ static cudaError_t mtxel_exec_n(const MtxelExec& x) {
   C* uc = reinterpret_cast<C*>(x.uc);
   C* U1 = reinterpret_cast<C*>(x.U1);
   C* Tb = reinterpret_cast<C*>(x.T);
-  C* M = reinterpret_cast<C*>(x.M);
+  void* M = x.M;
   cudaError_t e;
   {
     TimedScope ts(x.ctx, kTBand, x.st);
-    if ((e = band_transform<T, N>(x.bpv, x.cv, x.nv, U1, uv, x.st)) != cudaSuccess) return e;
-    if ((e = band_transform<T, N>(x.bpc, x.cc, x.nc, U1, uc, x.st)) != cudaSuccess) return e;
+    if ((e = band_transform<T, N>(x.bpv, x.cv, x.real, x.nv, U1, uv, x.st)) != cudaSuccess) return e;
+    if ((e = band_transform<T, N>(x.bpc, x.cc, x.real, x.nc, U1, uc, x.st)) != cudaSuccess) return e;
   }
   *x.launches += 4;
   const PairPlan* pp = x.pp;
@@ -312,7 +319,7 @@ static cudaError_t mtxel_exec_n(const MtxelExec& x) {
     }
     {
       TimedScope ts(x.ctx, kTPairZ, x.st);
-      pair_zgather<T, N><<<npb, 256, smz, x.st>>>(Tb, (int)p0, pp->ncol, pp->ng, pp->d_zmap, M);
+      pair_zgather<T, N><<<npb, 256, smz, x.st>>>(Tb, (int)p0, pp->ncol, pp->ng, pp->d_zmap, M, x.real);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *x.launches += 2;

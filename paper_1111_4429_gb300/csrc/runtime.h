@@ -170,8 +170,9 @@ struct MtxelExec {
   const BandPlan* bpv = nullptr;
   const BandPlan* bpc = nullptr;
   const PairPlan* pp = nullptr;
-  const double2* cv = nullptr;
-  const double2* cc = nullptr;
+  const void* cv = nullptr;      // c128 [nb][npw], or double when real
+  const void* cc = nullptr;
+  int real = 0;                  // real flavor: real coefficients in, real M out
   void* uv = nullptr;   // [nv][n^3]
   void* uc = nullptr;   // [nc][n^3]
   void* U1 = nullptr;   // [max(nv,nc)][n][max ncol]
@@ -189,9 +190,11 @@ cudaError_t mtxel_init_f64();
 cudaError_t mtxel_init_f32();
 
 // Launchers (each enqueues on `st`; return BGW_OK or an error code).
+// real = true: the real flavor (real coefficients, real M of the precision's
+// scalar type).
 int mtxel_run(Ctx* c, int n, int prec, int nv, const BandPlan* bpv, const void* cv,
               int nc, const BandPlan* bpc, const void* cc, const PairPlan* pp,
-              void* M, cudaStream_t st);
+              void* M, cudaStream_t st, bool real = false);
 // FP64 head of the mixed precisions at a small q (head.cu).  g0 < 0: not used.
 struct HeadPlan {
   int g0 = -1;                   // index of G = 0 in the epsilon list
@@ -208,9 +211,11 @@ int head_wings(Ctx* c, const HeadPlan* hp, long long K, int ng, const void* M, c
                int nrow, double scale, void* chi, cudaStream_t st);
 // hp/h: when hp->g0 >= 0 the mixed precisions add the FP64 head and wings
 // (column g0 of M must have been zeroed by head_dot).
+// real = true: the real flavor (real M, real symmetric chi of doubles).
 int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const double* d_ev,
             const double* d_ec, int nfreq, const double* d_omega, double scale, int accumulate,
-            void* chi, cudaStream_t st, const HeadPlan* hp = nullptr, const double2* h = nullptr);
+            void* chi, cudaStream_t st, const HeadPlan* hp = nullptr, const double2* h = nullptr,
+            bool real = false);
 // eps~ and its inverse for nmat matrices (per-matrix size, cell and q).
 // tc_update: the sweep's trailing updates run on the tensor cores with
 // FP64-level accuracy (sweep_tc.cu) instead of FP64 FMA.
@@ -238,6 +243,12 @@ constexpr int kGeneralMaxNg = 14336;   // row of the column unscramble in shared
 int chi_real_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const double* d_ev, const double* d_ec,
                  int nfreq, const double* d_energy, double delta, int advanced, double scale, int accumulate,
                  void* chi, cudaStream_t st);
+// Real flavor: eps~ and its inverse of real symmetric chi (doubles in and
+// out) through the Hermitian sweep on the complex embedding, whose imaginary
+// parts stay exactly zero.
+int epsinv_rflavor_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
+                       const void* const* chi, void* const* eps, void* const* epsinv, cudaStream_t st,
+                       bool tc_update);
 // W = v^1/2 epsinv v^1/2 for nmat matrices (bgw_screened_w).
 int screened_w_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
                    const void* const* epsinv, void* const* W, cudaStream_t st);

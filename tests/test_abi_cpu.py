@@ -74,3 +74,22 @@ def test_frequency_grid_host_matches_oracle():
     for bad in [(0.0, 1.0, 2.0, 0.1), (0.1, 1.0, 0.5, 0.1), (0.1, 1.0, 2.0, -0.1)]:
         with pytest.raises(bgw.BgwError):
             bgw.frequency_grid(*bad)
+
+
+def test_real_coefficients_host_matches_oracle_subspaces():
+    from paper_1111_4429_gb300 import bgw, synth
+    import numpy as np
+    import oracle
+    gen = np.random.default_rng(4)
+    q, _ = np.linalg.qr(gen.standard_normal((50, 8)))
+    real = q.T
+    e = np.array([-0.6, -0.2, -0.2, 0.0, 0.3, 0.3, 0.3, 0.9])
+    cplx = synth.scramble_phases(real, [[1, 2], [4, 5, 6]], seed=9)
+    got = bgw.real_coefficients(cplx, e, 1e-9)
+    ref = oracle.realify(cplx, e, 1e-9)
+    assert np.allclose(got @ got.T, np.eye(8), atol=1e-13)
+    for g in [[0], [1, 2], [3], [4, 5, 6], [7]]:
+        assert np.abs(got[g].T @ got[g] - ref[g].T @ ref[g]).max() < 1e-13
+    import pytest
+    with pytest.raises(bgw.BgwError):
+        bgw.real_coefficients(np.zeros((1, 50), complex), np.array([0.0]), 1e-9)
