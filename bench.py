@@ -297,6 +297,7 @@ def run_ours(args):
     batch = run_batch_c3(ctx, prec) if (ws == 1 and not args.skip_extra) else None
     f2 = run_f2(ctx, prec, flush) if (ws == 1 and not args.skip_extra) else None
     ra = run_real_axis(ctx, prec, flush) if (ws == 1 and not args.skip_extra) else None
+    rf = run_real_flavor(ctx, prec, flush) if (ws == 1 and not args.skip_extra) else None
     serve = run_serve_c4(prec) if (ws == 1 and not args.skip_extra) else None
 
     out = {
@@ -325,6 +326,7 @@ def run_ours(args):
         "serve_c4": serve,
         "w_and_q0": f2,
         "real_axis_c1": ra,
+        "real_flavor_c1": rf,
         "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(s.cv.nbytes + s.cc.nbytes),
                 "d2h_bytes_per_step": int(invh.numel() * 16)},
         "gpu_launches": int(launches),
@@ -478,6 +480,50 @@ def run_real_axis(ctx, prec, flush, steps=2, warmup=1):
             "ms_per_call": ms, "frequency_solves_per_s": nf * 1e3 / ms,
             "kernel_ms_per_call": {k: v[1] / steps for k, v in kt.items()},
             "epsinv_rel_err_vs_plain_fp64_gpu_at_1.4Ha": err}
+
+
+def run_real_flavor(ctx, prec, flush, steps=3, warmup=2):
+    """Real flavor on the c1 sizes: the same spheres, bands and energies with
+    real coefficients (inversion and time-reversal symmetry), one static solve
+    through bgw_epsilon on device buffers; the plain FP64 real-flavor solve of
+    the same input gives the error figure."""
+    import torch
+    from paper_1111_4429_gb300 import bgw, synth
+    st = torch.cuda.current_stream()
+    p = dict(synth.CONFIGS["c1"])
+    s = synth.make_system("c1_real", **p, real=True)
+    cell = bgw.system_cell(s)
+    cv = torch.from_numpy(s.cv).cuda()
+    cc = torch.from_numpy(s.cc).cuda()
+    out = torch.empty((1, s.ng, s.ng), dtype=torch.float64, device="cuda")
+    flav = prec | bgw.BGW_FLAVOR_REAL
+
+    def run(pr, n, nw):
+        for _ in range(nw):
+            ctx.epsilon(cell, s.gv, cv, s.ev, s.gc, cc, s.ec, s.geps, None, pr, 0, None, out)
+        ctx.sync()
+        ctx.set_option(bgw.BGW_OPT_TIMING, 1)
+        ctx.timing_report(reset=True)
+        tt = []
+        for k in range(n):
+            flush.fill_(k & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            ctx.epsilon(cell, s.gv, cv, s.ev, s.gc, cc, s.ec, s.geps, None, pr, 0, None, out)
+            b.record(st)
+            b.synchronize()
+            tt.append(a.elapsed_time(b))
+        kt = ctx.timing_report(reset=True)
+        ctx.set_option(bgw.BGW_OPT_TIMING, 0)
+        ctx.sync()
+        return float(np.mean(tt)), {k: v[1] / n for k, v in kt.items()}, out[0].clone()
+
+    ms, kt, inv = run(flav, steps, warmup)
+    _, _, ref = run(bgw.BGW_PREC_FP64 | bgw.BGW_FLAVOR_REAL, 1, 1)
+    err = float(torch.linalg.matrix_norm(inv - ref) / torch.linalg.matrix_norm(ref))
+    return {"workload": "c1 sizes with real coefficients (N_v 32, N_c 800, N_G 2120), static",
+            "solves_per_s": 1e3 / ms, "ms": ms, "kernel_ms_per_solve": kt,
+            "epsinv_rel_err_vs_plain_fp64_real_flavor_gpu": err}
 
 
 def run_batch_c3(ctx, prec, steps=2):

@@ -475,7 +475,7 @@ __global__ void sw_finish_kernel(const __grid_constant__ SweepBatch b) {
 // eps~ formation for every matrix of the batch, then the batched sweep.
 int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells,
                      const int32_t* const* d_geps, const void* const* chi, void* const* eps, void* const* epsinv,
-                     cudaStream_t st, bool tc_update) {
+                     cudaStream_t st, bool tc_update, bool real_values) {
   const int group = tc_update ? 96 : kSweepBatch;
   for (int m0 = 0; m0 < nmat; m0 += group) {
     const int nb = std::min(group, nmat - m0);
@@ -536,7 +536,8 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cel
         Ps[k] = sb.m[k].P;
         Ds[k] = sb.m[k].Dinv;
       }
-      if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), Ds.data(), oz.get())) != BGW_OK)
+      if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), Ds.data(), oz.get(), false,
+                           real_values)) != BGW_OK)
         return rc;
     }
     if (!tc_update) {
@@ -667,7 +668,7 @@ int epsinv_rflavor_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
   BGW_CUDA(c, cudaGetLastError());
   c->launches += nmat;
   if ((rc = epsinv_batch_run(c, nmat, ng, cells, d_geps, xin.data(), eps ? ein.data() : nullptr, ain.data(), st,
-                             tc_update)) != BGW_OK)
+                             tc_update, true)) != BGW_OK)
     return rc;
   for (int m = 0; m < nmat; ++m) {
     const size_t n2 = (size_t)ng[m] * ng[m];

@@ -221,7 +221,7 @@ int chi_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const doubl
 // FP64-level accuracy (sweep_tc.cu) instead of FP64 FMA.
 int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells,
                      const int32_t* const* d_geps, const void* const* chi, void* const* eps, void* const* epsinv,
-                     cudaStream_t st, bool tc_update);
+                     cudaStream_t st, bool tc_update, bool real_values = false);
 // eps~ = I - sv chi sv of one matrix into A (and eps when non-NULL), sv from
 // the cell's Coulomb model (epsinv.cu).
 int eps_form_run(Ctx* c, const bgw_cell* cell, const int32_t* d_geps, int ng, const void* chi, double* sv,
@@ -264,8 +264,11 @@ void oz_plan_delete(OzPlan* p);
 // general = false: the Hermitian sweep's update (C, P: [ng][32] panels, D
 // the next diagonal inverse).  general = true: the pivoted Gauss-Jordan
 // update A -= P R with P the column panel [ng][32] and C = R [32][ng].
+// real_values: every matrix is real (the real flavor's embedding), so only
+// the real-part products are formed.
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               double2* const* D, OzPlan* plan, bool general = false);
+               double2* const* D, OzPlan* plan, bool general = false, bool real_values = false);
+// epsinv_batch_run with real_values: the matrices are real (imaginary parts zero).
 int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);
 int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaStream_t st);
 

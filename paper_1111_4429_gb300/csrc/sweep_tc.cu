@@ -252,6 +252,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // mode 3: the general Gauss-Jordan update of the pivoted inverse, every
 // tile of the matrix: A_ij = (j in K ? 0 : A_ij) - (Cp R)_ij for rows
 // outside K (slices from slice_general_kernel).
+template <bool realv>
 __global__ void __launch_bounds__(kThreads, 1)
     update_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
                   const __grid_constant__ OzBatch b, int k0, int rows_total, int buf, int mode,
@@ -350,6 +351,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int L = a + bb;
           const uint32_t dre = tmem + L * 2 * BN, dim = dre + BN;
           const uint32_t ua = ub + a * kUTile, vb2 = vb + bb * kVTile;
+          if constexpr (realv) {
+            // real values (imaginary slices zero): Re = u[0:32] . v[0:32], no Im
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+              mma(dre, sdesc(ua + 32 * k), sdesc(vb2 + 32 * k), id, (first[L] && k == 0) ? 0u : 1u);
+            first[L] = false;
+            continue;
+          }
           // Re: u . v over the 64 real components (4 steps of 16)
 #pragma unroll
           for (int k = 0; k < 4; ++k) mma(dre, sdesc(ua + 32 * k), sdesc(vb2 + 32 * k), id, (first[L] && k == 0) ? 0u : 1u);
@@ -400,9 +409,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int L = 0; L < S; ++L) {
         tmem_ld4(tmem + lane_off + L * 2 * BN + c0, x[L]);
-        tmem_ld4(tmem + lane_off + L * 2 * BN + BN + c0, y[L]);
+        if constexpr (!realv) tmem_ld4(tmem + lane_off + L * 2 * BN + BN + c0, y[L]);
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if constexpr (realv) {
+#pragma unroll
+        for (int L = 0; L < S; ++L)
+#pragma unroll
+          for (int q = 0; q < kChunk; ++q) y[L][q] = 0u;
+      }
 #pragma unroll
       for (int q = 0; q < kChunk; ++q) {
         float hr = __uint_as_float(x[0][q]), lr = 0.f, hm = __uint_as_float(y[0][q]), lm = 0.f;
@@ -426,7 +441,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const double2 v = av[q];
         double2 o;
         const int e2 = ex[q];
-        if (e2 > -100 && e2 < 100) {
+        if (realv && e2 > -100 && e2 < 100) {
+          o.x = (v.x - f2d(ldexpf(hr, e2))) - f2d(ldexpf(lr, e2));
+          o.y = v.y;   // real values: the imaginary part stays zero
+        } else if (!realv && e2 > -100 && e2 < 100) {
           o.x = (v.x - f2d(ldexpf(hr, e2))) - f2d(ldexpf(lr, e2));
           o.y = (v.y - f2d(ldexpf(hm, e2))) - f2d(ldexpf(lm, e2));
         } else {
@@ -478,6 +496,7 @@ EncodeTiledFn g_encode_oz = nullptr;
 // State of one batched sweep that uses the tensor-core update.
 struct OzPlan {
   bool general = false;   // Gauss-Jordan update (mode 3) of the pivoted inverse
+  bool real_values = false;  // every matrix real (real flavor): only the real-part MMAs
   int nmat = 0;
   int rows_total = 0;
   int max_tiles = 0;
@@ -487,7 +506,7 @@ struct OzPlan {
 };
 
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               double2* const* D, OzPlan* plan, bool general) {
+               double2* const* D, OzPlan* plan, bool general, bool real_values) {
   using namespace oz;
   if (nmat > kBatch) return fail(c, BGW_EUNSUPPORTED, "tensor-core inverse: at most %d matrices per batch", kBatch);
   if (!g_encode_oz) {
@@ -500,6 +519,7 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
   }
   plan->nmat = nmat;
   plan->general = general;
+  plan->real_values = real_values;
   plan->batch.n = nmat;
   int rows = 0, tiles = 0;
   for (int m = 0; m < nmat; ++m) {
@@ -543,7 +563,8 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
     return fail(c, BGW_ECUDA, "tensor-core inverse: tensor map encoding failed");
   // about 142 KiB: leaves room on each SM for the look-ahead chain's kernels
   const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
-  BGW_CUDA(c, cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BGW_CUDA(c, cudaFuncSetAttribute(update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BGW_CUDA(c, cudaFuncSetAttribute(update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   return BGW_OK;
 }
 
@@ -577,9 +598,14 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
   }
   if (plan->general) mode = 3;
   const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
-  update_kernel<<<dim3(grid, plan->nmat), kThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,
-                                                                plan->rows_total, buf, mode, plan->sig.as<int>(),
-                                                                plan->tau.as<int>(), c->d_status);
+  if (plan->real_values)
+    update_kernel<true><<<dim3(grid, plan->nmat), kThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,
+                                                                      plan->rows_total, buf, mode, plan->sig.as<int>(),
+                                                                      plan->tau.as<int>(), c->d_status);
+  else
+    update_kernel<false><<<dim3(grid, plan->nmat), kThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,
+                                                                       plan->rows_total, buf, mode, plan->sig.as<int>(),
+                                                                       plan->tau.as<int>(), c->d_status);
   if (plan->general) {
     const long long ne = (long long)NB * ngmax;
     rows_from_r_kernel<<<dim3((unsigned)((ne + 255) / 256), plan->nmat), 256, 0, st>>>(plan->batch, k0);
