@@ -22,5 +22,5 @@ invariants and brute force live in ``tests/test_oracle_pins.py``.
 from .epsilon import (  # noqa: F401
     mtxel_direct, mtxel_fft, band_grids, chi_direct, chi, chi_weights, coulomb,
     eps_sym, eps_asym, inv_gauss_jordan, inv, screened_w, epsinv_sym, solve,
-    chi_entries, mtxel_fft_pairs, screened_w_sym, chi_weights_real, frequency_grid, solve_real, realify,
+    chi_entries, mtxel_fft_pairs, screened_w_sym, chi_weights_real, frequency_grid, solve_real, realify, sigma_mtxel, density_diag, sigma_cohsex,
 )

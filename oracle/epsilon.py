@@ -357,6 +357,59 @@ def epsinv_sym(chi_m: np.ndarray, v: np.ndarray, tier: int = 2):
     return e, (inv_gauss_jordan(e) if tier == 1 else inv(e))
 
 
+# ---------------------------------------------------------------------------
+# Static COHSEX and bare exchange, Eqs. (cohsex-sx), (cohsex-ch-sum),
+# (cohsex-ch-exact), (hf-x): diagonal elements for one q
+# ---------------------------------------------------------------------------
+
+def sigma_mtxel(g_inner, c_inner, g_outer, c_outer, geps) -> np.ndarray:
+    """M_{n''n}(k, -q, -G) = <n'' k-q| e^{-i(q+G).r} |n k> for G in geps, the
+    inner band n'' on the k-q sphere: sum_{G2} conj(c_n''(G2 - G)) c_n(G2).
+    Returns [n_inner * n_outer][ng], pair p = n'' * n_outer + n."""
+    return mtxel_direct(g_inner, c_inner, g_outer, c_outer, -np.asarray(geps))
+
+
+def density_diag(g_outer, c_outer, deltas) -> np.ndarray:
+    """rho_n(D) = M_nn(k, q = 0, D) = sum_{G2} conj(c_n(D + G2)) c_n(G2), [n][len(deltas)]."""
+    out = np.empty((c_outer.shape[0], len(deltas)), dtype=np.complex128)
+    for n in range(c_outer.shape[0]):
+        out[n] = mtxel_direct(g_outer, c_outer[n:n + 1], g_outer, c_outer[n:n + 1], deltas)[0]
+    return out
+
+
+def sigma_cohsex(g_inner, c_inner, nocc: int, g_outer, c_outer, geps, epsinv_sym_m, v, cell_volume: float):
+    """Diagonal <n|Sigma|n> for one q (Hartree), with W = eps^-1 v = V^1/2
+    eps~^-1 V^1/2 and the implicit 1/Omega of a q sum (one q point):
+      X       = -(1/Omega) sum_{n'' occ} sum_G |M(G)|^2 v(q+G)               (hf-x)
+      SX      = -(1/Omega) sum_{n'' occ} M^H W M                             (cohsex-sx)
+      CH      = (1/(2 Omega)) sum_{n'' all inner} M^H (W - V) M              (cohsex-ch-sum)
+      CH_exact = (1/(2 Omega)) sum_{G G'} rho_n(G - G') (W - V)_{G G'}       (cohsex-ch-exact)
+    with M = M_{n''n}(k, -q, -G) and rho_n(D) = <n| e^{i D.r} |n>.  Eq.
+    cohsex-ch-exact prints the argument as G' - G; the bra-ket it stands for,
+    <n| e^{i(G - G').r} |n'>, and the completeness relation applied to the
+    sum form both give G - G' in the convention of Eq. eqn_matrix_elem (the
+    pin on a complete inner basis checks it).  Returns dict of [n_outer]
+    arrays."""
+    no = c_outer.shape[0]
+    ni = c_inner.shape[0]
+    M = sigma_mtxel(g_inner, c_inner, g_outer, c_outer, geps).reshape(ni, no, -1)
+    s = np.sqrt(v)
+    W = s[:, None] * epsinv_sym_m * s[None, :]
+    WmV = W - np.diag(v)
+    qW = np.einsum("abg,gh,abh->ab", np.conj(M), W, M)
+    qV = np.einsum("abg,g,abg->ab", np.conj(M), v, M)
+    qWV = np.einsum("abg,gh,abh->ab", np.conj(M), WmV, M)
+    geps = np.asarray(geps, dtype=np.int64)
+    diffs = (geps[:, None, :] - geps[None, :, :]).reshape(-1, 3)       # [G][G'] -> G - G'
+    uniq, inv_idx = np.unique(diffs, axis=0, return_inverse=True)
+    rho = density_diag(g_outer, c_outer, uniq.astype(np.int32))[:, inv_idx.ravel()].reshape(no, len(geps), len(geps))
+    ch_exact = np.einsum("ngh,gh->n", rho, WmV) / (2.0 * cell_volume)
+    return dict(X=-qV[:nocc].sum(0).real / cell_volume,
+                SX=-qW[:nocc].sum(0) / cell_volume,
+                CH=qWV.sum(0) / (2.0 * cell_volume),
+                CH_exact=ch_exact)
+
+
 def solve_real(system, energies: Sequence[float], delta: float, advanced: bool = False,
                model: str = "bulk", rc: float = 0.0):
     """Real-axis chain for one q-point (Eq. retarded_advanced_epsilon in the

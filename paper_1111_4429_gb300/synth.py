@@ -216,6 +216,31 @@ def scramble_phases(c: np.ndarray, groups: Sequence[Sequence[int]], seed: int) -
     return np.ascontiguousarray(out)
 
 
+@dataclasses.dataclass
+class SigmaBands:
+    """Bands of a diagonal Sigma evaluation at one q: the outer bands n at k
+    (k = 0 sphere) and the inner bands n'' at k - q (sphere at -q), the first
+    nocc inner bands occupied."""
+    go: np.ndarray
+    co: np.ndarray
+    gi: np.ndarray
+    ci: np.ndarray
+    nocc: int
+
+
+def sigma_bands(system: System, n_outer: int, n_inner: int, nocc: int, seed: int) -> SigmaBands:
+    """Seeded orthonormal outer and inner bands on the spheres of a system's
+    cell and wavefunction cutoff (the cutoff read back from the system's
+    conduction sphere)."""
+    ecut = float(np.max(np.einsum("ij,ij->i", system.gc @ system.bvec, system.gc @ system.bvec))) + 1e-9
+    go = gsphere(system.bvec, (0.0, 0.0, 0.0), ecut)
+    gi = gsphere(system.bvec, -np.asarray(system.q_frac), ecut)
+    gen = np.random.Generator(np.random.PCG64(seed))
+    co = orthonormal_bands(gen, go.shape[0], n_outer)
+    ci = orthonormal_bands(gen, gi.shape[0], n_inner)
+    return SigmaBands(go=go, co=co, gi=gi, ci=ci, nocc=nocc)
+
+
 def batched_q_systems(nq: int = 8, seed: int = 1003) -> List[System]:
     """The c1 cell at q = (0.05 j, 0, 0), j = 1..nq: uneven epsilon spheres."""
     out = []

@@ -514,3 +514,62 @@ def test_real_flavor_chain_is_real_and_matches_complex_path():
     s.cc = s.cc.astype(np.complex128)
     rc = oracle.solve(s)
     assert np.abs(rc["epsinv"] - r["epsinv"]).max() < 1e-14
+
+
+# ------------------------------------------------------------------ static COHSEX / bare exchange
+
+def _sigma_case(seed=3):
+    s = synth.make_system("sg", a=8.0, fft=16, ecut_wfn=2.0, ecut_eps=1.0, nv=2, nc=4, seed=seed)
+    gen = np.random.default_rng(seed)
+    go = s.gc
+    co = synth.orthonormal_bands(gen, go.shape[0], 3)
+    return s, go, co
+
+
+def test_sigma_ch_sum_over_complete_inner_basis_equals_closed_form():
+    # Inner bands = every plane wave of a k-q sphere that holds all G2 - G
+    # (radius sqrt(E_wfn) + sqrt(E_eps)): completeness turns the sum form of
+    # Eq. cohsex-ch-sum into Eq. cohsex-ch-exact, whatever W is.
+    s, go, co = _sigma_case()
+    ecut_i = (math.sqrt(2.0) + math.sqrt(1.0)) ** 2 + 1e-9
+    gi = synth.gsphere(s.bvec, -np.asarray(s.q_frac), ecut_i)
+    ci = np.eye(gi.shape[0], dtype=np.complex128)
+    gen = np.random.default_rng(8)
+    z = gen.standard_normal((s.ng, s.ng)) + 1j * gen.standard_normal((s.ng, s.ng))
+    ei = np.eye(s.ng) + 0.1 * (z + np.conj(z).T)                 # any Hermitian eps~^-1
+    v = oracle.coulomb(s.bvec, s.q_frac, s.geps)
+    out = oracle.sigma_cohsex(gi, ci, 0, go, co, s.geps, ei, v, s.omega)
+    assert np.abs(out["CH"] - out["CH_exact"]).max() <= 1e-13 * np.abs(out["CH_exact"]).max()
+    # a truncated inner set does not reach the closed form
+    out2 = oracle.sigma_cohsex(gi, ci[:20], 0, go, co, s.geps, ei, v, s.omega)
+    assert np.abs(out2["CH"] - out2["CH_exact"]).max() > 1e-3 * np.abs(out2["CH_exact"]).max()
+
+
+def test_sigma_unscreened_limit_and_real_forms():
+    s, go, co = _sigma_case(seed=4)
+    sb = synth.sigma_bands(s, 3, 10, 4, seed=6)
+    v = oracle.coulomb(s.bvec, s.q_frac, s.geps)
+    # eps^-1 = 1: W = V, so SX is the bare exchange and CH vanishes
+    out = oracle.sigma_cohsex(sb.gi, sb.ci, sb.nocc, sb.go, sb.co, s.geps, np.eye(s.ng), v, s.omega)
+    assert np.allclose(out["SX"], out["X"], rtol=1e-13, atol=0)
+    assert np.abs(out["CH"]).max() < 1e-15 and np.abs(out["CH_exact"]).max() < 1e-15
+    assert np.all(out["X"] < 0)
+    # screened: quadratic forms of Hermitian matrices are real; screening
+    # weakens exchange (0 < eps~^-1 <= I gives |SX| <= |X|)
+    r = oracle.solve(s)
+    out = oracle.sigma_cohsex(sb.gi, sb.ci, sb.nocc, sb.go, sb.co, s.geps, r["epsinv"], r["v"], s.omega)
+    for k in ("SX", "CH", "CH_exact"):
+        assert np.abs(out[k].imag).max() <= 1e-14 * np.abs(out[k].real).max()
+    assert np.all(np.abs(out["SX"].real) <= np.abs(out["X"]) + 1e-15)
+    assert np.all(out["CH"].real <= 1e-15)                      # W - V <= 0
+
+
+def test_sigma_mtxel_fft_route_and_negated_g():
+    s, go, co = _sigma_case(seed=5)
+    sb = synth.sigma_bands(s, 2, 5, 2, seed=7)
+    md = oracle.sigma_mtxel(sb.gi, sb.ci, sb.go, sb.co, s.geps)
+    mf = oracle.mtxel_fft(sb.gi, sb.ci, sb.go, sb.co, -s.geps, s.fft)
+    assert np.abs(md - mf).max() < 1e-14
+    # M_{n''n}(-q, -G) = conj(M_{n n''}(+q, +G)) with the roles of the spheres swapped
+    mswap = oracle.mtxel_direct(sb.go, sb.co, sb.gi, sb.ci, s.geps).reshape(2, 5, -1)
+    assert np.abs(md.reshape(5, 2, -1) - np.conj(mswap.transpose(1, 0, 2))).max() < 1e-14
