@@ -275,6 +275,33 @@ int bgw_epsinv_rflavor(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int*
                        const int32_t* const* geps, const void* const* chi,
                        void* const* eps, void* const* epsinv, void* stream);
 
+/* ------------------------------------------------------------------------
+ * bgw_sigma_cohsex -- diagonal static COHSEX and bare-exchange self-energy
+ * for one q (Section "The Self-Energy": Eqs. cohsex-sx, cohsex-ch-sum,
+ * cohsex-ch-exact, hf-x), from this path's symmetrized eps~^-1 at that q:
+ *   m_{n''n}(G) = M_{n''n}(k, -q, -G) = sum_{G2} conj(c_n''(G2 - G)) c_n(G2)
+ *   W = eps^-1 v = V^1/2 eps~^-1 V^1/2   (the cell's Coulomb model)
+ *   sigma[0][n] X        = -(1/Omega) sum_{n'' < nocc} sum_G |m(G)|^2 v(q+G)
+ *   sigma[1][n] SX       = -(1/Omega) sum_{n'' < nocc} m^H W m
+ *   sigma[2][n] CH       = (1/(2 Omega)) sum_{n'' < ni} m^H (W - V) m
+ *   sigma[3][n] CH exact = (1/(2 Omega)) sum_{G G'} <n|e^{i(G-G').r}|n> (W - V)_{G G'}
+ * (1/Omega: one q point of a q sum; Hartree.  The closed form is the sum
+ * form over a complete set of inner bands.)
+ *   co  device c128 [no][npw_o], outer bands n at k on the G list go (host)
+ *   ci  device c128 [ni][npw_i], inner bands n'' at k - q on gi (host); the
+ *       first nocc are occupied
+ *   geps host int32 [ng][3], the eps sphere of q; epsinv device c128
+ *       [ng][ng] (bgw_epsinv of the same cell and list)
+ *   sigma host double [4][no]; the call returns after it is written.
+ * FP64.  EINVAL as bgw_mtxel for the lists and grid (n > max|Gi| + max|Go| +
+ * max|Geps| per axis, and -G inside [-n/2, n/2)), for non-device arrays or
+ * nocc outside [0, ni].                                                     */
+int bgw_sigma_cohsex(bgw_ctx* ctx, const bgw_cell* cell,
+                     int no, int npw_o, const int32_t* go, const void* co,
+                     int ni, int npw_i, const int32_t* gi, const void* ci,
+                     int nocc, int ng, const int32_t* geps, const void* epsinv,
+                     double* sigma, void* stream);
+
 /* bgw_real_coefficients -- real-flavor coefficients from complex ones (host
  * arrays), as the paper prescribes: bands whose energies (ascending) differ
  * by at most tol from their neighbour form a degenerate subspace of n

@@ -27,7 +27,7 @@ EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_s
            "bgw_mtxel",
            "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_screened_w",
            "bgw_chi_sum_real", "bgw_epsinv_general", "bgw_epsilon_real", "bgw_frequency_grid",
-           "bgw_epsinv_rflavor", "bgw_real_coefficients",
+           "bgw_epsinv_rflavor", "bgw_real_coefficients", "bgw_sigma_cohsex",
            "bgw_epsilon",
            "bgw_epsilon_batch", "bgw_serve_open", "bgw_serve_submit", "bgw_serve_poll", "bgw_serve_cancel",
            "bgw_serve_close")
@@ -137,6 +137,7 @@ def load() -> ctypes.CDLL:
     lib.bgw_frequency_grid.argtypes = [cd, cd, cd, cd, ci, dp, ctypes.POINTER(ci)]
     lib.bgw_epsinv_rflavor.argtypes = lib.bgw_epsinv.argtypes
     lib.bgw_real_coefficients.argtypes = [ci, ci, vp, dp, cd, dp]
+    lib.bgw_sigma_cohsex.argtypes = [vp, cellp, ci, ci, i32p, vp, ci, ci, i32p, vp, ci, ci, i32p, vp, dp, vp]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_char_p if name == "bgw_last_error" else ctypes.c_int
     _lib = lib
@@ -339,6 +340,18 @@ class Context:
         ip = (ctypes.c_void_p * n)(*[_ptr(x) for x in epsinvs])
         self._check(self.lib.bgw_epsinv_rflavor(self.h, n, carr, ng, gp, cp, ep, ip, _stream(stream)))
         return epsinvs
+
+    def sigma_cohsex(self, cell: Cell, go, co, gi, ci, nocc: int, geps, epsinv, stream=None) -> np.ndarray:
+        """bgw_sigma_cohsex: returns [4][no] (X, SX, CH sum form, CH closed form), Hartree."""
+        go_, gop = _i32(go)
+        gi_, gip = _i32(gi)
+        ge_, gep = _i32(geps)
+        out = np.zeros((4, co.shape[0]), dtype=np.float64)
+        self._check(self.lib.bgw_sigma_cohsex(self.h, ctypes.byref(cell), co.shape[0], go_.shape[0], gop, _ptr(co),
+                                              ci.shape[0], gi_.shape[0], gip, _ptr(ci), nocc, ge_.shape[0], gep,
+                                              _ptr(epsinv), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              _stream(stream)))
+        return out
 
     def screened_w(self, cells: Sequence[Cell], gepss: Sequence[np.ndarray], epsinvs, ws, stream=None):
         n = len(cells)

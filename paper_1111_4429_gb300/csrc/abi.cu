@@ -815,6 +815,47 @@ int bgw_epsilon_real(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, cons
                      epsinv, stream);
 }
 
+int bgw_sigma_cohsex(bgw_ctx* ctx, const bgw_cell* cell, int no, int npw_o, const int32_t* go, const void* co, int ni,
+                     int npw_i, const int32_t* gi, const void* ci, int nocc, int ng, const int32_t* geps,
+                     const void* epsinv, double* sigma, void* stream) {
+  Ctx* c = impl(ctx);
+  if (!c) return BGW_EINVAL;
+  int n, rc;
+  if ((rc = check_cell(c, cell, &n)) != BGW_OK) return rc;
+  if (no <= 0 || ni <= 0 || nocc < 0 || nocc > ni) return fail(c, BGW_EINVAL, "need no, ni >= 1 and 0 <= nocc <= ni");
+  if ((long long)no * ni > 0x7fffffffLL) return fail(c, BGW_EUNSUPPORTED, "no * ni exceeds 2^31 - 1");
+  if (!co || !ci || !epsinv || !sigma) return fail(c, BGW_EINVAL, "NULL coefficient, epsinv or output pointer");
+  if (!is_device_ptr(co) || !is_device_ptr(ci) || !is_device_ptr(epsinv))
+    return fail(c, BGW_EINVAL, "co, ci and epsinv must be device arrays");
+  if (ng > max_ng(BGW_PREC_FP64)) return fail(c, BGW_EUNSUPPORTED, "ng = %d exceeds %d", ng, max_ng(BGW_PREC_FP64));
+  int mo[3], mi[3], me[3];
+  if ((rc = check_glist(c, "go", npw_o, go, n, mo)) != BGW_OK) return rc;
+  if ((rc = check_glist(c, "gi", npw_i, gi, n, mi)) != BGW_OK) return rc;
+  if ((rc = check_glist(c, "geps", ng, geps, n, me)) != BGW_OK) return rc;
+  for (int d = 0; d < 3; ++d)
+    if (n <= mo[d] + mi[d] + me[d])
+      return fail(c, BGW_EINVAL, "FFT grid %d aliases on axis %d: need n > max|Gi| + max|Go| + max|Geps|", n, d);
+  if ((rc = check_q(c, cell, ng, geps)) != BGW_OK) return rc;
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<int32_t> neg((size_t)ng * 3);
+  for (size_t i = 0; i < neg.size(); ++i) neg[i] = -geps[i];
+  {   // -G must stay inside [-n/2, n/2) as well
+    int tmp[3];
+    if ((rc = check_glist(c, "-geps", ng, neg.data(), n, tmp)) != BGW_OK) return rc;
+  }
+  const BandPlan *bpo, *bpi;
+  const PairPlan* pp;
+  if ((rc = get_band_plan(c, n, npw_o, go, st, &bpo)) != BGW_OK) return rc;
+  if ((rc = get_band_plan(c, n, npw_i, gi, st, &bpi)) != BGW_OK) return rc;
+  if ((rc = get_pair_plan(c, n, ng, neg.data(), st, &pp)) != BGW_OK) return rc;
+  const void* dg;
+  if ((rc = upload_cached(c, geps, (size_t)ng * 3 * sizeof(int32_t), st, &dg)) != BGW_OK) return rc;
+  return sigma_run(c, cell, n, no, bpo, go, co, ni, bpi, ci, nocc, ng, geps, static_cast<const int32_t*>(dg), pp,
+                   epsinv, sigma, st);
+}
+
 int bgw_real_coefficients(int nb, int npw, const void* c, const double* energies, double tol, double* out) {
   if (nb <= 0 || npw <= 0 || !c || !energies || !out || !(tol >= 0.0)) return BGW_EINVAL;
   const double* z = static_cast<const double*>(c);   // interleaved (re, im)

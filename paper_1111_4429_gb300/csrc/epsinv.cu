@@ -681,6 +681,13 @@ int epsinv_rflavor_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
   return BGW_OK;
 }
 
+int coulomb_sqrt_run(Ctx* c, const bgw_cell* cell, const int32_t* d_geps, int ng, double* sv, cudaStream_t st) {
+  coulomb_sqrt_kernel<<<(ng + 255) / 256, 256, 0, st>>>(d_geps, ng, coulomb_args(cell), sv);
+  BGW_CUDA(c, cudaGetLastError());
+  c->launches += 1;
+  return BGW_OK;
+}
+
 int screened_w_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
                    const void* const* epsinv, void* const* W, cudaStream_t st) {
   int ngmax = 0;

@@ -249,6 +249,13 @@ int chi_real_run(Ctx* c, int prec, int nv, int nc, int ng, const void* M, const 
 int epsinv_rflavor_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
                        const void* const* chi, void* const* eps, void* const* epsinv, cudaStream_t st,
                        bool tc_update);
+// sv = v(q+G)^1/2 of the cell's Coulomb model.
+int coulomb_sqrt_run(Ctx* c, const bgw_cell* cell, const int32_t* d_geps, int ng, double* sv, cudaStream_t st);
+// Diagonal static COHSEX and bare exchange for one q (sigma.cu); pp_neg is the
+// pair plan of the negated epsilon list; sigma_host [4][no].
+int sigma_run(Ctx* c, const bgw_cell* cell, int n, int no, const BandPlan* bpo, const int32_t* go, const void* co,
+              int ni, const BandPlan* bpi, const void* ci, int nocc, int ng, const int32_t* geps_host,
+              const int32_t* d_geps, const PairPlan* pp_neg, const void* epsinv, double* sigma_host, cudaStream_t st);
 // W = v^1/2 epsinv v^1/2 for nmat matrices (bgw_screened_w).
 int screened_w_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
                    const void* const* epsinv, void* const* W, cudaStream_t st);
