@@ -298,6 +298,7 @@ def run_ours(args):
     f2 = run_f2(ctx, prec, flush) if (ws == 1 and not args.skip_extra) else None
     ra = run_real_axis(ctx, prec, flush) if (ws == 1 and not args.skip_extra) else None
     rf = run_real_flavor(ctx, prec, flush) if (ws == 1 and not args.skip_extra) else None
+    sg = run_sigma(ctx, prec, flush) if (ws == 1 and not args.skip_extra) else None
     serve = run_serve_c4(prec) if (ws == 1 and not args.skip_extra) else None
 
     out = {
@@ -327,6 +328,7 @@ def run_ours(args):
         "w_and_q0": f2,
         "real_axis_c1": ra,
         "real_flavor_c1": rf,
+        "sigma_cohsex_c1": sg,
         "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(s.cv.nbytes + s.cc.nbytes),
                 "d2h_bytes_per_step": int(invh.numel() * 16)},
         "gpu_launches": int(launches),
@@ -524,6 +526,43 @@ def run_real_flavor(ctx, prec, flush, steps=3, warmup=2):
     return {"workload": "c1 sizes with real coefficients (N_v 32, N_c 800, N_G 2120), static",
             "solves_per_s": 1e3 / ms, "ms": ms, "kernel_ms_per_solve": kt,
             "epsinv_rel_err_vs_plain_fp64_real_flavor_gpu": err}
+
+
+def run_sigma(ctx, prec, flush, steps=2, warmup=1):
+    """Diagonal static COHSEX / bare exchange (bgw_sigma_cohsex, FP64) on the
+    c1 cell: 8 outer bands at k, 832 inner bands at k - q (32 occupied), the
+    N_G = 2120 eps~^-1 of the c1 solve.  The quadratic forms are one FP64
+    GEMM of 8 K N_G^2 flops, K = 8 x 832 pairs."""
+    import torch
+    from paper_1111_4429_gb300 import bgw, synth
+    st = torch.cuda.current_stream()
+    s = synth.config_system("c1")
+    cell = bgw.system_cell(s)
+    inv = torch.empty((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
+    ctx.epsilon(cell, s.gv, torch.from_numpy(s.cv).cuda(), s.ev, s.gc, torch.from_numpy(s.cc).cuda(), s.ec, s.geps,
+                None, prec, 0, None, inv)
+    ctx.sync()
+    sb = synth.sigma_bands(s, 8, 832, 32, seed=2001)
+    co = torch.from_numpy(sb.co).cuda()
+    ci = torch.from_numpy(sb.ci).cuda()
+    for _ in range(warmup):
+        out = ctx.sigma_cohsex(cell, sb.go, co, sb.gi, ci, sb.nocc, s.geps, inv[0])
+    tt = []
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        out = ctx.sigma_cohsex(cell, sb.go, co, sb.gi, ci, sb.nocc, s.geps, inv[0])
+        b.record(st)
+        b.synchronize()
+        tt.append(a.elapsed_time(b))
+    ms = float(np.mean(tt))
+    K = 8 * 832
+    return {"workload": "c1 cell, 8 outer x 832 inner bands (32 occupied), N_G 2120, FP64",
+            "ms_per_call": ms, "quad_gemm_fp64_tflops_over_call": 8.0 * K * s.ng * s.ng / (ms / 1e3) / 1e12,
+            "sigma_ha": {"X": out[0].tolist(), "SX": out[1].tolist(), "CH": out[2].tolist(),
+                         "CH_exact": out[3].tolist()}}
 
 
 def run_batch_c3(ctx, prec, steps=2):
