@@ -34,8 +34,6 @@ constexpr int KR = 64;           // real inner length (32 complex)
 constexpr int BM = 128;          // tile rows (i)
 constexpr int BN = 32;           // tile cols (j)
 constexpr int NB = 32;           // sweep block width
-constexpr int kThreads = 512;          // 16 warps: four per tensor-memory lane quadrant in the epilogue
-constexpr int kChunk = 4;              // epilogue columns per tensor-memory load round
 constexpr int kUTile = BM * KR * 2;    // 16 KiB
 constexpr int kVTile = BN * KR * 2;    // 4 KiB
 constexpr unsigned long long kWaitNs = 1000000000ull;
@@ -94,11 +92,6 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(id), "r"(acc)
       : "memory");
-}
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -226,15 +219,15 @@ __global__ void rows_from_r_kernel(const __grid_constant__ OzBatch b, int k0) {
   M.A[(size_t)(k0 + r) * M.ng + j] = M.C[(size_t)r * M.ng + j];
 }
 
-// (double)f for a finite float, built from its bits with integer operations
-// (the FP64 pipe, which a conversion would occupy, is the scarce one here).
-__device__ __forceinline__ double f2d(float f) {
+// f 2^ex as a double, exactly, for a finite float f and |ex| < 900: the
+// exponent is added in the double's field (no FP32 scaling, no range issue).
+__device__ __forceinline__ double f2d_scaled(float f, int ex) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
   const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
   if (e == 0u && m == 0u) return __longlong_as_double((long long)sign);  // +-0
-  if (e == 0u || e == 0xFFu) return (double)f;                          // denormal, inf, nan
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+  if (e == 0u || e == 0xFFu) return ldexp((double)f, ex);                // denormal, inf, nan
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u + ex) << 52) |
                                           ((unsigned long long)m << 29)));
 }
 
@@ -244,72 +237,124 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// One CTA: the 128 x 32 tile (I, J) of the lower triangle of one matrix.
-// mode 0: every lower tile; 1: only the tiles touching the next block
-// (rows or columns k0 + NB .. k0 + 2 NB), which the next sweep step reads
-// first; 2: every other tile.  Modes 1 and 2 split one step's update so the
-// next step's diagonal block, panel and slices can proceed after mode 1.
-// mode 3: the general Gauss-Jordan update of the pivoted inverse, every
-// tile of the matrix: A_ij = (j in K ? 0 : A_ij) - (Cp R)_ij for rows
-// outside K (slices from slice_general_kernel).
+// ---------------------------------------------------------------------------
+// Persistent, pipelined form of the update.  A CTA takes work items of up to
+// kJPI column tiles of one row tile I: the row's U slices are loaded once per item, the V slices of
+// consecutive tiles are double-buffered, and one control thread (warp 16)
+// issues the TMA copies and the MMAs.  The 16 epilogue warps first read the
+// tile's 14 accumulators out of tensor memory and combine the levels in
+// double FP32 (registers), then release tensor memory -- the next tile's
+// MMAs start -- and apply the FP64 subtraction while they run.
+constexpr int kPipeEpiWarps = 16;
+constexpr int kPipeThreads = (kPipeEpiWarps + 1) * 32;
+constexpr int kJPI = 2;   // column tiles per work item
+
+__device__ __forceinline__ int row_width(int mode, int I, int nJ) { return mode == 3 ? nJ : min(4 * I + 4, nJ); }
+
+// Number of work items of a mode, and the decode of one.
+__host__ __device__ inline int pipe_items(int mode, int nI, int nJ, int In, bool has_next) {
+  int n = 0;
+  if (mode == 1) {
+    const int w = (4 * In + 4 < nJ) ? 4 * In + 4 : nJ;
+    return (w + kJPI - 1) / kJPI + (nI - In - 1 > 0 ? nI - In - 1 : 0);
+  }
+  for (int I = 0; I < nI; ++I) {
+    if (mode == 2 && has_next && I == In) continue;
+    const int w = mode == 3 ? nJ : ((4 * I + 4 < nJ) ? 4 * I + 4 : nJ);
+    n += (w + kJPI - 1) / kJPI;
+  }
+  return n;
+}
+__device__ inline void pipe_decode(int mode, int item, int nI, int nJ, int In, int Jn, bool has_next, int& I, int& J0,
+                                   int& J1) {
+  if (mode == 1) {
+    const int w = row_width(1, In, nJ);
+    const int nrow = (w + kJPI - 1) / kJPI;
+    if (item < nrow) {
+      I = In;
+      J0 = item * kJPI;
+      J1 = min(J0 + kJPI, w);
+    } else {
+      I = In + 1 + (item - nrow);
+      J0 = Jn;
+      J1 = Jn + 1;
+    }
+    return;
+  }
+  for (I = 0; I < nI; ++I) {
+    if (mode == 2 && has_next && I == In) continue;
+    const int w = row_width(mode, I, nJ);
+    const int n = (w + kJPI - 1) / kJPI;
+    if (item < n) {
+      J0 = item * kJPI;
+      J1 = min(J0 + kJPI, w);
+      return;
+    }
+    item -= n;
+  }
+  J0 = J1 = 0;
+}
+__device__ inline bool pipe_skip(int mode, int I, int J, int ng, int k0, int kb, int Jn, bool has_next) {
+  const int i0 = I * BM, j0 = J * BN;
+  if (j0 >= ng) return true;
+  if (mode == 2 && has_next && J == Jn) return true;
+  if (i0 >= k0 && min(i0 + BM, ng) <= k0 + kb) return true;
+  if (mode != 3 && j0 >= k0 && min(j0 + BN, ng) <= k0 + kb) return true;
+  return false;
+}
+
+// Bounded wait that also gives up when the CTA aborts.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+
 template <bool realv>
-__global__ void __launch_bounds__(kThreads, 1)
-    update_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
-                  const __grid_constant__ OzBatch b, int k0, int rows_total, int buf, int mode,
-                  const int* __restrict__ sig, const int* __restrict__ tau, int* __restrict__ status) {
+__global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per sub-partition, 96 registers
+    update_pipe_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
+                       const __grid_constant__ OzBatch b, int k0, int rows_total, int buf, int mode,
+                       const int* __restrict__ sig, const int* __restrict__ tau, int* __restrict__ status) {
   const OzMat& M = b.m[blockIdx.y];
   const int ng = M.ng;
   if (k0 >= ng) return;
   const int kb = min(NB, ng - k0);
   const int nI = (ng + BM - 1) / BM, nJ = (ng + BN - 1) / BN;
-  const int k1 = k0 + NB;                      // next block
+  const int k1 = k0 + NB;
   const bool has_next = k1 < ng;
   const int In = k1 / BM, Jn = k1 / BN;
-  int I = 0, J = 0;
-  if (mode == 1) {
-    if (!has_next) return;
-    const int crow = min(4 * In + 4, nJ);
-    const int t = blockIdx.x;
-    if (t < crow) {
-      I = In;
-      J = t;
-    } else {
-      I = In + 1 + (t - crow);
-      J = Jn;
-      if (I >= nI) return;
-    }
-  } else if (mode == 3) {
-    I = blockIdx.x / nJ;
-    J = blockIdx.x - I * nJ;
-    if (I >= nI) return;
-  } else {
-    // tile decode: row tile I holds column tiles J = 0 .. min(4I+3, nJ-1)
-    int t = blockIdx.x;
-    for (; I < nI; ++I) {
-      const int cI = min(4 * I + 4, nJ);
-      if (t < cI) break;
-      t -= cI;
-    }
-    if (I >= nI) return;
-    J = t;
-    if (mode == 2 && has_next && (I == In || J == Jn)) return;
-  }
-  const int i0 = I * BM, j0 = J * BN;
-  const int slice_base = buf * S * rows_total;  // first slice row of this step's buffer
-  if (i0 >= k0 && min(i0 + BM, ng) <= k0 + kb) return;
-  if (mode != 3 && j0 >= k0 && min(j0 + BN, ng) <= k0 + kb) return;
+  if (mode == 1 && !has_next) return;
+  const int nitems = pipe_items(mode, nI, nJ, In, has_next);
+  const int slice_base = buf * S * rows_total;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  unsigned char* us = smem;                  // S x 16 KiB
-  unsigned char* vs = smem + S * kUTile;     // S x 4 KiB
-  uint64_t* full = reinterpret_cast<uint64_t*>(vs + S * kVTile);
-  uint64_t* done = full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  unsigned char* us = smem;                          // S x 16 KiB
+  unsigned char* vs = smem + S * kUTile;             // 2 x S x 4 KiB
+  uint64_t* u_full = reinterpret_cast<uint64_t*>(vs + 2 * S * kVTile);
+  uint64_t* v_full = u_full + 1;                     // [2]
+  uint64_t* v_empty = v_full + 2;                    // [2]
+  uint64_t* t_full = v_empty + 2;
+  uint64_t* t_empty = t_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(t_empty + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  __shared__ DiagSmem dsm;
+
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool control = warp == kPipeEpiWarps;
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(full)) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(u_full)) : "memory");
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(v_full + q)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(v_empty + q)) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(t_full)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(t_empty)), "r"(kPipeEpiWarps) : "memory");
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -321,137 +366,212 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  bool ok = true;
-  if (warp == 0 && lane == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(full)),
-                 "r"((uint32_t)(S * (kUTile + kVTile)))
-                 : "memory");
-    for (int a = 0; a < S; ++a) {
-      tma_load_2d(us + a * kUTile, &umap, full, 0, slice_base + a * rows_total + M.row_off + i0);
-      tma_load_2d(vs + a * kVTile, &vmap, full, 0, slice_base + a * rows_total + M.row_off + j0);
-    }
-    // the copies must land before this CTA may exit, whatever happens next
-    const uint64_t t0 = globaltimer();
-    while (!mbar_try_wait(full, 0) && globaltimer() - t0 < kWaitNs) {
-    }
-  } else if (warp == 1 && lane == 0) {
-    if (!mbar_wait(full, 0)) {
-      ok = false;
-    } else {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ub = smem_u32(us), vb = smem_u32(vs);
-      const uint32_t id = idesc(false), idn = idesc(true);
-      bool first[S];
-#pragma unroll
-      for (int L = 0; L < S; ++L) first[L] = true;
-#pragma unroll 1
-      for (int a = 0; a < S; ++a) {
-#pragma unroll 1
-        for (int bb = 0; bb + a < S; ++bb) {
-          const int L = a + bb;
-          const uint32_t dre = tmem + L * 2 * BN, dim = dre + BN;
-          const uint32_t ua = ub + a * kUTile, vb2 = vb + bb * kVTile;
-          if constexpr (realv) {
-            // real values (imaginary slices zero): Re = u[0:32] . v[0:32], no Im
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-              mma(dre, sdesc(ua + 32 * k), sdesc(vb2 + 32 * k), id, (first[L] && k == 0) ? 0u : 1u);
-            first[L] = false;
-            continue;
+
+  int t = 0;           // tiles processed by this CTA (buffer and phase bookkeeping)
+  int items_done = 0;  // items processed
+  int u_loads = 0;     // U loads issued (control; phase of u_full)
+  int vissued = 0;     // V loads issued (control)
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++items_done) {
+    int I, J0, J1;
+    pipe_decode(mode, item, nI, nJ, In, Jn, has_next, I, J0, J1);
+    const int i0 = I * BM;
+    // tiles of the item that are not skipped, in order
+    int Js[kJPI], nt = 0;
+    for (int J = J0; J < J1; ++J)
+      if (!pipe_skip(mode, I, J, ng, k0, kb, Jn, has_next)) Js[nt++] = J;
+    if (control) {
+      if (lane == 0 && nt > 0 && !*abort_flag) {
+        // U slices of the row tile (the previous item's MMAs are complete:
+        // the item-end barrier follows its last epilogue)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(u_full)),
+                     "r"((uint32_t)(S * kUTile))
+                     : "memory");
+        for (int a = 0; a < S; ++a)
+          tma_load_2d(us + a * kUTile, &umap, u_full, 0, slice_base + a * rows_total + M.row_off + i0);
+        const int u_phase = u_loads & 1;
+        ++u_loads;
+        auto issue_v = [&](int tt, int J) {
+          const int bq = tt & 1;
+          if (tt >= 2 && !mbar_wait_ab(&v_empty[bq], ((tt - 2) >> 1) & 1, abort_flag)) return false;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(v_full + bq)),
+                       "r"((uint32_t)(S * kVTile))
+                       : "memory");
+          for (int a = 0; a < S; ++a)
+            tma_load_2d(vs + (bq * S + a) * kVTile, &vmap, v_full + bq, 0,
+                        slice_base + a * rows_total + M.row_off + J * BN);
+          return true;
+        };
+        bool ok = issue_v(t, Js[0]);
+        vissued = t + 1;
+        const uint32_t id = idesc(false), idn = idesc(true);
+        for (int k = 0; k < nt && ok; ++k) {
+          const int tt = t + k;
+          if (k + 1 < nt) {
+            ok = issue_v(tt + 1, Js[k + 1]);
+            vissued = tt + 2;
+            if (!ok) break;
           }
-          // Re: u . v over the 64 real components (4 steps of 16)
+          if ((k == 0 && !mbar_wait_ab(u_full, u_phase, abort_flag)) ||
+              !mbar_wait_ab(&v_full[tt & 1], (tt >> 1) & 1, abort_flag) ||
+              (tt > 0 && !mbar_wait_ab(t_empty, (tt - 1) & 1, abort_flag))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t ub = smem_u32(us), vb = smem_u32(vs + (tt & 1) * S * kVTile);
+          bool first[S];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) mma(dre, sdesc(ua + 32 * k), sdesc(vb2 + 32 * k), id, (first[L] && k == 0) ? 0u : 1u);
-          // Im: u[32:64] . v[0:32] - u[0:32] . v[32:64]
-          mma(dim, sdesc(ua + 64), sdesc(vb2 + 0), id, first[L] ? 0u : 1u);
-          mma(dim, sdesc(ua + 96), sdesc(vb2 + 32), id, 1u);
-          mma(dim, sdesc(ua + 0), sdesc(vb2 + 64), idn, 1u);
-          mma(dim, sdesc(ua + 32), sdesc(vb2 + 96), idn, 1u);
-          first[L] = false;
+          for (int L = 0; L < S; ++L) first[L] = true;
+#pragma unroll 1
+          for (int a = 0; a < S; ++a) {
+#pragma unroll 1
+            for (int bb = 0; bb + a < S; ++bb) {
+              const int L = a + bb;
+              const uint32_t dre = tmem + L * 2 * BN, dim = dre + BN;
+              const uint32_t ua = ub + a * kUTile, vb2 = vb + bb * kVTile;
+              if constexpr (realv) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                  mma(dre, sdesc(ua + 32 * q), sdesc(vb2 + 32 * q), id, (first[L] && q == 0) ? 0u : 1u);
+              } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  mma(dre, sdesc(ua + 32 * q), sdesc(vb2 + 32 * q), id, (first[L] && q == 0) ? 0u : 1u);
+                mma(dim, sdesc(ua + 64), sdesc(vb2 + 0), id, first[L] ? 0u : 1u);
+                mma(dim, sdesc(ua + 96), sdesc(vb2 + 32), id, 1u);
+                mma(dim, sdesc(ua + 0), sdesc(vb2 + 64), idn, 1u);
+                mma(dim, sdesc(ua + 32), sdesc(vb2 + 96), idn, 1u);
+              }
+              first[L] = false;
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(v_empty + (tt & 1)))
+                       : "memory");
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(t_full))
+                       : "memory");
+        }
+        if (!ok) {
+          *abort_flag = 1;
+          atomicExch(status, (int)kDevTimeout);
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(done))
-                   : "memory");
+      __syncwarp();
+    } else {
+      // ---------------- epilogue warps: rows 32 (warp % 4) + lane, columns 8 (warp / 4) .. + 7
+      const int quad = warp & 3, part = warp >> 2;
+      const int r = quad * 32 + lane;
+      const int i = i0 + r;
+      const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+      const bool row_ok = i < ng && !(i >= k0 && i < k0 + kb);
+      const int ei = row_ok ? sig[buf * rows_total + M.row_off + i] : 0;
+      for (int k = 0; k < nt; ++k) {
+        const int tt = t + k;
+        const int j0 = Js[k] * BN;
+        const int c0 = part * 8;
+        double2 av[8];
+        int ex[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = j0 + c0 + q;
+          const bool jblock = j >= k0 && j < k0 + kb;
+          const bool live = row_ok && j < ng && (mode == 3 ? true : (j <= i && !jblock));
+          av[q] = (live && !jblock) ? M.A[(size_t)i * ng + j] : make_double2(0.0, 0.0);
+          ex[q] = live ? ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA : 1 << 20;
+        }
+        bool have = mbar_wait_ab(t_full, tt & 1, abort_flag);
+        have = __all_sync(0xffffffffu, have) != 0;
+        float hr[8], lr[8], hm[8], lm[8];
+        if (have) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int L = 0; L < S; ++L) {
+            uint32_t x[8], y[8];
+            tmem_ld8(tmem + lane_off + L * 2 * BN + c0, x);
+            if constexpr (!realv) tmem_ld8(tmem + lane_off + L * 2 * BN + BN + c0, y);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const float w = ldexpf(1.f, -BETA * L);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float vr = __fmul_rn(__uint_as_float(x[q]), w);
+              const float vi = realv ? 0.f : __fmul_rn(__uint_as_float(y[q]), w);
+              if (L == 0) {
+                hr[q] = vr;
+                lr[q] = 0.f;
+                hm[q] = vi;
+                lm[q] = 0.f;
+              } else if (L <= 2) {
+                // levels 1, 2 can reach the running sum's last bits: exact two-sum
+                float sm, e;
+                two_sum(hr[q], vr, sm, e);
+                hr[q] = sm;
+                lr[q] = __fadd_rn(lr[q], e);
+                if constexpr (!realv) {
+                  two_sum(hm[q], vi, sm, e);
+                  hm[q] = sm;
+                  lm[q] = __fadd_rn(lm[q], e);
+                }
+              } else {
+                // levels 3..6 lie below 2^-24 of the sum: they go to the low word
+                lr[q] = __fadd_rn(lr[q], vr);
+                if constexpr (!realv) lm[q] = __fadd_rn(lm[q], vi);
+              }
+            }
+          }
+        } else if (lane == 0) {
+          *abort_flag = 1;
+          atomicExch(status, (int)kDevTimeout);
+        }
+        // tensor memory is free for the next tile's MMAs
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(t_empty)) : "memory");
+        if (!have) continue;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (ex[q] == (1 << 20)) continue;
+          const int j = j0 + c0 + q;
+          const double2 v = av[q];
+          const int e2 = ex[q];
+          double2 o;
+          // scale 2^e2 (sigma_i tau_j 2^-16) applied in the conversion; four FP64 adds
+          o.x = (v.x - f2d_scaled(hr[q], e2)) - f2d_scaled(lr[q], e2);
+          o.y = realv ? v.y : (v.y - f2d_scaled(hm[q], e2)) - f2d_scaled(lm[q], e2);
+          M.A[(size_t)i * ng + j] = o;
+        }
+      }
+    }
+    t += nt;
+    __syncthreads();   // the item's tiles are written; U and the V buffers are free
+    // The tile holding the next diagonal block (rows and columns k1 .. k1+31)
+    // has its final values: sweep it here (next step's D^-1 into Dinv, -D^-1
+    // into A_K1K1) without a separate launch.
+    if (mode == 1 && I == In && Jn >= J0 && Jn < J1 && !*abort_flag) {
+      const int kb1 = min(NB, ng - k1);
+      for (int e = threadIdx.x; e < NB * NB; e += kPipeThreads) {
+        const int rr = e / NB, c2 = e % NB;
+        if (rr < kb1 && c2 <= rr) dsm.L[rr][c2] = M.A[(size_t)(k1 + rr) * ng + k1 + c2];
+      }
+      diag_sweep_smem_n<kPipeThreads>(dsm, kb1, threadIdx.x, status);
+      for (int e = threadIdx.x; e < NB * NB; e += kPipeThreads) {
+        const int rr = e / NB, c2 = e % NB;
+        if (rr >= kb1 || c2 >= kb1) continue;
+        const double2 v = (rr >= c2) ? dsm.L[rr][c2] : make_double2(dsm.L[c2][rr].x, -dsm.L[c2][rr].y);
+        M.Dinv[rr * NB + c2] = make_double2(-v.x, -v.y);
+        if (rr >= c2) M.A[(size_t)(k1 + rr) * ng + k1 + c2] = v;
+      }
+      __syncthreads();
     }
   }
-  __syncwarp();
-  bool have = mbar_wait(done, 0);
-  have = __all_sync(0xffffffffu, have) != 0;
-  if (!have && threadIdx.x == 0) atomicExch(status, (int)kDevTimeout);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncwarp();
-  if (have && ok) {
-    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows of the tile)
-    // and the columns BN/4 (w / 4) .. + BN/4 - 1, in chunks of kChunk: the
-    // A values of a chunk are loaded first, then all 14 level loads (7
-    // levels, Re and Im) are issued before a single wait.
-    const int quad = warp & 3, part = warp >> 2;
-    constexpr int kCols = BN / (kThreads / 128);
-    const int r = quad * 32 + lane;
-    const int i = i0 + r;
-    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-    const bool row_ok = i < ng && !(i >= k0 && i < k0 + kb);
-    const int ei = row_ok ? sig[buf * rows_total + M.row_off + i] : 0;
-#pragma unroll 1
-    for (int c0 = part * kCols; c0 < (part + 1) * kCols; c0 += kChunk) {
-      double2 av[kChunk];
-      int ex[kChunk];
-#pragma unroll
-      for (int q = 0; q < kChunk; ++q) {
-        const int j = j0 + c0 + q;
-        const bool jblock = j >= k0 && j < k0 + kb;
-        const bool live = row_ok && j < ng && (mode == 3 ? true : (j <= i && !jblock));
-        av[q] = (live && !jblock) ? M.A[(size_t)i * ng + j] : make_double2(0.0, 0.0);
-        ex[q] = live ? ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA : 1 << 20;
-      }
-      uint32_t x[S][kChunk], y[S][kChunk];
-#pragma unroll
-      for (int L = 0; L < S; ++L) {
-        tmem_ld4(tmem + lane_off + L * 2 * BN + c0, x[L]);
-        if constexpr (!realv) tmem_ld4(tmem + lane_off + L * 2 * BN + BN + c0, y[L]);
-      }
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if constexpr (realv) {
-#pragma unroll
-        for (int L = 0; L < S; ++L)
-#pragma unroll
-          for (int q = 0; q < kChunk; ++q) y[L][q] = 0u;
-      }
-#pragma unroll
-      for (int q = 0; q < kChunk; ++q) {
-        float hr = __uint_as_float(x[0][q]), lr = 0.f, hm = __uint_as_float(y[0][q]), lm = 0.f;
-#pragma unroll
-        for (int L = 1; L < S; ++L) {
-          const float w = ldexpf(1.f, -BETA * L);
-          const float vr = __fmul_rn(__uint_as_float(x[L][q]), w), vi = __fmul_rn(__uint_as_float(y[L][q]), w);
-          float sm, e;
-          two_sum(hr, vr, sm, e);
-          hr = sm;
-          lr = __fadd_rn(lr, e);
-          two_sum(hm, vi, sm, e);
-          hm = sm;
-          lm = __fadd_rn(lm, e);
-        }
-        if (ex[q] == (1 << 20)) continue;
-        const int j = j0 + c0 + q;
-        // scale by sigma_i tau_j 2^-16 = 2^ex: exact power of two, applied to
-        // the FP32 pair when it stays a normal number, else in FP64; four
-        // FP64 adds per element, scaling and conversion off the FP64 pipe
-        const double2 v = av[q];
-        double2 o;
-        const int e2 = ex[q];
-        if (realv && e2 > -100 && e2 < 100) {
-          o.x = (v.x - f2d(ldexpf(hr, e2))) - f2d(ldexpf(lr, e2));
-          o.y = v.y;   // real values: the imaginary part stays zero
-        } else if (!realv && e2 > -100 && e2 < 100) {
-          o.x = (v.x - f2d(ldexpf(hr, e2))) - f2d(ldexpf(lr, e2));
-          o.y = (v.y - f2d(ldexpf(hm, e2))) - f2d(ldexpf(lm, e2));
-        } else {
-          o.x = v.x - ldexp((double)hr + (double)lr, e2);
-          o.y = v.y - ldexp((double)hm + (double)lm, e2);
-        }
-        M.A[(size_t)i * ng + j] = o;
+  // no copies in flight at exit (bounded waits on the last loads issued)
+  if (control && lane == 0 && u_loads > 0) {
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(u_full, (u_loads - 1) & 1) && globaltimer() - t0 < kWaitNs) {
+    }
+    for (int tt = max(0, vissued - 2); tt < vissued; ++tt) {
+      const uint64_t t1 = globaltimer();
+      while (!mbar_try_wait(&v_full[tt & 1], (tt >> 1) & 1) && globaltimer() - t1 < kWaitNs) {
       }
     }
   }
@@ -460,27 +580,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
-  }
-  // The tile holding the next diagonal block (rows and columns k1 .. k1+31)
-  // now has that block's final values: sweep it here, which leaves the next
-  // step's D^-1 in Dinv and -D^-1 in A_K1K1 without a separate launch.
-  // (I, J, mode) are the same for every thread of the CTA; the success
-  // flags are combined by the barrier so that all threads agree.
-  if (mode == 1 && I == In && J == Jn && __syncthreads_and(have && ok)) {
-    __shared__ DiagSmem dsm;
-    const int kb1 = min(NB, ng - k1);
-    for (int e = threadIdx.x; e < NB * NB; e += kThreads) {
-      const int r = e / NB, c2 = e % NB;
-      if (r < kb1 && c2 <= r) dsm.L[r][c2] = M.A[(size_t)(k1 + r) * ng + k1 + c2];
-    }
-    diag_sweep_smem_n<kThreads>(dsm, kb1, threadIdx.x, status);
-    for (int e = threadIdx.x; e < NB * NB; e += kThreads) {
-      const int r = e / NB, c2 = e % NB;
-      if (r >= kb1 || c2 >= kb1) continue;
-      const double2 v = (r >= c2) ? dsm.L[r][c2] : make_double2(dsm.L[c2][r].x, -dsm.L[c2][r].y);
-      M.Dinv[r * NB + c2] = make_double2(-v.x, -v.y);
-      if (r >= c2) M.A[(size_t)(k1 + r) * ng + k1 + c2] = v;
-    }
   }
 }
 
@@ -561,10 +660,12 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return fail(c, BGW_ECUDA, "tensor-core inverse: tensor map encoding failed");
-  // about 142 KiB: leaves room on each SM for the look-ahead chain's kernels
-  const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
-  BGW_CUDA(c, cudaFuncSetAttribute(update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  BGW_CUDA(c, cudaFuncSetAttribute(update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // U slices, two V buffers, alignment and barriers: about 170 KiB dynamic
+  const size_t psmem = (size_t)S * (kUTile + 2 * kVTile) + 1024 + 128;
+  BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)psmem));
+  BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)psmem));
   return BGW_OK;
 }
 
@@ -597,15 +698,21 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
     grid = std::min(4 * In + 4, nJ) + std::max(0, nI - In - 1);
   }
   if (plan->general) mode = 3;
-  const size_t smem = (size_t)S * (kUTile + kVTile) + 1024 + 64;
+  // one work item (up to kJPI tiles of a row tile) per CTA
+  {
+    const int nI = (ngmax + BM - 1) / BM, nJ = (ngmax + BN - 1) / BN, k1 = k0 + NB;
+    grid = pipe_items(mode, nI, nJ, k1 / BM, k1 < ngmax);
+  }
+  if (grid <= 0) return BGW_OK;
+  const size_t smem = (size_t)S * (kUTile + 2 * kVTile) + 1024 + 128;
   if (plan->real_values)
-    update_kernel<true><<<dim3(grid, plan->nmat), kThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,
-                                                                      plan->rows_total, buf, mode, plan->sig.as<int>(),
-                                                                      plan->tau.as<int>(), c->d_status);
+    update_pipe_kernel<true><<<dim3(grid, plan->nmat), kPipeThreads, smem, st>>>(
+        plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, buf, mode, plan->sig.as<int>(), plan->tau.as<int>(),
+        c->d_status);
   else
-    update_kernel<false><<<dim3(grid, plan->nmat), kThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,
-                                                                       plan->rows_total, buf, mode, plan->sig.as<int>(),
-                                                                       plan->tau.as<int>(), c->d_status);
+    update_pipe_kernel<false><<<dim3(grid, plan->nmat), kPipeThreads, smem, st>>>(
+        plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, buf, mode, plan->sig.as<int>(), plan->tau.as<int>(),
+        c->d_status);
   if (plan->general) {
     const long long ne = (long long)NB * ngmax;
     rows_from_r_kernel<<<dim3((unsigned)((ne + 255) / 256), plan->nmat), 256, 0, st>>>(plan->batch, k0);
