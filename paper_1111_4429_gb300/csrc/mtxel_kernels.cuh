@@ -108,8 +108,11 @@ __global__ void __launch_bounds__(64) band_yxpass(const cpx<T>* __restrict__ U1,
 // ---------------------------------------------------------------- pair y,x
 // grid (ceil(npb/ppb), N), block >= 32.  Pairs pbase .. pbase+npb-1.
 // smem: Y[ppb][nys][N+1] | Tz[ppb][ncol] | colmap[N*nys] | yslot[N]
+// FP32: at most 128 registers, so two 256-thread blocks share an SM (the
+// register-limited single block leaves the SM latency-bound); FP64 keeps
+// its registers (a cap would spill).
 template <typename T, int N>
-__global__ void __launch_bounds__(256) pair_yxpass(const cpx<T>* __restrict__ uv,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) pair_yxpass(const cpx<T>* __restrict__ uv,
                                                    const cpx<T>* __restrict__ uc, int nc,
                                                    int pbase, int npb, int ppb, int nys, int ncol,
                                                    const int* __restrict__ g_colmap,
