@@ -236,10 +236,10 @@ def run_ours(args):
         n_inv = kt["oz_update"][0] / (2 * nsteps)
         t_step = kt["oz_update"][1] / 1e3 / (n_inv * nsteps)      # s of update per sweep step
         # DRAM bytes of one sweep step's two update launches at N_G = 2120 (dram__bytes_read.sum +
-        # dram__bytes_write.sum of one ncu capture of this kernel): 3.85 MB + 37.4 MB.  The matrix
+        # dram__bytes_write.sum of one ncu capture of this kernel): 3.88 MB + 37.5 MB.  The matrix
         # stays in L2, so this is below the tiles' algorithmic traffic.
-        oz_traffic_step = 41.2e6 if s.ng == 2120 else None
-        roof = {"bound": "tensor", "kernel": "oz::update_kernel (tcgen05 kind::f16 M128 N32: the sweep's trailing "
+        oz_traffic_step = 41.4e6 if s.ng == 2120 else None
+        roof = {"bound": "tensor", "kernel": "oz::update_pipe_kernel (tcgen05 kind::f16 M128 N32: the sweep's trailing "
                                              "update from exact FP16 slices, FP64-level result)",
                 "achieved": issued_step / t_step / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                 "algorithmic": "issued tensor flops: lower 128x32 tiles x 224 MMAs x 2x128x32x16 per sweep step "

@@ -251,12 +251,15 @@ constexpr int kJPI = 2;   // column tiles per work item
 
 __device__ __forceinline__ int row_width(int mode, int I, int nJ) { return mode == 3 ? nJ : min(4 * I + 4, nJ); }
 
-// Number of work items of a mode, and the decode of one.
+// Number of work items of a mode, and the decode of one.  Mode 1 starts with
+// the tile holding the next diagonal block alone (its CTA sweeps that block:
+// the critical path of the next step), then the rest of row tile In in
+// chunks (tile Jn skipped there), then the tiles (I > In, Jn).
 __host__ __device__ inline int pipe_items(int mode, int nI, int nJ, int In, bool has_next) {
   int n = 0;
   if (mode == 1) {
     const int w = (4 * In + 4 < nJ) ? 4 * In + 4 : nJ;
-    return (w + kJPI - 1) / kJPI + (nI - In - 1 > 0 ? nI - In - 1 : 0);
+    return 1 + (w + kJPI - 1) / kJPI + (nI - In - 1 > 0 ? nI - In - 1 : 0);
   }
   for (int I = 0; I < nI; ++I) {
     if (mode == 2 && has_next && I == In) continue;
@@ -270,12 +273,16 @@ __device__ inline void pipe_decode(int mode, int item, int nI, int nJ, int In, i
   if (mode == 1) {
     const int w = row_width(1, In, nJ);
     const int nrow = (w + kJPI - 1) / kJPI;
-    if (item < nrow) {
+    if (item == 0) {
       I = In;
-      J0 = item * kJPI;
+      J0 = Jn;
+      J1 = Jn + 1;
+    } else if (item <= nrow) {
+      I = In;
+      J0 = (item - 1) * kJPI;
       J1 = min(J0 + kJPI, w);
     } else {
-      I = In + 1 + (item - nrow);
+      I = In + 1 + (item - 1 - nrow);
       J0 = Jn;
       J1 = Jn + 1;
     }
@@ -294,10 +301,12 @@ __device__ inline void pipe_decode(int mode, int item, int nI, int nJ, int In, i
   }
   J0 = J1 = 0;
 }
-__device__ inline bool pipe_skip(int mode, int I, int J, int ng, int k0, int kb, int Jn, bool has_next) {
+__device__ inline bool pipe_skip(int mode, int item, int I, int J, int ng, int k0, int kb, int In, int Jn,
+                                 bool has_next) {
   const int i0 = I * BM, j0 = J * BN;
   if (j0 >= ng) return true;
   if (mode == 2 && has_next && J == Jn) return true;
+  if (mode == 1 && item > 0 && I == In && J == Jn) return true;   // done by item 0
   if (i0 >= k0 && min(i0 + BM, ng) <= k0 + kb) return true;
   if (mode != 3 && j0 >= k0 && min(j0 + BN, ng) <= k0 + kb) return true;
   return false;
@@ -378,7 +387,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
     // tiles of the item that are not skipped, in order
     int Js[kJPI], nt = 0;
     for (int J = J0; J < J1; ++J)
-      if (!pipe_skip(mode, I, J, ng, k0, kb, Jn, has_next)) Js[nt++] = J;
+      if (!pipe_skip(mode, item, I, J, ng, k0, kb, In, Jn, has_next)) Js[nt++] = J;
     if (control) {
       if (lane == 0 && nt > 0 && !*abort_flag) {
         // U slices of the row tile (the previous item's MMAs are complete:
@@ -547,7 +556,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
     // The tile holding the next diagonal block (rows and columns k1 .. k1+31)
     // has its final values: sweep it here (next step's D^-1 into Dinv, -D^-1
     // into A_K1K1) without a separate launch.
-    if (mode == 1 && I == In && Jn >= J0 && Jn < J1 && !*abort_flag) {
+    if (mode == 1 && item == 0 && !*abort_flag) {
       const int kb1 = min(NB, ng - k1);
       for (int e = threadIdx.x; e < NB * NB; e += kPipeThreads) {
         const int rr = e / NB, c2 = e % NB;
