@@ -578,8 +578,7 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cel
           // the diagonal block of step k >= 1 was swept by step k-1's
           // next-block update (the CTA of the tile holding it)
           if (k == 0) sw_diag_kernel<<<nb, kDiagThreads, 0, s2>>>(sb, k0, c->d_status);
-          sw_panel_kernel<<<dim3((ngmax + 7) / 8, nb), 256, 0, s2>>>(sb, k0);
-          if ((rc = oz_slice(c, oz.get(), k0, ngmax, buf, s2)) != BGW_OK) return rc;
+          if ((rc = oz_panel_slice(c, oz.get(), k0, ngmax, buf, s2)) != BGW_OK) return rc;
         }
         BGW_CUDA(c, cudaEventRecord(ev_slice, s2));
         if (k >= 1) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf ^ 1], 0));
@@ -594,7 +593,7 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cel
         }
         BGW_CUDA(c, cudaEventRecord(ev_rest[buf], st));
         BGW_CUDA(c, cudaGetLastError());
-        c->launches += 5;
+        c->launches += 4;
       }
       // join: the main stream waits for the side stream's last work
       BGW_CUDA(c, cudaEventRecord(ev_fork, s2));

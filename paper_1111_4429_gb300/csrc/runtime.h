@@ -277,6 +277,8 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
                double2* const* D, OzPlan* plan, bool general = false, bool real_values = false);
 // epsinv_batch_run with real_values: the matrices are real (imaginary parts zero).
 int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);
+// The Hermitian sweep's panel (C, P = C D^-1, A_RK <- P) and its slices in one launch.
+int oz_panel_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);
 int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaStream_t st);
 
 }  // namespace bgw

@@ -176,6 +176,61 @@ __global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBa
             (blockIdx.z == 0 ? sig : tau) + (size_t)buf * rows_total + row);
 }
 
+// The Hermitian sweep's panel and its slices in one launch (the look-ahead
+// chain's critical path): for every row i outside the block K (warp per
+// row, lane k = column k), C_i = A_iK (read from the stored lower triangle),
+// P_i = C_i D^-1, the panel buffers and A_iK <- P_i written as the panel
+// kernel of the FP64 sweep does, then P_i and C_i cut into their slices.
+// Rows of K and padding rows get zero slices.  grid (ngpad/8, nmat).
+__global__ void __launch_bounds__(256) panel_slice_kernel(const __grid_constant__ OzBatch b, int k0, int rows_total,
+                                                          int buf, __half* __restrict__ U, __half* __restrict__ V,
+                                                          int* __restrict__ sig, int* __restrict__ tau) {
+  __shared__ double2 Ds[NB][NB];
+  __shared__ double2 Cs[8][NB];
+  const OzMat& M = b.m[blockIdx.y];
+  const int ng = M.ng;
+  const int ngpad = (ng + BM - 1) / BM * BM;
+  if (blockIdx.x * 8 >= ngpad) return;
+  const int kb = min(NB, ng - k0);
+  double2* A = M.A;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = M.Dinv[e];
+  const int i = blockIdx.x * 8 + warp;
+  const bool row_ok = k0 < ng && i < ng && (i < k0 || i >= k0 + kb);
+  double2 cv = make_double2(0.0, 0.0);
+  if (row_ok && lane < kb) {
+    if (i >= k0 + kb) {
+      cv = A[(size_t)i * ng + k0 + lane];
+    } else {
+      const double2 t = A[(size_t)(k0 + lane) * ng + i];
+      cv = make_double2(t.x, -t.y);
+    }
+  }
+  Cs[warp][lane] = cv;
+  __syncthreads();
+  double2 pv = make_double2(0.0, 0.0);
+  if (row_ok) {
+    for (int t = 0; t < kb; ++t) {
+      const double2 a = Cs[warp][t], d = Ds[t][lane];
+      pv.x = fma(a.x, d.x, fma(-a.y, d.y, pv.x));
+      pv.y = fma(a.x, d.y, fma(a.y, d.x, pv.y));
+    }
+    if (lane < kb) {
+      const_cast<double2*>(M.C)[(size_t)i * NB + lane] = cv;
+      const_cast<double2*>(M.P)[(size_t)i * NB + lane] = pv;
+      if (i >= k0 + kb)
+        A[(size_t)i * ng + k0 + lane] = pv;
+      else
+        A[(size_t)(k0 + lane) * ng + i] = make_double2(pv.x, -pv.y);
+    }
+  }
+  if (lane >= kb) pv = cv = make_double2(0.0, 0.0);
+  const size_t row = (size_t)M.row_off + i;
+  const size_t base = (size_t)buf * S * rows_total * KR + row * KR;
+  slice_row(pv.x, pv.y, lane, U + base, (size_t)rows_total * KR, sig + (size_t)buf * rows_total + row);
+  slice_row(cv.x, cv.y, lane, V + base, (size_t)rows_total * KR, tau + (size_t)buf * rows_total + row);
+}
+
 // Slices for the general (Gauss-Jordan) update A -= Cp R of the pivoted
 // inverse: z = 0 slices the column panel Cp [ng][NB] (rows of the block K
 // zero: they are overwritten with R afterwards), z = 1 slices R^H, read
@@ -690,6 +745,17 @@ int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) 
     slice_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
                                                                 plan->U.as<__half>(), plan->V.as<__half>(),
                                                                 plan->sig.as<int>(), plan->tau.as<int>());
+  BGW_CUDA(c, cudaGetLastError());
+  return BGW_OK;
+}
+
+// Panel and slices of one Hermitian sweep step in one launch (buffer buf).
+int oz_panel_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) {
+  using namespace oz;
+  const int rpad = (ngmax + BM - 1) / BM * BM;
+  panel_slice_kernel<<<dim3(rpad / 8, plan->nmat), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
+                                                                 plan->U.as<__half>(), plan->V.as<__half>(),
+                                                                 plan->sig.as<int>(), plan->tau.as<int>());
   BGW_CUDA(c, cudaGetLastError());
   return BGW_OK;
 }
