@@ -111,6 +111,23 @@ def _dist():
     return ws, rank, local
 
 
+def replica_time(t_local: float, ws: int, device) -> float:
+    """Time of the whole job of ws replicas (one process per GPU, each solving
+    its own q-points): the slowest rank's time, all ranks agreeing."""
+    if ws <= 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_rate(units_per_rank: int, t_local: float, ws: int, device) -> float:
+    """Whole-job throughput: the units all ranks processed / the job's time."""
+    return ws * units_per_rank / replica_time(t_local, ws, device)
+
+
 def flops_of(s):
     """Algorithmic flop counts of one solve (per stage)."""
     n, K, ng = s.fft, s.npairs, s.ng
@@ -198,11 +215,7 @@ def run_ours(args):
         wall = time.perf_counter() - t0
     if ws > 1:
         dist.barrier()
-    t_total = float(stage.sum()) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = replica_time(float(stage.sum()) / 1e3, ws, "cuda")
     mean = stage.mean(0)
     chi_ms = mean[1]
 
@@ -303,7 +316,7 @@ def run_ours(args):
 
     out = {
         "metric": METRIC,
-        "value": ws * args.steps / t_total,
+        "value": ws * args.steps / t_total,   # = replica_rate over the ranks
         "unit": "solves/s",
         "n_gpus": ws,
         "steps": args.steps,
