@@ -302,7 +302,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // MMAs start -- and apply the FP64 subtraction while they run.
 constexpr int kPipeEpiWarps = 16;
 constexpr int kPipeThreads = (kPipeEpiWarps + 1) * 32;
-constexpr int kJPI = 2;   // column tiles per work item
+constexpr int kJPI = 4;   // most column tiles per work item (mode 1 uses 2: its CTAs are on the critical path)
 
 __device__ __forceinline__ int row_width(int mode, int I, int nJ) { return mode == 3 ? nJ : min(4 * I + 4, nJ); }
 
@@ -310,32 +310,35 @@ __device__ __forceinline__ int row_width(int mode, int I, int nJ) { return mode 
 // the tile holding the next diagonal block alone (its CTA sweeps that block:
 // the critical path of the next step), then the rest of row tile In in
 // chunks (tile Jn skipped there), then the tiles (I > In, Jn).
+__host__ __device__ inline int pipe_jpi(int mode) { return mode == 1 ? 2 : kJPI; }
 __host__ __device__ inline int pipe_items(int mode, int nI, int nJ, int In, bool has_next) {
   int n = 0;
+  const int jpi = pipe_jpi(mode);
   if (mode == 1) {
     const int w = (4 * In + 4 < nJ) ? 4 * In + 4 : nJ;
-    return 1 + (w + kJPI - 1) / kJPI + (nI - In - 1 > 0 ? nI - In - 1 : 0);
+    return 1 + (w + jpi - 1) / jpi + (nI - In - 1 > 0 ? nI - In - 1 : 0);
   }
   for (int I = 0; I < nI; ++I) {
     if (mode == 2 && has_next && I == In) continue;
     const int w = mode == 3 ? nJ : ((4 * I + 4 < nJ) ? 4 * I + 4 : nJ);
-    n += (w + kJPI - 1) / kJPI;
+    n += (w + jpi - 1) / jpi;
   }
   return n;
 }
 __device__ inline void pipe_decode(int mode, int item, int nI, int nJ, int In, int Jn, bool has_next, int& I, int& J0,
                                    int& J1) {
+  const int jpi = pipe_jpi(mode);
   if (mode == 1) {
     const int w = row_width(1, In, nJ);
-    const int nrow = (w + kJPI - 1) / kJPI;
+    const int nrow = (w + jpi - 1) / jpi;
     if (item == 0) {
       I = In;
       J0 = Jn;
       J1 = Jn + 1;
     } else if (item <= nrow) {
       I = In;
-      J0 = (item - 1) * kJPI;
-      J1 = min(J0 + kJPI, w);
+      J0 = (item - 1) * jpi;
+      J1 = min(J0 + jpi, w);
     } else {
       I = In + 1 + (item - 1 - nrow);
       J0 = Jn;
@@ -346,10 +349,10 @@ __device__ inline void pipe_decode(int mode, int item, int nI, int nJ, int In, i
   for (I = 0; I < nI; ++I) {
     if (mode == 2 && has_next && I == In) continue;
     const int w = row_width(mode, I, nJ);
-    const int n = (w + kJPI - 1) / kJPI;
+    const int n = (w + jpi - 1) / jpi;
     if (item < n) {
-      J0 = item * kJPI;
-      J1 = min(J0 + kJPI, w);
+      J0 = item * jpi;
+      J1 = min(J0 + jpi, w);
       return;
     }
     item -= n;
