@@ -276,6 +276,7 @@ void oz_plan_delete(OzPlan* p);
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
                double2* const* D, OzPlan* plan, bool general = false, bool real_values = false);
 // epsinv_batch_run with real_values: the matrices are real (imaginary parts zero).
+// Slices of one pivoted Gauss-Jordan step (general plans).
 int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);
 // The Hermitian sweep's panel (C, P = C D^-1, A_RK <- P) and its slices in one launch.
 int oz_panel_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);

@@ -150,32 +150,6 @@ __device__ __forceinline__ void slice_row(double re, double im, int lane, __half
   if (lane == 0) *exp_out = e;
 }
 
-// Slices of P (z = 0) and C (z = 1): one warp per row, lane k holds the real
-// parts of column k and the imaginary parts (k + 32).  Rows inside the swept
-// block and padding rows get zero slices.
-__global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ OzBatch b, int k0, int rows_total,
-                                                    int buf, __half* __restrict__ U, __half* __restrict__ V,
-                                                    int* __restrict__ sig, int* __restrict__ tau) {
-  const OzMat& M = b.m[blockIdx.y];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * 8 + warp;
-  const int ngpad = (M.ng + BM - 1) / BM * BM;
-  if (i >= ngpad) return;
-  const int kb = min(NB, M.ng - k0);
-  const bool live = k0 < M.ng && i < M.ng && (i < k0 || i >= k0 + kb);
-  const double2* src = blockIdx.z == 0 ? M.P : M.C;
-  double re = 0.0, im = 0.0;
-  if (live && lane < kb) {
-    const double2 v = src[(size_t)i * NB + lane];
-    re = v.x;
-    im = v.y;
-  }
-  const size_t row = (size_t)M.row_off + i;
-  __half* out = (blockIdx.z == 0 ? U : V) + (size_t)buf * S * rows_total * KR + row * KR;
-  slice_row(re, im, lane, out, (size_t)rows_total * KR,
-            (blockIdx.z == 0 ? sig : tau) + (size_t)buf * rows_total + row);
-}
-
 // The Hermitian sweep's panel and its slices in one launch (the look-ahead
 // chain's critical path): for every row i outside the block K (warp per
 // row, lane k = column k), C_i = A_iK (read from the stored lower triangle),
@@ -736,18 +710,14 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
   return BGW_OK;
 }
 
-// Slices of one sweep step (P and C of every matrix) into buffer buf.
+// Slices of one pivoted Gauss-Jordan step (column panel and R^H of every matrix) into buffer buf.
 int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) {
   using namespace oz;
   const int rpad = (ngmax + BM - 1) / BM * BM;
-  if (plan->general)
-    slice_general_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
-                                                                        plan->U.as<__half>(), plan->V.as<__half>(),
-                                                                        plan->sig.as<int>(), plan->tau.as<int>());
-  else
-    slice_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
-                                                                plan->U.as<__half>(), plan->V.as<__half>(),
-                                                                plan->sig.as<int>(), plan->tau.as<int>());
+  if (!plan->general) return fail(c, BGW_EINVAL, "oz_slice: the Hermitian sweep slices in oz_panel_slice");
+  slice_general_kernel<<<dim3(rpad / 8, plan->nmat, 2), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
+                                                                      plan->U.as<__half>(), plan->V.as<__half>(),
+                                                                      plan->sig.as<int>(), plan->tau.as<int>());
   BGW_CUDA(c, cudaGetLastError());
   return BGW_OK;
 }
