@@ -542,10 +542,11 @@ def run_real_flavor(ctx, prec, flush, steps=3, warmup=2):
 
 
 def run_sigma(ctx, prec, flush, steps=2, warmup=1):
-    """Diagonal static COHSEX / bare exchange (bgw_sigma_cohsex, FP64) on the
-    c1 cell: 8 outer bands at k, 832 inner bands at k - q (32 occupied), the
-    N_G = 2120 eps~^-1 of the c1 solve.  The quadratic forms are one FP64
-    GEMM of 8 K N_G^2 flops, K = 8 x 832 pairs."""
+    """Diagonal static COHSEX / bare exchange (bgw_sigma_cohsex) on the c1
+    cell: 8 outer bands at k, 832 inner bands at k - q (32 occupied), the
+    N_G = 2120 eps~^-1 of the c1 solve.  The quadratic forms are one complex
+    GEMM of 8 K N_G^2 flops, K = 8 x 832 pairs: FP64 in the plain path, split
+    operands on the tensor cores in the mixed one.  Both are timed."""
     import torch
     from paper_1111_4429_gb300 import bgw, synth
     st = torch.cuda.current_stream()
@@ -558,24 +559,29 @@ def run_sigma(ctx, prec, flush, steps=2, warmup=1):
     sb = synth.sigma_bands(s, 8, 832, 32, seed=2001)
     co = torch.from_numpy(sb.co).cuda()
     ci = torch.from_numpy(sb.ci).cuda()
-    for _ in range(warmup):
-        out = ctx.sigma_cohsex(cell, sb.go, co, sb.gi, ci, sb.nocc, s.geps, inv[0])
-    tt = []
-    for k in range(steps):
-        flush.fill_(k & 0xff)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        out = ctx.sigma_cohsex(cell, sb.go, co, sb.gi, ci, sb.nocc, s.geps, inv[0])
-        b.record(st)
-        b.synchronize()
-        tt.append(a.elapsed_time(b))
-    ms = float(np.mean(tt))
     K = 8 * 832
-    return {"workload": "c1 cell, 8 outer x 832 inner bands (32 occupied), N_G 2120, FP64",
-            "ms_per_call": ms, "quad_gemm_fp64_tflops_over_call": 8.0 * K * s.ng * s.ng / (ms / 1e3) / 1e12,
-            "sigma_ha": {"X": out[0].tolist(), "SX": out[1].tolist(), "CH": out[2].tolist(),
-                         "CH_exact": out[3].tolist()}}
+    res = {"workload": "c1 cell, 8 outer x 832 inner bands (32 occupied), N_G 2120"}
+    outs = {}
+    for name, p in (("fp64", bgw.BGW_PREC_FP64), ("mixed", prec)):
+        for _ in range(warmup):
+            out = ctx.sigma_cohsex(cell, sb.go, co, sb.gi, ci, sb.nocc, s.geps, inv[0], prec=p)
+        tt = []
+        for k in range(steps):
+            flush.fill_(k & 0xff)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            out = ctx.sigma_cohsex(cell, sb.go, co, sb.gi, ci, sb.nocc, s.geps, inv[0], prec=p)
+            b.record(st)
+            b.synchronize()
+            tt.append(a.elapsed_time(b))
+        ms = float(np.mean(tt))
+        outs[name] = out
+        res[name] = {"ms_per_call": ms, "quad_gemm_tflops_over_call": 8.0 * K * s.ng * s.ng / (ms / 1e3) / 1e12}
+    f, m = outs["fp64"], outs["mixed"]
+    res["mixed_vs_fp64_max_rel"] = float(max(np.abs(m[k] - f[k]).max() / np.abs(f[k]).max() for k in range(4)))
+    res["sigma_ha"] = {"X": f[0].tolist(), "SX": f[1].tolist(), "CH": f[2].tolist(), "CH_exact": f[3].tolist()}
+    return res
 
 
 def run_batch_c3(ctx, prec, steps=2):

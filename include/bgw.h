@@ -172,8 +172,15 @@ int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
  *    -1 (default): on when the epsilon list holds G = 0, the interaction is
  *    bulk or slab and |q| < 0.02 min_i |b_i|; 0: off; 1: on whenever G = 0
  *    is in the list.  No effect on BGW_PREC_FP64 or on bgw_chi_sum.         */
+/*  BGW_OPT_SIGMA_DENSITY: how bgw_sigma_cohsex forms the band densities
+ *    rho_n(D) of the closed-form Coulomb hole.  -1 (default) and 1: as the
+ *    matrix element M_nn(D) of the band with itself, by the pruned product
+ *    transform on the smallest supported grid that aliases neither the
+ *    difference box nor the product's spectrum, else (no such grid up to 64)
+ *    as 0; 0: the direct sum over the outer sphere, O(box x npw) per band.
+ *    Both are FP64.                                                         */
 enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3, BGW_OPT_CHI_CHUNK_PAIRS = 4,
-       BGW_OPT_INVERSE = 5, BGW_OPT_HEAD = 6 };
+       BGW_OPT_INVERSE = 5, BGW_OPT_HEAD = 6, BGW_OPT_SIGMA_DENSITY = 7 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
 
 /* With BGW_OPT_TIMING = 1 the context records CUDA events around its main
@@ -292,15 +299,19 @@ int bgw_epsinv_rflavor(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int*
  *       first nocc are occupied
  *   geps host int32 [ng][3], the eps sphere of q; epsinv device c128
  *       [ng][ng] (bgw_epsinv of the same cell and list)
+ *   prec BGW_PREC_FP64: FP64 throughout.  BGW_PREC_MIX_FP16 / _BF16: m from
+ *        the FP32 matrix-element path and W m on the tensor cores (split
+ *        operands, FP32 segment sums, FP64 result); the quadratic forms,
+ *        the sums and the closed form in FP64.
  *   sigma host double [4][no]; the call returns after it is written.
- * FP64.  EINVAL as bgw_mtxel for the lists and grid (n > max|Gi| + max|Go| +
+ * EINVAL as bgw_mtxel for the lists and grid (n > max|Gi| + max|Go| +
  * max|Geps| per axis, and -G inside [-n/2, n/2)), for non-device arrays or
  * nocc outside [0, ni].                                                     */
 int bgw_sigma_cohsex(bgw_ctx* ctx, const bgw_cell* cell,
                      int no, int npw_o, const int32_t* go, const void* co,
                      int ni, int npw_i, const int32_t* gi, const void* ci,
                      int nocc, int ng, const int32_t* geps, const void* epsinv,
-                     double* sigma, void* stream);
+                     int prec, double* sigma, void* stream);
 
 /* bgw_real_coefficients -- real-flavor coefficients from complex ones (host
  * arrays), as the paper prescribes: bands whose energies (ascending) differ

@@ -33,6 +33,7 @@ EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_s
            "bgw_serve_close")
 BGW_OPT_CHI_SEGMENT_PAIRS, BGW_OPT_TIMING, BGW_OPT_AUTOTUNE, BGW_OPT_CHI_CHUNK_PAIRS, BGW_OPT_INVERSE = 1, 2, 3, 4, 5
 BGW_OPT_HEAD = 6
+BGW_OPT_SIGMA_DENSITY = 7
 BGW_FLAVOR_REAL = 0x100
 BGW_COULOMB_BULK, BGW_COULOMB_SPHERE, BGW_COULOMB_SLAB = 0, 1, 2
 COULOMB_MODELS = {"bulk": BGW_COULOMB_BULK, "sphere": BGW_COULOMB_SPHERE, "slab": BGW_COULOMB_SLAB}
@@ -137,7 +138,7 @@ def load() -> ctypes.CDLL:
     lib.bgw_frequency_grid.argtypes = [cd, cd, cd, cd, ci, dp, ctypes.POINTER(ci)]
     lib.bgw_epsinv_rflavor.argtypes = lib.bgw_epsinv.argtypes
     lib.bgw_real_coefficients.argtypes = [ci, ci, vp, dp, cd, dp]
-    lib.bgw_sigma_cohsex.argtypes = [vp, cellp, ci, ci, i32p, vp, ci, ci, i32p, vp, ci, ci, i32p, vp, dp, vp]
+    lib.bgw_sigma_cohsex.argtypes = [vp, cellp, ci, ci, i32p, vp, ci, ci, i32p, vp, ci, ci, i32p, vp, ci, dp, vp]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_char_p if name == "bgw_last_error" else ctypes.c_int
     _lib = lib
@@ -341,7 +342,8 @@ class Context:
         self._check(self.lib.bgw_epsinv_rflavor(self.h, n, carr, ng, gp, cp, ep, ip, _stream(stream)))
         return epsinvs
 
-    def sigma_cohsex(self, cell: Cell, go, co, gi, ci, nocc: int, geps, epsinv, stream=None) -> np.ndarray:
+    def sigma_cohsex(self, cell: Cell, go, co, gi, ci, nocc: int, geps, epsinv, stream=None,
+                     prec: int = 0) -> np.ndarray:
         """bgw_sigma_cohsex: returns [4][no] (X, SX, CH sum form, CH closed form), Hartree."""
         go_, gop = _i32(go)
         gi_, gip = _i32(gi)
@@ -349,7 +351,7 @@ class Context:
         out = np.zeros((4, co.shape[0]), dtype=np.float64)
         self._check(self.lib.bgw_sigma_cohsex(self.h, ctypes.byref(cell), co.shape[0], go_.shape[0], gop, _ptr(co),
                                               ci.shape[0], gi_.shape[0], gip, _ptr(ci), nocc, ge_.shape[0], gep,
-                                              _ptr(epsinv), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              _ptr(epsinv), prec, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                               _stream(stream)))
         return out
 

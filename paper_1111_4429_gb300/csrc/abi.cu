@@ -272,6 +272,11 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
     c->inverse_mode = (int)value;
     return BGW_OK;
   }
+  if (option == BGW_OPT_SIGMA_DENSITY) {
+    if (value < -1 || value > 1) return fail(c, BGW_EINVAL, "density mode is -1, 0 or 1");
+    c->sigma_density = (int)value;
+    return BGW_OK;
+  }
   if (option == BGW_OPT_HEAD) {
     if (value < -1 || value > 1) return fail(c, BGW_EINVAL, "head mode is -1, 0 or 1");
     c->head_mode = (int)value;
@@ -817,11 +822,13 @@ int bgw_epsilon_real(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, cons
 
 int bgw_sigma_cohsex(bgw_ctx* ctx, const bgw_cell* cell, int no, int npw_o, const int32_t* go, const void* co, int ni,
                      int npw_i, const int32_t* gi, const void* ci, int nocc, int ng, const int32_t* geps,
-                     const void* epsinv, double* sigma, void* stream) {
+                     const void* epsinv, int prec, double* sigma, void* stream) {
   Ctx* c = impl(ctx);
   if (!c) return BGW_EINVAL;
   int n, rc;
   if ((rc = check_cell(c, cell, &n)) != BGW_OK) return rc;
+  if ((rc = check_prec(c, prec)) != BGW_OK) return rc;
+  if (ng > max_ng(prec)) return fail(c, BGW_EUNSUPPORTED, "ng = %d exceeds %d", ng, max_ng(prec));
   if (no <= 0 || ni <= 0 || nocc < 0 || nocc > ni) return fail(c, BGW_EINVAL, "need no, ni >= 1 and 0 <= nocc <= ni");
   if ((long long)no * ni > 0x7fffffffLL) return fail(c, BGW_EUNSUPPORTED, "no * ni exceeds 2^31 - 1");
   if (!co || !ci || !epsinv || !sigma) return fail(c, BGW_EINVAL, "NULL coefficient, epsinv or output pointer");
@@ -853,7 +860,7 @@ int bgw_sigma_cohsex(bgw_ctx* ctx, const bgw_cell* cell, int no, int npw_o, cons
   const void* dg;
   if ((rc = upload_cached(c, geps, (size_t)ng * 3 * sizeof(int32_t), st, &dg)) != BGW_OK) return rc;
   return sigma_run(c, cell, n, no, bpo, go, co, ni, bpi, ci, nocc, ng, geps, static_cast<const int32_t*>(dg), pp,
-                   epsinv, sigma, st);
+                   epsinv, prec, sigma, st);
 }
 
 int bgw_real_coefficients(int nb, int npw, const void* c, const double* energies, double tol, double* out) {

@@ -631,6 +631,64 @@ __global__ void reduce_kernel(const float* __restrict__ work, int nseg, int ntil
   if (g != gp) chi[(size_t)gp * ng + g] = make_double2(v.x, -v.y);
 }
 
+// Row-major operands of a general product C = X^H-row Y-row (the Sigma
+// quadratic forms): planes[pl][r][k] from src[r][k], no transpose.  max|.|
+// of an operand (conj does not change it) into *out.
+template <typename S2>
+__global__ void maxabs_rows_kernel(const S2* __restrict__ src, long long n, unsigned int* __restrict__ out) {
+  float m = 0.f;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fmaxf(fabsf((float)src[e].x), fabsf((float)src[e].y)));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// planes[0..3][r][k] <- (conj ? conj(src) : src)[r][k] 2^e split hi/lo, rows
+// r < R of K values each; padding rows and columns zero.  grid (kpad/32, Rpad/8), block (32, 8).
+template <typename H, typename S2>
+__global__ void split_rows_kernel(const S2* __restrict__ src, int R, int K, int kpad, size_t plane, int conj,
+                                  const unsigned int* __restrict__ maxbits, int bf16, H* __restrict__ planes) {
+  const int k = blockIdx.x * 32 + threadIdx.x;
+  const int r = blockIdx.y * 8 + threadIdx.y;
+  const float sc = ldexpf(1.f, scale_exp(maxbits, bf16));
+  float2 v = make_float2(0.f, 0.f);
+  if (r < R && k < K) {
+    const S2 x = src[(size_t)r * K + k];
+    v = make_float2((float)x.x * sc, (conj ? -(float)x.y : (float)x.y) * sc);
+  }
+  split4<H>(v, planes, plane, (size_t)r * kpad + k);
+}
+
+// C[p][g] = 2^{-(eX + eY)} sum_seg W for p < R1, g < R2 (row stride R2).
+template <int BN>
+__global__ void reduce_rows_kernel(const float* __restrict__ work, int nseg, int ntiles,
+                                   const int2* __restrict__ tiles, int R1, int R2,
+                                   const unsigned int* __restrict__ maxbits, int bf16, double2* __restrict__ C) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)BM * BN;
+  if (e >= per * ntiles) return;
+  const int tix = (int)(e / per);
+  const int r = (int)((e - (long long)tix * per) / BN), cc = (int)(e % BN);
+  const int2 tl = tiles[tix];
+  const int p = tl.x * BM + r, g = tl.y * BN + cc;
+  if (p >= R1 || g >= R2) return;
+  float re = 0.f, rel = 0.f, im = 0.f, iml = 0.f;
+  for (int s = 0; s < nseg; ++s) {
+    const float* w = work + ((size_t)s * ntiles + tix) * 2 * per;
+    const float a = w[r * BN + cc], b = w[per + r * BN + cc];
+    float t = __fadd_rn(re, a);
+    float z = __fsub_rn(t, re);
+    rel = __fadd_rn(rel, __fadd_rn(__fsub_rn(re, __fsub_rn(t, z)), __fsub_rn(a, z)));
+    re = t;
+    t = __fadd_rn(im, b);
+    z = __fsub_rn(t, im);
+    iml = __fadd_rn(iml, __fadd_rn(__fsub_rn(im, __fsub_rn(t, z)), __fsub_rn(b, z)));
+    im = t;
+  }
+  const double f = ldexp(1.0, -(scale_exp(maxbits, bf16) + scale_exp(maxbits + 1, bf16)));
+  C[(size_t)p * R2 + g] = make_double2(((double)re + (double)rel) * f, ((double)im + (double)iml) * f);
+}
+
 }  // namespace tc
 
 namespace {
@@ -813,6 +871,89 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
 int chi_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double* w, int nrow, double scale,
                   int accumulate, void* chi, cudaStream_t st, bool real) {
   return chi_tc_run(c, prec, K, ng, M, w, nullptr, nrow, scale, accumulate, chi, st, real);
+}
+
+// C[p][g] = sum_k X[p][k] Y[g][k] on the tensor cores for a complex64 X
+// [R1][K] and a complex128 Y [R2][K] (both row-major), FP16 (or BF16) hi/lo
+// splits with their own power-of-two scales, FP32 segment sums, FP64 result
+// [R1][R2].  The general chi kernel computes sum_k conj(A[p][k]) B[g][k]:
+// A = conj(X), B = Y.
+int tc_rows_gemm(Ctx* c, int prec, int R1, int R2, int K, const void* X, const void* Y, void* C, cudaStream_t st) {
+  using namespace tc;
+  int rc;
+  if ((rc = get_encode(c)) != BGW_OK) return rc;
+  const int bf16 = prec == BGW_PREC_MIX_BF16;
+  const int rpad = (std::max(R1, R2) + BM - 1) / BM * BM;
+  const int kpad = (K + BK - 1) / BK * BK;
+  const int ntr = (R1 + BM - 1) / BM, ntc = (R2 + kBN - 1) / kBN;
+  std::vector<int2> tl;
+  for (int I = 0; I < ntr; ++I)
+    for (int J = 0; J < ntc; ++J) tl.push_back(make_int2(I, J));
+  const int ntiles = (int)tl.size();
+  const int kb_per_seg = std::max(1, kSegPairsDefault / BK);
+  const int nkb = kpad / BK;
+  const int nseg = (nkb + kb_per_seg - 1) / kb_per_seg;
+  const size_t plane = (size_t)rpad * kpad;
+  const void* d_tiles;
+  if ((rc = upload_cached(c, tl.data(), tl.size() * sizeof(int2), st, &d_tiles)) != BGW_OK) return rc;
+  Scratch planes, work, mx;
+  planes.pool = work.pool = mx.pool = &c->pool;
+  const size_t work_bytes = (size_t)nseg * ntiles * 2 * BM * kBN * sizeof(float);
+  if ((rc = c->pool.alloc(8 * plane * 2, &planes.ptr)) != BGW_OK || (rc = c->pool.alloc(work_bytes, &work.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc(2 * sizeof(unsigned int), &mx.ptr)) != BGW_OK)
+    return fail(c, rc, "tensor-core product: scratch allocation failed");
+  CUtensorMap tmap;
+  cuuint64_t gdim[2] = {(cuuint64_t)kpad, (cuuint64_t)8 * rpad};
+  cuuint64_t gstride[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult cr = g_encode(&tmap, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                         planes.ptr, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return fail(c, BGW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  const size_t smem = (size_t)kStages * Layout<kBN>::kStage + 1024 + 256;
+  BGW_CUDA(c, cudaFuncSetAttribute(chi_tc_kernel<kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  unsigned int* mb = mx.as<unsigned int>();
+  BGW_CUDA(c, cudaMemsetAsync(mb, 0, 2 * sizeof(unsigned int), st));
+  {
+    TimedScope ts(c, kTChiSplit, st);
+    const long long n1 = (long long)R1 * K, n2 = (long long)R2 * K;
+    maxabs_rows_kernel<float2><<<(unsigned)std::min<long long>((n1 + 255) / 256, 152LL * 8), 256, 0, st>>>(
+        static_cast<const float2*>(X), n1, mb);
+    maxabs_rows_kernel<double2><<<(unsigned)std::min<long long>((n2 + 255) / 256, 152LL * 8), 256, 0, st>>>(
+        static_cast<const double2*>(Y), n2, mb + 1);
+    // X rows fill the planes' rpad rows; Y's tiles read no row past ntc * BN
+    dim3 g((unsigned)(kpad / 32), (unsigned)(rpad / 8)), g2((unsigned)(kpad / 32), (unsigned)(ntc * kBN / 8)), b(32, 8);
+    if (bf16) {
+      split_rows_kernel<__nv_bfloat16, float2><<<g, b, 0, st>>>(static_cast<const float2*>(X), R1, K, kpad, plane, 1,
+                                                                 mb, 1, planes.as<__nv_bfloat16>());
+      split_rows_kernel<__nv_bfloat16, double2><<<g2, b, 0, st>>>(static_cast<const double2*>(Y), R2, K, kpad, plane,
+                                                                   0, mb + 1, 1, planes.as<__nv_bfloat16>() + 4 * plane);
+    } else {
+      split_rows_kernel<__half, float2><<<g, b, 0, st>>>(static_cast<const float2*>(X), R1, K, kpad, plane, 1, mb, 0,
+                                                          planes.as<__half>());
+      split_rows_kernel<__half, double2><<<g2, b, 0, st>>>(static_cast<const double2*>(Y), R2, K, kpad, plane, 0,
+                                                            mb + 1, 0, planes.as<__half>() + 4 * plane);
+    }
+  }
+  {
+    TimedScope ts(c, kTChiTc, st);
+    chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
+        tmap, rpad, 4 * rpad, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
+        c->d_status);
+  }
+  {
+    TimedScope ts(c, kTChiReduce, st);
+    const long long ne = (long long)ntiles * BM * kBN;
+    reduce_rows_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+        work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), R1, R2, mb, bf16,
+        static_cast<double2*>(C));
+  }
+  BGW_CUDA(c, cudaGetLastError());
+  c->launches += 7;
+  return BGW_OK;
 }
 
 int chi_real_mixed_run(Ctx* c, int prec, long long K, int ng, const void* M, const double2* w, int nrow,

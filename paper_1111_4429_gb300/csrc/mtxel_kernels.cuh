@@ -174,14 +174,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) pair_yxpass(const
 }
 
 // ---------------------------------------------------------------- pair z
-// grid (npb), block 256.  smem Mrow[ng].
+// grid (npb), block 256.  smem Mrow[ng], or none with direct != 0 (a list
+// too long for shared memory: the outputs go straight to M, complex only).
 template <typename T, int N>
 __global__ void __launch_bounds__(256) pair_zgather(const cpx<T>* __restrict__ Tbuf, int pbase,
                                                     int ncol, int ng,
                                                     const int* __restrict__ zmap,
-                                                    void* __restrict__ M, int real_out) {
+                                                    void* __restrict__ M, int real_out, int direct) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* Mrow = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* Mrow = direct ? static_cast<cpx<T>*>(M) + (size_t)(pbase + blockIdx.x) * ng
+                        : reinterpret_cast<cpx<T>*>(smem_raw);
   const int pl = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const T inv = T(1) / T(N * N * N);
   const cpx<T>* src = Tbuf + (size_t)pl * N * ncol;
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(256) pair_zgather(const cpx<T>* __restrict__ T
       if (g >= 0) Mrow[g] = scale<T>(a[k], inv);
     }
   }
+  if (direct) return;
   __syncthreads();
   if (real_out) {   // real flavor: M is real (its imaginary part vanishes up to rounding)
     T* dst = static_cast<T*>(M) + (size_t)(pbase + pl) * ng;
@@ -311,7 +314,9 @@ static cudaError_t mtxel_exec_n(const MtxelExec& x) {
   pair_block_shape<T, N>(ppb, pp->nys, pp->ncol, &threads, &sm);
   if ((e = set_smem(pair_yxpass<T, N>, sm)) != cudaSuccess) return e;
   size_t smz = (size_t)pp->ng * sizeof(C);
-  if ((e = set_smem(pair_zgather<T, N>, smz)) != cudaSuccess) return e;
+  const int zdirect = (smz > 200 * 1024 && !x.real) ? 1 : 0;
+  if (zdirect) smz = 0;
+  else if ((e = set_smem(pair_zgather<T, N>, smz)) != cudaSuccess) return e;
   const long long npairs = (long long)x.nv * x.nc;
   for (long long p0 = 0; p0 < npairs; p0 += x.pair_block) {
     const int npb = (int)((npairs - p0) < x.pair_block ? (npairs - p0) : x.pair_block);
@@ -322,7 +327,7 @@ static cudaError_t mtxel_exec_n(const MtxelExec& x) {
     }
     {
       TimedScope ts(x.ctx, kTPairZ, x.st);
-      pair_zgather<T, N><<<npb, 256, smz, x.st>>>(Tb, (int)p0, pp->ncol, pp->ng, pp->d_zmap, M, x.real);
+      pair_zgather<T, N><<<npb, 256, smz, x.st>>>(Tb, (int)p0, pp->ncol, pp->ng, pp->d_zmap, M, x.real, zdirect);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *x.launches += 2;

@@ -95,7 +95,7 @@ struct Timing {
   std::map<int, std::pair<long long, double>> acc;  // name -> (launches, ms)
 };
 enum TimedName { kTBand = 0, kTPairYX, kTPairZ, kTChiF64, kTChiSplit, kTChiTc, kTChiReduce, kTEpsForm, kTInverse,
-                 kTOzUpdate, kTSweepChain, kTHeadDot, kTHeadWings, kTScreenedW, kTPivot, kTNumNames };
+                 kTOzUpdate, kTSweepChain, kTHeadDot, kTHeadWings, kTScreenedW, kTPivot, kTSigmaForms, kTSigmaExact, kTNumNames };
 const char* timed_name(int n);
 
 // A captured batch (bgw_epsilon_batch) replayed while its key is unchanged.
@@ -113,6 +113,7 @@ struct Ctx {
   cudaEvent_t la_ev[4] = {};       // look-ahead dependencies (fork, slice, rest x2)
   int inverse_mode = -1;     // -1: tensor-core update for the mixed precisions; 0: FP64 FMA; 1: tensor cores
   int head_mode = -1;        // mixed chi head/wings in FP64: -1 automatic at small q, 0 off, 1 on
+  int sigma_density = -1;    // Sigma band densities: -1/1 product transform where alias-free, 0 direct sum
   std::unordered_map<uint64_t, const int32_t*> head_maps;  // conduction G -> valence index (head dot products)
   Pool pool;
   std::string err;
@@ -255,7 +256,11 @@ int coulomb_sqrt_run(Ctx* c, const bgw_cell* cell, const int32_t* d_geps, int ng
 // pair plan of the negated epsilon list; sigma_host [4][no].
 int sigma_run(Ctx* c, const bgw_cell* cell, int n, int no, const BandPlan* bpo, const int32_t* go, const void* co,
               int ni, const BandPlan* bpi, const void* ci, int nocc, int ng, const int32_t* geps_host,
-              const int32_t* d_geps, const PairPlan* pp_neg, const void* epsinv, double* sigma_host, cudaStream_t st);
+              const int32_t* d_geps, const PairPlan* pp_neg, const void* epsinv, int prec, double* sigma_host,
+              cudaStream_t st);
+// C[p][g] = sum_k X[p][k] Y[g][k] on the tensor cores (chi_tc.cu): X complex64
+// [R1][K], Y complex128 [R2][K], C complex128 [R1][R2].
+int tc_rows_gemm(Ctx* c, int prec, int R1, int R2, int K, const void* X, const void* Y, void* C, cudaStream_t st);
 // W = v^1/2 epsinv v^1/2 for nmat matrices (bgw_screened_w).
 int screened_w_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cells, const int32_t* const* d_geps,
                    const void* const* epsinv, void* const* W, cudaStream_t st);
