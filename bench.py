@@ -47,6 +47,13 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# Slices per value of the tensor-core update in the mixed solves (the
+# library's default after a mixed-precision chi).
+UPDATE_SLICES_MIXED = 5
+# DRAM bytes per sweep step of the two update launches (ncu, N_G = 2120), or
+# None until the current kernel has been captured.
+OZ_TRAFFIC_STEP = None
+
 # FP64 CUDA-core peak from unit counts and the maximum SM clock: 152 SMs x
 # 2 FP64 FMA lanes per SM per clock (the part's 1.25 TFLOP/s FP64 rating at
 # 2.07 GHz corresponds to 1.99 FMA/clk/SM) x 2 flop x 2.07 GHz.
@@ -170,6 +177,8 @@ def _solve_steps(ctx, s, prec, steps, warmup, flush, timing):
     # the mixed precisions invert with the tensor-core trailing update (FP64-level
     # accuracy), the plain path with FP64 FMA
     ctx.set_option(bgw.BGW_OPT_INVERSE, 0 if prec == bgw.BGW_PREC_FP64 else 1)
+    # the mixed solve's update slices: what bgw_epsilon uses after a mixed chi
+    ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0 if prec == bgw.BGW_PREC_FP64 else UPDATE_SLICES_MIXED)
     for _ in range(warmup):
         step()
     ctx.sync()
@@ -186,6 +195,7 @@ def _solve_steps(ctx, s, prec, steps, warmup, flush, timing):
     kt = ctx.timing_report(reset=True) if timing else {}
     ctx.set_option(bgw.BGW_OPT_TIMING, 0)
     ctx.set_option(bgw.BGW_OPT_INVERSE, -1)
+    ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0)
     stage = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in ev])
     return stage, kt, inv, launches
 
@@ -241,22 +251,25 @@ def run_ours(args):
     peaks, peak_src = _peaks()
     nsteps = (s.ng + 31) // 32
     if dom == "oz_update":
-        # tensor work issued per sweep step: every lower 128x32 tile runs 28
-        # slice pairs x (4 + 4) MMAs of 128x32x16
+        # tensor work issued per sweep step: every lower 128x32 tile runs
+        # SL(SL+1)/2 slice pairs x (4 + 4) MMAs of 128x32x16 (SL slices per value)
+        sl = UPDATE_SLICES_MIXED
+        pairs = sl * (sl + 1) // 2
         nI, nJ = (s.ng + 127) // 128, (s.ng + 31) // 32
         tiles = sum(min(4 * I + 4, nJ) for I in range(nI))
-        issued_step = tiles * 224 * 2.0 * 128 * 32 * 16
+        issued_step = tiles * pairs * 8 * 2.0 * 128 * 32 * 16
         n_inv = kt["oz_update"][0] / (2 * nsteps)
         t_step = kt["oz_update"][1] / 1e3 / (n_inv * nsteps)      # s of update per sweep step
-        # DRAM bytes of one sweep step's two update launches at N_G = 2120 (dram__bytes_read.sum +
-        # dram__bytes_write.sum of one ncu capture of this kernel): 3.88 MB + 37.5 MB.  The matrix
-        # stays in L2, so this is below the tiles' algorithmic traffic.
-        oz_traffic_step = 41.4e6 if s.ng == 2120 else None
-        roof = {"bound": "tensor", "kernel": "oz::update_pipe_kernel (tcgen05 kind::f16 M128 N32: the sweep's trailing "
-                                             "update from exact FP16 slices, FP64-level result)",
+        # DRAM bytes of one sweep step's two update launches at N_G = 2120
+        # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
+        # this kernel with 5 slices).  The matrix stays in L2, so this is below
+        # the tiles' algorithmic traffic.
+        oz_traffic_step = OZ_TRAFFIC_STEP if s.ng == 2120 else None
+        roof = {"bound": "tensor", "kernel": f"oz::update_pipe_kernel<{sl} slices> (tcgen05 kind::f16 M128 N32: the "
+                                             "sweep's trailing update from exact FP16 slices)",
                 "achieved": issued_step / t_step / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                "algorithmic": "issued tensor flops: lower 128x32 tiles x 224 MMAs x 2x128x32x16 per sweep step "
-                               "(28 slice pairs per FP64 product)",
+                "algorithmic": f"issued tensor flops: lower 128x32 tiles x {pairs * 8} MMAs x 2x128x32x16 per sweep "
+                               f"step ({pairs} slice pairs per FP64 product)",
                 "peak_source": "measured bf16 burst (fp16 has the same nominal rate)",
                 "fp64_equivalent_tflops": 4.0 * 32 * s.ng * s.ng / t_step / 1e12,
                 "fp64_pipe_peak_tflops": FP64_PEAK_TFLOPS,
@@ -753,6 +766,7 @@ def run_profile_case(args):
         cell = bgw.system_cell(s)
         prec = bgw.PREC[args.prec]
         ctx.set_option(bgw.BGW_OPT_INVERSE, 0 if prec == bgw.BGW_PREC_FP64 else 1)
+        ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0 if prec == bgw.BGW_PREC_FP64 else UPDATE_SLICES_MIXED)
         cv = torch.from_numpy(s.cv).cuda()
         cc = torch.from_numpy(s.cc).cuda()
         M = torch.empty((s.npairs, s.ng), dtype=torch.complex128 if prec == 0 else torch.complex64, device="cuda")

@@ -158,10 +158,11 @@ int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
  *    bgw_epsilon, bgw_epsilon_batch and the server use the tensor cores for
  *    the mixed precisions and FP64 FMA for BGW_PREC_FP64, bgw_epsinv uses
  *    FP64 FMA; 0: FP64 FMA everywhere; 1: the tensor cores everywhere.  The
- *    tensor-core update splits P and C into seven 8-bit slices held exactly
- *    in FP16, accumulates every slice product exactly in FP32 and combines
- *    them in double-FP32 before the FP64 subtraction: its error is near
- *    2^-48 of the update's scale (FP64 FMA: 2^-53).                        */
+ *    tensor-core update splits P and C into 8-bit slices held exactly in
+ *    FP16 (seven or five, BGW_OPT_UPDATE_SLICES), accumulates every slice
+ *    product exactly in FP32 and combines them in double-FP32 before the
+ *    FP64 subtraction: with seven its error is near 2^-48 of the update's
+ *    scale (FP64 FMA: 2^-53).                                              */
 /*  BGW_OPT_HEAD: the q0 head of the mixed precisions.  At a small q0 the
  *    head column M_vc(G = 0) is O(|q0|) while v(q0) = 4 pi / |q0|^2, so the
  *    FP32 FFTs' absolute error on it (near 2^-24 |M|) becomes a relative
@@ -179,8 +180,15 @@ int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
  *    difference box nor the product's spectrum, else (no such grid up to 64)
  *    as 0; 0: the direct sum over the outer sphere, O(box x npw) per band.
  *    Both are FP64.                                                         */
+/*  BGW_OPT_UPDATE_SLICES: slices per value of the tensor-core update.  7:
+ *    error near 2^-48 of the update's scale (FP64-level inverse); 5: near
+ *    2^-34, with 15 slice products per tile instead of 28.  0 (default):
+ *    5 where the inverse follows a mixed-precision chi (bgw_epsilon,
+ *    bgw_epsilon_batch and the server with BGW_PREC_MIX_*: their chi carries
+ *    errors near 1e-7), 7 elsewhere (bgw_epsinv, bgw_epsinv_general,
+ *    bgw_epsinv_rflavor and the FP64 precision).                            */
 enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3, BGW_OPT_CHI_CHUNK_PAIRS = 4,
-       BGW_OPT_INVERSE = 5, BGW_OPT_HEAD = 6, BGW_OPT_SIGMA_DENSITY = 7 };
+       BGW_OPT_INVERSE = 5, BGW_OPT_HEAD = 6, BGW_OPT_SIGMA_DENSITY = 7, BGW_OPT_UPDATE_SLICES = 8 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
 
 /* With BGW_OPT_TIMING = 1 the context records CUDA events around its main

@@ -162,6 +162,14 @@ bool use_tc_inverse(Ctx* c, int prec) {
   return prec != BGW_PREC_FP64;
 }
 
+// Slices of the tensor-core update for a call of precision prec: the
+// option's value, else 5 for the mixed precisions (their chi carries errors
+// near 1e-7, far above the 5-slice update's 2^-34) and 7 (FP64-level) for
+// FP64 inputs.  Recorded in the context for the inverse that follows.
+void set_run_slices(Ctx* c, int prec) {
+  c->run_slices = c->update_slices ? c->update_slices : (prec == BGW_PREC_FP64 ? 7 : 5);
+}
+
 int init_device(Ctx* c) {
   if (c->twiddles_ready) return BGW_OK;
   BGW_CUDA(c, mtxel_init_f64());
@@ -270,6 +278,11 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
   if (option == BGW_OPT_INVERSE) {
     if (value < -1 || value > 1) return fail(c, BGW_EINVAL, "inverse mode is -1, 0 or 1");
     c->inverse_mode = (int)value;
+    return BGW_OK;
+  }
+  if (option == BGW_OPT_UPDATE_SLICES) {
+    if (value != 0 && value != 5 && value != 7) return fail(c, BGW_EINVAL, "update slices are 0, 5 or 7");
+    c->update_slices = (int)value;
     return BGW_OK;
   }
   if (option == BGW_OPT_SIGMA_DENSITY) {
@@ -414,6 +427,7 @@ int bgw_epsinv_general(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int*
     dgeps[m] = static_cast<const int32_t*>(dg);
     cp[m] = &cells[m];
   }
+  set_run_slices(c, BGW_PREC_FP64);
   return epsinv_general_run(c, nmat, ng, cp.data(), dgeps.data(), chi, eps, epsinv, st, c->inverse_mode == 1);
 }
 
@@ -439,6 +453,7 @@ int bgw_epsinv_rflavor(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int*
     dgeps[m] = static_cast<const int32_t*>(dg);
     cp[m] = &cells[m];
   }
+  set_run_slices(c, BGW_PREC_FP64);
   return epsinv_rflavor_run(c, nmat, ng, cp.data(), dgeps.data(), chi, eps, epsinv, st, c->inverse_mode == 1);
 }
 
@@ -464,6 +479,7 @@ int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, con
     dgeps[m] = static_cast<const int32_t*>(dg);
     cp[m] = &cells[m];
   }
+  set_run_slices(c, BGW_PREC_FP64);
   if ((rc = epsinv_batch_run(c, nmat, ng, cp.data(), dgeps.data(), chi, eps, epsinv, st, c->inverse_mode == 1)) !=
       BGW_OK)
     return rc;
@@ -556,6 +572,7 @@ int run_batch(Ctx* c, int nq, const bgw_problem* pr, int nfreq, const double* de
       chis[f] = static_cast<char*>(sChi.ptr) + f * n2;
       invs[f] = static_cast<char*>(epsinv[q]) + f * n2;
     }
+    set_run_slices(c, prec);
     if ((rc = epsinv_batch_run(c, nrow, ngv.data(), cp.data(), gv.data(), chis.data(), nullptr,
                                invs.data(), st, use_tc_inverse(c, prec))) != BGW_OK)
       return rc;
@@ -592,7 +609,7 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   uint64_t key = hash_bytes(&nq, sizeof(nq), hash_bytes(&prec, sizeof(prec), hash_bytes(&nfreq, sizeof(nfreq))));
   if (nfreq > 0) key = hash_bytes(omega, nfreq * sizeof(double), key);
   key = hash_bytes(&st, sizeof(st), key);
-  const int modes[2] = {c->inverse_mode, c->head_mode};
+  const int modes[3] = {c->inverse_mode, c->head_mode, c->update_slices};
   key = hash_bytes(modes, sizeof(modes), key);
   for (int q = 0; q < nq; ++q) {
     const bgw_problem& p = problems[q];
@@ -774,6 +791,7 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
       chis[f] = static_cast<char*>(d_chi) + f * n2;
       invs[f] = static_cast<char*>(d_inv) + f * n2;
     }
+    set_run_slices(c, prec);
     if (fa.real)
       rc = epsinv_general_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
                               use_tc_inverse(c, prec));

@@ -114,6 +114,8 @@ struct Ctx {
   int inverse_mode = -1;     // -1: tensor-core update for the mixed precisions; 0: FP64 FMA; 1: tensor cores
   int head_mode = -1;        // mixed chi head/wings in FP64: -1 automatic at small q, 0 off, 1 on
   int sigma_density = -1;    // Sigma band densities: -1/1 product transform where alias-free, 0 direct sum
+  int update_slices = 0;     // tensor-core update slices: 0 automatic, 5 or 7
+  int run_slices = 7;        // slices of the call in progress (set by each entry point)
   std::unordered_map<uint64_t, const int32_t*> head_maps;  // conduction G -> valence index (head dot products)
   Pool pool;
   std::string err;
@@ -278,8 +280,9 @@ void oz_plan_delete(OzPlan* p);
 // update A -= P R with P the column panel [ng][32] and C = R [32][ng].
 // real_values: every matrix is real (the real flavor's embedding), so only
 // the real-part products are formed.
+// slices: 7 (update error near 2^-48 of its scale) or 5 (near 2^-34).
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               double2* const* D, OzPlan* plan, bool general = false, bool real_values = false);
+               double2* const* D, OzPlan* plan, bool general, bool real_values, int slices);
 // epsinv_batch_run with real_values: the matrices are real (imaginary parts zero).
 // Slices of one pivoted Gauss-Jordan step (general plans).
 int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);

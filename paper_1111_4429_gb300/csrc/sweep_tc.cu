@@ -251,13 +251,14 @@ __global__ void rows_from_r_kernel(const __grid_constant__ OzBatch b, int k0) {
 // f 2^ex as a double, exactly, for a finite float f and |ex| < 900: the
 // exponent is added in the double's field (no FP32 scaling, no range issue).
 __device__ __forceinline__ double f2d_scaled(float f, int ex) {
+  // f 2^ex as a double, built from f's fields in 32-bit halves (f is zero or
+  // a normal number here; other inputs take the library path)
   const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
-  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  if (e == 0u && m == 0u) return __longlong_as_double((long long)sign);  // +-0
-  if (e == 0u || e == 0xFFu) return ldexp((double)f, ex);                // denormal, inf, nan
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u + ex) << 52) |
-                                          ((unsigned long long)m << 29)));
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (u << 1) == 0u ? __longlong_as_double((long long)(u & 0x80000000u) << 32)
+                                                   : ldexp((double)f, ex);
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u + (unsigned)ex) << 20) | ((u >> 3) & 0xFFFFFu);
+  return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -355,11 +356,17 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, vol
   return true;
 }
 
-template <bool realv>
+// SL: slices used per value (the most significant SL of the S stored): 7
+// gives an update error near 2^-48 of its scale, 5 near 2^-34.
+template <bool realv, int SL>
 __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per sub-partition, 96 registers
     update_pipe_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
                        const __grid_constant__ OzBatch b, int k0, int rows_total, int buf, int mode,
                        const int* __restrict__ sig, const int* __restrict__ tau, int* __restrict__ status) {
+  // Levels 1 .. kTwoSumLevels are summed exactly (two-sum) into the high
+  // word: with 7 slices the target is near 2^-48, so levels 1 and 2 (2^-8,
+  // 2^-16 of the sum) need it; with 5 slices (near 2^-34) only level 1.
+  constexpr int kTwoSumLevels = SL >= 7 ? 2 : 1;
   const OzMat& M = b.m[blockIdx.y];
   const int ng = M.ng;
   if (k0 >= ng) return;
@@ -374,9 +381,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  unsigned char* us = smem;                          // S x 16 KiB
-  unsigned char* vs = smem + S * kUTile;             // 2 x S x 4 KiB
-  uint64_t* u_full = reinterpret_cast<uint64_t*>(vs + 2 * S * kVTile);
+  unsigned char* us = smem;                          // SL x 16 KiB
+  unsigned char* vs = smem + SL * kUTile;            // 2 x SL x 4 KiB
+  uint64_t* u_full = reinterpret_cast<uint64_t*>(vs + 2 * SL * kVTile);
   uint64_t* v_full = u_full + 1;                     // [2]
   uint64_t* v_empty = v_full + 2;                    // [2]
   uint64_t* t_full = v_empty + 2;
@@ -425,9 +432,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
         // U slices of the row tile (the previous item's MMAs are complete:
         // the item-end barrier follows its last epilogue)
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(u_full)),
-                     "r"((uint32_t)(S * kUTile))
+                     "r"((uint32_t)(SL * kUTile))
                      : "memory");
-        for (int a = 0; a < S; ++a)
+        for (int a = 0; a < SL; ++a)
           tma_load_2d(us + a * kUTile, &umap, u_full, 0, slice_base + a * rows_total + M.row_off + i0);
         const int u_phase = u_loads & 1;
         ++u_loads;
@@ -435,10 +442,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
           const int bq = tt & 1;
           if (tt >= 2 && !mbar_wait_ab(&v_empty[bq], ((tt - 2) >> 1) & 1, abort_flag)) return false;
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(v_full + bq)),
-                       "r"((uint32_t)(S * kVTile))
+                       "r"((uint32_t)(SL * kVTile))
                        : "memory");
-          for (int a = 0; a < S; ++a)
-            tma_load_2d(vs + (bq * S + a) * kVTile, &vmap, v_full + bq, 0,
+          for (int a = 0; a < SL; ++a)
+            tma_load_2d(vs + (bq * SL + a) * kVTile, &vmap, v_full + bq, 0,
                         slice_base + a * rows_total + M.row_off + J * BN);
           return true;
         };
@@ -459,14 +466,14 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t ub = smem_u32(us), vb = smem_u32(vs + (tt & 1) * S * kVTile);
-          bool first[S];
+          const uint32_t ub = smem_u32(us), vb = smem_u32(vs + (tt & 1) * SL * kVTile);
+          bool first[SL];
 #pragma unroll
-          for (int L = 0; L < S; ++L) first[L] = true;
+          for (int L = 0; L < SL; ++L) first[L] = true;
 #pragma unroll 1
-          for (int a = 0; a < S; ++a) {
+          for (int a = 0; a < SL; ++a) {
 #pragma unroll 1
-            for (int bb = 0; bb + a < S; ++bb) {
+            for (int bb = 0; bb + a < SL; ++bb) {
               const int L = a + bb;
               const uint32_t dre = tmem + L * 2 * BN, dim = dre + BN;
               const uint32_t ua = ub + a * kUTile, vb2 = vb + bb * kVTile;
@@ -527,7 +534,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
         if (have) {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-          for (int L = 0; L < S; ++L) {
+          for (int L = 0; L < SL; ++L) {
             uint32_t x[8], y[8];
             tmem_ld8(tmem + lane_off + L * 2 * BN + c0, x);
             if constexpr (!realv) tmem_ld8(tmem + lane_off + L * 2 * BN + BN + c0, y);
@@ -542,8 +549,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
                 lr[q] = 0.f;
                 hm[q] = vi;
                 lm[q] = 0.f;
-              } else if (L <= 2) {
-                // levels 1, 2 can reach the running sum's last bits: exact two-sum
+              } else if (L <= kTwoSumLevels) {
+                // levels that can reach the running sum's last bits: exact two-sum
                 float sm, e;
                 two_sum(hr[q], vr, sm, e);
                 hr[q] = sm;
@@ -554,7 +561,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
                   lm[q] = __fadd_rn(lm[q], e);
                 }
               } else {
-                // levels 3..6 lie below 2^-24 of the sum: they go to the low word
+                // deeper levels lie below the sum's last bit at the target
+                // precision: they go to the low word
                 lr[q] = __fadd_rn(lr[q], vr);
                 if constexpr (!realv) lm[q] = __fadd_rn(lm[q], vi);
               }
@@ -633,9 +641,14 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 EncodeTiledFn g_encode_oz = nullptr;
 }  // namespace
 
+// Dynamic shared memory of update_pipe_kernel with SL slices: U, two V
+// buffers, alignment slack and the barriers.
+size_t pipe_smem(int slices) { return (size_t)slices * (oz::kUTile + 2 * oz::kVTile) + 1024 + 128; }
+
 // State of one batched sweep that uses the tensor-core update.
 struct OzPlan {
   bool general = false;   // Gauss-Jordan update (mode 3) of the pivoted inverse
+  int slices = 7;         // slices per value the update uses (5 or 7)
   bool real_values = false;  // every matrix real (real flavor): only the real-part MMAs
   int nmat = 0;
   int rows_total = 0;
@@ -646,8 +659,10 @@ struct OzPlan {
 };
 
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               double2* const* D, OzPlan* plan, bool general, bool real_values) {
+               double2* const* D, OzPlan* plan, bool general, bool real_values, int slices) {
   using namespace oz;
+  if (slices != 5 && slices != 7) return fail(c, BGW_EINVAL, "tensor-core inverse: 5 or 7 slices");
+  plan->slices = slices;
   if (nmat > kBatch) return fail(c, BGW_EUNSUPPORTED, "tensor-core inverse: at most %d matrices per batch", kBatch);
   if (!g_encode_oz) {
     void* fn = nullptr;
@@ -701,12 +716,19 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return fail(c, BGW_ECUDA, "tensor-core inverse: tensor map encoding failed");
-  // U slices, two V buffers, alignment and barriers: about 170 KiB dynamic
-  const size_t psmem = (size_t)S * (kUTile + 2 * kVTile) + 1024 + 128;
-  BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)psmem));
-  BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)psmem));
+  // U slices, two V buffers, alignment and barriers: about 170 KiB dynamic (7 slices)
+  const size_t psmem = pipe_smem(slices);
+  if (slices == 7) {
+    BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<false, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)psmem));
+    BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<true, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)psmem));
+  } else {
+    BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)psmem));
+    BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<true, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)psmem));
+  }
   return BGW_OK;
 }
 
@@ -752,15 +774,24 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
     grid = pipe_items(mode, nI, nJ, k1 / BM, k1 < ngmax);
   }
   if (grid <= 0) return BGW_OK;
-  const size_t smem = (size_t)S * (kUTile + 2 * kVTile) + 1024 + 128;
-  if (plan->real_values)
-    update_pipe_kernel<true><<<dim3(grid, plan->nmat), kPipeThreads, smem, st>>>(
-        plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, buf, mode, plan->sig.as<int>(), plan->tau.as<int>(),
-        c->d_status);
-  else
-    update_pipe_kernel<false><<<dim3(grid, plan->nmat), kPipeThreads, smem, st>>>(
-        plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, buf, mode, plan->sig.as<int>(), plan->tau.as<int>(),
-        c->d_status);
+  const size_t smem = pipe_smem(plan->slices);
+  const dim3 g(grid, plan->nmat);
+#define BGW_PIPE_LAUNCH(RV, SLC)                                                                               \
+  update_pipe_kernel<RV, SLC><<<g, kPipeThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,          \
+                                                             plan->rows_total, buf, mode, plan->sig.as<int>(), \
+                                                             plan->tau.as<int>(), c->d_status)
+  if (plan->slices == 7) {
+    if (plan->real_values)
+      BGW_PIPE_LAUNCH(true, 7);
+    else
+      BGW_PIPE_LAUNCH(false, 7);
+  } else {
+    if (plan->real_values)
+      BGW_PIPE_LAUNCH(true, 5);
+    else
+      BGW_PIPE_LAUNCH(false, 5);
+  }
+#undef BGW_PIPE_LAUNCH
   if (plan->general) {
     const long long ne = (long long)NB * ngmax;
     rows_from_r_kernel<<<dim3((unsigned)((ne + 255) / 256), plan->nmat), 256, 0, st>>>(plan->batch, k0);

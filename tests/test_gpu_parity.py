@@ -290,3 +290,30 @@ def test_epsinv_tensor_core_update_vs_oracle(ctx, which):
         ctx.set_option(bgw.BGW_OPT_INVERSE, -1)
     for r, i in zip(refs, inv):
         assert _rel(i, r["epsinv"]) <= TOL64
+
+
+@pytest.mark.parametrize("which", ["c0", "two"])
+def test_epsinv_tensor_core_update_five_slices(ctx, which):
+    """Five slices per value (the mixed solves' default): the update error is
+    near 2^-34 of its scale instead of 2^-48, so the bar is 2^14 times the
+    FP64 one; the batch of two sizes covers ragged tiles."""
+    from paper_1111_4429_gb300 import bgw
+    if which == "c0":
+        systems = [synth.config_system("c0")]
+    else:
+        systems = [synth.make_system("r", a=20.52, fft=40, ecut_wfn=8.0, ecut_eps=3.0, nv=4, nc=90, seed=88),
+                   synth.make_system("s", a=17.0, fft=40, ecut_wfn=8.0, ecut_eps=3.5, nv=4, nc=90, seed=89)]
+    refs = [oracle.solve(s) for s in systems]
+    chis = [_dev(r["chi"]) for r in refs]
+    ctx.set_option(bgw.BGW_OPT_INVERSE, 1)
+    ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 5)
+    try:
+        _, inv5 = _epsinv(ctx, systems, chis)
+        ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 7)
+        _, inv7 = _epsinv(ctx, systems, chis)
+    finally:
+        ctx.set_option(bgw.BGW_OPT_INVERSE, -1)
+        ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0)
+    for r, a, b in zip(refs, inv5, inv7):
+        assert _rel(a, r["epsinv"]) <= TOL64 * 2 ** 14
+        assert _rel(b, r["epsinv"]) <= TOL64

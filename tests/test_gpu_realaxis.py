@@ -76,7 +76,7 @@ def test_real_axis_adjoint_chunks_and_static_limit(ctx):
     assert _rel(inv_r[0], inv_i[0].cpu().numpy()) <= TOL64
 
 
-@pytest.mark.parametrize("tc", [0, 1])
+@pytest.mark.parametrize("tc", [0, 1, 5])
 @pytest.mark.parametrize("ng,seed", [(85, 1), (300, 2), (700, 3), (2311, 4)])
 def test_general_inverse_pivoting_vs_library(ctx, ng, seed, tc):
     """bgw_epsinv_general on random complex chi of several sizes: one leaf,
@@ -102,18 +102,23 @@ def test_general_inverse_pivoting_vs_library(ctx, ng, seed, tc):
     inv = torch.zeros((ng, ng), dtype=torch.complex128, device="cuda")
     eps = torch.zeros_like(inv)
     try:
-        ctx.set_option(bgw.BGW_OPT_INVERSE, tc)
+        # tc: 0 FP64 FMA, 1 tensor cores (7 slices), 5 tensor cores with 5 slices
+        ctx.set_option(bgw.BGW_OPT_INVERSE, 1 if tc else 0)
+        ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 5 if tc == 5 else 0)
         ctx.epsinv_general([cell], [geps], [_dev(x)], [eps], [inv])
         ctx.sync()
     finally:
         ctx.set_option(bgw.BGW_OPT_INVERSE, -1)
+        ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0)
     assert _rel(eps.cpu().numpy(), e) <= 1e-15
     got = inv.cpu().numpy()
     cond = np.linalg.cond(e)
-    assert _rel(got, ref) <= 1e-15 * cond * ng ** 0.5
     # the tensor-core update is accurate to about 2^-48 of the update's scale
-    # (FP64 FMA: 2^-53), so its residual bar is 32 times the FP64 one
-    assert np.linalg.norm(e @ got - np.eye(ng)) / np.sqrt(ng) <= 1e-12 * (32 if tc else 1)
+    # with 7 slices, 2^-34 with 5 (FP64 FMA: 2^-53): bars 32 and 2^19 times
+    # the FP64 ones
+    k = {0: 1, 1: 32, 5: 2 ** 19}[tc]
+    assert _rel(got, ref) <= 1e-15 * cond * ng ** 0.5 * max(1, k // 32)
+    assert np.linalg.norm(e @ got - np.eye(ng)) / np.sqrt(ng) <= 1e-12 * k
 
 
 @pytest.mark.parametrize("prec", [1, 2])
