@@ -50,9 +50,36 @@ def _peaks():
 # Slices per value of the tensor-core update in the mixed solves (the
 # library's default after a mixed-precision chi).
 UPDATE_SLICES_MIXED = 5
-# DRAM bytes per sweep step of the two update launches (ncu, N_G = 2120), or
-# None until the current kernel has been captured.
-OZ_TRAFFIC_STEP = None
+# DRAM bytes of one bulk update launch (ncu, N_G = 2120), or None until the
+# current kernel has been captured.
+OZ_TRAFFIC_LAUNCH = None
+
+
+def oz_tiles(ng, k0):
+    """128x32 tiles of the look-ahead and the bulk update launches of the
+    sweep step at block k0 (the kernel's work-item decode and skips)."""
+    BM, BN, NB = 128, 32, 32
+    nI, nJ = (ng + BM - 1) // BM, (ng + BN - 1) // BN
+    kb = min(NB, ng - k0)
+    k1 = k0 + NB
+    has_next = k1 < ng
+    In, Jn = k1 // BM, k1 // BN
+
+    def skip(I, J):
+        i0, j0 = I * BM, J * BN
+        return (j0 >= ng or (k0 <= i0 and min(i0 + BM, ng) <= k0 + kb)
+                or (k0 <= j0 and min(j0 + BN, ng) <= k0 + kb))
+
+    ahead = bulk = 0
+    for I in range(nI):
+        for J in range(min(4 * I + 4, nJ)):
+            if skip(I, J):
+                continue
+            if has_next and (I == In or J == Jn):
+                ahead += 1
+            else:
+                bulk += 1
+    return ahead, bulk
 
 # FP64 CUDA-core peak from unit counts and the maximum SM clock: 152 SMs x
 # 2 FP64 FMA lanes per SM per clock (the part's 1.25 TFLOP/s FP64 rating at
@@ -251,27 +278,34 @@ def run_ours(args):
     peaks, peak_src = _peaks()
     nsteps = (s.ng + 31) // 32
     if dom == "oz_update":
-        # tensor work issued per sweep step: every lower 128x32 tile runs
-        # SL(SL+1)/2 slice pairs x (4 + 4) MMAs of 128x32x16 (SL slices per value)
+        # The bulk update launch of each sweep step (the look-ahead launch,
+        # timed apart, runs beside it on a second stream).  Tensor work
+        # issued per launch: its 128x32 tiles x SL(SL+1)/2 slice pairs x
+        # (4 + 4) MMAs of 128x32x16 (SL slices per value).
         sl = UPDATE_SLICES_MIXED
         pairs = sl * (sl + 1) // 2
-        nI, nJ = (s.ng + 127) // 128, (s.ng + 31) // 32
-        tiles = sum(min(4 * I + 4, nJ) for I in range(nI))
-        issued_step = tiles * pairs * 8 * 2.0 * 128 * 32 * 16
-        n_inv = kt["oz_update"][0] / (2 * nsteps)
-        t_step = kt["oz_update"][1] / 1e3 / (n_inv * nsteps)      # s of update per sweep step
-        # DRAM bytes of one sweep step's two update launches at N_G = 2120
+        bulk_tiles = sum(oz_tiles(s.ng, k0)[1] for k0 in range(0, s.ng, 32))
+        n_launch = kt["oz_update"][0]
+        t_launch = kt["oz_update"][1] / 1e3 / n_launch               # s per bulk launch
+        issued_launch = bulk_tiles / nsteps * pairs * 8 * 2.0 * 128 * 32 * 16
+        issued_step = issued_launch
+        t_step = t_launch
+        # DRAM bytes of one bulk update launch at N_G = 2120
         # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
         # this kernel with 5 slices).  The matrix stays in L2, so this is below
         # the tiles' algorithmic traffic.
-        oz_traffic_step = OZ_TRAFFIC_STEP if s.ng == 2120 else None
+        oz_traffic_step = OZ_TRAFFIC_LAUNCH if s.ng == 2120 else None
         roof = {"bound": "tensor", "kernel": f"oz::update_pipe_kernel<{sl} slices> (tcgen05 kind::f16 M128 N32: the "
                                              "sweep's trailing update from exact FP16 slices)",
                 "achieved": issued_step / t_step / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                "algorithmic": f"issued tensor flops: lower 128x32 tiles x {pairs * 8} MMAs x 2x128x32x16 per sweep "
-                               f"step ({pairs} slice pairs per FP64 product)",
+                "algorithmic": f"issued tensor flops: the bulk launch's 128x32 tiles (mean {bulk_tiles / nsteps:.0f} "
+                               f"per sweep step) x {pairs * 8} MMAs x 2x128x32x16 ({pairs} slice pairs per FP64 "
+                               f"product)",
+                "look_ahead_launch_us": (kt["oz_update_ahead"][1] / kt["oz_update_ahead"][0] * 1e3
+                                         if "oz_update_ahead" in kt else None),
+                "bulk_launch_us": t_launch * 1e6,
                 "peak_source": "measured bf16 burst (fp16 has the same nominal rate)",
-                "fp64_equivalent_tflops": 4.0 * 32 * s.ng * s.ng / t_step / 1e12,
+                "fp64_equivalent_tflops": bulk_tiles / nsteps * 4.0 * 32 * 128 * 32 / t_step / 1e12,
                 "fp64_pipe_peak_tflops": FP64_PEAK_TFLOPS,
                 "traffic_bytes_per_sweep_step": oz_traffic_step}
     elif dom == "inverse":

@@ -583,7 +583,7 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cel
         BGW_CUDA(c, cudaEventRecord(ev_slice, s2));
         if (k >= 1) BGW_CUDA(c, cudaStreamWaitEvent(s2, ev_rest[buf ^ 1], 0));
         {
-          TimedScope ts(c, kTOzUpdate, s2);
+          TimedScope ts(c, kTOzAhead, s2);
           if ((rc = oz_update(c, oz.get(), k0, ngmax, buf, 1, s2)) != BGW_OK) return rc;
         }
         BGW_CUDA(c, cudaStreamWaitEvent(st, ev_slice, 0));

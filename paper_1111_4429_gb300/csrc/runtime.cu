@@ -142,7 +142,7 @@ const char* timed_name(int n) {
   static const char* names[kTNumNames] = {"band_transform", "pair_yxpass", "pair_zgather", "chi_f64",
                                           "chi_split", "chi_tc", "chi_reduce", "eps_form", "inverse",
                                           "oz_update", "sweep_chain", "head_dot", "head_wings",
-                                          "screened_w", "pivot", "sigma_forms", "sigma_exact"};
+                                          "screened_w", "pivot", "sigma_forms", "sigma_exact", "oz_update_ahead"};
   return (n >= 0 && n < kTNumNames) ? names[n] : "?";
 }
 

@@ -95,7 +95,7 @@ struct Timing {
   std::map<int, std::pair<long long, double>> acc;  // name -> (launches, ms)
 };
 enum TimedName { kTBand = 0, kTPairYX, kTPairZ, kTChiF64, kTChiSplit, kTChiTc, kTChiReduce, kTEpsForm, kTInverse,
-                 kTOzUpdate, kTSweepChain, kTHeadDot, kTHeadWings, kTScreenedW, kTPivot, kTSigmaForms, kTSigmaExact, kTNumNames };
+                 kTOzUpdate, kTSweepChain, kTHeadDot, kTHeadWings, kTScreenedW, kTPivot, kTSigmaForms, kTSigmaExact, kTOzAhead, kTNumNames };
 const char* timed_name(int n);
 
 // A captured batch (bgw_epsilon_batch) replayed while its key is unchanged.

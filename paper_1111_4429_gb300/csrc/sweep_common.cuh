@@ -143,4 +143,146 @@ __device__ __forceinline__ void diag_sweep_smem_n(DiagSmem& sm, int kb, int t, i
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// The same sweep in double-FP32 arithmetic (a value is hi + lo, two floats,
+// about 2^-46 relative per operation) for updates whose target precision is
+// far coarser than FP64 (the five-slice tensor-core update, near 2^-34).
+// GB300's FP32 pipe issues 64 times the FP64 pipe's operations, so the
+// double-FP32 sweep, about 20 FP32 operations per FP64 multiply-add, leaves
+// the FP64 pipe, the sweep's limit, out of the step.  The error-free
+// transformations are Knuth's two-sum, the fast two-sum for |a| >= |b| and
+// the FMA product error.
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 ff_fast(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 ff_from(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double ff_to(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// a b
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return ff_fast(p, e);
+}
+// v + a b: the product as the pair (p, e) and the accurate pair sum (both
+// words two-summed, renormalized twice), which keeps its error relative to
+// the result when v and a b nearly cancel, as Schur-complement pivots do.
+__device__ __forceinline__ float2 ff_fma(float2 v, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  float2 s = ff_two_sum(v.x, p);
+  const float2 t = ff_two_sum(v.y, e);
+  s = ff_fast(s.x, __fadd_rn(s.y, t.x));
+  return ff_fast(s.x, __fadd_rn(s.y, t.y));
+}
+// 1 / d for d > 0: the FP32 reciprocal and one Newton step in double FP32
+__device__ __forceinline__ float2 ff_rcp(float2 d) {
+  const float r0 = __frcp_rn(d.x);
+  const float2 t = ff_mul(d, make_float2(r0, 0.f));                     // d r0 = 1 - err
+  const float2 e = ff_two_sum(1.f, -t.x);
+  const float err = __fsub_rn(__fadd_rn(e.x, e.y), t.y);               // 1 - d r0 (small)
+  return ff_fast(r0, __fmul_rn(r0, err));
+}
+
+// Double-FP32 form of diag_sweep_smem_n: converts the lower triangle of
+// sm.L in place (a double2 slot holds the four floats re_hi, re_lo, im_hi,
+// im_lo), sweeps, and converts back, so callers read and write sm.L as
+// double2 before and after.  Called by all NT threads after L (lower) is
+// loaded; ends with a __syncthreads().
+template <int NT>
+__device__ __forceinline__ void diag_sweep_ff_n(DiagSmem& sm, int kb, int t, int* status) {
+  constexpr int NE = (kSwNB * (kSwNB + 1) / 2 + NT - 1) / NT;
+  float4 (*L)[kSwNB + 1] = reinterpret_cast<float4 (*)[kSwNB + 1]>(sm.L);
+  float4* col = reinterpret_cast<float4*>(sm.col);
+  float4* ncolr = reinterpret_cast<float4*>(sm.ncolr);
+  float2* rpiv = reinterpret_cast<float2*>(&sm.rpiv);
+  int ei[NE], ej[NE];
+  bool el[NE];
+  __syncthreads();   // the caller's loads of L are visible before the conversion
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    diag_thread_element(t + q * NT, kb, ei[q], ej[q], el[q]);
+    if (el[q]) {
+      const double2 x = sm.L[ei[q]][ej[q]];
+      const float2 re = ff_from(x.x), im = ff_from(x.y);
+      L[ei[q]][ej[q]] = make_float4(re.x, re.y, im.x, im.y);
+    }
+  }
+  for (int s = 0; s < kb; ++s) {
+    __syncthreads();
+    if (t < kb) {
+      const int r = t;
+      float4 cv;
+      if (r > s) {
+        cv = L[r][s];
+      } else if (r < s) {
+        const float4 x = L[s][r];
+        cv = make_float4(x.x, x.y, -x.z, -x.w);
+      } else {
+        cv = L[s][s];
+      }
+      col[r] = cv;
+      const float2 d = make_float2(L[s][s].x, L[s][s].y);
+      float2 rr;
+      if (!(d.x > 0.f) || !isfinite(d.x)) {
+        if (r == 0) atomicExch(status, (int)kDevZeroPivot);
+        rr = make_float2(0.f, 0.f);
+      } else {
+        rr = ff_rcp(d);
+      }
+      // -conj(col_r) / d
+      const float2 nr = ff_mul(ff_neg(make_float2(cv.x, cv.y)), rr), ni = ff_mul(make_float2(cv.z, cv.w), rr);
+      ncolr[r] = make_float4(nr.x, nr.y, ni.x, ni.y);
+      if (r == s) *rpiv = rr;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NE; ++q) {
+      if (!el[q]) continue;
+      const int i = ei[q], j = ej[q];
+      if (i != s && j != s) {
+        const float4 a4 = col[i], c4 = ncolr[j], v4 = L[i][j];
+        const float2 ar = make_float2(a4.x, a4.y), ai = make_float2(a4.z, a4.w);
+        const float2 cr = make_float2(c4.x, c4.y), ci = make_float2(c4.z, c4.w);
+        float2 vr = make_float2(v4.x, v4.y), vi = make_float2(v4.z, v4.w);
+        vr = ff_fma(ff_fma(vr, ar, cr), ff_neg(ai), ci);   // + a_r c_r - a_i c_i
+        vi = ff_fma(ff_fma(vi, ar, ci), ai, cr);           // + a_r c_i + a_i c_r
+        L[i][j] = make_float4(vr.x, vr.y, vi.x, vi.y);
+      } else if (i == s && j == s) {
+        const float2 rp = *rpiv;
+        L[s][s] = make_float4(-rp.x, -rp.y, 0.f, 0.f);
+      } else if (j == s) {  // i > s: A_is / d
+        const float4 a4 = col[i];
+        const float2 rp = *rpiv;
+        const float2 xr = ff_mul(make_float2(a4.x, a4.y), rp), xi = ff_mul(make_float2(a4.z, a4.w), rp);
+        L[i][s] = make_float4(xr.x, xr.y, xi.x, xi.y);
+      } else {              // i == s, j < s: conj(col_j) / d
+        const float4 c4 = ncolr[j];
+        L[s][j] = make_float4(-c4.x, -c4.y, -c4.z, -c4.w);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    if (!el[q]) continue;
+    const float4 x = L[ei[q]][ej[q]];
+    sm.L[ei[q]][ej[q]] = make_double2(ff_to(make_float2(x.x, x.y)), ff_to(make_float2(x.z, x.w)));
+  }
+  __syncthreads();
+}
+
 }  // namespace bgw

@@ -602,7 +602,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
         const int rr = e / NB, c2 = e % NB;
         if (rr < kb1 && c2 <= rr) dsm.L[rr][c2] = M.A[(size_t)(k1 + rr) * ng + k1 + c2];
       }
-      diag_sweep_smem_n<kPipeThreads>(dsm, kb1, threadIdx.x, status);
+      // five slices (update error near 2^-34): the block's sweep in double
+      // FP32 (about 2^-46), off the SM's slow FP64 pipe; seven: FP64
+      if constexpr (SL < 7)
+        diag_sweep_ff_n<kPipeThreads>(dsm, kb1, threadIdx.x, status);
+      else
+        diag_sweep_smem_n<kPipeThreads>(dsm, kb1, threadIdx.x, status);
       for (int e = threadIdx.x; e < NB * NB; e += kPipeThreads) {
         const int rr = e / NB, c2 = e % NB;
         if (rr >= kb1 || c2 >= kb1) continue;
