@@ -140,10 +140,12 @@ __device__ __forceinline__ void digits7(long long X, __half* out, size_t stride)
 // Slices and exponent of one 64-value row held by a warp (lane: value k and
 // k + 32); all lanes call it.
 __device__ __forceinline__ void slice_row(double re, double im, int lane, __half* base, size_t stride, int* exp_out) {
-  double m = fmax(fabs(re), fabs(im));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);  // |value| 2^-e < 1
+  // e = frexp exponent of the row's largest magnitude, from the biased
+  // exponent fields (integer max over the warp; 0 for a zero row, and rows
+  // of subnormals alone are cut to zero)
+  const unsigned er = ((unsigned)__double2hiint(re) >> 20) & 0x7FFu, ei = ((unsigned)__double2hiint(im) >> 20) & 0x7FFu;
+  const unsigned emax = __reduce_max_sync(0xffffffffu, er > ei ? er : ei);
+  const int e = emax ? (int)emax - 1022 : 0;   // |value| 2^-e < 1
   const long long Xr = llrint(ldexp(re, 56 - e)), Xi = llrint(ldexp(im, 56 - e));
   digits7(Xr, base + lane, stride);
   digits7(Xi, base + lane + 32, stride);
@@ -156,10 +158,15 @@ __device__ __forceinline__ void slice_row(double re, double im, int lane, __half
 // P_i = C_i D^-1, the panel buffers and A_iK <- P_i written as the panel
 // kernel of the FP64 sweep does, then P_i and C_i cut into their slices.
 // Rows of K and padding rows get zero slices.  grid (ngpad/8, nmat).
+// FF: P_i = C_i D^-1 in double FP32 (the five-slice update, whose target
+// precision, near 2^-34, is far above the pair arithmetic's 2^-43): the
+// products as exact pairs, their high words two-summed and the errors
+// gathered in the low word; the FP64 pipe keeps only the conversions.
+template <bool FF>
 __global__ void __launch_bounds__(256) panel_slice_kernel(const __grid_constant__ OzBatch b, int k0, int rows_total,
                                                           int buf, __half* __restrict__ U, __half* __restrict__ V,
                                                           int* __restrict__ sig, int* __restrict__ tau) {
-  __shared__ double2 Ds[NB][NB];
+  __shared__ double2 Ds[NB][NB];   // FF: float4 (re hi, re lo, im hi, im lo)
   __shared__ double2 Cs[8][NB];
   const OzMat& M = b.m[blockIdx.y];
   const int ng = M.ng;
@@ -168,7 +175,15 @@ __global__ void __launch_bounds__(256) panel_slice_kernel(const __grid_constant_
   const int kb = min(NB, ng - k0);
   double2* A = M.A;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = M.Dinv[e];
+  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    const double2 d = M.Dinv[e];
+    if constexpr (FF) {
+      const float2 r = ff_from(d.x), m = ff_from(d.y);
+      reinterpret_cast<float4*>(&Ds[0][0])[e] = make_float4(r.x, r.y, m.x, m.y);
+    } else {
+      Ds[e / NB][e % NB] = d;
+    }
+  }
   const int i = blockIdx.x * 8 + warp;
   const bool row_ok = k0 < ng && i < ng && (i < k0 || i >= k0 + kb);
   double2 cv = make_double2(0.0, 0.0);
@@ -180,14 +195,42 @@ __global__ void __launch_bounds__(256) panel_slice_kernel(const __grid_constant_
       cv = make_double2(t.x, -t.y);
     }
   }
-  Cs[warp][lane] = cv;
+  if constexpr (FF) {
+    const float2 r = ff_from(cv.x), m = ff_from(cv.y);
+    reinterpret_cast<float4*>(&Cs[0][0])[warp * NB + lane] = make_float4(r.x, r.y, m.x, m.y);
+  } else {
+    Cs[warp][lane] = cv;
+  }
   __syncthreads();
   double2 pv = make_double2(0.0, 0.0);
   if (row_ok) {
-    for (int t = 0; t < kb; ++t) {
-      const double2 a = Cs[warp][t], d = Ds[t][lane];
-      pv.x = fma(a.x, d.x, fma(-a.y, d.y, pv.x));
-      pv.y = fma(a.x, d.y, fma(a.y, d.x, pv.y));
+    if constexpr (FF) {
+      const float4* Cf = reinterpret_cast<const float4*>(&Cs[0][0]) + warp * NB;
+      const float4* Df = reinterpret_cast<const float4*>(&Ds[0][0]);
+      float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;   // high word, gathered low terms
+      auto acc = [](float& S, float& c, float ah, float al, float bh, float bl) {
+        const float p = __fmul_rn(ah, bh);
+        float e = __fmaf_rn(ah, bh, -p);
+        e = __fmaf_rn(ah, bl, e);
+        e = __fmaf_rn(al, bh, e);
+        const float2 t = ff_two_sum(S, p);
+        S = t.x;
+        c = __fadd_rn(c, __fadd_rn(t.y, e));
+      };
+      for (int t = 0; t < kb; ++t) {
+        const float4 a = Cf[t], d = Df[t * NB + lane];
+        acc(sr, cr, a.x, a.y, d.x, d.y);     // + a_r d_r
+        acc(sr, cr, -a.z, -a.w, d.z, d.w);   // - a_i d_i
+        acc(si, ci, a.x, a.y, d.z, d.w);     // + a_r d_i
+        acc(si, ci, a.z, a.w, d.x, d.y);     // + a_i d_r
+      }
+      pv = make_double2((double)sr + (double)cr, (double)si + (double)ci);
+    } else {
+      for (int t = 0; t < kb; ++t) {
+        const double2 a = Cs[warp][t], d = Ds[t][lane];
+        pv.x = fma(a.x, d.x, fma(-a.y, d.y, pv.x));
+        pv.y = fma(a.x, d.y, fma(a.y, d.x, pv.y));
+      }
     }
     if (lane < kb) {
       const_cast<double2*>(M.C)[(size_t)i * NB + lane] = cv;
@@ -753,9 +796,14 @@ int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) 
 int oz_panel_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) {
   using namespace oz;
   const int rpad = (ngmax + BM - 1) / BM * BM;
-  panel_slice_kernel<<<dim3(rpad / 8, plan->nmat), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
-                                                                 plan->U.as<__half>(), plan->V.as<__half>(),
-                                                                 plan->sig.as<int>(), plan->tau.as<int>());
+  if (plan->slices < 7)
+    panel_slice_kernel<true><<<dim3(rpad / 8, plan->nmat), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
+                                                                         plan->U.as<__half>(), plan->V.as<__half>(),
+                                                                         plan->sig.as<int>(), plan->tau.as<int>());
+  else
+    panel_slice_kernel<false><<<dim3(rpad / 8, plan->nmat), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
+                                                                          plan->U.as<__half>(), plan->V.as<__half>(),
+                                                                          plan->sig.as<int>(), plan->tau.as<int>());
   BGW_CUDA(c, cudaGetLastError());
   return BGW_OK;
 }
