@@ -174,53 +174,64 @@ def flops_of(s):
 
 
 def _solve_steps(ctx, s, prec, steps, warmup, flush, timing):
-    """Timed one-q solves through bgw_mtxel / bgw_chi_sum / bgw_epsinv.
-    Returns per-step stage times [steps][3] (ms), the library's kernel-group
-    totals (when timing) and the last eps~^-1."""
+    """Timed one-q solves through bgw_mtxel / bgw_chi_sum / bgw_epsinv on a
+    dedicated stream (capturable: repeated bgw_epsinv calls replay a CUDA
+    graph).  Returns per-step stage times [steps][3] (ms), the library's
+    kernel-group totals (timing: from as many further steps run with
+    BGW_OPT_TIMING on, which run directly), the last eps~^-1 and the
+    library kernel launches of the timed steps."""
     import torch
     from paper_1111_4429_gb300 import bgw
     cell = bgw.system_cell(s)
-    st = torch.cuda.current_stream()
+    sstream = torch.cuda.Stream()
     cv = torch.from_numpy(s.cv).cuda()
     cc = torch.from_numpy(s.cc).cuda()
     cdt = torch.complex128 if prec == bgw.BGW_PREC_FP64 else torch.complex64
     M = torch.empty((s.npairs, s.ng), dtype=cdt, device="cuda")
     chi = torch.empty((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
     inv = torch.empty_like(chi)
+    torch.cuda.synchronize()
 
     def step(evs=None):
         if evs:
-            evs[0].record(st)
+            evs[0].record(sstream)
         ctx.mtxel(cell, s.gv, cv, s.gc, cc, s.geps, prec, M)
         if evs:
-            evs[1].record(st)
+            evs[1].record(sstream)
         ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, s.ec, None, prec, False, chi)
         if evs:
-            evs[2].record(st)
+            evs[2].record(sstream)
         ctx.epsinv([cell], [s.geps], [chi], None, [inv])
         if evs:
-            evs[3].record(st)
+            evs[3].record(sstream)
 
-    # the mixed precisions invert with the tensor-core trailing update (FP64-level
-    # accuracy), the plain path with FP64 FMA
+    # the mixed precisions invert with the tensor-core trailing update, the
+    # plain path with FP64 FMA
     ctx.set_option(bgw.BGW_OPT_INVERSE, 0 if prec == bgw.BGW_PREC_FP64 else 1)
     # the mixed solve's update slices: what bgw_epsilon uses after a mixed chi
     ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0 if prec == bgw.BGW_PREC_FP64 else UPDATE_SLICES_MIXED)
-    for _ in range(warmup):
-        step()
-    ctx.sync()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
-    ctx.set_option(bgw.BGW_OPT_TIMING, 1 if timing else 0)
-    ctx.timing_report(reset=True)
-    l0 = ctx.launch_count()
-    for k in range(steps):
-        flush.fill_(k & 0xff)       # evict L2 between steps (outside the events)
-        step(ev[k])
+    with torch.cuda.stream(sstream):
+        for _ in range(warmup):
+            step()
+        ctx.sync()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        l0 = ctx.launch_count()
+        for k in range(steps):
+            flush.fill_(k & 0xff)       # evict L2 between steps (outside the events)
+            step(ev[k])
+        sstream.synchronize()
+        launches = ctx.launch_count() - l0
+        kt = {}
+        if timing:
+            ctx.set_option(bgw.BGW_OPT_TIMING, 1)
+            ctx.timing_report(reset=True)
+            for k in range(steps):
+                flush.fill_(k & 0xff)
+                step()
+            sstream.synchronize()
+            kt = ctx.timing_report(reset=True)
+            ctx.set_option(bgw.BGW_OPT_TIMING, 0)
     torch.cuda.synchronize()
-    ctx.sync()
-    launches = ctx.launch_count() - l0
-    kt = ctx.timing_report(reset=True) if timing else {}
-    ctx.set_option(bgw.BGW_OPT_TIMING, 0)
     ctx.set_option(bgw.BGW_OPT_INVERSE, -1)
     ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0)
     stage = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in ev])

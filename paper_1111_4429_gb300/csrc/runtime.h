@@ -101,6 +101,7 @@ const char* timed_name(int n);
 // A captured batch (bgw_epsilon_batch) replayed while its key is unchanged.
 struct BatchGraph {
   cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;   // kernel launches the graph holds (added to the launch count per replay)
 };
 
 struct Ctx {

@@ -197,89 +197,110 @@ __device__ __forceinline__ float2 ff_rcp(float2 d) {
   return ff_fast(r0, __fmul_rn(r0, err));
 }
 
-// Double-FP32 form of diag_sweep_smem_n: converts the lower triangle of
-// sm.L in place (a double2 slot holds the four floats re_hi, re_lo, im_hi,
-// im_lo), sweeps, and converts back, so callers read and write sm.L as
-// double2 before and after.  Called by all NT threads after L (lower) is
-// loaded; ends with a __syncthreads().
+// v + a1 b1 + a2 b2 with both products as exact pairs and the high words
+// two-summed; the result is left unnormalized (hi, lo): lo gathers the
+// error terms, so hi + lo carries the sum to about 2^-43 of the largest
+// term, and consumers that need a leading word close to the value (the
+// pivot's reciprocal) renormalize it first.
+__device__ __forceinline__ float2 ff_dot2(float2 v, float2 a1, float2 b1, float2 a2, float2 b2) {
+  const float p1 = __fmul_rn(a1.x, b1.x);
+  float e1 = __fmaf_rn(a1.x, b1.x, -p1);
+  e1 = __fmaf_rn(a1.x, b1.y, e1);
+  e1 = __fmaf_rn(a1.y, b1.x, e1);
+  const float p2 = __fmul_rn(a2.x, b2.x);
+  float e2 = __fmaf_rn(a2.x, b2.x, -p2);
+  e2 = __fmaf_rn(a2.x, b2.y, e2);
+  e2 = __fmaf_rn(a2.y, b2.x, e2);
+  const float2 s1 = ff_two_sum(v.x, p1);
+  const float2 s2 = ff_two_sum(s1.x, p2);
+  return make_float2(s2.x, __fadd_rn(__fadd_rn(v.y, __fadd_rn(e1, e2)), __fadd_rn(s1.y, s2.y)));
+}
+
+// Double-FP32 form of diag_sweep_smem_n with one barrier per pivot: the
+// matrix ping-pongs between sm.L (as float4: re hi, re lo, im hi, im lo) and
+// the scratch buffer (32 x 33 float4, 16.9 KiB of shared memory the caller
+// does not need meanwhile).  Pivot s reads buffer s & 1 and writes every
+// lower element into the other; each thread forms the column entries it
+// needs itself, and the thread that writes the next pivot element forms its
+// reciprocal, so no step has a serial phase.  Converts sm.L from and back to
+// double2, so callers read and write sm.L as double2 before and after.
+// Called by all NT threads after L (lower) is loaded; ends with a
+// __syncthreads().  A non-positive or non-finite pivot sets *status.
 template <int NT>
-__device__ __forceinline__ void diag_sweep_ff_n(DiagSmem& sm, int kb, int t, int* status) {
+__device__ __forceinline__ void diag_sweep_ff_n(DiagSmem& sm, float4* scratch, int kb, int t, int* status) {
   constexpr int NE = (kSwNB * (kSwNB + 1) / 2 + NT - 1) / NT;
-  float4 (*L)[kSwNB + 1] = reinterpret_cast<float4 (*)[kSwNB + 1]>(sm.L);
-  float4* col = reinterpret_cast<float4*>(sm.col);
-  float4* ncolr = reinterpret_cast<float4*>(sm.ncolr);
-  float2* rpiv = reinterpret_cast<float2*>(&sm.rpiv);
+  typedef float4 Row[kSwNB + 1];
+  Row* const B0 = reinterpret_cast<Row*>(sm.L);
+  Row* const B1 = reinterpret_cast<Row*>(scratch);
+  float2* rps = reinterpret_cast<float2*>(sm.col);   // reciprocal of the pivot of step s in rps[s & 1]
   int ei[NE], ej[NE];
   bool el[NE];
   __syncthreads();   // the caller's loads of L are visible before the conversion
+  auto rcp_checked = [&](float2 d) {
+    d = ff_two_sum(d.x, d.y);   // leading word first (the pair may be unnormalized)
+    if (!(d.x > 0.f) || !isfinite(d.x)) {
+      atomicExch(status, (int)kDevZeroPivot);
+      return make_float2(0.f, 0.f);
+    }
+    return ff_rcp(d);
+  };
 #pragma unroll
   for (int q = 0; q < NE; ++q) {
     diag_thread_element(t + q * NT, kb, ei[q], ej[q], el[q]);
     if (el[q]) {
       const double2 x = sm.L[ei[q]][ej[q]];
       const float2 re = ff_from(x.x), im = ff_from(x.y);
-      L[ei[q]][ej[q]] = make_float4(re.x, re.y, im.x, im.y);
+      B0[ei[q]][ej[q]] = make_float4(re.x, re.y, im.x, im.y);
+      if (ei[q] == 0 && ej[q] == 0) rps[0] = rcp_checked(re);
     }
   }
   for (int s = 0; s < kb; ++s) {
     __syncthreads();
-    if (t < kb) {
-      const int r = t;
-      float4 cv;
-      if (r > s) {
-        cv = L[r][s];
-      } else if (r < s) {
-        const float4 x = L[s][r];
-        cv = make_float4(x.x, x.y, -x.z, -x.w);
-      } else {
-        cv = L[s][s];
-      }
-      col[r] = cv;
-      const float2 d = make_float2(L[s][s].x, L[s][s].y);
-      float2 rr;
-      if (!(d.x > 0.f) || !isfinite(d.x)) {
-        if (r == 0) atomicExch(status, (int)kDevZeroPivot);
-        rr = make_float2(0.f, 0.f);
-      } else {
-        rr = ff_rcp(d);
-      }
-      // -conj(col_r) / d
-      const float2 nr = ff_mul(ff_neg(make_float2(cv.x, cv.y)), rr), ni = ff_mul(make_float2(cv.z, cv.w), rr);
-      ncolr[r] = make_float4(nr.x, nr.y, ni.x, ni.y);
-      if (r == s) *rpiv = rr;
-    }
-    __syncthreads();
+    Row* const R = (s & 1) ? B1 : B0;   // selects, not an indexed array (kept out of local memory)
+    Row* const W = (s & 1) ? B0 : B1;
+    const float2 rp = rps[s & 1];
+    // column s of the full (Hermitian) matrix at index x: R[x][s] below the
+    // pivot, conj(R[s][x]) above it
+    auto col = [&](int x) {
+      const bool up = x < s;
+      const float4 v = up ? R[s][x] : R[x][s];
+      const float g = up ? -1.f : 1.f;
+      return make_float4(v.x, v.y, g * v.z, g * v.w);
+    };
 #pragma unroll
     for (int q = 0; q < NE; ++q) {
       if (!el[q]) continue;
       const int i = ei[q], j = ej[q];
+      float4 out;
       if (i != s && j != s) {
-        const float4 a4 = col[i], c4 = ncolr[j], v4 = L[i][j];
+        const float4 a4 = col(i), c4 = col(j), v4 = R[i][j];
+        // ncolr_j = -conj(col_j) / d
+        const float2 cr = ff_mul(ff_neg(make_float2(c4.x, c4.y)), rp), ci = ff_mul(make_float2(c4.z, c4.w), rp);
         const float2 ar = make_float2(a4.x, a4.y), ai = make_float2(a4.z, a4.w);
-        const float2 cr = make_float2(c4.x, c4.y), ci = make_float2(c4.z, c4.w);
-        float2 vr = make_float2(v4.x, v4.y), vi = make_float2(v4.z, v4.w);
-        vr = ff_fma(ff_fma(vr, ar, cr), ff_neg(ai), ci);   // + a_r c_r - a_i c_i
-        vi = ff_fma(ff_fma(vi, ar, ci), ai, cr);           // + a_r c_i + a_i c_r
-        L[i][j] = make_float4(vr.x, vr.y, vi.x, vi.y);
+        const float2 vr = ff_dot2(make_float2(v4.x, v4.y), ar, cr, ff_neg(ai), ci);   // + a_r c_r - a_i c_i
+        const float2 vi = ff_dot2(make_float2(v4.z, v4.w), ar, ci, ai, cr);           // + a_r c_i + a_i c_r
+        out = make_float4(vr.x, vr.y, vi.x, vi.y);
+        if (i == s + 1 && j == s + 1) rps[(s + 1) & 1] = rcp_checked(vr);
       } else if (i == s && j == s) {
-        const float2 rp = *rpiv;
-        L[s][s] = make_float4(-rp.x, -rp.y, 0.f, 0.f);
+        out = make_float4(-rp.x, -rp.y, 0.f, 0.f);
       } else if (j == s) {  // i > s: A_is / d
-        const float4 a4 = col[i];
-        const float2 rp = *rpiv;
+        const float4 a4 = R[i][s];
         const float2 xr = ff_mul(make_float2(a4.x, a4.y), rp), xi = ff_mul(make_float2(a4.z, a4.w), rp);
-        L[i][s] = make_float4(xr.x, xr.y, xi.x, xi.y);
+        out = make_float4(xr.x, xr.y, xi.x, xi.y);
       } else {              // i == s, j < s: conj(col_j) / d
-        const float4 c4 = ncolr[j];
-        L[s][j] = make_float4(-c4.x, -c4.y, -c4.z, -c4.w);
+        const float4 c4 = R[s][j];   // col_j = conj(R[s][j]); conj(col_j) = R[s][j]
+        const float2 xr = ff_mul(make_float2(c4.x, c4.y), rp), xi = ff_mul(make_float2(c4.z, c4.w), rp);
+        out = make_float4(xr.x, xr.y, xi.x, xi.y);
       }
+      W[i][j] = out;
     }
   }
   __syncthreads();
+  Row* const F = (kb & 1) ? B1 : B0;
 #pragma unroll
   for (int q = 0; q < NE; ++q) {
     if (!el[q]) continue;
-    const float4 x = L[ei[q]][ej[q]];
+    const float4 x = F[ei[q]][ej[q]];
     sm.L[ei[q]][ej[q]] = make_double2(ff_to(make_float2(x.x, x.y)), ff_to(make_float2(x.z, x.w)));
   }
   __syncthreads();

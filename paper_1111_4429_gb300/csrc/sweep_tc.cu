@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
       // five slices (update error near 2^-34): the block's sweep in double
       // FP32 (about 2^-46), off the SM's slow FP64 pipe; seven: FP64
       if constexpr (SL < 7)
-        diag_sweep_ff_n<kPipeThreads>(dsm, kb1, threadIdx.x, status);
+        diag_sweep_ff_n<kPipeThreads>(dsm, reinterpret_cast<float4*>(us), kb1, threadIdx.x, status);
       else
         diag_sweep_smem_n<kPipeThreads>(dsm, kb1, threadIdx.x, status);
       for (int e = threadIdx.x; e < NB * NB; e += kPipeThreads) {

@@ -317,3 +317,51 @@ def test_epsinv_tensor_core_update_five_slices(ctx, which):
     for r, a, b in zip(refs, inv5, inv7):
         assert _rel(a, r["epsinv"]) <= TOL64 * 2 ** 14
         assert _rel(b, r["epsinv"]) <= TOL64
+
+
+@pytest.mark.parametrize("slices", [5, 7])
+def test_epsinv_graph_replay_matches_direct(ctx, slices):
+    """On a capturable stream, repeated bgw_epsinv calls with the same
+    arguments replay a CUDA graph of the sweep: the replay reads the current
+    chi (same buffer, new contents) and gives the direct run's result bit for
+    bit, and the launch count grows by the graph's kernels."""
+    from paper_1111_4429_gb300 import bgw
+    systems = [synth.make_system("r", a=20.52, fft=40, ecut_wfn=8.0, ecut_eps=3.0, nv=4, nc=90, seed=88)]
+    s = systems[0]
+    r = oracle.solve(s)
+    chi_a = _dev(r["chi"])
+    chi_b = _dev(1.3 * r["chi"])
+    cell = bgw.system_cell(s)
+    buf = torch.empty_like(chi_a)
+    out = torch.empty_like(chi_a)
+    side = torch.cuda.Stream()
+    ctx.set_option(bgw.BGW_OPT_INVERSE, 1)
+    ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, slices)
+    try:
+        with torch.cuda.stream(side):
+            results = []
+            for src in (chi_a, chi_a, chi_b, chi_a):   # direct + capture, then replays
+                buf.copy_(src)
+                l0 = ctx.launch_count()
+                ctx.epsinv([cell], [s.geps], [buf], None, [out])
+                side.synchronize()
+                results.append((out.cpu().numpy().copy(), ctx.launch_count() - l0))
+        # direct results of the same inputs with graphs off (timing on runs directly)
+        ctx.set_option(bgw.BGW_OPT_TIMING, 1)
+        with torch.cuda.stream(side):
+            direct = []
+            for src in (chi_a, chi_b):
+                buf.copy_(src)
+                ctx.epsinv([cell], [s.geps], [buf], None, [out])
+                side.synchronize()
+                direct.append(out.cpu().numpy().copy())
+    finally:
+        ctx.set_option(bgw.BGW_OPT_TIMING, 0)
+        ctx.set_option(bgw.BGW_OPT_INVERSE, -1)
+        ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0)
+    assert np.array_equal(results[0][0], direct[0])
+    assert np.array_equal(results[1][0], direct[0])
+    assert np.array_equal(results[2][0], direct[1])
+    assert np.array_equal(results[3][0], direct[0])
+    assert results[1][1] == results[0][1] > 50   # a replay counts the graph's kernels
+    assert _rel(results[0][0], r["epsinv"]) <= TOL64 * (2 ** 14 if slices == 5 else 1)
