@@ -351,19 +351,23 @@ def run_ours(args):
                   "issued_tensor_tflops": issued / (kms["chi_tc"] / 1e3) / 1e12,
                   "issued_frac_of_measured_peak": issued / (kms["chi_tc"] / 1e3) / 1e12 / peaks["bf16_tflops"]}
 
-    # end to end through bgw_epsilon with pinned host buffers
+    # end to end through bgw_epsilon with pinned host buffers, on a stream of
+    # its own (repeated calls replay the library's graph of the whole path)
     cvh = torch.from_numpy(s.cv).pin_memory()
     cch = torch.from_numpy(s.cc).pin_memory()
     invh = torch.empty((1, s.ng, s.ng), dtype=torch.complex128).pin_memory()
-    for _ in range(2):
-        ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, prec, 0, None, invh)
-    e2e_steps = max(2, min(args.steps, 5))
+    es = torch.cuda.Stream()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, prec, 0, None, invh)
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    with torch.cuda.stream(es):
+        for _ in range(2):
+            ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, prec, 0, None, invh)
+        e2e_steps = max(2, min(args.steps, 5))
+        es.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, prec, 0, None, invh)
+        es.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
 
     batch = run_batch_c3(ctx, prec) if (ws == 1 and not args.skip_extra) else None
     f2 = run_f2(ctx, prec, flush) if (ws == 1 and not args.skip_extra) else None

@@ -137,8 +137,14 @@ int bgw_sync(bgw_ctx* ctx, void* stream);
 /* Bytes the library currently holds on the device, and the high-water mark. */
 int bgw_mem_stats(bgw_ctx* ctx, uint64_t* in_use, uint64_t* high_water);
 
-/* Number of kernels this context has launched since it was created.        */
+/* Number of kernels this context has launched since it was created (a CUDA
+ * graph replay counts the kernels the graph holds).                        */
 int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
+
+/* CUDA graphs the context holds (bgw_epsinv, bgw_epsilon and
+ * bgw_epsilon_batch capture one per argument set on capturable streams) and
+ * how many times they have been replayed.                                  */
+int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
 
 /* Tuning options of a context (EINVAL for an unknown option or value).
  *  BGW_OPT_CHI_SEGMENT_PAIRS: mixed-precision chi accumulates the products

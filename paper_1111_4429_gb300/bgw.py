@@ -24,6 +24,7 @@ PREC = {"fp64": BGW_PREC_FP64, "mix_fp16": BGW_PREC_MIX_FP16, "mix_bf16": BGW_PR
 
 # Every symbol include/bgw.h declares.
 EXPORTS = ("bgw_create", "bgw_destroy", "bgw_last_error", "bgw_sync", "bgw_mem_stats", "bgw_launch_count",
+           "bgw_graph_stats",
            "bgw_mtxel",
            "bgw_set_option", "bgw_timing_report", "bgw_chi_sum", "bgw_epsinv", "bgw_epsinv_noalloc", "bgw_screened_w",
            "bgw_chi_sum_real", "bgw_epsinv_general", "bgw_epsilon_real", "bgw_frequency_grid",
@@ -113,6 +114,7 @@ def load() -> ctypes.CDLL:
     lib.bgw_sync.argtypes = [vp, vp]
     lib.bgw_mem_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     lib.bgw_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.bgw_graph_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     lib.bgw_set_option.argtypes = [vp, ci, ctypes.c_int64]
     lib.bgw_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ci]
     lib.bgw_mtxel.argtypes = [vp, cellp, ci, ci, i32p, vp, ci, ci, i32p, vp, ci, i32p, ci, vp, vp]
@@ -254,6 +256,12 @@ class Context:
         a = ctypes.c_uint64()
         self._check(self.lib.bgw_launch_count(self.h, ctypes.byref(a)))
         return a.value
+
+    def graph_stats(self):
+        """(graphs held, replays so far): bgw_graph_stats."""
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self.lib.bgw_graph_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def set_option(self, option: int, value: int):
         self._check(self.lib.bgw_set_option(self.h, option, value))

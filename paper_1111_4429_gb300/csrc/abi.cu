@@ -167,6 +167,7 @@ int run_graphed(Ctx* c, uint64_t key, cudaStream_t st, const std::function<int()
   if (it != c->graphs.end()) {
     BGW_CUDA(c, cudaGraphLaunch(it->second.exec, st));
     c->launches += it->second.kernels;
+    c->graph_replays += 1;
     return BGW_OK;
   }
   int rc = body();
@@ -304,6 +305,16 @@ int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches) {
   Ctx* c = impl(ctx);
   if (!c || !launches) return BGW_EINVAL;
   *launches = c->launches;
+  return BGW_OK;
+}
+
+int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays) {
+  Ctx* c = impl(ctx);
+  if (!c || !graphs || !replays) return BGW_EINVAL;
+  uint64_t n = 0;
+  for (const auto& kv : c->graphs) n += kv.second.exec ? 1 : 0;
+  *graphs = n;
+  *replays = c->graph_replays;
   return BGW_OK;
 }
 
@@ -687,6 +698,7 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   if (it != c->graphs.end()) {
     BGW_CUDA(c, cudaGraphLaunch(it->second.exec, st));
     c->launches += it->second.kernels;
+    c->graph_replays += 1;
     return BGW_OK;
   }
   // Uploads of the small host arrays (cached by content).
@@ -777,95 +789,134 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
   DeviceGuard g(c->device);
   if (!g.ok) return fail(c, BGW_ECUDA, "cudaSetDevice failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int nrow = nfreq > 0 ? nfreq : 1;
-  // element sizes: coefficients, M, chi and eps~^-1 are real in the real flavor
-  const size_t coef = rf ? 8 : 16;
-  const size_t cs = (prec == BGW_PREC_FP64 ? 16 : 8) / (rf ? 2 : 1);
-  const size_t n2 = (size_t)ng * ng * (rf ? sizeof(double) : sizeof(double2));
   const bool cv_dev = is_device_ptr(cv), cc_dev = is_device_ptr(cc);
   const bool chi_dev = chi && is_device_ptr(chi), inv_dev = is_device_ptr(epsinv);
-  Scratch s_cv, s_cc, s_M, s_chi, s_inv;
-  s_cv.pool = s_cc.pool = s_M.pool = s_chi.pool = s_inv.pool = &c->pool;
-  const void* d_cv = cv;
-  const void* d_cc = cc;
-  if (!cv_dev) {
-    if ((rc = c->pool.alloc((size_t)nv * npw_v * coef, &s_cv.ptr)) != BGW_OK) return fail(c, rc, "cv staging");
-    BGW_CUDA(c, cudaMemcpyAsync(s_cv.ptr, cv, (size_t)nv * npw_v * coef, cudaMemcpyHostToDevice, st));
-    d_cv = s_cv.ptr;
-  }
-  if (!cc_dev) {
-    if ((rc = c->pool.alloc((size_t)nc * npw_c * coef, &s_cc.ptr)) != BGW_OK) return fail(c, rc, "cc staging");
-    BGW_CUDA(c, cudaMemcpyAsync(s_cc.ptr, cc, (size_t)nc * npw_c * coef, cudaMemcpyHostToDevice, st));
-    d_cc = s_cc.ptr;
-  }
-  void* d_chi = chi_dev ? chi : nullptr;
-  if (!d_chi) {
-    if ((rc = c->pool.alloc(nrow * n2, &s_chi.ptr)) != BGW_OK) return fail(c, rc, "chi scratch");
-    d_chi = s_chi.ptr;
-  }
-  void* d_inv = inv_dev ? epsinv : nullptr;
-  if (!d_inv) {
-    if ((rc = c->pool.alloc(nrow * n2, &s_inv.ptr)) != BGW_OK) return fail(c, rc, "epsinv scratch");
-    d_inv = s_inv.ptr;
-  }
-  if ((rc = c->pool.alloc((size_t)nv * nc_chunk * ng * cs, &s_M.ptr)) != BGW_OK) return fail(c, rc, "M scratch");
-  const BandPlan *bpv, *bpc;
-  const PairPlan* pp;
-  if ((rc = get_band_plan(c, n, npw_v, gv, st, &bpv)) != BGW_OK) return rc;
-  if ((rc = get_band_plan(c, n, npw_c, gc, st, &bpc)) != BGW_OK) return rc;
-  if ((rc = get_pair_plan(c, n, ng, geps, st, &pp)) != BGW_OK) return rc;
-  const void *dev_ev, *dev_ec, *dev_om = nullptr, *dev_geps;
-  if ((rc = upload_cached(c, ev, nv * sizeof(double), st, &dev_ev)) != BGW_OK) return rc;
-  if ((rc = upload_cached(c, ec, nc * sizeof(double), st, &dev_ec)) != BGW_OK) return rc;
-  if (nfreq > 0 && (rc = upload_cached(c, omega, nfreq * sizeof(double), st, &dev_om)) != BGW_OK) return rc;
-  if ((rc = upload_cached(c, geps, (size_t)ng * 3 * sizeof(int32_t), st, &dev_geps)) != BGW_OK) return rc;
-  HeadPlan hp;
-  Scratch s_h;
-  s_h.pool = &c->pool;
-  if (!fa.real && !rf && (rc = head_prepare(c, cell, npw_v, gv, npw_c, gc, ng, geps, prec, st, &hp)) != BGW_OK) return rc;
-  if (hp.g0 >= 0 && (rc = c->pool.alloc((size_t)nv * nc_chunk * sizeof(double2), &s_h.ptr)) != BGW_OK)
-    return fail(c, rc, "head scratch");
-  for (int c0 = 0; c0 < nc; c0 += nc_chunk) {
-    const int ncc = std::min(nc_chunk, nc - c0);
-    const void* cc0 = static_cast<const char*>(d_cc) + (size_t)c0 * npw_c * coef;
-    if ((rc = mtxel_run(c, n, prec, nv, bpv, d_cv, ncc, bpc, cc0, pp, s_M.ptr, st, rf)) != BGW_OK) return rc;
-    if (hp.g0 >= 0 &&
-        (rc = head_dot(c, &hp, nv, d_cv, npw_v, ncc, cc0, ng, s_M.ptr, s_h.as<double2>(), st)) != BGW_OK)
-      return rc;
-    if (fa.real)
-      rc = chi_real_run(c, prec, nv, ncc, ng, s_M.ptr, static_cast<const double*>(dev_ev),
-                        static_cast<const double*>(dev_ec) + c0, nfreq, static_cast<const double*>(dev_om), fa.delta,
-                        fa.advanced, 4.0 / cell->omega, c0 > 0, d_chi, st);
-    else
-      rc = chi_run(c, prec, nv, ncc, ng, s_M.ptr, static_cast<const double*>(dev_ev),
-                   static_cast<const double*>(dev_ec) + c0, nfreq, static_cast<const double*>(dev_om),
-                   4.0 / cell->omega, c0 > 0, d_chi, st, &hp, s_h.as<double2>(), rf);
-    if (rc != BGW_OK) return rc;
-  }
-  {
-    std::vector<int> ngv(nrow, ng);
-    std::vector<const bgw_cell*> cp(nrow, cell);
-    std::vector<const int32_t*> gv2(nrow, static_cast<const int32_t*>(dev_geps));
-    std::vector<const void*> chis(nrow);
-    std::vector<void*> invs(nrow);
-    for (int f = 0; f < nrow; ++f) {
-      chis[f] = static_cast<char*>(d_chi) + f * n2;
-      invs[f] = static_cast<char*>(d_inv) + f * n2;
+  auto body = [&]() -> int {
+    int rc;
+    const int nrow = nfreq > 0 ? nfreq : 1;
+    // element sizes: coefficients, M, chi and eps~^-1 are real in the real flavor
+    const size_t coef = rf ? 8 : 16;
+    const size_t cs = (prec == BGW_PREC_FP64 ? 16 : 8) / (rf ? 2 : 1);
+    const size_t n2 = (size_t)ng * ng * (rf ? sizeof(double) : sizeof(double2));
+    Scratch s_cv, s_cc, s_M, s_chi, s_inv;
+    s_cv.pool = s_cc.pool = s_M.pool = s_chi.pool = s_inv.pool = &c->pool;
+    const void* d_cv = cv;
+    const void* d_cc = cc;
+    if (!cv_dev) {
+      if ((rc = c->pool.alloc((size_t)nv * npw_v * coef, &s_cv.ptr)) != BGW_OK) return fail(c, rc, "cv staging");
+      BGW_CUDA(c, cudaMemcpyAsync(s_cv.ptr, cv, (size_t)nv * npw_v * coef, cudaMemcpyHostToDevice, st));
+      d_cv = s_cv.ptr;
     }
-    set_run_slices(c, prec);
-    if (fa.real)
-      rc = epsinv_general_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
+    if (!cc_dev) {
+      if ((rc = c->pool.alloc((size_t)nc * npw_c * coef, &s_cc.ptr)) != BGW_OK) return fail(c, rc, "cc staging");
+      BGW_CUDA(c, cudaMemcpyAsync(s_cc.ptr, cc, (size_t)nc * npw_c * coef, cudaMemcpyHostToDevice, st));
+      d_cc = s_cc.ptr;
+    }
+    void* d_chi = chi_dev ? chi : nullptr;
+    if (!d_chi) {
+      if ((rc = c->pool.alloc(nrow * n2, &s_chi.ptr)) != BGW_OK) return fail(c, rc, "chi scratch");
+      d_chi = s_chi.ptr;
+    }
+    void* d_inv = inv_dev ? epsinv : nullptr;
+    if (!d_inv) {
+      if ((rc = c->pool.alloc(nrow * n2, &s_inv.ptr)) != BGW_OK) return fail(c, rc, "epsinv scratch");
+      d_inv = s_inv.ptr;
+    }
+    if ((rc = c->pool.alloc((size_t)nv * nc_chunk * ng * cs, &s_M.ptr)) != BGW_OK) return fail(c, rc, "M scratch");
+    const BandPlan *bpv, *bpc;
+    const PairPlan* pp;
+    if ((rc = get_band_plan(c, n, npw_v, gv, st, &bpv)) != BGW_OK) return rc;
+    if ((rc = get_band_plan(c, n, npw_c, gc, st, &bpc)) != BGW_OK) return rc;
+    if ((rc = get_pair_plan(c, n, ng, geps, st, &pp)) != BGW_OK) return rc;
+    const void *dev_ev, *dev_ec, *dev_om = nullptr, *dev_geps;
+    if ((rc = upload_cached(c, ev, nv * sizeof(double), st, &dev_ev)) != BGW_OK) return rc;
+    if ((rc = upload_cached(c, ec, nc * sizeof(double), st, &dev_ec)) != BGW_OK) return rc;
+    if (nfreq > 0 && (rc = upload_cached(c, omega, nfreq * sizeof(double), st, &dev_om)) != BGW_OK) return rc;
+    if ((rc = upload_cached(c, geps, (size_t)ng * 3 * sizeof(int32_t), st, &dev_geps)) != BGW_OK) return rc;
+    HeadPlan hp;
+    Scratch s_h;
+    s_h.pool = &c->pool;
+    if (!fa.real && !rf && (rc = head_prepare(c, cell, npw_v, gv, npw_c, gc, ng, geps, prec, st, &hp)) != BGW_OK) return rc;
+    if (hp.g0 >= 0 && (rc = c->pool.alloc((size_t)nv * nc_chunk * sizeof(double2), &s_h.ptr)) != BGW_OK)
+      return fail(c, rc, "head scratch");
+    for (int c0 = 0; c0 < nc; c0 += nc_chunk) {
+      const int ncc = std::min(nc_chunk, nc - c0);
+      const void* cc0 = static_cast<const char*>(d_cc) + (size_t)c0 * npw_c * coef;
+      if ((rc = mtxel_run(c, n, prec, nv, bpv, d_cv, ncc, bpc, cc0, pp, s_M.ptr, st, rf)) != BGW_OK) return rc;
+      if (hp.g0 >= 0 &&
+          (rc = head_dot(c, &hp, nv, d_cv, npw_v, ncc, cc0, ng, s_M.ptr, s_h.as<double2>(), st)) != BGW_OK)
+        return rc;
+      if (fa.real)
+        rc = chi_real_run(c, prec, nv, ncc, ng, s_M.ptr, static_cast<const double*>(dev_ev),
+                          static_cast<const double*>(dev_ec) + c0, nfreq, static_cast<const double*>(dev_om), fa.delta,
+                          fa.advanced, 4.0 / cell->omega, c0 > 0, d_chi, st);
+      else
+        rc = chi_run(c, prec, nv, ncc, ng, s_M.ptr, static_cast<const double*>(dev_ev),
+                     static_cast<const double*>(dev_ec) + c0, nfreq, static_cast<const double*>(dev_om),
+                     4.0 / cell->omega, c0 > 0, d_chi, st, &hp, s_h.as<double2>(), rf);
+      if (rc != BGW_OK) return rc;
+    }
+    {
+      std::vector<int> ngv(nrow, ng);
+      std::vector<const bgw_cell*> cp(nrow, cell);
+      std::vector<const int32_t*> gv2(nrow, static_cast<const int32_t*>(dev_geps));
+      std::vector<const void*> chis(nrow);
+      std::vector<void*> invs(nrow);
+      for (int f = 0; f < nrow; ++f) {
+        chis[f] = static_cast<char*>(d_chi) + f * n2;
+        invs[f] = static_cast<char*>(d_inv) + f * n2;
+      }
+      set_run_slices(c, prec);
+      if (fa.real)
+        rc = epsinv_general_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
+                                use_tc_inverse(c, prec));
+      else if (rf)
+        rc = epsinv_rflavor_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
+                                use_tc_inverse(c, prec));
+      else
+        rc = epsinv_batch_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
                               use_tc_inverse(c, prec));
-    else if (rf)
-      rc = epsinv_rflavor_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
-                              use_tc_inverse(c, prec));
-    else
-      rc = epsinv_batch_run(c, nrow, ngv.data(), cp.data(), gv2.data(), chis.data(), nullptr, invs.data(), st,
-                            use_tc_inverse(c, prec));
-    if (rc != BGW_OK) return rc;
+      if (rc != BGW_OK) return rc;
+    }
+    if (chi && !chi_dev) BGW_CUDA(c, cudaMemcpyAsync(chi, d_chi, nrow * n2, cudaMemcpyDeviceToHost, st));
+    if (!inv_dev) BGW_CUDA(c, cudaMemcpyAsync(epsinv, d_inv, nrow * n2, cudaMemcpyDeviceToHost, st));
+    return BGW_OK;
+  };
+  // Repeated calls with the same arguments replay a CUDA graph of the whole
+  // path (copies included) when every host buffer is page-locked: the key
+  // holds the sizes, the pointers and the small host arrays' contents; the
+  // large coefficient and result buffers are read and written in place.
+  auto pinned_or_dev = [](const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged || at.type == cudaMemoryTypeHost;
+  };
+  const bool graphable = pinned_or_dev(cv) && pinned_or_dev(cc) && pinned_or_dev(chi) && pinned_or_dev(epsinv);
+  if (graphable) {
+    uint64_t key = hash_bytes("epsilon", 7, hash_bytes(cell, sizeof(bgw_cell)));
+    const int dims[10] = {nv, npw_v, nc, npw_c, ng, nfreq, prec | (rf ? BGW_FLAVOR_REAL : 0), nc_chunk,
+                          fa.real ? 1 : 0, fa.advanced};
+    key = hash_bytes(dims, sizeof(dims), key);
+    key = hash_bytes(&fa.delta, sizeof(double), key);
+    if (nfreq > 0) key = hash_bytes(omega, nfreq * sizeof(double), key);
+    const void* ptrs[5] = {cv, cc, chi, epsinv, (const void*)st};
+    key = hash_bytes(ptrs, sizeof(ptrs), key);
+    const int modes[3] = {c->inverse_mode, c->head_mode, c->update_slices};
+    key = hash_bytes(modes, sizeof(modes), key);
+    key = hash_bytes(gv, (size_t)npw_v * 12, key);
+    key = hash_bytes(gc, (size_t)npw_c * 12, key);
+    key = hash_bytes(geps, (size_t)ng * 12, key);
+    key = hash_bytes(ev, (size_t)nv * 8, key);
+    key = hash_bytes(ec, (size_t)nc * 8, key);
+    rc = run_graphed(c, key, st, body);
+  } else {
+    rc = body();
   }
-  if (chi && !chi_dev) BGW_CUDA(c, cudaMemcpyAsync(chi, d_chi, nrow * n2, cudaMemcpyDeviceToHost, st));
-  if (!inv_dev) BGW_CUDA(c, cudaMemcpyAsync(epsinv, d_inv, nrow * n2, cudaMemcpyDeviceToHost, st));
+  if (rc != BGW_OK) return rc;
   if (!inv_dev || (chi && !chi_dev)) return bgw_sync(ctx, stream);
   return BGW_OK;
 }

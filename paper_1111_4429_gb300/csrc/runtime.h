@@ -108,6 +108,7 @@ struct Ctx {
   int device = 0;
   Timing timing;
   std::unordered_map<uint64_t, BatchGraph> graphs;
+  uint64_t graph_replays = 0;
   std::map<std::tuple<int, int, int, int>, int> tuned_ppb;  // (n, prec, nys, ncol) -> pairs per CTA
   bool autotune = true;
   cudaStream_t side = nullptr;     // high-priority stream of the sweep's look-ahead chain

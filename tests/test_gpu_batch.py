@@ -92,3 +92,39 @@ def test_batch_graph_replay_and_fresh_inputs(ctx):
         ref = _oracle(o, om)
         for f in range(2):
             assert _rel(out[f].cpu().numpy(), ref[f]) <= 1e-6
+
+
+def test_epsilon_host_buffers_graph_replay(ctx):
+    """bgw_epsilon with page-locked host buffers on a capturable stream: the
+    second call replays a graph of the whole path (copies included); new
+    host coefficients in the same buffers give the direct result bit for bit."""
+    from paper_1111_4429_gb300 import bgw
+    s = synth.config_system("c0")
+    cell = bgw.system_cell(s)
+    cvh = torch.from_numpy(s.cv).pin_memory()
+    cch = torch.from_numpy(s.cc).pin_memory()
+    out = torch.empty((1, s.ng, s.ng), dtype=torch.complex128).pin_memory()
+    st = torch.cuda.Stream()
+    res = []
+    g0 = ctx.graph_stats()
+    with torch.cuda.stream(st):
+        for k in range(3):
+            if k == 2:   # new contents, same buffers: scrambled phases of the same bands
+                cvh.mul_(torch.exp(1j * torch.arange(cvh.shape[0], dtype=torch.float64))[:, None])
+            l0 = ctx.launch_count()
+            ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, 1, 0, None, out)
+            res.append((out.clone(), ctx.launch_count() - l0))
+    ctx.set_option(bgw.BGW_OPT_TIMING, 1)   # timing on: direct runs
+    try:
+        with torch.cuda.stream(st):
+            ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, 1, 0, None, out)
+            direct = out.clone()
+    finally:
+        ctx.set_option(bgw.BGW_OPT_TIMING, 0)
+    g1 = ctx.graph_stats()
+    assert g1[0] == g0[0] + 1 and g1[1] == g0[1] + 2   # one graph, replayed by the second and third calls
+    assert torch.equal(res[0][0], res[1][0])
+    assert torch.equal(res[2][0], direct)
+    assert res[1][1] > 0
+    # a band phase does not change chi: the result stays that of the first inputs up to rounding
+    assert float((res[2][0] - res[0][0]).abs().max()) <= 1e-6 * float(res[0][0].abs().max())

@@ -340,12 +340,14 @@ def test_epsinv_graph_replay_matches_direct(ctx, slices):
     try:
         with torch.cuda.stream(side):
             results = []
+            g0 = ctx.graph_stats()
             for src in (chi_a, chi_a, chi_b, chi_a):   # direct + capture, then replays
                 buf.copy_(src)
                 l0 = ctx.launch_count()
                 ctx.epsinv([cell], [s.geps], [buf], None, [out])
                 side.synchronize()
                 results.append((out.cpu().numpy().copy(), ctx.launch_count() - l0))
+            g1 = ctx.graph_stats()
         # direct results of the same inputs with graphs off (timing on runs directly)
         ctx.set_option(bgw.BGW_OPT_TIMING, 1)
         with torch.cuda.stream(side):
@@ -364,4 +366,5 @@ def test_epsinv_graph_replay_matches_direct(ctx, slices):
     assert np.array_equal(results[2][0], direct[1])
     assert np.array_equal(results[3][0], direct[0])
     assert results[1][1] == results[0][1] > 50   # a replay counts the graph's kernels
+    assert g1[1] == g0[1] + 3                        # calls 2-4 replayed
     assert _rel(results[0][0], r["epsinv"]) <= TOL64 * (2 ** 14 if slices == 5 else 1)
