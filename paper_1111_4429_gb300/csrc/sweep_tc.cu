@@ -320,7 +320,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // MMAs start -- and apply the FP64 subtraction while they run.
 constexpr int kPipeEpiWarps = 16;
 constexpr int kPipeThreads = (kPipeEpiWarps + 1) * 32;
-constexpr int kJPI = 4;   // most column tiles per work item (mode 1 uses 2: its CTAs are on the critical path)
+constexpr int kJPI = 3;   // most column tiles per work item (mode 1 uses 2: its CTAs are on the critical path)
 
 __device__ __forceinline__ int row_width(int mode, int I, int nJ) { return mode == 3 ? nJ : min(4 * I + 4, nJ); }
 
