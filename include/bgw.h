@@ -142,8 +142,11 @@ int bgw_mem_stats(bgw_ctx* ctx, uint64_t* in_use, uint64_t* high_water);
 int bgw_launch_count(bgw_ctx* ctx, uint64_t* launches);
 
 /* CUDA graphs the context holds (bgw_epsinv, bgw_epsilon and
- * bgw_epsilon_batch capture one per argument set on capturable streams) and
- * how many times they have been replayed.                                  */
+ * bgw_epsilon_batch capture one per argument set on capturable streams, up
+ * to 8 per context; each keeps the pool blocks it uses until
+ * bgw_destroy; the server's slot contexts capture none) and how many times
+ * they have been replayed.  A replay reads and writes the buffers at the
+ * captured addresses: its key matches only calls with the same pointers.   */
 int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
 
 /* Tuning options of a context (EINVAL for an unknown option or value).

@@ -162,7 +162,7 @@ int validate_mtxel(Ctx* c, const bgw_cell* cell, int nv, int npw_v, const int32_
 // pinned for the graph's life.  With BGW_OPT_TIMING on, or on the legacy
 // default stream (not capturable), every call runs directly.
 int run_graphed(Ctx* c, uint64_t key, cudaStream_t st, const std::function<int()>& body) {
-  if (c->timing.on || st == nullptr || st == cudaStreamLegacy) return body();
+  if (!c->use_graphs || c->timing.on || st == nullptr || st == cudaStreamLegacy) return body();
   auto it = c->graphs.find(key);
   if (it != c->graphs.end()) {
     BGW_CUDA(c, cudaGraphLaunch(it->second.exec, st));
@@ -172,6 +172,7 @@ int run_graphed(Ctx* c, uint64_t key, cudaStream_t st, const std::function<int()
   }
   int rc = body();
   if (rc != BGW_OK) return rc;
+  if (c->graphs.size() >= kMaxGraphs) return BGW_OK;   // no more pinned scratch: run directly
   c->pool.set_pinning(true);
   const uint64_t l0 = c->launches;
   cudaGraph_t graph = nullptr;
@@ -694,7 +695,7 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
     key = hash_bytes(p.ev, (size_t)p.nv * 8, key);
     key = hash_bytes(p.ec, (size_t)p.nc * 8, key);
   }
-  auto it = c->graphs.find(key);
+  auto it = c->use_graphs ? c->graphs.find(key) : c->graphs.end();
   if (it != c->graphs.end()) {
     BGW_CUDA(c, cudaGraphLaunch(it->second.exec, st));
     c->launches += it->second.kernels;
@@ -717,6 +718,7 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
                       dev_geps, st)) != BGW_OK)
     return rc;
   if (st == nullptr || st == cudaStreamLegacy) return BGW_OK;  // the legacy stream cannot be captured
+  if (!c->use_graphs || c->graphs.size() >= kMaxGraphs) return BGW_OK;
   const bool timing = c->timing.on;
   c->timing.on = false;
   c->pool.set_pinning(true);

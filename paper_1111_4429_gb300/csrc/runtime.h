@@ -99,6 +99,7 @@ enum TimedName { kTBand = 0, kTPairYX, kTPairZ, kTChiF64, kTChiSplit, kTChiTc, k
 const char* timed_name(int n);
 
 // A captured batch (bgw_epsilon_batch) replayed while its key is unchanged.
+constexpr size_t kMaxGraphs = 8;   // graphs one context keeps (each pins the pool blocks it uses)
 struct BatchGraph {
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels = 0;   // kernel launches the graph holds (added to the launch count per replay)
@@ -109,6 +110,7 @@ struct Ctx {
   Timing timing;
   std::unordered_map<uint64_t, BatchGraph> graphs;
   uint64_t graph_replays = 0;
+  bool use_graphs = true;          // false in the server's slot contexts (one-shot buffers per request)
   std::map<std::tuple<int, int, int, int>, int> tuned_ppb;  // (n, prec, nys, ncol) -> pairs per CTA
   bool autotune = true;
   cudaStream_t side = nullptr;     // high-priority stream of the sweep's look-ahead chain

@@ -262,6 +262,9 @@ int bgw_serve_open(int device, const bgw_serve_opts* opts, bgw_server** out) {
   for (auto& sl : s->slots) {
     int rc = bgw_create(&sl.ctx, device, 0);
     if (rc != BGW_OK) return rc;
+    // requests bring their own device buffers (one-shot pool blocks), so a
+    // graph per argument set would pin scratch without being replayed
+    sl.ctx->impl.use_graphs = false;
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
       return BGW_ECUDA;
