@@ -50,9 +50,10 @@ def _peaks():
 # Slices per value of the tensor-core update in the mixed solves (the
 # library's default after a mixed-precision chi).
 UPDATE_SLICES_MIXED = 5
-# DRAM bytes of one bulk update launch (ncu, N_G = 2120), or None until the
-# current kernel has been captured.
-OZ_TRAFFIC_LAUNCH = None
+# DRAM bytes of one bulk update launch at N_G = 2120 (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of the current kernel, the
+# inverse of the profile case: 36.04 MB + 0.20 MB).
+OZ_TRAFFIC_LAUNCH = 36.24e6
 
 
 def oz_tiles(ng, k0):
