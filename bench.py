@@ -309,14 +309,16 @@ def run_ours(args):
         oz_traffic_step = OZ_TRAFFIC_LAUNCH if s.ng == 2120 else None
         roof = {"bound": "tensor", "kernel": f"oz::update_pipe_kernel<{sl} slices> (tcgen05 kind::f16 M128 N32: the "
                                              "sweep's trailing update from exact FP16 slices)",
-                "achieved": issued_step / t_step / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "achieved": issued_step / t_step / 1e12, "peak": peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]),
+                "unit": "TFLOP/s",
                 "algorithmic": f"issued tensor flops: the bulk launch's 128x32 tiles (mean {bulk_tiles / nsteps:.0f} "
                                f"per sweep step) x {pairs * 8} MMAs x 2x128x32x16 ({pairs} slice pairs per FP64 "
                                f"product)",
                 "look_ahead_launch_us": (kt["oz_update_ahead"][1] / kt["oz_update_ahead"][0] * 1e3
                                          if "oz_update_ahead" in kt else None),
                 "bulk_launch_us": t_launch * 1e6,
-                "peak_source": "measured bf16 burst (fp16 has the same nominal rate)",
+                "peak_source": f"{peak_src} bf16 sustained (the kernel is timed inside back-to-back solves; fp16 has "
+                               "the same nominal rate)",
                 "fp64_equivalent_tflops": bulk_tiles / nsteps * 4.0 * 32 * 128 * 32 / t_step / 1e12,
                 "fp64_pipe_peak_tflops": FP64_PEAK_TFLOPS,
                 "traffic_bytes_per_sweep_step": oz_traffic_step}
@@ -332,9 +334,10 @@ def run_ours(args):
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz"}
     elif dom == "chi_tc":
         roof = {"bound": "tensor", "kernel": "chi_tc_kernel (tcgen05 kind::f16)",
-                "achieved": fl["chi_herm"] / (kms[dom] / 1e3) / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "achieved": fl["chi_herm"] / (kms[dom] / 1e3) / 1e12,
+                "peak": peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), "unit": "TFLOP/s",
                 "algorithmic": "4 N_G^2 K flop (Hermitian lower triangle)",
-                "peak_source": "measured bf16 burst (fp16 has the same nominal rate)"}
+                "peak_source": f"{peak_src} bf16 sustained (fp16 has the same nominal rate)"}
     else:
         roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": "TFLOP/s"}
     if roof.get("achieved") is not None:
