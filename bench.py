@@ -809,7 +809,9 @@ def run_profile_case(args):
                pairs, M = 217 MB > L2, about 1.5 GB on the device);
     general -- one pivoted general inverse (bgw_epsinv_general, tensor-core
                update) of a seeded random complex N_G = 2120 chi;
-    w       -- bgw_screened_w on 8 seeded random N_G = 2120 matrices."""
+    w       -- bgw_screened_w on 8 seeded random N_G = 2120 matrices;
+    sigma   -- bgw_sigma_cohsex, mixed, on the c1 cell (8 outer x 832 inner
+               bands, N_G = 2120) with a seeded random Hermitian eps~^-1."""
     import torch
     from paper_1111_4429_gb300 import bgw, synth
     ctx = bgw.Context(0)
@@ -843,6 +845,15 @@ def run_profile_case(args):
             for _ in range(2):
                 ctx.epsinv_general([cell], [s.geps], [x], None, [inv])
             desc = "general inverse N_G=2120, tensor-core update"
+        elif case == "sigma":
+            z = torch.randn((ng, ng), dtype=torch.complex128, device="cuda", generator=gen) * 1e-2
+            ei = torch.eye(ng, dtype=torch.complex128, device="cuda") + z + z.conj().T
+            sb = synth.sigma_bands(s, 8, 832, 32, seed=2001)
+            co = torch.from_numpy(sb.co).cuda()
+            ci = torch.from_numpy(sb.ci).cuda()
+            for _ in range(2):
+                ctx.sigma_cohsex(cell, sb.go, co, sb.gi, ci, sb.nocc, s.geps, ei, prec=bgw.PREC[args.prec])
+            desc = "Sigma COHSEX, c1 cell, 8 x 832 bands"
         else:
             x = torch.randn((8, ng, ng), dtype=torch.complex128, device="cuda", generator=gen)
             w = torch.empty_like(x)
@@ -862,9 +873,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="mix_fp16", choices=["fp64", "mix_fp16", "mix_bf16"])
     ap.add_argument("--skip-extra", action="store_true", help="skip the batched q x iw and served-stream parts")
-    ap.add_argument("--profile-case", nargs="?", const="solve", default=None, choices=["solve", "general", "w"],
+    ap.add_argument("--profile-case", nargs="?", const="solve", default=None,
+                    choices=["solve", "general", "w", "sigma"],
                     help="small case for ncu captures (solve: reduced c1 solve; general: one pivoted general "
-                         "inverse; w: screened W on 8 matrices)")
+                         "inverse; w: screened W on 8 matrices; sigma: one mixed Sigma call)")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
