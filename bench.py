@@ -48,12 +48,12 @@ def _peaks():
 
 
 # Slices per value of the tensor-core update in the mixed solves (the
-# library's default after a mixed-precision chi).
-UPDATE_SLICES_MIXED = 5
+# library's default: FP64-level updates).
+UPDATE_SLICES_MIXED = 7
 # DRAM bytes of one bulk update launch at N_G = 2120 (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture of the current kernel, the
-# inverse of the profile case: 36.04 MB + 0.20 MB).
-OZ_TRAFFIC_LAUNCH = 36.24e6
+# dram__bytes_write.sum of one ncu capture of the current seven-slice kernel,
+# the inverse of the profile case: 37.08 MB + 0.21 MB).
+OZ_TRAFFIC_LAUNCH = 37.29e6
 
 
 def oz_tiles(ng, k0):
@@ -209,8 +209,10 @@ def _solve_steps(ctx, s, prec, steps, warmup, flush, timing):
     # the mixed precisions invert with the tensor-core trailing update, the
     # plain path with FP64 FMA
     ctx.set_option(bgw.BGW_OPT_INVERSE, 0 if prec == bgw.BGW_PREC_FP64 else 1)
-    # the mixed solve's update slices: what bgw_epsilon uses after a mixed chi
+    # the mixed solve's inverse as bgw_epsilon runs it after a mixed chi:
+    # seven slices, the sweep's critical chain in double FP32
     ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0 if prec == bgw.BGW_PREC_FP64 else UPDATE_SLICES_MIXED)
+    ctx.set_option(bgw.BGW_OPT_DOUBLE_FP32, 0 if prec == bgw.BGW_PREC_FP64 else 1)
     with torch.cuda.stream(sstream):
         for _ in range(warmup):
             step()
@@ -235,6 +237,7 @@ def _solve_steps(ctx, s, prec, steps, warmup, flush, timing):
     torch.cuda.synchronize()
     ctx.set_option(bgw.BGW_OPT_INVERSE, -1)
     ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0)
+    ctx.set_option(bgw.BGW_OPT_DOUBLE_FP32, -1)
     stage = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in ev])
     return stage, kt, inv, launches
 
@@ -304,7 +307,7 @@ def run_ours(args):
         t_step = t_launch
         # DRAM bytes of one bulk update launch at N_G = 2120
         # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
-        # this kernel with 5 slices).  The matrix stays in L2, so this is below
+        # this kernel).  The matrix stays in L2, so this is below
         # the tiles' algorithmic traffic.
         oz_traffic_step = OZ_TRAFFIC_LAUNCH if s.ng == 2120 else None
         roof = {"bound": "tensor", "kernel": f"oz::update_pipe_kernel<{sl} slices> (tcgen05 kind::f16 M128 N32: the "
@@ -822,6 +825,7 @@ def run_profile_case(args):
         prec = bgw.PREC[args.prec]
         ctx.set_option(bgw.BGW_OPT_INVERSE, 0 if prec == bgw.BGW_PREC_FP64 else 1)
         ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0 if prec == bgw.BGW_PREC_FP64 else UPDATE_SLICES_MIXED)
+        ctx.set_option(bgw.BGW_OPT_DOUBLE_FP32, 0 if prec == bgw.BGW_PREC_FP64 else 1)
         cv = torch.from_numpy(s.cv).cuda()
         cc = torch.from_numpy(s.cc).cuda()
         M = torch.empty((s.npairs, s.ng), dtype=torch.complex128 if prec == 0 else torch.complex64, device="cuda")

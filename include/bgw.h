@@ -189,15 +189,22 @@ int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
  *    difference box nor the product's spectrum, else (no such grid up to 64)
  *    as 0; 0: the direct sum over the outer sphere, O(box x npw) per band.
  *    Both are FP64.                                                         */
-/*  BGW_OPT_UPDATE_SLICES: slices per value of the tensor-core update.  7:
- *    error near 2^-48 of the update's scale (FP64-level inverse); 5: near
- *    2^-34, with 15 slice products per tile instead of 28.  0 (default):
- *    5 where the inverse follows a mixed-precision chi (bgw_epsilon,
- *    bgw_epsilon_batch and the server with BGW_PREC_MIX_*: their chi carries
- *    errors near 1e-7), 7 elsewhere (bgw_epsinv, bgw_epsinv_general,
- *    bgw_epsinv_rflavor and the FP64 precision).                            */
+/*  BGW_OPT_UPDATE_SLICES: slices per value of the tensor-core update.  0
+ *    (default) and 7: error near 2^-48 of the update's scale (FP64-level
+ *    inverse); 5: near 2^-34 with 15 slice products per tile instead of 28
+ *    (implies BGW_OPT_DOUBLE_FP32).  For inputs whose own errors are far
+ *    larger and ε̃ that is well conditioned.                                 */
+/*  BGW_OPT_DOUBLE_FP32: the tensor-core sweep's critical chain -- the next
+ *    32 x 32 diagonal block's sweep and the panel product P = C D^-1 -- in
+ *    double-FP32 arithmetic (value = hi + lo, about 2^-46 per operation,
+ *    the FP64-level class of the seven-slice update) on the FP32 pipe, which
+ *    on GB300 issues 64 times the FP64 pipe's operations.  -1 (default): on
+ *    in bgw_epsilon, bgw_epsilon_real, bgw_epsilon_batch and the server for
+ *    the mixed precisions, off for FP64 inputs and for bgw_epsinv*; 0: off;
+ *    1: on.                                                                */
 enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3, BGW_OPT_CHI_CHUNK_PAIRS = 4,
-       BGW_OPT_INVERSE = 5, BGW_OPT_HEAD = 6, BGW_OPT_SIGMA_DENSITY = 7, BGW_OPT_UPDATE_SLICES = 8 };
+       BGW_OPT_INVERSE = 5, BGW_OPT_HEAD = 6, BGW_OPT_SIGMA_DENSITY = 7, BGW_OPT_UPDATE_SLICES = 8,
+       BGW_OPT_DOUBLE_FP32 = 9 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
 
 /* With BGW_OPT_TIMING = 1 the context records CUDA events around its main

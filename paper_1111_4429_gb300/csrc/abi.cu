@@ -210,12 +210,14 @@ bool use_tc_inverse(Ctx* c, int prec) {
   return prec != BGW_PREC_FP64;
 }
 
-// Slices of the tensor-core update for a call of precision prec: the
-// option's value, else 5 for the mixed precisions (their chi carries errors
-// near 1e-7, far above the 5-slice update's 2^-34) and 7 (FP64-level) for
-// FP64 inputs.  Recorded in the context for the inverse that follows.
+// Precision of the tensor-core inverse for a call of precision prec: seven
+// slices (FP64-level updates, near 2^-48) unless the option asks for five
+// (near 2^-34); the mixed precisions take the next diagonal block and the
+// panel product in double FP32 (about 2^-46), FP64 inputs in FP64.
+// Recorded in the context for the inverse that follows.
 void set_run_slices(Ctx* c, int prec) {
-  c->run_slices = c->update_slices ? c->update_slices : (prec == BGW_PREC_FP64 ? 7 : 5);
+  c->run_slices = c->update_slices ? c->update_slices : 7;
+  c->run_ff_chain = c->double_fp32 == 1 || (c->double_fp32 == -1 && prec != BGW_PREC_FP64) || c->run_slices < 7;
 }
 
 int init_device(Ctx* c) {
@@ -336,6 +338,11 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
   if (option == BGW_OPT_INVERSE) {
     if (value < -1 || value > 1) return fail(c, BGW_EINVAL, "inverse mode is -1, 0 or 1");
     c->inverse_mode = (int)value;
+    return BGW_OK;
+  }
+  if (option == BGW_OPT_DOUBLE_FP32) {
+    if (value < -1 || value > 1) return fail(c, BGW_EINVAL, "double-FP32 mode is -1, 0 or 1");
+    c->double_fp32 = (int)value;
     return BGW_OK;
   }
   if (option == BGW_OPT_UPDATE_SLICES) {
@@ -546,7 +553,7 @@ int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, con
   // graph's edges replace the streams' event waits.
   uint64_t key = hash_bytes("epsinv", 6, hash_bytes(&nmat, sizeof(nmat)));
   key = hash_bytes(&st, sizeof(st), key);
-  const int modes[3] = {c->inverse_mode, c->update_slices, c->run_slices};
+  const int modes[4] = {c->inverse_mode, c->update_slices, c->run_slices, c->run_ff_chain ? 1 : 0};
   key = hash_bytes(modes, sizeof(modes), key);
   key = hash_bytes(ng, nmat * sizeof(int), key);
   key = hash_bytes(cells, nmat * sizeof(bgw_cell), key);
@@ -680,7 +687,7 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   uint64_t key = hash_bytes(&nq, sizeof(nq), hash_bytes(&prec, sizeof(prec), hash_bytes(&nfreq, sizeof(nfreq))));
   if (nfreq > 0) key = hash_bytes(omega, nfreq * sizeof(double), key);
   key = hash_bytes(&st, sizeof(st), key);
-  const int modes[3] = {c->inverse_mode, c->head_mode, c->update_slices};
+  const int modes[4] = {c->inverse_mode, c->head_mode, c->update_slices, c->double_fp32};
   key = hash_bytes(modes, sizeof(modes), key);
   for (int q = 0; q < nq; ++q) {
     const bgw_problem& p = problems[q];
@@ -907,7 +914,7 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
     if (nfreq > 0) key = hash_bytes(omega, nfreq * sizeof(double), key);
     const void* ptrs[5] = {cv, cc, chi, epsinv, (const void*)st};
     key = hash_bytes(ptrs, sizeof(ptrs), key);
-    const int modes[3] = {c->inverse_mode, c->head_mode, c->update_slices};
+    const int modes[4] = {c->inverse_mode, c->head_mode, c->update_slices, c->double_fp32};
     key = hash_bytes(modes, sizeof(modes), key);
     key = hash_bytes(gv, (size_t)npw_v * 12, key);
     key = hash_bytes(gc, (size_t)npw_c * 12, key);

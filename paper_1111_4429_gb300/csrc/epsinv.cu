@@ -537,7 +537,7 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cel
         Ds[k] = sb.m[k].Dinv;
       }
       if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), Ds.data(), oz.get(), false,
-                           real_values, c->run_slices)) != BGW_OK)
+                           real_values, c->run_slices, c->run_ff_chain)) != BGW_OK)
         return rc;
     }
     if (!tc_update) {

@@ -412,7 +412,7 @@ int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
         Cs[k] = Cp.as<double2>() + (size_t)k * kPB * n;
       }
       if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Rs.data(), Cs.data(), nullptr, oz.get(), true, false,
-                           c->run_slices)) != BGW_OK)
+                           c->run_slices, c->run_ff_chain)) != BGW_OK)
         return rc;
     }
     int* piv = ipiv.as<int>();

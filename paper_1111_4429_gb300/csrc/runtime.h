@@ -118,8 +118,10 @@ struct Ctx {
   int inverse_mode = -1;     // -1: tensor-core update for the mixed precisions; 0: FP64 FMA; 1: tensor cores
   int head_mode = -1;        // mixed chi head/wings in FP64: -1 automatic at small q, 0 off, 1 on
   int sigma_density = -1;    // Sigma band densities: -1/1 product transform where alias-free, 0 direct sum
-  int update_slices = 0;     // tensor-core update slices: 0 automatic, 5 or 7
+  int update_slices = 0;     // tensor-core update slices: 0 automatic (7), 5 or 7
+  int double_fp32 = -1;      // double-FP32 sweep chain: -1 automatic (mixed precisions), 0 off, 1 on
   int run_slices = 7;        // slices of the call in progress (set by each entry point)
+  bool run_ff_chain = false; // double-FP32 chain for the call in progress (mixed precisions)
   std::unordered_map<uint64_t, const int32_t*> head_maps;  // conduction G -> valence index (head dot products)
   Pool pool;
   std::string err;
@@ -285,8 +287,11 @@ void oz_plan_delete(OzPlan* p);
 // real_values: every matrix is real (the real flavor's embedding), so only
 // the real-part products are formed.
 // slices: 7 (update error near 2^-48 of its scale) or 5 (near 2^-34).
+// ff_chain: the next diagonal block and the panel product in double FP32
+// (about 2^-46), the FP64-level class of the seven-slice update, on the
+// FP32 pipe (GB300's FP64 pipe is 64 times slower); five slices imply it.
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               double2* const* D, OzPlan* plan, bool general, bool real_values, int slices);
+               double2* const* D, OzPlan* plan, bool general, bool real_values, int slices, bool ff_chain);
 // epsinv_batch_run with real_values: the matrices are real (imaginary parts zero).
 // Slices of one pivoted Gauss-Jordan step (general plans).
 int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);

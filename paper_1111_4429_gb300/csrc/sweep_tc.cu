@@ -320,7 +320,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // MMAs start -- and apply the FP64 subtraction while they run.
 constexpr int kPipeEpiWarps = 16;
 constexpr int kPipeThreads = (kPipeEpiWarps + 1) * 32;
-constexpr int kJPI = 3;   // most column tiles per work item (mode 1 uses 2: its CTAs are on the critical path)
+constexpr int kJPI = 4;   // most column tiles per work item (see pipe_jpi)
 
 __device__ __forceinline__ int row_width(int mode, int I, int nJ) { return mode == 3 ? nJ : min(4 * I + 4, nJ); }
 
@@ -328,10 +328,13 @@ __device__ __forceinline__ int row_width(int mode, int I, int nJ) { return mode 
 // the tile holding the next diagonal block alone (its CTA sweeps that block:
 // the critical path of the next step), then the rest of row tile In in
 // chunks (tile Jn skipped there), then the tiles (I > In, Jn).
-__host__ __device__ inline int pipe_jpi(int mode) { return mode == 1 ? 2 : kJPI; }
-__host__ __device__ inline int pipe_items(int mode, int nI, int nJ, int In, bool has_next) {
+// Column tiles per work item: 2 in the look-ahead launch (its CTAs are on the
+// critical path); else 4 with seven slices and 3 with five (measured: the
+// five-slice items are cheaper, so smaller items balance the SMs better).
+__host__ __device__ inline int pipe_jpi(int mode, int sl) { return mode == 1 ? 2 : (sl < 7 ? 3 : kJPI); }
+__host__ __device__ inline int pipe_items(int mode, int sl, int nI, int nJ, int In, bool has_next) {
   int n = 0;
-  const int jpi = pipe_jpi(mode);
+  const int jpi = pipe_jpi(mode, sl);
   if (mode == 1) {
     const int w = (4 * In + 4 < nJ) ? 4 * In + 4 : nJ;
     return 1 + (w + jpi - 1) / jpi + (nI - In - 1 > 0 ? nI - In - 1 : 0);
@@ -343,9 +346,9 @@ __host__ __device__ inline int pipe_items(int mode, int nI, int nJ, int In, bool
   }
   return n;
 }
-__device__ inline void pipe_decode(int mode, int item, int nI, int nJ, int In, int Jn, bool has_next, int& I, int& J0,
+__device__ inline void pipe_decode(int mode, int sl, int item, int nI, int nJ, int In, int Jn, bool has_next, int& I, int& J0,
                                    int& J1) {
-  const int jpi = pipe_jpi(mode);
+  const int jpi = pipe_jpi(mode, sl);
   if (mode == 1) {
     const int w = row_width(1, In, nJ);
     const int nrow = (w + jpi - 1) / jpi;
@@ -400,8 +403,10 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, vol
 }
 
 // SL: slices used per value (the most significant SL of the S stored): 7
-// gives an update error near 2^-48 of its scale, 5 near 2^-34.
-template <bool realv, int SL>
+// gives an update error near 2^-48 of its scale, 5 near 2^-34.  FFC: the
+// look-ahead CTA sweeps the next diagonal block in double FP32 (about 2^-46
+// per operation, on the FP32 pipe) instead of FP64.
+template <bool realv, int SL, bool FFC>
 __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per sub-partition, 96 registers
     update_pipe_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
                        const __grid_constant__ OzBatch b, int k0, int rows_total, int buf, int mode,
@@ -419,7 +424,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
   const bool has_next = k1 < ng;
   const int In = k1 / BM, Jn = k1 / BN;
   if (mode == 1 && !has_next) return;
-  const int nitems = pipe_items(mode, nI, nJ, In, has_next);
+  const int nitems = pipe_items(mode, SL, nI, nJ, In, has_next);
   const int slice_base = buf * S * rows_total;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -464,7 +469,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
   int vissued = 0;     // V loads issued (control)
   for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++items_done) {
     int I, J0, J1;
-    pipe_decode(mode, item, nI, nJ, In, Jn, has_next, I, J0, J1);
+    pipe_decode(mode, SL, item, nI, nJ, In, Jn, has_next, I, J0, J1);
     const int i0 = I * BM;
     // tiles of the item that are not skipped, in order
     int Js[kJPI], nt = 0;
@@ -645,9 +650,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
         const int rr = e / NB, c2 = e % NB;
         if (rr < kb1 && c2 <= rr) dsm.L[rr][c2] = M.A[(size_t)(k1 + rr) * ng + k1 + c2];
       }
-      // five slices (update error near 2^-34): the block's sweep in double
-      // FP32 (about 2^-46), off the SM's slow FP64 pipe; seven: FP64
-      if constexpr (SL < 7)
+      // double-FP32 chain: the block's sweep in double FP32 (about 2^-46),
+      // off the SM's slow FP64 pipe; else FP64
+      if constexpr (FFC)
         diag_sweep_ff_n<kPipeThreads>(dsm, reinterpret_cast<float4*>(us), kb1, threadIdx.x, status);
       else
         diag_sweep_smem_n<kPipeThreads>(dsm, kb1, threadIdx.x, status);
@@ -697,6 +702,7 @@ size_t pipe_smem(int slices) { return (size_t)slices * (oz::kUTile + 2 * oz::kVT
 struct OzPlan {
   bool general = false;   // Gauss-Jordan update (mode 3) of the pivoted inverse
   int slices = 7;         // slices per value the update uses (5 or 7)
+  bool ff_chain = false;  // next diagonal block and panel product in double FP32
   bool real_values = false;  // every matrix real (real flavor): only the real-part MMAs
   int nmat = 0;
   int rows_total = 0;
@@ -707,10 +713,11 @@ struct OzPlan {
 };
 
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
-               double2* const* D, OzPlan* plan, bool general, bool real_values, int slices) {
+               double2* const* D, OzPlan* plan, bool general, bool real_values, int slices, bool ff_chain) {
   using namespace oz;
   if (slices != 5 && slices != 7) return fail(c, BGW_EINVAL, "tensor-core inverse: 5 or 7 slices");
   plan->slices = slices;
+  plan->ff_chain = ff_chain || slices < 7;   // five slices always use the double-FP32 chain
   if (nmat > kBatch) return fail(c, BGW_EUNSUPPORTED, "tensor-core inverse: at most %d matrices per batch", kBatch);
   if (!g_encode_oz) {
     void* fn = nullptr;
@@ -766,17 +773,20 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
     return fail(c, BGW_ECUDA, "tensor-core inverse: tensor map encoding failed");
   // U slices, two V buffers, alignment and barriers: about 170 KiB dynamic (7 slices)
   const size_t psmem = pipe_smem(slices);
-  if (slices == 7) {
-    BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<false, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)psmem));
-    BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<true, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)psmem));
+#define BGW_PIPE_ATTR(RV, SLC, FF)                                                                      \
+  BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<RV, SLC, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                   (int)psmem))
+  if (slices == 7 && !plan->ff_chain) {
+    BGW_PIPE_ATTR(false, 7, false);
+    BGW_PIPE_ATTR(true, 7, false);
+  } else if (slices == 7) {
+    BGW_PIPE_ATTR(false, 7, true);
+    BGW_PIPE_ATTR(true, 7, true);
   } else {
-    BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)psmem));
-    BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<true, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)psmem));
+    BGW_PIPE_ATTR(false, 5, true);
+    BGW_PIPE_ATTR(true, 5, true);
   }
+#undef BGW_PIPE_ATTR
   return BGW_OK;
 }
 
@@ -796,7 +806,7 @@ int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) 
 int oz_panel_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) {
   using namespace oz;
   const int rpad = (ngmax + BM - 1) / BM * BM;
-  if (plan->slices < 7)
+  if (plan->ff_chain)
     panel_slice_kernel<true><<<dim3(rpad / 8, plan->nmat), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
                                                                          plan->U.as<__half>(), plan->V.as<__half>(),
                                                                          plan->sig.as<int>(), plan->tau.as<int>());
@@ -824,25 +834,31 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
   // one work item (up to kJPI tiles of a row tile) per CTA
   {
     const int nI = (ngmax + BM - 1) / BM, nJ = (ngmax + BN - 1) / BN, k1 = k0 + NB;
-    grid = pipe_items(mode, nI, nJ, k1 / BM, k1 < ngmax);
+    grid = pipe_items(mode, plan->slices, nI, nJ, k1 / BM, k1 < ngmax);
   }
   if (grid <= 0) return BGW_OK;
   const size_t smem = pipe_smem(plan->slices);
   const dim3 g(grid, plan->nmat);
-#define BGW_PIPE_LAUNCH(RV, SLC)                                                                               \
-  update_pipe_kernel<RV, SLC><<<g, kPipeThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,          \
-                                                             plan->rows_total, buf, mode, plan->sig.as<int>(), \
-                                                             plan->tau.as<int>(), c->d_status)
-  if (plan->slices == 7) {
-    if (plan->real_values)
-      BGW_PIPE_LAUNCH(true, 7);
+#define BGW_PIPE_LAUNCH(RV, SLC, FF)                                                                          \
+  update_pipe_kernel<RV, SLC, FF><<<g, kPipeThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,      \
+                                                                 plan->rows_total, buf, mode, plan->sig.as<int>(), \
+                                                                 plan->tau.as<int>(), c->d_status)
+  const bool rv = plan->real_values;
+  if (plan->slices == 7 && !plan->ff_chain) {
+    if (rv)
+      BGW_PIPE_LAUNCH(true, 7, false);
     else
-      BGW_PIPE_LAUNCH(false, 7);
+      BGW_PIPE_LAUNCH(false, 7, false);
+  } else if (plan->slices == 7) {
+    if (rv)
+      BGW_PIPE_LAUNCH(true, 7, true);
+    else
+      BGW_PIPE_LAUNCH(false, 7, true);
   } else {
-    if (plan->real_values)
-      BGW_PIPE_LAUNCH(true, 5);
+    if (rv)
+      BGW_PIPE_LAUNCH(true, 5, true);
     else
-      BGW_PIPE_LAUNCH(false, 5);
+      BGW_PIPE_LAUNCH(false, 5, true);
   }
 #undef BGW_PIPE_LAUNCH
   if (plan->general) {
