@@ -148,7 +148,7 @@ __device__ __forceinline__ void diag_sweep_smem_n(DiagSmem& sm, int kb, int t, i
 // about 2^-46 relative per operation) for updates whose target precision is
 // far coarser than FP64 (the five-slice tensor-core update, near 2^-34).
 // GB300's FP32 pipe issues 64 times the FP64 pipe's operations, so the
-// double-FP32 sweep, about 20 FP32 operations per FP64 multiply-add, leaves
+// double-FP32 sweep, about 12 FP32 operations per FP64 multiply-add, leaves
 // the FP64 pipe, the sweep's limit, out of the step.  The error-free
 // transformations are Knuth's two-sum, the fast two-sum for |a| >= |b| and
 // the FMA product error.
@@ -174,19 +174,6 @@ __device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
   e = __fmaf_rn(a.x, b.y, e);
   e = __fmaf_rn(a.y, b.x, e);
   return ff_fast(p, e);
-}
-// v + a b: the product as the pair (p, e) and the accurate pair sum (both
-// words two-summed, renormalized twice), which keeps its error relative to
-// the result when v and a b nearly cancel, as Schur-complement pivots do.
-__device__ __forceinline__ float2 ff_fma(float2 v, float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  float e = __fmaf_rn(a.x, b.x, -p);
-  e = __fmaf_rn(a.x, b.y, e);
-  e = __fmaf_rn(a.y, b.x, e);
-  float2 s = ff_two_sum(v.x, p);
-  const float2 t = ff_two_sum(v.y, e);
-  s = ff_fast(s.x, __fadd_rn(s.y, t.x));
-  return ff_fast(s.x, __fadd_rn(s.y, t.y));
 }
 // 1 / d for d > 0: the FP32 reciprocal and one Newton step in double FP32
 __device__ __forceinline__ float2 ff_rcp(float2 d) {

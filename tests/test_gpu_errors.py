@@ -111,3 +111,21 @@ def test_zero_pivot_sets_numeric_status(ctx):
         ctx.sync()
     assert e.value.code == bgw.BGW_ENUMERIC
     ctx.sync()   # status was cleared
+
+
+@pytest.mark.parametrize("option,bad,good", [("BGW_OPT_UPDATE_SLICES", [1, 6, 8, -1], [0, 5, 7]),
+                                             ("BGW_OPT_DOUBLE_FP32", [2, -2], [-1, 0, 1]),
+                                             ("BGW_OPT_SIGMA_DENSITY", [2, -2], [-1, 0, 1]),
+                                             ("BGW_OPT_INVERSE", [2, -2], [-1, 0, 1])])
+def test_option_values(ctx, option, bad, good):
+    """Values outside an option's documented set are refused (code 1) and
+    leave the context usable; the documented ones are accepted."""
+    from paper_1111_4429_gb300 import bgw
+    opt = getattr(bgw, option)
+    for v in bad:
+        with pytest.raises(bgw.BgwError) as ex:
+            ctx.set_option(opt, v)
+        assert ex.value.code == 1
+    for v in good:
+        ctx.set_option(opt, v)
+    ctx.set_option(opt, good[0])   # back to the default (first listed)
