@@ -573,3 +573,64 @@ def test_sigma_mtxel_fft_route_and_negated_g():
     # M_{n''n}(-q, -G) = conj(M_{n n''}(+q, +G)) with the roles of the spheres swapped
     mswap = oracle.mtxel_direct(sb.go, sb.co, sb.gi, sb.ci, s.geps).reshape(2, 5, -1)
     assert np.abs(md.reshape(5, 2, -1) - np.conj(mswap.transpose(1, 0, 2))).max() < 1e-14
+
+
+# ------------------------------------------------------------ direct pins of helpers
+
+def test_density_diag_two_plane_wave_closed_form():
+    """rho_n(D) = sum_G2 conj(c(D + G2)) c(G2) for a band of two plane waves a at G1,
+    b at G2 (|a|^2 + |b|^2 = 1): 1 at D = 0, conj(a) b at G1 - G2, conj(b) a at G2 - G1,
+    0 elsewhere; and rho(-D) = conj(rho(D)) for a random band."""
+    g = np.array([[0, 0, 0], [1, 0, 0], [0, 2, -1], [1, 1, 1]], dtype=np.int32)
+    a, b = 0.6 * np.exp(0.3j), 0.8 * np.exp(-1.1j)
+    c = np.zeros((1, 4), dtype=np.complex128)
+    c[0, 1], c[0, 2] = a, b
+    d12 = g[1] - g[2]
+    deltas = np.array([[0, 0, 0], d12, -d12, [1, 0, 0], [0, 1, 0]], dtype=np.int32)
+    rho = oracle.density_diag(g, c, deltas)[0]
+    assert abs(rho[0] - 1.0) < 1e-15
+    assert abs(rho[1] - np.conj(a) * b) < 1e-15
+    assert abs(rho[2] - np.conj(b) * a) < 1e-15
+    assert np.abs(rho[3:]).max() < 1e-15
+    gen = np.random.default_rng(4)
+    s = _tiny(seed=11)
+    cr = synth.orthonormal_bands(gen, s.gc.shape[0], 2)
+    dd = np.array([[1, 0, 0], [0, -1, 2], [2, 1, 0]], dtype=np.int32)
+    p = oracle.density_diag(s.gc, cr, dd)
+    m = oracle.density_diag(s.gc, cr, -dd)
+    assert np.abs(p - np.conj(m)).max() < 1e-14
+    assert np.abs(oracle.density_diag(s.gc, cr, np.zeros((1, 3), np.int32))[:, 0] - 1.0).max() < 1e-14
+
+
+def test_chi_entries_are_the_entries_of_chi():
+    """chi_entries on column subsets of M equals those entries of the tier-1 pair
+    sum and the tier-2 product."""
+    gen = np.random.default_rng(5)
+    M = gen.standard_normal((12, 9)) + 1j * gen.standard_normal((12, 9))
+    w = -gen.uniform(0.1, 2.0, 12)
+    full1 = oracle.chi_direct(M, w, 37.0)
+    full2 = oracle.chi(M, w, 37.0)
+    rows, cols = [0, 3, 8], [1, 2, 3, 7]
+    sub = oracle.chi_entries(M[:, rows], M[:, cols], w, 37.0)
+    assert np.abs(sub - full1[np.ix_(rows, cols)]).max() <= 1e-13 * np.abs(full1).max()
+    assert np.abs(sub - full2[np.ix_(rows, cols)]).max() <= 1e-13 * np.abs(full2).max()
+
+
+def test_eps_sym_special_cases_and_similarity():
+    """eps~ = I - v^1/2 chi v^1/2: the identity for chi = 0, 1 - v_G chi_GG on a
+    diagonal chi, and V^-1/2 eps V^1/2 with eps = I - v chi the paper's asymmetric
+    form (same spectrum)."""
+    gen = np.random.default_rng(6)
+    ng = 7
+    v = gen.uniform(0.2, 3.0, ng)
+    assert np.array_equal(oracle.eps_sym(np.zeros((ng, ng), np.complex128), v), np.eye(ng))
+    d = -gen.uniform(0.0, 1.0, ng)
+    e = oracle.eps_sym(np.diag(d).astype(np.complex128), v)
+    assert np.abs(e - np.diag(1.0 - v * d)).max() < 1e-15
+    z = gen.standard_normal((ng, ng)) + 1j * gen.standard_normal((ng, ng))
+    chi = -(z @ np.conj(z).T) / ng
+    es = oracle.eps_sym(chi, v)
+    ea = oracle.eps_asym(chi, v)
+    s = np.sqrt(v)
+    assert np.abs(es - (ea * s[None, :]) / s[:, None]).max() < 1e-13
+    assert np.allclose(np.sort(np.linalg.eigvalsh(es)), np.sort(np.linalg.eigvals(ea).real), atol=1e-12)
