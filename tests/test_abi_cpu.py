@@ -93,3 +93,25 @@ def test_real_coefficients_host_matches_oracle_subspaces():
     import pytest
     with pytest.raises(bgw.BgwError):
         bgw.real_coefficients(np.zeros((1, 50), complex), np.array([0.0]), 1e-9)
+
+
+def test_binding_constants_match_the_header():
+    """Every BGW_* enumerator the binding names has the header's value (the
+    options, precisions, flavour flag, Coulomb models and status codes)."""
+    from paper_1111_4429_gb300 import bgw
+    txt = ""
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt += open(os.path.join(ROOT, "include", h)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    header = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", txt, flags=re.S):
+        for name, val in re.findall(r"\b(BGW_[A-Z0-9_]+)\s*=\s*(0x[0-9a-fA-F]+|-?\d+)", body):
+            header[name] = int(val, 0)
+    names = [n for n in dir(bgw) if n.startswith("BGW_") and isinstance(getattr(bgw, n), int)]
+    assert len(names) >= 15
+    for n in names:
+        assert n in header, n
+        assert getattr(bgw, n) == header[n], n
+    for n in ("BGW_OPT_UPDATE_SLICES", "BGW_OPT_DOUBLE_FP32", "BGW_OPT_SIGMA_DENSITY", "BGW_OPT_HEAD"):
+        assert n in names
