@@ -21,7 +21,7 @@ template <typename V>
 static int upload_vec(Ctx* c, const std::vector<V>& v, cudaStream_t st, V** dev) {
   void* p = nullptr;
   size_t bytes = std::max<size_t>(1, v.size()) * sizeof(V);
-  int rc = c->pool.alloc(bytes, &p);
+  int rc = c->pool.alloc_keep(bytes, &p);
   if (rc != BGW_OK) return fail(c, rc, "plan upload: device allocation of %zu bytes failed", bytes);
   if (!v.empty()) BGW_CUDA(c, cudaMemcpyAsync(p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice, st));
   *dev = static_cast<V*>(p);

@@ -75,9 +75,18 @@ Pool::~Pool() {
   for (auto& kv : live_) cudaFree(kv.first);
 }
 
-int Pool::alloc(size_t bytes, void** out) {
+int Pool::alloc(size_t bytes, void** out) { return alloc_impl(bytes, out, false); }
+int Pool::alloc_keep(size_t bytes, void** out) { return alloc_impl(bytes, out, true); }
+
+int Pool::alloc_impl(size_t bytes, void** out, bool keep) {
   const size_t sz = round(bytes);
-  auto it = free_.find(sz);
+  auto it = free_.end();
+  const auto range = free_.equal_range(sz);
+  for (auto j = range.first; j != range.second; ++j)
+    if (!keep || !pinned_.count(j->second)) {
+      it = j;
+      break;
+    }
   if (it != free_.end()) {
     void* p = it->second;
     free_.erase(it);
@@ -204,7 +213,7 @@ int upload_cached(Ctx* c, const void* host, size_t bytes, cudaStream_t st, const
     return BGW_OK;
   }
   void* p = nullptr;
-  int rc = c->pool.alloc(bytes, &p);
+  int rc = c->pool.alloc_keep(bytes, &p);
   if (rc != BGW_OK) return fail(c, rc, "upload of %zu bytes: device allocation failed", bytes);
   // Stream-ordered: the block may come from the pool's free list and still
   // be read by earlier work on this stream.

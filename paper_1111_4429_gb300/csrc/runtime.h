@@ -36,6 +36,11 @@ class Pool {
   ~Pool();
   // Returns BGW_OK / BGW_ENOMEM / BGW_ECUDA.
   int alloc(size_t bytes, void** out);
+  // For blocks kept for the context's life (uploaded inputs, plans): never
+  // a block pinned by a captured graph.  A pinned block on the free list is
+  // safe for a later call's scratch (stream order puts it after the graph's
+  // replays), but a replay would overwrite anything kept in it.
+  int alloc_keep(size_t bytes, void** out);
   void release(void* p);
   void trim();  // cudaFree every cached free block not pinned by a graph
   // While pinning is on, every block handed out is marked pinned: a CUDA
@@ -48,6 +53,7 @@ class Pool {
 
  private:
   static size_t round(size_t b);
+  int alloc_impl(size_t bytes, void** out, bool keep);
   uint64_t budget_;
   uint64_t reserved_ = 0;   // bytes obtained from cudaMalloc
   uint64_t in_use_ = 0;     // bytes handed out
