@@ -364,13 +364,17 @@ int bgw_real_coefficients(int nb, int npw, const void* c, const double* energies
  *   epsinv  device c128 [ng][ng]
  * Scratch: one fixed file-scope device array of about 4.1 MiB inside the
  * library, which every GPU that loads the library holds until the process
- * exits; it bounds ng <= 4096 (larger ng returns BGW_EINVAL).  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress,
- * with the device current) and caches it; make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
- * contents, so calls whose work overlaps on the GPU (other streams, other
- * host threads) race: serialize them.  Returns BGW_EINVAL for bad
- * arguments or |q+G| = 0, BGW_ECUDA when a CUDA call fails.  A zero or
+ * exits; it bounds ng <= 4096 (larger ng returns BGW_EINVAL before any
+ * work is queued).  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with the device current) and caches it with
+ * the id of the current CUDA context; a call made in another context of the
+ * device (after cudaDeviceReset, or under a driver-API context the caller
+ * made current) looks it up again.  Make the first call on a device before
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents (each call clears what must start at zero), so calls whose
+ * work overlaps on the GPU (other streams, other host threads) race:
+ * serialize them.  Returns BGW_EINVAL for bad arguments or |q+G| = 0,
+ * BGW_ECUDA when one of this call's CUDA calls or launches fails.  A zero or
  * non-finite pivot is not reported (there is no context to carry the status
  * word); the result is then meaningless.                                   */
 int bgw_epsinv_noalloc(const bgw_cell* cell, int ng, const int32_t* geps,

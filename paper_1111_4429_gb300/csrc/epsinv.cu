@@ -16,6 +16,8 @@
 // v^1/2 is Hermitian positive definite (chi <= 0), for which elimination
 // without pivoting is backward stable; a zero or non-finite pivot is
 // recorded in the device status word.
+#include <cuda.h>
+
 #include <cmath>
 #include <memory>
 #include <vector>
@@ -774,7 +776,28 @@ static_assert(kNaDinv % 256 == 0 && kNaR % 256 == 0 && kNaC % 256 == 0 && kNaGep
               "scratch regions must stay 256-byte aligned");
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[kMaxDevices] = {};
+// Per device: the CUDA context the address was looked up in (its
+// process-unique id) and the address.  A symbol's device address belongs to
+// one context, so a new context on the device (after cudaDeviceReset, or a
+// driver-API context made current by the caller) needs a new lookup.
+struct NoallocAddr {
+  unsigned long long ctx_id = 0;
+  bool valid = false;
+  void* ptr = nullptr;
+};
+NoallocAddr g_noalloc_addr[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+cudaError_t driver_entry(const char* name, int version, void** fn) {
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion(name, fn, version, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  return (q == cudaDriverEntryPointSuccess && *fn) ? cudaSuccess : cudaErrorNotSupported;
+}
 }  // namespace
 
 // The scratch itself (about 4.1 MiB).  Host code must not use this name as an
@@ -782,22 +805,42 @@ void* g_noalloc_addr[kMaxDevices] = {};
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device (the lookup needs that device current).
+// Device address of g_noalloc_scratch in the current device's current
+// context.  Set-up: looked up once per device (with that device current) and
+// again whenever the current context is not the one of the cached lookup.
 static cudaError_t noalloc_scratch_address(unsigned char** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    if (!p) return cudaErrorInvalidSymbol;
-    g_noalloc_addr[dev] = p;
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    void *a = nullptr, *b = nullptr;
+    if ((e = driver_entry("cuCtxGetCurrent", 4000, &a)) != cudaSuccess) return e;
+    if ((e = driver_entry("cuCtxGetId", 12000, &b)) != cudaSuccess) return e;
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(b);
   }
-  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  CUcontext cur = nullptr;
+  if (g_ctx_get_current(&cur) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  void* p = nullptr;
+  if (!cur) {
+    // No context bound to this thread yet: the runtime binds the device's
+    // primary context on its first call that needs one.
+    if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
+    if (g_ctx_get_current(&cur) != CUDA_SUCCESS || !cur) return cudaErrorDeviceUninitialized;
+  }
+  unsigned long long id = 0;
+  if (g_ctx_get_id(cur, &id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  NoallocAddr& a = g_noalloc_addr[dev];
+  if (!a.valid || a.ctx_id != id) {
+    if (!p && (e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
+    if (!p) return cudaErrorInvalidSymbol;
+    a.ptr = p;
+    a.ctx_id = id;
+    a.valid = true;
+  }
+  *out = static_cast<unsigned char*>(a.ptr);
   return cudaSuccess;
 }
 
@@ -828,25 +871,42 @@ extern "C" int bgw_epsinv_noalloc(const bgw_cell* cell, int ng, const int32_t* g
     cudaGetLastError();
     return BGW_ECUDA;
   }
-  coulomb_sqrt_kernel<<<(ng + 255) / 256, 256, 0, st>>>(dgeps, ng, coulomb_args(cell), sv);
+  // Each launch's own status (not the thread's last error, which may hold
+  // an earlier call's failure): a failed launch is reported as this call's.
+  auto launch = [st](dim3 grid, dim3 block, size_t smem, auto kernel, auto... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+  };
+  cudaError_t e = launch(dim3((ng + 255) / 256), dim3(256), 0, coulomb_sqrt_kernel, (const int32_t*)dgeps, ng,
+                         coulomb_args(cell), sv);
   double2* A = static_cast<double2*>(epsinv);
   const size_t n2 = (size_t)ng * ng;
   const unsigned eb = (unsigned)std::min<size_t>((n2 + 255) / 256, 152 * 16);
-  eps_form_kernel<<<eb, 256, 0, st>>>(static_cast<const double2*>(chi), sv, ng, A, static_cast<double2*>(eps));
+  if (e == cudaSuccess)
+    e = launch(dim3(eb), dim3(256), 0, eps_form_kernel, static_cast<const double2*>(chi), (const double*)sv, ng, A,
+               static_cast<double2*>(eps));
   const int nt = (ng + TU - 1) / TU;
   const size_t upd_smem = sizeof(double2) * (TU * (NB + 1) + NB * TU);
-  if (cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem) !=
-      cudaSuccess) {
-    cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem);
+  for (int k0 = 0; k0 < ng && e == cudaSuccess; k0 += NB) {
+    const int kb = std::min(NB, ng - k0);
+    e = launch(dim3(1), dim3(NB, NB), 0, gj_diag_kernel, A, ng, k0, kb, dinv, status);
+    if (e == cudaSuccess)
+      e = launch(dim3((ng + 63) / 64, 1 + (ng + 255) / 256), dim3(256), 0, gj_panels_kernel, (const double2*)A, ng, k0,
+                 kb, (const double2*)dinv, R, Cp);
+    if (e == cudaSuccess)
+      e = launch(dim3(nt, nt), dim3(256), upd_smem, gj_update_kernel, A, ng, k0, kb, (const double2*)R,
+                 (const double2*)Cp);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();   // the failure just reported is this call's own
     return BGW_ECUDA;
   }
-  for (int k0 = 0; k0 < ng; k0 += NB) {
-    const int kb = std::min(NB, ng - k0);
-    gj_diag_kernel<<<1, dim3(NB, NB), 0, st>>>(A, ng, k0, kb, dinv, status);
-    gj_panels_kernel<<<dim3((ng + 63) / 64, 1 + (ng + 255) / 256), 256, 0, st>>>(A, ng, k0, kb, dinv, R, Cp);
-    gj_update_kernel<<<dim3(nt, nt), 256, upd_smem, st>>>(A, ng, k0, kb, R, Cp);
-  }
-  if (cudaGetLastError() != cudaSuccess) return BGW_ECUDA;
   return BGW_OK;
 }
 
