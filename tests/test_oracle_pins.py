@@ -575,6 +575,85 @@ def test_sigma_mtxel_fft_route_and_negated_g():
     assert np.abs(md.reshape(5, 2, -1) - np.conj(mswap.transpose(1, 0, 2))).max() < 1e-14
 
 
+def test_sigma_plane_wave_closed_forms_fix_the_prefactors():
+    """Every inner and outer band one plane wave: M_{n''n}(-G) is 1 exactly
+    when G = G_n - G_i (inner band at G_i on the k - q sphere) and 0 otherwise,
+    so the four sums of Eqs. hf-x, cohsex-sx, cohsex-ch-sum and cohsex-ch-exact
+    collapse to sums of single matrix entries at G = G_n - G_i:
+      X  = -(1/Omega) sum_{i occ} v(q + G),   SX = -(1/Omega) sum_{i occ} W_GG,
+      CH = (1/(2 Omega)) sum_{i all} (W - V)_GG,
+    and rho_n(D) = delta_{D,0} gives CH_exact = (1/(2 Omega)) sum_{G in geps} (W - V)_GG.
+    A dropped 1/2, a spin factor 2 or 4/Omega in place of 1/Omega fails."""
+    s = _tiny(seed=21, n=16, a=9.0, ew=4.0, ee=3.0)
+    v = oracle.coulomb(s.bvec, s.q_frac, s.geps)
+    gen = np.random.default_rng(22)
+    z = gen.standard_normal((s.ng, s.ng)) + 1j * gen.standard_normal((s.ng, s.ng))
+    ei = np.eye(s.ng) + 0.05 * (z + np.conj(z).T)
+    sq = np.sqrt(v)
+    W = sq[:, None] * ei * sq[None, :]
+    go = synth.gsphere(s.bvec, (0.0, 0.0, 0.0), 1.0)          # outer plane waves at k = 0
+    gi = synth.gsphere(s.bvec, -np.asarray(s.q_frac), 1.2)    # inner plane waves at k - q
+    co = np.eye(go.shape[0], dtype=np.complex128)[:3]
+    ci = np.eye(gi.shape[0], dtype=np.complex128)
+    nocc = gi.shape[0] // 2
+    out = oracle.sigma_cohsex(gi, ci, nocc, go, co, s.geps, ei, v, s.omega)
+    gidx = {tuple(g): k for k, g in enumerate(s.geps.tolist())}
+    for n in range(3):
+        x = sx = ch = 0.0
+        for i in range(gi.shape[0]):
+            k = gidx.get(tuple((go[n] - gi[i]).tolist()))
+            if k is None:
+                continue
+            if i < nocc:
+                x -= v[k] / s.omega
+                sx -= W[k, k].real / s.omega
+            ch += (W[k, k].real - v[k]) / (2.0 * s.omega)
+        che = np.sum(np.diag(W).real - v) / (2.0 * s.omega)
+        assert x < 0 and abs(out["X"][n] - x) <= 1e-13 * abs(x)
+        assert abs(out["SX"][n] - sx) <= 1e-13 * abs(sx)
+        assert abs(out["CH"][n] - ch) <= 1e-13 * abs(ch)
+        assert abs(out["CH_exact"][n] - che) <= 1e-13 * abs(che)
+
+
+def _heg_exchange(k, kf):
+    """Hartree-Fock exchange of the electron gas for one spin (Hartree units):
+    -(2 kF / pi) F(k / kF), F(x) = 1/2 + (1 - x^2)/(4x) ln|(1 + x)/(1 - x)|,
+    F(0) = 1 (the textbook result, independent of the paper)."""
+    x = k / kf
+    if x == 0.0:
+        return -2.0 * kf / math.pi
+    return -(2.0 * kf / math.pi) * (0.5 + (1.0 - x * x) / (4.0 * x) * math.log(abs((1.0 + x) / (1.0 - x))))
+
+
+def test_sigma_exchange_of_the_electron_gas():
+    """The bare exchange of Eq. hf-x with the q sum's 1/(N_q Omega), for
+    plane-wave states filling a Fermi sphere |k - q + G_i| < kF (the electron
+    gas: one orbital per plane wave and spin) and averaged over a 2x2x2 grid
+    of q in the zone, approaches the textbook Hartree-Fock exchange
+    -(2 kF / pi) F(k / kF).  The discrete q grid misses the neighbourhood of
+    the integrable 1/|k - k'|^2 point, so the sum lies a few per cent below
+    in magnitude at this cell (12 bohr, kF = 1.5 bohr^-1); a spin factor 2, a
+    dropped 1/Omega or 4/Omega would be off by 100 % or more."""
+    a, kf, nq = 12.0, 1.5, 2
+    bvec, omega = synth.cubic_cell(a)
+    go = np.zeros((1, 3), dtype=np.int32)                     # outer state: k = 0, G = 0
+    co = np.ones((1, 1), dtype=np.complex128)
+    xs = []
+    for i in range(nq):
+        for j in range(nq):
+            for k in range(nq):
+                q = np.array([(i + 0.5) / nq - 0.5, (j + 0.5) / nq - 0.5, (k + 0.5) / nq - 0.5])
+                gi = synth.gsphere(bvec, -q, kf * kf)
+                ci = np.eye(gi.shape[0], dtype=np.complex128)
+                geps = synth.gsphere(bvec, q, 4.0 * kf * kf * 1.0001)
+                v = oracle.coulomb(bvec, q, geps)
+                out = oracle.sigma_cohsex(gi, ci, gi.shape[0], go, co, geps, np.eye(geps.shape[0]), v, omega)
+                xs.append(out["X"][0])
+    x = float(np.mean(xs))
+    ref = _heg_exchange(0.0, kf)
+    assert -0.09 < x / ref - 1.0 < 0.0, (x, ref)
+
+
 # ------------------------------------------------------------ direct pins of helpers
 
 def test_density_diag_two_plane_wave_closed_form():
