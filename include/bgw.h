@@ -151,10 +151,11 @@ int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
 
 /* Tuning options of a context (EINVAL for an unknown option or value).
  *  BGW_OPT_CHI_SEGMENT_PAIRS: mixed-precision chi accumulates the products
- *    of this many pairs in FP32 on the tensor cores before adding them in
- *    FP64 (rounded down to a multiple of 32; 0 restores the default, 512).
- *    Shorter segments lower the FP32 accumulation error and cost more
- *    workspace traffic.                                                     */
+ *    of this many pairs in FP32 in tensor memory, restarting every segment
+ *    (rounded down to a multiple of 32; 0 restores the default, 512); the
+ *    segments of a tile are added in FP32 registers and the tiles' partial
+ *    sums in FP64.  Shorter segments lower the FP32 accumulation error and
+ *    cost more drains of tensor memory.                                      */
 /*  BGW_OPT_AUTOTUNE: 1 (default) lets the context time the candidate tile
  *    shapes of the pair transform (pairs per block) the first time it meets
  *    a (grid, precision, epsilon-sphere shape) and keep the fastest; 0 uses
@@ -162,7 +163,7 @@ int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
 /*  BGW_OPT_CHI_CHUNK_PAIRS: mixed-precision chi converts and sums the pairs
  *    in chunks of this many pairs (rounded down to a multiple of 32), each
  *    chunk's FP64 sum added into chi; 0 (default) sizes chunks so that their
- *    operand planes and FP32 workspace stay near 1 GiB each.               */
+ *    operand planes (as large as the chunk's complex64 M) stay within 4 GiB. */
 /*  BGW_OPT_INVERSE: how the sweep's trailing updates run.  -1 (default):
  *    bgw_epsilon, bgw_epsilon_batch and the server use the tensor cores for
  *    the mixed precisions and FP64 FMA for BGW_PREC_FP64, bgw_epsinv uses
@@ -202,9 +203,17 @@ int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
  *    in bgw_epsilon, bgw_epsilon_real, bgw_epsilon_batch and the server for
  *    the mixed precisions, off for FP64 inputs and for bgw_epsinv*; 0: off;
  *    1: on.                                                                */
+/*  BGW_OPT_WAIT_LIMIT_NS: how long (nanoseconds, 0 .. 10^10; default 10^9)
+ *    a wait of the tensor-core chi kernels on its pipeline (a copy landing,
+ *    an MMA stage finishing, tensor memory being drained) may last before
+ *    the kernel gives up: it then lets its copies and MMAs in flight finish
+ *    (within 1 s), frees its tensor memory, returns, and the next bgw_sync
+ *    (or call that synchronizes) reports BGW_ETIMEOUT; the outputs of that
+ *    call are undefined, the context stays usable.  0 gives up at the first
+ *    wait that is not already complete (a test of that path).              */
 enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3, BGW_OPT_CHI_CHUNK_PAIRS = 4,
        BGW_OPT_INVERSE = 5, BGW_OPT_HEAD = 6, BGW_OPT_SIGMA_DENSITY = 7, BGW_OPT_UPDATE_SLICES = 8,
-       BGW_OPT_DOUBLE_FP32 = 9 };
+       BGW_OPT_DOUBLE_FP32 = 9, BGW_OPT_WAIT_LIMIT_NS = 10 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
 
 /* With BGW_OPT_TIMING = 1 the context records CUDA events around its main

@@ -365,6 +365,11 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
     c->autotune = value == 1;
     return BGW_OK;
   }
+  if (option == BGW_OPT_WAIT_LIMIT_NS) {
+    if (value < 0 || value > 10000000000LL) return fail(c, BGW_EINVAL, "wait limit must be in [0, 1e10] ns");
+    c->wait_ns = (unsigned long long)value;
+    return BGW_OK;
+  }
   if (option == BGW_OPT_TIMING) {
     if (value != 0 && value != 1) return fail(c, BGW_EINVAL, "timing is 0 or 1");
     c->timing.on = value == 1;

@@ -42,8 +42,9 @@ namespace tc {
 
 constexpr int BM = 128;          // tile rows (G)
 constexpr int BK = 32;           // pairs per TMA box / stage (64 B of 16-bit values)
-constexpr int kThreads = 128;    // 4 warps
-constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
+constexpr int kEpiWarps = 8;     // epilogue warps of the GEMM kernel (two per tensor-memory lane quadrant)
+constexpr int kThreads = 32 * (kEpiWarps + 2);   // + TMA producer + MMA issuer
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: default limit of every wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -71,16 +72,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false when the barrier did not complete within kWaitNs or the
-// CTA is aborting.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait: false when the barrier did not complete within limit_ns or
+// (watch_abort) the CTA is aborting.  A limit of 0 gives up at the first
+// failed try.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit_ns = kWaitNs, bool watch_abort = true) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (watch_abort && *abort_flag) return false;
+    if (globaltimer() - t0 >= limit_ns) return false;
   }
   return true;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
@@ -123,12 +129,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -144,31 +148,53 @@ struct Layout {
   static constexpr int kTmemCols = 4 * BN;
 };
 
-// grid: nseg * ntiles CTAs (segment-major), block 128, dynamic smem
-// STAGES * stage + 1 KiB (alignment) + barriers.  The A operand (rows G)
-// reads planes 0..3; the B operand (columns G') reads the planes starting at
-// row brow of the tensor map: 0 for the Hermitian product (X = Y), 4 ngpad
-// when a second operand Y follows X (real-axis chi).
+// grid: ngroups * ntiles CTAs (group-major, so the CTAs that run together
+// read the same pairs), block kThreads = 10 warps, dynamic smem STAGES *
+// stage + 1 KiB (alignment) + barriers.  One CTA computes one 128 x BN tile
+// of the lower triangle over one group of `segs` segments of KS = kb_per_seg
+// * BK pairs: each segment is accumulated in FP32 in tensor memory, then
+// drained by the eight epilogue warps into FP32 running sums in registers
+// (the accumulator's rounding error grows with the number of adds into it,
+// so it restarts every segment), and the group's sum is written once as an
+// FP32 partial W[group][tile][re|im][128][BN].
+//
+// Warps 0..7: epilogue (warp w reads tensor-memory lanes 32 (w % 4).. and
+// columns (w / 4) BN/2..); warp 8: TMA producer and tensor-memory owner;
+// warp 9: MMA issuer.  Barriers: full/empty per stage (TMA <-> MMA), done
+// (MMA -> epilogue, one phase per segment), tfree (epilogue -> MMA: tensor
+// memory drained, the next segment may start).
+//
+// Waits: the waits on the pipeline (empty, full, tfree) give up after
+// wait_ns, set the abort flag and record BGW_ETIMEOUT.  An MMA issuer that
+// gives up first waits (1 s bound) until its issued MMAs have finished, then
+// commits `done` once more so that the epilogue (which waits on it with the
+// fixed 1 s bound) wakes and stops; the producer waits (1 s bound) for its
+// copies in flight.  Only then does the CTA free its tensor memory and exit.
 template <int BN, int STAGES, int NP = 4>
 __global__ void __launch_bounds__(kThreads, 1)
-    chi_tc_kernel(const __grid_constant__ CUtensorMap tmap, int ngpad, int brow, int nkb, int kb_per_seg, int ntiles,
-                  const int2* __restrict__ tiles, int bf16, float* __restrict__ work, int* __restrict__ status) {
+    chi_tc_kernel(const __grid_constant__ CUtensorMap tmap, int ngpad, int brow, int nkb, int kb_per_seg, int segs,
+                  int ntiles, const int2* __restrict__ tiles, int bf16, unsigned long long wait_ns,
+                  float* __restrict__ work, int* __restrict__ status) {
   using L = Layout<BN, NP>;
+  constexpr int HC = BN / 2;        // columns per epilogue thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage);
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* tfree = done + 1;
+  uint64_t* mflush = tfree + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mflush + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int seg = blockIdx.x / ntiles, tix = blockIdx.x - seg * ntiles;
+  const int grp = blockIdx.x / ntiles, tix = blockIdx.x - grp * ntiles;
   const int2 tile = tiles[tix];
   const int row0 = tile.x * BM, col0 = tile.y * BN;
-  const int kb0 = seg * kb_per_seg;
-  const int kb1 = min(nkb, kb0 + kb_per_seg);
-  const int nk = kb1 - kb0;
+  const int kb0 = grp * segs * kb_per_seg;
+  const int kb1 = min(nkb, kb0 + segs * kb_per_seg);
+  const int nk = max(0, kb1 - kb0);
+  const int nseg = (nk + kb_per_seg - 1) / kb_per_seg;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -176,10 +202,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(done, 1);
+    mbar_init(tfree, kEpiWarps);
+    mbar_init(mflush, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == kEpiWarps) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"((uint32_t)L::kTmemCols)
                  : "memory");
@@ -191,128 +219,162 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
   const uint32_t t_re = tmem, t_im = tmem + BN, t_rec = tmem + 2 * BN, t_imc = tmem + 3 * BN;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    int issued = 0;
-    for (int i = 0; i < nk; ++i) {
-      const int s = i % STAGES;
-      if (i >= STAGES && !mbar_wait(&empty[s], ((i / STAGES) - 1) & 1, abort_flag)) {
-        *abort_flag = 1;
-        break;
-      }
-      unsigned char* st = smem + s * L::kStage;
-      mbar_expect_tx(&full[s], L::kStage);
-      const int kx = (kb0 + i) * BK;
+  if (warp == kEpiWarps) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % STAGES;
+        if (i >= STAGES && !mbar_wait(&empty[s], ((i / STAGES) - 1) & 1, abort_flag, wait_ns)) {
+          if (!*abort_flag) atomicExch(status, (int)kDevTimeout);
+          *abort_flag = 1;
+          break;
+        }
+        unsigned char* st = smem + s * L::kStage;
+        mbar_expect_tx(&full[s], L::kStage);
+        const int kx = (kb0 + i) * BK;
 #pragma unroll
-      for (int pl = 0; pl < NP; ++pl) {
-        tma_load_2d(st + pl * L::kATile, &tmap, &full[s], kx, pl * ngpad + row0);
-        tma_load_2d(st + NP * L::kATile + pl * L::kBTile, &tmap, &full[s], kx, brow + pl * ngpad + col0);
+        for (int pl = 0; pl < NP; ++pl) {
+          tma_load_2d(st + pl * L::kATile, &tmap, &full[s], kx, pl * ngpad + row0);
+          tma_load_2d(st + NP * L::kATile + pl * L::kBTile, &tmap, &full[s], kx, brow + pl * ngpad + col0);
+        }
+        issued = i + 1;
       }
-      issued = i + 1;
-    }
-    // Never leave copies in flight: wait (bounded) until every issued stage
-    // has landed before this CTA may exit.
-    for (int i = max(0, issued - STAGES); i < issued; ++i) {
-      uint64_t t0 = globaltimer();
-      while (!mbar_try_wait(&full[i % STAGES], (i / STAGES) & 1) && globaltimer() - t0 < kWaitNs) {
+      // Never leave copies in flight: wait (bounded) until every issued stage
+      // has landed before this CTA may exit.
+      for (int i = max(0, issued - STAGES); i < issued; ++i) {
+        uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(&full[i % STAGES], (i / STAGES) & 1) && globaltimer() - t0 < kWaitNs) {
+        }
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    const uint32_t id = idesc(BN, bf16 != 0, false);
-    const uint32_t idn = idesc(BN, bf16 != 0, true);
-    bool ok = true;
-    for (int i = 0; i < nk && ok; ++i) {
-      const int s = i % STAGES;
-      if (!mbar_wait(&full[s], (i / STAGES) & 1, abort_flag)) {
+  } else if (warp == kEpiWarps + 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t id = idesc(BN, bf16 != 0, false);
+      const uint32_t idn = idesc(BN, bf16 != 0, true);
+      bool ok = true;
+      for (int i = 0; i < nk && ok; ++i) {
+        const int s = i % STAGES;
+        const int kin = i % kb_per_seg;       // k-block inside the segment
+        if (kin == 0 && i > 0) {
+          // the previous segment's sums must have left tensor memory
+          if (!mbar_wait(tfree, ((i / kb_per_seg) - 1) & 1, abort_flag, wait_ns)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+        }
+        if (!mbar_wait(&full[s], (i / STAGES) & 1, abort_flag, wait_ns)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t base = smem_u32(smem + s * L::kStage);
+#pragma unroll
+        for (int ks = 0; ks < BK / 16; ++ks) {
+          const uint32_t off = ks * 32;  // 16 values x 2 B along K
+          const uint32_t first = (kin > 0 || ks > 0) ? 1u : 0u;
+          if constexpr (NP == 2) {
+            // real flavor: planes (x_hi, x_lo); x x' = hi hi' + (hi lo' + lo hi')
+            const uint64_t ah = sdesc(base + off), al = sdesc(base + L::kATile + off);
+            const uint64_t bh = sdesc(base + 2 * L::kATile + off), bl = sdesc(base + 2 * L::kATile + L::kBTile + off);
+            mma(t_re, ah, bh, id, first);
+            mma(t_rec, ah, bl, id, first);
+            mma(t_rec, al, bh, id, 1);
+            continue;
+          }
+          const uint64_t arh = sdesc(base + 0 * L::kATile + off), aih = sdesc(base + 1 * L::kATile + off);
+          const uint64_t arl = sdesc(base + 2 * L::kATile + off), ail = sdesc(base + 3 * L::kATile + off);
+          const uint32_t bb = base + 4 * L::kATile;
+          const uint64_t brh = sdesc(bb + 0 * L::kBTile + off), bih = sdesc(bb + 1 * L::kBTile + off);
+          const uint64_t brl = sdesc(bb + 2 * L::kBTile + off), bil = sdesc(bb + 3 * L::kBTile + off);
+          // Re += xr xr' + xi xi': hi*hi into t_re, hi*lo + lo*hi into t_rec
+          mma(t_re, arh, brh, id, first);
+          mma(t_re, aih, bih, id, 1);
+          mma(t_rec, arh, brl, id, first);
+          mma(t_rec, arl, brh, id, 1);
+          mma(t_rec, aih, bil, id, 1);
+          mma(t_rec, ail, bih, id, 1);
+          // Im += xr xi' - xi xr': hi*hi into t_im, corrections into t_imc
+          mma(t_im, arh, bih, id, first);
+          mma(t_im, aih, brh, idn, 1);
+          mma(t_imc, arh, bil, id, first);
+          mma(t_imc, arl, bih, id, 1);
+          mma(t_imc, aih, brl, idn, 1);
+          mma(t_imc, ail, brh, idn, 1);
+        }
+        mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+        if (kin == kb_per_seg - 1 || i == nk - 1) mma_commit(done);   // the segment's sums are complete
+      }
+      if (!ok) {
+        // Let every MMA issued so far finish (the tensor memory is freed
+        // after this thread reaches the final barrier), then wake the
+        // epilogue: it sees the abort flag and stops.
+        mma_commit(mflush);
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(mflush, 0) && globaltimer() - t0 < kWaitNs) {
+        }
+        if (!*abort_flag) atomicExch(status, (int)kDevTimeout);
         *abort_flag = 1;
-        ok = false;
+        mma_commit(done);
+      }
+    }
+  } else {
+    // ---------------- epilogue: tensor memory -> FP32 running sums
+    const int q = warp & 3, h = warp >> 2;
+    const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + (uint32_t)(h * HC);
+    float acc_re[HC], acc_im[HC];
+#pragma unroll
+    for (int j = 0; j < HC; ++j) acc_re[j] = acc_im[j] = 0.f;
+    bool have = nseg > 0;
+    for (int sg = 0; sg < nseg; ++sg) {
+      bool got = mbar_wait(done, sg & 1, abort_flag, kWaitNs, false);
+      got = __all_sync(0xffffffffu, got) != 0;   // tcgen05.ld needs the whole warp
+      if (!got) {
+        if (lane == 0 && !*abort_flag) atomicExch(status, (int)kDevTimeout);
+        *abort_flag = 1;
+      }
+      if (!got || __any_sync(0xffffffffu, *abort_flag != 0)) {
+        have = false;
         break;
       }
       fence_after();
-      const uint32_t base = smem_u32(smem + s * L::kStage);
 #pragma unroll
-      for (int ks = 0; ks < BK / 16; ++ks) {
-        const uint32_t off = ks * 32;  // 16 values x 2 B along K
-        const uint32_t first = (i > 0 || ks > 0) ? 1u : 0u;
-        if constexpr (NP == 2) {
-          // real flavor: planes (x_hi, x_lo); x x' = hi hi' + (hi lo' + lo hi')
-          const uint64_t ah = sdesc(base + off), al = sdesc(base + L::kATile + off);
-          const uint64_t bh = sdesc(base + 2 * L::kATile + off), bl = sdesc(base + 2 * L::kATile + L::kBTile + off);
-          mma(t_re, ah, bh, id, first);
-          mma(t_rec, ah, bl, id, first);
-          mma(t_rec, al, bh, id, 1);
-          continue;
+      for (int c0 = 0; c0 < HC; c0 += 8) {
+        uint32_t a[8], b[8], ac[8], bc[8];
+        tmem_ld8(t_re + lane_off + c0, a);
+        tmem_ld8(t_rec + lane_off + c0, ac);
+        if constexpr (NP != 2) {
+          tmem_ld8(t_im + lane_off + c0, b);
+          tmem_ld8(t_imc + lane_off + c0, bc);
         }
-        const uint64_t arh = sdesc(base + 0 * L::kATile + off), aih = sdesc(base + 1 * L::kATile + off);
-        const uint64_t arl = sdesc(base + 2 * L::kATile + off), ail = sdesc(base + 3 * L::kATile + off);
-        const uint32_t bb = base + 4 * L::kATile;
-        const uint64_t brh = sdesc(bb + 0 * L::kBTile + off), bih = sdesc(bb + 1 * L::kBTile + off);
-        const uint64_t brl = sdesc(bb + 2 * L::kBTile + off), bil = sdesc(bb + 3 * L::kBTile + off);
-        // Re += xr xr' + xi xi': hi*hi into t_re, hi*lo + lo*hi into t_rec
-        mma(t_re, arh, brh, id, first);
-        mma(t_re, aih, bih, id, 1);
-        mma(t_rec, arh, brl, id, first);
-        mma(t_rec, arl, brh, id, 1);
-        mma(t_rec, aih, bil, id, 1);
-        mma(t_rec, ail, bih, id, 1);
-        // Im += xr xi' - xi xr': hi*hi into t_im, corrections into t_imc
-        mma(t_im, arh, bih, id, first);
-        mma(t_im, aih, brh, idn, 1);
-        mma(t_imc, arh, bil, id, first);
-        mma(t_imc, arl, bih, id, 1);
-        mma(t_imc, aih, brl, idn, 1);
-        mma(t_imc, ail, brh, idn, 1);
+        tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          acc_re[c0 + k] += __uint_as_float(a[k]) + __uint_as_float(ac[k]);
+          if constexpr (NP != 2) acc_im[c0 + k] += __uint_as_float(b[k]) + __uint_as_float(bc[k]);
+        }
       }
-      mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tfree);   // this warp's share of tensor memory is free again
     }
-    if (ok) mma_commit(done);
-  }
-  __syncwarp();
-
-  // ---------------- epilogue: tensor memory -> FP32 workspace
-  bool have = mbar_wait(done, 0, abort_flag);
-  have = __all_sync(0xffffffffu, have) != 0;   // tcgen05.ld needs the whole warp
-  if (!have) {
-    if (threadIdx.x == 0) atomicExch(status, (int)kDevTimeout);
-    *abort_flag = 1;
-  }
-  fence_after();
-  __syncwarp();
-  if (have && nk > 0) {
-    const int row = warp * 32 + lane;
-    float* wre = work + ((size_t)seg * ntiles + tix) * 2 * BM * BN;
-    float* wim = wre + BM * BN;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t a[16], b[16], ac[16], bc[16];
-      tmem_ld16(t_re + lane_off + c0, a);
-      tmem_ld16(t_rec + lane_off + c0, ac);
-      if constexpr (NP == 2) {
+    if (have) {
+      const int row = q * 32 + lane;
+      float* wre = work + ((size_t)grp * ntiles + tix) * 2 * BM * BN + (size_t)row * BN + h * HC;
+      float* wim = wre + BM * BN;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) b[q] = bc[q] = 0u;   // real flavor: no imaginary part
-      } else {
-        tmem_ld16(t_im + lane_off + c0, b);
-        tmem_ld16(t_imc + lane_off + c0, bc);
+      for (int c = 0; c < HC; c += 4) {
+        *reinterpret_cast<float4*>(wre + c) = make_float4(acc_re[c], acc_re[c + 1], acc_re[c + 2], acc_re[c + 3]);
+        *reinterpret_cast<float4*>(wim + c) = make_float4(acc_im[c], acc_im[c + 1], acc_im[c + 2], acc_im[c + 3]);
       }
-      tmem_ld_wait();
-      float4* pr = reinterpret_cast<float4*>(wre + (size_t)row * BN + c0);
-      float4* pi = reinterpret_cast<float4*>(wim + (size_t)row * BN + c0);
-#define BGW_SUM(x, y, k) (__uint_as_float(x[k]) + __uint_as_float(y[k]))
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        pr[q] = make_float4(BGW_SUM(a, ac, 4 * q), BGW_SUM(a, ac, 4 * q + 1), BGW_SUM(a, ac, 4 * q + 2),
-                            BGW_SUM(a, ac, 4 * q + 3));
-        pi[q] = make_float4(BGW_SUM(b, bc, 4 * q), BGW_SUM(b, bc, 4 * q + 1), BGW_SUM(b, bc, 4 * q + 2),
-                            BGW_SUM(b, bc, 4 * q + 3));
-      }
-#undef BGW_SUM
     }
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == kEpiWarps) {
+    __syncwarp();
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)L::kTmemCols)
                  : "memory");
@@ -714,12 +776,43 @@ constexpr int kStages = 3;
 constexpr int kSegPairsDefault = 512;
 }  // namespace
 
-// Bound of the FP32 segment workspace and of the operand planes of one chunk
-// of pairs; larger calls are processed chunk by chunk, each chunk's FP64 sum
-// added into chi.
-constexpr size_t kChunkBytes = size_t(1) << 30;
+// Bound of the operand planes of one chunk of pairs (as large as the chunk's
+// complex64 M); larger calls are processed chunk by chunk, each chunk's FP64
+// sum added into chi.
+constexpr size_t kChunkBytes = size_t(4) << 30;
 
 namespace {
+
+// Segments per CTA for nseg segments over ntiles tiles: the fewest groups of
+// segments (one FP32 partial per tile and group) whose grid of groups x
+// tiles CTAs fills the SMs in nearly whole waves (at least 90 % of the last
+// wave busy), else the grid with the best wave efficiency.
+int segs_per_cta(long long nseg, int ntiles, int nsm) {
+  if (nseg <= 1) return 1;
+  int best = (int)nseg;
+  double best_eff = -1.0;
+  for (long long gc = 1; gc <= nseg; ++gc) {
+    const long long per = (nseg + gc - 1) / gc;
+    const long long groups = (nseg + per - 1) / per;
+    const double waves = (double)(groups * ntiles) / nsm;
+    const double eff = waves / std::ceil(waves);
+    if (eff >= 0.9) return (int)per;
+    if (eff > best_eff) {
+      best_eff = eff;
+      best = (int)per;
+    }
+  }
+  return best;
+}
+
+int sm_count(Ctx* c) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = 152;
+  }
+  return n;
+}
 
 // Both products: the Hermitian one (wr: real weights, X = Y = M sqrt|w|,
 // lower tiles, mirrored) and the general one (wc: complex weights, X = M,
@@ -742,20 +835,27 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
     for (int J = 0; J < ntc; ++J)
       if (general || J * kBN <= I * BM + BM - 1) tl.push_back(make_int2(I, J));
   const int ntiles = (int)tl.size();
-  const size_t seg_bytes = (size_t)ntiles * 2 * BM * kBN * sizeof(float);
-  long long segs_per_chunk = std::max<long long>(1, (long long)(kChunkBytes / seg_bytes));
-  segs_per_chunk = std::min<long long>(
-      segs_per_chunk, std::max<long long>(1, (long long)(kChunkBytes / (2ull * nplanes * ngpad * seg_pairs))));
+  const size_t part_bytes = (size_t)ntiles * 2 * BM * kBN * sizeof(float);   // one FP32 partial per tile
+  const long long segs_per_chunk =
+      std::max<long long>(1, (long long)(kChunkBytes / (2ull * nplanes * ngpad * seg_pairs)));
   long long kchunk = std::min<long long>(segs_per_chunk * seg_pairs, (K + BK - 1) / BK * BK);
   if (c->chi_chunk_pairs > 0) kchunk = std::max<long long>(BK, (long long)c->chi_chunk_pairs / BK * BK);
   const long long kcpad = (kchunk + BK - 1) / BK * BK;
+  const int nsm = sm_count(c);
+  // groups of segments per chunk (a shorter last chunk may take more groups)
+  auto groups_of = [&](long long kc) {
+    const long long nseg = ((kc + BK - 1) / BK + kb_per_seg - 1) / kb_per_seg;
+    const int per = segs_per_cta(nseg, ntiles, nsm);
+    return std::make_pair(per, (nseg + per - 1) / per);
+  };
+  const long long last = K - (K - 1) / kchunk * kchunk;
+  const long long ngroups_max = std::max(groups_of(std::min(kchunk, K)).second, groups_of(last).second);
   const void* d_tiles;
   if ((rc = upload_cached(c, tl.data(), tl.size() * sizeof(int2), st, &d_tiles)) != BGW_OK) return rc;
   Scratch planes, work, mx;
   planes.pool = work.pool = mx.pool = &c->pool;
-  const long long nseg_max = (kcpad / BK + kb_per_seg - 1) / kb_per_seg;
   const size_t plane_bytes = (size_t)nplanes * ngpad * kcpad * 2;
-  const size_t work_bytes = (size_t)nseg_max * seg_bytes;
+  const size_t work_bytes = (size_t)ngroups_max * part_bytes;
   if ((rc = c->pool.alloc(plane_bytes, &planes.ptr)) != BGW_OK || (rc = c->pool.alloc(work_bytes, &work.ptr)) != BGW_OK ||
       (rc = c->pool.alloc(2 * sizeof(unsigned int), &mx.ptr)) != BGW_OK)
     return fail(c, rc, "bgw_chi_sum (mixed): scratch allocation failed (planes %zu B, workspace %zu B)", plane_bytes,
@@ -801,7 +901,8 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
       const long long kc = std::min(kchunk, K - p0);
       const long long kpad = (kc + BK - 1) / BK * BK;
       const int nkb = (int)(kpad / BK);
-      const int nseg = (nkb + kb_per_seg - 1) / kb_per_seg;
+      const auto grp = groups_of(kc);
+      const int per = grp.first, ngroups = (int)grp.second;
       {
         TimedScope ts(c, kTChiSplit, st);
         dim3 sg((unsigned)(kpad / 32), (unsigned)(ngpad / 32));
@@ -833,13 +934,13 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
       {
         TimedScope ts(c, kTChiTc, st);
         if (real)
-          chi_tc_kernel<kBN, kStages, 2><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
-              tmap, ngpad, brow, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
-              c->d_status);
+          chi_tc_kernel<kBN, kStages, 2><<<(unsigned)((long long)ngroups * ntiles), kThreads, smem, st>>>(
+              tmap, ngpad, brow, nkb, kb_per_seg, per, ntiles, static_cast<const int2*>(d_tiles), bf16, c->wait_ns,
+              work.as<float>(), c->d_status);
         else
-          chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
-              tmap, ngpad, brow, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
-              c->d_status);
+          chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)ngroups * ntiles), kThreads, smem, st>>>(
+              tmap, ngpad, brow, nkb, kb_per_seg, per, ntiles, static_cast<const int2*>(d_tiles), bf16, c->wait_ns,
+              work.as<float>(), c->d_status);
       }
       {
         TimedScope ts(c, kTChiReduce, st);
@@ -848,15 +949,15 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
         const int acc = (accumulate || p0 > 0) ? 1 : 0;
         if (real)
           reduce_real_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-              work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(),
+              work.as<float>(), ngroups, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(),
               bf16, acc, static_cast<double*>(chi) + (size_t)f * ng * ng);
         else if (general)
           reduce_general_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-              work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, scale, mx.as<unsigned int>(),
+              work.as<float>(), ngroups, ntiles, static_cast<const int2*>(d_tiles), ng, scale, mx.as<unsigned int>(),
               bf16, acc, cf);
         else
           reduce_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-              work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(),
+              work.as<float>(), ngroups, ntiles, static_cast<const int2*>(d_tiles), ng, -scale, mx.as<unsigned int>(),
               bf16, acc, cf);
       }
       BGW_CUDA(c, cudaGetLastError());
@@ -893,12 +994,14 @@ int tc_rows_gemm(Ctx* c, int prec, int R1, int R2, int K, const void* X, const v
   const int kb_per_seg = std::max(1, kSegPairsDefault / BK);
   const int nkb = kpad / BK;
   const int nseg = (nkb + kb_per_seg - 1) / kb_per_seg;
+  const int per = segs_per_cta(nseg, ntiles, sm_count(c));
+  const int ngroups = (nseg + per - 1) / per;
   const size_t plane = (size_t)rpad * kpad;
   const void* d_tiles;
   if ((rc = upload_cached(c, tl.data(), tl.size() * sizeof(int2), st, &d_tiles)) != BGW_OK) return rc;
   Scratch planes, work, mx;
   planes.pool = work.pool = mx.pool = &c->pool;
-  const size_t work_bytes = (size_t)nseg * ntiles * 2 * BM * kBN * sizeof(float);
+  const size_t work_bytes = (size_t)ngroups * ntiles * 2 * BM * kBN * sizeof(float);
   if ((rc = c->pool.alloc(8 * plane * 2, &planes.ptr)) != BGW_OK || (rc = c->pool.alloc(work_bytes, &work.ptr)) != BGW_OK ||
       (rc = c->pool.alloc(2 * sizeof(unsigned int), &mx.ptr)) != BGW_OK)
     return fail(c, rc, "tensor-core product: scratch allocation failed");
@@ -940,15 +1043,15 @@ int tc_rows_gemm(Ctx* c, int prec, int R1, int R2, int K, const void* X, const v
   }
   {
     TimedScope ts(c, kTChiTc, st);
-    chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)nseg * ntiles), kThreads, smem, st>>>(
-        tmap, rpad, 4 * rpad, nkb, kb_per_seg, ntiles, static_cast<const int2*>(d_tiles), bf16, work.as<float>(),
-        c->d_status);
+    chi_tc_kernel<kBN, kStages><<<(unsigned)((long long)ngroups * ntiles), kThreads, smem, st>>>(
+        tmap, rpad, 4 * rpad, nkb, kb_per_seg, per, ntiles, static_cast<const int2*>(d_tiles), bf16, c->wait_ns,
+        work.as<float>(), c->d_status);
   }
   {
     TimedScope ts(c, kTChiReduce, st);
     const long long ne = (long long)ntiles * BM * kBN;
     reduce_rows_kernel<kBN><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-        work.as<float>(), nseg, ntiles, static_cast<const int2*>(d_tiles), R1, R2, mb, bf16,
+        work.as<float>(), ngroups, ntiles, static_cast<const int2*>(d_tiles), R1, R2, mb, bf16,
         static_cast<double2*>(C));
   }
   BGW_CUDA(c, cudaGetLastError());

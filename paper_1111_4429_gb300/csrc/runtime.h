@@ -136,7 +136,8 @@ struct Ctx {
   bool chi_tc_ready = false;
   uint64_t launches = 0;     // kernels launched by this context
   int chi_segment_pairs = 0; // mixed chi: pairs per FP32 accumulation segment (0 = default)
-  int chi_chunk_pairs = 0;   // mixed chi: pairs per workspace chunk (0 = sized to 1 GiB)
+  int chi_chunk_pairs = 0;   // mixed chi: pairs per chunk of operand planes (0 = sized to 4 GiB)
+  unsigned long long wait_ns = 1000000000ull;  // limit of the tensor-core chi kernels' pipeline waits
   // Content-keyed caches (hash_bytes over the bytes plus sizes).
   std::unordered_map<uint64_t, void*> uploads;           // small host arrays
   std::unordered_map<uint64_t, std::unique_ptr<BandPlan>> band_plans;

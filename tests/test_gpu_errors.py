@@ -113,7 +113,42 @@ def test_zero_pivot_sets_numeric_status(ctx):
     ctx.sync()   # status was cleared
 
 
-@pytest.mark.parametrize("option,bad,good", [("BGW_OPT_UPDATE_SLICES", [1, 6, 8, -1], [0, 5, 7]),
+def test_chi_wait_limit_reports_timeout_and_context_recovers(ctx):
+    """With a wait limit of 0, every wait of the tensor-core chi kernels that
+    is not already complete gives up (a TMA copy cannot land before the MMA
+    issuer's first look): each CTA lets its copies and MMAs in flight finish,
+    frees its tensor memory and returns, and bgw_sync reports BGW_ETIMEOUT.
+    The context and the GPU stay usable: the same call with the default
+    limit then gives the oracle's chi."""
+    from paper_1111_4429_gb300 import bgw
+    import oracle
+    # K = 5400 pairs: several 512-pair segments per CTA
+    s = synth.make_system("k", a=14.0, fft=24, ecut_wfn=8.0, ecut_eps=2.0, nv=6, nc=900, seed=55)
+    cell = bgw.system_cell(s)
+    M = torch.empty((s.npairs, s.ng), dtype=torch.complex64, device="cuda")
+    ctx.mtxel(cell, s.gv, torch.from_numpy(s.cv).cuda(), s.gc, torch.from_numpy(s.cc).cuda(), s.geps,
+              bgw.BGW_PREC_MIX_FP16, M)
+    chi = torch.zeros((1, s.ng, s.ng), dtype=torch.complex128, device="cuda")
+    ctx.sync()
+    ctx.set_option(bgw.BGW_OPT_WAIT_LIMIT_NS, 0)
+    try:
+        ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, s.ec, None, bgw.BGW_PREC_MIX_FP16, False, chi)
+        with pytest.raises(bgw.BgwError) as e:
+            ctx.sync()
+        assert e.value.code == bgw.BGW_ETIMEOUT
+    finally:
+        ctx.set_option(bgw.BGW_OPT_WAIT_LIMIT_NS, 10 ** 9)
+    ctx.sync()   # status was cleared
+    ctx.chi_sum(cell, s.nv, s.nc, s.ng, M, s.ev, s.ec, None, bgw.BGW_PREC_MIX_FP16, False, chi)
+    ctx.sync()
+    m = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    want = oracle.chi(m, oracle.chi_weights(s.ev, s.ec), s.omega)
+    got = chi[0].cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-5
+
+
+@pytest.mark.parametrize("option,bad,good", [("BGW_OPT_WAIT_LIMIT_NS", [-1, 10 ** 10 + 1], [10 ** 9, 0, 10 ** 10]),
+                                             ("BGW_OPT_UPDATE_SLICES", [1, 6, 8, -1], [0, 5, 7]),
                                              ("BGW_OPT_DOUBLE_FP32", [2, -2], [-1, 0, 1]),
                                              ("BGW_OPT_SIGMA_DENSITY", [2, -2], [-1, 0, 1]),
                                              ("BGW_OPT_INVERSE", [2, -2], [-1, 0, 1])])

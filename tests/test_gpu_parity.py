@@ -106,6 +106,21 @@ def test_mtxel_fp32_vs_oracle(ctx, n):
     assert _rel(got, ref) <= TOL32_M
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [30, 36, 48, 50, 60, 64])
+def test_mtxel_large_grids_vs_oracle(ctx, n, prec):
+    # the grids of the larger cells (60: the 30.78 bohr cell's grid; radices
+    # 2, 3, 4, 5 in every mix), a 12 Ry wavefunction and 6 Ry epsilon sphere
+    # in a cell of n / 2 bohr (alias-free: 2 sqrt(12) + sqrt(6) < 2 pi n / a)
+    s = synth.make_system("mL", a=0.5 * n, fft=n, ecut_wfn=12.0, ecut_eps=6.0, nv=3, nc=7, seed=400 + n)
+    ref = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    got = _mtxel(ctx, s, prec=prec).cpu().numpy().astype(np.complex128)
+    assert _rel(got, ref) <= (TOL64 if prec == 0 else TOL32_M)
+    # element by element: every entry within the bar of its row's largest
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(got - ref) <= (TOL64 if prec == 0 else TOL32_M) * scale)
+
+
 # ------------------------------------------------------------------ chi, eps, inverse
 
 def _chi(ctx, s, M, omega=None, chunks=None):
