@@ -38,7 +38,12 @@ def gsphere(bvec: np.ndarray, kfrac: Sequence[float], ecut: float) -> np.ndarray
     """All integer G with |(G + k) . B|^2 < ecut (strict, FP64).
 
     Ordered by |(G+k)B|^2 ascending, ties broken lexicographically on
-    (Gx, Gy, Gz).  Returns int32 [n][3].
+    (Gx, Gy, Gz).  Lengths that are equal in exact arithmetic (G vectors
+    related by a symmetry of the cell) can differ in their last bits
+    depending on the order of the floating-point sum, which differs between
+    machines; lengths within a relative 1e-9 of their predecessor therefore
+    count as ties, so the order -- and every input drawn in that order -- is
+    the same on every machine.  Returns int32 [n][3].
     """
     bvec = np.asarray(bvec, dtype=np.float64)
     kf = np.asarray(kfrac, dtype=np.float64)
@@ -54,7 +59,11 @@ def gsphere(bvec: np.ndarray, kfrac: Sequence[float], ecut: float) -> np.ndarray
     e = np.einsum("ij,ij->i", kc, kc)
     keep = e < ecut
     g, e = g[keep], e[keep]
-    order = np.lexsort((g[:, 2], g[:, 1], g[:, 0], e))
+    by_len = np.argsort(e, kind="stable")
+    es = e[by_len]
+    tie_group = np.concatenate([[0], np.cumsum(np.diff(es) > 1e-9 * np.maximum(es[1:], 1e-300))])
+    gs = g[by_len]
+    order = by_len[np.lexsort((gs[:, 2], gs[:, 1], gs[:, 0], tie_group))]
     return np.ascontiguousarray(g[order].astype(np.int32))
 
 

@@ -42,6 +42,21 @@ def test_gsphere_strict_cutoff_and_order():
     assert len({tuple(x) for x in g.tolist()}) == g.shape[0]
 
 
+@pytest.mark.parametrize("a,ecut,qx10", [(30.78, 6.0, 1), (30.78, 12.0, 1), (30.78, 12.0, 0), (20.52, 6.0, 5)])
+def test_gsphere_order_is_exact(a, ecut, qx10):
+    """The order of a sphere is the exact one, so it is the same on every
+    machine: in a cubic cell |q + G|^2 b^-2 = (G_x + q_x)^2 + G_y^2 + G_z^2,
+    which for q_x = qx10 / 10 is the integer (10 G_x + qx10)^2 + 100 (G_y^2 +
+    G_z^2) over 100.  Lengths equal in exact arithmetic (G_y and G_z swapped,
+    signs flipped) must follow the lexicographic order of (G_x, G_y, G_z),
+    whatever the last bits of their floating-point lengths."""
+    bvec, _ = synth.cubic_cell(a)
+    g = synth.gsphere(bvec, (qx10 / 10.0, 0, 0), ecut).astype(np.int64)
+    key = (10 * g[:, 0] + qx10) ** 2 + 100 * (g[:, 1] ** 2 + g[:, 2] ** 2)
+    exact = np.lexsort((g[:, 2], g[:, 1], g[:, 0], key))
+    assert np.array_equal(exact, np.arange(g.shape[0]))
+
+
 def test_config_sphere_sizes():
     for name, ng, npw_c, npw_v in [("c0", 85, 587, 583), ("c1", 2120, 6031, 6059)]:
         p = synth.CONFIGS[name]
