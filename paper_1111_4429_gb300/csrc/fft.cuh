@@ -41,12 +41,14 @@ template <typename T, int S> __device__ __forceinline__ cpx<T> mul_i(cpx<T> a) {
 }
 
 // Supported line lengths and their offsets in the twiddle table.
+// Lengths 6, 9 and 15 serve only as the quarter-length sub-transforms of
+// 24, 36 and 60 (fft_quarters).
 __host__ __device__ constexpr int twiddle_offset(int n) {
   return n == 8 ? 0 : n == 10 ? 8 : n == 12 ? 18 : n == 16 ? 30 : n == 20 ? 46 : n == 24 ? 66
        : n == 30 ? 90 : n == 32 ? 120 : n == 36 ? 152 : n == 40 ? 188 : n == 48 ? 228
-       : n == 50 ? 276 : n == 60 ? 326 : n == 64 ? 386 : -1;
+       : n == 50 ? 276 : n == 60 ? 326 : n == 64 ? 386 : n == 9 ? 450 : n == 15 ? 459 : n == 6 ? 474 : -1;
 }
-constexpr int kTwiddleTotal = 450;
+constexpr int kTwiddleTotal = 480;
 constexpr int kSupportedN[] = {8, 10, 12, 16, 20, 24, 30, 32, 36, 40, 48, 50, 60, 64};
 
 // First radix of a sub-length: 4 while it divides, then 2, 3, 5.
@@ -116,6 +118,7 @@ template <> __device__ __forceinline__ float2 twiddle_entry<float>(int i) { retu
 // e^{S 2 pi i t / N}
 template <typename T, int N, int S>
 __device__ __forceinline__ cpx<T> twiddle(int t) {
+  static_assert(twiddle_offset(N) >= 0, "no twiddle table for this length");
   cpx<T> w = twiddle_entry<T>(twiddle_offset(N) + t);
   return mk<T>(w.x, T(S) * w.y);
 }
@@ -135,7 +138,9 @@ __device__ __forceinline__ void fft_stage(cpx<T> (&x)[N], cpx<T> (&y)[N]) {
       y[q + st * (r * p)] = b[0];
 #pragma unroll
       for (int k = 1; k < r; ++k) {
-        if (p == 0) {
+        if constexpr (m == 1) {   // a single stage: no twiddles
+          y[q + st * (r * p + k)] = b[k];
+        } else if (p == 0) {
           y[q + st * (r * p + k)] = b[k];
         } else {
           y[q + st * (r * p + k)] = mul<T>(b[k], twiddle<T, N, S>((p * k * (N / n)) % N));
@@ -160,10 +165,45 @@ __device__ __forceinline__ void fft_line(cpx<T> (&a)[N]) {
   }
 }
 
+// The two outer quarters of a length-N transform (N = 4M), for lines whose
+// kept outputs all lie in k < M or k >= 3M (a band |k| < M around zero):
+//   lo[k2] = X[k2],  hi[k2] = X[k2 + 3M],  k2 = 0 .. M-1,
+// with X[k] = sum_n x_n e^{+2 pi i n k / N} and x_n = load(n).  Decimation
+// in time by 4: with n = n1 + 4 n2 and k = k2 + M k1,
+//   X[k2 + M k1] = sum_{n1} e^{2 pi i n1 k1 / 4} e^{2 pi i n1 k2 / N} Y_{n1}[k2],
+// Y_{n1} the length-M transform of x_{n1 + 4 n2}; k1 = 0 and 3 only, so the
+// factors e^{2 pi i n1 k1 / 4} are 1 and (-i)^{n1}.  One sub-transform is
+// live at a time: about 2.5 N registers instead of the 4 N of a full line,
+// and half of the final radix-4 combinations are never formed.
+template <typename T, int N, typename Load>
+__device__ __forceinline__ void fft_quarters(Load load, cpx<T> (&lo)[N / 4], cpx<T> (&hi)[N / 4]) {
+  constexpr int M = N / 4;
+  static_assert(N % 4 == 0, "fft_quarters needs N divisible by 4");
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    cpx<T> y[M];
+#pragma unroll
+    for (int n2 = 0; n2 < M; ++n2) y[n2] = load(n1 + 4 * n2);
+    fft_line<T, M, 1>(y);
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) {
+      const cpx<T> t = (n1 == 0 || k2 == 0) ? y[k2] : mul<T>(y[k2], twiddle<T, N, 1>(n1 * k2));
+      const cpx<T> u = n1 == 0 ? t : n1 == 1 ? mk<T>(t.y, -t.x) : n1 == 2 ? mk<T>(-t.x, -t.y) : mk<T>(-t.y, t.x);
+      if (n1 == 0) {
+        lo[k2] = t;
+        hi[k2] = u;
+      } else {
+        lo[k2] = add<T>(lo[k2], t);
+        hi[k2] = add<T>(hi[k2], u);
+      }
+    }
+  }
+}
+
 // Fill this translation unit's twiddle tables on the current device.  The
 // values are computed on the host in long double and rounded once.
 static inline cudaError_t upload_twiddles() {
-  static const int ns[] = {8, 10, 12, 16, 20, 24, 30, 32, 36, 40, 48, 50, 60, 64};
+  static const int ns[] = {8, 10, 12, 16, 20, 24, 30, 32, 36, 40, 48, 50, 60, 64, 9, 15, 6};
   double2 h64[kTwiddleTotal];
   float2 h32[kTwiddleTotal];
   const long double two_pi = 6.283185307179586476925286766559005768L;

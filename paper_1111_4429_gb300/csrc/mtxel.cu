@@ -112,6 +112,13 @@ int get_pair_plan(Ctx* c, int n, int ng, const int32_t* geps, cudaStream_t st, c
   plan->ng = ng;
   plan->ncol = ncol;
   plan->nys = nys;
+  // The low-band kernels take only the outer quarters k < n/4 and k >= 3n/4
+  // of every line: allowed when each kept frequency on each axis is there.
+  auto in_band = [n](int k) { return 4 * k < n || 4 * k >= 3 * n; };
+  plan->lowband = n % 4 == 0;
+  for (int i = 0; i < ng && plan->lowband; ++i)
+    for (int d = 0; d < 3; ++d)
+      if (!in_band(wrap(geps[3 * i + d], n))) plan->lowband = false;
   int rc;
   if ((rc = upload_vec(c, yslot_of_k, st, &plan->d_yslot_of_k)) != BGW_OK) return rc;
   if ((rc = upload_vec(c, colmap, st, &plan->d_colmap)) != BGW_OK) return rc;

@@ -108,11 +108,15 @@ __global__ void __launch_bounds__(64) band_yxpass(const cpx<T>* __restrict__ U1,
 // ---------------------------------------------------------------- pair y,x
 // grid (ceil(npb/ppb), N), block >= 32.  Pairs pbase .. pbase+npb-1.
 // smem: Y[ppb][nys][N+1] | Tz[ppb][ncol] | colmap[N*nys] | yslot[N]
-// FP32: at most 128 registers, so two 256-thread blocks share an SM (the
-// register-limited single block leaves the SM latency-bound); FP64 keeps
-// its registers (a cap would spill).
-template <typename T, int N>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) pair_yxpass(const cpx<T>* __restrict__ uv,
+// LB (low band): every kept frequency lies in |k| < N/4 along y and x, so
+// each line takes the two outer quarters of its transform (fft_quarters:
+// one quarter-length sub-transform live at a time) instead of the whole
+// line in registers.  FP32: at most 128 registers, so two 256-thread blocks
+// share an SM (a register-limited single block leaves the SM latency-bound);
+// a whole FP32 line of more than 40 points needs more, and FP64 keeps its
+// registers (a cap would spill).
+template <typename T, int N, bool LB>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && (LB || N <= 40)) ? 2 : 1) pair_yxpass(const cpx<T>* __restrict__ uv,
                                                    const cpx<T>* __restrict__ uc, int nc,
                                                    int pbase, int npb, int ppb, int nys, int ncol,
                                                    const int* __restrict__ g_colmap,
@@ -138,15 +142,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) pair_yxpass(const
     const int v = p / nc, c = p - v * nc;
     const cpx<T>* pv = uv + ((size_t)v * N + z) * plane + x;
     const cpx<T>* pc = uc + ((size_t)c * N + z) * plane + x;
-    cpx<T> a[N];
-#pragma unroll
-    for (int y = 0; y < N; ++y) a[y] = cmulc<T>(pv[(size_t)y * N], pc[(size_t)y * N]);
-    fft_line<T, N, 1>(a);
     cpx<T>* yrow = Y + (size_t)pp * nys * LD + x;
+    if constexpr (LB) {
+      constexpr int Q = N / 4;
+      cpx<T> lo[Q], hi[Q];
+      fft_quarters<T, N>([&](int y) { return cmulc<T>(pv[(size_t)y * N], pc[(size_t)y * N]); }, lo, hi);
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int s = yslot[k];
-      if (s >= 0) yrow[s * LD] = a[k];
+      for (int k = 0; k < Q; ++k) {
+        const int s0 = yslot[k], s3 = yslot[k + 3 * Q];
+        if (s0 >= 0) yrow[s0 * LD] = lo[k];
+        if (s3 >= 0) yrow[s3 * LD] = hi[k];
+      }
+    } else {
+      cpx<T> a[N];
+#pragma unroll
+      for (int y = 0; y < N; ++y) a[y] = cmulc<T>(pv[(size_t)y * N], pc[(size_t)y * N]);
+      fft_line<T, N, 1>(a);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int s = yslot[k];
+        if (s >= 0) yrow[s * LD] = a[k];
+      }
     }
   }
   __syncthreads();
@@ -154,15 +170,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) pair_yxpass(const
   for (int j = tid; j < npp * nys; j += nt) {
     const int pp = j / nys, s = j - pp * nys;
     const cpx<T>* row = Y + ((size_t)pp * nys + s) * LD;
-    cpx<T> a[N];
-#pragma unroll
-    for (int x = 0; x < N; ++x) a[x] = row[x];
-    fft_line<T, N, 1>(a);
     cpx<T>* tz = Tz + (size_t)pp * ncol;
+    if constexpr (LB) {
+      constexpr int Q = N / 4;
+      cpx<T> lo[Q], hi[Q];
+      fft_quarters<T, N>([&](int x) { return row[x]; }, lo, hi);
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int col = colmap[k * nys + s];
-      if (col >= 0) tz[col] = a[k];
+      for (int k = 0; k < Q; ++k) {
+        const int c0 = colmap[k * nys + s], c3 = colmap[(k + 3 * Q) * nys + s];
+        if (c0 >= 0) tz[c0] = lo[k];
+        if (c3 >= 0) tz[c3] = hi[k];
+      }
+    } else {
+      cpx<T> a[N];
+#pragma unroll
+      for (int x = 0; x < N; ++x) a[x] = row[x];
+      fft_line<T, N, 1>(a);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int col = colmap[k * nys + s];
+        if (col >= 0) tz[col] = a[k];
+      }
     }
   }
   __syncthreads();
@@ -176,7 +204,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) pair_yxpass(const
 // ---------------------------------------------------------------- pair z
 // grid (npb), block 256.  smem Mrow[ng], or none with direct != 0 (a list
 // too long for shared memory: the outputs go straight to M, complex only).
-template <typename T, int N>
+template <typename T, int N, bool LB>
 __global__ void __launch_bounds__(256) pair_zgather(const cpx<T>* __restrict__ Tbuf, int pbase,
                                                     int ncol, int ng,
                                                     const int* __restrict__ zmap,
@@ -188,14 +216,26 @@ __global__ void __launch_bounds__(256) pair_zgather(const cpx<T>* __restrict__ T
   const T inv = T(1) / T(N * N * N);
   const cpx<T>* src = Tbuf + (size_t)pl * N * ncol;
   for (int col = tid; col < ncol; col += nt) {
-    cpx<T> a[N];
+    if constexpr (LB) {
+      constexpr int Q = N / 4;
+      cpx<T> lo[Q], hi[Q];
+      fft_quarters<T, N>([&](int z) { return src[(size_t)z * ncol + col]; }, lo, hi);
 #pragma unroll
-    for (int z = 0; z < N; ++z) a[z] = src[(size_t)z * ncol + col];
-    fft_line<T, N, 1>(a);
+      for (int k = 0; k < Q; ++k) {
+        const int g0 = zmap[k * ncol + col], g3 = zmap[(k + 3 * Q) * ncol + col];
+        if (g0 >= 0) Mrow[g0] = scale<T>(lo[k], inv);
+        if (g3 >= 0) Mrow[g3] = scale<T>(hi[k], inv);
+      }
+    } else {
+      cpx<T> a[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int g = zmap[k * ncol + col];
-      if (g >= 0) Mrow[g] = scale<T>(a[k], inv);
+      for (int z = 0; z < N; ++z) a[z] = src[(size_t)z * ncol + col];
+      fft_line<T, N, 1>(a);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int g = zmap[k * ncol + col];
+        if (g >= 0) Mrow[g] = scale<T>(a[k], inv);
+      }
     }
   }
   if (direct) return;
@@ -229,7 +269,7 @@ static void pair_block_shape(int ppb, int nys, int ncol, int* threads, size_t* s
 // the first pairs of the call (the second run is timed with CUDA events on
 // the call's stream) and the fastest is kept for this (grid, precision,
 // epsilon-sphere shape).  Runs once per shape, outside graph capture.
-template <typename T, int N>
+template <typename T, int N, bool LB>
 static int tune_pairs_per_block(const MtxelExec& x, const cpx<T>* uv, const cpx<T>* uc, cpx<T>* Tb) {
   const PairPlan* pp = x.pp;
   const int npb = (int)std::min<long long>((long long)x.nv * x.nc, std::min<long long>(x.pair_block, 4096));
@@ -247,14 +287,14 @@ static int tune_pairs_per_block(const MtxelExec& x, const cpx<T>* uv, const cpx<
     size_t sm;
     pair_block_shape<T, N>(p, pp->nys, pp->ncol, &threads, &sm);
     if (sm > 200 * 1024 || p * N > 1024) continue;
-    if (set_smem(pair_yxpass<T, N>, sm) != cudaSuccess) {
+    if (set_smem(pair_yxpass<T, N, LB>, sm) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {
       cudaEventRecord(e0, x.st);
-      pair_yxpass<T, N><<<dim3((npb + p - 1) / p, N), threads, sm, x.st>>>(
+      pair_yxpass<T, N, LB><<<dim3((npb + p - 1) / p, N), threads, sm, x.st>>>(
           uv, uc, x.nc, 0, npb, p, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
       cudaEventRecord(e1, x.st);
     }
@@ -288,8 +328,8 @@ static cudaError_t band_transform(const BandPlan* bp, const void* coef, int real
   return cudaGetLastError();
 }
 
-template <typename T, int N>
-static cudaError_t mtxel_exec_n(const MtxelExec& x) {
+template <typename T, int N, bool LB>
+static cudaError_t mtxel_exec_lb(const MtxelExec& x) {
   using C = cpx<T>;
   C* uv = reinterpret_cast<C*>(x.uv);
   C* uc = reinterpret_cast<C*>(x.uc);
@@ -306,33 +346,45 @@ static cudaError_t mtxel_exec_n(const MtxelExec& x) {
   const PairPlan* pp = x.pp;
   int ppb = x.tuned_ppb ? *x.tuned_ppb : 0;
   if (ppb <= 0) {
-    ppb = tune_pairs_per_block<T, N>(x, uv, uc, Tb);
+    ppb = tune_pairs_per_block<T, N, LB>(x, uv, uc, Tb);
     if (x.tuned_ppb) *x.tuned_ppb = ppb;
   }
   int threads;
   size_t sm;
   pair_block_shape<T, N>(ppb, pp->nys, pp->ncol, &threads, &sm);
-  if ((e = set_smem(pair_yxpass<T, N>, sm)) != cudaSuccess) return e;
+  if ((e = set_smem(pair_yxpass<T, N, LB>, sm)) != cudaSuccess) return e;
   size_t smz = (size_t)pp->ng * sizeof(C);
   const int zdirect = (smz > 200 * 1024 && !x.real) ? 1 : 0;
   if (zdirect) smz = 0;
-  else if ((e = set_smem(pair_zgather<T, N>, smz)) != cudaSuccess) return e;
+  else if ((e = set_smem(pair_zgather<T, N, LB>, smz)) != cudaSuccess) return e;
   const long long npairs = (long long)x.nv * x.nc;
   for (long long p0 = 0; p0 < npairs; p0 += x.pair_block) {
     const int npb = (int)((npairs - p0) < x.pair_block ? (npairs - p0) : x.pair_block);
     {
       TimedScope ts(x.ctx, kTPairYX, x.st);
-      pair_yxpass<T, N><<<dim3((npb + ppb - 1) / ppb, N), threads, sm, x.st>>>(
+      pair_yxpass<T, N, LB><<<dim3((npb + ppb - 1) / ppb, N), threads, sm, x.st>>>(
           uv, uc, x.nc, (int)p0, npb, ppb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
     }
     {
       TimedScope ts(x.ctx, kTPairZ, x.st);
-      pair_zgather<T, N><<<npb, 256, smz, x.st>>>(Tb, (int)p0, pp->ncol, pp->ng, pp->d_zmap, M, x.real, zdirect);
+      pair_zgather<T, N, LB><<<npb, 256, smz, x.st>>>(Tb, (int)p0, pp->ncol, pp->ng, pp->d_zmap, M, x.real,
+                                                      zdirect);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *x.launches += 2;
   }
   return cudaSuccess;
+}
+
+// The low-band kernels where the plan allows them (every kept frequency in
+// |k| < N/4 on all three axes, N divisible by 4), the whole-line ones
+// otherwise.
+template <typename T, int N>
+static cudaError_t mtxel_exec_n(const MtxelExec& x) {
+  if constexpr (N % 4 == 0 && N >= 16) {
+    if (x.pp->lowband) return mtxel_exec_lb<T, N, true>(x);
+  }
+  return mtxel_exec_lb<T, N, false>(x);
 }
 
 #define BGW_FOR_EACH_N(X) X(8) X(10) X(12) X(16) X(20) X(24) X(30) X(32) X(36) X(40) X(48) X(50) X(60) X(64)

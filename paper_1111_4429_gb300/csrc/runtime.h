@@ -87,6 +87,7 @@ struct BandPlan {        // band transform of one wavefunction sphere
 };
 struct PairPlan {        // pruned product transform onto the epsilon sphere
   int n = 0, ng = 0, ncol = 0, nys = 0;
+  bool lowband = false;         // every kept k (all three axes) in k < n/4 or k >= 3n/4
   int* d_yslot_of_k = nullptr;  // [n] ky-slot of FFT index k along y, or -1
   int* d_colmap = nullptr;      // [n][nys] column of (kx=k, ky=slot) or -1 (k-major)
   int* d_zmap = nullptr;        // [n][ncol] G index of (column, kz=k) or -1 (k-major)

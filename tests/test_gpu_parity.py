@@ -121,6 +121,18 @@ def test_mtxel_large_grids_vs_oracle(ctx, n, prec):
     assert np.all(np.abs(got - ref) <= (TOL64 if prec == 0 else TOL32_M) * scale)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mtxel_wide_eps_sphere_vs_oracle(ctx, prec):
+    # an epsilon sphere reaching |G_x| = 6 = n / 4 on the 24 grid: the kernels
+    # that keep only the outer quarters of each line cannot serve it, the
+    # whole-line ones must
+    s = synth.make_system("mw", a=14.0, fft=24, ecut_wfn=3.0, ecut_eps=9.0, nv=3, nc=5, seed=451)
+    assert np.abs(s.geps).max() >= 6
+    ref = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    got = _mtxel(ctx, s, prec=prec).cpu().numpy().astype(np.complex128)
+    assert _rel(got, ref) <= (TOL64 if prec == 0 else TOL32_M)
+
+
 # ------------------------------------------------------------------ chi, eps, inverse
 
 def _chi(ctx, s, M, omega=None, chunks=None):
