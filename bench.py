@@ -832,7 +832,7 @@ def run_serve_c4(prec, nreq=24, seed=1004):
     reqs = synth.serve_requests(200, seed)[:nreq]
     systems = [synth.request_system(r) for r in reqs]
     outs = [torch.empty((s.ng, s.ng), dtype=torch.complex128).pin_memory() for s in systems]
-    srv = bgw.Server(0, hbm_budget_bytes=120 << 30, max_slots=4, prec=prec)
+    srv = bgw.Server(bgw.Context(0), hbm_budget_bytes=120 << 30, max_slots=4, prec=prec)
     # warm the slots' plans and tuning with one pass, then calibrate
     t = [srv.submit(s, o) for s, o in zip(systems, outs)]
     for x in t:

@@ -436,6 +436,12 @@ int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* problems,
  * Every request runs the whole path (bgw_epsilon) in opts->prec.
  * Thread safety: submit, poll and cancel may be called from any thread.
  *
+ *   ctx                    the context whose device serves the requests;
+ *                          the server gives every slot a context of its own
+ *                          on that device (a slot's pool, plans and streams
+ *                          must not be shared with other slots or with the
+ *                          caller's own calls), so ctx is only read at open
+ *                          and may be used or destroyed independently
  *   opts.hbm_budget_bytes  bound on the sum of the estimates of admitted
  *                          requests (0 = 90 % of the free device memory at
  *                          open); a request whose estimate exceeds it alone
@@ -472,7 +478,7 @@ typedef struct bgw_result {
 
 typedef struct bgw_server bgw_server;
 
-int bgw_serve_open(int device, const bgw_serve_opts* opts, bgw_server** out);
+int bgw_serve_open(bgw_ctx* ctx, const bgw_serve_opts* opts, bgw_server** out);
 int bgw_serve_submit(bgw_server* srv, const bgw_request* req, uint64_t* ticket);
 int bgw_serve_poll(bgw_server* srv, uint64_t ticket, int timeout_ms, bgw_result* out);
 int bgw_serve_cancel(bgw_server* srv, uint64_t ticket);

@@ -125,7 +125,7 @@ def load() -> ctypes.CDLL:
                                ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.bgw_epsinv_noalloc.argtypes = [cellp, ci, i32p, vp, vp, vp, vp]
     lib.bgw_epsilon_batch.argtypes = [vp, ci, ctypes.POINTER(Problem), ci, dp, ci, ctypes.POINTER(vp), vp]
-    lib.bgw_serve_open.argtypes = [ci, ctypes.POINTER(ServeOpts), ctypes.POINTER(vp)]
+    lib.bgw_serve_open.argtypes = [vp, ctypes.POINTER(ServeOpts), ctypes.POINTER(vp)]
     lib.bgw_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     lib.bgw_serve_poll.argtypes = [vp, ctypes.c_uint64, ci, ctypes.POINTER(Result)]
     lib.bgw_serve_cancel.argtypes = [vp, ctypes.c_uint64]
@@ -439,11 +439,12 @@ class Server:
     """bgw_serve_*: requests of different sizes, admitted by an HBM budget
     and run concurrently on per-slot streams."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_slots: int = 4, prec: int = BGW_PREC_MIX_FP16):
+    def __init__(self, ctx: "Context", hbm_budget_bytes: int = 0, max_slots: int = 4, prec: int = BGW_PREC_MIX_FP16):
+        """ctx: the Context whose device serves the requests (read at open)."""
         self.lib = load()
         o = ServeOpts(hbm_budget_bytes, max_slots, prec)
         h = ctypes.c_void_p()
-        rc = self.lib.bgw_serve_open(device, ctypes.byref(o), ctypes.byref(h))
+        rc = self.lib.bgw_serve_open(ctx.h, ctypes.byref(o), ctypes.byref(h))
         if rc != BGW_OK:
             raise BgwError(rc, "bgw_serve_open failed")
         self.h = h

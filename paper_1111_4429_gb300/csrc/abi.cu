@@ -187,6 +187,7 @@ int run_graphed(Ctx* c, uint64_t key, cudaStream_t st, const std::function<int()
   if (e != cudaSuccess || rc != BGW_OK || !graph) {
     cudaGetLastError();
     if (graph) cudaGraphDestroy(graph);
+    c->pool.abandon_pins();   // no graph refers to them
     c->err.clear();
     return BGW_OK;  // the direct run's results stand; the next call runs directly again
   }
@@ -195,6 +196,7 @@ int run_graphed(Ctx* c, uint64_t key, cudaStream_t st, const std::function<int()
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    c->pool.abandon_pins();
     return BGW_OK;
   }
   c->graphs[key].exec = exec;
@@ -749,6 +751,7 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   if (e != cudaSuccess || rc != BGW_OK || !graph) {
     cudaGetLastError();
     if (graph) cudaGraphDestroy(graph);
+    c->pool.abandon_pins();   // no graph refers to them
     c->err.clear();
     return BGW_OK;  // results of the direct run stand; the next call runs directly again
   }
@@ -757,6 +760,7 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    c->pool.abandon_pins();
     return BGW_OK;
   }
   c->graphs[key].exec = exec;

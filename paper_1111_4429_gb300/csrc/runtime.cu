@@ -93,7 +93,7 @@ int Pool::alloc_impl(size_t bytes, void** out, bool keep) {
     live_[p] = sz;
     in_use_ += sz;
     if (in_use_ > high_water_) high_water_ = in_use_;
-    if (pinning_) pinned_[p] = sz;
+    if (pinning_ && pinned_.emplace(p, sz).second) capture_pins_.push_back(p);
     *out = p;
     return BGW_OK;
   }

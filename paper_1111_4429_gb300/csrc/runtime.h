@@ -45,7 +45,15 @@ class Pool {
   void trim();  // cudaFree every cached free block not pinned by a graph
   // While pinning is on, every block handed out is marked pinned: a CUDA
   // graph captured meanwhile refers to it, so trim() must never free it.
-  void set_pinning(bool on) { pinning_ = on; }
+  // A capture that fails unpins what it pinned (abandon_pins).
+  void set_pinning(bool on) {
+    pinning_ = on;
+    if (on) capture_pins_.clear();
+  }
+  void abandon_pins() {
+    for (void* p : capture_pins_) pinned_.erase(p);
+    capture_pins_.clear();
+  }
   void unpin_all() { pinned_.clear(); }
   uint64_t in_use() const { return in_use_; }
   uint64_t reserved() const { return reserved_; }
@@ -61,6 +69,7 @@ class Pool {
   std::multimap<size_t, void*> free_;
   std::unordered_map<void*, size_t> live_;
   std::unordered_map<void*, size_t> pinned_;
+  std::vector<void*> capture_pins_;   // blocks pinned by the capture in progress
   bool pinning_ = false;
 };
 

@@ -129,7 +129,10 @@ uint64_t estimate_bytes(const Req& r, int prec) {
   const uint64_t u1 = (uint64_t)std::max(r.nv, r.nc) * n * ncol_wfn * cs;
   const uint64_t T = std::min<uint64_t>(K * n * ncol_eps * cs, uint64_t(4) << 30);
   const uint64_t M = K * r.ng * cs;
-  const uint64_t chi_mixed = prec == BGW_PREC_FP64 ? 0 : (uint64_t(2) << 30) + K * 8;
+  // operand planes (at most 4 GiB per chunk), per-tile FP32 partials, weights
+  const uint64_t ngpad = (r.ng + 127) / 128 * 128;
+  const uint64_t chi_mixed = prec == BGW_PREC_FP64 ? 0
+                             : std::min<uint64_t>(8 * ngpad * K, uint64_t(4) << 30) + (uint64_t(1) << 30) + K * 8;
   const uint64_t mats = 3ull * r.ng * r.ng * 16 + 2ull * r.ng * 32 * 16;
   const uint64_t coef = ((uint64_t)r.nv * r.npw_v + (uint64_t)r.nc * r.npw_c) * 16;
   return grids + u1 + T + M + chi_mixed + mats + coef + (64ull << 20);
@@ -246,8 +249,9 @@ using bgw::Server;
 
 extern "C" {
 
-int bgw_serve_open(int device, const bgw_serve_opts* opts, bgw_server** out) {
-  if (!opts || !out || opts->max_slots <= 0 || opts->max_slots > 64) return BGW_EINVAL;
+int bgw_serve_open(bgw_ctx* ctx, const bgw_serve_opts* opts, bgw_server** out) {
+  if (!ctx || !opts || !out || opts->max_slots <= 0 || opts->max_slots > 64) return BGW_EINVAL;
+  const int device = ctx->impl.device;
   if (opts->prec != BGW_PREC_FP64 && opts->prec != BGW_PREC_MIX_FP16 && opts->prec != BGW_PREC_MIX_BF16)
     return BGW_EINVAL;
   *out = nullptr;

@@ -40,7 +40,7 @@ def test_served_mix_matches_alone_and_oracle():
         pytest.skip("no CUDA device")
     from paper_1111_4429_gb300 import bgw
     reqs = _requests()
-    srv = bgw.Server(0, hbm_budget_bytes=64 << 30, max_slots=3, prec=bgw.BGW_PREC_MIX_FP16)
+    srv = bgw.Server(bgw.Context(0), hbm_budget_bytes=64 << 30, max_slots=3, prec=bgw.BGW_PREC_MIX_FP16)
     outs = [np.zeros((s.ng, s.ng), dtype=np.complex128) for s in reqs]
     pinned = [torch.zeros((s.ng, s.ng), dtype=torch.complex128).pin_memory() for s in reqs[:2]]
     tickets = []
@@ -65,14 +65,14 @@ def test_over_budget_request_is_refused_and_queue_cancel():
     from paper_1111_4429_gb300 import bgw
     small = synth.config_system("c0")
     big = synth.make_system("big", a=20.52, fft=40, ecut_wfn=10.0, ecut_eps=3.0, nv=8, nc=400, seed=9)
-    srv = bgw.Server(0, hbm_budget_bytes=256 << 20, max_slots=1, prec=bgw.BGW_PREC_MIX_FP16)
+    srv = bgw.Server(bgw.Context(0), hbm_budget_bytes=256 << 20, max_slots=1, prec=bgw.BGW_PREC_MIX_FP16)
     o1 = np.zeros((big.ng, big.ng), dtype=np.complex128)
     t_big = srv.submit(big, o1)                 # estimate far above 256 MiB
     r = srv.poll(t_big, timeout_ms=60000)
     assert r["status"] == bgw.BGW_ENOMEM
     srv.close()
 
-    srv = bgw.Server(0, hbm_budget_bytes=0, max_slots=1, prec=bgw.BGW_PREC_MIX_FP16)
+    srv = bgw.Server(bgw.Context(0), hbm_budget_bytes=0, max_slots=1, prec=bgw.BGW_PREC_MIX_FP16)
     outs = [np.zeros((small.ng, small.ng), dtype=np.complex128) for _ in range(4)]
     o_big = np.zeros((big.ng, big.ng), dtype=np.complex128)
     t0 = srv.submit(big, o_big)                 # occupies the only slot
