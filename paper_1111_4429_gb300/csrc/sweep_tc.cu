@@ -93,6 +93,11 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
       "l"(a), "l"(b), "r"(id), "r"(acc)
       : "memory");
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -407,7 +412,7 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, vol
 // look-ahead CTA sweeps the next diagonal block in double FP32 (about 2^-46
 // per operation, on the FP32 pipe) instead of FP64.
 template <bool realv, int SL, bool FFC>
-__global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per sub-partition, 96 registers
+__global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per sub-partition, 120 registers
     update_pipe_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
                        const __grid_constant__ OzBatch b, int k0, int rows_total, int buf, int mode,
                        const int* __restrict__ sig, const int* __restrict__ tau, int* __restrict__ status) {
@@ -566,14 +571,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
         const int tt = t + k;
         const int j0 = Js[k] * BN;
         const int c0 = part * 8;
-        double2 av[8];
         int ex[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int j = j0 + c0 + q;
           const bool jblock = j >= k0 && j < k0 + kb;
           const bool live = row_ok && j < ng && (mode == 3 ? true : (j <= i && !jblock));
-          av[q] = (live && !jblock) ? M.A[(size_t)i * ng + j] : make_double2(0.0, 0.0);
           ex[q] = live ? ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA : 1 << 20;
         }
         bool have = mbar_wait_ab(t_full, tt & 1, abort_flag);
@@ -581,38 +584,48 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
         float hr[8], lr[8], hm[8], lm[8];
         if (have) {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // Two passes of four columns: each issues the loads of every level
+          // (re and im) before one wait, so the tensor-memory round trips of
+          // a tile are two instead of one per level.
 #pragma unroll
-          for (int L = 0; L < SL; ++L) {
-            uint32_t x[8], y[8];
-            tmem_ld8(tmem + lane_off + L * 2 * BN + c0, x);
-            if constexpr (!realv) tmem_ld8(tmem + lane_off + L * 2 * BN + BN + c0, y);
+          for (int hh = 0; hh < 2; ++hh) {
+            uint32_t x[SL][4], y[SL][4];
+#pragma unroll
+            for (int L = 0; L < SL; ++L) {
+              tmem_ld4(tmem + lane_off + L * 2 * BN + c0 + 4 * hh, x[L]);
+              if constexpr (!realv) tmem_ld4(tmem + lane_off + L * 2 * BN + BN + c0 + 4 * hh, y[L]);
+            }
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const float w = ldexpf(1.f, -BETA * L);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float vr = __fmul_rn(__uint_as_float(x[q]), w);
-              const float vi = realv ? 0.f : __fmul_rn(__uint_as_float(y[q]), w);
-              if (L == 0) {
-                hr[q] = vr;
-                lr[q] = 0.f;
-                hm[q] = vi;
-                lm[q] = 0.f;
-              } else if (L <= kTwoSumLevels) {
-                // levels that can reach the running sum's last bits: exact two-sum
-                float sm, e;
-                two_sum(hr[q], vr, sm, e);
-                hr[q] = sm;
-                lr[q] = __fadd_rn(lr[q], e);
-                if constexpr (!realv) {
-                  two_sum(hm[q], vi, sm, e);
-                  hm[q] = sm;
-                  lm[q] = __fadd_rn(lm[q], e);
+            for (int L = 0; L < SL; ++L) {
+              const float w = ldexpf(1.f, -BETA * L);
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                const int q = 4 * hh + qq;
+                const float vr = __fmul_rn(__uint_as_float(x[L][qq]), w);
+                const float vi = realv ? 0.f : __fmul_rn(__uint_as_float(y[L][qq]), w);
+                if (L == 0) {
+                  hr[q] = vr;
+                  lr[q] = 0.f;
+                  hm[q] = vi;
+                  lm[q] = 0.f;
+                } else if (L <= kTwoSumLevels) {
+                  // levels that can reach the running sum's last bits: exact two-sum
+                  float sm, e;
+                  two_sum(hr[q], vr, sm, e);
+                  hr[q] = sm;
+                  lr[q] = __fadd_rn(lr[q], e);
+                  if constexpr (!realv) {
+                    two_sum(hm[q], vi, sm, e);
+                    hm[q] = sm;
+                    lm[q] = __fadd_rn(lm[q], e);
+                  }
+                } else {
+                  // deeper levels lie below the sum's last bit at the target
+                  // precision: they go to the low word
+                  lr[q] = __fadd_rn(lr[q], vr);
+                  if constexpr (!realv) lm[q] = __fadd_rn(lm[q], vi);
                 }
-              } else {
-                // deeper levels lie below the sum's last bit at the target
-                // precision: they go to the low word
-                lr[q] = __fadd_rn(lr[q], vr);
-                if constexpr (!realv) lm[q] = __fadd_rn(lm[q], vi);
               }
             }
           }
@@ -625,6 +638,14 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(t_empty)) : "memory");
         if (!have) continue;
+        // the tile's FP64 values, read while the next tile's MMAs run
+        double2 av[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = j0 + c0 + q;
+          const bool jblock = j >= k0 && j < k0 + kb;
+          av[q] = (ex[q] != (1 << 20) && !jblock) ? M.A[(size_t)i * ng + j] : make_double2(0.0, 0.0);
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           if (ex[q] == (1 << 20)) continue;
