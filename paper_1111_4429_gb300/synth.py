@@ -283,6 +283,44 @@ def serve_requests(n: int = 200, seed: int = 1004):
     return reqs
 
 
+def serve_systems(reqs, seed: int = 1004) -> List[System]:
+    """Systems of a served stream built from one band set per cell scale s:
+    the valence bands (N_v = 4 s^3) and the conduction bands of a request
+    are the first N_v and N_c columns of one QR-orthonormalized Gaussian
+    matrix per s (the first columns of Q depend only on the first columns of
+    the matrix, so each request's bands are exactly those its own QR would
+    give for that matrix), and every request draws its own energies from its
+    seed.  Requests of one scale therefore share coefficient values, which
+    keeps a stream of hundreds of requests cheap to generate; shapes and
+    distributions are those of request_system."""
+    masters = {}
+    out = []
+    q = (0.1, 0.0, 0.0)
+    for r in reqs:
+        sc = r["s"]
+        if sc not in masters:
+            a = 10.26 * sc
+            bvec, omega = cubic_cell(a)
+            gv = gsphere(bvec, q, 10.0)
+            gc = gsphere(bvec, (0.0, 0.0, 0.0), 10.0)
+            gen = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, sc])))
+            cv = orthonormal_bands(gen, gv.shape[0], 4 * sc ** 3)
+            cc = orthonormal_bands(gen, gc.shape[0], min(1500, gc.shape[0]))
+            masters[sc] = (a, bvec, omega, gv, gc, cv, cc, {})
+        a, bvec, omega, gv, gc, cv, cc, eps_spheres = masters[sc]
+        e = r["ecut_eps"]
+        if e not in eps_spheres:
+            eps_spheres[e] = gsphere(bvec, q, e)
+        nc = min(r["nc_draw"], cc.shape[0])
+        ss = np.random.SeedSequence(r["seed"]).spawn(len(_STREAMS))
+        gens = {k: np.random.Generator(np.random.PCG64(x)) for k, x in zip(_STREAMS, ss)}
+        ev = np.sort(gens["ev"].uniform(-0.5, 0.0, cv.shape[0]))
+        ec = np.sort(gens["ec"].uniform(0.04, 1.5, nc))
+        out.append(System(name=f"req{r['index']}", a=a, bvec=bvec, omega=omega, q_frac=np.asarray(q), fft=20 * sc,
+                          gv=gv, gc=gc, geps=eps_spheres[e], cv=cv, cc=cc[:nc], ev=ev, ec=ec, seed=r["seed"]))
+    return out
+
+
 def request_system(req: dict) -> System:
     s = req["s"]
     a = 10.26 * s
