@@ -201,6 +201,68 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && (LB || N <= 40)) ? 2 :
   }
 }
 
+// ---------------------------------------------------------------- pair y,x (warp per pair)
+// The low-band form of pair_yxpass with one warp per pair and no block-wide
+// barrier between the passes: the y pass over the N x columns (lane = x),
+// __syncwarp, then the x pass over the nys kept ky rows (lane = row), whose
+// kept columns go straight to T (a lane's columns are consecutive in T).  A
+// pair's two passes keep 32 lanes busy for 83 of 96 lane-lines at N = 60
+// instead of the block kernel's 332 of 512, and warps of a block move on
+// independently.  grid (ceil(npb / kPairWarps), N), block 32 kPairWarps.
+// smem: Y[kPairWarps][nys][N+1] | colmap[N*nys] | yslot[N].
+constexpr int kPairWarps = 4;
+constexpr int kWarpPerPair = 1000;   // tuner's code for pair_yxpass_warp
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * kPairWarps, sizeof(T) == 4 ? 4 : 2)
+    pair_yxpass_warp(const cpx<T>* __restrict__ uv, const cpx<T>* __restrict__ uc, int nc, int pbase, int npb,
+                     int nys, int ncol, const int* __restrict__ g_colmap, const int* __restrict__ g_yslot,
+                     cpx<T>* __restrict__ Tbuf) {
+  static_assert(N % 4 == 0, "low-band lines need N divisible by 4");
+  constexpr int LD = N + 1, Q = N / 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* Y = reinterpret_cast<cpx<T>*>(smem_raw);
+  int* colmap = reinterpret_cast<int*>(Y + (size_t)kPairWarps * nys * LD);
+  int* yslot = colmap + N * nys;
+  const int z = blockIdx.y, tid = threadIdx.x;
+  for (int i = tid; i < N * nys; i += blockDim.x) colmap[i] = g_colmap[i];
+  for (int i = tid; i < N; i += blockDim.x) yslot[i] = g_yslot[i];
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  const int pl = blockIdx.x * kPairWarps + warp;     // pair of this warp inside the call's block of pairs
+  if (pl >= npb) return;
+  const int p = pbase + pl;
+  const int v = p / nc, c = p - v * nc;
+  const size_t plane = (size_t)N * N;
+  const cpx<T>* pv = uv + ((size_t)v * N + z) * plane;
+  const cpx<T>* pc = uc + ((size_t)c * N + z) * plane;
+  cpx<T>* Yw = Y + (size_t)warp * nys * LD;
+  // y pass: conj(u_v) u_c formed on load, the kept ky of every x column
+  for (int x = lane; x < N; x += 32) {
+    cpx<T> lo[Q], hi[Q];
+    fft_quarters<T, N>([&](int y) { return cmulc<T>(pv[(size_t)y * N + x], pc[(size_t)y * N + x]); }, lo, hi);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const int s0 = yslot[k], s3 = yslot[k + 3 * Q];
+      if (s0 >= 0) Yw[s0 * LD + x] = lo[k];
+      if (s3 >= 0) Yw[s3 * LD + x] = hi[k];
+    }
+  }
+  __syncwarp();
+  // x pass: the kept (kx, ky) columns of each kept ky row, straight to T
+  cpx<T>* Tp = Tbuf + ((size_t)pl * N + z) * ncol;
+  for (int s = lane; s < nys; s += 32) {
+    const cpx<T>* row = Yw + (size_t)s * LD;
+    cpx<T> lo[Q], hi[Q];
+    fft_quarters<T, N>([&](int x) { return row[x]; }, lo, hi);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const int c0 = colmap[k * nys + s], c3 = colmap[(k + 3 * Q) * nys + s];
+      if (c0 >= 0) Tp[c0] = lo[k];
+      if (c3 >= 0) Tp[c3] = hi[k];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- pair z
 // grid (npb), block 256.  smem Mrow[ng], or none with direct != 0 (a list
 // too long for shared memory: the outputs go straight to M, complex only).
@@ -308,6 +370,29 @@ static int tune_pairs_per_block(const MtxelExec& x, const cpx<T>* uv, const cpx<
       best = p;
     }
   }
+  if constexpr (LB) {   // the warp-per-pair kernel as one more candidate
+    const size_t sm = (size_t)kPairWarps * pp->nys * (N + 1) * sizeof(cpx<T>) + (size_t)(N * pp->nys + N) * sizeof(int);
+    float ms = 0.f;
+    if (sm <= 200 * 1024 && set_smem(pair_yxpass_warp<T, N>, sm) == cudaSuccess) {
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, x.st);
+        pair_yxpass_warp<T, N><<<dim3((npb + kPairWarps - 1) / kPairWarps, N), 32 * kPairWarps, sm, x.st>>>(
+            uv, uc, x.nc, 0, npb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
+        cudaEventRecord(e1, x.st);
+      }
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+        *x.launches += 2;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = kWarpPerPair;
+        }
+      } else {
+        cudaGetLastError();
+      }
+    } else {
+      cudaGetLastError();
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return best > 0 ? best : (256 / N > 0 ? 256 / N : 1);
@@ -349,10 +434,19 @@ static cudaError_t mtxel_exec_lb(const MtxelExec& x) {
     ppb = tune_pairs_per_block<T, N, LB>(x, uv, uc, Tb);
     if (x.tuned_ppb) *x.tuned_ppb = ppb;
   }
-  int threads;
-  size_t sm;
-  pair_block_shape<T, N>(ppb, pp->nys, pp->ncol, &threads, &sm);
-  if ((e = set_smem(pair_yxpass<T, N, LB>, sm)) != cudaSuccess) return e;
+  const bool warp_kernel = LB && ppb == kWarpPerPair;
+  int threads = 32 * kPairWarps;
+  size_t sm = 0;
+  if constexpr (LB) {
+    if (warp_kernel) {
+      sm = (size_t)kPairWarps * pp->nys * (N + 1) * sizeof(C) + (size_t)(N * pp->nys + N) * sizeof(int);
+      if ((e = set_smem(pair_yxpass_warp<T, N>, sm)) != cudaSuccess) return e;
+    }
+  }
+  if (!warp_kernel) {
+    pair_block_shape<T, N>(ppb, pp->nys, pp->ncol, &threads, &sm);
+    if ((e = set_smem(pair_yxpass<T, N, LB>, sm)) != cudaSuccess) return e;
+  }
   size_t smz = (size_t)pp->ng * sizeof(C);
   const int zdirect = (smz > 200 * 1024 && !x.real) ? 1 : 0;
   if (zdirect) smz = 0;
@@ -362,8 +456,14 @@ static cudaError_t mtxel_exec_lb(const MtxelExec& x) {
     const int npb = (int)((npairs - p0) < x.pair_block ? (npairs - p0) : x.pair_block);
     {
       TimedScope ts(x.ctx, kTPairYX, x.st);
-      pair_yxpass<T, N, LB><<<dim3((npb + ppb - 1) / ppb, N), threads, sm, x.st>>>(
-          uv, uc, x.nc, (int)p0, npb, ppb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
+      if constexpr (LB) {
+        if (warp_kernel)
+          pair_yxpass_warp<T, N><<<dim3((npb + kPairWarps - 1) / kPairWarps, N), threads, sm, x.st>>>(
+              uv, uc, x.nc, (int)p0, npb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
+      }
+      if (!warp_kernel)
+        pair_yxpass<T, N, LB><<<dim3((npb + ppb - 1) / ppb, N), threads, sm, x.st>>>(
+            uv, uc, x.nc, (int)p0, npb, ppb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
     }
     {
       TimedScope ts(x.ctx, kTPairZ, x.st);
