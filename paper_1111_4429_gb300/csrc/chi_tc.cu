@@ -805,15 +805,6 @@ int segs_per_cta(long long nseg, int ntiles, int nsm) {
   return best;
 }
 
-int sm_count(Ctx* c) {
-  int n = 0;
-  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || n <= 0) {
-    cudaGetLastError();
-    n = 152;
-  }
-  return n;
-}
-
 // Both products: the Hermitian one (wr: real weights, X = Y = M sqrt|w|,
 // lower tiles, mirrored) and the general one (wc: complex weights, X = M,
 // Y = w M, all tiles).

@@ -62,6 +62,15 @@ int cuda_fail(Ctx* c, cudaError_t e, const char* what) {
   return fail(c, BGW_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+int sm_count(Ctx* c) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = 152;
+  }
+  return n;
+}
+
 // ------------------------------------------------------------------ Pool
 size_t Pool::round(size_t b) {
   if (b == 0) b = 1;

@@ -175,6 +175,8 @@ void timing_collect(Ctx* c);
 // Errors: set ctx->err and return the code.
 int fail(Ctx* c, int code, const char* fmt, ...);
 int cuda_fail(Ctx* c, cudaError_t e, const char* what);
+// Streaming multiprocessors of the context's device (152 if the query fails).
+int sm_count(Ctx* c);
 #define BGW_CUDA(c, expr)                                    \
   do {                                                       \
     cudaError_t _e = (expr);                                 \

@@ -98,6 +98,13 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* r) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
 }
+// 16 lanes x 256 bits: register pair (0, 1) holds lane base + l / 4, columns
+// 2 (l % 4) and 2 (l % 4) + 1; pair (2, 3) the same columns of lane base + 8 + l / 4.
+__device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -315,6 +322,41 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// (h + l) 2^ex as one double (rounded to nearest, ties away from zero) for
+// finite floats h, l and |ex| < 900, built in the integer pipe: the SM's FP64
+// pipe is the epilogue's bottleneck, and the FP64 form of the same value takes
+// a conversion-free add there per word.  A two-sum first makes the pair
+// non-overlapping (s = fl(h + l), |t| <= ulp(s) / 2), so s's 24-bit mantissa
+// placed at bits 61..38 of a 64-bit word plus t's shifted mantissa stays in
+// [2^61 - 2^37, 2^62): at most one bit of renormalisation.  Zero and
+// subnormal words take the two-conversion path.
+__device__ __forceinline__ double ff2d_scaled(float h, float l, int ex) {
+  float s, t;
+  two_sum(h, l, s, t);
+  const unsigned us = __float_as_uint(s), ut = __float_as_uint(t);
+  const unsigned es = (us >> 23) & 0xFFu, et = (ut >> 23) & 0xFFu;
+  if (es == 0u || es == 0xFFu || et == 0xFFu || (et == 0u && (ut << 1) != 0u))
+    return f2d_scaled(s, ex) + f2d_scaled(t, ex);
+  unsigned long long m = (unsigned long long)((us & 0x7FFFFFu) | 0x800000u) << 38;
+  int e = (int)es;
+  if ((ut << 1) != 0u) {
+    const unsigned g = es - et;   // >= 24 for a nonzero two-sum error
+    const unsigned long long b =
+        g < 64u ? ((unsigned long long)((ut & 0x7FFFFFu) | 0x800000u) << 38) >> g : 0ull;
+    m = ((us ^ ut) >> 31) ? m - b : m + b;
+    if (m < (1ull << 61)) {
+      m <<= 1;
+      --e;
+    }
+  }
+  // the mantissa's leading bit (bit 52 after the shift) adds one to the
+  // exponent field; the rounding carry may propagate into it
+  const unsigned long long bits =
+      ((unsigned long long)(us & 0x80000000u) << 32) |
+      ((((unsigned long long)(unsigned)(e + 895 + ex)) << 52) + (m >> 9) + ((m >> 8) & 1ull));
+  return __longlong_as_double((long long)bits);
+}
+
 // ---------------------------------------------------------------------------
 // Persistent, pipelined form of the update.  A CTA takes work items of up to
 // kJPI column tiles of one row tile I: the row's U slices are loaded once per item, the V slices of
@@ -385,6 +427,33 @@ __device__ inline void pipe_decode(int mode, int sl, int item, int nI, int nJ, i
   }
   J0 = J1 = 0;
 }
+// The same decode for a CTA that takes its items in increasing order: the
+// cursor keeps the row tile reached and its first item, so a persistent CTA
+// walks the rows once in all instead of once per item.
+struct PipeCursor {
+  int I = 0, base = 0;
+};
+__device__ inline void pipe_decode_next(PipeCursor& cur, int mode, int sl, int item, int nI, int nJ, int In, int Jn,
+                                        bool has_next, int& I, int& J0, int& J1) {
+  if (mode == 1) {
+    pipe_decode(mode, sl, item, nI, nJ, In, Jn, has_next, I, J0, J1);
+    return;
+  }
+  const int jpi = pipe_jpi(mode, sl);
+  for (; cur.I < nI; ++cur.I) {
+    const int w = row_width(mode, cur.I, nJ);
+    const int n = (mode == 2 && has_next && cur.I == In) ? 0 : (w + jpi - 1) / jpi;
+    if (item < cur.base + n) {
+      I = cur.I;
+      J0 = (item - cur.base) * jpi;
+      J1 = min(J0 + jpi, w);
+      return;
+    }
+    cur.base += n;
+  }
+  I = nI;
+  J0 = J1 = 0;
+}
 __device__ inline bool pipe_skip(int mode, int item, int I, int J, int ng, int k0, int kb, int In, int Jn,
                                  bool has_next) {
   const int i0 = I * BM, j0 = J * BN;
@@ -412,7 +481,7 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, vol
 // look-ahead CTA sweeps the next diagonal block in double FP32 (about 2^-46
 // per operation, on the FP32 pipe) instead of FP64.
 template <bool realv, int SL, bool FFC>
-__global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per sub-partition, 120 registers
+__global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per sub-partition, 96 registers
     update_pipe_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
                        const __grid_constant__ OzBatch b, int k0, int rows_total, int buf, int mode,
                        const int* __restrict__ sig, const int* __restrict__ tau, int* __restrict__ status) {
@@ -441,7 +510,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
   uint64_t* v_empty = v_full + 2;                    // [2]
   uint64_t* t_full = v_empty + 2;
   uint64_t* t_empty = t_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(t_empty + 1);
+  uint64_t* u_empty = t_empty + 1;                   // an item's MMAs are complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(u_empty + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ DiagSmem dsm;
 
@@ -455,6 +525,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(t_full)) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(t_empty)), "r"(kPipeEpiWarps) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(u_empty)) : "memory");
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -472,9 +543,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
   int items_done = 0;  // items processed
   int u_loads = 0;     // U loads issued (control; phase of u_full)
   int vissued = 0;     // V loads issued (control)
+  PipeCursor cursor;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++items_done) {
     int I, J0, J1;
-    pipe_decode(mode, SL, item, nI, nJ, In, Jn, has_next, I, J0, J1);
+    pipe_decode_next(cursor, mode, SL, item, nI, nJ, In, Jn, has_next, I, J0, J1);
     const int i0 = I * BM;
     // tiles of the item that are not skipped, in order
     int Js[kJPI], nt = 0;
@@ -482,15 +554,18 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
       if (!pipe_skip(mode, item, I, J, ng, k0, kb, In, Jn, has_next)) Js[nt++] = J;
     if (control) {
       if (lane == 0 && nt > 0 && !*abort_flag) {
-        // U slices of the row tile (the previous item's MMAs are complete:
-        // the item-end barrier follows its last epilogue)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(u_full)),
-                     "r"((uint32_t)(SL * kUTile))
-                     : "memory");
-        for (int a = 0; a < SL; ++a)
-          tma_load_2d(us + a * kUTile, &umap, u_full, 0, slice_base + a * rows_total + M.row_off + i0);
+        // U slices of the row tile, once the previous item's MMAs have read
+        // the last ones (its epilogue may still run: items are independent)
+        bool ok = u_loads == 0 || mbar_wait_ab(u_empty, (u_loads - 1) & 1, abort_flag);
         const int u_phase = u_loads & 1;
-        ++u_loads;
+        if (ok) {
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(u_full)),
+                       "r"((uint32_t)(SL * kUTile))
+                       : "memory");
+          for (int a = 0; a < SL; ++a)
+            tma_load_2d(us + a * kUTile, &umap, u_full, 0, slice_base + a * rows_total + M.row_off + i0);
+          ++u_loads;
+        }
         auto issue_v = [&](int tt, int J) {
           const int bq = tt & 1;
           if (tt >= 2 && !mbar_wait_ab(&v_empty[bq], ((tt - 2) >> 1) & 1, abort_flag)) return false;
@@ -502,8 +577,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
                         slice_base + a * rows_total + M.row_off + J * BN);
           return true;
         };
-        bool ok = issue_v(t, Js[0]);
-        vissued = t + 1;
+        ok = ok && issue_v(t, Js[0]);
+        if (ok) vissued = t + 1;
         for (int k = 0; k < nt && ok; ++k) {
           const int tt = t + k;
           if (k + 1 < nt) {
@@ -556,6 +631,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
                            smem_u32(t_full))
                        : "memory");
         }
+        if (ok)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(u_empty))
+                       : "memory");
         if (!ok) {
           *abort_flag = 1;
           atomicExch(status, (int)kDevTimeout);
@@ -563,40 +642,87 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
       }
       __syncwarp();
     } else {
-      // ---------------- epilogue warps: rows 32 (warp % 4) + lane, columns 8 (warp / 4) .. + 7
+      // ---------------- epilogue warps: rows 32 (warp % 4) .. + 31, columns 8 (warp / 4) .. + 7.
+      // The accumulators are read in the 16x256b shape: lane l holds rows
+      // g, g + 8, g + 16, g + 24 (g = l / 4) and columns 2 (l % 4), + 1, so one
+      // warp-wide access of A touches 8 rows of 128 contiguous bytes instead
+      // of 32 rows of 16 (four times fewer cache lines per instruction).
       const int quad = warp & 3, part = warp >> 2;
-      const int r = quad * 32 + lane;
-      const int i = i0 + r;
-      const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-      const bool row_ok = i < ng && !(i >= k0 && i < k0 + kb);
-      const int ei = row_ok ? sig[buf * rows_total + M.row_off + i] : 0;
+      const int g = lane >> 2, cl = 2 * (lane & 3);
+      const int c0 = part * 8;
+      // rows r0 + 8 m (m = 0 .. 3) and their exponents sigma
+      const int r0 = i0 + quad * 32 + g;
+      auto row_ok = [&](int i) { return i < ng && !(i >= k0 && i < k0 + kb); };
+      int ei[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) ei[m] = row_ok(r0 + 8 * m) ? sig[buf * rows_total + M.row_off + r0 + 8 * m] : 0;
+      // 128 bytes of A for tile kk (row g + 8 (lane % 4), the warp's eight
+      // columns) into L2, one tile ahead
+      const int prow = i0 + quad * 32 + g + 8 * (lane & 3);
+      const bool prow_ok = prow < ng;
+      auto prefetch_a = [&](int kk) {
+        if (!prow_ok || kk >= nt) return;
+        const int j = Js[kk] * BN + c0;
+        if (j >= ng) return;
+        const double2* row = M.A + (size_t)prow * ng;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(row + j));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(row + min(j + 7, ng - 1)));
+      };
+      // the column exponents of tile kk (read one tile ahead)
+      auto load_tau = [&](int kk, int (&tv)[2]) {
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+          const int j = kk < nt ? Js[kk] * BN + c0 + cl + n : ng;
+          tv[n] = j < ng ? tau[buf * rows_total + M.row_off + j] : 0;
+        }
+      };
+      // element e = 2 m + n of tile kk: row r0 + 8 m, column Js[kk] BN + c0 + cl + n,
+      // scale exponent ei[m] + tv[n] - 16.  Bit e of the mask: the element is
+      // updated; bit 8 + e: its old value is read (columns of the block K
+      // start from zero in the Gauss-Jordan form).
+      int tv[2];
+      unsigned mask = 0;
+      auto tile_mask = [&](int kk) {
+        const int j0 = Js[kk] * BN;
+        unsigned mk = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int i = r0 + 8 * (e >> 1), j = j0 + c0 + cl + (e & 1);
+          const bool jblock = j >= k0 && j < k0 + kb;
+          const bool live = row_ok(i) && j < ng && (mode == 3 ? true : (j <= i && !jblock));
+          mk |= (live ? 1u : 0u) << e;
+          mk |= (live && !jblock ? 1u : 0u) << (8 + e);
+        }
+        return mk;
+      };
+      if (nt > 0) {
+        load_tau(0, tv);
+        mask = tile_mask(0);
+      }
+      prefetch_a(0);
       for (int k = 0; k < nt; ++k) {
         const int tt = t + k;
         const int j0 = Js[k] * BN;
-        const int c0 = part * 8;
-        int ex[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int j = j0 + c0 + q;
-          const bool jblock = j >= k0 && j < k0 + kb;
-          const bool live = row_ok && j < ng && (mode == 3 ? true : (j <= i && !jblock));
-          ex[q] = live ? ei + tau[buf * rows_total + M.row_off + j] - 2 * BETA : 1 << 20;
-        }
+        prefetch_a(k + 1);
+        // the next tile's column exponents, used after this tile's FP64 part
+        int tnext[2];
+        load_tau(k + 1, tnext);
         bool have = mbar_wait_ab(t_full, tt & 1, abort_flag);
         have = __all_sync(0xffffffffu, have) != 0;
         float hr[8], lr[8], hm[8], lm[8];
         if (have) {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          // Two passes of four columns: each issues the loads of every level
-          // (re and im) before one wait, so the tensor-memory round trips of
-          // a tile are two instead of one per level.
+          // Two passes of 16 rows: each issues the loads of every level (re
+          // and im) before one wait, so the tensor-memory round trips of a
+          // tile are two instead of one per level.
 #pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
+          for (int hb = 0; hb < 2; ++hb) {
+            const uint32_t tl = tmem + ((uint32_t)(quad * 32 + 16 * hb) << 16) + c0;
             uint32_t x[SL][4], y[SL][4];
 #pragma unroll
             for (int L = 0; L < SL; ++L) {
-              tmem_ld4(tmem + lane_off + 32 * L + c0 + 4 * hh, x[L]);
-              if constexpr (!realv) tmem_ld4(tmem + lane_off + 32 * (SL + L) + c0 + 4 * hh, y[L]);
+              tmem_ld16x256(tl + 32 * L, x[L]);
+              if constexpr (!realv) tmem_ld16x256(tl + 32 * (SL + L), y[L]);
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
@@ -604,7 +730,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
               const float w = ldexpf(1.f, -BETA * L);
 #pragma unroll
               for (int qq = 0; qq < 4; ++qq) {
-                const int q = 4 * hh + qq;
+                const int q = 4 * hb + qq;
                 const float vr = __fmul_rn(__uint_as_float(x[L][qq]), w);
                 const float vi = realv ? 0.f : __fmul_rn(__uint_as_float(y[L][qq]), w);
                 if (L == 0) {
@@ -644,27 +770,36 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
         // the tile's FP64 values, read while the next tile's MMAs run
         double2 av[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int j = j0 + c0 + q;
-          const bool jblock = j >= k0 && j < k0 + kb;
-          av[q] = (ex[q] != (1 << 20) && !jblock) ? M.A[(size_t)i * ng + j] : make_double2(0.0, 0.0);
+        for (int e = 0; e < 8; ++e) {
+          const int j = j0 + c0 + cl + (e & 1);
+          av[e] = ((mask >> (8 + e)) & 1u) ? M.A[(size_t)(r0 + 8 * (e >> 1)) * ng + j] : make_double2(0.0, 0.0);
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (ex[q] == (1 << 20)) continue;
-          const int j = j0 + c0 + q;
-          const double2 v = av[q];
-          const int e2 = ex[q];
+        for (int e = 0; e < 8; ++e) {
+          if (!((mask >> e) & 1u)) continue;
+          const int j = j0 + c0 + cl + (e & 1);
+          const double2 v = av[e];
+          const int e2 = ei[e >> 1] + tv[e & 1] - 2 * BETA;
           double2 o;
-          // scale 2^e2 (sigma_i tau_j 2^-16) applied in the conversion; four FP64 adds
-          o.x = (v.x - f2d_scaled(hr[q], e2)) - f2d_scaled(lr[q], e2);
-          o.y = realv ? v.y : (v.y - f2d_scaled(hm[q], e2)) - f2d_scaled(lm[q], e2);
-          M.A[(size_t)i * ng + j] = o;
+          // scale 2^e2 (sigma_i tau_j 2^-16) applied in the conversion; one
+          // FP64 add per word
+          o.x = v.x - ff2d_scaled(hr[e], lr[e], e2);
+          o.y = realv ? v.y : v.y - ff2d_scaled(hm[e], lm[e], e2);
+          M.A[(size_t)(r0 + 8 * (e >> 1)) * ng + j] = o;
+        }
+        if (k + 1 < nt) {
+          tv[0] = tnext[0];
+          tv[1] = tnext[1];
+          mask = tile_mask(k + 1);
         }
       }
     }
     t += nt;
-    __syncthreads();   // the item's tiles are written; U and the V buffers are free
+    // Items of the bulk launches are independent and the barriers order the
+    // buffers' reuse, so the next item's copies and MMAs overlap this item's
+    // last epilogue.  The look-ahead launch's first item is followed by the
+    // next diagonal block's sweep (all threads, U as scratch).
+    if (mode == 1) __syncthreads();
     // The tile holding the next diagonal block (rows and columns k1 .. k1+31)
     // has its final values: sweep it here (next step's D^-1 into Dinv, -D^-1
     // into A_K1K1) without a separate launch.
@@ -694,6 +829,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
   if (control && lane == 0 && u_loads > 0) {
     const uint64_t t0 = globaltimer();
     while (!mbar_try_wait(u_full, (u_loads - 1) & 1) && globaltimer() - t0 < kWaitNs) {
+    }
+    const uint64_t t2 = globaltimer();
+    while (!*abort_flag && !mbar_try_wait(u_empty, (u_loads - 1) & 1) && globaltimer() - t2 < kWaitNs) {
     }
     for (int tt = max(0, vissued - 2); tt < vissued; ++tt) {
       const uint64_t t1 = globaltimer();
@@ -861,6 +999,16 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
     grid = pipe_items(mode, plan->slices, nI, nJ, k1 / BM, k1 < ngmax);
   }
   if (grid <= 0) return BGW_OK;
+  // Bulk launches with more items than SMs run persistent CTAs (items taken
+  // round-robin): the next item's copies and MMAs then overlap the last
+  // epilogue of the one before, and a CTA's start-up is paid once.  Only when
+  // the matrices of the batch share the SMs evenly; the look-ahead launch
+  // (on the critical path, few items) keeps one item per CTA.
+  if (mode != 1) {
+    const int nsm = sm_count(c), per = nsm / plan->nmat;
+    if (per >= 1 && (long long)grid * plan->nmat > nsm && 10 * per * plan->nmat >= 9 * nsm)
+      grid = std::min(grid, per);
+  }
   const size_t smem = pipe_smem(plan->slices);
   const dim3 g(grid, plan->nmat);
 #define BGW_PIPE_LAUNCH(RV, SLC, FF)                                                                          \
