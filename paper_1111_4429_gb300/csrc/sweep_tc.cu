@@ -322,6 +322,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Two consecutive complex values in one 256-bit access (p 32-byte aligned).
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) {
+  asm("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(a.x), "=d"(a.y), "=d"(b.x), "=d"(b.y) : "l"(p));
+}
+__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(a.x), "d"(a.y), "d"(b.x), "d"(b.y) : "memory");
+}
+
 // (h + l) 2^ex as one double (rounded to nearest, ties away from zero) for
 // finite floats h, l and |ex| < 900, built in the integer pipe: the SM's FP64
 // pipe is the epilogue's bottleneck, and the FP64 form of the same value takes
@@ -768,24 +776,44 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(t_empty)) : "memory");
         if (!have) continue;
         // the tile's FP64 values, read while the next tile's MMAs run
+        // a lane's two columns are adjacent: one 256-bit access per row
+        // where both are read (written) and the pair is 32-byte aligned
+        // (every row for an even N_G and an aligned matrix), else one
+        // 128-bit access per element
         double2 av[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int j = j0 + c0 + cl + (e & 1);
-          av[e] = ((mask >> (8 + e)) & 1u) ? M.A[(size_t)(r0 + 8 * (e >> 1)) * ng + j] : make_double2(0.0, 0.0);
+        for (int m = 0; m < 4; ++m) {
+          const size_t off = (size_t)(r0 + 8 * m) * ng + j0 + c0 + cl;
+          const unsigned rd = (mask >> (8 + 2 * m)) & 3u;
+          av[2 * m] = av[2 * m + 1] = make_double2(0.0, 0.0);
+          if (rd == 3u && !(reinterpret_cast<uintptr_t>(M.A + off) & 31u)) {
+            ld_pair(M.A + off, av[2 * m], av[2 * m + 1]);
+          } else {
+            if (rd & 1u) av[2 * m] = M.A[off];
+            if (rd & 2u) av[2 * m + 1] = M.A[off + 1];
+          }
         }
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          if (!((mask >> e) & 1u)) continue;
-          const int j = j0 + c0 + cl + (e & 1);
-          const double2 v = av[e];
-          const int e2 = ei[e >> 1] + tv[e & 1] - 2 * BETA;
-          double2 o;
-          // scale 2^e2 (sigma_i tau_j 2^-16) applied in the conversion; one
-          // FP64 add per word
-          o.x = v.x - ff2d_scaled(hr[e], lr[e], e2);
-          o.y = realv ? v.y : v.y - ff2d_scaled(hm[e], lm[e], e2);
-          M.A[(size_t)(r0 + 8 * (e >> 1)) * ng + j] = o;
+        for (int m = 0; m < 4; ++m) {
+          const size_t off = (size_t)(r0 + 8 * m) * ng + j0 + c0 + cl;
+          double2 o[2];
+#pragma unroll
+          for (int n = 0; n < 2; ++n) {
+            const int e = 2 * m + n;
+            const double2 v = av[e];
+            const int e2 = ei[m] + tv[n] - 2 * BETA;
+            // scale 2^e2 (sigma_i tau_j 2^-16) applied in the conversion; one
+            // FP64 add per word
+            o[n].x = v.x - ff2d_scaled(hr[e], lr[e], e2);
+            o[n].y = realv ? v.y : v.y - ff2d_scaled(hm[e], lm[e], e2);
+          }
+          const unsigned wr = (mask >> (2 * m)) & 3u;
+          if (wr == 3u && !(reinterpret_cast<uintptr_t>(M.A + off) & 31u)) {
+            st_pair(M.A + off, o[0], o[1]);
+          } else {
+            if (wr & 1u) M.A[off] = o[0];
+            if (wr & 2u) M.A[off + 1] = o[1];
+          }
         }
         if (k + 1 < nt) {
           tv[0] = tnext[0];
