@@ -330,39 +330,36 @@ __device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
   asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(a.x), "d"(a.y), "d"(b.x), "d"(b.y) : "memory");
 }
 
-// (h + l) 2^ex as one double (rounded to nearest, ties away from zero) for
-// finite floats h, l and |ex| < 900, built in the integer pipe: the SM's FP64
-// pipe is the epilogue's bottleneck, and the FP64 form of the same value takes
-// a conversion-free add there per word.  A two-sum first makes the pair
-// non-overlapping (s = fl(h + l), |t| <= ulp(s) / 2), so s's 24-bit mantissa
-// placed at bits 61..38 of a 64-bit word plus t's shifted mantissa stays in
-// [2^61 - 2^37, 2^62): at most one bit of renormalisation.  Zero and
-// subnormal words take the two-conversion path.
+// (h + l) 2^ex as one double for the level sums of the update, built in the
+// integer pipe without branches (the SM's FP64 pipe is the epilogue's
+// bottleneck, and straight-line code lets the compiler interleave a thread's
+// sixteen conversions).  h and l are finite and, where nonzero, far inside
+// FP32's normal range (sums of level values, integers times 2^-8L, and their
+// rounding errors); |ex| < 900.  A two-sum first makes the pair
+// non-overlapping: s = fl(h + l) and |t| <= ulp(s) / 2, so t's exponent lies
+// at least 24 below s's.  In units of 2^-30 ulp(s), s is ms 2^30 (ms its
+// 24-bit mantissa) and t, truncated, an integer below 2^30; their sum lies in
+// (2^53 - 2^30, 2^54): at most one bit of renormalisation, then one rounding
+// bit (half away from zero) to 53 bits.  The result is within one unit in
+// the last place of the exact (h + l) 2^ex.
 __device__ __forceinline__ double ff2d_scaled(float h, float l, int ex) {
   float s, t;
   two_sum(h, l, s, t);
   const unsigned us = __float_as_uint(s), ut = __float_as_uint(t);
-  const unsigned es = (us >> 23) & 0xFFu, et = (ut >> 23) & 0xFFu;
-  if (es == 0u || es == 0xFFu || et == 0xFFu || (et == 0u && (ut << 1) != 0u))
-    return f2d_scaled(s, ex) + f2d_scaled(t, ex);
-  unsigned long long m = (unsigned long long)((us & 0x7FFFFFu) | 0x800000u) << 38;
-  int e = (int)es;
-  if ((ut << 1) != 0u) {
-    const unsigned g = es - et;   // >= 24 for a nonzero two-sum error
-    const unsigned long long b =
-        g < 64u ? ((unsigned long long)((ut & 0x7FFFFFu) | 0x800000u) << 38) >> g : 0ull;
-    m = ((us ^ ut) >> 31) ? m - b : m + b;
-    if (m < (1ull << 61)) {
-      m <<= 1;
-      --e;
-    }
-  }
-  // the mantissa's leading bit (bit 52 after the shift) adds one to the
-  // exponent field; the rounding carry may propagate into it
+  const int es = (int)((us >> 23) & 0xFFu), g = es - (int)((ut >> 23) & 0xFFu);
+  const unsigned ms = (us & 0x7FFFFFu) | 0x800000u, mt = (ut & 0x7FFFFFu) | 0x800000u;
+  const unsigned bt0 = g <= 30 ? mt << (30 - g) : (g < 62 ? mt >> (g - 30) : 0u);
+  const unsigned bt = (ut << 1) != 0u ? bt0 : 0u;
+  unsigned long long m = ((unsigned long long)ms << 30);
+  m = ((us ^ ut) >> 31) ? m - bt : m + bt;
+  const bool nrm = m < (1ull << 53);
+  m = nrm ? m << 1 : m;
+  // the mantissa's leading bit (bit 52) adds one to the exponent field; the
+  // rounding carry may propagate into it
+  const unsigned long long sign = (unsigned long long)(us & 0x80000000u) << 32;
   const unsigned long long bits =
-      ((unsigned long long)(us & 0x80000000u) << 32) |
-      ((((unsigned long long)(unsigned)(e + 895 + ex)) << 52) + (m >> 9) + ((m >> 8) & 1ull));
-  return __longlong_as_double((long long)bits);
+      sign | ((((unsigned long long)(unsigned)(es - (nrm ? 1 : 0) + 895 + ex)) << 52) + (m >> 1) + (m & 1ull));
+  return __longlong_as_double((long long)((us << 1) != 0u ? bits : sign));
 }
 
 // ---------------------------------------------------------------------------
