@@ -340,11 +340,12 @@ def _roofline(s, kt, step_ms, peaks, peak_src, size_tag="c2"):
         # FP64-equivalent: 128x32 complex elements x 32 complex multiply-adds
         # of 8 flop each per tile (the sweep's 4 N_G^3 in total)
         fp64eq = bulk_tiles * 8.0 * 128 * 32 * 32
-        roof = {"bound": "tensor", "kernel": f"oz::update_pipe_kernel<{sl} slices> (tcgen05 kind::f16 M128 N32: the "
-                                             "sweep's trailing update from exact FP16 slices)",
+        roof = {"bound": "tensor", "kernel": f"oz::update_pipe_kernel<{sl} slices> (tcgen05 kind::f16 M128, one MMA "
+                                             "per U slice and K quarter over its V slices: the sweep's trailing "
+                                             "update from exact FP16 slices)",
                 "achieved": issued / t_launch / 1e12, "peak": bf16, "unit": "TFLOP/s",
                 "algorithmic": f"issued tensor flops of the bulk launch: {bulk_tiles:.0f} tiles of 128x32 x "
-                               f"{pairs * 8} MMAs x 2x128x32x16",
+                               f"{pairs * 8} slice-pair products of 2x128x32x16 ({sl * 8} MMAs of N = 32 (SL - a))",
                 "peak_source": f"{peak_src} bf16 sustained",
                 "fp64_equivalent_tflops": fp64eq / t_launch / 1e12,
                 "fp64_equivalent_frac_of_fp64_pipe": fp64eq / t_launch / 1e12 / FP64_PEAK_TFLOPS,
