@@ -203,6 +203,14 @@ int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
  *    in bgw_epsilon, bgw_epsilon_real, bgw_epsilon_batch and the server for
  *    the mixed precisions, off for FP64 inputs and for bgw_epsinv*; 0: off;
  *    1: on.                                                                */
+/*  BGW_OPT_PAIR_KERNEL: which kernel runs the pair transform's y and x
+ *    passes.  -1 (default): the autotuner's choice among all of them (or the
+ *    fixed default while BGW_OPT_AUTOTUNE is 0); 0: one (pair block, plane)
+ *    per CTA with the default pairs per block; 1: one warp per pair; 11 to
+ *    14: the pair products of 1 to 4 pairs staged in shared memory before
+ *    the y pass.  1 and 11-14 apply where every kept frequency lies in
+ *    |k| < N/4 (and 11-14 to the FP32 transform); elsewhere 0 runs.  The
+ *    results agree to rounding; the choice only changes the speed.          */
 /*  BGW_OPT_WAIT_LIMIT_NS: how long (nanoseconds, 0 .. 10^10; default 10^9)
  *    a wait of the tensor-core chi kernels on its pipeline (a copy landing,
  *    an MMA stage finishing, tensor memory being drained) may last before
@@ -213,7 +221,7 @@ int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
  *    wait that is not already complete (a test of that path).              */
 enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3, BGW_OPT_CHI_CHUNK_PAIRS = 4,
        BGW_OPT_INVERSE = 5, BGW_OPT_HEAD = 6, BGW_OPT_SIGMA_DENSITY = 7, BGW_OPT_UPDATE_SLICES = 8,
-       BGW_OPT_DOUBLE_FP32 = 9, BGW_OPT_WAIT_LIMIT_NS = 10 };
+       BGW_OPT_DOUBLE_FP32 = 9, BGW_OPT_WAIT_LIMIT_NS = 10, BGW_OPT_PAIR_KERNEL = 11 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
 
 /* With BGW_OPT_TIMING = 1 the context records CUDA events around its main

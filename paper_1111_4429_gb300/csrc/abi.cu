@@ -367,6 +367,12 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
     c->autotune = value == 1;
     return BGW_OK;
   }
+  if (option == BGW_OPT_PAIR_KERNEL) {
+    if (!(value == -1 || value == 0 || value == 1 || (value >= 11 && value <= 14)))
+      return fail(c, BGW_EINVAL, "pair kernel is -1, 0, 1 or 11 .. 14");
+    c->pair_kernel = (int)value;
+    return BGW_OK;
+  }
   if (option == BGW_OPT_WAIT_LIMIT_NS) {
     if (value < 0 || value > 10000000000LL) return fail(c, BGW_EINVAL, "wait limit must be in [0, 1e10] ns");
     c->wait_ns = (unsigned long long)value;

@@ -175,6 +175,13 @@ int mtxel_run(Ctx* c, int n, int prec, int nv, const BandPlan* bpv, const void* 
   const int ppb_default = std::max(1, 256 / n);
   int* slot = &c->tuned_ppb[std::make_tuple(n, prec == BGW_PREC_FP64 ? 0 : 1, pp->nys, pp->ncol)];
   if (!c->autotune && *slot <= 0) *slot = ppb_default;
+  int forced = 0;   // a kernel chosen by BGW_OPT_PAIR_KERNEL (the table is left alone)
+  if (c->pair_kernel >= 0) {
+    forced = c->pair_kernel == 0 ? ppb_default
+           : c->pair_kernel == 1 ? kPairWarpCode
+                                 : kPairStagedCode + (c->pair_kernel - 10);
+    slot = &forced;
+  }
   x.tuned_ppb = slot;
   cudaError_t e = prec == BGW_PREC_FP64 ? mtxel_exec_f64(x) : mtxel_exec_f32(x);
   if (e != cudaSuccess) return cuda_fail(c, e, "bgw_mtxel kernels");

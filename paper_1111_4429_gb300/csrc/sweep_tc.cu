@@ -335,31 +335,29 @@ __device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
 // bottleneck, and straight-line code lets the compiler interleave a thread's
 // sixteen conversions).  h and l are finite and, where nonzero, far inside
 // FP32's normal range (sums of level values, integers times 2^-8L, and their
-// rounding errors); |ex| < 900.  A two-sum first makes the pair
-// non-overlapping: s = fl(h + l) and |t| <= ulp(s) / 2, so t's exponent lies
-// at least 24 below s's.  In units of 2^-30 ulp(s), s is ms 2^30 (ms its
-// 24-bit mantissa) and t, truncated, an integer below 2^30; their sum lies in
-// (2^53 - 2^30, 2^54): at most one bit of renormalisation, then one rounding
-// bit (half away from zero) to 53 bits.  The result is within one unit in
-// the last place of the exact (h + l) 2^ex.
+// rounding errors: |h + l| >= 2^-90 or 0); |ex| < 900.  A two-sum first
+// makes the pair non-overlapping: s = fl(h + l), |t| <= ulp(s) / 2, and
+// |t| <= ulp(s) / 4 when s is a power of two and t lowers it.  The bits of
+// s 2^ex as a double are s's own fields re-biased; t, counted in units of
+// that double's last place (half that unit where t takes s below a power of
+// two) and rounded, is added to the bit pattern as an integer: s + t stays
+// inside the binade of s otherwise, and the pattern is monotonic in the
+// magnitude.  The result is within half a unit in the last place of the
+// exact (h + l) 2^ex plus the rounding of t to that unit.
 __device__ __forceinline__ double ff2d_scaled(float h, float l, int ex) {
   float s, t;
   two_sum(h, l, s, t);
   const unsigned us = __float_as_uint(s), ut = __float_as_uint(t);
-  const int es = (int)((us >> 23) & 0xFFu), g = es - (int)((ut >> 23) & 0xFFu);
-  const unsigned ms = (us & 0x7FFFFFu) | 0x800000u, mt = (ut & 0x7FFFFFu) | 0x800000u;
-  const unsigned bt0 = g <= 30 ? mt << (30 - g) : (g < 62 ? mt >> (g - 30) : 0u);
-  const unsigned bt = (ut << 1) != 0u ? bt0 : 0u;
-  unsigned long long m = ((unsigned long long)ms << 30);
-  m = ((us ^ ut) >> 31) ? m - bt : m + bt;
-  const bool nrm = m < (1ull << 53);
-  m = nrm ? m << 1 : m;
-  // the mantissa's leading bit (bit 52) adds one to the exponent field; the
-  // rounding carry may propagate into it
-  const unsigned long long sign = (unsigned long long)(us & 0x80000000u) << 32;
-  const unsigned long long bits =
-      sign | ((((unsigned long long)(unsigned)(es - (nrm ? 1 : 0) + 895 + ex)) << 52) + (m >> 1) + (m & 1ull));
-  return __longlong_as_double((long long)((us << 1) != 0u ? bits : sign));
+  const unsigned k = (us << 1) != 0u ? (unsigned)(896 + ex) << 20 : 0u;
+  const unsigned hi = (us & 0x80000000u) | (((us & 0x7FFFFFFFu) >> 3) + k);
+  const unsigned lo = us << 29;
+  const bool lowers = (int)(us ^ ut) < 0;   // t's sign differs from s's
+  const int ge = (int)((us >> 23) & 0xFFu) - (int)((ut >> 23) & 0xFFu) - ((lowers && (us << 9) == 0u) ? 1 : 0);
+  const unsigned mt = (ut & 0x7FFFFFu) | 0x800000u;
+  const unsigned d = ge <= 29 ? mt << (29 - ge) : (((mt >> min(ge - 30, 31)) + 1u) >> 1);
+  const long long b =
+      (long long)(((unsigned long long)hi << 32) | lo) + (lowers ? -(long long)d : (long long)d);
+  return __longlong_as_double(b);
 }
 
 // ---------------------------------------------------------------------------

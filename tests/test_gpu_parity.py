@@ -121,6 +121,29 @@ def test_mtxel_large_grids_vs_oracle(ctx, n, prec):
     assert np.all(np.abs(got - ref) <= (TOL64 if prec == 0 else TOL32_M) * scale)
 
 
+@pytest.mark.parametrize("kernel", [0, 1, 11, 12, 13, 14])
+@pytest.mark.parametrize("n,prec", [(40, 1), (60, 1), (60, 0), (24, 1)])
+def test_mtxel_pair_kernels_vs_oracle(ctx, n, prec, kernel):
+    # every y,x kernel of the pair transform (block, warp per pair, staged
+    # products with 1-4 pairs per block) on low-band grids, against the
+    # oracle element by element; ragged pair counts (nv nc = 3 x 7 = 21 is
+    # no multiple of 2, 3 or 4), pairs of a block across two bands v; FP64
+    # and a variant that does not apply fall back to the block kernel
+    from paper_1111_4429_gb300 import bgw
+    a, ew, ee = {40: (20.52, 12.0, 6.0), 60: (30.0, 12.0, 6.0), 24: (12.0, 12.0, 6.0)}[n]
+    s = synth.make_system("mk", a=a, fft=n, ecut_wfn=ew, ecut_eps=ee, nv=3, nc=7, seed=460 + n)
+    ref = oracle.mtxel_fft(s.gv, s.cv, s.gc, s.cc, s.geps, s.fft)
+    ctx.set_option(bgw.BGW_OPT_PAIR_KERNEL, kernel)
+    try:
+        got = _mtxel(ctx, s, prec=prec).cpu().numpy().astype(np.complex128)
+    finally:
+        ctx.set_option(bgw.BGW_OPT_PAIR_KERNEL, -1)
+    tol = TOL64 if prec == 0 else TOL32_M
+    assert _rel(got, ref) <= tol
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(got - ref) <= tol * scale)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_mtxel_wide_eps_sphere_vs_oracle(ctx, prec):
     # an epsilon sphere reaching |G_x| = 6 = n / 4 on the 24 grid: the kernels
