@@ -269,6 +269,9 @@ int bgw_destroy(bgw_ctx* ctx) {
   if (ctx->impl.side) cudaStreamDestroy(ctx->impl.side);
   for (cudaEvent_t e : ctx->impl.la_ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->impl.copy_st) cudaStreamDestroy(ctx->impl.copy_st);
+  for (cudaEvent_t e : ctx->impl.copy_ev)
+    if (e) cudaEventDestroy(e);
   ctx->impl.graphs.clear();
   ctx->impl.pool.unpin_all();
   cudaFree(ctx->impl.d_status);
@@ -700,7 +703,7 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   uint64_t key = hash_bytes(&nq, sizeof(nq), hash_bytes(&prec, sizeof(prec), hash_bytes(&nfreq, sizeof(nfreq))));
   if (nfreq > 0) key = hash_bytes(omega, nfreq * sizeof(double), key);
   key = hash_bytes(&st, sizeof(st), key);
-  const int modes[4] = {c->inverse_mode, c->head_mode, c->update_slices, c->double_fp32};
+  const int modes[5] = {c->inverse_mode, c->head_mode, c->update_slices, c->double_fp32, c->pair_kernel};
   key = hash_bytes(modes, sizeof(modes), key);
   for (int q = 0; q < nq; ++q) {
     const bgw_problem& p = problems[q];
@@ -831,9 +834,33 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
       BGW_CUDA(c, cudaMemcpyAsync(s_cv.ptr, cv, (size_t)nv * npw_v * coef, cudaMemcpyHostToDevice, st));
       d_cv = s_cv.ptr;
     }
+    // Host conduction coefficients are copied chunk by chunk on a copy stream,
+    // one chunk ahead of the chunk being transformed: the copies overlap the
+    // matrix elements and chi of the chunk before (forked from and joined
+    // back to the call's stream by events, so graph capture keeps them).
+    const bool cc_chunked = !cc_dev && nc_chunk < nc;
+    auto copy_chunk = [&](int c0, cudaEvent_t done) -> int {
+      const int ncc = std::min(nc_chunk, nc - c0);
+      const size_t off = (size_t)c0 * npw_c * coef, bytes = (size_t)ncc * npw_c * coef;
+      BGW_CUDA(c, cudaMemcpyAsync(static_cast<char*>(s_cc.ptr) + off, static_cast<const char*>(cc) + off, bytes,
+                                  cudaMemcpyHostToDevice, c->copy_st));
+      BGW_CUDA(c, cudaEventRecord(done, c->copy_st));
+      return BGW_OK;
+    };
     if (!cc_dev) {
       if ((rc = c->pool.alloc((size_t)nc * npw_c * coef, &s_cc.ptr)) != BGW_OK) return fail(c, rc, "cc staging");
-      BGW_CUDA(c, cudaMemcpyAsync(s_cc.ptr, cc, (size_t)nc * npw_c * coef, cudaMemcpyHostToDevice, st));
+      if (cc_chunked) {
+        if (!c->copy_st) {
+          BGW_CUDA(c, cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
+          for (auto& e : c->copy_ev) BGW_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        // the staging block may still be read by earlier work on the stream
+        BGW_CUDA(c, cudaEventRecord(c->copy_ev[0], st));
+        BGW_CUDA(c, cudaStreamWaitEvent(c->copy_st, c->copy_ev[0], 0));
+        if ((rc = copy_chunk(0, c->copy_ev[1])) != BGW_OK) return rc;
+      } else {
+        BGW_CUDA(c, cudaMemcpyAsync(s_cc.ptr, cc, (size_t)nc * npw_c * coef, cudaMemcpyHostToDevice, st));
+      }
       d_cc = s_cc.ptr;
     }
     void* d_chi = chi_dev ? chi : nullptr;
@@ -863,9 +890,15 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
     if (!fa.real && !rf && (rc = head_prepare(c, cell, npw_v, gv, npw_c, gc, ng, geps, prec, st, &hp)) != BGW_OK) return rc;
     if (hp.g0 >= 0 && (rc = c->pool.alloc((size_t)nv * nc_chunk * sizeof(double2), &s_h.ptr)) != BGW_OK)
       return fail(c, rc, "head scratch");
-    for (int c0 = 0; c0 < nc; c0 += nc_chunk) {
+    for (int c0 = 0, k = 0; c0 < nc; c0 += nc_chunk, ++k) {
       const int ncc = std::min(nc_chunk, nc - c0);
       const void* cc0 = static_cast<const char*>(d_cc) + (size_t)c0 * npw_c * coef;
+      if (cc_chunked) {
+        // next chunk's copy first (its event was last waited on by chunk k - 1),
+        // then wait for this chunk's
+        if (c0 + nc_chunk < nc && (rc = copy_chunk(c0 + nc_chunk, c->copy_ev[1 + (k + 1) % 2])) != BGW_OK) return rc;
+        BGW_CUDA(c, cudaStreamWaitEvent(st, c->copy_ev[1 + k % 2], 0));
+      }
       if ((rc = mtxel_run(c, n, prec, nv, bpv, d_cv, ncc, bpc, cc0, pp, s_M.ptr, st, rf)) != BGW_OK) return rc;
       if (hp.g0 >= 0 &&
           (rc = head_dot(c, &hp, nv, d_cv, npw_v, ncc, cc0, ng, s_M.ptr, s_h.as<double2>(), st)) != BGW_OK)
@@ -929,7 +962,7 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
     if (nfreq > 0) key = hash_bytes(omega, nfreq * sizeof(double), key);
     const void* ptrs[5] = {cv, cc, chi, epsinv, (const void*)st};
     key = hash_bytes(ptrs, sizeof(ptrs), key);
-    const int modes[4] = {c->inverse_mode, c->head_mode, c->update_slices, c->double_fp32};
+    const int modes[5] = {c->inverse_mode, c->head_mode, c->update_slices, c->double_fp32, c->pair_kernel};
     key = hash_bytes(modes, sizeof(modes), key);
     key = hash_bytes(gv, (size_t)npw_v * 12, key);
     key = hash_bytes(gc, (size_t)npw_c * 12, key);

@@ -132,6 +132,8 @@ struct Ctx {
   int pair_kernel = -1;      // pair transform y,x kernel: -1 autotuned, 0 block, 1 warp per pair, 11-14 staged
   cudaStream_t side = nullptr;     // high-priority stream of the sweep's look-ahead chain
   cudaEvent_t la_ev[4] = {};       // look-ahead dependencies (fork, slice, rest x2)
+  cudaStream_t copy_st = nullptr;  // host-to-device copies of bgw_epsilon's conduction chunks
+  cudaEvent_t copy_ev[3] = {};     // fork, and the chunk copies (ping-pong)
   int inverse_mode = -1;     // -1: tensor-core update for the mixed precisions; 0: FP64 FMA; 1: tensor cores
   int head_mode = -1;        // mixed chi head/wings in FP64: -1 automatic at small q, 0 off, 1 on
   int sigma_density = -1;    // Sigma band densities: -1/1 product transform where alias-free, 0 direct sum

@@ -94,10 +94,13 @@ def test_batch_graph_replay_and_fresh_inputs(ctx):
             assert _rel(out[f].cpu().numpy(), ref[f]) <= 1e-6
 
 
-def test_epsilon_host_buffers_graph_replay(ctx):
+@pytest.mark.parametrize("nc_chunk", [0, 25])
+def test_epsilon_host_buffers_graph_replay(ctx, nc_chunk):
     """bgw_epsilon with page-locked host buffers on a capturable stream: the
     second call replays a graph of the whole path (copies included); new
-    host coefficients in the same buffers give the direct result bit for bit."""
+    host coefficients in the same buffers give the direct result bit for bit.
+    With conduction chunks (25 of 60 bands) the chunk copies run on the
+    context's copy stream, one chunk ahead, inside the graph as well."""
     from paper_1111_4429_gb300 import bgw
     s = synth.config_system("c0")
     cell = bgw.system_cell(s)
@@ -112,12 +115,12 @@ def test_epsilon_host_buffers_graph_replay(ctx):
             if k == 2:   # new contents, same buffers: scrambled phases of the same bands
                 cvh.mul_(torch.exp(1j * torch.arange(cvh.shape[0], dtype=torch.float64))[:, None])
             l0 = ctx.launch_count()
-            ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, 1, 0, None, out)
+            ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, 1, nc_chunk, None, out)
             res.append((out.clone(), ctx.launch_count() - l0))
     ctx.set_option(bgw.BGW_OPT_TIMING, 1)   # timing on: direct runs
     try:
         with torch.cuda.stream(st):
-            ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, 1, 0, None, out)
+            ctx.epsilon(cell, s.gv, cvh, s.ev, s.gc, cch, s.ec, s.geps, None, 1, nc_chunk, None, out)
             direct = out.clone()
     finally:
         ctx.set_option(bgw.BGW_OPT_TIMING, 0)
