@@ -204,13 +204,11 @@ int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
  *    the mixed precisions, off for FP64 inputs and for bgw_epsinv*; 0: off;
  *    1: on.                                                                */
 /*  BGW_OPT_PAIR_KERNEL: which kernel runs the pair transform's y and x
- *    passes.  -1 (default): the autotuner's choice among all of them (or the
- *    fixed default while BGW_OPT_AUTOTUNE is 0); 0: one (pair block, plane)
- *    per CTA with the default pairs per block; 1: one warp per pair; 11 to
- *    14: the pair products of 1 to 4 pairs staged in shared memory before
- *    the y pass.  1 and 11-14 apply where every kept frequency lies in
- *    |k| < N/4 (and 11-14 to the FP32 transform); elsewhere 0 runs.  The
- *    results agree to rounding; the choice only changes the speed.          */
+ *    passes.  -1 (default): the autotuner's choice (or the fixed default
+ *    while BGW_OPT_AUTOTUNE is 0); 0: one (pair block, plane) per CTA with
+ *    the default pairs per block; 1: one warp per pair, where every kept
+ *    frequency lies in |k| < N/4 (elsewhere 0 runs).  The results agree to
+ *    rounding; the choice only changes the speed.                          */
 /*  BGW_OPT_WAIT_LIMIT_NS: how long (nanoseconds, 0 .. 10^10; default 10^9)
  *    a wait of the tensor-core chi kernels on its pipeline (a copy landing,
  *    an MMA stage finishing, tensor memory being drained) may last before

@@ -371,8 +371,7 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
     return BGW_OK;
   }
   if (option == BGW_OPT_PAIR_KERNEL) {
-    if (!(value == -1 || value == 0 || value == 1 || (value >= 11 && value <= 14)))
-      return fail(c, BGW_EINVAL, "pair kernel is -1, 0, 1 or 11 .. 14");
+    if (value < -1 || value > 1) return fail(c, BGW_EINVAL, "pair kernel is -1, 0 or 1");
     c->pair_kernel = (int)value;
     return BGW_OK;
   }

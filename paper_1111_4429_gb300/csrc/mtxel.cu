@@ -177,9 +177,7 @@ int mtxel_run(Ctx* c, int n, int prec, int nv, const BandPlan* bpv, const void* 
   if (!c->autotune && *slot <= 0) *slot = ppb_default;
   int forced = 0;   // a kernel chosen by BGW_OPT_PAIR_KERNEL (the table is left alone)
   if (c->pair_kernel >= 0) {
-    forced = c->pair_kernel == 0 ? ppb_default
-           : c->pair_kernel == 1 ? kPairWarpCode
-                                 : kPairStagedCode + (c->pair_kernel - 10);
+    forced = c->pair_kernel == 0 ? ppb_default : kPairWarpCode;
     slot = &forced;
   }
   x.tuned_ppb = slot;

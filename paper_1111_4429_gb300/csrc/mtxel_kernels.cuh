@@ -263,126 +263,6 @@ __global__ void __launch_bounds__(32 * kPairWarps, sizeof(T) == 4 ? 4 : 2)
   }
 }
 
-// ---------------------------------------------------------------- pair y,x (staged products)
-// The low-band FP32 form with the pair products staged in shared memory: the
-// block first forms P_p(y, x) = conj(u_v) u_c of its ppb pairs on plane z
-// with batched loads (four elements of every pair per thread in flight, the
-// u_v value loaded once per band v of the block), so a thread waits on
-// global memory four times per block instead of once per load group of
-// every line; the y pass then reads its lines from shared memory, and its
-// kept rows Y are written over P once every line is read.  The x pass and the store of the
-// kept columns are those of pair_yxpass.  ppb * N <= 256 (one y line per
-// thread).  grid (ceil(npb / ppb), N), block 256.
-// smem: P[ppb][N*N] (later Y[ppb][nys][N+1]) | Tz[ppb][ncol] | colmap[N*nys] | yslot[N]
-constexpr int kStagedBase = kPairStagedCode;   // tuner's code for pair_yxpass_staged: kStagedBase + ppb
-template <typename T, int N>
-__global__ void __launch_bounds__(256, 2)
-    pair_yxpass_staged(const cpx<T>* __restrict__ uv, const cpx<T>* __restrict__ uc, int nc, int pbase, int npb,
-                       int ppb, int nys, int ncol, const int* __restrict__ g_colmap,
-                       const int* __restrict__ g_yslot, cpx<T>* __restrict__ Tbuf) {
-  static_assert(N % 4 == 0, "low-band lines need N divisible by 4");
-  constexpr int LD = N + 1, Q = N / 4, NN = N * N, kBatch = 4, kMaxPairs = 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* P = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* Tz = P + (size_t)ppb * NN;
-  int* colmap = reinterpret_cast<int*>(Tz + (size_t)ppb * ncol);
-  int* yslot = colmap + N * nys;
-  const int z = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
-  const int pl0 = blockIdx.x * ppb;
-  const int npp = min(ppb, npb - pl0);
-  for (int i = tid; i < N * nys; i += nt) colmap[i] = g_colmap[i];
-  for (int i = tid; i < N; i += nt) yslot[i] = g_yslot[i];
-  // the block's planes; a new band v starts a new u_v plane (uniform per block)
-  const cpx<T>* pvp[kMaxPairs];
-  const cpx<T>* pcp[kMaxPairs];
-  const size_t plane = (size_t)NN;
-#pragma unroll
-  for (int pp = 0; pp < kMaxPairs; ++pp) {
-    const int p = pbase + pl0 + min(pp, npp - 1);
-    const int v = p / nc, c = p - v * nc;
-    pvp[pp] = uv + ((size_t)v * N + z) * plane;
-    pcp[pp] = uc + ((size_t)c * N + z) * plane;
-  }
-  // stage the products: kBatch elements of every pair of the block per round
-  // trip (the u_v values loaded once per band v of the block)
-  bool newv[kMaxPairs];
-#pragma unroll
-  for (int pp = 0; pp < kMaxPairs; ++pp) newv[pp] = pp == 0 || pvp[pp] != pvp[pp - 1];
-  for (int e0 = tid; e0 < NN; e0 += kBatch * nt) {
-    cpx<T> a[kMaxPairs][kBatch], b[kMaxPairs][kBatch];
-#pragma unroll
-    for (int pp = 0; pp < kMaxPairs; ++pp) {
-      if (pp < npp) {
-#pragma unroll
-        for (int q = 0; q < kBatch; ++q) {
-          const int e = e0 + q * nt;
-          if (e < NN) {
-            b[pp][q] = pcp[pp][e];
-            if (newv[pp]) a[pp][q] = pvp[pp][e];
-          }
-        }
-      }
-    }
-    cpx<T> cur[kBatch];
-#pragma unroll
-    for (int pp = 0; pp < kMaxPairs; ++pp) {
-      if (pp < npp) {
-#pragma unroll
-        for (int q = 0; q < kBatch; ++q) {
-          const int e = e0 + q * nt;
-          if (newv[pp]) cur[q] = a[pp][q];
-          if (e < NN) P[(size_t)pp * NN + e] = cmulc<T>(cur[q], b[pp][q]);
-        }
-      }
-    }
-  }
-  __syncthreads();
-  // y pass from shared memory: one line (pair pp, column x) per thread
-  const bool has = tid < npp * N;
-  const int pp = has ? tid / N : 0, x = has ? tid - pp * N : 0;
-  cpx<T> lo[Q], hi[Q];
-  if (has) {
-    const cpx<T>* col = P + (size_t)pp * NN + x;
-    fft_quarters<T, N>([&](int y) { return col[(size_t)y * N]; }, lo, hi);
-  }
-  __syncthreads();   // every line read: Y goes over P
-  if (has) {
-    cpx<T>* yrow = P + (size_t)pp * nys * LD + x;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      const int s0 = yslot[k], s3 = yslot[k + 3 * Q];
-      if (s0 >= 0) yrow[s0 * LD] = lo[k];
-      if (s3 >= 0) yrow[s3 * LD] = hi[k];
-    }
-  }
-  __syncthreads();
-  // x pass: the kept (kx, ky) columns of each kept ky row
-  for (int j = tid; j < npp * nys; j += nt) {
-    const int qp = j / nys, s = j - qp * nys;
-    const cpx<T>* row = P + ((size_t)qp * nys + s) * LD;
-    cpx<T>* tz = Tz + (size_t)qp * ncol;
-    cpx<T> xl[Q], xh[Q];
-    fft_quarters<T, N>([&](int xx) { return row[xx]; }, xl, xh);
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      const int c0 = colmap[k * nys + s], c3 = colmap[(k + 3 * Q) * nys + s];
-      if (c0 >= 0) tz[c0] = xl[k];
-      if (c3 >= 0) tz[c3] = xh[k];
-    }
-  }
-  __syncthreads();
-  for (int i = tid; i < npp * ncol; i += nt) {
-    const int qp = i / ncol, col = i - qp * ncol;
-    Tbuf[((size_t)(pl0 + qp) * N + z) * ncol + col] = Tz[i];
-  }
-}
-
-// Shared memory of a pair_yxpass_staged block holding ppb pairs.
-template <typename T, int N>
-static size_t pair_staged_smem(int ppb, int nys, int ncol) {
-  return (size_t)ppb * N * N * sizeof(cpx<T>) + (size_t)ppb * ncol * sizeof(cpx<T>) + (size_t)(N * nys + N) * sizeof(int);
-}
-
 // ---------------------------------------------------------------- pair z
 // grid (npb), block 256.  smem Mrow[ng], or none with direct != 0 (a list
 // too long for shared memory: the outputs go straight to M, complex only).
@@ -513,31 +393,6 @@ static int tune_pairs_per_block(const MtxelExec& x, const cpx<T>* uv, const cpx<
       cudaGetLastError();
     }
   }
-  if constexpr (LB && sizeof(T) == 4) {   // the staged-product kernel, 1 to 4 pairs per block
-    for (int p = 1; p <= 4 && p * N <= 256; ++p) {
-      const size_t sm = pair_staged_smem<T, N>(p, pp->nys, pp->ncol);
-      if (sm > 200 * 1024 || set_smem(pair_yxpass_staged<T, N>, sm) != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {
-        cudaEventRecord(e0, x.st);
-        pair_yxpass_staged<T, N><<<dim3((npb + p - 1) / p, N), 256, sm, x.st>>>(
-            uv, uc, x.nc, 0, npb, p, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
-        cudaEventRecord(e1, x.st);
-      }
-      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      *x.launches += 2;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = kStagedBase + p;
-      }
-    }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return best > 0 ? best : (256 / N > 0 ? 256 / N : 1);
@@ -582,10 +437,7 @@ static cudaError_t mtxel_exec_lb(const MtxelExec& x) {
   // a variant that does not apply to this grid or precision (a forced
   // choice) falls back to the block kernel with the default pairs per block
   const bool warp_kernel = LB && ppb == kWarpPerPair;
-  const bool staged = LB && sizeof(T) == 4 && ppb > kStagedBase && ppb <= kStagedBase + 4 &&
-                      (ppb - kStagedBase) * N <= 256 &&
-                      pair_staged_smem<T, N>(ppb - kStagedBase, pp->nys, pp->ncol) <= 200 * 1024;
-  if (ppb >= kWarpPerPair && !warp_kernel && !staged) ppb = 256 / N > 0 ? 256 / N : 1;
+  if (ppb >= kWarpPerPair && !warp_kernel) ppb = 256 / N > 0 ? 256 / N : 1;
   int threads = 32 * kPairWarps;
   size_t sm = 0;
   if constexpr (LB) {
@@ -593,15 +445,8 @@ static cudaError_t mtxel_exec_lb(const MtxelExec& x) {
       sm = (size_t)kPairWarps * pp->nys * (N + 1) * sizeof(C) + (size_t)(N * pp->nys + N) * sizeof(int);
       if ((e = set_smem(pair_yxpass_warp<T, N>, sm)) != cudaSuccess) return e;
     }
-    if constexpr (sizeof(T) == 4) {
-      if (staged) {
-        threads = 256;
-        sm = pair_staged_smem<T, N>(ppb - kStagedBase, pp->nys, pp->ncol);
-        if ((e = set_smem(pair_yxpass_staged<T, N>, sm)) != cudaSuccess) return e;
-      }
-    }
   }
-  if (!warp_kernel && !staged) {
+  if (!warp_kernel) {
     pair_block_shape<T, N>(ppb, pp->nys, pp->ncol, &threads, &sm);
     if ((e = set_smem(pair_yxpass<T, N, LB>, sm)) != cudaSuccess) return e;
   }
@@ -618,15 +463,8 @@ static cudaError_t mtxel_exec_lb(const MtxelExec& x) {
         if (warp_kernel)
           pair_yxpass_warp<T, N><<<dim3((npb + kPairWarps - 1) / kPairWarps, N), threads, sm, x.st>>>(
               uv, uc, x.nc, (int)p0, npb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
-        if constexpr (sizeof(T) == 4) {
-          if (staged) {
-            const int sp = ppb - kStagedBase;
-            pair_yxpass_staged<T, N><<<dim3((npb + sp - 1) / sp, N), threads, sm, x.st>>>(
-                uv, uc, x.nc, (int)p0, npb, sp, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
-          }
-        }
       }
-      if (!warp_kernel && !staged)
+      if (!warp_kernel)
         pair_yxpass<T, N, LB><<<dim3((npb + ppb - 1) / ppb, N), threads, sm, x.st>>>(
             uv, uc, x.nc, (int)p0, npb, ppb, pp->nys, pp->ncol, pp->d_colmap, pp->d_yslot_of_k, Tb);
     }

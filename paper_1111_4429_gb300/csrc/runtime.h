@@ -129,7 +129,7 @@ struct Ctx {
   bool use_graphs = true;          // false in the server's slot contexts (one-shot buffers per request)
   std::map<std::tuple<int, int, int, int>, int> tuned_ppb;  // (n, prec, nys, ncol) -> pairs per CTA
   bool autotune = true;
-  int pair_kernel = -1;      // pair transform y,x kernel: -1 autotuned, 0 block, 1 warp per pair, 11-14 staged
+  int pair_kernel = -1;      // pair transform y,x kernel: -1 autotuned, 0 block, 1 warp per pair
   cudaStream_t side = nullptr;     // high-priority stream of the sweep's look-ahead chain
   cudaEvent_t la_ev[4] = {};       // look-ahead dependencies (fork, slice, rest x2)
   cudaStream_t copy_st = nullptr;  // host-to-device copies of bgw_epsilon's conduction chunks
@@ -199,7 +199,6 @@ bool fft_size_supported(int n);
 // Codes of the pair transform's y,x kernel in the tuned-shape table: a
 // positive number below kPairWarpCode is the block kernel's pairs per block.
 constexpr int kPairWarpCode = 1000;     // one warp per pair (low-band grids)
-constexpr int kPairStagedCode = 2000;   // + p: staged products, p pairs per block (low-band FP32 grids)
 
 struct MtxelExec {
   int n = 0, nv = 0, nc = 0;

@@ -121,14 +121,13 @@ def test_mtxel_large_grids_vs_oracle(ctx, n, prec):
     assert np.all(np.abs(got - ref) <= (TOL64 if prec == 0 else TOL32_M) * scale)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 11, 12, 13, 14])
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("n,prec", [(40, 1), (60, 1), (60, 0), (24, 1)])
 def test_mtxel_pair_kernels_vs_oracle(ctx, n, prec, kernel):
-    # every y,x kernel of the pair transform (block, warp per pair, staged
-    # products with 1-4 pairs per block) on low-band grids, against the
-    # oracle element by element; ragged pair counts (nv nc = 3 x 7 = 21 is
-    # no multiple of 2, 3 or 4), pairs of a block across two bands v; FP64
-    # and a variant that does not apply fall back to the block kernel
+    # both y,x kernels of the pair transform (block, warp per pair) on
+    # low-band grids, against the oracle element by element; ragged pair
+    # counts (nv nc = 3 x 7 = 21 is no multiple of the 4 pairs of a warp
+    # kernel's block), pairs of a block across two bands v
     from paper_1111_4429_gb300 import bgw
     a, ew, ee = {40: (20.52, 12.0, 6.0), 60: (30.0, 12.0, 6.0), 24: (12.0, 12.0, 6.0)}[n]
     s = synth.make_system("mk", a=a, fft=n, ecut_wfn=ew, ecut_eps=ee, nv=3, nc=7, seed=460 + n)
