@@ -383,15 +383,31 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // max |Re|, |Im| of M[p][g] sqrt|w_p| over all p, g (as float bits: the
 // values are >= 0 so integer order is float order).
-__global__ void maxabs_kernel(const float2* __restrict__ M, const double* __restrict__ w, long long K, int ng,
+// Per-pair FP32 factors of a weight row, converted once: sqrt|w_p| (the
+// Hermitian and real products) or the complex w_p (the general product).
+// The conversions run on the SM's slow FP64-conversion path, so they are
+// taken once per pair instead of once per element.
+__global__ void pair_factors_kernel(const double* __restrict__ w, const double2* __restrict__ wc, long long K,
+                                    float2* __restrict__ out) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < K; p += (long long)gridDim.x * blockDim.x)
+    out[p] = wc ? make_float2((float)wc[p].x, (float)wc[p].y) : make_float2(sqrtf(fabsf((float)w[p])), 0.f);
+}
+
+// max over the pairs p and G of max(|Re|, |Im|) M[p][G] sqrt|w_p| (float
+// bits into out; values >= 0).  A block takes whole rows (the row's factor
+// once, coalesced loads); max(|v|) s equals max(|v| s) for s >= 0, rounding
+// included.
+__global__ void maxabs_kernel(const float2* __restrict__ M, const float2* __restrict__ f, long long K, int ng,
                               unsigned int* __restrict__ out) {
   float m = 0.f;
-  const long long n = K * ng;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const long long p = e / ng;
-    const float s = sqrtf(fabsf((float)w[p]));  // FP32: the split itself is FP32-based
-    const float2 v = M[e];
-    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)) * s);
+  for (long long p = blockIdx.x; p < K; p += gridDim.x) {
+    const float2* row = M + p * ng;
+    float mr = 0.f;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+      const float2 v = row[g];
+      mr = fmaxf(mr, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    m = fmaxf(m, mr * f[p].x);
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
@@ -412,7 +428,7 @@ __device__ __forceinline__ int scale_exp(const unsigned int* maxbits, int bf16) 
 // for the K pairs of one chunk:
 // x = M sqrt|w_p| 2^e split into hi + lo.  32 x 32 transposing tiles.
 template <typename H>
-__global__ void split_kernel(const float2* __restrict__ M, const double* __restrict__ w, long long p0, long long K,
+__global__ void split_kernel(const float2* __restrict__ M, const float2* __restrict__ f, long long p0, long long K,
                              int ng, int ngpad, int kpad, const unsigned int* __restrict__ maxbits, int bf16,
                              H* __restrict__ planes) {
   __shared__ float2 t[32][33];
@@ -426,7 +442,7 @@ __global__ void split_kernel(const float2* __restrict__ M, const double* __restr
     float2 v = make_float2(0.f, 0.f);
     if (p < K && g < ng) {
       v = M[(p0 + p) * ng + g];
-      const float s = sqrtf(fabsf((float)w[p0 + p])) * sc;
+      const float s = f[p0 + p].x * sc;
       v.x *= s;
       v.y *= s;
     }
@@ -460,18 +476,21 @@ __global__ void split_kernel(const float2* __restrict__ M, const double* __restr
 
 // Real flavor: X[p][G] = M[p][G] sqrt|w_p| 2^e with real M, two planes
 // (hi, lo) per operand, chi real symmetric.
-__global__ void maxabs_real_kernel(const float* __restrict__ M, const double* __restrict__ w, long long K, int ng,
+__global__ void maxabs_real_kernel(const float* __restrict__ M, const float2* __restrict__ f, long long K, int ng,
                                    unsigned int* __restrict__ out) {
   float m = 0.f;
-  const long long n = K * ng;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf(M[e]) * sqrtf(fabsf((float)w[e / ng])));
+  for (long long p = blockIdx.x; p < K; p += gridDim.x) {
+    const float* row = M + p * ng;
+    float mr = 0.f;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) mr = fmaxf(mr, fabsf(row[g]));
+    m = fmaxf(m, mr * f[p].x);
+  }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
 template <typename H>
-__global__ void split_real_kernel(const float* __restrict__ M, const double* __restrict__ w, long long p0,
+__global__ void split_real_kernel(const float* __restrict__ M, const float2* __restrict__ f, long long p0,
                                   long long K, int ng, int ngpad, int kpad, const unsigned int* __restrict__ maxbits,
                                   int bf16, H* __restrict__ planes) {
   __shared__ float t[32][33];
@@ -483,7 +502,7 @@ __global__ void split_real_kernel(const float* __restrict__ M, const double* __r
     const long long p = pc0 + r;
     const int g = g0 + tx;
     float v = 0.f;
-    if (p < K && g < ng) v = M[(p0 + p) * ng + g] * (sqrtf(fabsf((float)w[p0 + p])) * sc);
+    if (p < K && g < ng) v = M[(p0 + p) * ng + g] * (f[p0 + p].x * sc);
     t[r][tx] = v;
   }
   __syncthreads();
@@ -535,16 +554,17 @@ __global__ void reduce_real_kernel(const float* __restrict__ work, int nseg, int
 
 // Real-axis operands: X = M 2^eX and Y = (w_p M) 2^eY with complex w_p.
 // out[0] = max|Re,Im| of M, out[1] = that of w M (float bits, values >= 0).
-__global__ void maxabs_general_kernel(const float2* __restrict__ M, const double2* __restrict__ w, long long K,
+__global__ void maxabs_general_kernel(const float2* __restrict__ M, const float2* __restrict__ f, long long K,
                                       int ng, unsigned int* __restrict__ out) {
   float mx = 0.f, my = 0.f;
-  const long long n = K * ng;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const long long p = e / ng;
-    const float2 v = M[e];
-    const float wr = (float)w[p].x, wi = (float)w[p].y;
-    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
-    my = fmaxf(my, fmaxf(fabsf(fmaf(wr, v.x, -wi * v.y)), fabsf(fmaf(wr, v.y, wi * v.x))));
+  for (long long p = blockIdx.x; p < K; p += gridDim.x) {
+    const float2* row = M + p * ng;
+    const float wr = f[p].x, wi = f[p].y;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+      const float2 v = row[g];
+      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+      my = fmaxf(my, fmaxf(fabsf(fmaf(wr, v.x, -wi * v.y)), fabsf(fmaf(wr, v.y, wi * v.x))));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -579,7 +599,7 @@ __device__ __forceinline__ void split4(float2 v, H* planes, size_t plane, size_t
 // planes[0..3] <- X = M 2^eX, planes[4..7] <- Y = w M 2^eY, transposed to
 // [plane][g][p] like split_kernel.
 template <typename H>
-__global__ void split_general_kernel(const float2* __restrict__ M, const double2* __restrict__ w, long long p0,
+__global__ void split_general_kernel(const float2* __restrict__ M, const float2* __restrict__ f, long long p0,
                                      long long K, int ng, int ngpad, int kpad,
                                      const unsigned int* __restrict__ maxbits, int bf16, H* __restrict__ planes) {
   __shared__ float2 tx_[32][33];
@@ -594,7 +614,7 @@ __global__ void split_general_kernel(const float2* __restrict__ M, const double2
     float2 x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
     if (p < K && g < ng) {
       const float2 v = M[(p0 + p) * ng + g];
-      const float wr = (float)w[p0 + p].x, wi = (float)w[p0 + p].y;
+      const float wr = f[p0 + p].x, wi = f[p0 + p].y;
       x = make_float2(v.x * sx, v.y * sx);
       y = make_float2(fmaf(wr, v.x, -wi * v.y) * sy, fmaf(wr, v.y, wi * v.x) * sy);
     }
@@ -843,12 +863,13 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
   const long long ngroups_max = std::max(groups_of(std::min(kchunk, K)).second, groups_of(last).second);
   const void* d_tiles;
   if ((rc = upload_cached(c, tl.data(), tl.size() * sizeof(int2), st, &d_tiles)) != BGW_OK) return rc;
-  Scratch planes, work, mx;
-  planes.pool = work.pool = mx.pool = &c->pool;
+  Scratch planes, work, mx, fac;
+  planes.pool = work.pool = mx.pool = fac.pool = &c->pool;
   const size_t plane_bytes = (size_t)nplanes * ngpad * kcpad * 2;
   const size_t work_bytes = (size_t)ngroups_max * part_bytes;
   if ((rc = c->pool.alloc(plane_bytes, &planes.ptr)) != BGW_OK || (rc = c->pool.alloc(work_bytes, &work.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc(2 * sizeof(unsigned int), &mx.ptr)) != BGW_OK)
+      (rc = c->pool.alloc(2 * sizeof(unsigned int), &mx.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)K * sizeof(float2), &fac.ptr)) != BGW_OK)
     return fail(c, rc, "bgw_chi_sum (mixed): scratch allocation failed (planes %zu B, workspace %zu B)", plane_bytes,
                 work_bytes);
   CUtensorMap tmap;
@@ -878,15 +899,19 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
     {
       TimedScope ts(c, kTChiSplit, st);
       BGW_CUDA(c, cudaMemsetAsync(mx.ptr, 0, 2 * sizeof(unsigned int), st));
-      const long long n = K * ng;
-      const unsigned mb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8);
+      pair_factors_kernel<<<(unsigned)std::min<long long>((K + 255) / 256, (long long)nsm * 4), 256, 0, st>>>(
+          wf, wcf, K, fac.as<float2>());
+      const unsigned mb = (unsigned)std::min<long long>(K, (long long)nsm * 8);
       if (general)
-        maxabs_general_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wcf, K, ng, mx.as<unsigned int>());
+        maxabs_general_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), fac.as<float2>(), K, ng,
+                                                  mx.as<unsigned int>());
       else if (real)
-        maxabs_real_kernel<<<mb, 256, 0, st>>>(static_cast<const float*>(M), wf, K, ng, mx.as<unsigned int>());
+        maxabs_real_kernel<<<mb, 256, 0, st>>>(static_cast<const float*>(M), fac.as<float2>(), K, ng,
+                                               mx.as<unsigned int>());
       else
-        maxabs_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), wf, K, ng, mx.as<unsigned int>());
-      c->launches += 1;
+        maxabs_kernel<<<mb, 256, 0, st>>>(static_cast<const float2*>(M), fac.as<float2>(), K, ng,
+                                          mx.as<unsigned int>());
+      c->launches += 2;
     }
     for (long long p0 = 0; p0 < K; p0 += kchunk) {
       const long long kc = std::min(kchunk, K - p0);
@@ -902,24 +927,24 @@ int chi_tc_run(Ctx* c, int prec, long long K, int ng, const void* M, const doubl
         // reads no further than nkb = kpad / BK k-blocks
         const unsigned int* mb = mx.as<unsigned int>();
         if (real && bf16)
-          split_real_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float*>(M), wf, p0, kc, ng,
+          split_real_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float*>(M), fac.as<float2>(), p0, kc, ng,
                                                                        ngpad, (int)kcpad, mb, 1,
                                                                        planes.as<__nv_bfloat16>());
         else if (real)
-          split_real_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float*>(M), wf, p0, kc, ng, ngpad,
+          split_real_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float*>(M), fac.as<float2>(), p0, kc, ng, ngpad,
                                                                 (int)kcpad, mb, 0, planes.as<__half>());
         else if (general && bf16)
           split_general_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(
-              static_cast<const float2*>(M), wcf, p0, kc, ng, ngpad, (int)kcpad, mb, 1, planes.as<__nv_bfloat16>());
+              static_cast<const float2*>(M), fac.as<float2>(), p0, kc, ng, ngpad, (int)kcpad, mb, 1, planes.as<__nv_bfloat16>());
         else if (general)
-          split_general_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wcf, p0, kc, ng,
+          split_general_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), fac.as<float2>(), p0, kc, ng,
                                                                    ngpad, (int)kcpad, mb, 0, planes.as<__half>());
         else if (bf16)
-          split_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, p0, kc, ng,
+          split_kernel<__nv_bfloat16><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), fac.as<float2>(), p0, kc, ng,
                                                                   ngpad, (int)kcpad, mb, 1,
                                                                   planes.as<__nv_bfloat16>());
         else
-          split_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), wf, p0, kc, ng, ngpad,
+          split_kernel<__half><<<sg, dim3(32, 8), 0, st>>>(static_cast<const float2*>(M), fac.as<float2>(), p0, kc, ng, ngpad,
                                                            (int)kcpad, mb, 0, planes.as<__half>());
       }
       {
