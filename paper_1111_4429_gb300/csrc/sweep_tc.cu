@@ -330,6 +330,14 @@ __device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
   asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(a.x), "d"(a.y), "d"(b.x), "d"(b.y) : "memory");
 }
 
+// two_sum(a, x w) for a power of two w (x w exact): the products enter fused
+// multiply-adds, the results are those of two_sum(a, x w) bit for bit.
+__device__ __forceinline__ void two_sum_scaled(float a, float x, float w, float& s, float& e) {
+  s = __fmaf_rn(x, w, a);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fmaf_rn(x, w, -bb));
+}
+
 // (h + l) 2^ex as one double for the level sums of the update, built in the
 // integer pipe without branches (the SM's FP64 pipe is the epilogue's
 // bottleneck, and straight-line code lets the compiler interleave a thread's
@@ -719,46 +727,52 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
           // and im) before one wait, so the tensor-memory round trips of a
           // tile are two instead of one per level.
 #pragma unroll
-          for (int hb = 0; hb < 2; ++hb) {
-            const uint32_t tl = tmem + ((uint32_t)(quad * 32 + 16 * hb) << 16) + c0;
-            uint32_t x[SL][4], y[SL][4];
-#pragma unroll
-            for (int L = 0; L < SL; ++L) {
-              tmem_ld16x256(tl + 32 * L, x[L]);
-              if constexpr (!realv) tmem_ld16x256(tl + 32 * (SL + L), y[L]);
-            }
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          // Four rounds (two 16-row halves, real then imaginary parts):
+          // each issues the loads of all SL levels before one wait.
+          // level L enters scaled by w = 2^-8L (exact), folded into fused
+          // multiply-adds: the same roundings as scaling first
+          auto combine = [&](const uint32_t (&x)[SL][4], int hb, float (&h)[8], float (&l)[8]) {
 #pragma unroll
             for (int L = 0; L < SL; ++L) {
               const float w = ldexpf(1.f, -BETA * L);
 #pragma unroll
               for (int qq = 0; qq < 4; ++qq) {
                 const int q = 4 * hb + qq;
-                const float vr = __fmul_rn(__uint_as_float(x[L][qq]), w);
-                const float vi = realv ? 0.f : __fmul_rn(__uint_as_float(y[L][qq]), w);
+                const float v = __uint_as_float(x[L][qq]);
                 if (L == 0) {
-                  hr[q] = vr;
-                  lr[q] = 0.f;
-                  hm[q] = vi;
-                  lm[q] = 0.f;
+                  h[q] = v;
+                  l[q] = 0.f;
                 } else if (L <= kTwoSumLevels) {
                   // levels that can reach the running sum's last bits: exact two-sum
                   float sm, e;
-                  two_sum(hr[q], vr, sm, e);
-                  hr[q] = sm;
-                  lr[q] = __fadd_rn(lr[q], e);
-                  if constexpr (!realv) {
-                    two_sum(hm[q], vi, sm, e);
-                    hm[q] = sm;
-                    lm[q] = __fadd_rn(lm[q], e);
-                  }
+                  two_sum_scaled(h[q], v, w, sm, e);
+                  h[q] = sm;
+                  l[q] = __fadd_rn(l[q], e);
                 } else {
                   // deeper levels lie below the sum's last bit at the target
                   // precision: they go to the low word
-                  lr[q] = __fadd_rn(lr[q], vr);
-                  if constexpr (!realv) lm[q] = __fadd_rn(lm[q], vi);
+                  l[q] = __fmaf_rn(v, w, l[q]);
                 }
               }
+            }
+          };
+#pragma unroll
+          for (int hb = 0; hb < 2; ++hb) {
+            const uint32_t tl = tmem + ((uint32_t)(quad * 32 + 16 * hb) << 16) + c0;
+#pragma unroll
+            for (int part = 0; part < (realv ? 1 : 2); ++part) {
+              uint32_t x[SL][4];
+#pragma unroll
+              for (int L = 0; L < SL; ++L) tmem_ld16x256(tl + 32 * (part * SL + L), x[L]);
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+              if (part == 0)
+                combine(x, hb, hr, lr);
+              else
+                combine(x, hb, hm, lm);
+            }
+            if constexpr (realv) {
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) hm[4 * hb + qq] = lm[4 * hb + qq] = 0.f;
             }
           }
         } else if (lane == 0) {
