@@ -214,7 +214,8 @@ __device__ __forceinline__ float2 ff_dot2(float2 v, float2 a1, float2 b1, float2
 // Called by all NT threads after L (lower) is loaded; ends with a
 // __syncthreads().  A non-positive or non-finite pivot sets *status.
 template <int NT>
-__device__ __forceinline__ void diag_sweep_ff_n(DiagSmem& sm, float4* scratch, int kb, int t, int* status) {
+__device__ __forceinline__ void diag_sweep_ff_n(DiagSmem& sm, float4* scratch, int kb, int t, int* status,
+                                                float4* dff = nullptr) {
   constexpr int NE = (kSwNB * (kSwNB + 1) / 2 + NT - 1) / NT;
   typedef float4 Row[kSwNB + 1];
   Row* const B0 = reinterpret_cast<Row*>(sm.L);
@@ -289,6 +290,14 @@ __device__ __forceinline__ void diag_sweep_ff_n(DiagSmem& sm, float4* scratch, i
     if (!el[q]) continue;
     const float4 x = F[ei[q]][ej[q]];
     sm.L[ei[q]][ej[q]] = make_double2(ff_to(make_float2(x.x, x.y)), ff_to(make_float2(x.z, x.w)));
+    if (dff) {
+      // -D^-1 as normalized double-FP32 pairs, both triangles (ld kSwNB):
+      // the next panel product reads them without FP64 conversions
+      const float2 re = ff_two_sum(x.x, x.y), im = ff_two_sum(x.z, x.w);
+      const int i = ei[q], j = ej[q];
+      dff[i * kSwNB + j] = make_float4(-re.x, -re.y, -im.x, -im.y);
+      if (i != j) dff[j * kSwNB + i] = make_float4(-re.x, -re.y, im.x, im.y);
+    }
   }
   __syncthreads();
 }

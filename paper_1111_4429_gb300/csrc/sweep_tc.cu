@@ -124,6 +124,7 @@ struct OzMat {
   const double2* C;   // [ng][NB]
   const double2* P;   // [ng][NB]
   double2* Dinv;      // [NB][NB] D^-1 of the next diagonal block (written by mode 1)
+  float4* Dff;        // [NB][NB] the same as double-FP32 pairs (re hi, re lo, im hi, im lo)
   int ng;
   int row_off;        // first slice row of this matrix (multiple of BM)
 };
@@ -187,13 +188,20 @@ __global__ void __launch_bounds__(256) panel_slice_kernel(const __grid_constant_
   const int kb = min(NB, ng - k0);
   double2* A = M.A;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // FF: the look-ahead CTA that swept the block (every step after the first)
+  // left D^-1 as double-FP32 pairs; the first step's block comes in FP64
+  const bool have_ff = FF && M.Dff != nullptr && k0 > 0;
   for (int e = threadIdx.x; e < NB * NB; e += 256) {
-    const double2 d = M.Dinv[e];
     if constexpr (FF) {
-      const float2 r = ff_from(d.x), m = ff_from(d.y);
-      reinterpret_cast<float4*>(&Ds[0][0])[e] = make_float4(r.x, r.y, m.x, m.y);
+      if (have_ff) {
+        reinterpret_cast<float4*>(&Ds[0][0])[e] = M.Dff[e];
+      } else {
+        const double2 d = M.Dinv[e];
+        const float2 r = ff_from(d.x), m = ff_from(d.y);
+        reinterpret_cast<float4*>(&Ds[0][0])[e] = make_float4(r.x, r.y, m.x, m.y);
+      }
     } else {
-      Ds[e / NB][e % NB] = d;
+      Ds[e / NB][e % NB] = M.Dinv[e];
     }
   }
   const int i = blockIdx.x * 8 + warp;
@@ -849,7 +857,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
       // double-FP32 chain: the block's sweep in double FP32 (about 2^-46),
       // off the SM's slow FP64 pipe; else FP64
       if constexpr (FFC)
-        diag_sweep_ff_n<kPipeThreads>(dsm, reinterpret_cast<float4*>(us), kb1, threadIdx.x, status);
+        diag_sweep_ff_n<kPipeThreads>(dsm, reinterpret_cast<float4*>(us), kb1, threadIdx.x, status, M.Dff);
       else
         diag_sweep_smem_n<kPipeThreads>(dsm, kb1, threadIdx.x, status);
       for (int e = threadIdx.x; e < NB * NB; e += kPipeThreads) {
@@ -908,7 +916,7 @@ struct OzPlan {
   int max_tiles = 0;
   oz::OzBatch batch;
   CUtensorMap umap, vmap;
-  Scratch U, V, sig, tau;
+  Scratch U, V, sig, tau, dff;
 };
 
 int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2* const* C, const double2* const* P,
@@ -949,15 +957,17 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
   }
   plan->rows_total = rows;
   plan->max_tiles = tiles;
-  plan->U.pool = plan->V.pool = plan->sig.pool = plan->tau.pool = &c->pool;
+  plan->U.pool = plan->V.pool = plan->sig.pool = plan->tau.pool = plan->dff.pool = &c->pool;
   int rc;
   // two slice buffers: a step may slice while the previous step's update
   // still reads its own
   const size_t sb = (size_t)2 * S * rows * KR * sizeof(__half);
   if ((rc = c->pool.alloc(sb, &plan->U.ptr)) != BGW_OK || (rc = c->pool.alloc(sb, &plan->V.ptr)) != BGW_OK ||
       (rc = c->pool.alloc((size_t)2 * rows * sizeof(int), &plan->sig.ptr)) != BGW_OK ||
-      (rc = c->pool.alloc((size_t)2 * rows * sizeof(int), &plan->tau.ptr)) != BGW_OK)
+      (rc = c->pool.alloc((size_t)2 * rows * sizeof(int), &plan->tau.ptr)) != BGW_OK ||
+      (rc = c->pool.alloc((size_t)nmat * NB * NB * sizeof(float4), &plan->dff.ptr)) != BGW_OK)
     return fail(c, rc, "tensor-core inverse: slice buffers (%zu B each) could not be allocated", sb);
+  for (int m = 0; m < nmat; ++m) plan->batch.m[m].Dff = plan->dff.as<float4>() + (size_t)m * NB * NB;
   cuuint64_t gdim[2] = {(cuuint64_t)KR, (cuuint64_t)2 * S * rows};
   cuuint64_t gstride[1] = {(cuuint64_t)KR * sizeof(__half)};
   cuuint32_t estr[2] = {1, 1};
