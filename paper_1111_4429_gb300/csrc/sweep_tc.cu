@@ -134,6 +134,114 @@ struct OzBatch {
   OzMat m[kBatch];
 };
 
+// f 2^ex as a double, exactly, for a finite float f and |ex| < 900: the
+// exponent is added in the double's field (no FP32 scaling, no range issue).
+__device__ __forceinline__ double f2d_scaled(float f, int ex) {
+  // f 2^ex as a double, built from f's fields in 32-bit halves (f is zero or
+  // a normal number here; other inputs take the library path)
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (u << 1) == 0u ? __longlong_as_double((long long)(u & 0x80000000u) << 32)
+                                                   : ldexp((double)f, ex);
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u + (unsigned)ex) << 20) | ((u >> 3) & 0xFFFFFu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Two consecutive complex values in one 256-bit access (p 32-byte aligned).
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) {
+  asm("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(a.x), "=d"(a.y), "=d"(b.x), "=d"(b.y) : "l"(p));
+}
+__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(a.x), "d"(a.y), "d"(b.x), "d"(b.y) : "memory");
+}
+
+// two_sum(a, x w) for a power of two w (x w exact): the products enter fused
+// multiply-adds, the results are those of two_sum(a, x w) bit for bit.
+__device__ __forceinline__ void two_sum_scaled(float a, float x, float w, float& s, float& e) {
+  s = __fmaf_rn(x, w, a);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fmaf_rn(x, w, -bb));
+}
+
+// (h + l) 2^ex as one double for the level sums of the update, built in the
+// integer pipe without branches (the SM's FP64 pipe is the epilogue's
+// bottleneck, and straight-line code lets the compiler interleave a thread's
+// sixteen conversions).  h and l are finite and, where nonzero, far inside
+// FP32's normal range (sums of level values, integers times 2^-8L, and their
+// rounding errors: |h + l| >= 2^-90 or 0); |ex| < 900.  A two-sum first
+// makes the pair non-overlapping: s = fl(h + l), |t| <= ulp(s) / 2, and
+// |t| <= ulp(s) / 4 when s is a power of two and t lowers it.  The bits of
+// s 2^ex as a double are s's own fields re-biased; t, counted in units of
+// that double's last place (half that unit where t takes s below a power of
+// two) and rounded, is added to the bit pattern as an integer: s + t stays
+// inside the binade of s otherwise, and the pattern is monotonic in the
+// magnitude.  The result is within half a unit in the last place of the
+// exact (h + l) 2^ex plus the rounding of t to that unit.
+__device__ __forceinline__ double ff2d_pair(float s, float t, int ex) {
+  const unsigned us = __float_as_uint(s), ut = __float_as_uint(t);
+  const unsigned k = (us << 1) != 0u ? (unsigned)(896 + ex) << 20 : 0u;
+  const unsigned hi = (us & 0x80000000u) | (((us & 0x7FFFFFFFu) >> 3) + k);
+  const unsigned lo = us << 29;
+  const bool lowers = (int)(us ^ ut) < 0;   // t's sign differs from s's
+  const int ge = (int)((us >> 23) & 0xFFu) - (int)((ut >> 23) & 0xFFu) - ((lowers && (us << 9) == 0u) ? 1 : 0);
+  const unsigned mt = (ut & 0x7FFFFFu) | 0x800000u;
+  const unsigned d = ge <= 29 ? mt << (29 - ge) : (((mt >> min(ge - 30, 31)) + 1u) >> 1);
+  const long long b =
+      (long long)(((unsigned long long)hi << 32) | lo) + (lowers ? -(long long)d : (long long)d);
+  return __longlong_as_double(b);
+}
+__device__ __forceinline__ double ff2d_scaled(float h, float l, int ex) {
+  float s, t;
+  two_sum(h, l, s, t);
+  return ff2d_pair(s, t, ex);
+}
+
+// The rare FP64 forms, out of line: a short slow path inline would be
+// predicated and its FP64 instructions issued on every call.
+__device__ __noinline__ double ff_to_slow(float hi, float lo) { return (double)hi + (double)lo; }
+__device__ __noinline__ float2 ff_from_slow(double x) { return ff_from(x); }
+
+// hi + lo as a double for any finite pair: the integer form above where the
+// sum lies in [2^-66, 2^123), else the FP64 pipe.
+__device__ __forceinline__ double ff_to_any(float hi, float lo) {
+  float s, t;
+  two_sum(hi, lo, s, t);
+  const unsigned es = (__float_as_uint(s) >> 23) & 0xFFu;
+  if (es >= 61u && es <= 250u) return ff2d_pair(s, t, 0);
+  return ff_to_slow(hi, lo);
+}
+
+// ff_from(x) (hi = x rounded to FP32, lo = the remainder rounded) from x's
+// fields in the integer pipe for 2^-74 <= |x| < 2^126 (FP64 pipe otherwise):
+// hi is x's 53-bit mantissa rounded to 24 bits (half to even, the carry runs
+// into the exponent), lo the integer remainder d (|d| <= 2^28) converted and
+// scaled by x's last place, exactly as the FP64 form rounds it.
+__device__ __forceinline__ float2 ff_from_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FFull);
+  if (E < 949 || E > 1149) return ff_from_slow(x);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned q = (unsigned)(m >> 29);
+  const unsigned r = (unsigned)(m & 0x1FFFFFFFull);
+  const unsigned up = (r > 0x10000000u || (r == 0x10000000u && (q & 1u))) ? 1u : 0u;
+  q += up;
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sgn | (((unsigned)(E - 897) << 23) + q));
+  const float lo = __int2float_rn((int)r - (int)(up << 29)) * __uint_as_float((unsigned)(E - 948) << 23);
+  return make_float2(hi, sgn ? -lo : lo);
+}
+
+// -x by the sign bit (no FP64 instruction)
+__device__ __forceinline__ double neg_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
 // Balanced base-256 digits of a 56-bit fixed-point value: x = sum_a h_a
 // 2^{-8(a+1)} for |x| < 1, |h_0| <= 256 and |h_a| <= 128 (a >= 1).  X is
 // rint(x 2^56); integer arithmetic only.
@@ -146,8 +254,35 @@ __device__ __forceinline__ void digits7(long long X, __half* out, size_t stride)
     X = (X - dp) >> 8;
   }
   d[0] = (int)X;
+  // |d| <= 256: FP16 bits 0x6600 + d are 1536 + d exactly (unit spacing in
+  // [1024, 2048)); one FP16 subtraction leaves d, with no conversion
+  // instruction
 #pragma unroll
-  for (int a = 0; a < S; ++a) out[a * stride] = __int2half_rn(d[a]);
+  for (int a = 0; a < S; ++a)
+    out[a * stride] = __hsub(__ushort_as_half((unsigned short)(0x6600 + d[a])), __ushort_as_half(0x6600));
+}
+
+// rint(v 2^(56 - e)) for |v| < 2^e, rounded half to even, from v's own
+// fields in the integer pipe (the FP64 scaling and conversion it replaces run
+// on the SM's slow FP64 pipe): v = m 2^(E - 1075) with the 53-bit mantissa m
+// (no implicit bit below the normal range), so the result is m shifted by
+// E - 1019 - e (at most 3 to the left).
+__device__ __forceinline__ long long fixed56(double v, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7FFull);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+  const int sh = (E ? E : 1) - 1019 - e;
+  unsigned long long X;
+  if (sh >= 0) {
+    X = m << sh;
+  } else if (sh > -64) {
+    const int k = -sh;
+    const unsigned long long q = m >> k, r = m & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+    X = q + ((r > half || (r == half && (q & 1ull))) ? 1ull : 0ull);
+  } else {
+    X = 0ull;
+  }
+  return (b >> 63) ? -(long long)X : (long long)X;
 }
 
 // Slices and exponent of one 64-value row held by a warp (lane: value k and
@@ -159,7 +294,7 @@ __device__ __forceinline__ void slice_row(double re, double im, int lane, __half
   const unsigned er = ((unsigned)__double2hiint(re) >> 20) & 0x7FFu, ei = ((unsigned)__double2hiint(im) >> 20) & 0x7FFu;
   const unsigned emax = __reduce_max_sync(0xffffffffu, er > ei ? er : ei);
   const int e = emax ? (int)emax - 1022 : 0;   // |value| 2^-e < 1
-  const long long Xr = llrint(ldexp(re, 56 - e)), Xi = llrint(ldexp(im, 56 - e));
+  const long long Xr = fixed56(re, e), Xi = fixed56(im, e);
   digits7(Xr, base + lane, stride);
   digits7(Xi, base + lane + 32, stride);
   if (lane == 0) *exp_out = e;
@@ -175,7 +310,7 @@ __device__ __forceinline__ void slice_row(double re, double im, int lane, __half
 // precision, near 2^-34, is far above the pair arithmetic's 2^-43): the
 // products as exact pairs, their high words two-summed and the errors
 // gathered in the low word; the FP64 pipe keeps only the conversions.
-template <bool FF>
+template <bool FF, bool FFD>
 __global__ void __launch_bounds__(256) panel_slice_kernel(const __grid_constant__ OzBatch b, int k0, int rows_total,
                                                           int buf, __half* __restrict__ U, __half* __restrict__ V,
                                                           int* __restrict__ sig, int* __restrict__ tau) {
@@ -188,12 +323,13 @@ __global__ void __launch_bounds__(256) panel_slice_kernel(const __grid_constant_
   const int kb = min(NB, ng - k0);
   double2* A = M.A;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // FF: the look-ahead CTA that swept the block (every step after the first)
-  // left D^-1 as double-FP32 pairs; the first step's block comes in FP64
-  const bool have_ff = FF && M.Dff != nullptr && k0 > 0;
+  // FFD: the look-ahead CTA that swept the block (every step after the
+  // first) left D^-1 as double-FP32 pairs; the first step's block comes in
+  // FP64 (a template flag: a runtime test would leave the conversions
+  // predicated in every launch)
   for (int e = threadIdx.x; e < NB * NB; e += 256) {
     if constexpr (FF) {
-      if (have_ff) {
+      if constexpr (FFD) {
         reinterpret_cast<float4*>(&Ds[0][0])[e] = M.Dff[e];
       } else {
         const double2 d = M.Dinv[e];
@@ -212,11 +348,12 @@ __global__ void __launch_bounds__(256) panel_slice_kernel(const __grid_constant_
       cv = A[(size_t)i * ng + k0 + lane];
     } else {
       const double2 t = A[(size_t)(k0 + lane) * ng + i];
-      cv = make_double2(t.x, -t.y);
+      cv = make_double2(t.x, neg_bits(t.y));
     }
   }
+  // FF: the conversions in the integer pipe (the FP64 pipe bounds this kernel)
   if constexpr (FF) {
-    const float2 r = ff_from(cv.x), m = ff_from(cv.y);
+    const float2 r = ff_from_int(cv.x), m = ff_from_int(cv.y);
     reinterpret_cast<float4*>(&Cs[0][0])[warp * NB + lane] = make_float4(r.x, r.y, m.x, m.y);
   } else {
     Cs[warp][lane] = cv;
@@ -244,7 +381,7 @@ __global__ void __launch_bounds__(256) panel_slice_kernel(const __grid_constant_
         acc(si, ci, a.x, a.y, d.z, d.w);     // + a_r d_i
         acc(si, ci, a.z, a.w, d.x, d.y);     // + a_i d_r
       }
-      pv = make_double2((double)sr + (double)cr, (double)si + (double)ci);
+      pv = make_double2(ff_to_any(sr, cr), ff_to_any(si, ci));
     } else {
       for (int t = 0; t < kb; ++t) {
         const double2 a = Cs[warp][t], d = Ds[t][lane];
@@ -258,7 +395,7 @@ __global__ void __launch_bounds__(256) panel_slice_kernel(const __grid_constant_
       if (i >= k0 + kb)
         A[(size_t)i * ng + k0 + lane] = pv;
       else
-        A[(size_t)(k0 + lane) * ng + i] = make_double2(pv.x, -pv.y);
+        A[(size_t)(k0 + lane) * ng + i] = make_double2(pv.x, neg_bits(pv.y));
     }
   }
   if (lane >= kb) pv = cv = make_double2(0.0, 0.0);
@@ -311,70 +448,6 @@ __global__ void rows_from_r_kernel(const __grid_constant__ OzBatch b, int k0) {
   M.A[(size_t)(k0 + r) * M.ng + j] = M.C[(size_t)r * M.ng + j];
 }
 
-// f 2^ex as a double, exactly, for a finite float f and |ex| < 900: the
-// exponent is added in the double's field (no FP32 scaling, no range issue).
-__device__ __forceinline__ double f2d_scaled(float f, int ex) {
-  // f 2^ex as a double, built from f's fields in 32-bit halves (f is zero or
-  // a normal number here; other inputs take the library path)
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) return (u << 1) == 0u ? __longlong_as_double((long long)(u & 0x80000000u) << 32)
-                                                   : ldexp((double)f, ex);
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u + (unsigned)ex) << 20) | ((u >> 3) & 0xFFFFFu);
-  return __hiloint2double((int)hi, (int)(u << 29));
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// Two consecutive complex values in one 256-bit access (p 32-byte aligned).
-__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) {
-  asm("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(a.x), "=d"(a.y), "=d"(b.x), "=d"(b.y) : "l"(p));
-}
-__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
-  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(a.x), "d"(a.y), "d"(b.x), "d"(b.y) : "memory");
-}
-
-// two_sum(a, x w) for a power of two w (x w exact): the products enter fused
-// multiply-adds, the results are those of two_sum(a, x w) bit for bit.
-__device__ __forceinline__ void two_sum_scaled(float a, float x, float w, float& s, float& e) {
-  s = __fmaf_rn(x, w, a);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fmaf_rn(x, w, -bb));
-}
-
-// (h + l) 2^ex as one double for the level sums of the update, built in the
-// integer pipe without branches (the SM's FP64 pipe is the epilogue's
-// bottleneck, and straight-line code lets the compiler interleave a thread's
-// sixteen conversions).  h and l are finite and, where nonzero, far inside
-// FP32's normal range (sums of level values, integers times 2^-8L, and their
-// rounding errors: |h + l| >= 2^-90 or 0); |ex| < 900.  A two-sum first
-// makes the pair non-overlapping: s = fl(h + l), |t| <= ulp(s) / 2, and
-// |t| <= ulp(s) / 4 when s is a power of two and t lowers it.  The bits of
-// s 2^ex as a double are s's own fields re-biased; t, counted in units of
-// that double's last place (half that unit where t takes s below a power of
-// two) and rounded, is added to the bit pattern as an integer: s + t stays
-// inside the binade of s otherwise, and the pattern is monotonic in the
-// magnitude.  The result is within half a unit in the last place of the
-// exact (h + l) 2^ex plus the rounding of t to that unit.
-__device__ __forceinline__ double ff2d_scaled(float h, float l, int ex) {
-  float s, t;
-  two_sum(h, l, s, t);
-  const unsigned us = __float_as_uint(s), ut = __float_as_uint(t);
-  const unsigned k = (us << 1) != 0u ? (unsigned)(896 + ex) << 20 : 0u;
-  const unsigned hi = (us & 0x80000000u) | (((us & 0x7FFFFFFFu) >> 3) + k);
-  const unsigned lo = us << 29;
-  const bool lowers = (int)(us ^ ut) < 0;   // t's sign differs from s's
-  const int ge = (int)((us >> 23) & 0xFFu) - (int)((ut >> 23) & 0xFFu) - ((lowers && (us << 9) == 0u) ? 1 : 0);
-  const unsigned mt = (ut & 0x7FFFFFu) | 0x800000u;
-  const unsigned d = ge <= 29 ? mt << (29 - ge) : (((mt >> min(ge - 30, 31)) + 1u) >> 1);
-  const long long b =
-      (long long)(((unsigned long long)hi << 32) | lo) + (lowers ? -(long long)d : (long long)d);
-  return __longlong_as_double(b);
-}
 
 // ---------------------------------------------------------------------------
 // Persistent, pipelined form of the update.  A CTA takes work items of up to
@@ -731,10 +804,6 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
         float hr[8], lr[8], hm[8], lm[8];
         if (have) {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          // Two passes of 16 rows: each issues the loads of every level (re
-          // and im) before one wait, so the tensor-memory round trips of a
-          // tile are two instead of one per level.
-#pragma unroll
           // Four rounds (two 16-row halves, real then imaginary parts):
           // each issues the loads of all SL levels before one wait.
           // level L enters scaled by w = 2^-8L (exact), folded into fused
@@ -1015,14 +1084,20 @@ int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) 
 int oz_panel_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st) {
   using namespace oz;
   const int rpad = (ngmax + BM - 1) / BM * BM;
-  if (plan->ff_chain)
-    panel_slice_kernel<true><<<dim3(rpad / 8, plan->nmat), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
-                                                                         plan->U.as<__half>(), plan->V.as<__half>(),
-                                                                         plan->sig.as<int>(), plan->tau.as<int>());
+  // the look-ahead launches of the double-FP32 chain leave D^-1 as pairs
+  // for every step after the first
+  if (plan->ff_chain && k0 > 0)
+    panel_slice_kernel<true, true><<<dim3(rpad / 8, plan->nmat), 256, 0, st>>>(
+        plan->batch, k0, plan->rows_total, buf, plan->U.as<__half>(), plan->V.as<__half>(), plan->sig.as<int>(),
+        plan->tau.as<int>());
+  else if (plan->ff_chain)
+    panel_slice_kernel<true, false><<<dim3(rpad / 8, plan->nmat), 256, 0, st>>>(
+        plan->batch, k0, plan->rows_total, buf, plan->U.as<__half>(), plan->V.as<__half>(), plan->sig.as<int>(),
+        plan->tau.as<int>());
   else
-    panel_slice_kernel<false><<<dim3(rpad / 8, plan->nmat), 256, 0, st>>>(plan->batch, k0, plan->rows_total, buf,
-                                                                          plan->U.as<__half>(), plan->V.as<__half>(),
-                                                                          plan->sig.as<int>(), plan->tau.as<int>());
+    panel_slice_kernel<false, false><<<dim3(rpad / 8, plan->nmat), 256, 0, st>>>(
+        plan->batch, k0, plan->rows_total, buf, plan->U.as<__half>(), plan->V.as<__half>(), plan->sig.as<int>(),
+        plan->tau.as<int>());
   BGW_CUDA(c, cudaGetLastError());
   return BGW_OK;
 }
