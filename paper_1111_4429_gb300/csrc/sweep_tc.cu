@@ -134,19 +134,6 @@ struct OzBatch {
   OzMat m[kBatch];
 };
 
-// f 2^ex as a double, exactly, for a finite float f and |ex| < 900: the
-// exponent is added in the double's field (no FP32 scaling, no range issue).
-__device__ __forceinline__ double f2d_scaled(float f, int ex) {
-  // f 2^ex as a double, built from f's fields in 32-bit halves (f is zero or
-  // a normal number here; other inputs take the library path)
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) return (u << 1) == 0u ? __longlong_as_double((long long)(u & 0x80000000u) << 32)
-                                                   : ldexp((double)f, ex);
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u + (unsigned)ex) << 20) | ((u >> 3) & 0xFFFFFu);
-  return __hiloint2double((int)hi, (int)(u << 29));
-}
-
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
@@ -169,78 +156,12 @@ __device__ __forceinline__ void two_sum_scaled(float a, float x, float w, float&
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fmaf_rn(x, w, -bb));
 }
 
-// (h + l) 2^ex as one double for the level sums of the update, built in the
-// integer pipe without branches (the SM's FP64 pipe is the epilogue's
-// bottleneck, and straight-line code lets the compiler interleave a thread's
-// sixteen conversions).  h and l are finite and, where nonzero, far inside
-// FP32's normal range (sums of level values, integers times 2^-8L, and their
-// rounding errors: |h + l| >= 2^-90 or 0); |ex| < 900.  A two-sum first
-// makes the pair non-overlapping: s = fl(h + l), |t| <= ulp(s) / 2, and
-// |t| <= ulp(s) / 4 when s is a power of two and t lowers it.  The bits of
-// s 2^ex as a double are s's own fields re-biased; t, counted in units of
-// that double's last place (half that unit where t takes s below a power of
-// two) and rounded, is added to the bit pattern as an integer: s + t stays
-// inside the binade of s otherwise, and the pattern is monotonic in the
-// magnitude.  The result is within half a unit in the last place of the
-// exact (h + l) 2^ex plus the rounding of t to that unit.
-__device__ __forceinline__ double ff2d_pair(float s, float t, int ex) {
-  const unsigned us = __float_as_uint(s), ut = __float_as_uint(t);
-  const unsigned k = (us << 1) != 0u ? (unsigned)(896 + ex) << 20 : 0u;
-  const unsigned hi = (us & 0x80000000u) | (((us & 0x7FFFFFFFu) >> 3) + k);
-  const unsigned lo = us << 29;
-  const bool lowers = (int)(us ^ ut) < 0;   // t's sign differs from s's
-  const int ge = (int)((us >> 23) & 0xFFu) - (int)((ut >> 23) & 0xFFu) - ((lowers && (us << 9) == 0u) ? 1 : 0);
-  const unsigned mt = (ut & 0x7FFFFFu) | 0x800000u;
-  const unsigned d = ge <= 29 ? mt << (29 - ge) : (((mt >> min(ge - 30, 31)) + 1u) >> 1);
-  const long long b =
-      (long long)(((unsigned long long)hi << 32) | lo) + (lowers ? -(long long)d : (long long)d);
-  return __longlong_as_double(b);
-}
 __device__ __forceinline__ double ff2d_scaled(float h, float l, int ex) {
   float s, t;
   two_sum(h, l, s, t);
   return ff2d_pair(s, t, ex);
 }
 
-// The rare FP64 forms, out of line: a short slow path inline would be
-// predicated and its FP64 instructions issued on every call.
-__device__ __noinline__ double ff_to_slow(float hi, float lo) { return (double)hi + (double)lo; }
-__device__ __noinline__ float2 ff_from_slow(double x) { return ff_from(x); }
-
-// hi + lo as a double for any finite pair: the integer form above where the
-// sum lies in [2^-66, 2^123), else the FP64 pipe.
-__device__ __forceinline__ double ff_to_any(float hi, float lo) {
-  float s, t;
-  two_sum(hi, lo, s, t);
-  const unsigned es = (__float_as_uint(s) >> 23) & 0xFFu;
-  if (es >= 61u && es <= 250u) return ff2d_pair(s, t, 0);
-  return ff_to_slow(hi, lo);
-}
-
-// ff_from(x) (hi = x rounded to FP32, lo = the remainder rounded) from x's
-// fields in the integer pipe for 2^-74 <= |x| < 2^126 (FP64 pipe otherwise):
-// hi is x's 53-bit mantissa rounded to 24 bits (half to even, the carry runs
-// into the exponent), lo the integer remainder d (|d| <= 2^28) converted and
-// scaled by x's last place, exactly as the FP64 form rounds it.
-__device__ __forceinline__ float2 ff_from_int(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int E = (int)((b >> 52) & 0x7FFull);
-  if (E < 949 || E > 1149) return ff_from_slow(x);
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  unsigned q = (unsigned)(m >> 29);
-  const unsigned r = (unsigned)(m & 0x1FFFFFFFull);
-  const unsigned up = (r > 0x10000000u || (r == 0x10000000u && (q & 1u))) ? 1u : 0u;
-  q += up;
-  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
-  const float hi = __uint_as_float(sgn | (((unsigned)(E - 897) << 23) + q));
-  const float lo = __int2float_rn((int)r - (int)(up << 29)) * __uint_as_float((unsigned)(E - 948) << 23);
-  return make_float2(hi, sgn ? -lo : lo);
-}
-
-// -x by the sign bit (no FP64 instruction)
-__device__ __forceinline__ double neg_bits(double x) {
-  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
-}
 
 // Balanced base-256 digits of a 56-bit fixed-point value: x = sum_a h_a
 // 2^{-8(a+1)} for |x| < 1, |h_0| <= 256 and |h_a| <= 128 (a >= 1).  X is
