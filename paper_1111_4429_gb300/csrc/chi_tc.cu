@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "runtime.h"
+#include "sweep_common.cuh"
 
 namespace bgw {
 
@@ -700,8 +701,10 @@ __global__ void reduce_kernel(const float* __restrict__ work, int nseg, int ntil
     iml = __fadd_rn(iml, __fadd_rn(__fsub_rn(im, __fsub_rn(t, z)), __fsub_rn(b, z)));
     im = t;
   }
-  const double f = factor * ldexp(1.0, -2 * scale_exp(maxbits, bf16));
-  double2 v = make_double2(((double)re + (double)rel) * f, ((double)im + (double)iml) * f);
+  // the pairs to FP64 with the scale 2^-2e applied in the integer pipe: the
+  // FP64 pipe keeps one multiply by the factor and one add per word
+  const int ex = -2 * scale_exp(maxbits, bf16);
+  double2 v = make_double2(ff_to_scaled_any(re, rel, ex) * factor, ff_to_scaled_any(im, iml, ex) * factor);
   double2* lo = chi + (size_t)g * ng + gp;
   if (accumulate) {
     const double2 o = *lo;
@@ -710,7 +713,7 @@ __global__ void reduce_kernel(const float* __restrict__ work, int nseg, int ntil
   }
   if (g == gp) v.y = 0.0;
   *lo = v;
-  if (g != gp) chi[(size_t)gp * ng + g] = make_double2(v.x, -v.y);
+  if (g != gp) chi[(size_t)gp * ng + g] = make_double2(v.x, neg_bits(v.y));
 }
 
 // Row-major operands of a general product C = X^H-row Y-row (the Sigma

@@ -208,6 +208,18 @@ __device__ __forceinline__ double ff_to_any(float hi, float lo) {
   return ff_to_slow(hi, lo);
 }
 
+// (hi + lo) 2^ex as a double for any finite pair and |ex| < 600: the integer
+// form where the two-summed pair lies in [2^-66, 2^123), else the FP64 pipe.
+static __device__ __noinline__ double ff_to_scaled_slow(float hi, float lo, int ex) {
+  return ldexp((double)hi + (double)lo, ex);
+}
+__device__ __forceinline__ double ff_to_scaled_any(float hi, float lo, int ex) {
+  const float2 st = ff_two_sum(hi, lo);
+  const unsigned es = (__float_as_uint(st.x) >> 23) & 0xFFu;
+  if (es >= 61u && es <= 250u) return ff2d_pair(st.x, st.y, ex);
+  return ff_to_scaled_slow(hi, lo, ex);
+}
+
 // ff_from(x) (hi = x rounded to FP32, lo = the remainder rounded) from x's
 // fields in the integer pipe for 2^-74 <= |x| < 2^126 (FP64 pipe otherwise):
 // hi is x's 53-bit mantissa rounded to 24 bits (half to even, the carry runs
