@@ -460,16 +460,19 @@ __global__ void sw_finish_kernel(const __grid_constant__ SweepBatch b) {
   const long long nlow = (long long)ng * (ng + 1) / 2;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nlow;
        e += (long long)gridDim.x * blockDim.x) {
-    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    // row of the packed index: an FP32 estimate (the FP64 pipe is slow on
+    // this part) corrected by integer steps; signs flipped on the bits
+    int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
     while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
     while ((long long)i * (i + 1) / 2 > e) --i;
     const int j = (int)(e - (long long)i * (i + 1) / 2);
     const double2 v = A[(size_t)i * ng + j];
+    const double nx = neg_bits(v.x);
     if (i == j) {
-      A[(size_t)i * ng + j] = make_double2(-v.x, 0.0);
+      A[(size_t)i * ng + j] = make_double2(nx, 0.0);
     } else {
-      A[(size_t)i * ng + j] = make_double2(-v.x, -v.y);
-      A[(size_t)j * ng + i] = make_double2(-v.x, v.y);
+      A[(size_t)i * ng + j] = make_double2(nx, neg_bits(v.y));
+      A[(size_t)j * ng + i] = make_double2(nx, v.y);
     }
   }
 }
