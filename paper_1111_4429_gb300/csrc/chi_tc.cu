@@ -450,28 +450,32 @@ __global__ void split_kernel(const float2* __restrict__ M, const float2* __restr
     t[r][tx] = v;
   }
   __syncthreads();
+  // two adjacent pairs per thread and row: paired conversions (one
+  // instruction rounds two values) and 4-byte stores
   const size_t plane = (size_t)ngpad * kpad;
-  for (int r = ty; r < 32; r += 8) {
-    const int g = g0 + r;
-    const long long p = pc0 + tx;
-    const float2 v = t[tx][r];
-    H rh, ih, rl, il;
-    if constexpr (sizeof(H) == 2 && std::is_same<H, __half>::value) {
-      rh = __float2half_rn(v.x);
-      ih = __float2half_rn(v.y);
-      rl = __float2half_rn(v.x - __half2float(rh));
-      il = __float2half_rn(v.y - __half2float(ih));
+  const int q = ty * 32 + tx, pp = 2 * (q & 15);
+#pragma unroll
+  for (int gr = q >> 4; gr < 32; gr += 16) {
+    const float2 a = t[pp][gr], b = t[pp + 1][gr];
+    const size_t o = (size_t)(g0 + gr) * kpad + pc0 + pp;   // even: 4-byte aligned (kpad is even)
+    if constexpr (std::is_same<H, __half>::value) {
+      const __half2 rh = __floats2half2_rn(a.x, b.x), ih = __floats2half2_rn(a.y, b.y);
+      const float2 rf = __half22float2(rh), jf = __half22float2(ih);
+      const __half2 rl = __floats2half2_rn(a.x - rf.x, b.x - rf.y), il = __floats2half2_rn(a.y - jf.x, b.y - jf.y);
+      *reinterpret_cast<__half2*>(planes + o) = rh;
+      *reinterpret_cast<__half2*>(planes + plane + o) = ih;
+      *reinterpret_cast<__half2*>(planes + 2 * plane + o) = rl;
+      *reinterpret_cast<__half2*>(planes + 3 * plane + o) = il;
     } else {
-      rh = __float2bfloat16_rn(v.x);
-      ih = __float2bfloat16_rn(v.y);
-      rl = __float2bfloat16_rn(v.x - __bfloat162float(rh));
-      il = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+      const __nv_bfloat162 rh = __floats2bfloat162_rn(a.x, b.x), ih = __floats2bfloat162_rn(a.y, b.y);
+      const float2 rf = __bfloat1622float2(rh), jf = __bfloat1622float2(ih);
+      const __nv_bfloat162 rl = __floats2bfloat162_rn(a.x - rf.x, b.x - rf.y),
+                           il = __floats2bfloat162_rn(a.y - jf.x, b.y - jf.y);
+      *reinterpret_cast<__nv_bfloat162*>(planes + o) = rh;
+      *reinterpret_cast<__nv_bfloat162*>(planes + plane + o) = ih;
+      *reinterpret_cast<__nv_bfloat162*>(planes + 2 * plane + o) = rl;
+      *reinterpret_cast<__nv_bfloat162*>(planes + 3 * plane + o) = il;
     }
-    const size_t o = (size_t)g * kpad + p;
-    planes[o] = rh;
-    planes[plane + o] = ih;
-    planes[2 * plane + o] = rl;
-    planes[3 * plane + o] = il;
   }
 }
 
