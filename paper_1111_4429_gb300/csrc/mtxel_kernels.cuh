@@ -248,19 +248,27 @@ __global__ void __launch_bounds__(32 * kPairWarps, sizeof(T) == 4 ? 4 : 2)
     }
   }
   __syncwarp();
-  // x pass: the kept (kx, ky) columns of each kept ky row, straight to T
+  // x pass: the kept (kx, ky) columns of each kept ky row (low-band grids
+  // keep at most N/2 <= 32 rows: one per lane); the columns are staged over
+  // Y once every row is read and stored to T in coalesced runs
   cpx<T>* Tp = Tbuf + ((size_t)pl * N + z) * ncol;
-  for (int s = lane; s < nys; s += 32) {
+  const int s = lane;
+  cpx<T> lo[Q], hi[Q];
+  if (s < nys) {
     const cpx<T>* row = Yw + (size_t)s * LD;
-    cpx<T> lo[Q], hi[Q];
     fft_quarters<T, N>([&](int x) { return row[x]; }, lo, hi);
+  }
+  __syncwarp();
+  if (s < nys) {
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       const int c0 = colmap[k * nys + s], c3 = colmap[(k + 3 * Q) * nys + s];
-      if (c0 >= 0) Tp[c0] = lo[k];
-      if (c3 >= 0) Tp[c3] = hi[k];
+      if (c0 >= 0) Yw[c0] = lo[k];
+      if (c3 >= 0) Yw[c3] = hi[k];
     }
   }
+  __syncwarp();
+  for (int c = lane; c < ncol; c += 32) Tp[c] = Yw[c];
 }
 
 // ---------------------------------------------------------------- pair z
