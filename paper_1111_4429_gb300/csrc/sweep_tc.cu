@@ -389,12 +389,12 @@ __device__ __forceinline__ int row_width(int mode, int I, int nJ) { return mode 
 // the critical path of the next step), then the rest of row tile In in
 // chunks (tile Jn skipped there), then the tiles (I > In, Jn).
 // Column tiles per work item: 2 in the look-ahead launch (its CTAs are on the
-// critical path); else 4 with seven slices and 3 with five (measured: the
-// five-slice items are cheaper, so smaller items balance the SMs better).
-__host__ __device__ inline int pipe_jpi(int mode, int sl) { return mode == 1 ? 2 : (sl < 7 ? 3 : kJPI); }
-__host__ __device__ inline int pipe_items(int mode, int sl, int nI, int nJ, int In, bool has_next) {
+// critical path); else the launch's width (oz_update picks it: 4 with seven
+// slices, 3 with five, 2 where fewer items than SMs would result).
+__host__ __device__ inline int pipe_jpi(int mode, int wide) { return mode == 1 ? 2 : wide; }
+__host__ __device__ inline int pipe_items(int mode, int wide, int nI, int nJ, int In, bool has_next) {
   int n = 0;
-  const int jpi = pipe_jpi(mode, sl);
+  const int jpi = pipe_jpi(mode, wide);
   if (mode == 1) {
     const int w = (4 * In + 4 < nJ) ? 4 * In + 4 : nJ;
     return 1 + (w + jpi - 1) / jpi + (nI - In - 1 > 0 ? nI - In - 1 : 0);
@@ -406,9 +406,9 @@ __host__ __device__ inline int pipe_items(int mode, int sl, int nI, int nJ, int 
   }
   return n;
 }
-__device__ inline void pipe_decode(int mode, int sl, int item, int nI, int nJ, int In, int Jn, bool has_next, int& I, int& J0,
+__device__ inline void pipe_decode(int mode, int wide, int item, int nI, int nJ, int In, int Jn, bool has_next, int& I, int& J0,
                                    int& J1) {
-  const int jpi = pipe_jpi(mode, sl);
+  const int jpi = pipe_jpi(mode, wide);
   if (mode == 1) {
     const int w = row_width(1, In, nJ);
     const int nrow = (w + jpi - 1) / jpi;
@@ -446,13 +446,13 @@ __device__ inline void pipe_decode(int mode, int sl, int item, int nI, int nJ, i
 struct PipeCursor {
   int I = 0, base = 0;
 };
-__device__ inline void pipe_decode_next(PipeCursor& cur, int mode, int sl, int item, int nI, int nJ, int In, int Jn,
+__device__ inline void pipe_decode_next(PipeCursor& cur, int mode, int wide, int item, int nI, int nJ, int In, int Jn,
                                         bool has_next, int& I, int& J0, int& J1) {
   if (mode == 1) {
-    pipe_decode(mode, sl, item, nI, nJ, In, Jn, has_next, I, J0, J1);
+    pipe_decode(mode, wide, item, nI, nJ, In, Jn, has_next, I, J0, J1);
     return;
   }
-  const int jpi = pipe_jpi(mode, sl);
+  const int jpi = pipe_jpi(mode, wide);
   for (; cur.I < nI; ++cur.I) {
     const int w = row_width(mode, cur.I, nJ);
     const int n = (mode == 2 && has_next && cur.I == In) ? 0 : (w + jpi - 1) / jpi;
@@ -493,11 +493,14 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, vol
 // gives an update error near 2^-48 of its scale, 5 near 2^-34.  FFC: the
 // look-ahead CTA sweeps the next diagonal block in double FP32 (about 2^-46
 // per operation, on the FP32 pipe) instead of FP64.
-template <bool realv, int SL, bool FFC>
+template <bool realv, int SL, bool FFC, bool NARROW>
 __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per sub-partition, 96 registers
     update_pipe_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap vmap,
                        const __grid_constant__ OzBatch b, int k0, int rows_total, int buf, int mode,
                        const int* __restrict__ sig, const int* __restrict__ tau, int* __restrict__ status) {
+  // column tiles per bulk work item, a compile-time constant (a runtime
+  // width costs 2% in the item decode)
+  constexpr int wide = NARROW ? 2 : (SL < 7 ? 3 : kJPI);
   // Levels 1 .. kTwoSumLevels are summed exactly (two-sum) into the high
   // word: with 7 slices the target is near 2^-48, so levels 1 and 2 (2^-8,
   // 2^-16 of the sum) need it; with 5 slices (near 2^-34) only level 1.
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
   const bool has_next = k1 < ng;
   const int In = k1 / BM, Jn = k1 / BN;
   if (mode == 1 && !has_next) return;
-  const int nitems = pipe_items(mode, SL, nI, nJ, In, has_next);
+  const int nitems = pipe_items(mode, wide, nI, nJ, In, has_next);
   const int slice_base = buf * S * rows_total;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -559,7 +562,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)   // 17 warps: at most 5 per 
   PipeCursor cursor;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++items_done) {
     int I, J0, J1;
-    pipe_decode_next(cursor, mode, SL, item, nI, nJ, In, Jn, has_next, I, J0, J1);
+    pipe_decode_next(cursor, mode, wide, item, nI, nJ, In, Jn, has_next, I, J0, J1);
     const int i0 = I * BM;
     // tiles of the item that are not skipped, in order
     int Js[kJPI], nt = 0;
@@ -972,9 +975,11 @@ int oz_prepare(Ctx* c, int nmat, const int* ng, double2* const* A, const double2
     return fail(c, BGW_ECUDA, "tensor-core inverse: tensor map encoding failed");
   // U slices, two V buffers, alignment and barriers: about 170 KiB dynamic (7 slices)
   const size_t psmem = pipe_smem(slices);
-#define BGW_PIPE_ATTR(RV, SLC, FF)                                                                      \
-  BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<RV, SLC, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                   (int)psmem))
+#define BGW_PIPE_ATTR(RV, SLC, FF)                                                                        \
+  BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<RV, SLC, FF, false>,                                       \
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));                    \
+  BGW_CUDA(c, cudaFuncSetAttribute(update_pipe_kernel<RV, SLC, FF, true>,                                        \
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem))
   if (slices == 7 && !plan->ff_chain) {
     BGW_PIPE_ATTR(false, 7, false);
     BGW_PIPE_ATTR(true, 7, false);
@@ -1036,10 +1041,19 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
     grid = std::min(4 * In + 4, nJ) + std::max(0, nI - In - 1);
   }
   if (plan->general) mode = 3;
-  // one work item (up to kJPI tiles of a row tile) per CTA
+  // Column tiles per bulk work item: 4 with seven slices, 3 with five; 2
+  // where those items would not exceed the SMs (each CTA then pipelines two
+  // items instead of running one alone; measured with seven slices: N_G 2120
+  // 3.10 -> 2.95 ms per inverse, while at 7180 items of 4 stay best).
+  const int nsm = sm_count(c);
+  int wide = plan->slices < 7 ? 3 : kJPI;
   {
     const int nI = (ngmax + BM - 1) / BM, nJ = (ngmax + BN - 1) / BN, k1 = k0 + NB;
-    grid = pipe_items(mode, plan->slices, nI, nJ, k1 / BM, k1 < ngmax);
+    grid = pipe_items(mode, wide, nI, nJ, k1 / BM, k1 < ngmax);
+    if (mode != 1 && (long long)grid * plan->nmat <= nsm) {
+      wide = 2;
+      grid = pipe_items(mode, wide, nI, nJ, k1 / BM, k1 < ngmax);
+    }
   }
   if (grid <= 0) return BGW_OK;
   // Bulk launches with more items than SMs run persistent CTAs (items taken
@@ -1048,16 +1062,23 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
   // the matrices of the batch share the SMs evenly; the look-ahead launch
   // (on the critical path, few items) keeps one item per CTA.
   if (mode != 1) {
-    const int nsm = sm_count(c), per = nsm / plan->nmat;
+    const int per = nsm / plan->nmat;
     if (per >= 1 && (long long)grid * plan->nmat > nsm && 10 * per * plan->nmat >= 9 * nsm)
       grid = std::min(grid, per);
   }
   const size_t smem = pipe_smem(plan->slices);
   const dim3 g(grid, plan->nmat);
 #define BGW_PIPE_LAUNCH(RV, SLC, FF)                                                                          \
-  update_pipe_kernel<RV, SLC, FF><<<g, kPipeThreads, smem, st>>>(plan->umap, plan->vmap, plan->batch, k0,      \
-                                                                 plan->rows_total, buf, mode, plan->sig.as<int>(), \
-                                                                 plan->tau.as<int>(), c->d_status)
+  do {                                                                                                         \
+    if (wide == 2)                                                                                             \
+      update_pipe_kernel<RV, SLC, FF, true><<<g, kPipeThreads, smem, st>>>(                                     \
+          plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, buf, mode, plan->sig.as<int>(),           \
+          plan->tau.as<int>(), c->d_status);                                                                   \
+    else                                                                                                       \
+      update_pipe_kernel<RV, SLC, FF, false><<<g, kPipeThreads, smem, st>>>(                                    \
+          plan->umap, plan->vmap, plan->batch, k0, plan->rows_total, buf, mode, plan->sig.as<int>(),           \
+          plan->tau.as<int>(), c->d_status);                                                                   \
+  } while (0)
   const bool rv = plan->real_values;
   if (plan->slices == 7 && !plan->ff_chain) {
     if (rv)
