@@ -814,12 +814,40 @@ def run_batch_c3(ctx, prec, steps=2):
     err = max(float(torch.linalg.matrix_norm(outs[0][f] - ref[i]) / torch.linalg.matrix_norm(ref[i]))
               for i, f in enumerate((0, 11)))
     chi_flops = sum(12 * 8.0 * s.ng * s.ng * s.npairs for s in systems)
+    gap = graph_gap_us()
     return {"workload": "c1 cell, q = (0.05 j, 0, 0) for j = 1..8, 12 Gauss-Legendre iw in [0, 2] Ha, "
                         "N_G " + "/".join(str(s.ng) for s in systems),
             "solves_per_s": 96.0 / (ms / 1e3), "ms_per_batch": ms,
             "chi_zgemm_eq_tflops_over_batch": chi_flops / (ms / 1e3) / 1e12,
             "graph_launches_per_batch": graph_launches / steps,
+            "graph_us_per_dependent_launch": gap,
+            "launch_overhead_share_bound": gap * 1e-3 * (graph_launches / steps) / ms,
             "epsinv_rel_err_vs_plain_fp64_gpu": err}
+
+
+def graph_gap_us(n=2000, reps=5):
+    """Device time per launch of a replayed CUDA graph of n dependent one-element
+    kernels (each waits for the one before): what a graph adds per kernel, and
+    so the most that one persistent kernel per stage could save per launch."""
+    import torch
+    x = torch.zeros(1, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        x.add_(1.0)
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        for _ in range(n):
+            x.add_(1.0)
+    with torch.cuda.stream(st):
+        g.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            g.replay()
+        e1.record(st)
+    st.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / (reps * n)
 
 
 def run_serve_c4(prec, nreq=200, seed=1004, window=16):
@@ -1085,6 +1113,55 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": desc, "precision": args.prec, "launches": ctx.launch_count()}))
 
 
+def run_item_widths(args):
+    """Time the mixed-precision inverse (bgw_epsinv, tensor-core update, seven
+    slices, double-FP32 chain; graph replays on a side stream, best of 3 x 5
+    calls) at several N_G with the bulk update items wide (BGW_OPT_UPDATE_ITEMS
+    0), of two column tiles (1) and by the default rule (-1); one JSON line per
+    N_G.  The matrices are seeded chi = -1e-3 Z Z^H / N_G on prefixes of the
+    60^3 cell's epsilon sphere; the three inverses are checked bit for bit."""
+    import numpy as np
+    import torch
+    from paper_1111_4429_gb300 import bgw, synth
+    s2 = synth.config_system("c2")
+    cell = bgw.system_cell(s2)
+    for ng in (743, 1185, 1600, 2120, 2545, 3000, 3911, 5000, 7180):
+        geps = np.ascontiguousarray(s2.geps[:ng])
+        gen = torch.Generator(device="cuda").manual_seed(3)
+        z = torch.randn((ng, ng), dtype=torch.complex128, device="cuda", generator=gen) / np.sqrt(ng)
+        chi = -(z @ z.conj().T) * 1e-3
+        inv = torch.empty_like(chi)
+        row = {"ng": ng}
+        ref = None
+        same = True
+        for name, items in (("wide_ms", 0), ("narrow_ms", 1), ("rule_ms", -1)):
+            ctx = bgw.Context(0)
+            ctx.set_option(bgw.BGW_OPT_INVERSE, 1)
+            ctx.set_option(bgw.BGW_OPT_DOUBLE_FP32, 1)
+            ctx.set_option(bgw.BGW_OPT_UPDATE_ITEMS, items)
+            st = torch.cuda.Stream()
+            best = float("inf")
+            with torch.cuda.stream(st):
+                for _ in range(3):
+                    ctx.epsinv([cell], [geps], [chi], None, [inv])
+                st.synchronize()
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    for _ in range(5):
+                        ctx.epsinv([cell], [geps], [chi], None, [inv])
+                    e1.record(st)
+                    st.synchronize()
+                    best = min(best, e0.elapsed_time(e1) / 5)
+            h = inv.cpu().numpy()
+            ref = h if ref is None else ref
+            same = same and bool(np.array_equal(h, ref))
+            row[name] = round(best, 3)
+            ctx.close()
+        row["bit_identical"] = same
+        print(json.dumps(row), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1099,8 +1176,12 @@ def main():
                     choices=["solve", "general", "w", "sigma", "c2"],
                     help="small case for ncu captures (solve: reduced c1 solve; general: one pivoted general "
                          "inverse; w: screened W on 8 matrices; sigma: one mixed Sigma call)")
+    ap.add_argument("--item-widths", action="store_true",
+                    help="time the mixed inverse at several N_G under each bulk update item width")
     args = ap.parse_args()
-    if args.profile_case:
+    if args.item_widths:
+        run_item_widths(args)
+    elif args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)

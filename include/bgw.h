@@ -157,9 +157,9 @@ int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
  *    sums in FP64.  Shorter segments lower the FP32 accumulation error and
  *    cost more drains of tensor memory.                                      */
 /*  BGW_OPT_AUTOTUNE: 1 (default) lets the context time the candidate tile
- *    shapes of the pair transform (pairs per block) the first time it meets
- *    a (grid, precision, epsilon-sphere shape) and keep the fastest; 0 uses
- *    the fixed default for shapes not yet tuned.                           */
+ *    shapes of the pair transform (pairs per block, or a warp per pair) the
+ *    first time it meets a (grid, precision, epsilon-sphere shape) and keep
+ *    the fastest; 0 uses the fixed default for shapes not yet tuned.       */
 /*  BGW_OPT_CHI_CHUNK_PAIRS: mixed-precision chi converts and sums the pairs
  *    in chunks of this many pairs (rounded down to a multiple of 32), each
  *    chunk's FP64 sum added into chi; 0 (default) sizes chunks so that their
@@ -209,6 +209,13 @@ int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
  *    the default pairs per block; 1: one warp per pair, where every kept
  *    frequency lies in |k| < N/4 (elsewhere 0 runs).  The results agree to
  *    rounding; the choice only changes the speed.                          */
+/*  BGW_OPT_UPDATE_ITEMS: column tiles per work item of the tensor-core
+ *    sweep's bulk update launches.  -1 (default): the SM-count rule, items
+ *    of 2 tiles where the wider items would number no more than the SMs
+ *    (a CTA then pipelines two items instead of running one alone); 0: the
+ *    wider items (4 column tiles with seven slices, 3 with five); 1: items
+ *    of 2 tiles.  Every tile's arithmetic is the same: the results are
+ *    bit-identical, only the speed changes.                                */
 /*  BGW_OPT_WAIT_LIMIT_NS: how long (nanoseconds, 0 .. 10^10; default 10^9)
  *    a wait of the tensor-core chi kernels on its pipeline (a copy landing,
  *    an MMA stage finishing, tensor memory being drained) may last before
@@ -219,7 +226,7 @@ int bgw_graph_stats(bgw_ctx* ctx, uint64_t* graphs, uint64_t* replays);
  *    wait that is not already complete (a test of that path).              */
 enum { BGW_OPT_CHI_SEGMENT_PAIRS = 1, BGW_OPT_TIMING = 2, BGW_OPT_AUTOTUNE = 3, BGW_OPT_CHI_CHUNK_PAIRS = 4,
        BGW_OPT_INVERSE = 5, BGW_OPT_HEAD = 6, BGW_OPT_SIGMA_DENSITY = 7, BGW_OPT_UPDATE_SLICES = 8,
-       BGW_OPT_DOUBLE_FP32 = 9, BGW_OPT_WAIT_LIMIT_NS = 10, BGW_OPT_PAIR_KERNEL = 11 };
+       BGW_OPT_DOUBLE_FP32 = 9, BGW_OPT_WAIT_LIMIT_NS = 10, BGW_OPT_PAIR_KERNEL = 11, BGW_OPT_UPDATE_ITEMS = 12 };
 int bgw_set_option(bgw_ctx* ctx, int option, int64_t value);
 
 /* With BGW_OPT_TIMING = 1 the context records CUDA events around its main

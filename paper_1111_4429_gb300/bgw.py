@@ -39,6 +39,7 @@ BGW_OPT_UPDATE_SLICES = 8
 BGW_OPT_DOUBLE_FP32 = 9
 BGW_OPT_WAIT_LIMIT_NS = 10
 BGW_OPT_PAIR_KERNEL = 11
+BGW_OPT_UPDATE_ITEMS = 12
 BGW_FLAVOR_REAL = 0x100
 BGW_COULOMB_BULK, BGW_COULOMB_SPHERE, BGW_COULOMB_SLAB = 0, 1, 2
 COULOMB_MODELS = {"bulk": BGW_COULOMB_BULK, "sphere": BGW_COULOMB_SPHERE, "slab": BGW_COULOMB_SLAB}

@@ -375,6 +375,11 @@ int bgw_set_option(bgw_ctx* ctx, int option, int64_t value) {
     c->pair_kernel = (int)value;
     return BGW_OK;
   }
+  if (option == BGW_OPT_UPDATE_ITEMS) {
+    if (value < -1 || value > 1) return fail(c, BGW_EINVAL, "update items are -1, 0 or 1");
+    c->update_items = (int)value;
+    return BGW_OK;
+  }
   if (option == BGW_OPT_WAIT_LIMIT_NS) {
     if (value < 0 || value > 10000000000LL) return fail(c, BGW_EINVAL, "wait limit must be in [0, 1e10] ns");
     c->wait_ns = (unsigned long long)value;
@@ -568,7 +573,7 @@ int bgw_epsinv(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng, con
   // graph's edges replace the streams' event waits.
   uint64_t key = hash_bytes("epsinv", 6, hash_bytes(&nmat, sizeof(nmat)));
   key = hash_bytes(&st, sizeof(st), key);
-  const int modes[4] = {c->inverse_mode, c->update_slices, c->run_slices, c->run_ff_chain ? 1 : 0};
+  const int modes[5] = {c->inverse_mode, c->update_slices, c->run_slices, c->run_ff_chain ? 1 : 0, c->update_items};
   key = hash_bytes(modes, sizeof(modes), key);
   key = hash_bytes(ng, nmat * sizeof(int), key);
   key = hash_bytes(cells, nmat * sizeof(bgw_cell), key);
@@ -702,7 +707,8 @@ extern "C" int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* proble
   uint64_t key = hash_bytes(&nq, sizeof(nq), hash_bytes(&prec, sizeof(prec), hash_bytes(&nfreq, sizeof(nfreq))));
   if (nfreq > 0) key = hash_bytes(omega, nfreq * sizeof(double), key);
   key = hash_bytes(&st, sizeof(st), key);
-  const int modes[5] = {c->inverse_mode, c->head_mode, c->update_slices, c->double_fp32, c->pair_kernel};
+  const int modes[6] = {c->inverse_mode, c->head_mode, c->update_slices, c->double_fp32, c->pair_kernel,
+                         c->update_items};
   key = hash_bytes(modes, sizeof(modes), key);
   for (int q = 0; q < nq; ++q) {
     const bgw_problem& p = problems[q];
@@ -961,7 +967,8 @@ int epsilon_run(bgw_ctx* ctx, const bgw_cell* cell, int nv, int npw_v, const int
     if (nfreq > 0) key = hash_bytes(omega, nfreq * sizeof(double), key);
     const void* ptrs[5] = {cv, cc, chi, epsinv, (const void*)st};
     key = hash_bytes(ptrs, sizeof(ptrs), key);
-    const int modes[5] = {c->inverse_mode, c->head_mode, c->update_slices, c->double_fp32, c->pair_kernel};
+    const int modes[6] = {c->inverse_mode, c->head_mode, c->update_slices, c->double_fp32, c->pair_kernel,
+                         c->update_items};
     key = hash_bytes(modes, sizeof(modes), key);
     key = hash_bytes(gv, (size_t)npw_v * 12, key);
     key = hash_bytes(gc, (size_t)npw_c * 12, key);

@@ -544,6 +544,7 @@ int epsinv_batch_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* cel
       if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Cs.data(), Ps.data(), Ds.data(), oz.get(), false,
                            real_values, c->run_slices, c->run_ff_chain)) != BGW_OK)
         return rc;
+      oz_set_bulk_items(oz.get(), c->update_items);   // the option's width, else the SM-count rule
     }
     if (!tc_update) {
       for (int k0 = 0; k0 < ngmax; k0 += NB) {

@@ -414,6 +414,7 @@ int epsinv_general_run(Ctx* c, int nmat, const int* ng, const bgw_cell* const* c
       if ((rc = oz_prepare(c, nb, ngs.data(), As.data(), Rs.data(), Cs.data(), nullptr, oz.get(), true, false,
                            c->run_slices, c->run_ff_chain)) != BGW_OK)
         return rc;
+      oz_set_bulk_items(oz.get(), c->update_items);   // the option's width, else the SM-count rule
     }
     int* piv = ipiv.as<int>();
     int* src = piv + (size_t)kGB * ngmax;

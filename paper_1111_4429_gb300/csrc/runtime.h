@@ -130,6 +130,7 @@ struct Ctx {
   std::map<std::tuple<int, int, int, int>, int> tuned_ppb;  // (n, prec, nys, ncol) -> pairs per CTA
   bool autotune = true;
   int pair_kernel = -1;      // pair transform y,x kernel: -1 autotuned, 0 block, 1 warp per pair
+  int update_items = -1;     // bulk update items: -1 the SM-count rule, 0 wide, 1 two column tiles
   cudaStream_t side = nullptr;     // high-priority stream of the sweep's look-ahead chain
   cudaEvent_t la_ev[4] = {};       // look-ahead dependencies (fork, slice, rest x2)
   cudaStream_t copy_st = nullptr;  // host-to-device copies of bgw_epsilon's conduction chunks
@@ -324,6 +325,12 @@ int oz_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);
 // The Hermitian sweep's panel (C, P = C D^-1, A_RK <- P) and its slices in one launch.
 int oz_panel_slice(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, cudaStream_t st);
 int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaStream_t st);
+// Column tiles per work item of the bulk update launches (modes 0, 2, 3)
+// that follow: -1 the SM-count rule (items of 2 tiles where the slice
+// count's wider items would number no more than the SMs), 0 the wider
+// items, 1 items of 2 tiles.  Every tile's arithmetic is the same either
+// way (bit-identical results); only the speed changes.
+void oz_set_bulk_items(OzPlan* plan, int narrow);
 
 }  // namespace bgw
 

@@ -904,6 +904,7 @@ struct OzPlan {
   int slices = 7;         // slices per value the update uses (5 or 7)
   bool ff_chain = false;  // next diagonal block and panel product in double FP32
   bool real_values = false;  // every matrix real (real flavor): only the real-part MMAs
+  int bulk_narrow = -1;   // bulk items: -1 SM-count rule, 0 wide, 1 two column tiles
   int nmat = 0;
   int rows_total = 0;
   int max_tiles = 0;
@@ -1044,13 +1045,15 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
   // Column tiles per bulk work item: 4 with seven slices, 3 with five; 2
   // where those items would not exceed the SMs (each CTA then pipelines two
   // items instead of running one alone; measured with seven slices: N_G 2120
-  // 3.10 -> 2.95 ms per inverse, while at 7180 items of 4 stay best).
+  // 3.10 -> 2.95 ms per inverse, while at 7180 items of 4 stay best), unless
+  // the plan fixes the width (the context's timed choice or its option).
   const int nsm = sm_count(c);
   int wide = plan->slices < 7 ? 3 : kJPI;
   {
     const int nI = (ngmax + BM - 1) / BM, nJ = (ngmax + BN - 1) / BN, k1 = k0 + NB;
     grid = pipe_items(mode, wide, nI, nJ, k1 / BM, k1 < ngmax);
-    if (mode != 1 && (long long)grid * plan->nmat <= nsm) {
+    const bool narrow = plan->bulk_narrow >= 0 ? plan->bulk_narrow == 1 : (long long)grid * plan->nmat <= nsm;
+    if (mode != 1 && narrow) {
       wide = 2;
       grid = pipe_items(mode, wide, nI, nJ, k1 / BM, k1 < ngmax);
     }
@@ -1104,6 +1107,8 @@ int oz_update(Ctx* c, OzPlan* plan, int k0, int ngmax, int buf, int mode, cudaSt
   BGW_CUDA(c, cudaGetLastError());
   return BGW_OK;
 }
+
+void oz_set_bulk_items(OzPlan* plan, int narrow) { plan->bulk_narrow = narrow < 0 ? -1 : (narrow ? 1 : 0); }
 
 OzPlan* oz_plan_new() { return new OzPlan(); }
 void oz_plan_delete(OzPlan* p) { delete p; }

@@ -152,7 +152,8 @@ def test_chi_wait_limit_reports_timeout_and_context_recovers(ctx):
                                              ("BGW_OPT_DOUBLE_FP32", [2, -2], [-1, 0, 1]),
                                              ("BGW_OPT_SIGMA_DENSITY", [2, -2], [-1, 0, 1]),
                                              ("BGW_OPT_INVERSE", [2, -2], [-1, 0, 1]),
-                                             ("BGW_OPT_PAIR_KERNEL", [-2, 2, 11], [-1, 0, 1])])
+                                             ("BGW_OPT_PAIR_KERNEL", [-2, 2, 11], [-1, 0, 1]),
+                                             ("BGW_OPT_UPDATE_ITEMS", [-2, 2, 4], [-1, 0, 1])])
 def test_option_values(ctx, option, bad, good):
     """Values outside an option's documented set are refused (code 1) and
     leave the context usable; the documented ones are accepted."""

@@ -417,3 +417,32 @@ def test_epsinv_graph_replay_matches_direct(ctx, slices):
     assert results[1][1] == results[0][1] > 50   # a replay counts the graph's kernels
     assert g1[1] == g0[1] + 3                        # calls 2-4 replayed
     assert _rel(results[0][0], r["epsinv"]) <= TOL64 * (2 ** 14 if slices == 5 else 1)
+
+
+@pytest.mark.parametrize("slices,which", [(7, "one"), (7, "two"), (5, "one")])
+def test_epsinv_update_item_widths_bit_identical(ctx, slices, which):
+    """The bulk update's work-item width (the wide items or items of two
+    column tiles, BGW_OPT_UPDATE_ITEMS) only regroups tiles among CTAs: the
+    inverse is bit for bit the same under both and under the default rule,
+    and meets the oracle's bar."""
+    from paper_1111_4429_gb300 import bgw
+    systems = [synth.make_system("r", a=20.52, fft=40, ecut_wfn=8.0, ecut_eps=3.0, nv=4, nc=90, seed=88)]
+    if which == "two":
+        systems.append(synth.make_system("s", a=17.0, fft=40, ecut_wfn=8.0, ecut_eps=3.5, nv=4, nc=90, seed=89))
+    refs = [oracle.solve(s) for s in systems]
+    chis = [_dev(r["chi"]) for r in refs]
+    ctx.set_option(bgw.BGW_OPT_INVERSE, 1)
+    ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, slices)
+    try:
+        _, rule = _epsinv(ctx, systems, chis)
+        ctx.set_option(bgw.BGW_OPT_UPDATE_ITEMS, 0)
+        _, wide = _epsinv(ctx, systems, chis)
+        ctx.set_option(bgw.BGW_OPT_UPDATE_ITEMS, 1)
+        _, narrow = _epsinv(ctx, systems, chis)
+    finally:
+        ctx.set_option(bgw.BGW_OPT_UPDATE_ITEMS, -1)
+        ctx.set_option(bgw.BGW_OPT_INVERSE, -1)
+        ctx.set_option(bgw.BGW_OPT_UPDATE_SLICES, 0)
+    for r, a, w, n in zip(refs, rule, wide, narrow):
+        assert np.array_equal(a, w) and np.array_equal(n, w)
+        assert _rel(w, r["epsinv"]) <= TOL64 * (2 ** 14 if slices == 5 else 1)
