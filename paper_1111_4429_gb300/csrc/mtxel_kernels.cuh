@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && (LB || N <= 40)) ? 2 :
 // The low-band form of pair_yxpass with one warp per pair and no block-wide
 // barrier between the passes: the y pass over the N x columns (lane = x),
 // __syncwarp, then the x pass over the nys kept ky rows (lane = row), whose
-// kept columns go straight to T (a lane's columns are consecutive in T).  A
+// kept columns are staged over the warp's Y rows and stored to T in whole,
+// coalesced runs.  A
 // pair's two passes keep 32 lanes busy for 83 of 96 lane-lines at N = 60
 // instead of the block kernel's 332 of 512, and warps of a block move on
 // independently.  grid (ceil(npb / kPairWarps), N), block 32 kPairWarps.

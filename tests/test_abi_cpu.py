@@ -113,5 +113,6 @@ def test_binding_constants_match_the_header():
     for n in names:
         assert n in header, n
         assert getattr(bgw, n) == header[n], n
-    for n in ("BGW_OPT_UPDATE_SLICES", "BGW_OPT_DOUBLE_FP32", "BGW_OPT_SIGMA_DENSITY", "BGW_OPT_HEAD"):
+    for n in ("BGW_OPT_UPDATE_SLICES", "BGW_OPT_DOUBLE_FP32", "BGW_OPT_SIGMA_DENSITY", "BGW_OPT_HEAD",
+              "BGW_OPT_PAIR_KERNEL", "BGW_OPT_UPDATE_ITEMS", "BGW_OPT_WAIT_LIMIT_NS"):
         assert n in names
