@@ -1059,12 +1059,27 @@ def run_profile_case(args):
     c2      -- one solve of the large cell and spheres (60^3 grid, N_G =
                7180) with N_c = 100 (K = 10,800 pairs, M = 620 MB > L2, chi
                in chunks of 2048 pairs as at full size, the full N_G = 7180
-               inverse; about 4 GB on the device)."""
+               inverse; about 4 GB on the device);
+    mtxel_c2 -- the matrix elements alone of that case (mixed precision),
+               with the warp-per-pair y,x kernel that the autotuner picks on
+               the 60^3 grid at full size."""
     import torch
     from paper_1111_4429_gb300 import bgw, synth
     ctx = bgw.Context(0)
     case = args.profile_case
-    if case in ("solve", "c2"):
+    if case == "mtxel_c2":
+        s = synth.config_system("c2", nc=100)
+        cell = bgw.system_cell(s)
+        prec = bgw.PREC[args.prec]
+        ctx.set_option(bgw.BGW_OPT_PAIR_KERNEL, 1)
+        cv = torch.from_numpy(s.cv).cuda()
+        cc = torch.from_numpy(s.cc).cuda()
+        M = torch.empty((s.npairs, s.ng), dtype=torch.complex128 if prec == 0 else torch.complex64, device="cuda")
+        for _ in range(2):
+            ctx.mtxel(cell, s.gv, cv, s.gc, cc, s.geps, prec, M)
+        ctx.sync()
+        desc = "c2 cell, N_c=100, matrix elements, warp-per-pair kernel"
+    elif case in ("solve", "c2"):
         s = synth.config_system("c1", nc=200) if case == "solve" else synth.config_system("c2", nc=100)
         cell = bgw.system_cell(s)
         prec = bgw.PREC[args.prec]
@@ -1173,7 +1188,7 @@ def main():
     ap.add_argument("--skip-extra", action="store_true", help="skip the batched q x iw and served-stream parts")
     ap.add_argument("--serve-requests", type=int, default=200, help="requests of the served stream")
     ap.add_argument("--profile-case", nargs="?", const="solve", default=None,
-                    choices=["solve", "general", "w", "sigma", "c2"],
+                    choices=["solve", "general", "w", "sigma", "c2", "mtxel_c2"],
                     help="small case for ncu captures (solve: reduced c1 solve; general: one pivoted general "
                          "inverse; w: screened W on 8 matrices; sigma: one mixed Sigma call)")
     ap.add_argument("--item-widths", action="store_true",
