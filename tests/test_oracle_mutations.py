@@ -183,8 +183,47 @@ def _sigma_sx_screening_dropped(g_inner, c_inner, nocc, g_outer, c_outer, geps, 
                                  np.eye(len(v), dtype=np.complex128), v, cell_volume)
 
 
+def _slab_normal_x(bvec, q_frac, geps, model="bulk", rc=0.0):
+    if model != "slab":
+        return _ORIG["coulomb"](bvec, q_frac, geps, model, rc)
+    perm = np.asarray(bvec, dtype=np.float64)[:, [2, 1, 0]]   # the slab normal taken along x
+    return _ORIG["coulomb"](perm, q_frac, geps, model, rc)
+
+
+def _w_v_on_the_left(epsinv_asym, v):
+    return v[:, None] * epsinv_asym
+
+
+def _eps_asym_v_on_the_right(chi_m, v):
+    return np.eye(chi_m.shape[0], dtype=np.complex128) - chi_m * v[None, :]
+
+
+def _sigma_mtxel_plus_g(g_inner, c_inner, g_outer, c_outer, geps):
+    return _ORIG["mtxel_direct"](g_inner, c_inner, g_outer, c_outer, np.asarray(geps))
+
+
+def _density_reversed(g_outer, c_outer, deltas):
+    return _ORIG["density_diag"](g_outer, c_outer, -np.asarray(deltas))
+
+
+def _broadening_sign(ev, ec, energy, delta, advanced=False):
+    return _ORIG["chi_weights_real"](ev, ec, energy, -delta, advanced)
+
+
+def _pairs_c_major(gv, cv, gc, cc, geps, n, pairs):
+    nv, nc = cv.shape[0], cc.shape[0]
+    pairs = np.asarray(pairs, dtype=np.int64)
+    swapped = (pairs % nv) * nc + (pairs // nv) % nc
+    return _ORIG["mtxel_fft_pairs"](gv, cv, gc, cc, geps, n, swapped)
+
+
+def _realify_real_parts(c, energies, tol, rank_tol=1e-8):
+    r = np.asarray(c).real.copy()
+    return r / np.linalg.norm(r, axis=1, keepdims=True)
+
+
 _ORIG = {n: getattr(E, n) for n in ("mtxel_direct", "band_grids", "chi_direct", "chi_weights", "coulomb",
-                                     "chi_weights_real", "sigma_cohsex")}
+                                     "chi_weights_real", "sigma_cohsex", "density_diag", "mtxel_fft_pairs")}
 
 MISTAKES = {
     "product without the conjugate": [("mtxel_fft", _mtxel_fft_no_conj)],
@@ -205,6 +244,14 @@ MISTAKES = {
     "Coulomb hole without the 1/2": [("sigma_cohsex", _sigma_ch_prefactor)],
     "exchange sign flipped": [("sigma_cohsex", _sigma_x_sign)],
     "screened exchange unscreened": [("sigma_cohsex", _sigma_sx_screening_dropped)],
+    "slab normal along x": [("coulomb", _slab_normal_x)],
+    "W with v on the wrong side": [("screened_w", _w_v_on_the_left)],
+    "asymmetric eps with v on the right": [("eps_asym", _eps_asym_v_on_the_right)],
+    "Sigma matrix elements at +G": [("sigma_mtxel", _sigma_mtxel_plus_g)],
+    "band density at G' - G": [("density_diag", _density_reversed)],
+    "broadening with the wrong sign": [("chi_weights_real", _broadening_sign)],
+    "sampled pairs read conduction-major": [("mtxel_fft_pairs", _pairs_c_major)],
+    "real flavour from the real parts alone": [("realify", _realify_real_parts)],
 }
 
 
