@@ -116,3 +116,26 @@ def test_binding_constants_match_the_header():
     for n in ("BGW_OPT_UPDATE_SLICES", "BGW_OPT_DOUBLE_FP32", "BGW_OPT_SIGMA_DENSITY", "BGW_OPT_HEAD",
               "BGW_OPT_PAIR_KERNEL", "BGW_OPT_UPDATE_ITEMS", "BGW_OPT_WAIT_LIMIT_NS"):
         assert n in names
+
+
+def test_frequency_grid_error_codes():
+    """The documented codes of bgw_frequency_grid: EINVAL for a negative low
+    cutoff or more than 2^24 points, ENOMEM for a short output (the count is
+    still written, nothing past max_points), and a NULL output to count."""
+    import ctypes
+    import numpy as np
+    from paper_1111_4429_gb300 import bgw
+    lib = bgw.load()
+    d = ctypes.c_double
+    n = ctypes.c_int(-1)
+    assert lib.bgw_frequency_grid(d(0.1), d(-0.5), d(2.0), d(0.1), 0, None, ctypes.byref(n)) == bgw.BGW_EINVAL
+    assert lib.bgw_frequency_grid(d(1e-9), d(1.0), d(1.0), d(0.0), 0, None, ctypes.byref(n)) == bgw.BGW_EINVAL
+    assert lib.bgw_frequency_grid(d(0.1), d(0.5), d(2.0), d(0.1), 0, None, ctypes.byref(n)) == bgw.BGW_OK
+    full = n.value
+    assert full == len(bgw.frequency_grid(0.1, 0.5, 2.0, 0.1))
+    out = np.full(full, -7.0)
+    n2 = ctypes.c_int(-1)
+    rc = lib.bgw_frequency_grid(d(0.1), d(0.5), d(2.0), d(0.1), full - 2,
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(n2))
+    assert rc == bgw.BGW_ENOMEM and n2.value == full
+    assert np.all(out[full - 2:] == -7.0)
