@@ -322,8 +322,11 @@ int bgw_screened_w(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
                    const int32_t* const* geps, const void* const* epsinv,
                    void* const* W, void* stream);
 
-/* bgw_epsinv_rflavor -- bgw_epsinv for the real flavor: chi[i], eps[i] (or
- * NULL) and epsinv[i] are real double [ng[i]][ng[i]], symmetric.            */
+/* bgw_epsinv_rflavor -- bgw_epsinv for the real flavor (Section "Real and
+ * complex flavors": with inversion and time-reversal symmetry the
+ * coefficients, M, chi and eps are real; Eq. epsilon as for bgw_epsinv):
+ * chi[i], eps[i] (or NULL) and epsinv[i] are real double [ng[i]][ng[i]],
+ * symmetric.  Errors as bgw_epsinv.                                        */
 int bgw_epsinv_rflavor(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int* ng,
                        const int32_t* const* geps, const void* const* chi,
                        void* const* eps, void* const* epsinv, void* stream);
@@ -440,7 +443,12 @@ int bgw_epsilon_batch(bgw_ctx* ctx, int nq, const bgw_problem* problems,
 
 /* ------------------------------------------------------------------------
  * Serving: a stream of independent eps~^-1 requests of different sizes.
- * The server keeps max_slots requests in flight, each on its own CUDA
+ * Each request is one q-point's whole path; the paper notes that Eq.
+ * eqn_static_xi separates in q, so q-points run as independent epsilon
+ * calculations (Section "Parallelization and Performance", epsilon), and
+ * that each run estimates the memory its largest arrays need against what
+ * is available (Section "Memory estimation"): the server admits a request
+ * against such an estimate.  The server keeps max_slots requests in flight, each on its own CUDA
  * stream and context; a request waiting in the FIFO is admitted as soon as
  * a slot is free and its device-memory estimate fits in what the HBM budget
  * has left, so its work overlaps with the requests already running
@@ -499,14 +507,17 @@ int bgw_serve_close(bgw_server* srv);
 
 /* ------------------------------------------------------------------------
  * bgw_epsilon -- the whole path for one q-point and nfreq frequencies
- * (nfreq = 0: static): bgw_mtxel, bgw_chi_sum over conduction chunks of at
+ * (nfreq = 0: static), the three steps of Section "RPA Dielectric Matrix:
+ * epsilon" (Eqs. eqn_matrix_elem, eqn_static_xi / eqn_static_xi_compact,
+ * epsilon): bgw_mtxel, bgw_chi_sum over conduction chunks of at
  * most `nc_chunk` bands (0 = all at once), then bgw_epsinv per frequency.
  * Bulk inputs (cv, cc) and outputs (chi, epsinv) may be host or device
  * memory (detected per pointer); host buffers are copied inside the call
  * and the call then returns after the results are back on the host.
  *   chi     c128 [max(1,nfreq)][ng][ng] or NULL (not returned)
  *   epsinv  c128 [max(1,nfreq)][ng][ng]
- * The library holds M and the chi accumulator in its own scratch memory.  */
+ * The library holds M and the chi accumulator in its own scratch memory.
+ * Errors as the three calls it makes.                                      */
 int bgw_epsilon(bgw_ctx* ctx, const bgw_cell* cell,
                 int nv, int npw_v, const int32_t* gv, const void* cv,
                 const double* ev,
@@ -545,8 +556,9 @@ int bgw_epsinv_general(bgw_ctx* ctx, int nmat, const bgw_cell* cells, const int*
                        const int32_t* const* geps, const void* const* chi,
                        void* const* eps, void* const* epsinv, void* stream);
 
-/* bgw_epsilon_real -- bgw_epsilon on the real axis: bgw_mtxel,
- * bgw_chi_sum_real over conduction chunks, bgw_epsinv_general per frequency.
+/* bgw_epsilon_real -- bgw_epsilon on the real axis (Eq.
+ * retarded_advanced_epsilon): bgw_mtxel, bgw_chi_sum_real over conduction
+ * chunks, bgw_epsinv_general per frequency.
  * chi and epsinv are c128 [nfreq][ng][ng]; other arguments as bgw_epsilon
  * and bgw_chi_sum_real.                                                    */
 int bgw_epsilon_real(bgw_ctx* ctx, const bgw_cell* cell,
