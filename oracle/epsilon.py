@@ -92,7 +92,9 @@ def mtxel_direct(gv: np.ndarray, cv: np.ndarray, gc: np.ndarray, cc: np.ndarray,
 
 
 def band_grids(g: np.ndarray, c: np.ndarray, n: int) -> np.ndarray:
-    """u_b(r_j) = sum_G c_b(G) e^{+2 pi i G.j/n} on the n^3 grid (unnormalized).
+    """u_b(r_j) = sum_G c_b(G) e^{+2 pi i G.j/n} on the n^3 grid (unnormalized):
+    the bands in real space, the first step of the FFT form of the matrix
+    elements (the unnumbered equation after Eq. eqn_matrix_elem).
 
     Returns complex128 [nb][n][n][n] indexed [b][jx][jy][jz].
     """
@@ -104,7 +106,8 @@ def band_grids(g: np.ndarray, c: np.ndarray, n: int) -> np.ndarray:
 
 
 def mtxel_fft_pairs(gv, cv, gc, cc, geps, n: int, pairs: Sequence[int]) -> np.ndarray:
-    """Tier 2 for a subset of pairs p = v*nc + c (rows of M in that order)."""
+    """Tier 2 (the FFT form after Eq. eqn_matrix_elem, as in mtxel_fft) for a
+    subset of pairs p = v*nc + c (rows of M in that order)."""
     nc = cc.shape[0]
     pairs = np.asarray(pairs, dtype=np.int64)
     vs = np.unique(pairs // nc)
@@ -176,7 +179,8 @@ def chi(M: np.ndarray, w: np.ndarray, cell_volume: float) -> np.ndarray:
 
 def chi_entries(M_rows_g: np.ndarray, M_rows_gp: np.ndarray, w: np.ndarray,
                 cell_volume: float) -> np.ndarray:
-    """chi restricted to given G (columns of M_rows_g) and G' (columns of M_rows_gp)."""
+    """Eq. eqn_static_xi_compact restricted to given G (columns of M_rows_g)
+    and G' (columns of M_rows_gp), with the 4/Omega of chi."""
     return (4.0 / cell_volume) * (np.conj(M_rows_g).T @ (w[:, None] * M_rows_gp))
 
 
@@ -347,7 +351,8 @@ def inv_gauss_jordan(a: np.ndarray) -> np.ndarray:
 
 
 def inv(a: np.ndarray) -> np.ndarray:
-    """Tier 2 inverse: library LU (numpy.linalg.inv)."""
+    """Tier 2 inverse: library LU (numpy.linalg.inv; the paper inverts eps
+    with LAPACK's ZGESV, Section "RPA Dielectric Matrix: epsilon")."""
     return np.linalg.inv(a)
 
 
@@ -370,7 +375,9 @@ def sigma_mtxel(g_inner, c_inner, g_outer, c_outer, geps) -> np.ndarray:
 
 
 def density_diag(g_outer, c_outer, deltas) -> np.ndarray:
-    """rho_n(D) = M_nn(k, q = 0, D) = sum_{G2} conj(c_n(D + G2)) c_n(G2), [n][len(deltas)]."""
+    """rho_n(D) = M_nn(k, q = 0, D) = sum_{G2} conj(c_n(D + G2)) c_n(G2), [n][len(deltas)]:
+    the band density of Eq. cohsex-ch-exact, the matrix element of Eq.
+    eqn_matrix_elem of a band with itself at q = 0."""
     out = np.empty((c_outer.shape[0], len(deltas)), dtype=np.complex128)
     for n in range(c_outer.shape[0]):
         out[n] = mtxel_direct(g_outer, c_outer[n:n + 1], g_outer, c_outer[n:n + 1], deltas)[0]
