@@ -1,4 +1,6 @@
-// In-register mixed-radix FFT of one line per thread (radices 2, 3, 4, 5).
+// In-register mixed-radix FFT of one line per thread (radices 2, 3, 4, 5),
+// the 1D transforms of the matrix elements' FFT form (the unnumbered
+// equation after Eq. eqn_matrix_elem).
 //
 // The line length N is a compile-time constant, so every loop below unrolls
 // completely and every array index is static: the line lives in registers.

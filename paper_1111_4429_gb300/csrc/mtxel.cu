@@ -1,5 +1,6 @@
-// Host side of the matrix-element step: plans of the pruned transforms and
-// the scratch layout of one evaluation (kernels in mtxel_kernels.cuh).
+// Host side of the matrix-element step (Eq. eqn_matrix_elem, evaluated by
+// the FFT form that follows it): plans of the pruned transforms and the
+// scratch layout of one evaluation (kernels in mtxel_kernels.cuh).
 #include <algorithm>
 #include <map>
 #include <vector>

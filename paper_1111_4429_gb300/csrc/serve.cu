@@ -1,4 +1,9 @@
-// Serving loop for eps~^-1 requests (bgw_serve_* in include/bgw.h).
+// Serving loop for eps~^-1 requests (bgw_serve_* in include/bgw.h).  Each
+// request is one q-point's whole path: Eq. eqn_static_xi separates in q,
+// so q-points are independent epsilon calculations (Section "Parallelization
+// and Performance"); requests are admitted against an estimate of their
+// largest arrays, as each of the paper's runs estimates its memory needs
+// (Section "Memory estimation").
 //
 // A scheduler thread owns `max_slots` slots; each slot is a context (its own
 // scratch pool, plans and tuning) with its own CUDA stream.  Requests are

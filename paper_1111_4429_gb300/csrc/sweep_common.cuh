@@ -1,5 +1,5 @@
 // Sweep of one diagonal block in shared memory (the diagonal step of both
-// sweeps in epsinv.cu).
+// sweeps in epsinv.cu, which invert eps~ of Eq. epsilon).
 //
 // D (Hermitian positive definite, kb <= 32) is held as its lower triangle
 // L[i][j], i >= j.  Pivot s: every lower element outside row/column s loses

@@ -1,5 +1,8 @@
 // Trailing update of the Hermitian sweep on the tensor cores with FP64-level
-// accuracy (error-free splitting of the operands, the Ozaki scheme).
+// accuracy (error-free splitting of the operands, the Ozaki scheme).  The
+// sweep inverts eps~ = I - v^1/2 chi v^1/2 (Eq. epsilon in its symmetric
+// form; the paper inverts eps with LAPACK's ZGESV, Section "RPA Dielectric
+// Matrix: epsilon").
 //
 // Each sweep step subtracts the rank-kb product P C^H from the lower triangle
 // (kb <= 32).  With u_i = [Re P_i, Im P_i] and v_j = [Re C_j, Im C_j] (64 real
