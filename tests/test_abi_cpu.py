@@ -139,3 +139,16 @@ def test_frequency_grid_error_codes():
                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(n2))
     assert rc == bgw.BGW_ENOMEM and n2.value == full
     assert np.all(out[full - 2:] == -7.0)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with the shared library missing, loading the binding
+    raises instead of computing anything another way."""
+    import pytest
+    from paper_1111_4429_gb300 import bgw
+    monkeypatch.setattr(bgw, "_lib", None)
+    monkeypatch.setattr(bgw, "LIB_PATH", str(tmp_path / "libbgw.so"))
+    with pytest.raises(ImportError):
+        bgw.load()
+    with pytest.raises(ImportError):
+        bgw.frequency_grid(0.1, 0.5, 2.0, 0.1)
